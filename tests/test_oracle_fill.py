@@ -1,0 +1,142 @@
+"""Pins of the oracle's EFIE Z entries: RWG construction, brute-force
+high-order quadrature (regular and near pairs), Galerkin symmetry, and the
+table-vs-direct agreement the paper reports (Section IV.B)."""
+import math
+
+import numpy as np
+import pytest
+
+import brute as B
+import oracle as O
+import workloads as W
+
+K = 2 * math.pi
+
+
+def diamonds(size=0.01, gap=0.5):
+    # two 2-triangle "diamonds", each with one interior edge, gap apart
+    a = np.array([[0, 0, 0], [size, 0, 0], [0, size, 0], [size, size, 0.2 * size]])
+    b = a + np.array([gap, 0.3 * gap, 0.1 * gap])
+    xyz = np.concatenate([a, b])
+    tri = np.array([[0, 1, 2], [1, 3, 2], [4, 5, 6], [5, 7, 6]], dtype=np.int32)
+    return xyz, tri
+
+
+def test_rwg_edges_match_convention():
+    for wl in (W.plate_280(), W.sphere_3072()):
+        m = O.Mesh(wl.xyz, wl.tri)
+        ev, et = m.edges()
+        ref = B.rwg(wl.xyz, wl.tri.tolist())
+        assert m.ne == len(ref)
+        np.testing.assert_array_equal(ev, [e[0] for e in ref])
+        np.testing.assert_array_equal(et, [(e[1], e[2]) for e in ref])
+    assert O.Mesh(*W.icosphere(2)).ne == 3 * 320 // 2
+
+
+def test_bad_meshes_rejected():
+    xyz = np.zeros((4, 3))
+    with pytest.raises(ValueError):
+        O.Mesh(xyz, np.array([[0, 1, 1]], dtype=np.int32))
+    with pytest.raises(ValueError):  # three triangles on one edge
+        O.Mesh(xyz, np.array([[0, 1, 2], [0, 1, 3], [1, 0, 2]], dtype=np.int32))
+
+
+def test_regular_entry_vs_brute_force():
+    # the m-point rule on both triangles vs the same outer rule with a
+    # 3 x 16^2-point Duffy rule inside: the difference is the inner rule's
+    # error, which must be small and shrink quickly with the triangle size h
+    edges = None
+    errs = {}
+    for rule, tol in ((3, 1e-5), (4, 1e-7), (6, 1e-9), (7, 1e-11)):
+        for size in (0.01, 0.005):
+            xyz, tri = diamonds(size)
+            m = O.Mesh(xyz, tri)
+            assert m.ne == 2 and not m.is_near(0, 2)
+            edges = B.rwg(xyz, tri.tolist())
+            z = m.z_entries(K, rule, [0, 1], [1, 0])
+            ref = B.entry_brute(xyz, tri.tolist(), edges, 0, 1, K, O.rule(rule), "gauss", 16)
+            errs[rule, size] = abs(z[0] - ref) / abs(ref)
+            assert errs[rule, size] <= tol, (rule, size, errs[rule, size])
+            # symmetric to rounding of the (much larger) terms of the integrand
+            assert abs(z[1] - z[0]) <= 1e-10 * abs(ref)
+    for rule in (3, 4, 6):
+        assert errs[rule, 0.01] / errs[rule, 0.005] > 3.0
+
+
+def test_near_entries_vs_brute_force():
+    wl = W.plate_280()
+    m = O.Mesh(wl.xyz, wl.tri)
+    edges = B.rwg(wl.xyz, wl.tri.tolist())
+    ev, et = m.edges()
+    # entries whose four triangle pairs are all near pairs
+    rng = np.random.default_rng(5)
+    pairs = [(0, 0), (10, 10), (10, 11), (40, 41)]
+    while len(pairs) < 10:
+        a, b = (int(x) for x in rng.integers(0, m.ne, 2))
+        if all(m.is_near(p, q) for p in et[a] for q in et[b]):
+            pairs.append((a, b))
+    for (a, b) in pairs:
+        assert all(m.is_near(p, q) for p in et[a] for q in et[b])
+    for (a, b) in pairs:
+        ref = B.entry_brute(wl.xyz, wl.tri.tolist(), edges, a, b, K, O.rule(3), "singular", 24)
+        z32 = m.z_entries(K, 3, [a], [b], nphi=32, nl=32)[0]
+        z8 = m.z_entries(K, 3, [a], [b])[0]
+        assert abs(z32 - ref) <= 1e-9 * abs(ref), (a, b, z32, ref)
+        assert abs(z8 - ref) <= 1e-4 * abs(ref), (a, b, z8, ref)
+
+
+def test_galerkin_symmetry_of_regular_entries():
+    xyz, tri = W.octasphere(2, 1.0)
+    xyz = W.jitter(xyz, tri, 0.02, 11)
+    m = O.Mesh(xyz, tri)
+    Z = m.z_full(K, 6)
+    ev, et = m.edges()
+    regular = np.ones((m.ne, m.ne), bool)
+    for i in range(m.ne):
+        for j in range(m.ne):
+            regular[i, j] = not any(m.is_near(p, q) for p in et[i] for q in et[j])
+    assert regular.sum() > 0.5 * m.ne**2
+    d = np.abs(Z - Z.T)[regular].max()
+    assert d <= 1e-13 * np.abs(Z).max()
+    # near entries are not symmetric (outer rule vs exact inner), but close
+    assert np.linalg.norm(Z - Z.T) <= 1e-2 * np.linalg.norm(Z)
+
+
+def test_table_vs_direct_z_matches_paper_order():
+    # Section IV.B: element-wise relative error of the table fill vs the
+    # analytical fill reaches ~1e-5 (Re) / 1e-6 (Im) for the EFIE
+    wl = W.plate_280()
+    m = O.Mesh(wl.xyz, wl.tri)
+    lo, hi = m.range(3)
+    g, e = O.make_tables(K, lo, hi)
+    Zd = m.z_full(K, 3)
+    Zt = m.z_full(K, 3, mode="table", tables=(g, e))
+    rel = np.linalg.norm(Zt - Zd) / np.linalg.norm(Zd)
+    assert 1e-9 < rel < 1e-5
+    assert np.abs(Zt - Zd).max() < 1e-5 * np.abs(Zd).max()
+
+
+def test_range_is_brute_force_min_max():
+    xyz, tri = W.octasphere(1, 1.0)
+    m = O.Mesh(xyz, tri)
+    lo, hi = m.range(4)
+    b, _ = O.rule(4)
+    pts = np.einsum("aj,tjc->tac", b, xyz[tri])
+    R = []
+    for p in range(len(tri)):
+        for q in range(len(tri)):
+            if not set(tri[p]) & set(tri[q]):
+                R.append(np.linalg.norm(pts[p][:, None] - pts[q][None], axis=2).ravel())
+    R = np.concatenate(R)
+    assert lo == R.min() and hi == R.max()
+
+
+def test_near_dist_criterion():
+    wl = W.cube_73728(4)
+    m0 = O.Mesh(wl.xyz, wl.tri)
+    m1 = O.Mesh(wl.xyz, wl.tri, near_dist=0.8)
+    cen = wl.xyz[wl.tri].mean(axis=1)
+    for p, q in [(0, 1), (0, 40), (3, 90), (17, 170)]:
+        share = bool(set(wl.tri[p]) & set(wl.tri[q]))
+        assert m0.is_near(p, q) == share
+        assert m1.is_near(p, q) == (share or np.linalg.norm(cen[p] - cen[q]) < 0.8)
