@@ -1,0 +1,162 @@
+/* gfmom: GB300 (sm_103a) method-of-moments impedance-matrix fill with the
+ * adaptive interpolation tables of Yang & Su, "Fast Green Function
+ * Evaluation for Method of Moment".
+ *
+ * Operator (Section II.A, Section IV.B: EFIE "L" operator, RWG basis on
+ * planar triangles, Galerkin testing), e^{jwt} convention:
+ *   Z_mn = jk eta int_{T_m} int_{T_n} [f_m . f_n - (1/k^2) div f_m div' f_n]
+ *          e^{-jkR} / (4 pi R) dS' dS.
+ * Regular triangle pairs use the m-point rule on both triangles with
+ * e^{-jkR}/R from the Lagrange table (Eq. 3, 5) or from sincos/exp; near pairs
+ * (sharing a vertex, or centroids closer than near_dist) use singularity
+ * cancellation with an angular transformation in FP64, with e^{-jkR} on the
+ * source edges from the linear table (Eq. 3, 4) when r_min <= R <= r_max
+ * (Section II.C), else directly.
+ *
+ * Conventions
+ *   - RWG unknown n = the n-th interior edge in lexicographic order of its
+ *     (lower, higher) vertex-index pair; T+ = the adjacent triangle with the
+ *     smaller index. Boundary edges carry no unknown; an edge shared by more
+ *     than two triangles is an error.
+ *   - Z is row-major on the device: Z[m * ldz + n] = Z_mn (test edge m,
+ *     source edge n), ldz >= ne, complex64 (GF_FP32) or complex128 (GF_FP64)
+ *     as interleaved (re, im).
+ *   - Device pointers, sizes and the stream are the caller's; the caller owns
+ *     every buffer it passes. The library owns its handles and the device
+ *     memory inside them (geometry, near lists, table images), released by
+ *     the matching *_destroy. Handles are bound to the device that was
+ *     current at creation; calls must be made with that device current.
+ *   - Calls that launch kernels are asynchronous on `stream` (a cudaStream_t,
+ *     NULL = legacy default stream) unless stated otherwise.
+ *   - Every call returns GF_OK or a negative status; gf_last_error() gives the
+ *     message of the calling thread's last failure. Nothing is thrown across
+ *     the ABI.
+ */
+#ifndef GFMOM_H
+#define GFMOM_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int gf_status;
+#define GF_OK 0
+#define GF_ERR_ARG (-1)     /* invalid argument (null pointer, bad size, bad option) */
+#define GF_ERR_MESH (-2)    /* degenerate / non-manifold mesh, bad vertex index */
+#define GF_ERR_RANGE (-3)   /* no regular pair, or a table that would be too large */
+#define GF_ERR_CUDA (-4)    /* a CUDA runtime call failed */
+#define GF_ERR_ALLOC (-5)   /* device or host allocation failed */
+#define GF_ERR_DEVICE (-6)  /* handle used with another device current */
+
+#define GF_FP32 32          /* FP32 quadrature with Kahan outer sums, complex64 Z */
+#define GF_FP64 64          /* FP64 throughout, complex128 Z */
+
+#define GF_GREEN 1          /* e^{-jkr}/r, Lagrange table */
+#define GF_EXP 0            /* e^{-jkr}, linear table */
+
+typedef struct gf_mesh gf_mesh;
+typedef struct gf_table gf_table;
+
+typedef struct {
+  int rule;                   /* points per triangle: 1, 3, 4, 6, 7 (Dunavant)          */
+  double table_tol;           /* relative tolerance of both tables (default 1e-6)       */
+  int green_n_per_lambda;     /* Green table base samples per wavelength, Eq. (2) (1000)*/
+  int exp_n_per_lambda;       /* Exp table samples per wavelength; 0 = smallest multiple
+                                 of 4 in [1000, 10000] with (k t)^2/8 <= tol, Eq. (10)   */
+  int lagrange_degree;        /* degree n of Eq. (5) for the Green table (3)            */
+  int refine;                 /* local refinement + forced zeros, Section II.B (1)      */
+  double refine_factor;       /* refined spacing / t (0.5)                              */
+  double refine_halfwidth_t;  /* refinement window |r - z| <= this * t (2.0 = "4t")     */
+  double merge_t;             /* samples closer than this * t to a zero are dropped (0.25) */
+  int grade;                  /* bisect intervals whose Eq. (11) bound exceeds tol (1)  */
+  int nphi;                   /* angular points per source edge, near pairs (8)         */
+  int nl;                     /* line points per source edge, near pairs (8)            */
+  double eta;                 /* wave impedance (376.730313668)                         */
+} gf_params;
+
+/* Fills *p with the defaults listed above. */
+void gf_params_default(gf_params* p);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* gf_last_error(void);
+
+/* ---------------------------------------------------------------- mesh ---
+ * xyz: host [nv][3] float64, tri: host [nt][3] int32 (copied). Builds the RWG
+ * edges and the near-pair lists on the host, uploads the geometry to the
+ * current device (synchronous). near_dist > 0 adds every pair of triangles
+ * whose centroids are closer than near_dist to the vertex-sharing near pairs.
+ * Errors: GF_ERR_ARG (null, nv < 3, nt < 1), GF_ERR_MESH (index out of range,
+ * repeated vertex in a triangle, edge shared by more than two triangles),
+ * GF_ERR_CUDA / GF_ERR_ALLOC. */
+gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt,
+                         double near_dist, gf_mesh** out);
+
+/* Sizes: vertices, triangles, RWG edges, ordered near pairs (p, q) (any may be NULL). */
+gf_status gf_mesh_info(const gf_mesh* m, int64_t* nv, int64_t* nt, int64_t* ne, int64_t* n_near);
+
+/* Host copies: edge_verts [ne][2] (lower, higher), edge_tris [ne][2] (T+, T-);
+ * either may be NULL. */
+gf_status gf_mesh_edges(const gf_mesh* m, int32_t* edge_verts, int32_t* edge_tris);
+
+/* Replaces the vertex coordinates (host [nv][3] float64, same topology) and
+ * re-uploads the geometry (synchronous). Near lists are kept. */
+gf_status gf_mesh_set_vertices(gf_mesh* m, const double* xyz);
+
+gf_status gf_mesh_destroy(gf_mesh* m);
+
+/* ---------------------------------------------------------------- range --
+ * Minimum and maximum distance between integration points of the `rule` over
+ * all regular (not near) triangle pairs: the table range of Section II.B
+ * (abstract: "the maximum and minimum distance between any two integration
+ * points"). GF_FP64 reduces FP64 distances; GF_FP32 screens with FP32
+ * distances and reports the FP64 distance of the extremal point pairs.
+ * Runs on the device on `stream`, then synchronizes it and writes the two
+ * host doubles. GF_ERR_RANGE if every pair is near. */
+gf_status gf_range(const gf_mesh* m, int rule, int precision, double* r_min, double* r_max,
+                   void* stream);
+
+/* ---------------------------------------------------------------- tables -
+ * Builds the Green (Lagrange, Eq. 3 + 5) and Exp (linear, Eq. 3 + 4) tables
+ * of Section II.B-C over [r_min, r_max] for wavenumber k: sample positions on
+ * the host in FP64 (uniform t from r_min, refinement near the zeros of the
+ * real and imaginary parts, forced zeros, Eq. (11) grading), then sample
+ * values, per-interval polynomial coefficients (FP64 and FP32 images) and the
+ * hash array of Eq. (6) by kernels on `stream` (the call synchronizes it).
+ * Errors: GF_ERR_ARG (k <= 0, r_min <= 0, r_max <= r_min, bad params),
+ * GF_ERR_RANGE (more than 2^26 samples or hash cells). */
+gf_status gf_table_create(double k, double r_min, double r_max, const gf_params* p, void* stream,
+                          gf_table** out);
+
+/* kind = GF_GREEN or GF_EXP: number of samples, hash cells, hash cell width
+ * (= smallest sample spacing); any output may be NULL. */
+gf_status gf_table_info(const gf_table* t, int kind, int64_t* n_nodes, int64_t* n_hash, double* dr);
+
+/* Host copies of one table: sample positions r [n_nodes], sample values
+ * (fre, fim) [n_nodes] and the hash array [n_hash]; any may be NULL. */
+gf_status gf_table_nodes(const gf_table* t, int kind, double* r, double* fre, double* fim,
+                         int32_t* hash);
+
+/* Device lookup of n distances: r_dev is float (GF_FP32) or double (GF_FP64),
+ * out_dev is interleaved complex of the same type: the table's f(r) (Green:
+ * e^{-jkr}/r, Exp: e^{-jkr}, without 1/(4 pi)). Points outside [r_min, r_max]
+ * are clamped to the first / last interval. Asynchronous on `stream`. */
+gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* r_dev, int64_t n,
+                        void* out_dev, void* stream);
+
+gf_status gf_table_destroy(gf_table* t);
+
+/* ---------------------------------------------------------------- fill ---
+ * Fills Z (device, row-major, ld = ldz) for wavenumber k. table == NULL
+ * selects direct evaluation (sincos / exp) everywhere; otherwise regular
+ * pairs use its Green table and near pairs its Exp table (the table must
+ * cover the range of gf_range for this mesh and rule; distances outside it
+ * fall back to direct evaluation in the near-pair path). precision GF_FP32
+ * (complex64 Z) or GF_FP64 (complex128 Z). Z is overwritten. Asynchronous on
+ * `stream`. */
+gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
+                  int precision, void* Z_dev, int64_t ldz, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,684 @@
+// gfmom host side: errors, quadrature rules, mesh topology (RWG edges, near
+// pairs), table sample placement (FP64), and the C-ABI entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "gf_internal.h"
+
+namespace gf {
+
+static thread_local std::string g_err;
+
+gf_status fail(gf_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+gf_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? GF_ERR_ALLOC : GF_ERR_CUDA;
+}
+
+// Dunavant rules. Degree 2 (3 points), 3 (4 points, negative centroid
+// weight), 4 (6 points), 5 (7 points, Radon's closed form in sqrt 15).
+bool rule_points(int npts, double bary[][3], double* w) {
+  int n = 0;
+  auto one = [&](double a, double b, double c, double wt) {
+    bary[n][0] = a;
+    bary[n][1] = b;
+    bary[n][2] = c;
+    w[n] = wt;
+    ++n;
+  };
+  auto s21 = [&](double a, double wt) {  // orbit of (1-2a, a, a)
+    one(1.0 - 2.0 * a, a, a, wt);
+    one(a, 1.0 - 2.0 * a, a, wt);
+    one(a, a, 1.0 - 2.0 * a, wt);
+  };
+  if (npts == 1) {
+    one(1.0 / 3, 1.0 / 3, 1.0 / 3, 1.0);
+  } else if (npts == 3) {
+    s21(1.0 / 6, 1.0 / 3);
+  } else if (npts == 4) {
+    one(1.0 / 3, 1.0 / 3, 1.0 / 3, -27.0 / 48);
+    s21(0.2, 25.0 / 48);
+  } else if (npts == 6) {
+    s21(0.44594849091596488632, 0.22338158967801146570);
+    s21(0.091576213509770743460, 0.10995174365532186764);
+  } else if (npts == 7) {
+    const double r15 = std::sqrt(15.0);
+    one(1.0 / 3, 1.0 / 3, 1.0 / 3, 0.225);
+    s21((6.0 - r15) / 21.0, (155.0 - r15) / 1200.0);
+    s21((6.0 + r15) / 21.0, (155.0 + r15) / 1200.0);
+  } else {
+    return false;
+  }
+  return true;
+}
+
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on the three-term
+// recurrence of P_n.
+static void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), d = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      d = n * (z * p1 - p2) / (z * z - 1.0);
+      double dz = p1 / d;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p1 = 1.0, p2 = 0.0;
+    for (int j = 1; j <= n; ++j) {
+      double p3 = p2;
+      p2 = p1;
+      p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+    }
+    d = n * (z * p1 - p2) / (z * z - 1.0);
+    double wt = 2.0 / ((1.0 - z * z) * d * d);
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = wt;
+    w[n - 1 - i] = wt;
+  }
+  if (n % 2) x[n / 2] = 0.0;
+}
+
+// ---------------------------------------------------------------- table samples
+struct Placement {
+  std::vector<double> r;
+  std::vector<int8_t> zflag;
+  double dr;
+  int64_t n_hash;
+};
+
+static double fact(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= i;
+  return f;
+}
+
+// Eq. (11) bound of interval j relative to min |f| on it (see gf_table_create).
+static double eq11_rel(const std::vector<double>& r, int j, int deg, int kind, double k) {
+  const int n = (int)r.size();
+  int s0 = deg <= 1 ? j : std::min(std::max(j - (deg - 1) / 2, 0), n - 1 - deg);
+  const double h = r[j + 1] - r[j];
+  double om = h * h / 4.0;
+  for (int s = s0; s <= s0 + deg; ++s)
+    if (s != j && s != j + 1) om *= std::max(std::fabs(r[j] - r[s]), std::fabs(r[j + 1] - r[s]));
+  const int q = deg + 1;
+  double mq = 0.0;
+  if (kind == GF_EXP) {
+    mq = std::pow(k, q);
+  } else {
+    for (int i = 0; i <= q; ++i)
+      mq += fact(q) / (fact(i) * fact(q - i)) * std::pow(k, q - i) * fact(i) / std::pow(r[s0], i + 1);
+  }
+  double b = om * mq / fact(q);
+  return kind == GF_GREEN ? b * r[j + 1] : b;
+}
+
+static gf_status place_samples(int kind, int deg, double k, double lo, double hi, double t,
+                               const gf_params& p, Placement* out) {
+  const double merge = p.merge_t * t;
+  const double hw = p.refine_halfwidth_t * t;
+  // uniform samples from r_min with spacing t (Eq. 2); r_max is a sample
+  std::vector<double> base;
+  for (int64_t i = 0;; ++i) {
+    const double x = lo + (double)i * t;
+    if (x >= hi) break;
+    base.push_back(x);
+    if (base.size() > (1u << 26)) return fail(GF_ERR_RANGE, "table: too many samples");
+  }
+  if (base.size() > 1 && hi - base.back() < merge) base.pop_back();
+  base.push_back(hi);
+  std::vector<double> all = base;
+  std::vector<double> zeros;
+  const double lam = 2.0 * kPi / k;
+  const double quarter = lam / 4.0;
+  if (p.refine) {
+    // zeros of Re / Im of e^{-jkr} (and of e^{-jkr}/r): r = q lambda / 4
+    for (int64_t q = 1;; ++q) {
+      const double z = (double)q * quarter;
+      if (z >= hi) break;
+      if (z > lo) zeros.push_back(z);
+    }
+    const int nsub = (int)std::lround(1.0 / p.refine_factor);
+    for (double z : zeros) {
+      // base intervals meeting the window [z - hw, z + hw] are subdivided
+      auto it = std::lower_bound(base.begin(), base.end(), z - hw);
+      size_t i0 = (it == base.begin()) ? 0 : (size_t)(it - base.begin()) - 1;
+      for (size_t i = i0; i + 1 < base.size() && base[i] < z + hw; ++i) {
+        const double a = base[i], b = base[i + 1];
+        if (b > z - hw)
+          for (int s = 1; s < nsub; ++s) all.push_back(a + (b - a) * s / nsub);
+      }
+    }
+    // forced zeros: keep z, drop other samples within `merge` of it
+    std::vector<double> kept_zeros;
+    for (double z : zeros)
+      if (z - lo >= merge && hi - z >= merge) kept_zeros.push_back(z);
+    std::vector<double> tmp;
+    tmp.reserve(all.size() + kept_zeros.size());
+    for (double x : all) {
+      bool drop = false;
+      if (x != lo && x != hi) {
+        auto it = std::lower_bound(kept_zeros.begin(), kept_zeros.end(), x - merge);
+        for (; it != kept_zeros.end() && *it <= x + merge; ++it)
+          if (std::fabs(x - *it) < merge) drop = true;
+      }
+      if (!drop) tmp.push_back(x);
+    }
+    for (double z : kept_zeros) tmp.push_back(z);
+    all.swap(tmp);
+  }
+  std::sort(all.begin(), all.end());
+  all.erase(std::unique(all.begin(), all.end()), all.end());
+  while ((int)all.size() < deg + 1) {
+    const size_t n = all.size();
+    for (size_t i = 0; i + 1 < n; ++i) all.push_back(0.5 * (all[i] + all[i + 1]));
+    std::sort(all.begin(), all.end());
+  }
+  if (p.grade) {
+    for (int pass = 0; pass < 200; ++pass) {
+      std::vector<double> add;
+      for (int j = 0; j + 1 < (int)all.size(); ++j)
+        if (eq11_rel(all, j, deg, kind, k) > p.table_tol) add.push_back(0.5 * (all[j] + all[j + 1]));
+      if (add.empty()) break;
+      all.insert(all.end(), add.begin(), add.end());
+      std::sort(all.begin(), all.end());
+      if (all.size() > (1u << 26)) return fail(GF_ERR_RANGE, "table: too many samples");
+    }
+  }
+  out->r = all;
+  out->zflag.assign(all.size(), 0);
+  if (p.refine) {
+    for (size_t j = 0; j < all.size(); ++j) {
+      const double q = std::nearbyint(all[j] / quarter);
+      if (q >= 1 && q * quarter == all[j]) out->zflag[j] = ((int64_t)q % 2) ? 1 : 2;
+    }
+  }
+  double dr = INFINITY;
+  for (size_t j = 0; j + 1 < all.size(); ++j) dr = std::min(dr, all[j + 1] - all[j]);
+  out->dr = dr;
+  const double cells = std::floor((hi - lo) / dr) + 1.0;
+  if (!(cells < (double)(1 << 26))) return fail(GF_ERR_RANGE, "table: hash array too large");
+  out->n_hash = (int64_t)cells;
+  return GF_OK;
+}
+
+}  // namespace gf
+
+using namespace gf;
+
+gf::TabView gf_table::One::view() const {
+  gf::TabView v;
+  v.n_nodes = (int)r.size();
+  v.n_hash = (int)n_hash;
+  v.r_lo = r.front();
+  v.r_hi = r.back();
+  v.dr = dr;
+  v.inv_dr = 1.0 / dr;
+  v.r_lo32 = (float)r.front();
+  v.inv_dr32 = (float)(1.0 / dr);
+  v.hash = d_hash;
+  v.node64 = d_node64;
+  v.c64 = d_c64;
+  v.node32 = d_node32;
+  v.c32a = d_c32a;
+  v.c32b = d_c32b;
+  return v;
+}
+
+namespace {
+
+template <class T>
+gf_status dev_alloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+  return GF_OK;
+}
+
+gf_status check_device(int dev) {
+  int cur = -1;
+  GF_CUDA(cudaGetDevice(&cur));
+  if (cur != dev) return fail(GF_ERR_DEVICE, "handle belongs to device " + std::to_string(dev));
+  return GF_OK;
+}
+
+void free_mesh_device(gf_mesh* m) {
+  void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_pts32,
+                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+gf_status upload_vertices(gf_mesh* m) {
+  std::vector<double> v64(9 * (size_t)m->nt);
+  for (int64_t t = 0; t < m->nt; ++t)
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) v64[9 * t + 3 * c + x] = m->xyz[3 * (size_t)m->tri[3 * t + c] + x];
+  std::vector<double> elen(m->ne);
+  for (int64_t e = 0; e < m->ne; ++e) {
+    double s = 0;
+    for (int x = 0; x < 3; ++x) {
+      double d = m->xyz[3 * (size_t)m->ev[2 * e] + x] - m->xyz[3 * (size_t)m->ev[2 * e + 1] + x];
+      s += d * d;
+    }
+    elen[e] = std::sqrt(s);
+  }
+  GF_CUDA(cudaMemcpy(m->d_v64, v64.data(), v64.size() * 8, cudaMemcpyHostToDevice));
+  GF_CUDA(cudaMemcpy(m->d_elen, elen.data(), elen.size() * 8 + 8 * (m->ne == 0), cudaMemcpyHostToDevice));
+  m->rule = 0;  // geometry cache invalid
+  return GF_OK;
+}
+
+// Builds (or reuses) the per-rule geometry on the device.
+gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s) {
+  if (m->rule == rule) return GF_OK;
+  double bary[kMaxRule][3], w[kMaxRule];
+  if (!rule_points(rule, bary, w)) return fail(GF_ERR_ARG, "rule must be 1, 3, 4, 6 or 7");
+  double* d_bw = nullptr;
+  gf_status st = dev_alloc(&d_bw, 4 * kMaxRule);
+  if (st) return st;
+  std::vector<double> bw(4 * kMaxRule, 0.0);
+  for (int a = 0; a < rule; ++a) {
+    for (int c = 0; c < 3; ++c) bw[3 * a + c] = bary[a][c];
+    bw[3 * kMaxRule + a] = w[a];
+  }
+  cudaError_t e = cudaMemcpy(d_bw, bw.data(), bw.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_prep_geometry(m->d_v64, (int)m->nt, rule, d_bw, d_bw + 3 * kMaxRule, m->d_tedge, m->d_elen,
+                             m->d_pts32, m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(d_bw);
+  if (e != cudaSuccess) return cuda_fail(e, "prepare geometry");
+  m->rule = rule;
+  return GF_OK;
+}
+
+GeoView geo_view(const gf_mesh* m) {
+  GeoView g;
+  g.nt = (int)m->nt;
+  g.m = m->rule;
+  g.pts32 = m->d_pts32;
+  g.cen32 = m->d_cen32;
+  g.geo32 = m->d_geo32;
+  g.pts64 = m->d_pts64;
+  g.cen64 = m->d_cen64;
+  g.geo64 = m->d_geo64;
+  g.v64 = m->d_v64;
+  g.tvert = m->d_tvert;
+  g.tedge = m->d_tedge;
+  g.near_ptr = m->d_near_ptr;
+  g.near_idx = m->d_near_idx;
+  g.near_dist32 = (float)m->near_dist;
+  return g;
+}
+
+bool params_ok(const gf_params* p) {
+  return p && p->table_tol > 0 && p->green_n_per_lambda >= 0 && p->exp_n_per_lambda >= 0 &&
+         p->lagrange_degree >= 1 && p->lagrange_degree <= 3 && p->refine_factor > 0 && p->refine_factor <= 1 &&
+         p->refine_halfwidth_t >= 0 && p->merge_t >= 0 && p->nphi >= 1 && p->nphi <= 32 && p->nl >= 1 &&
+         p->nl <= 32 && p->eta > 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gf_params_default(gf_params* p) {
+  if (!p) return;
+  p->rule = 3;
+  p->table_tol = 1e-6;
+  p->green_n_per_lambda = 1000;
+  p->exp_n_per_lambda = 0;
+  p->lagrange_degree = 3;
+  p->refine = 1;
+  p->refine_factor = 0.5;
+  p->refine_halfwidth_t = 2.0;
+  p->merge_t = 0.25;
+  p->grade = 1;
+  p->nphi = 8;
+  p->nl = 8;
+  p->eta = 376.730313668;
+}
+
+const char* gf_last_error(void) { return gf::g_err.c_str(); }
+
+gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int64_t nt, double near_dist,
+                         gf_mesh** out) {
+  if (!xyz || !tri || !out || nv < 3 || nt < 1) return fail(GF_ERR_ARG, "gf_mesh_create: bad arguments");
+  if (nt > (1LL << 30) || nv > (1LL << 31) - 1) return fail(GF_ERR_ARG, "gf_mesh_create: mesh too large");
+  if (!(near_dist >= 0)) return fail(GF_ERR_ARG, "gf_mesh_create: near_dist must be >= 0");
+  for (int64_t i = 0; i < 3 * nv; ++i)
+    if (!std::isfinite(xyz[i])) return fail(GF_ERR_MESH, "gf_mesh_create: non-finite vertex coordinate");
+  std::unique_ptr<gf_mesh> m(new (std::nothrow) gf_mesh);
+  if (!m) return fail(GF_ERR_ALLOC, "gf_mesh_create: out of host memory");
+  GF_CUDA(cudaGetDevice(&m->device));
+  m->nv = nv;
+  m->nt = nt;
+  m->near_dist = near_dist;
+  m->xyz.assign(xyz, xyz + 3 * nv);
+  m->tri.assign(tri, tri + 3 * nt);
+  // ---- RWG edges: sort (lower, higher, triangle, local index) records
+  std::vector<std::tuple<int32_t, int32_t, int32_t, int32_t>> rec;
+  rec.reserve(3 * nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int32_t* v = &tri[3 * t];
+    for (int c = 0; c < 3; ++c) {
+      if (v[c] < 0 || v[c] >= nv) return fail(GF_ERR_MESH, "gf_mesh_create: vertex index out of range");
+    }
+    if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) return fail(GF_ERR_MESH, "gf_mesh_create: repeated vertex");
+    for (int i = 0; i < 3; ++i) {  // local edge i is opposite local vertex i
+      int32_t a = v[(i + 1) % 3], b = v[(i + 2) % 3];
+      rec.emplace_back(std::min(a, b), std::max(a, b), (int32_t)t, i);
+    }
+  }
+  std::sort(rec.begin(), rec.end());
+  m->tedge.assign(3 * nt, -1);
+  for (size_t i = 0; i < rec.size();) {
+    size_t j = i;
+    while (j < rec.size() && std::get<0>(rec[j]) == std::get<0>(rec[i]) && std::get<1>(rec[j]) == std::get<1>(rec[i])) ++j;
+    if (j - i > 2) return fail(GF_ERR_MESH, "gf_mesh_create: edge shared by more than two triangles");
+    if (j - i == 2) {
+      const int32_t e = (int32_t)m->ev.size() / 2;
+      const int32_t tp = std::get<2>(rec[i]), tm = std::get<2>(rec[i + 1]);  // sorted: T+ first
+      if (tp == tm) return fail(GF_ERR_MESH, "gf_mesh_create: degenerate triangle");
+      m->ev.push_back(std::get<0>(rec[i]));
+      m->ev.push_back(std::get<1>(rec[i]));
+      m->et.push_back(tp);
+      m->et.push_back(tm);
+      m->tedge[3 * tp + std::get<3>(rec[i])] = 2 * e;          // even: T+ side
+      m->tedge[3 * tm + std::get<3>(rec[i + 1])] = 2 * e + 1;  // odd: T- side
+    }
+    i = j;
+  }
+  m->ne = (int64_t)m->ev.size() / 2;
+  // ---- near pairs: vertex sharing, plus centroids closer than near_dist
+  std::vector<std::vector<int32_t>> vt(nv);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int c = 0; c < 3; ++c) vt[tri[3 * t + c]].push_back((int32_t)t);
+  std::vector<double> cen(3 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int x = 0; x < 3; ++x)
+      cen[3 * t + x] = (xyz[3 * (size_t)tri[3 * t] + x] + xyz[3 * (size_t)tri[3 * t + 1] + x] +
+                        xyz[3 * (size_t)tri[3 * t + 2] + x]) / 3.0;
+  std::unordered_map<int64_t, std::vector<int32_t>> grid;
+  double cell = near_dist;
+  auto key = [](int64_t a, int64_t b, int64_t c) { return ((a & 0x1FFFFF) << 42) | ((b & 0x1FFFFF) << 21) | (c & 0x1FFFFF); };
+  if (near_dist > 0) {
+    for (int64_t t = 0; t < nt; ++t)
+      grid[key((int64_t)std::floor(cen[3 * t] / cell), (int64_t)std::floor(cen[3 * t + 1] / cell),
+               (int64_t)std::floor(cen[3 * t + 2] / cell))]
+          .push_back((int32_t)t);
+  }
+  m->near_ptr.assign(nt + 1, 0);
+  std::vector<int32_t> row;
+  for (int64_t p = 0; p < nt; ++p) {
+    row.clear();
+    for (int c = 0; c < 3; ++c)
+      for (int32_t q : vt[tri[3 * p + c]]) row.push_back(q);
+    if (near_dist > 0) {
+      int64_t gx = (int64_t)std::floor(cen[3 * p] / cell), gy = (int64_t)std::floor(cen[3 * p + 1] / cell),
+              gz = (int64_t)std::floor(cen[3 * p + 2] / cell);
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy)
+          for (int dz = -1; dz <= 1; ++dz) {
+            auto it = grid.find(key(gx + dx, gy + dy, gz + dz));
+            if (it == grid.end()) continue;
+            for (int32_t q : it->second) {
+              double ax = cen[3 * p] - cen[3 * (size_t)q], ay = cen[3 * p + 1] - cen[3 * (size_t)q + 1],
+                     az = cen[3 * p + 2] - cen[3 * (size_t)q + 2];
+              if (std::sqrt(ax * ax + ay * ay + az * az) < near_dist) row.push_back(q);
+            }
+          }
+    }
+    std::sort(row.begin(), row.end());
+    row.erase(std::unique(row.begin(), row.end()), row.end());
+    m->near_idx.insert(m->near_idx.end(), row.begin(), row.end());
+    m->near_ptr[p + 1] = (int64_t)m->near_idx.size();
+  }
+  // ---- device upload
+  gf_status st;
+  if ((st = dev_alloc(&m->d_v64, 9 * nt)) || (st = dev_alloc(&m->d_tvert, nt)) || (st = dev_alloc(&m->d_tedge, nt)) ||
+      (st = dev_alloc(&m->d_elen, m->ne)) || (st = dev_alloc(&m->d_near_ptr, nt + 1)) ||
+      (st = dev_alloc(&m->d_near_idx, m->near_idx.size())) || (st = dev_alloc(&m->d_pts32, kMaxRule * nt)) ||
+      (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
+      (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
+      (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_minmax, 4))) {
+    free_mesh_device(m.get());
+    return st;
+  }
+  std::vector<int4> tv(nt), te(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    tv[t] = make_int4(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2], 0);
+    te[t] = make_int4(m->tedge[3 * t], m->tedge[3 * t + 1], m->tedge[3 * t + 2], 0);
+  }
+  cudaError_t e = cudaMemcpy(m->d_tvert, tv.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_tedge, te.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m->d_near_ptr, m->near_ptr.data(), (nt + 1) * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !m->near_idx.empty())
+    e = cudaMemcpy(m->d_near_idx, m->near_idx.data(), m->near_idx.size() * 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_mesh_device(m.get());
+    return cuda_fail(e, "gf_mesh_create upload");
+  }
+  if ((st = upload_vertices(m.get()))) {
+    free_mesh_device(m.get());
+    return st;
+  }
+  *out = m.release();
+  return GF_OK;
+}
+
+gf_status gf_mesh_info(const gf_mesh* m, int64_t* nv, int64_t* nt, int64_t* ne, int64_t* n_near) {
+  if (!m) return fail(GF_ERR_ARG, "gf_mesh_info: null mesh");
+  if (nv) *nv = m->nv;
+  if (nt) *nt = m->nt;
+  if (ne) *ne = m->ne;
+  if (n_near) *n_near = (int64_t)m->near_idx.size();
+  return GF_OK;
+}
+
+gf_status gf_mesh_edges(const gf_mesh* m, int32_t* edge_verts, int32_t* edge_tris) {
+  if (!m) return fail(GF_ERR_ARG, "gf_mesh_edges: null mesh");
+  if (edge_verts) std::memcpy(edge_verts, m->ev.data(), m->ev.size() * 4);
+  if (edge_tris) std::memcpy(edge_tris, m->et.data(), m->et.size() * 4);
+  return GF_OK;
+}
+
+gf_status gf_mesh_set_vertices(gf_mesh* m, const double* xyz) {
+  if (!m || !xyz) return fail(GF_ERR_ARG, "gf_mesh_set_vertices: null argument");
+  gf_status st = check_device(m->device);
+  if (st) return st;
+  for (int64_t i = 0; i < 3 * m->nv; ++i)
+    if (!std::isfinite(xyz[i])) return fail(GF_ERR_MESH, "gf_mesh_set_vertices: non-finite coordinate");
+  m->xyz.assign(xyz, xyz + 3 * m->nv);
+  return upload_vertices(m);
+}
+
+gf_status gf_mesh_destroy(gf_mesh* m) {
+  if (!m) return GF_OK;
+  free_mesh_device(m);
+  delete m;
+  return GF_OK;
+}
+
+gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, double* r_max, void* stream) {
+  if (!mc || !r_min || !r_max) return fail(GF_ERR_ARG, "gf_range: null argument");
+  if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_range: bad precision");
+  gf_mesh* m = const_cast<gf_mesh*>(mc);
+  gf_status st = check_device(m->device);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_rule(m, rule, s))) return st;
+  GF_CUDA(launch_range(geo_view(m), precision, m->d_minmax, s));
+  unsigned long long mm[2];
+  GF_CUDA(cudaMemcpyAsync(mm, m->d_minmax, 16, cudaMemcpyDeviceToHost, s));
+  GF_CUDA(cudaStreamSynchronize(s));
+  double lo, hi;
+  std::memcpy(&lo, &mm[0], 8);
+  std::memcpy(&hi, &mm[1], 8);
+  if (!(hi >= 0) || !(lo < INFINITY)) return fail(GF_ERR_RANGE, "gf_range: every triangle pair is near");
+  *r_min = lo;
+  *r_max = hi;
+  return GF_OK;
+}
+
+gf_status gf_table_create(double k, double r_min, double r_max, const gf_params* p, void* stream, gf_table** out) {
+  if (!out || !params_ok(p)) return fail(GF_ERR_ARG, "gf_table_create: bad params");
+  if (!(k > 0) || !(r_min > 0) || !(r_max > r_min) || !std::isfinite(r_max))
+    return fail(GF_ERR_ARG, "gf_table_create: need k > 0 and 0 < r_min < r_max");
+  std::unique_ptr<gf_table> T(new (std::nothrow) gf_table);
+  if (!T) return fail(GF_ERR_ALLOC, "gf_table_create: out of host memory");
+  GF_CUDA(cudaGetDevice(&T->device));
+  T->k = k;
+  T->r_lo = r_min;
+  T->r_hi = r_max;
+  const double lam = 2.0 * kPi / k;
+  int n_exp = p->exp_n_per_lambda;
+  if (n_exp == 0) {
+    n_exp = 1000;
+    while (n_exp < 10000 && std::pow(2.0 * kPi / n_exp, 2) / 8.0 > p->table_tol) n_exp += 4;
+  }
+  const int n_green = p->green_n_per_lambda ? p->green_n_per_lambda : 1000;
+  cudaStream_t s = (cudaStream_t)stream;
+  gf_table::One* ones[2] = {&T->green, &T->exp};
+  for (int which = 0; which < 2; ++which) {
+    gf_table::One& o = *ones[which];
+    o.kind = which == 0 ? GF_GREEN : GF_EXP;
+    o.degree = which == 0 ? p->lagrange_degree : 1;
+    const double t = lam / (which == 0 ? n_green : n_exp);
+    Placement pl;
+    gf_status st = place_samples(o.kind, o.degree, k, r_min, r_max, t, *p, &pl);
+    if (st) return st;
+    o.r = pl.r;
+    o.zflag = pl.zflag;
+    o.dr = pl.dr;
+    o.n_hash = pl.n_hash;
+    const size_t n = o.r.size();
+    if ((st = dev_alloc(&o.d_node64, n)) || (st = dev_alloc(&o.d_zflag, n)) || (st = dev_alloc(&o.d_fval, 2 * n)) ||
+        (st = dev_alloc(&o.d_c64, 4 * n)) || (st = dev_alloc(&o.d_node32, n)) || (st = dev_alloc(&o.d_c32a, n)) ||
+        (st = dev_alloc(&o.d_c32b, n)) || (st = dev_alloc(&o.d_hash, (size_t)o.n_hash))) {
+      gf_table_destroy(T.release());
+      return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(o.d_node64, o.r.data(), n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(o.d_zflag, o.zflag.data(), n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = launch_table_image(o.kind, k, o.degree, (int)n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a,
+                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      gf_table_destroy(T.release());
+      return cuda_fail(e, "gf_table_create");
+    }
+  }
+  *out = T.release();
+  return GF_OK;
+}
+
+gf_status gf_table_info(const gf_table* t, int kind, int64_t* n_nodes, int64_t* n_hash, double* dr) {
+  if (!t || (kind != GF_GREEN && kind != GF_EXP)) return fail(GF_ERR_ARG, "gf_table_info: bad argument");
+  const gf_table::One& o = t->get(kind);
+  if (n_nodes) *n_nodes = (int64_t)o.r.size();
+  if (n_hash) *n_hash = o.n_hash;
+  if (dr) *dr = o.dr;
+  return GF_OK;
+}
+
+gf_status gf_table_nodes(const gf_table* t, int kind, double* r, double* fre, double* fim, int32_t* hash) {
+  if (!t || (kind != GF_GREEN && kind != GF_EXP)) return fail(GF_ERR_ARG, "gf_table_nodes: bad argument");
+  gf_status st = check_device(t->device);
+  if (st) return st;
+  const gf_table::One& o = t->get(kind);
+  const size_t n = o.r.size();
+  if (r) std::memcpy(r, o.r.data(), n * 8);
+  if (fre || fim) {
+    std::vector<double> f(2 * n);
+    GF_CUDA(cudaMemcpy(f.data(), o.d_fval, 2 * n * 8, cudaMemcpyDeviceToHost));
+    for (size_t j = 0; j < n; ++j) {
+      if (fre) fre[j] = f[2 * j];
+      if (fim) fim[j] = f[2 * j + 1];
+    }
+  }
+  if (hash) GF_CUDA(cudaMemcpy(hash, o.d_hash, (size_t)o.n_hash * 4, cudaMemcpyDeviceToHost));
+  return GF_OK;
+}
+
+gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* r_dev, int64_t n, void* out_dev,
+                        void* stream) {
+  if (!t || (kind != GF_GREEN && kind != GF_EXP) || (precision != GF_FP32 && precision != GF_FP64) || n < 0 ||
+      (n > 0 && (!r_dev || !out_dev)))
+    return fail(GF_ERR_ARG, "gf_table_eval: bad argument");
+  gf_status st = check_device(t->device);
+  if (st) return st;
+  if (n == 0) return GF_OK;
+  GF_CUDA(launch_table_eval(t->get(kind).view(), kind, precision, r_dev, n, out_dev, (cudaStream_t)stream));
+  return GF_OK;
+}
+
+gf_status gf_table_destroy(gf_table* t) {
+  if (!t) return GF_OK;
+  for (gf_table::One* o : {&t->green, &t->exp}) {
+    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval, o->d_c64, o->d_node32, o->d_c32a, o->d_c32b, o->d_hash};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+  delete t;
+  return GF_OK;
+}
+
+gf_status gf_fill(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision, void* Z,
+                  int64_t ldz, void* stream) {
+  if (!mc || !params_ok(p) || !Z) return fail(GF_ERR_ARG, "gf_fill: bad argument");
+  if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_fill: bad precision");
+  if (!(k > 0) || ldz < mc->ne) return fail(GF_ERR_ARG, "gf_fill: need k > 0 and ldz >= ne");
+  gf_mesh* m = const_cast<gf_mesh*>(mc);
+  gf_status st = check_device(m->device);
+  if (st) return st;
+  if (table && (table->device != m->device)) return fail(GF_ERR_DEVICE, "gf_fill: table on another device");
+  if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill: table built for another k");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_rule(m, p->rule, s))) return st;
+  if (m->ne == 0) return GF_OK;
+  const size_t esz = precision == GF_FP32 ? 8 : 16;
+  GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
+  GeoView g = geo_view(m);
+  TabView tg, te;
+  if (table) {
+    tg = table->green.view();
+    te = table->exp.view();
+  }
+  GF_CUDA(launch_fill_regular(g, table ? &tg : nullptr, precision, k, p->eta, Z, ldz, s));
+  double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
+  gauss_legendre(p->nphi, gx_phi, gw_phi);
+  gauss_legendre(p->nl, gx_l, gw_l);
+  double glp[64], gll[64];
+  for (int i = 0; i < p->nphi; ++i) {
+    glp[i] = gx_phi[i];
+    glp[32 + i] = gw_phi[i];
+  }
+  for (int i = 0; i < p->nl; ++i) {
+    gll[i] = gx_l[i];
+    gll[32 + i] = gw_l[i];
+  }
+  GF_CUDA(launch_fill_near(g, table ? &te : nullptr, precision, k, p->eta, p->nphi, p->nl, glp, gll, Z, ldz, s));
+  return GF_OK;
+}
+
+}  // extern "C"

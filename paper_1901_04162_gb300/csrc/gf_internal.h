@@ -1,0 +1,133 @@
+// Internal declarations of the gfmom library (host side and kernels).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "gfmom.h"
+
+namespace gf {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxRule = 7;
+
+// ---------------------------------------------------------------- errors
+gf_status fail(gf_status st, const std::string& msg);
+gf_status cuda_fail(cudaError_t e, const char* what);
+#define GF_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t _e = (call);                            \
+    if (_e != cudaSuccess) return gf::cuda_fail(_e, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------- rules
+// Barycentric coordinates and weights (sum 1) of the Dunavant rules.
+bool rule_points(int npts, double bary[][3], double* w);
+
+// ---------------------------------------------------------------- device views
+// Geometry of one triangle set for one quadrature rule (structure of arrays).
+struct GeoView {
+  int nt, m;
+  const float4* pts32;   // [m][nt]: offset of point a from the centroid, weight
+  const float4* cen32;   // [nt]: centroid (FP32), area
+  const float4* geo32;   // [nt][3]: delta_i = c - v_i (xyz), s_i * l_i
+  const double* pts64;   // [m][nt][4]
+  const double* cen64;   // [nt][4]
+  const double* geo64;   // [nt][3][4]
+  const double* v64;     // [nt][9] vertices
+  const int4* tvert;     // [nt]: vertex ids (x, y, z)
+  const int4* tedge;     // [nt]: RWG edge id of local edge i, or -1
+  const int64_t* near_ptr;  // [nt + 1]
+  const int32_t* near_idx;  // sorted per row
+  float near_dist32;        // > 0: centroid criterion present (FP32 screen)
+};
+
+// One interpolation table as the kernels see it.
+struct TabView {
+  int n_nodes, n_hash;
+  double r_lo, r_hi, dr, inv_dr;
+  float r_lo32, inv_dr32;
+  const int32_t* hash;     // [n_hash]
+  const double* node64;    // [n_nodes]
+  const double2* c64;      // [n_nodes-1][4]: (re, im) of c0..c3 about node64[j]
+  const float* node32;     // [n_nodes]: FP32 anchors
+  const float4* c32a;      // [n_nodes-1]: (c0re, c0im, c1re, c1im) about node32[j]
+  const float4* c32b;      // [n_nodes-1]: (c2re, c2im, c3re, c3im)
+  size_t smem32_bytes() const {
+    return (size_t)n_hash * 4 + (size_t)n_nodes * 4 + (size_t)(n_nodes - 1) * 32 + 64;
+  }
+};
+
+// ---------------------------------------------------------------- kernels (gf_kernels.cu)
+cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
+                                 const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
+                                 float4* geo32, double* pts64, double* cen64, double* geo64,
+                                 cudaStream_t s);
+cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, const double* node64,
+                               const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
+                               float4* c32b, double* fval, int n_hash, double r_lo, double dr,
+                               int32_t* hash, cudaStream_t s);
+cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
+                              void* out, cudaStream_t s);
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s);
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int precision, double k,
+                                double eta, void* Z, int64_t ldz, cudaStream_t s);
+cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, double k,
+                             double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
+                             void* Z, int64_t ldz, cudaStream_t s);
+
+}  // namespace gf
+
+// ---------------------------------------------------------------- handles
+struct gf_mesh {
+  int device;
+  int64_t nv, nt, ne;
+  double near_dist;
+  std::vector<double> xyz;        // [nv][3]
+  std::vector<int32_t> tri;       // [nt][3]
+  std::vector<int32_t> ev, et;    // [ne][2]
+  std::vector<int32_t> tedge;     // [nt][3], -1 if boundary
+  std::vector<double> elen;       // [ne]
+  std::vector<int64_t> near_ptr;  // [nt + 1]
+  std::vector<int32_t> near_idx;
+  // device
+  double* d_v64 = nullptr;
+  int4* d_tvert = nullptr;
+  int4* d_tedge = nullptr;
+  double* d_elen = nullptr;
+  int64_t* d_near_ptr = nullptr;
+  int32_t* d_near_idx = nullptr;
+  // per-rule geometry cache
+  int rule = 0;
+  float4* d_pts32 = nullptr;
+  float4* d_cen32 = nullptr;
+  float4* d_geo32 = nullptr;
+  double* d_pts64 = nullptr;
+  double* d_cen64 = nullptr;
+  double* d_geo64 = nullptr;
+  unsigned long long* d_minmax = nullptr;  // range scratch [4]
+};
+
+struct gf_table {
+  int device;
+  double k, r_lo, r_hi;
+  struct One {
+    int kind, degree;
+    std::vector<double> r;        // host sample positions
+    std::vector<int8_t> zflag;    // 1: real part is an exact zero, 2: imaginary part
+    double dr;
+    int64_t n_hash;
+    double* d_node64 = nullptr;
+    int8_t* d_zflag = nullptr;
+    double* d_fval = nullptr;     // [n][2] sample values
+    double2* d_c64 = nullptr;
+    float* d_node32 = nullptr;
+    float4* d_c32a = nullptr;
+    float4* d_c32b = nullptr;
+    int32_t* d_hash = nullptr;
+    gf::TabView view() const;
+  } green, exp;
+  const One& get(int kind) const { return kind == GF_GREEN ? green : exp; }
+};

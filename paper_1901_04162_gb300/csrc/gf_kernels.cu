@@ -1,0 +1,857 @@
+// gfmom kernels for sm_103a.
+//
+// Regular pairs (Section II.A): one warp per (test triangle p, 32 source
+// triangles q), one source triangle per lane. For each test point a the lane
+// runs over the source points b: R = |(c_p - c_q) + alpha_a - beta_b|, Green
+// value from the Lagrange table (hash of Eq. 6 -> interval -> cubic in
+// s = R - r_j, Eq. 3 + 5 re-expanded as monomials) or from sincospi, and four
+// moments M0 = sum w w G, Ma = sum w w alpha G, Mb = sum w w beta G,
+// Mab = sum w w (alpha . beta) G (8 complex numbers; Kahan-compensated over a
+// in FP32). The 3 x 3 RWG block of the pair follows from the moments:
+//   Z(e_i, e_j) += jk eta/(4 pi) s_i l_i s_j l_j
+//                  [ (Mab + eps_j . Ma + delta_i . Mb + (delta_i . eps_j) M0) / 4 - M0 / k^2 ]
+// with delta_i = c_p - v_i, eps_j = c_q - v_j (v = vertex opposite the edge).
+// The table sits in shared memory when it fits.
+//
+// Near pairs: FP64, one thread per (p, q) near pair; the inner integrals over
+// q for each test point come from singularity cancellation (exact radial
+// integral) with the angular variable u = asinh(tan phi) for the scalar part,
+// and from the surface-gradient theorem (line integrals over q's edges, static
+// part in closed form) for the vector part. e^{-jkR} on those lines is the
+// linear Exp table when r_min <= R <= r_max (Section II.C), else sincos.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "gf_internal.h"
+
+namespace gf {
+namespace {
+
+constexpr int kWarps = 8;              // warps per block of the pair kernels
+constexpr int kThreads = kWarps * 32;
+
+__device__ __forceinline__ int edge_of(int code) { return code >> 1; }
+__device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
+
+// ---------------------------------------------------------------- geometry prep
+__global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, const double* __restrict__ bary,
+                                const double* __restrict__ w, const int4* __restrict__ tedge,
+                                const double* __restrict__ elen, float4* pts32, float4* cen32, float4* geo32,
+                                double* pts64, double* cen64, double* geo64) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  double v[3][3];
+  for (int c = 0; c < 3; ++c)
+    for (int x = 0; x < 3; ++x) v[c][x] = v64[9 * (size_t)t + 3 * c + x];
+  double c0 = (v[0][0] + v[1][0] + v[2][0]) / 3.0;
+  double c1 = (v[0][1] + v[1][1] + v[2][1]) / 3.0;
+  double c2 = (v[0][2] + v[1][2] + v[2][2]) / 3.0;
+  double e1x = v[1][0] - v[0][0], e1y = v[1][1] - v[0][1], e1z = v[1][2] - v[0][2];
+  double e2x = v[2][0] - v[0][0], e2y = v[2][1] - v[0][1], e2z = v[2][2] - v[0][2];
+  double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+  double area = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
+  cen64[4 * (size_t)t + 0] = c0;
+  cen64[4 * (size_t)t + 1] = c1;
+  cen64[4 * (size_t)t + 2] = c2;
+  cen64[4 * (size_t)t + 3] = area;
+  cen32[t] = make_float4((float)c0, (float)c1, (float)c2, (float)area);
+  for (int a = 0; a < m; ++a) {
+    double px = bary[3 * a] * v[0][0] + bary[3 * a + 1] * v[1][0] + bary[3 * a + 2] * v[2][0];
+    double py = bary[3 * a] * v[0][1] + bary[3 * a + 1] * v[1][1] + bary[3 * a + 2] * v[2][1];
+    double pz = bary[3 * a] * v[0][2] + bary[3 * a + 1] * v[1][2] + bary[3 * a + 2] * v[2][2];
+    size_t o = (size_t)a * nt + t;
+    pts64[4 * o + 0] = px - c0;
+    pts64[4 * o + 1] = py - c1;
+    pts64[4 * o + 2] = pz - c2;
+    pts64[4 * o + 3] = w[a];
+    pts32[o] = make_float4((float)(px - c0), (float)(py - c1), (float)(pz - c2), (float)w[a]);
+  }
+  int codes[3] = {tedge[t].x, tedge[t].y, tedge[t].z};
+  for (int i = 0; i < 3; ++i) {
+    double sl = 0.0;
+    if (codes[i] >= 0) sl = (codes[i] & 1 ? -1.0 : 1.0) * elen[codes[i] >> 1];
+    double dx = c0 - v[i][0], dy = c1 - v[i][1], dz = c2 - v[i][2];
+    size_t o = 3 * (size_t)t + i;
+    geo64[4 * o + 0] = dx;
+    geo64[4 * o + 1] = dy;
+    geo64[4 * o + 2] = dz;
+    geo64[4 * o + 3] = sl;
+    geo32[o] = make_float4((float)dx, (float)dy, (float)dz, (float)sl);
+  }
+}
+
+// ---------------------------------------------------------------- table image
+__global__ void k_table_values(int kind, double k, int n, const double* __restrict__ r,
+                               const int8_t* __restrict__ zflag, double* fval) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s, c;
+  sincos(k * r[j], &s, &c);
+  double re = c, im = -s;
+  if (kind == GF_GREEN) {
+    re = c / r[j];
+    im = -s / r[j];
+  }
+  if (zflag[j] == 1) re = 0.0;
+  if (zflag[j] == 2) im = 0.0;
+  fval[2 * j] = re;
+  fval[2 * j + 1] = im;
+}
+
+// Coefficients of the interpolant on interval j as a polynomial in u = x - x0:
+// linear (Eq. 4) or the Lagrange form (Eq. 5) on the stencil s0..s0+deg,
+// expanded by multiplying out prod_{m != i} (u - (r_m - x0)) / (r_i - r_m).
+__device__ void interval_poly(int deg, int n, const double* __restrict__ r, const double* __restrict__ f, int j,
+                              double x0, double cre[4], double cim[4]) {
+  for (int p = 0; p < 4; ++p) cre[p] = cim[p] = 0.0;
+  if (deg <= 1) {
+    double h = r[j + 1] - r[j];
+    double sre = (f[2 * j + 2] - f[2 * j]) / h, sim = (f[2 * j + 3] - f[2 * j + 1]) / h;
+    double u0 = x0 - r[j];
+    cre[0] = f[2 * j] + sre * u0;
+    cim[0] = f[2 * j + 1] + sim * u0;
+    cre[1] = sre;
+    cim[1] = sim;
+    return;
+  }
+  int s0 = j - (deg - 1) / 2;
+  if (s0 > n - 1 - deg) s0 = n - 1 - deg;
+  if (s0 < 0) s0 = 0;
+  for (int i = s0; i <= s0 + deg; ++i) {
+    double poly[4] = {1.0, 0.0, 0.0, 0.0};
+    double den = 1.0;
+    int len = 1;
+    for (int mm = s0; mm <= s0 + deg; ++mm) {
+      if (mm == i) continue;
+      double e = r[mm] - x0;
+      for (int p = len; p >= 1; --p) poly[p] = poly[p - 1] - e * poly[p];
+      poly[0] = -e * poly[0];
+      ++len;
+      den *= (r[i] - r[mm]);
+    }
+    for (int p = 0; p < len; ++p) {
+      double b = poly[p] / den;
+      cre[p] += f[2 * i] * b;
+      cim[p] += f[2 * i + 1] * b;
+    }
+  }
+}
+
+__global__ void k_table_coef(int deg, int n, const double* __restrict__ r, const double* __restrict__ f,
+                             double2* c64, float* node32, float4* c32a, float4* c32b) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float a32 = (float)r[j];
+  node32[j] = a32;
+  if (j >= n - 1) return;
+  double cre[4], cim[4];
+  interval_poly(deg, n, r, f, j, r[j], cre, cim);
+  for (int p = 0; p < 4; ++p) c64[4 * j + p] = make_double2(cre[p], cim[p]);
+  // FP32 image: the same polynomial about the FP32-representable anchor, so
+  // that s = R - node32[j] carries no anchor rounding error
+  interval_poly(deg, n, r, f, j, (double)a32, cre, cim);
+  c32a[j] = make_float4((float)cre[0], (float)cim[0], (float)cre[1], (float)cim[1]);
+  c32b[j] = make_float4((float)cre[2], (float)cim[2], (float)cre[3], (float)cim[3]);
+}
+
+// Hash of Eq. (6): cell c holds the largest sample index whose cell
+// floor((r_j - r_min)/dr) is <= c (the forward-filled array); cell 0 holds 0.
+__global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, double r_lo, double dr, int32_t* hash) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_hash) return;
+  if (c == 0) {
+    hash[0] = 0;
+    return;
+  }
+  int lo = 0, hi = n - 1;  // invariant: cell(lo) <= c
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (floor((r[mid] - r_lo) / dr) <= (double)c) lo = mid;
+    else hi = mid - 1;
+  }
+  hash[c] = lo;
+}
+
+// ---------------------------------------------------------------- lookups
+struct Tab32 {  // FP32 view (shared or global memory)
+  const int32_t* hash;
+  const float* node;
+  const float4* ca;
+  const float4* cb;
+  int n_nodes, n_hash;
+  float r_lo, inv_dr;
+};
+
+__device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
+  float x = (R - T.r_lo) * T.inv_dr;
+  int c = (int)x;
+  c = min(max(c, 0), T.n_hash - 1);
+  int j = T.hash[c];
+#pragma unroll
+  for (int it = 0; it < 2; ++it)
+    if (j > 0 && R < T.node[j]) --j;
+#pragma unroll
+  for (int it = 0; it < 2; ++it)
+    if (j < T.n_nodes - 2 && R >= T.node[j + 1]) ++j;
+  j = min(j, T.n_nodes - 2);
+  float s = R - T.node[j];
+  float4 a = T.ca[j], b = T.cb[j];
+  float re = fmaf(s, b.z, b.x), im = fmaf(s, b.w, b.y);
+  re = fmaf(s, re, a.z);
+  im = fmaf(s, im, a.w);
+  re = fmaf(s, re, a.x);
+  im = fmaf(s, im, a.y);
+  return make_float2(re, im);
+}
+
+__device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
+  double x = (R - T.r_lo) * T.inv_dr;
+  int cell = (int)fmin(fmax(floor(x), 0.0), (double)(T.n_hash - 1));
+  int j = T.hash[cell];
+  for (int it = 0; it < 2; ++it)
+    if (j > 0 && R < T.node64[j]) --j;
+  for (int it = 0; it < 2; ++it)
+    if (j < T.n_nodes - 2 && R >= T.node64[j + 1]) ++j;
+  j = min(j, T.n_nodes - 2);
+  double s = R - T.node64[j];
+  const double2* cf = T.c64 + 4 * j;
+  double2 c3 = cf[3], c2 = cf[2], c1 = cf[1], c0 = cf[0];
+  double re = fma(s, c3.x, c2.x), im = fma(s, c3.y, c2.y);
+  re = fma(s, re, c1.x);
+  im = fma(s, im, c1.y);
+  re = fma(s, re, c0.x);
+  im = fma(s, im, c0.y);
+  return make_double2(re, im);
+}
+
+__global__ void k_table_eval32(TabView t, const float* __restrict__ r, int64_t n, float2* out) {
+  Tab32 T{t.hash, t.node32, t.c32a, t.c32b, t.n_nodes, t.n_hash, t.r_lo32, t.inv_dr32};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = lookup32(T, r[i]);
+}
+
+__global__ void k_table_eval64(TabView t, const double* __restrict__ r, int64_t n, double2* out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = lookup64(t, r[i]);
+}
+
+// ---------------------------------------------------------------- near test
+// A pair is near when it shares a vertex, or (centroid criterion) when q is in
+// p's sorted near list; the FP32 centroid distance only screens out pairs that
+// are clearly farther than near_dist.
+__device__ __forceinline__ bool pair_is_near(const GeoView& g, int p, int q, int4 vp, int4 vq, float3 dc) {
+  if (vp.x == vq.x || vp.x == vq.y || vp.x == vq.z || vp.y == vq.x || vp.y == vq.y || vp.y == vq.z ||
+      vp.z == vq.x || vp.z == vq.y || vp.z == vq.z)
+    return true;
+  if (g.near_dist32 > 0.f) {
+    float th = g.near_dist32 * 1.0001f + 1e-6f;
+    if (dc.x * dc.x + dc.y * dc.y + dc.z * dc.z < th * th) {
+      int64_t lo = g.near_ptr[p], hi = g.near_ptr[p + 1];
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int v = g.near_idx[mid];
+        if (v == q) return true;
+        if (v < q) lo = mid + 1;
+        else hi = mid;
+      }
+    }
+  }
+  return false;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+__global__ void k_range_init(unsigned long long* mm) {
+  mm[0] = dbits(INFINITY);
+  mm[1] = 0ull;
+}
+
+// ---------------------------------------------------------------- range
+// One warp per (p, 32 consecutive q). FP32: each lane keeps the FP32 extremes
+// with their point pairs and re-evaluates those two pairs in FP64 at the end.
+template <bool FP64>
+__global__ void __launch_bounds__(kThreads) k_range(GeoView g, unsigned long long* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunk = (g.nt + 31) / 32;
+  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double best_lo = INFINITY, best_hi = 0.0;
+  float lo32 = INFINITY, hi32 = -1.f;
+  int lo_p = 0, lo_q = 0, lo_ab = 0, hi_p = 0, hi_q = 0, hi_ab = 0;
+  for (int64_t task = warp0; task < ntask; task += nwarp) {
+    const int p = (int)(task / nchunk);
+    const int q0 = (int)(task % nchunk) * 32;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+    if (!ok) continue;
+    if (FP64) {
+      const double* cp64 = g.cen64 + 4 * (size_t)p;
+      const double* cq64 = g.cen64 + 4 * (size_t)q;
+      double dx = cp64[0] - cq64[0], dy = cp64[1] - cq64[1], dz = cp64[2] - cq64[2];
+      for (int a = 0; a < g.m; ++a) {
+        const double* pa = g.pts64 + 4 * ((size_t)a * g.nt + p);
+        double ux = dx + pa[0], uy = dy + pa[1], uz = dz + pa[2];
+        for (int b = 0; b < g.m; ++b) {
+          const double* pb = g.pts64 + 4 * ((size_t)b * g.nt + q);
+          double rx = ux - pb[0], ry = uy - pb[1], rz = uz - pb[2];
+          double R = sqrt(rx * rx + ry * ry + rz * rz);
+          best_lo = fmin(best_lo, R);
+          best_hi = fmax(best_hi, R);
+        }
+      }
+    } else {
+      for (int a = 0; a < g.m; ++a) {
+        float4 pa = g.pts32[(size_t)a * g.nt + p];
+        float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
+        for (int b = 0; b < g.m; ++b) {
+          float4 pb = g.pts32[(size_t)b * g.nt + q];
+          float rx = ux - pb.x, ry = uy - pb.y, rz = uz - pb.z;
+          float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+          if (R2 < lo32) { lo32 = R2; lo_p = p; lo_q = q; lo_ab = a * 8 + b; }
+          if (R2 > hi32) { hi32 = R2; hi_p = p; hi_q = q; hi_ab = a * 8 + b; }
+        }
+      }
+    }
+  }
+  if (!FP64) {
+    auto dist64 = [&](int p, int q, int ab) {
+      const double* cp64 = g.cen64 + 4 * (size_t)p;
+      const double* cq64 = g.cen64 + 4 * (size_t)q;
+      const double* pa = g.pts64 + 4 * ((size_t)(ab >> 3) * g.nt + p);
+      const double* pb = g.pts64 + 4 * ((size_t)(ab & 7) * g.nt + q);
+      double rx = (cp64[0] - cq64[0]) + pa[0] - pb[0];
+      double ry = (cp64[1] - cq64[1]) + pa[1] - pb[1];
+      double rz = (cp64[2] - cq64[2]) + pa[2] - pb[2];
+      return sqrt(rx * rx + ry * ry + rz * rz);
+    };
+    if (lo32 < INFINITY) best_lo = dist64(lo_p, lo_q, lo_ab);
+    if (hi32 >= 0.f) best_hi = dist64(hi_p, hi_q, hi_ab);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    best_lo = fmin(best_lo, __shfl_xor_sync(0xffffffffu, best_lo, off));
+    best_hi = fmax(best_hi, __shfl_xor_sync(0xffffffffu, best_hi, off));
+  }
+  if (lane == 0) {
+    if (best_lo < INFINITY) atomicMin(&mm[0], dbits(best_lo));
+    if (best_hi > 0.0) atomicMax(&mm[1], dbits(best_hi));
+  }
+}
+
+// ---------------------------------------------------------------- regular fill
+struct KSum {  // Kahan-compensated FP32 sum
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+template <bool TABLE, bool SMEM>
+__global__ void __launch_bounds__(kThreads) k_fill_regular32(GeoView g, TabView tv, float k, float kpi,
+                                                             float scale, float inv_k2, float2* Z, int64_t ldz) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Tab32 T{tv.hash, tv.node32, tv.c32a, tv.c32b, tv.n_nodes, tv.n_hash, tv.r_lo32, tv.inv_dr32};
+  if (TABLE && SMEM) {
+    const int nn = tv.n_nodes;
+    float4* sa = reinterpret_cast<float4*>(smem);
+    float4* sb = sa + (nn - 1);
+    float* sn = reinterpret_cast<float*>(sb + (nn - 1));
+    int32_t* sh = reinterpret_cast<int32_t*>(sn + nn);
+    for (int i = threadIdx.x; i < nn - 1; i += blockDim.x) {
+      sa[i] = tv.c32a[i];
+      sb[i] = tv.c32b[i];
+    }
+    for (int i = threadIdx.x; i < nn; i += blockDim.x) sn[i] = tv.node32[i];
+    for (int i = threadIdx.x; i < tv.n_hash; i += blockDim.x) sh[i] = tv.hash[i];
+    __syncthreads();
+    T.ca = sa;
+    T.cb = sb;
+    T.node = sn;
+    T.hash = sh;
+  }
+  const int lane = threadIdx.x & 31;
+  const int m = g.m;
+  const int64_t nchunk = (g.nt + 31) / 32;
+  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
+    const int p = (int)(task / nchunk);
+    const int q0 = (int)(task % nchunk) * 32;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+    if (!__any_sync(0xffffffffu, ok)) continue;
+    float4 beta[kMaxRule];
+#pragma unroll
+    for (int b = 0; b < kMaxRule; ++b)
+      if (b < m) beta[b] = g.pts32[(size_t)b * g.nt + q];
+    KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
+    for (int a = 0; a < m; ++a) {
+      const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+      float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < kMaxRule; ++b) {
+        if (b < m) {
+          const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+          const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+          const float rs = rsqrtf(R2);
+          const float R = R2 * rs;
+          float gr, gi;
+          if (TABLE) {
+            float2 f = lookup32(T, R);  // e^{-jkR}/R
+            gr = f.x * beta[b].w;
+            gi = f.y * beta[b].w;
+          } else {
+            float sn, cs;
+            sincospif(R * kpi, &sn, &cs);  // kR / pi
+            const float wr = beta[b].w * rs;
+            gr = cs * wr;
+            gi = -sn * wr;
+          }
+          s0r += gr;
+          s0i += gi;
+          sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
+          sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
+          sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
+          sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
+          sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
+          sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
+        }
+      }
+      const float wa = al.w;
+      M0r.add(wa * s0r);
+      M0i.add(wa * s0i);
+      const float wal[3] = {wa * al.x, wa * al.y, wa * al.z};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Mar[c].add(wal[c] * s0r);
+        Mai[c].add(wal[c] * s0i);
+        Mbr[c].add(wa * sbr[c]);
+        Mbi[c].add(wa * sbi[c]);
+      }
+      Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
+      Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
+    }
+    if (!ok) continue;
+    const int4 ep = g.tedge[p], eq = g.tedge[q];
+    const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+    const float m0r = M0r.s, m0i = M0i.s;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (!edge_valid(ecp[i])) continue;
+      const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
+      const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
+      const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
+      float2* zrow = Z + (int64_t)edge_of(ecp[i]) * ldz;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        if (!edge_valid(ecq[j])) continue;
+        const float4 gq = g.geo32[3 * (size_t)q + j];  // eps_j, s_j l_j
+        const float eMar = gq.x * Mar[0].s + gq.y * Mar[1].s + gq.z * Mar[2].s;
+        const float eMai = gq.x * Mai[0].s + gq.y * Mai[1].s + gq.z * Mai[2].s;
+        const float de = gp.x * gq.x + gp.y * gq.y + gp.z * gq.z;
+        const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
+        const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
+        const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
+        // j * c * (br + j bi) = c * (-bi + j br)
+        atomicAdd(zrow + edge_of(ecq[j]), make_float2(-c * bi, c * br));
+      }
+    }
+  }
+}
+
+template <bool TABLE>
+__global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView tv, double k, double scale,
+                                                             double inv_k2, double2* Z, int64_t ldz) {
+  const int lane = threadIdx.x & 31;
+  const int m = g.m;
+  const int64_t nchunk = (g.nt + 31) / 32;
+  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
+    const int p = (int)(task / nchunk);
+    const int q0 = (int)(task % nchunk) * 32;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp32 = g.cen32[p], cq32 = g.cen32[q];
+    const float3 dc32 = make_float3(cp32.x - cq32.x, cp32.y - cq32.y, cp32.z - cq32.z);
+    const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc32);
+    if (!ok) continue;
+    const double* cp = g.cen64 + 4 * (size_t)p;
+    const double* cq = g.cen64 + 4 * (size_t)q;
+    const double dx = cp[0] - cq[0], dy = cp[1] - cq[1], dz = cp[2] - cq[2];
+    double M0r = 0, M0i = 0, Mar[3] = {0, 0, 0}, Mai[3] = {0, 0, 0}, Mbr[3] = {0, 0, 0}, Mbi[3] = {0, 0, 0};
+    double Mabr = 0, Mabi = 0;
+    for (int a = 0; a < m; ++a) {
+      const double* al = g.pts64 + 4 * ((size_t)a * g.nt + p);
+      const double ux = dx + al[0], uy = dy + al[1], uz = dz + al[2];
+      double s0r = 0, s0i = 0, sbr[3] = {0, 0, 0}, sbi[3] = {0, 0, 0};
+      for (int b = 0; b < m; ++b) {
+        const double* be = g.pts64 + 4 * ((size_t)b * g.nt + q);
+        const double rx = ux - be[0], ry = uy - be[1], rz = uz - be[2];
+        const double R = sqrt(rx * rx + ry * ry + rz * rz);
+        double gr, gi;
+        if (TABLE) {
+          double2 f = lookup64(tv, R);
+          gr = f.x * be[3];
+          gi = f.y * be[3];
+        } else {
+          double sn, cs;
+          sincos(k * R, &sn, &cs);
+          const double wr = be[3] / R;
+          gr = cs * wr;
+          gi = -sn * wr;
+        }
+        s0r += gr;
+        s0i += gi;
+        for (int c = 0; c < 3; ++c) {
+          sbr[c] += be[c] * gr;
+          sbi[c] += be[c] * gi;
+        }
+      }
+      const double wa = al[3];
+      M0r += wa * s0r;
+      M0i += wa * s0i;
+      for (int c = 0; c < 3; ++c) {
+        Mar[c] += wa * al[c] * s0r;
+        Mai[c] += wa * al[c] * s0i;
+        Mbr[c] += wa * sbr[c];
+        Mbi[c] += wa * sbi[c];
+      }
+      Mabr += wa * (al[0] * sbr[0] + al[1] * sbr[1] + al[2] * sbr[2]);
+      Mabi += wa * (al[0] * sbi[0] + al[1] * sbi[1] + al[2] * sbi[2]);
+    }
+    const int4 ep = g.tedge[p], eq = g.tedge[q];
+    const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+    for (int i = 0; i < 3; ++i) {
+      if (!edge_valid(ecp[i])) continue;
+      const double* gp = g.geo64 + 4 * (3 * (size_t)p + i);
+      const double dMbr = gp[0] * Mbr[0] + gp[1] * Mbr[1] + gp[2] * Mbr[2];
+      const double dMbi = gp[0] * Mbi[0] + gp[1] * Mbi[1] + gp[2] * Mbi[2];
+      double* zrow = reinterpret_cast<double*>(Z + (int64_t)edge_of(ecp[i]) * ldz);
+      for (int j = 0; j < 3; ++j) {
+        if (!edge_valid(ecq[j])) continue;
+        const double* gq = g.geo64 + 4 * (3 * (size_t)q + j);
+        const double eMar = gq[0] * Mar[0] + gq[1] * Mar[1] + gq[2] * Mar[2];
+        const double eMai = gq[0] * Mai[0] + gq[1] * Mai[1] + gq[2] * Mai[2];
+        const double de = gp[0] * gq[0] + gp[1] * gq[1] + gp[2] * gq[2];
+        const double br = 0.25 * (Mabr + eMar + dMbr + de * M0r) - M0r * inv_k2;
+        const double bi = 0.25 * (Mabi + eMai + dMbi + de * M0i) - M0i * inv_k2;
+        const double c = scale * gp[3] * gq[3];
+        double* z = zrow + 2 * edge_of(ecq[j]);
+        atomicAdd(z, -c * bi);
+        atomicAdd(z + 1, c * br);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- near pairs (FP64)
+struct NearArgs {
+  double k, scale, inv_k2;
+  int nphi, nl;
+  double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
+};
+
+struct C2 {
+  double re, im;
+};
+
+__device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
+  if (use_table && R >= te->r_lo && R <= te->r_hi) {
+    double2 f = lookup64(*te, R);
+    return C2{f.x, f.y};
+  }
+  double s, c;
+  sincos(k * R, &s, &c);
+  return C2{c, -s};
+}
+
+// Inner integrals over triangle v for observation point r (1/(4 pi) included).
+__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, const TabView* te,
+                                bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
+  const double k = A.k;
+  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  n[0] *= inv;
+  n[1] *= inv;
+  n[2] *= inv;
+  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+  const double d = fabs(h);
+  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  const C2 ed = exp_mjkr(k, d, te, use_table);
+  double sre = 0, sim = 0;                       // scalar sector sums
+  double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0};  // vector remainder
+  double vst[3] = {0, 0, 0};                     // vector static part
+  for (int e = 0; e < 3; ++e) {
+    const double* a = v[e];
+    const double* b = v[(e + 1) % 3];
+    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    t[0] /= len;
+    t[1] /= len;
+    t[2] /= len;
+    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
+    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
+    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
+    if (fabs(P0) > 1e-12 * len) {
+      const double aP = fabs(P0);
+      const double um = asinh(lm / aP), up = asinh(lp / aP);
+      const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
+      double cr = 0, ci = 0;
+      for (int i = 0; i < A.nphi; ++i) {
+        const double u = mid + half * A.gx_phi[i];
+        const double ch = cosh(u);
+        const double rho = aP * ch;
+        const double Re = sqrt(rho * rho + d * d);
+        const C2 eR = exp_mjkr(k, Re, te, use_table);
+        const double wt = A.gw_phi[i] / ch;
+        cr += (ed.re - eR.re) * wt;
+        ci += (ed.im - eR.im) * wt;
+      }
+      const double sg = P0 > 0 ? half : -half;
+      sre += cr * sg;
+      sim += ci * sg;
+    }
+    double lr = 0, li = 0;
+    for (int i = 0; i < A.nl; ++i) {
+      const double s = 0.5 * len * (A.gx_l[i] + 1.0);
+      const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
+      const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+      const C2 eR = exp_mjkr(k, R, te, use_table);
+      lr += (eR.re - 1.0) * A.gw_l[i];
+      li += (eR.im + k * R) * A.gw_l[i];
+    }
+    lr *= 0.5 * len;
+    li *= 0.5 * len;
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    if (R02 > 0) {
+      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
+      st += 0.5 * R02 * (log(fp) - log(fm));
+    }
+    for (int x = 0; x < 3; ++x) {
+      vre[x] += mh[x] * lr;
+      vim[x] += mh[x] * li;
+      vst[x] += mh[x] * st;
+    }
+  }
+  const double c4 = 1.0 / (4.0 * kPi);
+  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
+  I0->re = sim / k * c4;
+  I0->im = -sre / k * c4;
+  for (int x = 0; x < 3; ++x) {
+    I1[x].re = (-vim[x] / k + vst[x]) * c4;
+    I1[x].im = (vre[x] / k) * c4;
+  }
+}
+
+template <class Out>
+__global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
+                                                   int64_t ldz) {
+  const int64_t n_near = g.near_ptr[g.nt];
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_near;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = g.nt - 1;  // p = row containing idx
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (g.near_ptr[mid] <= idx) lo = mid;
+      else hi = mid - 1;
+    }
+    const int p = lo, q = g.near_idx[idx];
+    double vp[3][3], vq[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) {
+        vp[c][x] = g.v64[9 * (size_t)p + 3 * c + x];
+        vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
+      }
+    const double* cp = g.cen64 + 4 * (size_t)p;
+    const double area_q = g.cen64[4 * (size_t)q + 3];
+    double accr[3][3], acci[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.0;
+    for (int a = 0; a < g.m; ++a) {
+      const double* al = g.pts64 + 4 * ((size_t)a * g.nt + p);
+      const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
+      C2 I0, I1[3];
+      double rho0[3];
+      inner_integrals(ra, vq, A, &te, use_table, &I0, I1, rho0);
+      for (int j = 0; j < 3; ++j) {
+        // J_j = I1 + (rho0 - v_j) I0
+        C2 J[3];
+        for (int x = 0; x < 3; ++x) {
+          const double dv = rho0[x] - vq[j][x];
+          J[x].re = I1[x].re + dv * I0.re;
+          J[x].im = I1[x].im + dv * I0.im;
+        }
+        for (int i = 0; i < 3; ++i) {
+          const double f0 = ra[0] - vp[i][0], f1 = ra[1] - vp[i][1], f2 = ra[2] - vp[i][2];
+          const double dr = f0 * J[0].re + f1 * J[1].re + f2 * J[2].re;
+          const double di = f0 * J[0].im + f1 * J[1].im + f2 * J[2].im;
+          accr[i][j] += al[3] * (0.25 * dr - I0.re * A.inv_k2);
+          acci[i][j] += al[3] * (0.25 * di - I0.im * A.inv_k2);
+        }
+      }
+    }
+    const int4 ep = g.tedge[p], eq = g.tedge[q];
+    const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+    for (int i = 0; i < 3; ++i) {
+      if (!edge_valid(ecp[i])) continue;
+      const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3];
+      for (int j = 0; j < 3; ++j) {
+        if (!edge_valid(ecq[j])) continue;
+        const double slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
+        const double c = A.scale * slp * slq / area_q;  // k eta s_i l_i s_j l_j / A_q
+        const double zr = -c * acci[i][j], zi = c * accr[i][j];
+        Out* z = Z + (int64_t)edge_of(ecp[i]) * ldz + edge_of(ecq[j]);
+        if constexpr (sizeof(Out) == 8) {
+          atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
+        } else {
+          atomicAdd(reinterpret_cast<double*>(z), zr);
+          atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
+        }
+      }
+    }
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+int64_t pair_grid(const GeoView& g, int blocks_per_sm) {
+  const int64_t ntask = (int64_t)g.nt * ((g.nt + 31) / 32);
+  int64_t blocks = (ntask + kWarps - 1) / kWarps;
+  return std::min<int64_t>(blocks, (int64_t)sm_count() * blocks_per_sm);
+}
+
+}  // namespace
+
+cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
+                                 const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
+                                 float4* geo32, double* pts64, double* cen64, double* geo64, cudaStream_t s) {
+  k_prep_geometry<<<(nt + 127) / 128, 128, 0, s>>>(v64, nt, m, bary, w, tedge, edge_len, pts32, cen32, geo32,
+                                                   pts64, cen64, geo64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_image(int kind, double k, int degree, int n, const double* node64, const int8_t* zflag,
+                               float* node32, double2* c64, float4* c32a, float4* c32b, double* fval, int n_hash,
+                               double r_lo, double dr, int32_t* hash, cudaStream_t s) {
+  k_table_values<<<(n + 255) / 256, 256, 0, s>>>(kind, k, n, node64, zflag, fval);
+  k_table_coef<<<(n + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, c64, node32, c32a, c32b);
+  k_table_hash<<<(n_hash + 255) / 256, 256, 0, s>>>(n, node64, n_hash, r_lo, dr, hash);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n, void* out,
+                              cudaStream_t s) {
+  (void)kind;
+  int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
+  if (precision == GF_FP32)
+    k_table_eval32<<<(unsigned)blocks, 256, 0, s>>>(t, (const float*)r, n, (float2*)out);
+  else
+    k_table_eval64<<<(unsigned)blocks, 256, 0, s>>>(t, (const double*)r, n, (double2*)out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s) {
+  k_range_init<<<1, 1, 0, s>>>(d_minmax);
+  int64_t blocks = pair_grid(g, 8);
+  if (precision == GF_FP64)
+    k_range<true><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
+  else
+    k_range<false><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int precision, double k, double eta, void* Z,
+                                int64_t ldz, cudaStream_t s) {
+  const double scale = k * eta / (4.0 * kPi);
+  TabView tv{};
+  if (green) tv = *green;
+  if (precision == GF_FP64) {
+    int64_t blocks = pair_grid(g, 4);
+    if (green)
+      k_fill_regular64<true><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, 1.0 / (k * k), (double2*)Z, ldz);
+    else
+      k_fill_regular64<false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, 1.0 / (k * k), (double2*)Z, ldz);
+    return cudaGetLastError();
+  }
+  const float kpi = (float)(k / kPi);
+  if (!green) {
+    int64_t blocks = pair_grid(g, 4);
+    k_fill_regular32<false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kpi, (float)scale,
+                                                                         (float)(1.0 / (k * k)), (float2*)Z, ldz);
+    return cudaGetLastError();
+  }
+  size_t smem = tv.smem32_bytes();
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem <= (size_t)max_optin) {
+    cudaError_t e = cudaFuncSetAttribute(k_fill_regular32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_regular32<true, true>, kThreads, smem);
+    int64_t blocks = pair_grid(g, std::max(per_sm, 1));
+    k_fill_regular32<true, true><<<(unsigned)blocks, kThreads, smem, s>>>(g, tv, (float)k, kpi, (float)scale,
+                                                                          (float)(1.0 / (k * k)), (float2*)Z, ldz);
+  } else {
+    int64_t blocks = pair_grid(g, 4);
+    k_fill_regular32<true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kpi, (float)scale,
+                                                                        (float)(1.0 / (k * k)), (float2*)Z, ldz);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, double k, double eta, int nphi,
+                             int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz, cudaStream_t s) {
+  NearArgs A;
+  A.k = k;
+  A.scale = k * eta;
+  A.inv_k2 = 1.0 / (k * k);
+  A.nphi = nphi;
+  A.nl = nl;
+  for (int i = 0; i < 32; ++i) {
+    A.gx_phi[i] = gl_phi[i];
+    A.gw_phi[i] = gl_phi[32 + i];
+    A.gx_l[i] = gl_l[i];
+    A.gw_l[i] = gl_l[32 + i];
+  }
+  TabView te{};
+  if (texp) te = *texp;
+  const int64_t n_near = 0;  // read on the device
+  (void)n_near;
+  int64_t blocks = (int64_t)sm_count() * 8;
+  if (precision == GF_FP32)
+    k_fill_near<float2><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
+  else
+    k_fill_near<double2><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (double2*)Z, ldz);
+  return cudaGetLastError();
+}
+
+}  // namespace gf

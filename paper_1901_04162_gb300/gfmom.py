@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libgfmom (include/gfmom.h), same names as the C ABI.
+
+Argument marshalling only: every step of the fill runs in the library
+(host-side topology and table sample placement in C++, everything else in
+sm_103a kernels). PyTorch supplies device memory and streams. There is no
+fallback: if the library cannot be built or loaded, or a call fails, an
+exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+GF_OK = 0
+GF_FP32, GF_FP64 = 32, 64
+GF_GREEN, GF_EXP = 1, 0
+_STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_CUDA", -5: "GF_ERR_ALLOC",
+           -6: "GF_ERR_DEVICE"}
+
+EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
+           "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
+           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill"]
+
+
+class GfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gf_params(C.Structure):
+    _fields_ = [("rule", C.c_int), ("table_tol", C.c_double), ("green_n_per_lambda", C.c_int),
+                ("exp_n_per_lambda", C.c_int), ("lagrange_degree", C.c_int), ("refine", C.c_int),
+                ("refine_factor", C.c_double), ("refine_halfwidth_t", C.c_double), ("merge_t", C.c_double),
+                ("grade", C.c_int), ("nphi", C.c_int), ("nl", C.c_int), ("eta", C.c_double)]
+
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Loads (building first if missing or stale) the in-tree libgfmom.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, i64, dp = C.c_void_p, C.c_int64, C.POINTER(C.c_double)
+        L.gf_params_default.argtypes = [C.POINTER(gf_params)]
+        L.gf_params_default.restype = None
+        L.gf_last_error.restype = C.c_char_p
+        L.gf_mesh_create.argtypes = [vp, i64, vp, i64, C.c_double, C.POINTER(vp)]
+        L.gf_mesh_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+        L.gf_mesh_edges.argtypes = [vp, vp, vp]
+        L.gf_mesh_set_vertices.argtypes = [vp, vp]
+        L.gf_mesh_destroy.argtypes = [vp]
+        L.gf_range.argtypes = [vp, C.c_int, C.c_int, dp, dp, vp]
+        L.gf_table_create.argtypes = [C.c_double, C.c_double, C.c_double, C.POINTER(gf_params), vp, C.POINTER(vp)]
+        L.gf_table_info.argtypes = [vp, C.c_int, C.POINTER(i64), C.POINTER(i64), dp]
+        L.gf_table_nodes.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+        L.gf_table_eval.argtypes = [vp, C.c_int, C.c_int, vp, i64, vp, vp]
+        L.gf_table_destroy.argtypes = [vp]
+        L.gf_fill.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
+        for name in EXPORTS:
+            if name not in ("gf_params_default", "gf_last_error"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != GF_OK:
+        raise GfError(st, lib().gf_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    return C.c_void_p(getattr(stream, "cuda_stream", stream))
+
+
+# ----------------------------------------------------------------------------
+# C-ABI mirrors
+# ----------------------------------------------------------------------------
+def gf_params_default(**overrides) -> gf_params:
+    p = gf_params()
+    lib().gf_params_default(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def gf_last_error() -> str:
+    return lib().gf_last_error().decode()
+
+
+def gf_mesh_create(xyz, tri, near_dist=0.0):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    if xyz.ndim != 2 or xyz.shape[1] != 3 or tri.ndim != 2 or tri.shape[1] != 3:
+        raise ValueError("xyz must be [nv,3] and tri [nt,3]")
+    h = C.c_void_p()
+    _check(lib().gf_mesh_create(_ptr(xyz), len(xyz), _ptr(tri), len(tri), float(near_dist), C.byref(h)))
+    return h
+
+
+def gf_mesh_info(h):
+    out = [C.c_int64() for _ in range(4)]
+    _check(lib().gf_mesh_info(h, *[C.byref(o) for o in out]))
+    return tuple(o.value for o in out)
+
+
+def gf_mesh_edges(h):
+    ne = gf_mesh_info(h)[2]
+    ev = np.zeros((ne, 2), np.int32)
+    et = np.zeros((ne, 2), np.int32)
+    _check(lib().gf_mesh_edges(h, _ptr(ev), _ptr(et)))
+    return ev, et
+
+
+def gf_mesh_set_vertices(h, xyz):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    _check(lib().gf_mesh_set_vertices(h, _ptr(xyz)))
+
+
+def gf_mesh_destroy(h):
+    _check(lib().gf_mesh_destroy(h))
+
+
+def gf_range(h, rule, precision=GF_FP32, stream=None):
+    lo, hi = C.c_double(), C.c_double()
+    _check(lib().gf_range(h, int(rule), int(precision), C.byref(lo), C.byref(hi), _stream_ptr(stream)))
+    return lo.value, hi.value
+
+
+def gf_table_create(k, r_min, r_max, params=None, stream=None):
+    params = params or gf_params_default()
+    h = C.c_void_p()
+    _check(lib().gf_table_create(float(k), float(r_min), float(r_max), C.byref(params), _stream_ptr(stream),
+                                 C.byref(h)))
+    return h
+
+
+def gf_table_info(h, kind):
+    n, L, dr = C.c_int64(), C.c_int64(), C.c_double()
+    _check(lib().gf_table_info(h, int(kind), C.byref(n), C.byref(L), C.byref(dr)))
+    return n.value, L.value, dr.value
+
+
+def gf_table_nodes(h, kind):
+    n, L, _ = gf_table_info(h, kind)
+    r, fr, fi = np.zeros(n), np.zeros(n), np.zeros(n)
+    hsh = np.zeros(L, np.int32)
+    _check(lib().gf_table_nodes(h, int(kind), _ptr(r), _ptr(fr), _ptr(fi), _ptr(hsh)))
+    return r, fr + 1j * fi, hsh
+
+
+def gf_table_eval(h, kind, r, stream=None):
+    """r: CUDA tensor (float32 or float64); returns complex tensor of f(r)."""
+    import torch
+    if not r.is_cuda:
+        raise ValueError("gf_table_eval needs a CUDA tensor")
+    r = r.contiguous()
+    prec = GF_FP32 if r.dtype == torch.float32 else GF_FP64
+    out = torch.empty(r.numel(), dtype=torch.complex64 if prec == GF_FP32 else torch.complex128, device=r.device)
+    _check(lib().gf_table_eval(h, int(kind), prec, C.c_void_p(r.data_ptr()), r.numel(),
+                               C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def gf_table_destroy(h):
+    _check(lib().gf_table_destroy(h))
+
+
+def gf_fill(mesh, k, params, table, precision, Z, ldz=None, stream=None):
+    """Z: CUDA tensor (complex64 for GF_FP32, complex128 for GF_FP64), at
+    least [ne, ldz] row-major; overwritten."""
+    import torch
+    want = torch.complex64 if precision == GF_FP32 else torch.complex128
+    if not Z.is_cuda or Z.dtype != want or not Z.is_contiguous():
+        raise ValueError(f"Z must be a contiguous CUDA {want} tensor")
+    ldz = Z.shape[-1] if ldz is None else ldz
+    _check(lib().gf_fill(mesh, float(k), C.byref(params), table, int(precision), C.c_void_p(Z.data_ptr()),
+                         int(ldz), _stream_ptr(stream)))
+    return Z
+
+
+# ----------------------------------------------------------------------------
+# convenience objects
+# ----------------------------------------------------------------------------
+class Mesh:
+    """Owns a gf_mesh handle."""
+
+    def __init__(self, xyz, tri, near_dist=0.0):
+        self.h = gf_mesh_create(xyz, tri, near_dist)
+        self.nv, self.nt, self.ne, self.n_near = gf_mesh_info(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().gf_mesh_destroy(h)
+            self.h = None
+
+    def edges(self):
+        return gf_mesh_edges(self.h)
+
+    def set_vertices(self, xyz):
+        gf_mesh_set_vertices(self.h, xyz)
+
+    def range(self, rule, precision=GF_FP32, stream=None):
+        return gf_range(self.h, rule, precision, stream)
+
+
+class Table:
+    """Owns a gf_table handle (Green + Exp tables for one k and range)."""
+
+    def __init__(self, k, r_min, r_max, params=None, stream=None):
+        self.k = k
+        self.h = gf_table_create(k, r_min, r_max, params, stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().gf_table_destroy(h)
+            self.h = None
+
+    def info(self, kind=GF_GREEN):
+        return gf_table_info(self.h, kind)
+
+    def nodes(self, kind=GF_GREEN):
+        return gf_table_nodes(self.h, kind)
+
+    def __call__(self, r, kind=GF_GREEN, stream=None):
+        return gf_table_eval(self.h, kind, r, stream)
+
+
+def fill(mesh: Mesh, k, params=None, table: Table | None = None, precision=GF_FP32, Z=None, stream=None,
+         device=None):
+    """Returns Z (torch, row-major [ne, ne]) filled on the current stream."""
+    import torch
+    params = params or gf_params_default()
+    if Z is None:
+        dt = torch.complex64 if precision == GF_FP32 else torch.complex128
+        Z = torch.empty((mesh.ne, mesh.ne), dtype=dt, device=device or "cuda")
+    return gf_fill(mesh.h, k, params, table.h if table is not None else None, precision, Z, stream=stream)

@@ -1,0 +1,129 @@
+"""GPU fill vs the FP64 oracle on the same seeded meshes: element-wise on
+small meshes and on the 0.5 lambda plate (FP64, 1e-12), relative Frobenius
+<= 1e-5 in FP32, sampled rows on the 7680-unknown sphere, and edge cases."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1901_04162_gb300 as gf
+import workloads as W
+from gpu_util import rel_fro, rel_max
+
+pytestmark = pytest.mark.gpu
+K = 2 * math.pi
+
+
+def gpu_fill(xyz, tri, k, rule, precision, table=True, near_dist=0.0, **pk):
+    m = gf.Mesh(xyz, tri, near_dist)
+    p = gf.gf_params_default(rule=rule, **pk)
+    tab = None
+    if table:
+        lo, hi = m.range(rule, precision)
+        tab = gf.Table(k, lo, hi, p)
+    z = gf.fill(m, k, p, tab, precision).cpu().numpy()
+    return m, z, tab
+
+
+def oracle_full(xyz, tri, k, rule, table=True, near_dist=0.0, **kw):
+    om = O.Mesh(xyz, tri, near_dist)
+    if table:
+        lo, hi = om.range(rule)
+        return om.z_full(k, rule, mode="table", tables=O.make_tables(k, lo, hi), **kw)
+    return om.z_full(k, rule, **kw)
+
+
+@pytest.mark.parametrize("table", [False, True])
+def test_plate_fp64_matches_oracle(table):
+    wl = W.plate_280()
+    m, z, _ = gpu_fill(wl.xyz, wl.tri, wl.k, 3, gf.GF_FP64, table)
+    ref = oracle_full(wl.xyz, wl.tri, wl.k, 3, table)
+    assert m.ne == 280
+    assert rel_fro(z, ref) <= 1e-12
+    assert rel_max(z, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("rule", [3, 4, 6, 7])
+@pytest.mark.parametrize("table", [False, True])
+def test_small_sphere_fp32_matches_oracle(rule, table):
+    xyz, tri = W.octasphere(2, 1.0)
+    xyz = W.jitter(xyz, tri, 0.02, 3)
+    _, z, _ = gpu_fill(xyz, tri, K, rule, gf.GF_FP32, table)
+    ref = oracle_full(xyz, tri, K, rule, table)
+    assert rel_fro(z, ref) <= 1e-5
+    assert rel_max(z, ref) <= 1e-5
+
+
+def test_small_sphere_fp64_both_modes():
+    xyz, tri = W.icosphere(1, 0.7)
+    for table in (False, True):
+        _, z, _ = gpu_fill(xyz, tri, K, 6, gf.GF_FP64, table)
+        ref = oracle_full(xyz, tri, K, 6, table)
+        assert rel_fro(z, ref) <= 1e-12
+
+
+def test_range_matches_oracle():
+    wl = W.plate_280()
+    m = gf.Mesh(wl.xyz, wl.tri)
+    om = O.Mesh(wl.xyz, wl.tri)
+    for rule in (3, 7):
+        lo, hi = om.range(rule)
+        g64 = m.range(rule, gf.GF_FP64)
+        g32 = m.range(rule, gf.GF_FP32)
+        assert abs(g64[0] - lo) <= 1e-14 * lo and abs(g64[1] - hi) <= 1e-14 * hi
+        assert abs(g32[0] - lo) <= 1e-6 * lo and abs(g32[1] - hi) <= 1e-6 * hi
+
+
+def test_near_dist_criterion_matches_oracle():
+    wl = W.cube_73728(3)
+    _, z, _ = gpu_fill(wl.xyz, wl.tri, wl.k, 4, gf.GF_FP64, True, near_dist=0.6)
+    ref = oracle_full(wl.xyz, wl.tri, wl.k, 4, True, near_dist=0.6)
+    assert rel_fro(z, ref) <= 1e-12
+
+
+def test_sphere_7680_sampled_rows():
+    wl = W.sphere_7680()
+    m, z, tab = gpu_fill(wl.xyz, wl.tri, wl.k, 7, gf.GF_FP32, True)
+    lo, hi = m.range(7, gf.GF_FP64)
+    om = O.Mesh(wl.xyz, wl.tri)
+    rows = np.random.default_rng(11).choice(m.ne, 12, replace=False)
+    ref = om.z_rows(wl.k, 7, rows, mode="table", tables=O.make_tables(wl.k, lo, hi))
+    assert rel_fro(z[rows], ref) <= 1e-5
+    # the diagonal blocks (self and near terms) of the sampled rows
+    assert rel_max(z[rows, rows], ref[np.arange(len(rows)), rows]) <= 1e-5
+
+
+def test_ldz_padding_untouched_and_open_plate():
+    xyz, tri = W.plate(0.3, 4)
+    m = gf.Mesh(xyz, tri)
+    ev, et = m.edges()
+    assert m.ne == 40  # interior edges of a 4 x 4 split-square plate
+    p = gf.gf_params_default(rule=3)
+    lo, hi = m.range(3, gf.GF_FP64)
+    tab = gf.Table(K, lo, hi, p)
+    Z = torch.full((m.ne, m.ne + 5), 7.0 + 7.0j, dtype=torch.complex128, device="cuda")
+    gf.gf_fill(m.h, K, p, tab.h, gf.GF_FP64, Z, ldz=m.ne + 5)
+    Zc = Z.cpu().numpy()
+    assert np.all(Zc[:, m.ne:] == 7.0 + 7.0j)
+    ref = oracle_full(xyz, tri, K, 3, True)
+    assert rel_fro(Zc[:, :m.ne], ref) <= 1e-12
+
+
+def test_errors():
+    xyz, tri = W.plate(0.1, 1)  # two triangles: every pair is near
+    m = gf.Mesh(xyz, tri)
+    with pytest.raises(gf.GfError):
+        m.range(3)
+    z = gf.fill(m, K, gf.gf_params_default(rule=3), None, gf.GF_FP64).cpu().numpy()
+    ref = oracle_full(xyz, tri, K, 3, False)
+    assert rel_fro(z, ref) <= 1e-12
+    with pytest.raises(gf.GfError):
+        gf.Mesh(np.zeros((4, 3)), np.array([[0, 1, 2], [0, 1, 3], [1, 0, 3]], np.int32))
+    with pytest.raises(ValueError):
+        gf.gf_fill(m.h, K, gf.gf_params_default(), None, gf.GF_FP32, torch.zeros(1, 1, dtype=torch.complex128,
+                                                                                   device="cuda"))
+    t = gf.Table(K, 0.1, 1.0)
+    with pytest.raises(gf.GfError):  # table built for another k
+        gf.fill(m, 2 * K, gf.gf_params_default(rule=3), t, gf.GF_FP64)

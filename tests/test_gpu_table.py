@@ -1,0 +1,60 @@
+"""GPU tables vs the oracle's (Section II.B-C): identical sample positions and
+hash array, node values to the last bits, device lookups in FP64 and FP32."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1901_04162_gb300 as gf
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2 * math.pi, 0.0471, 0.684), (2 * math.pi, 0.03, 2.06), (4 * math.pi, 0.011, 7.9),
+         (math.pi, 0.2, 5.2), (2 * math.pi, 1e-4, 1.0)]
+
+
+@pytest.mark.parametrize("k,lo,hi", CASES)
+def test_samples_and_hash_match_oracle(k, lo, hi):
+    t = gf.Table(k, lo, hi)
+    og, oe = O.make_tables(k, lo, hi)
+    for kind, ot in ((gf.GF_GREEN, og), (gf.GF_EXP, oe)):
+        r, f, h = t.nodes(kind)
+        orr, of, oh = ot.nodes()
+        np.testing.assert_array_equal(r, orr)
+        np.testing.assert_array_equal(h, oh)
+        n, L, dr = t.info(kind)
+        assert (n, L, dr) == (ot.n_nodes, ot.n_hash, ot.dr)
+        # CUDA's and the C library's sincos may differ in the last bits
+        np.testing.assert_allclose(f, of, rtol=4e-16, atol=0)
+        assert np.all((f.real == 0) == (of.real == 0)) and np.all((f.imag == 0) == (of.imag == 0))
+
+
+@pytest.mark.parametrize("k,lo,hi", CASES)
+def test_device_lookup_matches_oracle(k, lo, hi):
+    t = gf.Table(k, lo, hi)
+    og, oe = O.make_tables(k, lo, hi)
+    rng = np.random.default_rng(1)
+    r64 = np.concatenate([rng.uniform(lo, hi, 200000), t.nodes(gf.GF_GREEN)[0], [lo, hi]])
+    r32 = r64.astype(np.float32).astype(np.float64)
+    r32 = r32[(r32 >= lo) & (r32 <= hi)]
+    for kind, ot in ((gf.GF_GREEN, og), (gf.GF_EXP, oe)):
+        ref = ot(r64)
+        got = t(torch.from_numpy(r64).cuda(), kind).cpu().numpy()
+        assert np.max(np.abs(got - ref) / np.abs(ref)) < 1e-13
+        ref32 = ot(r32)
+        got32 = t(torch.from_numpy(r32.astype(np.float32)).cuda(), kind).cpu().numpy()
+        assert np.max(np.abs(got32 - ref32) / np.abs(ref32)) < 1e-6
+
+
+@pytest.mark.parametrize("k,lo,hi", CASES[:4])
+def test_device_table_vs_direct_1e6(k, lo, hi):
+    # spec accuracy: table Green values vs direct at relative <= 1e-6 (FP64)
+    t = gf.Table(k, lo, hi)
+    r = np.random.default_rng(2).uniform(lo, hi, 10**6)
+    got = t(torch.from_numpy(r).cuda(), gf.GF_GREEN).cpu().numpy()
+    exact = np.exp(-1j * k * r) / r
+    assert np.max(np.abs(got - exact) / np.abs(exact)) <= 1e-6
+    got = t(torch.from_numpy(r).cuda(), gf.GF_EXP).cpu().numpy()
+    assert np.max(np.abs(got - np.exp(-1j * k * r))) <= 1e-6
