@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the EFIE impedance-matrix fill with the adaptive Green table.
+
+Default workload: PEC sphere r = 1 lambda, icosphere with 5120 triangles
+(7680 RWG unknowns), vertices jittered by 2% of the mean edge length, 7-point
+rule on both triangles, FP32 table fill with Kahan outer sums, FP64 near
+terms, table tolerance 1e-6. Synthetic, seeded input.
+
+One step = the whole hot path on a device-resident mesh: R_min/R_max
+reduction, Green + Exp table construction, zeroing Z, the regular-pair fill
+kernel and the near-pair kernel. `value` is Z entries / s over all ranks.
+Alongside: the direct (sincospi) fill on the same mesh, the regular kernel's
+roofline fraction, an end-to-end number through the C ABI from host arrays to
+a host copy of Z, the oracle's accuracy check on sampled rows, and the FP64
+CPU oracle timed on a bounded sample (the CPU baseline).
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+FALLBACK_SM_MHZ = 2070.0
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
+# table kernel, from the ncu capture summarised in profiles/; valid only while
+# the kernel source hash matches.
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "67e1a6b659a43fd1"): 925523200}
+
+
+def kernel_source_hash():
+    path = os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", "gf_kernels.cu")
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+
+
+WORKLOADS = {
+    "sphere_7680": W.sphere_7680,
+    "plate_280": W.plate_280,
+    "sphere_3072": W.sphere_3072,
+    "cube_73728": W.cube_73728,
+}
+
+
+def regular_ops_per_pair(m):
+    """FP32 lane operations of the algorithm per regular triangle pair:
+    28 per Green evaluation (distance 7, table lookup + cubic 11, weight 2,
+    moment sums 8), 92 per test point (offset 3, 16 compensated moment
+    updates 80, weighted offsets 3, alpha . S_beta 6), 210 for the 3 x 3 RWG
+    block of the pair."""
+    return 28 * m * m + 92 * m + 210
+
+
+# ----------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampler (200 ms) for the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": FALLBACK_SM_MHZ}, "fallback"
+
+
+# ----------------------------------------------------------------------------
+def oracle_baseline(wl, target_s=12.0, reference=False):
+    """The FP64 CPU oracle as it stands on the host cores: range reduction,
+    tables and a sample of Z rows; returns seconds per full fill projected
+    from the sample, and a description."""
+    import oracle as O
+    om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    t0 = time.perf_counter()
+    lo, hi = om.range(wl.rule)
+    t_range = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tabs = O.make_tables(wl.k, lo, hi)
+    t_table = time.perf_counter() - t0
+    rng = np.random.default_rng(123)
+    rows = 1
+    t0 = time.perf_counter()
+    om.z_rows(wl.k, wl.rule, rng.choice(om.ne, rows, replace=False), mode="table", tables=tabs)
+    t1 = time.perf_counter() - t0
+    rows = int(max(1, min(om.ne, round(target_s / max(t1, 1e-3)))))
+    sel = rng.choice(om.ne, rows, replace=False)
+    t0 = time.perf_counter()
+    om.z_rows(wl.k, wl.rule, sel, mode="table", tables=tabs)
+    t_rows = time.perf_counter() - t0
+    t_full = t_range + t_table + t_rows * om.ne / rows
+    cores = os.cpu_count()
+    desc = (f"oracle table-mode fill: full R range ({t_range:.2f} s) + tables ({t_table:.3f} s) + "
+            f"{rows} of {om.ne} Z rows ({t_rows:.2f} s), projected to the full matrix; "
+            f"OpenMP over Z entries on {cores} threads")
+    return t_full, desc, cores, om.ne
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    times = []
+    desc = cores = ne = None
+    for i in range(args.warmup + args.steps):
+        t_full, desc, cores, ne = oracle_baseline(wl, target_s=args.ref_seconds, reference=True)
+        if i >= args.warmup:
+            times.append(t_full)
+    t = statistics.median(times)
+    value = ne * ne / t
+    line = {"impl": "reference", "metric": "Z entries/s (table fill)", "value": value, "unit": "Z entries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl.name},
+            "cpu_baseline": {"value": value, "unit": "Z entries/s", "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": "Z entries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+
+    import paper_1901_04162_gb300 as gf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prec = gf.GF_FP32 if wl.precision == "fp32" else gf.GF_FP64
+    zdt = torch.complex64 if prec == gf.GF_FP32 else torch.complex128
+    p = gf.gf_params_default(rule=wl.rule)
+    mesh = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    ne, nt, n_near = mesh.ne, mesh.nt, mesh.n_near
+    Z = torch.empty((ne, ne), dtype=zdt, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    parts = (gf.GF_PART_ZERO, gf.GF_PART_REGULAR, gf.GF_PART_NEAR)
+
+    def step(direct, ev):
+        tab = None
+        ev[0].record(stream)
+        if not direct:
+            lo, hi = mesh.range(wl.rule, prec)
+            tab = gf.Table(wl.k, lo, hi, p)
+        for i, part in enumerate(parts):
+            ev[1 + i].record(stream)
+            gf.gf_fill_parts(mesh.h, wl.k, p, tab.h if tab else None, prec, Z, part)
+        ev[4].record(stream)
+        return tab
+
+    def timed(direct, steps, warmup):
+        keep = []
+        for _ in range(warmup):
+            keep.append(step(direct, [torch.cuda.Event(enable_timing=True) for _ in range(5)]))
+        torch.cuda.synchronize()
+        keep.clear()
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)  # evict Z and the geometry from L2 between steps
+            keep.append(step(direct, evs[i]))
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - t0
+        st = [e[0].elapsed_time(e[4]) for e in evs]
+        reg = [e[2].elapsed_time(e[3]) for e in evs]
+        near = [e[3].elapsed_time(e[4]) for e in evs]
+        pre = [e[0].elapsed_time(e[1]) for e in evs]
+        keep.clear()
+        return {"step_ms": st, "regular_ms": reg, "near_ms": near, "range_table_ms": pre, "wall_s": wall}
+
+    # ---- table path (the method) with clocks sampled in the timed region
+    with Clocks(local_rank) as clk:
+        tt = timed(False, args.steps, args.warmup)
+    clocks = clk.summary()
+    td = timed(True, args.steps, args.warmup)
+
+    def reduce_max(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_ms = reduce_max(sum(tt["step_ms"]))
+    ms_step = total_ms / args.steps
+    value = world * ne * ne * args.steps / (total_ms / 1e3)
+    direct_ms = reduce_max(sum(td["step_ms"])) / args.steps
+
+    # ---- end to end: host arrays in, host copy of Z out, through the C ABI
+    zhost = torch.empty((ne, ne), dtype=zdt, pin_memory=True)
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+        lo, hi = m2.range(wl.rule, prec)
+        tab = gf.Table(wl.k, lo, hi, p)
+        gf.gf_fill(m2.h, wl.k, p, tab.h, prec, Z)
+        zhost.copy_(Z, non_blocking=True)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e.append(time.perf_counter() - t0)
+        del tab, m2
+    e2e_s = reduce_max(statistics.median(e2e))
+    h2d = wl.xyz.nbytes + wl.tri.nbytes
+    d2h = Z.numel() * Z.element_size()
+
+    # ---- roofline of the regular-pair kernel (table), CUDA events on its stream
+    m = wl.rule
+    n_regular = nt * nt - n_near
+    reg_ms = statistics.mean(tt["regular_ms"])
+    ops = n_regular * regular_ops_per_pair(m)
+    pk, src = peaks()
+    sm_mhz = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
+    peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    achieved = ops / (reg_ms / 1e3) / 1e12
+    khash = kernel_source_hash()
+    traffic = TRAFFIC.get((wl.name, khash))
+    evals_regular = n_regular * m * m
+    evals_near = n_near * m * (3 * (p.nphi + p.nl) + 1)
+
+    line = {
+        "metric": "Z entries/s (table fill)", "value": value, "unit": "Z entries/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == gf.GF_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "triangles": nt, "rwg_unknowns": ne, "rule_points": m, "k": wl.k,
+                   "table_tol": p.table_tol, "near_pairs": n_near, "regular_pairs": n_regular,
+                   "precision": "fp32 regular (Kahan outer sums), fp64 near" if prec == gf.GF_FP32 else "fp64",
+                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+        "green_evals_per_s": world * (evals_regular + evals_near) * args.steps / (total_ms / 1e3),
+        "step_breakdown_ms": {"range_and_tables": statistics.mean(tt["range_table_ms"]),
+                              "regular_kernel": reg_ms, "near_kernel": statistics.mean(tt["near_ms"])},
+        "direct": {"value": world * ne * ne / (direct_ms / 1e3), "unit": "Z entries/s", "ms_per_step": direct_ms,
+                   "regular_kernel_ms": statistics.mean(td["regular_ms"]),
+                   "near_kernel_ms": statistics.mean(td["near_ms"])},
+        "table_speedup_vs_direct": {"step": direct_ms / ms_step,
+                                    "regular_kernel": statistics.mean(td["regular_ms"]) / reg_ms,
+                                    "near_kernel": statistics.mean(td["near_ms"]) / statistics.mean(tt["near_ms"])},
+        "roofline": {"kernel": "k_fill_regular32<table>", "bound": "alu", "achieved": achieved,
+                     "peak": peak_tops, "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_tops,
+                     "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
+                                    f"({src} max SM clock)",
+                     "ops_per_launch": ops, "traffic": traffic,
+                     "mufu_frac": n_regular * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6)},
+        "clocks": clocks,
+        "e2e": {"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3},
+        "gpu_launches": 10 * args.steps,
+    }
+
+    # ---- accuracy vs the FP64 oracle on sampled rows (outside the timed region)
+    if rank == 0 and not args.skip_oracle:
+        import oracle as O
+        om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
+        lo, hi = mesh.range(wl.rule, gf.GF_FP64)
+        rows = np.random.default_rng(5).choice(ne, 8, replace=False)
+        tab = gf.Table(wl.k, lo, hi, p)
+        gf.gf_fill(mesh.h, wl.k, p, tab.h, prec, Z)
+        zt = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        gf.gf_fill(mesh.h, wl.k, p, None, prec, Z)
+        zd = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        ref_t = om.z_rows(wl.k, wl.rule, rows, mode="table", tables=O.make_tables(wl.k, lo, hi))
+        ref_d = om.z_rows(wl.k, wl.rule, rows)
+        rf = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+        line["accuracy"] = {"rows_sampled": 8, "gpu_table_vs_oracle_table": rf(zt, ref_t),
+                            "gpu_direct_vs_oracle_direct": rf(zd, ref_d),
+                            "gpu_table_vs_oracle_direct": rf(zt, ref_d), "tolerance": 1e-5}
+    if rank == 0 and not args.skip_cpu_baseline:
+        t_full, desc, cores, _ = oracle_baseline(wl)
+        line["cpu_baseline"] = {"value": ne * ne / t_full, "unit": "Z entries/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere_7680", choices=sorted(WORKLOADS))
+    ap.add_argument("--skip-oracle", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOADS[args.workload]()
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        run_ours(args, wl, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

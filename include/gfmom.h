@@ -156,6 +156,17 @@ gf_status gf_table_destroy(gf_table* t);
 gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                   int precision, void* Z_dev, int64_t ldz, void* stream);
 
+/* The stages of gf_fill, for callers that time or overlap them: GF_PART_ZERO
+ * clears the ne x ne block of Z, GF_PART_REGULAR adds the regular-pair terms
+ * (one kernel), GF_PART_NEAR adds the near-pair terms (one kernel). gf_fill is
+ * gf_fill_parts with all three, in that order. parts = 0 or a bit outside the
+ * three is GF_ERR_ARG. */
+#define GF_PART_ZERO 1u
+#define GF_PART_REGULAR 2u
+#define GF_PART_NEAR 4u
+gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
+                        int precision, void* Z_dev, int64_t ldz, unsigned parts, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -645,7 +645,14 @@ gf_status gf_table_destroy(gf_table* t) {
 
 gf_status gf_fill(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision, void* Z,
                   int64_t ldz, void* stream) {
+  return gf_fill_parts(mc, k, p, table, precision, Z, ldz, GF_PART_ZERO | GF_PART_REGULAR | GF_PART_NEAR, stream);
+}
+
+gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision,
+                        void* Z, int64_t ldz, unsigned parts, void* stream) {
   if (!mc || !params_ok(p) || !Z) return fail(GF_ERR_ARG, "gf_fill: bad argument");
+  if (parts == 0 || (parts & ~(GF_PART_ZERO | GF_PART_REGULAR | GF_PART_NEAR)))
+    return fail(GF_ERR_ARG, "gf_fill_parts: bad parts mask");
   if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_fill: bad precision");
   if (!(k > 0) || ldz < mc->ne) return fail(GF_ERR_ARG, "gf_fill: need k > 0 and ldz >= ne");
   gf_mesh* m = const_cast<gf_mesh*>(mc);
@@ -657,14 +664,17 @@ gf_status gf_fill(const gf_mesh* mc, double k, const gf_params* p, const gf_tabl
   if ((st = prepare_rule(m, p->rule, s))) return st;
   if (m->ne == 0) return GF_OK;
   const size_t esz = precision == GF_FP32 ? 8 : 16;
-  GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
+  if (parts & GF_PART_ZERO)
+    GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
   GeoView g = geo_view(m);
   TabView tg, te;
   if (table) {
     tg = table->green.view();
     te = table->exp.view();
   }
-  GF_CUDA(launch_fill_regular(g, table ? &tg : nullptr, precision, k, p->eta, Z, ldz, s));
+  if (parts & GF_PART_REGULAR)
+    GF_CUDA(launch_fill_regular(g, table ? &tg : nullptr, precision, k, p->eta, Z, ldz, s));
+  if (!(parts & GF_PART_NEAR)) return GF_OK;
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
   gauss_legendre(p->nphi, gx_phi, gw_phi);
   gauss_legendre(p->nl, gx_l, gw_l);

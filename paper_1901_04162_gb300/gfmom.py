@@ -24,7 +24,8 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
-           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill"]
+           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts"]
+GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
 
 class GfError(RuntimeError):
@@ -69,6 +70,7 @@ def lib():
         L.gf_table_eval.argtypes = [vp, C.c_int, C.c_int, vp, i64, vp, vp]
         L.gf_table_destroy.argtypes = [vp]
         L.gf_fill.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
+        L.gf_fill_parts.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, C.c_uint, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -190,16 +192,28 @@ def gf_table_destroy(h):
     _check(lib().gf_table_destroy(h))
 
 
-def gf_fill(mesh, k, params, table, precision, Z, ldz=None, stream=None):
-    """Z: CUDA tensor (complex64 for GF_FP32, complex128 for GF_FP64), at
-    least [ne, ldz] row-major; overwritten."""
+def _check_z(Z, precision):
     import torch
     want = torch.complex64 if precision == GF_FP32 else torch.complex128
     if not Z.is_cuda or Z.dtype != want or not Z.is_contiguous():
         raise ValueError(f"Z must be a contiguous CUDA {want} tensor")
+
+
+def gf_fill(mesh, k, params, table, precision, Z, ldz=None, stream=None):
+    """Z: CUDA tensor (complex64 for GF_FP32, complex128 for GF_FP64), at
+    least [ne, ldz] row-major; overwritten."""
+    _check_z(Z, precision)
     ldz = Z.shape[-1] if ldz is None else ldz
     _check(lib().gf_fill(mesh, float(k), C.byref(params), table, int(precision), C.c_void_p(Z.data_ptr()),
                          int(ldz), _stream_ptr(stream)))
+    return Z
+
+
+def gf_fill_parts(mesh, k, params, table, precision, Z, parts, ldz=None, stream=None):
+    _check_z(Z, precision)
+    ldz = Z.shape[-1] if ldz is None else ldz
+    _check(lib().gf_fill_parts(mesh, float(k), C.byref(params), table, int(precision), C.c_void_p(Z.data_ptr()),
+                               int(ldz), int(parts), _stream_ptr(stream)))
     return Z
 
 
