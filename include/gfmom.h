@@ -167,6 +167,31 @@ gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table
 gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                         int precision, void* Z_dev, int64_t ldz, unsigned parts, void* stream);
 
+/* ---------------------------------------------------------------- no-alloc -
+ * gf_range for callers that cannot allocate device memory (for example code
+ * running while a CUDA graph is captured, or a plug-in whose host application
+ * owns every device allocation). The paper has no counterpart: this is a
+ * deployment variant of the range reduction above. It allocates nothing: its
+ * scratch (the integration points and a min/max accumulator) is a fixed
+ * array of (GF_NOALLOC_MAX_POINTS + 1) x 32 bytes (4 MiB) inside the library,
+ * present on every GPU that loads the library until the process exits.
+ *
+ * tri_xyz: device [nt][9] float64, the three vertices of each triangle;
+ * tri_vert: device [nt][3] int32 vertex ids (pairs sharing a vertex are near
+ * pairs and are skipped; no centroid criterion); minmax: device [2] float64,
+ * written with (r_min, r_max) over the FP64 distances between the `rule`
+ * points of all other pairs ((+inf, 0) if there is none). Asynchronous on
+ * `stream`. GF_ERR_ARG if nt * rule > GF_NOALLOC_MAX_POINTS, a pointer is
+ * null, nt < 1 or the rule is not 1, 3, 4, 6 or 7.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture. Every call on a device shares the one scratch array:
+ * calls whose work overlaps on the GPU (other streams, other threads) race
+ * and give wrong results; serialize them. */
+#define GF_NOALLOC_MAX_POINTS 131072
+gf_status gf_range_noalloc(const double* tri_xyz, const int32_t* tri_vert, int64_t nt, int rule,
+                           double* minmax, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

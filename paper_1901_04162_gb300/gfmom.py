@@ -24,7 +24,8 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
-           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts"]
+           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc"]
+GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
 
@@ -71,6 +72,7 @@ def lib():
         L.gf_table_destroy.argtypes = [vp]
         L.gf_fill.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
         L.gf_fill_parts.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, C.c_uint, vp]
+        L.gf_range_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -275,3 +277,22 @@ def fill(mesh: Mesh, k, params=None, table: Table | None = None, precision=GF_FP
         dt = torch.complex64 if precision == GF_FP32 else torch.complex128
         Z = torch.empty((mesh.ne, mesh.ne), dtype=dt, device=device or "cuda")
     return gf_fill(mesh.h, k, params, table.h if table is not None else None, precision, Z, stream=stream)
+
+
+def gf_range_noalloc(tri_xyz, tri_vert, rule, minmax, stream=None):
+    """Range reduction that allocates nothing (see include/gfmom.h): tri_xyz
+    a CUDA float64 tensor [nt, 9], tri_vert a CUDA int32 tensor [nt, 3],
+    minmax a CUDA float64 tensor with 2 elements, written asynchronously."""
+    import torch
+    if not (tri_xyz.is_cuda and tri_vert.is_cuda and minmax.is_cuda):
+        raise ValueError("gf_range_noalloc needs CUDA tensors")
+    if tri_xyz.dtype != torch.float64 or tri_vert.dtype != torch.int32 or minmax.dtype != torch.float64:
+        raise ValueError("dtypes: tri_xyz float64, tri_vert int32, minmax float64")
+    if not (tri_xyz.is_contiguous() and tri_vert.is_contiguous() and minmax.is_contiguous()):
+        raise ValueError("tensors must be contiguous")
+    nt = tri_xyz.shape[0]
+    if tri_xyz.shape != (nt, 9) or tri_vert.shape != (nt, 3) or minmax.numel() < 2:
+        raise ValueError("shapes: tri_xyz [nt, 9], tri_vert [nt, 3], minmax [2]")
+    _check(lib().gf_range_noalloc(C.c_void_p(tri_xyz.data_ptr()), C.c_void_p(tri_vert.data_ptr()), nt, int(rule),
+                                  C.c_void_p(minmax.data_ptr()), _stream_ptr(stream)))
+    return minmax
