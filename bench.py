@@ -211,22 +211,23 @@ def run_ours(args, wl, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
     parts = (gf.GF_PART_ZERO, gf.GF_PART_REGULAR, gf.GF_PART_NEAR)
 
-    def step(direct, ev):
+    def step(direct, ev, params=None):
+        pp = params or p
         tab = None
         ev[0].record(stream)
         if not direct:
             lo, hi = mesh.range(wl.rule, prec)
-            tab = gf.Table(wl.k, lo, hi, p)
+            tab = gf.Table(wl.k, lo, hi, pp)
         for i, part in enumerate(parts):
             ev[1 + i].record(stream)
-            gf.gf_fill_parts(mesh.h, wl.k, p, tab.h if tab else None, prec, Z, part)
+            gf.gf_fill_parts(mesh.h, wl.k, pp, tab.h if tab else None, prec, Z, part)
         ev[4].record(stream)
         return tab
 
-    def timed(direct, steps, warmup):
+    def timed(direct, steps, warmup, params=None):
         keep = []
         for _ in range(warmup):
-            keep.append(step(direct, [torch.cuda.Event(enable_timing=True) for _ in range(5)]))
+            keep.append(step(direct, [torch.cuda.Event(enable_timing=True) for _ in range(5)], params))
         torch.cuda.synchronize()
         keep.clear()
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
@@ -235,7 +236,7 @@ def run_ours(args, wl, rank, world, local_rank):
         t0 = time.perf_counter()
         for i in range(steps):
             flush.fill_(i & 0xFF)  # evict Z and the geometry from L2 between steps
-            keep.append(step(direct, evs[i]))
+            keep.append(step(direct, evs[i], params))
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t0
@@ -251,6 +252,9 @@ def run_ours(args, wl, rank, world, local_rank):
         tt = timed(False, args.steps, args.warmup)
     clocks = clk.summary()
     td = timed(True, args.steps, args.warmup)
+    p64 = gf.gf_params_default(rule=wl.rule, near_fp64=1)
+    t64 = timed(False, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
+    d64 = timed(True, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
 
     def reduce_max(x):
         if dist is None:
@@ -312,6 +316,10 @@ def run_ours(args, wl, rank, world, local_rank):
         "direct": {"value": world * ne * ne / (direct_ms / 1e3), "unit": "Z entries/s", "ms_per_step": direct_ms,
                    "regular_kernel_ms": statistics.mean(td["regular_ms"]),
                    "near_kernel_ms": statistics.mean(td["near_ms"])},
+        "near_fp64_variant": None if t64 is None else {
+            "ms_per_step": statistics.mean(t64["step_ms"]), "near_kernel_ms": statistics.mean(t64["near_ms"]),
+            "direct_near_kernel_ms": statistics.mean(d64["near_ms"]),
+            "note": "near pairs sampled in FP64 too (near_fp64=1)"},
         "table_speedup_vs_direct": {"step": direct_ms / ms_step,
                                     "regular_kernel": statistics.mean(td["regular_ms"]) / reg_ms,
                                     "near_kernel": statistics.mean(td["near_ms"]) / statistics.mean(tt["near_ms"])},

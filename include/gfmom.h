@@ -72,6 +72,9 @@ typedef struct {
   int nphi;                   /* angular points per source edge, near pairs (8)         */
   int nl;                     /* line points per source edge, near pairs (8)            */
   double eta;                 /* wave impedance (376.730313668)                         */
+  int near_fp64;              /* GF_FP32 fills: 0 = near pairs with FP64 geometry, static
+                                 parts and sums and FP32 sampling on the source edges;
+                                 1 = FP64 throughout (GF_FP64 fills always are) (0)       */
 } gf_params;
 
 /* Fills *p with the defaults listed above. */

@@ -239,6 +239,14 @@ gf::TabView gf_table::One::view() const {
   v.node32 = d_node32;
   v.c32a = d_c32a;
   v.c32b = d_c32b;
+  v.n_cells32 = n_cells32;
+  v.lo32c = lo32c;
+  v.inv32c = inv32c;
+  v.cells32 = d_cells32;
+  v.n_cells64 = n_cells64;
+  v.lo64c = lo64c;
+  v.inv64c = inv64c;
+  v.cells64 = d_cells64;
   return v;
 }
 
@@ -261,7 +269,7 @@ gf_status check_device(int dev) {
 
 void free_mesh_device(gf_mesh* m) {
   void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_pts32,
-                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax};
+                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -302,7 +310,8 @@ gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s) {
   cudaError_t e = cudaMemcpy(d_bw, bw.data(), bw.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = launch_prep_geometry(m->d_v64, (int)m->nt, rule, d_bw, d_bw + 3 * kMaxRule, m->d_tedge, m->d_elen,
-                             m->d_pts32, m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64, s);
+                             m->d_pts32, m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64, m->d_rad32,
+                             s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_bw);
   if (e != cudaSuccess) return cuda_fail(e, "prepare geometry");
@@ -326,6 +335,7 @@ GeoView geo_view(const gf_mesh* m) {
   g.near_ptr = m->d_near_ptr;
   g.near_idx = m->d_near_idx;
   g.near_dist32 = (float)m->near_dist;
+  g.rad32 = m->d_rad32;
   return g;
 }
 
@@ -333,7 +343,7 @@ bool params_ok(const gf_params* p) {
   return p && p->table_tol > 0 && p->green_n_per_lambda >= 0 && p->exp_n_per_lambda >= 0 &&
          p->lagrange_degree >= 1 && p->lagrange_degree <= 3 && p->refine_factor > 0 && p->refine_factor <= 1 &&
          p->refine_halfwidth_t >= 0 && p->merge_t >= 0 && p->nphi >= 1 && p->nphi <= 32 && p->nl >= 1 &&
-         p->nl <= 32 && p->eta > 0;
+         p->nl <= 32 && p->eta > 0 && (p->near_fp64 == 0 || p->near_fp64 == 1);
 }
 
 }  // namespace
@@ -355,6 +365,7 @@ void gf_params_default(gf_params* p) {
   p->nphi = 8;
   p->nl = 8;
   p->eta = 376.730313668;
+  p->near_fp64 = 0;
 }
 
 const char* gf_last_error(void) { return gf::g_err.c_str(); }
@@ -459,7 +470,8 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       (st = dev_alloc(&m->d_near_idx, m->near_idx.size())) || (st = dev_alloc(&m->d_pts32, kMaxRule * nt)) ||
       (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
       (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
-      (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_minmax, 4))) {
+      (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_minmax, 4)) ||
+      (st = dev_alloc(&m->d_rad32, nt))) {
     free_mesh_device(m.get());
     return st;
   }
@@ -571,21 +583,43 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o.dr = pl.dr;
     o.n_hash = pl.n_hash;
     const size_t n = o.r.size();
+    // FP32 cell map (the same float operations as the device lookups)
+    o.lo32c = (float)r_min;
+    o.inv32c = (float)(1.0 / (0.99 * o.dr));
+    const float span = ((float)r_max - o.lo32c) * o.inv32c;
+    if (!(span < (float)(1 << 26))) {
+      gf_table_destroy(T.release());
+      return fail(GF_ERR_RANGE, "table: FP32 cell array too large");
+    }
+    o.n_cells32 = (int)span + 1;
+    o.lo64c = r_min;
+    o.inv64c = 1.0 / (0.99 * o.dr);
+    o.n_cells64 = (int)std::floor((r_max - r_min) * o.inv64c) + 1;
     if ((st = dev_alloc(&o.d_node64, n)) || (st = dev_alloc(&o.d_zflag, n)) || (st = dev_alloc(&o.d_fval, 2 * n)) ||
         (st = dev_alloc(&o.d_c64, 4 * n)) || (st = dev_alloc(&o.d_node32, n)) || (st = dev_alloc(&o.d_c32a, n)) ||
-        (st = dev_alloc(&o.d_c32b, n)) || (st = dev_alloc(&o.d_hash, (size_t)o.n_hash))) {
+        (st = dev_alloc(&o.d_c32b, n)) || (st = dev_alloc(&o.d_hash, (size_t)o.n_hash)) ||
+        (st = dev_alloc(&o.d_cells32, (size_t)o.n_cells32)) || (st = dev_alloc(&o.d_cells64, (size_t)o.n_cells64)) ||
+        (st = dev_alloc(&o.d_flag, 1))) {
       gf_table_destroy(T.release());
       return st;
     }
     cudaError_t e = cudaMemcpyAsync(o.d_node64, o.r.data(), n * 8, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(o.d_zflag, o.zflag.data(), n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.d_flag, 0, sizeof(int), s);
     if (e == cudaSuccess)
       e = launch_table_image(o.kind, k, o.degree, (int)n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a,
-                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, s);
+                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells32, o.lo32c,
+                             o.inv32c, o.d_cells32, o.n_cells64, o.lo64c, o.inv64c, o.d_cells64, o.d_flag, s);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, o.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
       gf_table_destroy(T.release());
       return cuda_fail(e, "gf_table_create");
+    }
+    if (flag) {
+      gf_table_destroy(T.release());
+      return fail(GF_ERR_RANGE, "table: two samples in one hash cell (spacing below FP32 resolution)");
     }
   }
   *out = T.release();
@@ -635,7 +669,8 @@ gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* 
 gf_status gf_table_destroy(gf_table* t) {
   if (!t) return GF_OK;
   for (gf_table::One* o : {&t->green, &t->exp}) {
-    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval, o->d_c64, o->d_node32, o->d_c32a, o->d_c32b, o->d_hash};
+    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval,    o->d_c64,     o->d_node32, o->d_c32a,
+                    o->d_c32b,   o->d_hash,  o->d_cells32, o->d_cells64, o->d_flag};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }
@@ -687,7 +722,8 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
     gll[i] = gx_l[i];
     gll[32 + i] = gw_l[i];
   }
-  GF_CUDA(launch_fill_near(g, table ? &te : nullptr, precision, k, p->eta, p->nphi, p->nl, glp, gll, Z, ldz, s));
+  GF_CUDA(launch_fill_near(g, table ? &te : nullptr, precision, precision == GF_FP32 && !p->near_fp64, k, p->eta,
+                           p->nphi, p->nl, glp, gll, Z, ldz, s));
   return GF_OK;
 }
 

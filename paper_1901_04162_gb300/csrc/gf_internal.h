@@ -42,6 +42,14 @@ struct GeoView {
   const int64_t* near_ptr;  // [nt + 1]
   const int32_t* near_idx;  // sorted per row
   float near_dist32;        // > 0: centroid criterion present (FP32 screen)
+  const float* rad32;       // [nt]: largest |point - centroid| of the rule, rounded up
+};
+
+// FP64 cell record: every x in the cell lies in interval j0 if x < split,
+// else in j0 + 1 whose left sample is split; anchor = sample j0.
+struct __align__(32) Cell64 {
+  double split, anchor;
+  int j0, pad;
 };
 
 // One interpolation table as the kernels see it.
@@ -55,26 +63,36 @@ struct TabView {
   const float* node32;     // [n_nodes]: FP32 anchors
   const float4* c32a;      // [n_nodes-1]: (c0re, c0im, c1re, c1im) about node32[j]
   const float4* c32b;      // [n_nodes-1]: (c2re, c2im, c3re, c3im)
-  size_t smem32_bytes() const {
-    return (size_t)n_hash * 4 + (size_t)n_nodes * 4 + (size_t)(n_nodes - 1) * 32 + 64;
-  }
+  // FP32 image of the hash: cells of width 0.99 dr in the FP32 map
+  // c(x) = trunc((x - lo32c) * inv32c); record c = (j0 as int bits, split,
+  // node32[j0], 0): every x in cell c lies in interval j0 if x < split, else in
+  // j0 + 1 whose anchor is split (at most one sample falls inside a cell).
+  int n_cells32;
+  float lo32c, inv32c;
+  const float4* cells32;
+  int n_cells64;  // FP64 cell image, same construction in FP64
+  double lo64c, inv64c;
+  const Cell64* cells64;
+  size_t smem32_bytes() const { return (size_t)n_cells32 * 16 + (size_t)(n_nodes - 1) * 32; }
 };
 
 // ---------------------------------------------------------------- kernels (gf_kernels.cu)
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
-                                 float4* geo32, double* pts64, double* cen64, double* geo64,
+                                 float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
                                  cudaStream_t s);
 cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, const double* node64,
                                const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
                                float4* c32b, double* fval, int n_hash, double r_lo, double dr,
-                               int32_t* hash, cudaStream_t s);
+                               int32_t* hash, int n_cells32, float lo32c, float inv32c, float4* cells32,
+                               int n_cells64, double lo64c, double inv64c, Cell64* cells64, int* flag,
+                               cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s);
 cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int precision, double k,
                                 double eta, void* Z, int64_t ldz, cudaStream_t s);
-cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, double k,
+cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k,
                              double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
                              void* Z, int64_t ldz, cudaStream_t s);
 
@@ -107,6 +125,7 @@ struct gf_mesh {
   double* d_pts64 = nullptr;
   double* d_cen64 = nullptr;
   double* d_geo64 = nullptr;
+  float* d_rad32 = nullptr;
   unsigned long long* d_minmax = nullptr;  // range scratch [4]
 };
 
@@ -127,6 +146,13 @@ struct gf_table {
     float4* d_c32a = nullptr;
     float4* d_c32b = nullptr;
     int32_t* d_hash = nullptr;
+    int n_cells32 = 0;
+    float lo32c = 0.f, inv32c = 0.f;
+    float4* d_cells32 = nullptr;
+    int n_cells64 = 0;
+    double lo64c = 0, inv64c = 0;
+    gf::Cell64* d_cells64 = nullptr;
+    int* d_flag = nullptr;
     gf::TabView view() const;
   } green, exp;
   const One& get(int kind) const { return kind == GF_GREEN ? green : exp; }

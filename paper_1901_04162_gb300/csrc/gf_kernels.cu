@@ -39,7 +39,7 @@ __device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
 __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, const double* __restrict__ bary,
                                 const double* __restrict__ w, const int4* __restrict__ tedge,
                                 const double* __restrict__ elen, float4* pts32, float4* cen32, float4* geo32,
-                                double* pts64, double* cen64, double* geo64) {
+                                double* pts64, double* cen64, double* geo64, float* rad32) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double v[3][3];
@@ -57,6 +57,7 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
   cen64[4 * (size_t)t + 2] = c2;
   cen64[4 * (size_t)t + 3] = area;
   cen32[t] = make_float4((float)c0, (float)c1, (float)c2, (float)area);
+  double rad = 0.0;
   for (int a = 0; a < m; ++a) {
     double px = bary[3 * a] * v[0][0] + bary[3 * a + 1] * v[1][0] + bary[3 * a + 2] * v[2][0];
     double py = bary[3 * a] * v[0][1] + bary[3 * a + 1] * v[1][1] + bary[3 * a + 2] * v[2][1];
@@ -67,7 +68,9 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
     pts64[4 * o + 2] = pz - c2;
     pts64[4 * o + 3] = w[a];
     pts32[o] = make_float4((float)(px - c0), (float)(py - c1), (float)(pz - c2), (float)w[a]);
+    rad = fmax(rad, sqrt((px - c0) * (px - c0) + (py - c1) * (py - c1) + (pz - c2) * (pz - c2)));
   }
+  rad32[t] = (float)(rad * (1.0 + 1e-6));
   int codes[3] = {tedge[t].x, tedge[t].y, tedge[t].z};
   for (int i = 0; i < 3; ++i) {
     double sl = 0.0;
@@ -176,28 +179,35 @@ __global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, do
 
 // ---------------------------------------------------------------- lookups
 struct Tab32 {  // FP32 view (shared or global memory)
-  const int32_t* hash;
-  const float* node;
+  const float4* cells;
   const float4* ca;
   const float4* cb;
-  int n_nodes, n_hash;
-  float r_lo, inv_dr;
+  int n_cells;
+  float lo, inv;
 };
 
+__device__ __forceinline__ Tab32 tab32(const TabView& t) {
+  return Tab32{t.cells32, t.c32a, t.c32b, t.n_cells32, t.lo32c, t.inv32c};
+}
+
+// FP32 cell of x; the table builder uses the same two rounded operations
+__device__ __forceinline__ int cell32_of(float x, float lo, float inv) {
+  return __float2int_rz(__fmul_rn(__fsub_rn(x, lo), inv));
+}
+
+// e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 image: one cell record
+// gives the interval (Eq. 6 hash with the bracketing sample inlined), one or
+// two records give the polynomial about the interval's anchor.
+template <int DEG>
 __device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
-  float x = (R - T.r_lo) * T.inv_dr;
-  int c = (int)x;
-  c = min(max(c, 0), T.n_hash - 1);
-  int j = T.hash[c];
-#pragma unroll
-  for (int it = 0; it < 2; ++it)
-    if (j > 0 && R < T.node[j]) --j;
-#pragma unroll
-  for (int it = 0; it < 2; ++it)
-    if (j < T.n_nodes - 2 && R >= T.node[j + 1]) ++j;
-  j = min(j, T.n_nodes - 2);
-  float s = R - T.node[j];
-  float4 a = T.ca[j], b = T.cb[j];
+  const int c = min(max(cell32_of(R, T.lo, T.inv), 0), T.n_cells - 1);
+  const float4 rec = T.cells[c];
+  const bool up = R >= rec.y;
+  const int j = __float_as_int(rec.x) + (up ? 1 : 0);
+  const float s = R - (up ? rec.y : rec.z);
+  const float4 a = T.ca[j];
+  if (DEG == 1) return make_float2(fmaf(s, a.z, a.x), fmaf(s, a.w, a.y));
+  const float4 b = T.cb[j];
   float re = fmaf(s, b.z, b.x), im = fmaf(s, b.w, b.y);
   re = fmaf(s, re, a.z);
   im = fmaf(s, im, a.w);
@@ -206,18 +216,24 @@ __device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
   return make_float2(re, im);
 }
 
+// FP64 lookup through the FP64 cell image (same construction as the FP32
+// one, in FP64): exact bracketing against the FP64 samples, then the FP64
+// polynomial about the interval's left sample.
+__device__ __forceinline__ int cell64_of(double x, double lo, double inv) {
+  return __double2int_rz(__dmul_rn(__dsub_rn(x, lo), inv));
+}
+
+template <int DEG>
 __device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
-  double x = (R - T.r_lo) * T.inv_dr;
-  int cell = (int)fmin(fmax(floor(x), 0.0), (double)(T.n_hash - 1));
-  int j = T.hash[cell];
-  for (int it = 0; it < 2; ++it)
-    if (j > 0 && R < T.node64[j]) --j;
-  for (int it = 0; it < 2; ++it)
-    if (j < T.n_nodes - 2 && R >= T.node64[j + 1]) ++j;
-  j = min(j, T.n_nodes - 2);
-  double s = R - T.node64[j];
+  const int c = min(max(cell64_of(R, T.lo64c, T.inv64c), 0), T.n_cells64 - 1);
+  const Cell64 rec = T.cells64[c];
+  const bool up = R >= rec.split;
+  const int j = rec.j0 + (up ? 1 : 0);
+  const double s = R - (up ? rec.split : rec.anchor);
   const double2* cf = T.c64 + 4 * j;
-  double2 c3 = cf[3], c2 = cf[2], c1 = cf[1], c0 = cf[0];
+  const double2 c0 = cf[0], c1 = cf[1];
+  if (DEG == 1) return make_double2(fma(s, c1.x, c0.x), fma(s, c1.y, c0.y));
+  const double2 c2 = cf[2], c3 = cf[3];
   double re = fma(s, c3.x, c2.x), im = fma(s, c3.y, c2.y);
   re = fma(s, re, c1.x);
   im = fma(s, im, c1.y);
@@ -226,15 +242,66 @@ __device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
   return make_double2(re, im);
 }
 
-__global__ void k_table_eval32(TabView t, const float* __restrict__ r, int64_t n, float2* out) {
-  Tab32 T{t.hash, t.node32, t.c32a, t.c32b, t.n_nodes, t.n_hash, t.r_lo32, t.inv_dr32};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = lookup32(T, r[i]);
+__global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_cells, double lo, double inv,
+                                Cell64* cells, int* flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  auto first_at_or_after = [&](int cc) {
+    int a = 1, b = n - 1;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (cell64_of(node64[mid], lo, inv) >= cc) b = mid;
+      else a = mid + 1;
+    }
+    return a;
+  };
+  const int a = first_at_or_after(c);
+  const int b = first_at_or_after(c + 1);
+  if (b - a > 1) atomicOr(flag, 2);
+  Cell64 rec;
+  rec.j0 = a - 1;
+  rec.split = (a < n - 1 && cell64_of(node64[a], lo, inv) == c) ? node64[a] : INFINITY;
+  rec.anchor = node64[a - 1];
+  rec.pad = 0;
+  cells[c] = rec;
 }
 
+// Cell records of the FP32 image. Samples 1..n-2 may split a cell; with cells
+// 1 % narrower than the smallest spacing at most one sample falls in a cell
+// (checked: flag set otherwise). j0 = last sample whose cell is below c.
+__device__ __forceinline__ int first_sample_at_or_after(const float* node32, int n, float lo, float inv, int c) {
+  int a = 1, b = n - 1;  // search samples 1..n-2; result in [1, n-1]
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (cell32_of(node32[mid], lo, inv) >= c) b = mid;
+    else a = mid + 1;
+  }
+  return a;
+}
+
+__global__ void k_table_cells32(int n, const float* __restrict__ node32, int n_cells, float lo, float inv,
+                                float4* cells, int* flag) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n_cells) return;
+  const int a = first_sample_at_or_after(node32, n, lo, inv, c);
+  const int b = first_sample_at_or_after(node32, n, lo, inv, c + 1);
+  if (b - a > 1) atomicOr(flag, 1);
+  const int j0 = a - 1;
+  const float split = (a < n - 1 && cell32_of(node32[a], lo, inv) == c) ? node32[a] : INFINITY;
+  cells[c] = make_float4(__int_as_float(j0), split, node32[j0], 0.f);
+}
+
+template <int DEG>
+__global__ void k_table_eval32(TabView t, const float* __restrict__ r, int64_t n, float2* out) {
+  const Tab32 T = tab32(t);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = lookup32<DEG>(T, r[i]);
+}
+
+template <int DEG>
 __global__ void k_table_eval64(TabView t, const double* __restrict__ r, int64_t n, double2* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = lookup64(t, r[i]);
+    out[i] = lookup64<DEG>(t, r[i]);
 }
 
 // ---------------------------------------------------------------- near test
@@ -266,6 +333,53 @@ __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned
 __global__ void k_range_init(unsigned long long* mm) {
   mm[0] = dbits(INFINITY);
   mm[1] = 0ull;
+  mm[2] = dbits(INFINITY);
+  mm[3] = 0ull;
+}
+
+// Every point distance of a pair lies in [D - r_p - r_q, D + r_p + r_q]
+// (D = centroid distance, r = largest point offset from the centroid).
+// Pass 1 bounds the extremes: r_min <= min(D + r_p + r_q) = mm[2] and
+// r_max >= max(D - r_p - r_q) = mm[3]; pass 2 (k_range) evaluates the point
+// pairs only of triangle pairs that can reach below mm[2] or above mm[3].
+// FP32 bounds are widened by a slack that covers their rounding.
+__device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, float3 dc, float4 cp, float4 cq,
+                                            float* lb, float* ub) {
+  const float D = sqrtf(fmaf(dc.x, dc.x, fmaf(dc.y, dc.y, dc.z * dc.z)));
+  const float r = g.rad32[p] + g.rad32[q];
+  const float mag = fmaxf(fmaxf(fabsf(cp.x), fabsf(cp.y)), fmaxf(fabsf(cp.z), fmaxf(fmaxf(fabsf(cq.x), fabsf(cq.y)),
+                                                                                      fabsf(cq.z))));
+  const float slack = 1e-5f * (D + r + mag);
+  *lb = fmaxf(D - r - slack, 0.f);
+  *ub = D + r + slack;
+}
+
+__global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunk = (g.nt + 31) / 32;
+  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float min_ub = INFINITY, max_lb = 0.f;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
+    const int p = (int)(task / nchunk);
+    const int q0 = (int)(task % nchunk) * 32;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    if (!((q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
+    float lb, ub;
+    pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
+    min_ub = fminf(min_ub, ub);
+    max_lb = fmaxf(max_lb, lb);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    min_ub = fminf(min_ub, __shfl_xor_sync(0xffffffffu, min_ub, off));
+    max_lb = fmaxf(max_lb, __shfl_xor_sync(0xffffffffu, max_lb, off));
+  }
+  if (lane == 0) {
+    if (min_ub < INFINITY) atomicMin(&mm[2], dbits((double)min_ub));
+    if (max_lb > 0.f) atomicMax(&mm[3], dbits((double)max_lb));
+  }
 }
 
 // ---------------------------------------------------------------- range
@@ -274,6 +388,8 @@ __global__ void k_range_init(unsigned long long* mm) {
 template <bool FP64>
 __global__ void __launch_bounds__(kThreads) k_range(GeoView g, unsigned long long* mm) {
   const int lane = threadIdx.x & 31;
+  const float u_min = (float)__longlong_as_double((long long)mm[2]);
+  const float l_max = (float)__longlong_as_double((long long)mm[3]);
   const int64_t nchunk = (g.nt + 31) / 32;
   const int64_t ntask = (int64_t)g.nt * nchunk;
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -289,6 +405,11 @@ __global__ void __launch_bounds__(kThreads) k_range(GeoView g, unsigned long lon
     float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
     bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
     if (!ok) continue;
+    if (!FP64) {
+      float lb, ub;
+      pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
+      if (lb > u_min && ub < l_max) continue;  // cannot hold an extreme
+    }
     if (FP64) {
       const double* cp64 = g.cen64 + 4 * (size_t)p;
       const double* cq64 = g.cen64 + 4 * (size_t)q;
@@ -353,31 +474,30 @@ struct KSum {  // Kahan-compensated FP32 sum
   }
 };
 
-template <bool TABLE, bool SMEM>
-__global__ void __launch_bounds__(kThreads) k_fill_regular32(GeoView g, TabView tv, float k, float kpi,
-                                                             float scale, float inv_k2, float2* Z, int64_t ldz) {
+// Blocks of 512 threads when the table is staged in shared memory (one CTA
+// per SM holds it), 256 otherwise.
+template <int M, bool TABLE, bool SMEM>
+__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoView g, TabView tv, float kpi,
+                                                                          float scale, float inv_k2, float2* Z,
+                                                                          int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
-  Tab32 T{tv.hash, tv.node32, tv.c32a, tv.c32b, tv.n_nodes, tv.n_hash, tv.r_lo32, tv.inv_dr32};
+  Tab32 T = tab32(tv);
   if (TABLE && SMEM) {
-    const int nn = tv.n_nodes;
+    const int ni = tv.n_nodes - 1;
     float4* sa = reinterpret_cast<float4*>(smem);
-    float4* sb = sa + (nn - 1);
-    float* sn = reinterpret_cast<float*>(sb + (nn - 1));
-    int32_t* sh = reinterpret_cast<int32_t*>(sn + nn);
-    for (int i = threadIdx.x; i < nn - 1; i += blockDim.x) {
+    float4* sb = sa + ni;
+    float4* sc = sb + ni;
+    for (int i = threadIdx.x; i < ni; i += blockDim.x) {
       sa[i] = tv.c32a[i];
       sb[i] = tv.c32b[i];
     }
-    for (int i = threadIdx.x; i < nn; i += blockDim.x) sn[i] = tv.node32[i];
-    for (int i = threadIdx.x; i < tv.n_hash; i += blockDim.x) sh[i] = tv.hash[i];
+    for (int i = threadIdx.x; i < tv.n_cells32; i += blockDim.x) sc[i] = tv.cells32[i];
     __syncthreads();
     T.ca = sa;
     T.cb = sb;
-    T.node = sn;
-    T.hash = sh;
+    T.cells = sc;
   }
   const int lane = threadIdx.x & 31;
-  const int m = g.m;
   const int64_t nchunk = (g.nt + 31) / 32;
   const int64_t ntask = (int64_t)g.nt * nchunk;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -389,43 +509,40 @@ __global__ void __launch_bounds__(kThreads) k_fill_regular32(GeoView g, TabView 
     const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
     const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
     if (!__any_sync(0xffffffffu, ok)) continue;
-    float4 beta[kMaxRule];
+    float4 beta[M];
 #pragma unroll
-    for (int b = 0; b < kMaxRule; ++b)
-      if (b < m) beta[b] = g.pts32[(size_t)b * g.nt + q];
+    for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
     KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
-    for (int a = 0; a < m; ++a) {
+#pragma unroll 1
+    for (int a = 0; a < M; ++a) {
       const float4 al = g.pts32[(size_t)a * g.nt + p];
       const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
       float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-      for (int b = 0; b < kMaxRule; ++b) {
-        if (b < m) {
-          const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-          const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-          const float rs = rsqrtf(R2);
-          const float R = R2 * rs;
-          float gr, gi;
-          if (TABLE) {
-            float2 f = lookup32(T, R);  // e^{-jkR}/R
-            gr = f.x * beta[b].w;
-            gi = f.y * beta[b].w;
-          } else {
-            float sn, cs;
-            sincospif(R * kpi, &sn, &cs);  // kR / pi
-            const float wr = beta[b].w * rs;
-            gr = cs * wr;
-            gi = -sn * wr;
-          }
-          s0r += gr;
-          s0i += gi;
-          sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
-          sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
-          sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
-          sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
-          sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
-          sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
+      for (int b = 0; b < M; ++b) {
+        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float rs = rsqrtf(R2);
+        float gr, gi;
+        if (TABLE) {
+          const float2 f = lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
+          gr = f.x * beta[b].w;
+          gi = f.y * beta[b].w;
+        } else {
+          float sn, cs;
+          sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
+          const float wr = beta[b].w * rs;
+          gr = cs * wr;
+          gi = -sn * wr;
         }
+        s0r += gr;
+        s0i += gi;
+        sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
+        sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
+        sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
+        sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
+        sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
+        sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
       }
       const float wa = al.w;
       M0r.add(wa * s0r);
@@ -500,7 +617,7 @@ __global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView 
         const double R = sqrt(rx * rx + ry * ry + rz * rz);
         double gr, gi;
         if (TABLE) {
-          double2 f = lookup64(tv, R);
+          double2 f = lookup64<3>(tv, R);
           gr = f.x * be[3];
           gi = f.y * be[3];
         } else {
@@ -559,6 +676,7 @@ struct NearArgs {
   double k, scale, inv_k2;
   int nphi, nl;
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
+  float fx_phi[32], fw_phi[32], fx_l[32], fw_l[32];  // the same rules in FP32
 };
 
 struct C2 {
@@ -567,7 +685,7 @@ struct C2 {
 
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
   if (use_table && R >= te->r_lo && R <= te->r_hi) {
-    double2 f = lookup64(*te, R);
+    double2 f = lookup64<1>(*te, R);
     return C2{f.x, f.y};
   }
   double s, c;
@@ -661,36 +779,152 @@ __device__ void inner_integrals(const double r[3], const double v[3][3], const N
   }
 }
 
-template <class Out>
+__device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, bool use_table, float lo, float hi) {
+  if (use_table && R >= lo && R <= hi) return lookup32<1>(te, R);
+  float sn, cs;
+  sincospif(R * kpi, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+// Mixed precision: the geometry (normal, projection, foot distances, edge
+// frames), the closed-form static part and all accumulation in FP64; the
+// sampling of e^{-jkR} at the angular and line nodes of each edge in FP32
+// (relative quantities of the size of a triangle, FP32 Exp table).
+__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const NearArgs& A, const Tab32& te,
+                                      bool use_table, float lo, float hi, C2* I0, C2 I1[3], double rho0[3]) {
+  const double k = A.k;
+  const float kpi = (float)(A.k / kPi), k32 = (float)A.k;
+  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  n[0] *= inv;
+  n[1] *= inv;
+  n[2] *= inv;
+  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+  const double d = fabs(h);
+  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  const float d32 = (float)d;
+  const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
+  double sre = 0, sim = 0;
+  double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0}, vst[3] = {0, 0, 0};
+  for (int e = 0; e < 3; ++e) {
+    const double* a = v[e];
+    const double* b = v[(e + 1) % 3];
+    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const double il = 1.0 / len;
+    t[0] *= il;
+    t[1] *= il;
+    t[2] *= il;
+    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
+    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
+    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
+    if (fabs(P0) > 1e-12 * len) {
+      const double aP = fabs(P0);
+      const double iaP = 1.0 / aP;
+      const float um = asinhf((float)(lm * iaP)), up = asinhf((float)(lp * iaP));
+      const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
+      const float aP32 = (float)aP;
+      float cr = 0.f, ci = 0.f;
+      for (int i = 0; i < A.nphi; ++i) {
+        const float u = fmaf(half, A.fx_phi[i], mid);
+        const float E = expf(u);
+        const float ch = 0.5f * (E + __frcp_rn(E));
+        const float rho = aP32 * ch;
+        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
+        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        cr = fmaf(ed.x - eR.x, wt, cr);
+        ci = fmaf(ed.y - eR.y, wt, ci);
+      }
+      const double sg = P0 > 0 ? (double)half : -(double)half;
+      sre += (double)cr * sg;
+      sim += (double)ci * sg;
+    }
+    // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
+    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    const float tx = (float)t[0], ty = (float)t[1], tz = (float)t[2];
+    const float hl = 0.5f * (float)len;
+    float lr = 0.f, li = 0.f;
+    for (int i = 0; i < A.nl; ++i) {
+      const float sp = hl * (A.fx_l[i] + 1.0f);
+      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
+      lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
+      li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
+    }
+    const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    if (R02 > 0) {
+      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
+      st += 0.5 * R02 * (log(fp) - log(fm));
+    }
+    for (int x = 0; x < 3; ++x) {
+      vre[x] += mh[x] * lrd;
+      vim[x] += mh[x] * lid;
+      vst[x] += mh[x] * st;
+    }
+  }
+  const double c4 = 1.0 / (4.0 * kPi);
+  I0->re = sim / k * c4;
+  I0->im = -sre / k * c4;
+  for (int x = 0; x < 3; ++x) {
+    I1[x].re = (-vim[x] / k + vst[x]) * c4;
+    I1[x].im = (vre[x] / k) * c4;
+  }
+}
+
+// One near pair per group of 8 lanes, one test point per lane (lanes >= m
+// idle); the 3 x 3 block is reduced across the group with shuffles and added
+// to Z by the group's first lane.
+template <class Out, bool MIXED>
 __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
                                                    int64_t ldz) {
+  const Tab32 te32 = tab32(te);
+  const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
   const int64_t n_near = g.near_ptr[g.nt];
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n_near;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    int lo = 0, hi = g.nt - 1;  // p = row containing idx
+  const int sub = threadIdx.x & 7;
+  const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t idx = g0 + it * ngroups;
+    const bool valid_pair = idx < n_near;
+    const int64_t pidx = valid_pair ? idx : n_near - 1;
+    int lo = 0, hi = g.nt - 1;  // p = row containing pidx
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
-      if (g.near_ptr[mid] <= idx) lo = mid;
+      if (g.near_ptr[mid] <= pidx) lo = mid;
       else hi = mid - 1;
     }
-    const int p = lo, q = g.near_idx[idx];
-    double vp[3][3], vq[3][3];
-    for (int c = 0; c < 3; ++c)
-      for (int x = 0; x < 3; ++x) {
-        vp[c][x] = g.v64[9 * (size_t)p + 3 * c + x];
-        vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
-      }
-    const double* cp = g.cen64 + 4 * (size_t)p;
-    const double area_q = g.cen64[4 * (size_t)q + 3];
+    const int p = lo, q = g.near_idx[pidx];
     double accr[3][3], acci[3][3];
+#pragma unroll
     for (int i = 0; i < 3; ++i)
+#pragma unroll
       for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.0;
-    for (int a = 0; a < g.m; ++a) {
-      const double* al = g.pts64 + 4 * ((size_t)a * g.nt + p);
+    if (valid_pair && sub < g.m) {
+      double vq[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int x = 0; x < 3; ++x) vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
+      const double* cp = g.cen64 + 4 * (size_t)p;
+      const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
       const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
       C2 I0, I1[3];
       double rho0[3];
-      inner_integrals(ra, vq, A, &te, use_table, &I0, I1, rho0);
+      if (MIXED) inner_integrals_mixed(ra, vq, A, te32, use_table, lo32, hi32, &I0, I1, rho0);
+      else inner_integrals(ra, vq, A, &te, use_table, &I0, I1, rho0);
+      const double wa = al[3];
+#pragma unroll
       for (int j = 0; j < 3; ++j) {
         // J_j = I1 + (rho0 - v_j) I0
         C2 J[3];
@@ -699,15 +933,28 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
           J[x].re = I1[x].re + dv * I0.re;
           J[x].im = I1[x].im + dv * I0.im;
         }
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
-          const double f0 = ra[0] - vp[i][0], f1 = ra[1] - vp[i][1], f2 = ra[2] - vp[i][2];
+          const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
+          const double f0 = ra[0] - vpi[0], f1 = ra[1] - vpi[1], f2 = ra[2] - vpi[2];
           const double dr = f0 * J[0].re + f1 * J[1].re + f2 * J[2].re;
           const double di = f0 * J[0].im + f1 * J[1].im + f2 * J[2].im;
-          accr[i][j] += al[3] * (0.25 * dr - I0.re * A.inv_k2);
-          acci[i][j] += al[3] * (0.25 * di - I0.im * A.inv_k2);
+          accr[i][j] = wa * (0.25 * dr - I0.re * A.inv_k2);
+          acci[i][j] = wa * (0.25 * di - I0.im * A.inv_k2);
         }
       }
     }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+          accr[i][j] += __shfl_xor_sync(gmask, accr[i][j], off);
+          acci[i][j] += __shfl_xor_sync(gmask, acci[i][j], off);
+        }
+    if (!valid_pair || sub != 0) continue;
+    const double area_q = g.cen64[4 * (size_t)q + 3];
     const int4 ep = g.tedge[p], eq = g.tedge[q];
     const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
     for (int i = 0; i < 3; ++i) {
@@ -751,39 +998,78 @@ int64_t pair_grid(const GeoView& g, int blocks_per_sm) {
 
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
-                                 float4* geo32, double* pts64, double* cen64, double* geo64, cudaStream_t s) {
+                                 float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
+                                 cudaStream_t s) {
   k_prep_geometry<<<(nt + 127) / 128, 128, 0, s>>>(v64, nt, m, bary, w, tedge, edge_len, pts32, cen32, geo32,
-                                                   pts64, cen64, geo64);
+                                                   pts64, cen64, geo64, rad32);
   return cudaGetLastError();
 }
 
 cudaError_t launch_table_image(int kind, double k, int degree, int n, const double* node64, const int8_t* zflag,
                                float* node32, double2* c64, float4* c32a, float4* c32b, double* fval, int n_hash,
-                               double r_lo, double dr, int32_t* hash, cudaStream_t s) {
+                               double r_lo, double dr, int32_t* hash, int n_cells32, float lo32c, float inv32c,
+                               float4* cells32, int n_cells64, double lo64c, double inv64c, Cell64* cells64,
+                               int* flag, cudaStream_t s) {
   k_table_values<<<(n + 255) / 256, 256, 0, s>>>(kind, k, n, node64, zflag, fval);
   k_table_coef<<<(n + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, c64, node32, c32a, c32b);
   k_table_hash<<<(n_hash + 255) / 256, 256, 0, s>>>(n, node64, n_hash, r_lo, dr, hash);
+  k_table_cells32<<<(n_cells32 + 255) / 256, 256, 0, s>>>(n, node32, n_cells32, lo32c, inv32c, cells32, flag);
+  k_table_cells64<<<(n_cells64 + 255) / 256, 256, 0, s>>>(n, node64, n_cells64, lo64c, inv64c, cells64, flag);
   return cudaGetLastError();
 }
 
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n, void* out,
                               cudaStream_t s) {
-  (void)kind;
   int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 16);
-  if (precision == GF_FP32)
-    k_table_eval32<<<(unsigned)blocks, 256, 0, s>>>(t, (const float*)r, n, (float2*)out);
-  else
-    k_table_eval64<<<(unsigned)blocks, 256, 0, s>>>(t, (const double*)r, n, (double2*)out);
+  const bool lin = kind == GF_EXP;
+  if (precision == GF_FP32) {
+    if (lin) k_table_eval32<1><<<(unsigned)blocks, 256, 0, s>>>(t, (const float*)r, n, (float2*)out);
+    else k_table_eval32<3><<<(unsigned)blocks, 256, 0, s>>>(t, (const float*)r, n, (float2*)out);
+  } else {
+    if (lin) k_table_eval64<1><<<(unsigned)blocks, 256, 0, s>>>(t, (const double*)r, n, (double2*)out);
+    else k_table_eval64<3><<<(unsigned)blocks, 256, 0, s>>>(t, (const double*)r, n, (double2*)out);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s) {
   k_range_init<<<1, 1, 0, s>>>(d_minmax);
   int64_t blocks = pair_grid(g, 8);
-  if (precision == GF_FP64)
+  if (precision == GF_FP64) {
     k_range<true><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
-  else
+  } else {
+    k_range_bounds<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
     k_range<false><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
+  }
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_regular32(const GeoView& g, const TabView* green, float kpi, float scale, float inv_k2, float2* Z,
+                             int64_t ldz, cudaStream_t s) {
+  TabView tv{};
+  if (!green) {
+    int64_t blocks = pair_grid(g, 4);
+    k_fill_regular32<M, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+    return cudaGetLastError();
+  }
+  tv = *green;
+  const size_t smem = tv.smem32_bytes();
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem <= (size_t)max_optin) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fill_regular32<M, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_regular32<M, true, true>, 512, smem);
+    int64_t blocks = std::min<int64_t>(pair_grid(g, 2 * std::max(per_sm, 1)), (int64_t)sm_count() * std::max(per_sm, 1));
+    k_fill_regular32<M, true, true><<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+  } else {
+    int64_t blocks = pair_grid(g, 4);
+    k_fill_regular32<M, true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+  }
   return cudaGetLastError();
 }
 
@@ -801,35 +1087,19 @@ cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int prec
     return cudaGetLastError();
   }
   const float kpi = (float)(k / kPi);
-  if (!green) {
-    int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kpi, (float)scale,
-                                                                         (float)(1.0 / (k * k)), (float2*)Z, ldz);
-    return cudaGetLastError();
+  switch (g.m) {
+    case 1: return launch_regular32<1>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    case 3: return launch_regular32<3>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    case 4: return launch_regular32<4>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    case 6: return launch_regular32<6>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    case 7: return launch_regular32<7>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    default: return cudaErrorInvalidValue;
   }
-  size_t smem = tv.smem32_bytes();
-  int dev = 0, max_optin = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem <= (size_t)max_optin) {
-    cudaError_t e = cudaFuncSetAttribute(k_fill_regular32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_regular32<true, true>, kThreads, smem);
-    int64_t blocks = pair_grid(g, std::max(per_sm, 1));
-    k_fill_regular32<true, true><<<(unsigned)blocks, kThreads, smem, s>>>(g, tv, (float)k, kpi, (float)scale,
-                                                                          (float)(1.0 / (k * k)), (float2*)Z, ldz);
-  } else {
-    int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kpi, (float)scale,
-                                                                        (float)(1.0 / (k * k)), (float2*)Z, ldz);
-  }
-  return cudaGetLastError();
 }
 
-cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, double k, double eta, int nphi,
-                             int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz, cudaStream_t s) {
+cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k, double eta,
+                             int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
+                             cudaStream_t s) {
   NearArgs A;
   A.k = k;
   A.scale = k * eta;
@@ -841,16 +1111,22 @@ cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precisio
     A.gw_phi[i] = gl_phi[32 + i];
     A.gx_l[i] = gl_l[i];
     A.gw_l[i] = gl_l[32 + i];
+    A.fx_phi[i] = (float)A.gx_phi[i];
+    A.fw_phi[i] = (float)A.gw_phi[i];
+    A.fx_l[i] = (float)A.gx_l[i];
+    A.fw_l[i] = (float)A.gw_l[i];
   }
   TabView te{};
   if (texp) te = *texp;
   const int64_t n_near = 0;  // read on the device
   (void)n_near;
-  int64_t blocks = (int64_t)sm_count() * 8;
-  if (precision == GF_FP32)
-    k_fill_near<float2><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
+  int64_t blocks = (int64_t)sm_count() * 16;
+  if (precision == GF_FP32 && mixed)
+    k_fill_near<float2, true><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
+  else if (precision == GF_FP32)
+    k_fill_near<float2, false><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
   else
-    k_fill_near<double2><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (double2*)Z, ldz);
+    k_fill_near<double2, false><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (double2*)Z, ldz);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,7 @@ def test_params_default_values():
     assert p.rule == 3 and p.table_tol == 1e-6 and p.green_n_per_lambda == 1000
     assert p.exp_n_per_lambda == 0 and p.lagrange_degree == 3 and p.refine == 1
     assert p.refine_factor == 0.5 and p.refine_halfwidth_t == 2.0 and p.merge_t == 0.25
-    assert p.grade == 1 and p.nphi == 8 and p.nl == 8 and p.eta == 376.730313668
+    assert p.grade == 1 and p.nphi == 8 and p.nl == 8 and p.eta == 376.730313668 and p.near_fp64 == 0
 
 
 def test_argument_errors_before_any_device_call():

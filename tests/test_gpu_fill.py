@@ -47,10 +47,11 @@ def test_plate_fp64_matches_oracle(table):
 
 @pytest.mark.parametrize("rule", [3, 4, 6, 7])
 @pytest.mark.parametrize("table", [False, True])
-def test_small_sphere_fp32_matches_oracle(rule, table):
+@pytest.mark.parametrize("near_fp64", [0, 1])
+def test_small_sphere_fp32_matches_oracle(rule, table, near_fp64):
     xyz, tri = W.octasphere(2, 1.0)
     xyz = W.jitter(xyz, tri, 0.02, 3)
-    _, z, _ = gpu_fill(xyz, tri, K, rule, gf.GF_FP32, table)
+    _, z, _ = gpu_fill(xyz, tri, K, rule, gf.GF_FP32, table, near_fp64=near_fp64)
     ref = oracle_full(xyz, tri, K, rule, table)
     assert rel_fro(z, ref) <= 1e-5
     assert rel_max(z, ref) <= 1e-5
@@ -64,10 +65,11 @@ def test_small_sphere_fp64_both_modes():
         assert rel_fro(z, ref) <= 1e-12
 
 
-def test_range_matches_oracle():
-    wl = W.plate_280()
-    m = gf.Mesh(wl.xyz, wl.tri)
-    om = O.Mesh(wl.xyz, wl.tri)
+@pytest.mark.parametrize("which", ["plate", "sphere", "cube"])
+def test_range_matches_oracle(which):
+    wl = {"plate": W.plate_280, "sphere": W.sphere_3072, "cube": lambda: W.cube_73728(6)}[which]()
+    m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
     for rule in (3, 7):
         lo, hi = om.range(rule)
         g64 = m.range(rule, gf.GF_FP64)
@@ -83,9 +85,10 @@ def test_near_dist_criterion_matches_oracle():
     assert rel_fro(z, ref) <= 1e-12
 
 
-def test_sphere_7680_sampled_rows():
+@pytest.mark.parametrize("near_fp64", [0, 1])
+def test_sphere_7680_sampled_rows(near_fp64):
     wl = W.sphere_7680()
-    m, z, tab = gpu_fill(wl.xyz, wl.tri, wl.k, 7, gf.GF_FP32, True)
+    m, z, tab = gpu_fill(wl.xyz, wl.tri, wl.k, 7, gf.GF_FP32, True, near_fp64=near_fp64)
     lo, hi = m.range(7, gf.GF_FP64)
     om = O.Mesh(wl.xyz, wl.tri)
     rows = np.random.default_rng(11).choice(m.ne, 12, replace=False)
