@@ -54,6 +54,7 @@ def lib():
         L.or_table_free.argtypes = [vp]
         L.or_singular.argtypes = [dp, dp, dp, dp, C.c_double, C.c_int, C.c_int, vp, dp, dp, dp]
         L.or_range.argtypes = [vp, C.c_int, dp, dp, C.c_int]
+        L.or_range_ex.argtypes = [vp, C.c_int, C.c_int, dp, dp, C.c_int]
         L.or_z_entries.argtypes = [vp, C.POINTER(FillParams), vp, vp, C.c_long, ip, ip, dp, dp, C.c_int]
         L.or_loss_grad.argtypes = [vp, C.POINTER(FillParams), dp, dp, dp, dp, dp, dp, dp, C.c_int]
         _lib = L
@@ -202,10 +203,10 @@ class Mesh:
     def is_near(self, p, q):
         return bool(lib().or_mesh_is_near(self.h, int(p), int(q)))
 
-    def range(self, rule, nthreads=0):
+    def range(self, rule, nthreads=0, prune=False):
         lo = C.c_double()
         hi = C.c_double()
-        rc = lib().or_range(self.h, rule, C.byref(lo), C.byref(hi), nthreads)
+        rc = lib().or_range_ex(self.h, rule, int(prune), C.byref(lo), C.byref(hi), nthreads)
         if rc != 0:
             raise ValueError(f"or_range failed: {rc}")
         return lo.value, hi.value

@@ -409,25 +409,56 @@ int or_singular(const double* r, const double* v0, const double* v1, const doubl
 }
 
 int or_range(const or_mesh* m, int rule, double* r_min, double* r_max, int nthreads) {
+  return or_range_ex(m, rule, 0, r_min, r_max, nthreads);
+}
+
+// prune = 1: every point distance of a pair lies in [D - r_p - r_q, D + r_p + r_q]
+// (D centroid distance, r largest point-to-centroid distance), so only pairs
+// whose interval reaches below min(D + r_p + r_q) or above max(D - r_p - r_q)
+// can hold an extreme; those are evaluated point by point (exact result).
+int or_range_ex(const or_mesh* m, int rule, int prune, double* r_min, double* r_max, int nthreads) {
   Quad Q;
   if (!m || !make_quad(rule, 1, 1, &Q)) return -1;
   int nt = m->nt;
-  std::vector<double> pts(3 * (size_t)nt * Q.n);
+  std::vector<double> pts(3 * (size_t)nt * Q.n), rad(nt, 0.0);
   for (int t = 0; t < nt; ++t) {
     V3<double> v[3] = {vtx(m, m->tri[3 * t]), vtx(m, m->tri[3 * t + 1]), vtx(m, m->tri[3 * t + 2])};
+    V3<double> c(m->cen[3 * t], m->cen[3 * t + 1], m->cen[3 * t + 2]);
     for (int a = 0; a < Q.n; ++a) {
       V3<double> x = v[0] * Q.bary[a][0] + v[1] * Q.bary[a][1] + v[2] * Q.bary[a][2];
       pts[3 * ((size_t)t * Q.n + a)] = x.x;
       pts[3 * ((size_t)t * Q.n + a) + 1] = x.y;
       pts[3 * ((size_t)t * Q.n + a) + 2] = x.z;
+      rad[t] = std::max(rad[t], norm(x - c));
     }
   }
-  double lo = 1e300, hi = -1.0;
+  auto cdist = [&](int p, int q) {
+    double dx = m->cen[3 * p] - m->cen[3 * q], dy = m->cen[3 * p + 1] - m->cen[3 * q + 1],
+           dz = m->cen[3 * p + 2] - m->cen[3 * q + 2];
+    return std::sqrt(dx * dx + dy * dy + dz * dz);
+  };
   int nth = nthreads_or_default(nthreads);
+  double ub_min = 1e300, lb_max = -1.0;
+  if (prune) {
+#pragma omp parallel for num_threads(nth) reduction(min : ub_min) reduction(max : lb_max) schedule(dynamic, 16)
+    for (int p = 0; p < nt; ++p)
+      for (int q = 0; q < nt; ++q) {
+        if (is_near(m, p, q)) continue;
+        double D = cdist(p, q), r = rad[p] + rad[q];
+        ub_min = std::min(ub_min, D + r);
+        lb_max = std::max(lb_max, D - r);
+      }
+  }
+  double lo = 1e300, hi = -1.0;
 #pragma omp parallel for num_threads(nth) reduction(min : lo) reduction(max : hi) schedule(dynamic, 4)
   for (int p = 0; p < nt; ++p) {
     for (int q = 0; q < nt; ++q) {
       if (is_near(m, p, q)) continue;
+      if (prune) {
+        double D = cdist(p, q), r = rad[p] + rad[q];
+        double slack = 1e-12 * (D + r + 1.0);
+        if (D - r - slack > ub_min && D + r + slack < lb_max) continue;
+      }
       for (int a = 0; a < Q.n; ++a) {
         const double* x = &pts[3 * ((size_t)p * Q.n + a)];
         for (int b = 0; b < Q.n; ++b) {

@@ -87,6 +87,9 @@ int or_singular(const double* r, const double* v0, const double* v1, const doubl
 /* Min / max distance between integration points over all regular (not near)
  * triangle pairs (Section II.B: table range). */
 int or_range(const or_mesh* m, int rule, double* r_min, double* r_max, int nthreads);
+/* The same result; prune = 1 skips triangle pairs that cannot hold an extreme
+ * (centroid-distance bounds), for large meshes. */
+int or_range_ex(const or_mesh* m, int rule, int prune, double* r_min, double* r_max, int nthreads);
 
 /* Z entries (m_i, n_i), i < nent. green_mode 0: direct; 1: tables (tgreen for
  * regular pairs, texp for the near-pair line integrals). */

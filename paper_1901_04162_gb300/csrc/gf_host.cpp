@@ -275,10 +275,12 @@ void free_mesh_device(gf_mesh* m) {
 }
 
 gf_status upload_vertices(gf_mesh* m) {
-  std::vector<double> v64(9 * (size_t)m->nt);
-  for (int64_t t = 0; t < m->nt; ++t)
+  std::vector<double> v64(9 * (size_t)m->nt);  // internal (Morton) triangle order
+  for (int64_t i = 0; i < m->nt; ++i) {
+    const int64_t t = m->perm[i];
     for (int c = 0; c < 3; ++c)
-      for (int x = 0; x < 3; ++x) v64[9 * t + 3 * c + x] = m->xyz[3 * (size_t)m->tri[3 * t + c] + x];
+      for (int x = 0; x < 3; ++x) v64[9 * i + 3 * c + x] = m->xyz[3 * (size_t)m->tri[3 * t + c] + x];
+  }
   std::vector<double> elen(m->ne);
   for (int64_t e = 0; e < m->ne; ++e) {
     double s = 0;
@@ -419,15 +421,51 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
     i = j;
   }
   m->ne = (int64_t)m->ev.size() / 2;
-  // ---- near pairs: vertex sharing, plus centroids closer than near_dist
-  std::vector<std::vector<int32_t>> vt(nv);
-  for (int64_t t = 0; t < nt; ++t)
-    for (int c = 0; c < 3; ++c) vt[tri[3 * t + c]].push_back((int32_t)t);
+  // ---- internal triangle order: Morton order of the centroids (locality of
+  // table windows, Z rows and range pruning); outputs use the original ids
   std::vector<double> cen(3 * nt);
   for (int64_t t = 0; t < nt; ++t)
     for (int x = 0; x < 3; ++x)
       cen[3 * t + x] = (xyz[3 * (size_t)tri[3 * t] + x] + xyz[3 * (size_t)tri[3 * t + 1] + x] +
                         xyz[3 * (size_t)tri[3 * t + 2] + x]) / 3.0;
+  {
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < nt; ++t)
+      for (int x = 0; x < 3; ++x) {
+        lo[x] = std::min(lo[x], cen[3 * t + x]);
+        hi[x] = std::max(hi[x], cen[3 * t + x]);
+      }
+    double ext = std::max(std::max(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+    const double scale = ext > 0 ? 2097151.0 / ext : 0.0;
+    auto spread = [](uint64_t v) {  // 21 bits -> every third bit
+      v &= 0x1FFFFF;
+      v = (v | (v << 32)) & 0x1F00000000FFFFULL;
+      v = (v | (v << 16)) & 0x1F0000FF0000FFULL;
+      v = (v | (v << 8)) & 0x100F00F00F00F00FULL;
+      v = (v | (v << 4)) & 0x10C30C30C30C30C3ULL;
+      v = (v | (v << 2)) & 0x1249249249249249ULL;
+      return v;
+    };
+    std::vector<std::pair<uint64_t, int32_t>> key(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+      uint64_t code = 0;
+      for (int x = 0; x < 3; ++x) code |= spread((uint64_t)((cen[3 * t + x] - lo[x]) * scale)) << x;
+      key[t] = std::make_pair(code, (int32_t)t);
+    }
+    std::sort(key.begin(), key.end());
+    m->perm.resize(nt);
+    std::vector<int32_t> inv(nt);
+    for (int64_t i = 0; i < nt; ++i) {
+      m->perm[i] = key[i].second;
+      inv[key[i].second] = (int32_t)i;
+    }
+    m->inv_perm = inv;
+  }
+  // ---- near pairs (internal ids): vertex sharing, plus centroids closer
+  // than near_dist
+  std::vector<std::vector<int32_t>> vt(nv);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int c = 0; c < 3; ++c) vt[tri[3 * t + c]].push_back((int32_t)t);
   std::unordered_map<int64_t, std::vector<int32_t>> grid;
   double cell = near_dist;
   auto key = [](int64_t a, int64_t b, int64_t c) { return ((a & 0x1FFFFF) << 42) | ((b & 0x1FFFFF) << 21) | (c & 0x1FFFFF); };
@@ -439,7 +477,8 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   }
   m->near_ptr.assign(nt + 1, 0);
   std::vector<int32_t> row;
-  for (int64_t p = 0; p < nt; ++p) {
+  for (int64_t pi = 0; pi < nt; ++pi) {
+    const int64_t p = m->perm[pi];  // original id
     row.clear();
     for (int c = 0; c < 3; ++c)
       for (int32_t q : vt[tri[3 * p + c]]) row.push_back(q);
@@ -458,10 +497,11 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
             }
           }
     }
+    for (int32_t& q : row) q = m->inv_perm[q];  // internal ids
     std::sort(row.begin(), row.end());
     row.erase(std::unique(row.begin(), row.end()), row.end());
     m->near_idx.insert(m->near_idx.end(), row.begin(), row.end());
-    m->near_ptr[p + 1] = (int64_t)m->near_idx.size();
+    m->near_ptr[pi + 1] = (int64_t)m->near_idx.size();
   }
   // ---- device upload
   gf_status st;
@@ -476,9 +516,10 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
     return st;
   }
   std::vector<int4> tv(nt), te(nt);
-  for (int64_t t = 0; t < nt; ++t) {
-    tv[t] = make_int4(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2], 0);
-    te[t] = make_int4(m->tedge[3 * t], m->tedge[3 * t + 1], m->tedge[3 * t + 2], 0);
+  for (int64_t i = 0; i < nt; ++i) {
+    const int64_t t = m->perm[i];
+    tv[i] = make_int4(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2], 0);
+    te[i] = make_int4(m->tedge[3 * t], m->tedge[3 * t + 1], m->tedge[3 * t + 2], 0);
   }
   cudaError_t e = cudaMemcpy(m->d_tvert, tv.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->d_tedge, te.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);

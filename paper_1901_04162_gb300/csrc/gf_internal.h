@@ -108,7 +108,9 @@ struct gf_mesh {
   std::vector<int32_t> ev, et;    // [ne][2]
   std::vector<int32_t> tedge;     // [nt][3], -1 if boundary
   std::vector<double> elen;       // [ne]
-  std::vector<int64_t> near_ptr;  // [nt + 1]
+  std::vector<int32_t> perm;      // internal triangle i = original triangle perm[i] (Morton order)
+  std::vector<int32_t> inv_perm;  // original -> internal
+  std::vector<int64_t> near_ptr;  // [nt + 1], internal ids
   std::vector<int32_t> near_idx;
   // device
   double* d_v64 = nullptr;

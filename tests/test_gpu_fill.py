@@ -89,8 +89,8 @@ def test_near_dist_criterion_matches_oracle():
 def test_sphere_7680_sampled_rows(near_fp64):
     wl = W.sphere_7680()
     m, z, tab = gpu_fill(wl.xyz, wl.tri, wl.k, 7, gf.GF_FP32, True, near_fp64=near_fp64)
-    lo, hi = m.range(7, gf.GF_FP64)
     om = O.Mesh(wl.xyz, wl.tri)
+    lo, hi = om.range(7)
     rows = np.random.default_rng(11).choice(m.ne, 12, replace=False)
     ref = om.z_rows(wl.k, 7, rows, mode="table", tables=O.make_tables(wl.k, lo, hi))
     assert rel_fro(z[rows], ref) <= 1e-5
@@ -130,3 +130,26 @@ def test_errors():
     t = gf.Table(K, 0.1, 1.0)
     with pytest.raises(gf.GfError):  # table built for another k
         gf.fill(m, 2 * K, gf.gf_params_default(rule=3), t, gf.GF_FP64)
+
+
+def test_cube_73728_sampled_rows():
+    # 49152 triangles, 73728 unknowns, complex64 Z of 43.5 GB; near pairs are
+    # those with centroids closer than 0.2 lambda; the Green table is larger
+    # than shared memory, so the regular kernel reads it through L1
+    wl = W.cube_73728()
+    m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    assert m.ne == 73728 and m.nt == 49152
+    p = gf.gf_params_default(rule=4)
+    lo, hi = m.range(4, gf.GF_FP32)
+    om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    olo, ohi = om.range(4, prune=True)
+    assert abs(lo - olo) <= 1e-6 * olo and abs(hi - ohi) <= 1e-6 * ohi
+    tab = gf.Table(wl.k, lo, hi, p)
+    Z = torch.empty((m.ne, m.ne), dtype=torch.complex64, device="cuda")
+    gf.gf_fill(m.h, wl.k, p, tab.h, gf.GF_FP32, Z)
+    rows = np.random.default_rng(17).choice(m.ne, 6, replace=False)
+    z = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
+    del Z
+    ref = om.z_rows(wl.k, 4, rows, mode="table", tables=O.make_tables(wl.k, olo, ohi))
+    assert rel_fro(z, ref) <= 1e-5
+    assert rel_max(z, ref) <= 1e-5

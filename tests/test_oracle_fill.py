@@ -131,6 +131,13 @@ def test_range_is_brute_force_min_max():
     assert lo == R.min() and hi == R.max()
 
 
+def test_pruned_range_equals_brute_force():
+    for xyz, tri, nd, rule in [(*W.octasphere(3, 1.0), 0.0, 7), (*W.plate(0.5, 10), 0.0, 3),
+                               (W.cube_73728(5).xyz, W.cube_73728(5).tri, 0.2, 4)]:
+        m = O.Mesh(xyz, tri, nd)
+        assert m.range(rule, prune=True) == m.range(rule)
+
+
 def test_near_dist_criterion():
     wl = W.cube_73728(4)
     m0 = O.Mesh(wl.xyz, wl.tri)
