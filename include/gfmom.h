@@ -170,6 +170,34 @@ gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table
 gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                         int precision, void* Z_dev, int64_t ldz, unsigned parts, void* stream);
 
+/* ---------------------------------------------------------------- batched --
+ * Many meshes in one launch per kernel: each mesh i has its own wavenumber
+ * k[i], tables[i] (built for k[i] over that mesh's gf_range; tables == NULL:
+ * direct evaluation for all) and Z[i] (device, row-major, complex64, ld
+ * ldz[i]); all share the params (rule, near-pair options). The work of all
+ * meshes forms one task list, largest meshes first, pulled by persistent
+ * kernels through an atomic counter; the zeroing of every Z and the kernels
+ * are captured once into a CUDA graph on a stream owned by the batch
+ * (Section II.A fill; the batching is this library's, not the paper's).
+ * autotune != 0 times the launch shapes (block size, CTAs per SM, task
+ * chunk) on the batch and keeps the fastest; choices are cached in the file
+ * named by $GF_AUTOTUNE_CACHE (default ~/.cache/gfmom_autotune.txt, "off"
+ * disables the cache). precision must be GF_FP32. Meshes, tables and Z must
+ * outlive the batch; the batch stores their device pointers. gf_batch_create
+ * synchronizes `stream`. */
+typedef struct gf_batch gf_batch;
+gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double* k, const gf_params* p,
+                          const gf_table* const* tables, int precision, void* const* Z, const int64_t* ldz,
+                          int autotune, void* stream, gf_batch** out);
+
+/* Replays the captured graph on `stream` (asynchronous): refills every Z. */
+gf_status gf_batch_launch(const gf_batch* b, void* stream);
+
+/* The launch shape in use and the tuner's time per launch (0 if not tuned). */
+gf_status gf_batch_config(const gf_batch* b, int* block, int* ctas_per_sm, int* chunk, double* tuned_ms);
+
+gf_status gf_batch_destroy(gf_batch* b);
+
 /* ---------------------------------------------------------------- no-alloc -
  * gf_range for callers that cannot allocate device memory (for example code
  * running while a CUDA graph is captured, or a plug-in whose host application

@@ -297,7 +297,7 @@ gf_status upload_vertices(gf_mesh* m) {
 }
 
 // Builds (or reuses) the per-rule geometry on the device.
-gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s) {
+gf_status prepare_rule_impl(gf_mesh* m, int rule, cudaStream_t s) {
   if (m->rule == rule) return GF_OK;
   double bary[kMaxRule][3], w[kMaxRule];
   if (!rule_points(rule, bary, w)) return fail(GF_ERR_ARG, "rule must be 1, 3, 4, 6 or 7");
@@ -321,7 +321,7 @@ gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s) {
   return GF_OK;
 }
 
-GeoView geo_view(const gf_mesh* m) {
+GeoView geo_view_impl(const gf_mesh* m) {
   GeoView g;
   g.nt = (int)m->nt;
   g.m = m->rule;
@@ -349,6 +349,12 @@ bool params_ok(const gf_params* p) {
 }
 
 }  // namespace
+
+namespace gf {
+gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s) { return ::prepare_rule_impl(m, rule, s); }
+GeoView geo_view(const gf_mesh* m) { return ::geo_view_impl(m); }
+void gauss_legendre_host(int n, double* x, double* w) { gauss_legendre(n, x, w); }
+}  // namespace gf
 
 extern "C" {
 
@@ -578,8 +584,8 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
   gf_status st = check_device(m->device);
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = prepare_rule(m, rule, s))) return st;
-  GF_CUDA(launch_range(geo_view(m), precision, m->d_minmax, s));
+  if ((st = prepare_rule_impl(m, rule, s))) return st;
+  GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, s));
   unsigned long long mm[2];
   GF_CUDA(cudaMemcpyAsync(mm, m->d_minmax, 16, cudaMemcpyDeviceToHost, s));
   GF_CUDA(cudaStreamSynchronize(s));
@@ -737,12 +743,12 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   if (table && (table->device != m->device)) return fail(GF_ERR_DEVICE, "gf_fill: table on another device");
   if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill: table built for another k");
   cudaStream_t s = (cudaStream_t)stream;
-  if ((st = prepare_rule(m, p->rule, s))) return st;
+  if ((st = prepare_rule_impl(m, p->rule, s))) return st;
   if (m->ne == 0) return GF_OK;
   const size_t esz = precision == GF_FP32 ? 8 : 16;
   if (parts & GF_PART_ZERO)
     GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
-  GeoView g = geo_view(m);
+  GeoView g = geo_view_impl(m);
   TabView tg, te;
   if (table) {
     tg = table->green.view();

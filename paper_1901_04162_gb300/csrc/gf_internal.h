@@ -13,6 +13,11 @@ namespace gf {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxRule = 7;
 
+}  // namespace gf
+struct gf_mesh;
+struct gf_table;
+namespace gf {
+
 // ---------------------------------------------------------------- errors
 gf_status fail(gf_status st, const std::string& msg);
 gf_status cuda_fail(cudaError_t e, const char* what);
@@ -76,6 +81,19 @@ struct TabView {
   size_t smem32_bytes() const { return (size_t)n_cells32 * 16 + (size_t)(n_nodes - 1) * 32; }
 };
 
+// One mesh of a batched fill (device-resident descriptor).
+struct BatchItem {
+  GeoView g;
+  TabView green, exp;
+  int use_table;
+  float kpi, scale32, inv_k2_32;  // k/pi, k eta/(4 pi), 1/k^2 for the FP32 regular kernel
+  double k, scale, inv_k2;        // k, k eta, 1/k^2 for the near kernel
+  void* Z;
+  int64_t ldz;
+  int64_t reg_begin, nchunk;      // first global regular task, 32-wide chunks per test triangle
+  int64_t near_begin, n_near;     // first global near pair, near pairs
+};
+
 // ---------------------------------------------------------------- kernels (gf_kernels.cu)
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
@@ -95,6 +113,17 @@ cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int prec
 cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k,
                              double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
                              void* Z, int64_t ldz, cudaStream_t s);
+
+cudaError_t launch_batch_regular(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter, int m,
+                                 bool table, int block, int grid, int chunk, cudaStream_t s);
+cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter,
+                              bool mixed, int nphi, int nl, const double* gl_phi, const double* gl_l, int grid,
+                              cudaStream_t s);
+int batch_regular_blocks_per_sm(int m, bool table, int block);
+void gauss_legendre_host(int n, double* x, double* w);
+// host helpers shared by the single and batched fills (gf_host.cpp)
+gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s);
+GeoView geo_view(const gf_mesh* m);
 
 }  // namespace gf
 

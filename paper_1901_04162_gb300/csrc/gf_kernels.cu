@@ -476,6 +476,92 @@ struct KSum {  // Kahan-compensated FP32 sum
 
 // Blocks of 512 threads when the table is staged in shared memory (one CTA
 // per SM holds it), 256 otherwise.
+// One warp task of the regular-pair fill: test triangle p, source triangles
+// q0..q0+31 (one per lane).
+template <int M, bool TABLE>
+__device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               float2* Z, int64_t ldz, int p, int q0, int lane) {
+  const int q = min(q0 + lane, g.nt - 1);
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+  const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  if (!__any_sync(0xffffffffu, ok)) return;
+  float4 beta[M];
+#pragma unroll
+  for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
+  KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
+#pragma unroll 1
+  for (int a = 0; a < M; ++a) {
+    const float4 al = g.pts32[(size_t)a * g.nt + p];
+    const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+    float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      float gr, gi;
+      if (TABLE) {
+        const float2 f = lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
+        gr = f.x * beta[b].w;
+        gi = f.y * beta[b].w;
+      } else {
+        float sn, cs;
+        sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
+        const float wr = beta[b].w * rs;
+        gr = cs * wr;
+        gi = -sn * wr;
+      }
+      s0r += gr;
+      s0i += gi;
+      sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
+      sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
+      sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
+      sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
+      sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
+      sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
+    }
+    const float wa = al.w;
+    M0r.add(wa * s0r);
+    M0i.add(wa * s0i);
+    const float wal[3] = {wa * al.x, wa * al.y, wa * al.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Mar[c].add(wal[c] * s0r);
+      Mai[c].add(wal[c] * s0i);
+      Mbr[c].add(wa * sbr[c]);
+      Mbi[c].add(wa * sbi[c]);
+    }
+    Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
+    Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
+  }
+  if (!ok) return;
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+  const float m0r = M0r.s, m0i = M0i.s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!edge_valid(ecp[i])) continue;
+    const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
+    const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
+    const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
+    float2* zrow = Z + (int64_t)edge_of(ecp[i]) * ldz;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!edge_valid(ecq[j])) continue;
+      const float4 gq = g.geo32[3 * (size_t)q + j];  // eps_j, s_j l_j
+      const float eMar = gq.x * Mar[0].s + gq.y * Mar[1].s + gq.z * Mar[2].s;
+      const float eMai = gq.x * Mai[0].s + gq.y * Mai[1].s + gq.z * Mai[2].s;
+      const float de = gp.x * gq.x + gp.y * gq.y + gp.z * gq.z;
+      const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
+      const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
+      const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
+      // j * c * (br + j bi) = c * (-bi + j br)
+      atomicAdd(zrow + edge_of(ecq[j]), make_float2(-c * bi, c * br));
+    }
+  }
+}
+
 template <int M, bool TABLE, bool SMEM>
 __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoView g, TabView tv, float kpi,
                                                                           float scale, float inv_k2, float2* Z,
@@ -502,87 +588,7 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoVie
   const int64_t ntask = (int64_t)g.nt * nchunk;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
-    const int p = (int)(task / nchunk);
-    const int q0 = (int)(task % nchunk) * 32;
-    const int q = min(q0 + lane, g.nt - 1);
-    const float4 cp = g.cen32[p], cq = g.cen32[q];
-    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-    const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
-    if (!__any_sync(0xffffffffu, ok)) continue;
-    float4 beta[M];
-#pragma unroll
-    for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
-    KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
-#pragma unroll 1
-    for (int a = 0; a < M; ++a) {
-      const float4 al = g.pts32[(size_t)a * g.nt + p];
-      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
-      float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int b = 0; b < M; ++b) {
-        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float rs = rsqrtf(R2);
-        float gr, gi;
-        if (TABLE) {
-          const float2 f = lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
-          gr = f.x * beta[b].w;
-          gi = f.y * beta[b].w;
-        } else {
-          float sn, cs;
-          sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
-          const float wr = beta[b].w * rs;
-          gr = cs * wr;
-          gi = -sn * wr;
-        }
-        s0r += gr;
-        s0i += gi;
-        sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
-        sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
-        sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
-        sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
-        sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
-        sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
-      }
-      const float wa = al.w;
-      M0r.add(wa * s0r);
-      M0i.add(wa * s0i);
-      const float wal[3] = {wa * al.x, wa * al.y, wa * al.z};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        Mar[c].add(wal[c] * s0r);
-        Mai[c].add(wal[c] * s0i);
-        Mbr[c].add(wa * sbr[c]);
-        Mbi[c].add(wa * sbi[c]);
-      }
-      Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
-      Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
-    }
-    if (!ok) continue;
-    const int4 ep = g.tedge[p], eq = g.tedge[q];
-    const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-    const float m0r = M0r.s, m0i = M0i.s;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      if (!edge_valid(ecp[i])) continue;
-      const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
-      const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
-      const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
-      float2* zrow = Z + (int64_t)edge_of(ecp[i]) * ldz;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        if (!edge_valid(ecq[j])) continue;
-        const float4 gq = g.geo32[3 * (size_t)q + j];  // eps_j, s_j l_j
-        const float eMar = gq.x * Mar[0].s + gq.y * Mar[1].s + gq.z * Mar[2].s;
-        const float eMai = gq.x * Mai[0].s + gq.y * Mai[1].s + gq.z * Mai[2].s;
-        const float de = gp.x * gq.x + gp.y * gq.y + gp.z * gq.z;
-        const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
-        const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
-        const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
-        // j * c * (br + j bi) = c * (-bi + j br)
-        atomicAdd(zrow + edge_of(ecq[j]), make_float2(-c * bi, c * br));
-      }
-    }
+    regular_task32<M, TABLE>(g, T, kpi, scale, inv_k2, Z, ldz, (int)(task / nchunk), (int)(task % nchunk) * 32, lane);
   }
 }
 
@@ -683,6 +689,10 @@ struct C2 {
   double re, im;
 };
 
+struct KScal {  // per-wavenumber scalars of the near-pair fill
+  double k, scale, inv_k2;
+};
+
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
   if (use_table && R >= te->r_lo && R <= te->r_hi) {
     double2 f = lookup64<1>(*te, R);
@@ -694,9 +704,8 @@ __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bo
 }
 
 // Inner integrals over triangle v for observation point r (1/(4 pi) included).
-__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, const TabView* te,
-                                bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
-  const double k = A.k;
+__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, double k,
+                                const TabView* te, bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
   double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
   double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
   double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -790,10 +799,10 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 // frames), the closed-form static part and all accumulation in FP64; the
 // sampling of e^{-jkR} at the angular and line nodes of each edge in FP32
 // (relative quantities of the size of a triangle, FP32 Exp table).
-__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const NearArgs& A, const Tab32& te,
-                                      bool use_table, float lo, float hi, C2* I0, C2 I1[3], double rho0[3]) {
-  const double k = A.k;
-  const float kpi = (float)(A.k / kPi), k32 = (float)A.k;
+__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const NearArgs& A, double k,
+                                      const Tab32& te, bool use_table, float lo, float hi, C2* I0, C2 I1[3],
+                                      double rho0[3]) {
+  const float kpi = (float)(k / kPi), k32 = (float)k;
   double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
   double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
   double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -885,6 +894,91 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
 // One near pair per group of 8 lanes, one test point per lane (lanes >= m
 // idle); the 3 x 3 block is reduced across the group with shuffles and added
 // to Z by the group's first lane.
+// One near pair (index idx of the CSR list; valid_pair false: padding) on a
+// group of 8 lanes, one test point per lane; every lane of the group must call.
+template <class Out, bool MIXED>
+__device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
+                                          int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
+                                          unsigned gmask) {
+  if (!valid_pair) return;  // uniform over the 8-lane group
+  const int64_t pidx = idx;
+  int lo = 0, hi = g.nt - 1;  // p = row containing pidx
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.near_ptr[mid] <= pidx) lo = mid;
+    else hi = mid - 1;
+  }
+  const int p = lo, q = g.near_idx[pidx];
+  double accr[3][3], acci[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.0;
+  if (sub < g.m) {
+    double vq[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
+    const double* cp = g.cen64 + 4 * (size_t)p;
+    const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
+    const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
+    C2 I0, I1[3];
+    double rho0[3];
+    if (MIXED) inner_integrals_mixed(ra, vq, A, ks.k, te32, use_table, lo32, hi32, &I0, I1, rho0);
+    else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
+    const double wa = al[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // J_j = I1 + (rho0 - v_j) I0
+      C2 J[3];
+      for (int x = 0; x < 3; ++x) {
+        const double dv = rho0[x] - vq[j][x];
+        J[x].re = I1[x].re + dv * I0.re;
+        J[x].im = I1[x].im + dv * I0.im;
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
+        const double f0 = ra[0] - vpi[0], f1 = ra[1] - vpi[1], f2 = ra[2] - vpi[2];
+        const double dr = f0 * J[0].re + f1 * J[1].re + f2 * J[2].re;
+        const double di = f0 * J[0].im + f1 * J[1].im + f2 * J[2].im;
+        accr[i][j] = wa * (0.25 * dr - I0.re * ks.inv_k2);
+        acci[i][j] = wa * (0.25 * di - I0.im * ks.inv_k2);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int off = 1; off < 8; off <<= 1) {
+        accr[i][j] += __shfl_xor_sync(gmask, accr[i][j], off);
+        acci[i][j] += __shfl_xor_sync(gmask, acci[i][j], off);
+      }
+  if (sub != 0) return;
+  const double area_q = g.cen64[4 * (size_t)q + 3];
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+  for (int i = 0; i < 3; ++i) {
+    if (!edge_valid(ecp[i])) continue;
+    const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3];
+    for (int j = 0; j < 3; ++j) {
+      if (!edge_valid(ecq[j])) continue;
+      const double slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
+      const double c = ks.scale * slp * slq / area_q;  // k eta s_i l_i s_j l_j / A_q
+      const double zr = -c * acci[i][j], zi = c * accr[i][j];
+      Out* z = Z + (int64_t)edge_of(ecp[i]) * ldz + edge_of(ecq[j]);
+      if constexpr (sizeof(Out) == 8) {
+        atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
+      } else {
+        atomicAdd(reinterpret_cast<double*>(z), zr);
+        atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
+      }
+    }
+  }
+}
+
 template <class Out, bool MIXED>
 __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
                                                    int64_t ldz) {
@@ -898,81 +992,65 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
   const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
   for (int64_t it = 0; it < iters; ++it) {
     const int64_t idx = g0 + it * ngroups;
-    const bool valid_pair = idx < n_near;
-    const int64_t pidx = valid_pair ? idx : n_near - 1;
-    int lo = 0, hi = g.nt - 1;  // p = row containing pidx
-    while (lo < hi) {
-      int mid = (lo + hi + 1) >> 1;
-      if (g.near_ptr[mid] <= pidx) lo = mid;
-      else hi = mid - 1;
+    near_task<Out, MIXED>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2}, Z, ldz, n_near, idx,
+                          idx < n_near, sub, gmask);
+  }
+}
+
+// ---------------------------------------------------------------- batched
+// Persistent kernels over the regular tasks and near pairs of many meshes:
+// warps pull chunks of a global task list (meshes with the most work first)
+// from an atomic counter; the mesh of a task is found by binary search in the
+// descriptors' prefix offsets. Every mesh has its own k, tables and Z.
+__device__ __forceinline__ int batch_item_of(const BatchItem* items, int nitems, int64_t t, bool near) {
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t b = near ? items[mid].near_begin : items[mid].reg_begin;
+    if (b <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int M, bool TABLE>
+__global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __restrict__ items, int nitems, int64_t total,
+                                                         unsigned long long* counter, int chunk) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, (unsigned long long)chunk);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)base >= total) break;
+    const int64_t end = min((int64_t)base + chunk, total);
+    for (int64_t t = (int64_t)base; t < end; ++t) {
+      const BatchItem& it = items[batch_item_of(items, nitems, t, false)];
+      const int64_t local = t - it.reg_begin;
+      const Tab32 T = tab32(it.green);
+      regular_task32<M, TABLE>(it.g, T, it.kpi, it.scale32, it.inv_k2_32, reinterpret_cast<float2*>(it.Z), it.ldz,
+                               (int)(local / it.nchunk), (int)(local % it.nchunk) * 32, lane);
     }
-    const int p = lo, q = g.near_idx[pidx];
-    double accr[3][3], acci[3][3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.0;
-    if (valid_pair && sub < g.m) {
-      double vq[3][3];
-      for (int c = 0; c < 3; ++c)
-        for (int x = 0; x < 3; ++x) vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
-      const double* cp = g.cen64 + 4 * (size_t)p;
-      const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
-      const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
-      C2 I0, I1[3];
-      double rho0[3];
-      if (MIXED) inner_integrals_mixed(ra, vq, A, te32, use_table, lo32, hi32, &I0, I1, rho0);
-      else inner_integrals(ra, vq, A, &te, use_table, &I0, I1, rho0);
-      const double wa = al[3];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        // J_j = I1 + (rho0 - v_j) I0
-        C2 J[3];
-        for (int x = 0; x < 3; ++x) {
-          const double dv = rho0[x] - vq[j][x];
-          J[x].re = I1[x].re + dv * I0.re;
-          J[x].im = I1[x].im + dv * I0.im;
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
-          const double f0 = ra[0] - vpi[0], f1 = ra[1] - vpi[1], f2 = ra[2] - vpi[2];
-          const double dr = f0 * J[0].re + f1 * J[1].re + f2 * J[2].re;
-          const double di = f0 * J[0].im + f1 * J[1].im + f2 * J[2].im;
-          accr[i][j] = wa * (0.25 * dr - I0.re * A.inv_k2);
-          acci[i][j] = wa * (0.25 * di - I0.im * A.inv_k2);
-        }
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int off = 1; off < 8; off <<= 1) {
-          accr[i][j] += __shfl_xor_sync(gmask, accr[i][j], off);
-          acci[i][j] += __shfl_xor_sync(gmask, acci[i][j], off);
-        }
-    if (!valid_pair || sub != 0) continue;
-    const double area_q = g.cen64[4 * (size_t)q + 3];
-    const int4 ep = g.tedge[p], eq = g.tedge[q];
-    const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-    for (int i = 0; i < 3; ++i) {
-      if (!edge_valid(ecp[i])) continue;
-      const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3];
-      for (int j = 0; j < 3; ++j) {
-        if (!edge_valid(ecq[j])) continue;
-        const double slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
-        const double c = A.scale * slp * slq / area_q;  // k eta s_i l_i s_j l_j / A_q
-        const double zr = -c * acci[i][j], zi = c * accr[i][j];
-        Out* z = Z + (int64_t)edge_of(ecp[i]) * ldz + edge_of(ecq[j]);
-        if constexpr (sizeof(Out) == 8) {
-          atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
-        } else {
-          atomicAdd(reinterpret_cast<double*>(z), zr);
-          atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
-        }
-      }
+  }
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) k_batch_near(const BatchItem* __restrict__ items, int nitems, int64_t total,
+                                                    unsigned long long* counter, NearArgs A) {
+  const int lane = threadIdx.x & 31;
+  const int sub = threadIdx.x & 7;
+  const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+  for (;;) {
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(counter, 4ull);  // one near pair per 8-lane group
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((int64_t)base >= total) break;
+    const int64_t t = (int64_t)base + (lane >> 3);
+    if (t < total) {
+      const BatchItem& it = items[batch_item_of(items, nitems, t, true)];
+      const Tab32 te32 = tab32(it.exp);
+      near_task<float2, MIXED>(it.g, it.exp, te32, (float)it.exp.r_lo, (float)it.exp.r_hi, it.use_table != 0, A,
+                               KScal{it.k, it.scale, it.inv_k2}, reinterpret_cast<float2*>(it.Z), it.ldz, it.n_near,
+                               t - it.near_begin, true, sub, gmask);
     }
   }
 }
@@ -995,6 +1073,69 @@ int64_t pair_grid(const GeoView& g, int blocks_per_sm) {
 }
 
 }  // namespace
+
+template <int M>
+cudaError_t launch_batch_regular_m(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter,
+                                   bool table, int block, int grid, int chunk, cudaStream_t s) {
+  if (table)
+    k_batch_regular32<M, true><<<grid, block, 0, s>>>(items, nitems, total, counter, chunk);
+  else
+    k_batch_regular32<M, false><<<grid, block, 0, s>>>(items, nitems, total, counter, chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_regular(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter, int m,
+                                 bool table, int block, int grid, int chunk, cudaStream_t s) {
+  switch (m) {
+    case 1: return launch_batch_regular_m<1>(items, nitems, total, counter, table, block, grid, chunk, s);
+    case 3: return launch_batch_regular_m<3>(items, nitems, total, counter, table, block, grid, chunk, s);
+    case 4: return launch_batch_regular_m<4>(items, nitems, total, counter, table, block, grid, chunk, s);
+    case 6: return launch_batch_regular_m<6>(items, nitems, total, counter, table, block, grid, chunk, s);
+    case 7: return launch_batch_regular_m<7>(items, nitems, total, counter, table, block, grid, chunk, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int M>
+int batch_blocks_m(bool table, int block) {
+  int n = 0;
+  if (table) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_regular32<M, true>, block, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_regular32<M, false>, block, 0);
+  return n;
+}
+
+int batch_regular_blocks_per_sm(int m, bool table, int block) {
+  switch (m) {
+    case 1: return batch_blocks_m<1>(table, block);
+    case 3: return batch_blocks_m<3>(table, block);
+    case 4: return batch_blocks_m<4>(table, block);
+    case 6: return batch_blocks_m<6>(table, block);
+    case 7: return batch_blocks_m<7>(table, block);
+    default: return 0;
+  }
+}
+
+cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter,
+                              bool mixed, int nphi, int nl, const double* gl_phi, const double* gl_l, int grid,
+                              cudaStream_t s) {
+  NearArgs A;
+  A.k = A.scale = A.inv_k2 = 0.0;  // per mesh, from the descriptors
+  A.nphi = nphi;
+  A.nl = nl;
+  for (int i = 0; i < 32; ++i) {
+    A.gx_phi[i] = gl_phi[i];
+    A.gw_phi[i] = gl_phi[32 + i];
+    A.gx_l[i] = gl_l[i];
+    A.gw_l[i] = gl_l[32 + i];
+    A.fx_phi[i] = (float)A.gx_phi[i];
+    A.fw_phi[i] = (float)A.gw_phi[i];
+    A.fx_l[i] = (float)A.gx_l[i];
+    A.fw_l[i] = (float)A.gw_l[i];
+  }
+  if (mixed) k_batch_near<true><<<grid, 128, 0, s>>>(items, nitems, total, counter, A);
+  else k_batch_near<false><<<grid, 128, 0, s>>>(items, nitems, total, counter, A);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,

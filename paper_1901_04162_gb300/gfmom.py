@@ -24,7 +24,8 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
-           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc"]
+           "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
+           "gf_batch_config", "gf_batch_destroy"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -74,6 +75,12 @@ def lib():
         L.gf_fill.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
         L.gf_fill_parts.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, C.c_uint, vp]
         L.gf_range_noalloc.argtypes = [vp, vp, i64, C.c_int, vp, vp]
+        L.gf_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(C.c_double), C.POINTER(gf_params),
+                                      C.POINTER(vp), C.c_int, C.POINTER(vp), C.POINTER(i64), C.c_int, vp,
+                                      C.POINTER(vp)]
+        L.gf_batch_launch.argtypes = [vp, vp]
+        L.gf_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
+        L.gf_batch_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -297,3 +304,54 @@ def gf_range_noalloc(tri_xyz, tri_vert, rule, minmax, stream=None):
     _check(lib().gf_range_noalloc(C.c_void_p(tri_xyz.data_ptr()), C.c_void_p(tri_vert.data_ptr()), nt, int(rule),
                                   C.c_void_p(minmax.data_ptr()), _stream_ptr(stream)))
     return minmax
+
+
+def gf_batch_create(meshes, ks, params, tables, Zs, autotune=True, stream=None):
+    """meshes: Mesh objects; ks: wavenumbers; tables: Table objects or None;
+    Zs: contiguous CUDA complex64 tensors [ne_i, ldz_i]."""
+    n = len(meshes)
+    for Z in Zs:
+        _check_z(Z, GF_FP32)
+    mh = (C.c_void_p * n)(*[m.h.value for m in meshes])
+    kk = (C.c_double * n)(*[float(k) for k in ks])
+    th = (C.c_void_p * n)(*[t.h.value for t in tables]) if tables is not None else None
+    zz = (C.c_void_p * n)(*[Z.data_ptr() for Z in Zs])
+    ld = (C.c_int64 * n)(*[Z.shape[-1] for Z in Zs])
+    h = C.c_void_p()
+    _check(lib().gf_batch_create(n, mh, kk, C.byref(params), th, GF_FP32, zz, ld, int(bool(autotune)),
+                                 _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def gf_batch_launch(h, stream=None):
+    _check(lib().gf_batch_launch(h, _stream_ptr(stream)))
+
+
+def gf_batch_config(h):
+    b, c, ch, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+    _check(lib().gf_batch_config(h, C.byref(b), C.byref(c), C.byref(ch), C.byref(ms)))
+    return {"block": b.value, "ctas_per_sm": c.value, "chunk": ch.value, "tuned_ms": ms.value}
+
+
+def gf_batch_destroy(h):
+    _check(lib().gf_batch_destroy(h))
+
+
+class Batch:
+    """Owns a gf_batch handle; keeps the meshes, tables and Z tensors alive."""
+
+    def __init__(self, meshes, ks, params, tables, Zs, autotune=True, stream=None):
+        self.meshes, self.tables, self.Zs, self.params = list(meshes), tables, list(Zs), params
+        self.h = gf_batch_create(self.meshes, ks, params, tables, self.Zs, autotune, stream)
+
+    def launch(self, stream=None):
+        gf_batch_launch(self.h, stream)
+
+    def config(self):
+        return gf_batch_config(self.h)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().gf_batch_destroy(h)
+            self.h = None

@@ -1,0 +1,86 @@
+"""Batched fill (many meshes, own k, tables and Z, persistent kernels in a
+CUDA graph) vs the single-mesh fill and the oracle."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_1901_04162_gb300 as gf
+import workloads as W
+from gpu_util import rel_fro
+
+pytestmark = pytest.mark.gpu
+
+
+def build(count, table=True, rule=6):
+    wls = W.ellipsoid_batch(count)
+    p = gf.gf_params_default(rule=rule)
+    meshes, tables, Zs, ks = [], [], [], []
+    for wl in wls:
+        m = gf.Mesh(wl.xyz, wl.tri)
+        meshes.append(m)
+        ks.append(wl.k)
+        if table:
+            lo, hi = m.range(rule, gf.GF_FP32)
+            tables.append(gf.Table(wl.k, lo, hi, p))
+        Zs.append(torch.full((m.ne, m.ne + 3), float("nan"), dtype=torch.complex64, device="cuda"))
+    return wls, p, meshes, (tables if table else None), Zs, ks
+
+
+@pytest.mark.parametrize("table", [True, False])
+def test_batch_matches_single_fills(table, tmp_path, monkeypatch):
+    monkeypatch.setenv("GF_AUTOTUNE_CACHE", str(tmp_path / "tune.txt"))
+    wls, p, meshes, tables, Zs, ks = build(5, table)
+    b = gf.Batch(meshes, ks, p, tables, Zs, autotune=False)
+    for rep in range(2):  # graph replay refills every Z
+        for Z in Zs:
+            Z.fill_(float("nan"))
+        b.launch()
+        torch.cuda.synchronize()
+        for i, m in enumerate(meshes):
+            ref = gf.fill(m, ks[i], p, tables[i] if table else None, gf.GF_FP32).cpu().numpy()
+            z = Zs[i].cpu().numpy()
+            assert np.all(np.isnan(z[:, m.ne:]))  # padding columns untouched
+            assert rel_fro(z[:, :m.ne], ref) <= 1e-6, (rep, i)
+
+
+def test_batch_matches_oracle_rows():
+    wls, p, meshes, tables, Zs, ks = build(3)
+    b = gf.Batch(meshes, ks, p, tables, Zs, autotune=False)
+    b.launch()
+    torch.cuda.synchronize()
+    for i, wl in enumerate(wls):
+        om = O.Mesh(wl.xyz, wl.tri)
+        lo, hi = om.range(6)
+        rows = np.random.default_rng(i).choice(om.ne, 4, replace=False)
+        ref = om.z_rows(wl.k, 6, rows, mode="table", tables=O.make_tables(wl.k, lo, hi))
+        z = Zs[i][torch.from_numpy(rows).cuda(), :meshes[i].ne].cpu().numpy()
+        assert rel_fro(z, ref) <= 1e-5
+
+
+def test_autotune_and_cache(tmp_path, monkeypatch):
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("GF_AUTOTUNE_CACHE", str(path))
+    wls, p, meshes, tables, Zs, ks = build(3)
+    b1 = gf.Batch(meshes, ks, p, tables, Zs, autotune=True)
+    c1 = b1.config()
+    assert c1["tuned_ms"] > 0 and c1["block"] in (128, 256, 512) and 1 <= c1["ctas_per_sm"] <= 4
+    assert path.exists() and len(path.read_text().splitlines()) == 1
+    b2 = gf.Batch(meshes, ks, p, tables, Zs, autotune=True)  # read from the cache, no new line
+    c2 = b2.config()
+    assert all(c2[k] == c1[k] for k in ("block", "ctas_per_sm", "chunk"))
+    assert abs(c2["tuned_ms"] - c1["tuned_ms"]) <= 1e-5 and len(path.read_text().splitlines()) == 1
+    b2.launch()
+    torch.cuda.synchronize()
+    ref = gf.fill(meshes[0], ks[0], p, tables[0], gf.GF_FP32).cpu().numpy()
+    assert rel_fro(Zs[0][:, :meshes[0].ne].cpu().numpy(), ref) <= 1e-6
+
+
+def test_batch_rejects_bad_input():
+    wls, p, meshes, tables, Zs, ks = build(2)
+    with pytest.raises(gf.GfError):
+        gf.Batch(meshes, [ks[0], 2 * ks[1]], p, tables, Zs, autotune=False)  # table for another k
+    with pytest.raises(gf.GfError):
+        gf.Batch(meshes, ks, p, tables, [Zs[0], Zs[0][:, :10].contiguous()], autotune=False)  # ldz < ne
