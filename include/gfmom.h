@@ -170,6 +170,22 @@ gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table
 gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                         int precision, void* Z_dev, int64_t ldz, unsigned parts, void* stream);
 
+/* ---------------------------------------------------------------- adjoint --
+ * Backward of the fill (no counterpart in the paper; the gradient of a loss of
+ * Z with respect to the geometry and the wavenumber). gZ: device complex64
+ * [ne][ldg], the upstream gradient in the convention dL = Re sum conj(gZ) dZ
+ * (PyTorch's for a real loss). Writes dxyz (device float64 [nv][3], original
+ * vertex ids) = dL/d(vertex coordinates) and *dk (device float64) = dL/dk.
+ * Regular pairs: FP32 reverse mode with the Green values recomputed from
+ * `table` (direct if NULL), F' = -(jk + 1/R) F, dF/dk = -jR F. Near pairs: FP64
+ * forward mode (one dual direction per coordinate of the pair and k). The
+ * near / regular classification, the table range and its samples are held
+ * fixed. precision must be GF_FP32. Asynchronous on `stream`; uses per-mesh
+ * scratch, so backward calls on one mesh must not overlap. */
+gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
+                           int precision, const void* gZ, int64_t ldg, double* dxyz, double* dk,
+                           void* stream);
+
 /* ---------------------------------------------------------------- batched --
  * Many meshes in one launch per kernel: each mesh i has its own wavenumber
  * k[i], tables[i] (built for k[i] over that mesh's gf_range; tables == NULL:

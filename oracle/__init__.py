@@ -57,6 +57,8 @@ def lib():
         L.or_range_ex.argtypes = [vp, C.c_int, C.c_int, dp, dp, C.c_int]
         L.or_z_entries.argtypes = [vp, C.POINTER(FillParams), vp, vp, C.c_long, ip, ip, dp, dp, C.c_int]
         L.or_loss_grad.argtypes = [vp, C.POINTER(FillParams), dp, dp, dp, dp, dp, dp, dp, C.c_int]
+        L.or_loss_grad_masked.argtypes = [vp, C.POINTER(FillParams), dp, dp, dp, dp, ip, dp, dp, dp, C.c_int]
+        L.or_loss_dk.argtypes = [vp, C.POINTER(FillParams), dp, dp, dp, dp, dp, dp, C.c_int]
         _lib = L
     return _lib
 
@@ -235,18 +237,31 @@ class Mesh:
         m, n = np.meshgrid(rows, np.arange(self.ne), indexing="ij")
         return self.z_entries(k, rule, m.ravel(), n.ravel(), **kw).reshape(len(rows), self.ne)
 
-    def loss_grad(self, k, rule, a, b, nphi=8, nl=8, eta=ETA0, nthreads=0):
+    def loss_grad(self, k, rule, a, b, nphi=8, nl=8, eta=ETA0, nthreads=0, tri_mask=None):
         ar, ai = np.ascontiguousarray(a.real), np.ascontiguousarray(a.imag)
         br, bi = np.ascontiguousarray(b.real), np.ascontiguousarray(b.imag)
         loss = C.c_double()
         dk = C.c_double()
         dx = np.zeros(self.xyz.shape)
         fp = FillParams(k, eta, rule, nphi, nl, 0)
-        rc = lib().or_loss_grad(self.h, C.byref(fp), _dp(ar), _dp(ai), _dp(br), _dp(bi),
-                                C.byref(loss), _dp(dx), C.byref(dk), nthreads)
+        mask = None if tri_mask is None else np.ascontiguousarray(tri_mask, dtype=np.int32)
+        rc = lib().or_loss_grad_masked(self.h, C.byref(fp), _dp(ar), _dp(ai), _dp(br), _dp(bi),
+                                       None if mask is None else _ip(mask), C.byref(loss), _dp(dx),
+                                       C.byref(dk), nthreads)
         if rc != 0:
             raise ValueError(rc)
         return loss.value, dx, dk.value
+
+    def loss_dk(self, k, rule, a, b, nphi=8, nl=8, eta=ETA0, nthreads=0):
+        ar, ai = np.ascontiguousarray(a.real), np.ascontiguousarray(a.imag)
+        br, bi = np.ascontiguousarray(b.real), np.ascontiguousarray(b.imag)
+        loss, dk = C.c_double(), C.c_double()
+        fp = FillParams(k, eta, rule, nphi, nl, 0)
+        rc = lib().or_loss_dk(self.h, C.byref(fp), _dp(ar), _dp(ai), _dp(br), _dp(bi), C.byref(loss),
+                              C.byref(dk), nthreads)
+        if rc != 0:
+            raise ValueError(rc)
+        return loss.value, dk.value
 
 
 def singular(r, v0, v1, v2, k, nphi=8, nl=8, texp=None):

@@ -525,6 +525,14 @@ int or_z_entries(const or_mesh* m, const or_fill_params* fp, const or_table* tgr
 // to the vertices it touches. Near / regular classification is held fixed.
 int or_loss_grad(const or_mesh* m, const or_fill_params* fp, const double* are, const double* aim,
                  const double* bre, const double* bim, double* loss, double* dxyz, double* dk, int nthreads) {
+  return or_loss_grad_masked(m, fp, are, aim, bre, bim, nullptr, loss, dxyz, dk, nthreads);
+}
+
+// tri_mask (may be NULL): only pairs with p or q marked are differentiated;
+// the gradient of a vertex whose triangles are all marked is then complete.
+int or_loss_grad_masked(const or_mesh* m, const or_fill_params* fp, const double* are, const double* aim,
+                        const double* bre, const double* bim, const int* tri_mask, double* loss, double* dxyz,
+                        double* dk, int nthreads) {
   typedef Dual<19> D;
   Quad Q;
   if (!m || !fp || !make_quad(fp->rule, fp->nphi, fp->nl, &Q)) return -1;
@@ -541,6 +549,7 @@ int or_loss_grad(const or_mesh* m, const or_fill_params* fp, const double* are, 
 #pragma omp for schedule(dynamic, 1)
     for (int p = 0; p < nt; ++p) {
       for (int q = 0; q < nt; ++q) {
+        if (tri_mask && !tri_mask[p] && !tri_mask[q]) continue;
         bool nr = is_near(m, p, q);
         V3<D> pv[3], qv[3];
         for (int c = 0; c < 3; ++c) {
@@ -583,6 +592,53 @@ int or_loss_grad(const or_mesh* m, const or_fill_params* fp, const double* are, 
     for (size_t i = 0; i < 3 * (size_t)m->nv; ++i) dxyz[i] += g[i];
     L += g[3 * (size_t)m->nv];
     gk += g[3 * (size_t)m->nv + 1];
+  }
+  *loss = L;
+  *dk = gk;
+  return 0;
+}
+
+// dL/dk alone (one dual direction), all pairs.
+int or_loss_dk(const or_mesh* m, const or_fill_params* fp, const double* are, const double* aim, const double* bre,
+               const double* bim, double* loss, double* dk, int nthreads) {
+  typedef Dual<1> D;
+  Quad Q;
+  if (!m || !fp || !make_quad(fp->rule, fp->nphi, fp->nl, &Q)) return -1;
+  int nt = m->nt;
+  int nth = nthreads_or_default(nthreads);
+  double L = 0, gk = 0;
+#pragma omp parallel for num_threads(nth) reduction(+ : L, gk) schedule(dynamic, 1)
+  for (int p = 0; p < nt; ++p) {
+    V3<D> pv[3];
+    for (int c = 0; c < 3; ++c) {
+      V3<double> x = vtx(m, m->tri[3 * p + c]);
+      pv[c] = V3<D>(D(x.x), D(x.y), D(x.z));
+    }
+    TriGeo<D> P = tri_geo(pv);
+    for (int q = 0; q < nt; ++q) {
+      bool nr = is_near(m, p, q);
+      V3<D> qv[3];
+      for (int c = 0; c < 3; ++c) {
+        V3<double> y = vtx(m, m->tri[3 * q + c]);
+        qv[c] = V3<D>(D(y.x), D(y.y), D(y.z));
+      }
+      D k = D::var(fp->k, 0);
+      TriGeo<D> Qg = tri_geo(qv);
+      Cx<D> acc;
+      for (int i = 0; i < 3; ++i) {
+        int em = m->tedge[3 * p + i];
+        if (em < 0) continue;
+        for (int j = 0; j < 3; ++j) {
+          int en = m->tedge[3 * q + j];
+          if (en < 0) continue;
+          Cx<D> c = pair_term<D>(P, i, m->tsign[3 * p + i], Qg, j, m->tsign[3 * q + j], nr, k, Q, nullptr, nullptr);
+          acc += Cx<D>(D(are[em]), D(-aim[em])) * c * Cx<D>(D(bre[en]), D(bim[en]));
+        }
+      }
+      D Lp = -(k * fp->eta) * acc.im;
+      L += Lp.v;
+      gk += Lp.d[0];
+    }
   }
   *loss = L;
   *dk = gk;

@@ -112,6 +112,16 @@ int or_loss_grad(const or_mesh* m, const or_fill_params* p, const double* are, c
                  const double* bre, const double* bim, double* loss, double* dxyz, double* dk,
                  int nthreads);
 
+/* As or_loss_grad, but only triangle pairs with p or q marked in tri_mask
+ * [nt] contribute (exact gradient for vertices whose triangles are all
+ * marked; dk and the loss partial). */
+int or_loss_grad_masked(const or_mesh* m, const or_fill_params* p, const double* are, const double* aim,
+                        const double* bre, const double* bim, const int* tri_mask, double* loss, double* dxyz,
+                        double* dk, int nthreads);
+/* L and dL/dk over all pairs (one dual direction). */
+int or_loss_dk(const or_mesh* m, const or_fill_params* p, const double* are, const double* aim, const double* bre,
+               const double* bim, double* loss, double* dk, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif

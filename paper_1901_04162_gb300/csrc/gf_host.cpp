@@ -269,7 +269,8 @@ gf_status check_device(int dev) {
 
 void free_mesh_device(gf_mesh* m) {
   void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_pts32,
-                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32};
+                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
+                  m->d_dtri,  m->d_dk};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -771,6 +772,43 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   }
   GF_CUDA(launch_fill_near(g, table ? &te : nullptr, precision, precision == GF_FP32 && !p->near_fp64, k, p->eta,
                            p->nphi, p->nl, glp, gll, Z, ldz, s));
+  return GF_OK;
+}
+
+gf_status gf_fill_backward(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision,
+                           const void* gZ, int64_t ldg, double* dxyz, double* dk, void* stream) {
+  if (!mc || !params_ok(p) || !gZ || !dxyz || !dk) return fail(GF_ERR_ARG, "gf_fill_backward: bad argument");
+  if (precision != GF_FP32) return fail(GF_ERR_ARG, "gf_fill_backward: GF_FP32 only");
+  if (!(k > 0) || ldg < mc->ne) return fail(GF_ERR_ARG, "gf_fill_backward: need k > 0 and ldg >= ne");
+  gf_mesh* m = const_cast<gf_mesh*>(mc);
+  gf_status st = check_device(m->device);
+  if (st) return st;
+  if (table && (table->device != m->device || table->k != k))
+    return fail(GF_ERR_ARG, "gf_fill_backward: table on another device or for another k");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_rule_impl(m, p->rule, s))) return st;
+  if (!m->d_dtri && ((st = dev_alloc(&m->d_dtri, 9 * (size_t)m->nt)) || (st = dev_alloc(&m->d_dk, 1)))) return st;
+  double bary[kMaxRule][3], w[kMaxRule];
+  rule_points(p->rule, bary, w);
+  double gx[32], gw[32], glp[64] = {0}, gll[64] = {0};
+  gauss_legendre(p->nphi, gx, gw);
+  for (int i = 0; i < p->nphi; ++i) {
+    glp[i] = gx[i];
+    glp[32 + i] = gw[i];
+  }
+  gauss_legendre(p->nl, gx, gw);
+  for (int i = 0; i < p->nl; ++i) {
+    gll[i] = gx[i];
+    gll[32 + i] = gw[i];
+  }
+  TabView tg, te;
+  if (table) {
+    tg = table->green.view();
+    te = table->exp.view();
+  }
+  GF_CUDA(launch_adjoint(geo_view_impl(m), table ? &tg : nullptr, table ? &te : nullptr, k, p->eta, &bary[0][0],
+                         p->nphi, p->nl, glp, gll, gZ, ldg, m->d_dtri, m->d_dk, dxyz, m->nv, s));
+  GF_CUDA(cudaMemcpyAsync(dk, m->d_dk, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return GF_OK;
 }
 

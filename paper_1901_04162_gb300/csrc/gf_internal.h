@@ -120,6 +120,10 @@ cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total,
                               bool mixed, int nphi, int nl, const double* gl_phi, const double* gl_l, int grid,
                               cudaStream_t s);
 int batch_regular_blocks_per_sm(int m, bool table, int block);
+cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView* texp, double k, double eta,
+                           const double* bary, int nphi, int nl, const double* gl_phi, const double* gl_l,
+                           const void* gZ, int64_t ldg, double* dtri, double* dk, double* dxyz, int64_t nv,
+                           cudaStream_t s);
 void gauss_legendre_host(int n, double* x, double* w);
 // host helpers shared by the single and batched fills (gf_host.cpp)
 gf_status prepare_rule(gf_mesh* m, int rule, cudaStream_t s);
@@ -157,6 +161,8 @@ struct gf_mesh {
   double* d_cen64 = nullptr;
   double* d_geo64 = nullptr;
   float* d_rad32 = nullptr;
+  double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
+  double* d_dk = nullptr;                   // adjoint scratch [1]
   unsigned long long* d_minmax = nullptr;  // range scratch [4]
 };
 

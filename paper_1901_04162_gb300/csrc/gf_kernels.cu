@@ -997,6 +997,472 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
   }
 }
 
+// ---------------------------------------------------------------- adjoint
+// Backward of L with respect to the vertex coordinates and k, given the
+// upstream gZ = dL/dconj(Z) (dL = Re sum conj(gZ) dZ). Per regular pair,
+//   S = sum_ij h_ij Bt_ij,  h_ij = j kappa s_i l_i s_j l_j conj(gZ_ij),
+// Bt_ij the bracket of the forward block, so S = sum_ab w_a w_b F(R_ab) K_ab
+// with K_ab = A0 + Aa . alpha_a + Ab . beta_b + Aab alpha_a . beta_b. Green
+// values F are recomputed from the table; F' = -(jk + 1/R) F, dF/dk = -jR F.
+// Gradients reach the vertices through the points (R and the offsets
+// alpha, beta), the edge vectors delta_i = c_p - v_i, eps_j = c_q - v_j, the
+// signed edge lengths and k. Classification, range and table samples are held
+// fixed. Triangle gradients accumulate in FP64 per triangle (9 values).
+struct BaryF {
+  float l[kMaxRule][3];
+};
+
+__device__ __forceinline__ float re_mul(float ar, float ai, float br, float bi) { return ar * br - ai * bi; }
+__device__ __forceinline__ float im_mul(float ar, float ai, float br, float bi) { return ar * bi + ai * br; }
+
+template <int M, bool TABLE>
+__device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const Tab32& T, float k, float kappa,
+                                                       float inv_k2, const BaryF& bw, const float2* __restrict__ gZ,
+                                                       int64_t ldg, double* dtri, double* dkacc, int p, int q0,
+                                                       int lane) {
+  const int q = min(q0 + lane, g.nt - 1);
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+  const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  if (!__any_sync(0xffffffffu, ok)) return;
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+  float4 gp[3], gq[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    gp[i] = g.geo32[3 * (size_t)p + i];
+    gq[i] = g.geo32[3 * (size_t)q + i];
+  }
+  // h_ij = j kappa sigma_i sigma_j conj(gZ_ij) = c (Im gZ + j Re gZ)
+  auto h_of = [&](int i, int j, float* hr, float* hi) {
+    *hr = *hi = 0.f;
+    if (ok && edge_valid(ecp[i]) && edge_valid(ecq[j])) {
+      const float2 z = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+      const float c = kappa * gp[i].w * gq[j].w;
+      *hr = c * z.y;
+      *hi = c * z.x;
+    }
+  };
+  float Aabr = 0.f, Aabi = 0.f, A0r = 0.f, A0i = 0.f, Aar[3] = {0.f, 0.f, 0.f}, Aai[3] = {0.f, 0.f, 0.f};
+  float Abr[3] = {0.f, 0.f, 0.f}, Abi[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float hr, hi;
+      h_of(i, j, &hr, &hi);
+      Aabr += 0.25f * hr;
+      Aabi += 0.25f * hi;
+      const float de = gp[i].x * gq[j].x + gp[i].y * gq[j].y + gp[i].z * gq[j].z;
+      A0r += hr * (0.25f * de - inv_k2);
+      A0i += hi * (0.25f * de - inv_k2);
+      const float ej[3] = {gq[j].x, gq[j].y, gq[j].z}, di[3] = {gp[i].x, gp[i].y, gp[i].z};
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        Aar[x] += 0.25f * hr * ej[x];
+        Aai[x] += 0.25f * hi * ej[x];
+        Abr[x] += 0.25f * hr * di[x];
+        Abi[x] += 0.25f * hi * di[x];
+      }
+    }
+  float4 beta[M];
+#pragma unroll
+  for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
+  float gqb[M][3], gB[M][3];
+#pragma unroll
+  for (int b = 0; b < M; ++b)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) gqb[b][x] = gB[b][x] = 0.f;
+  float dp[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float M0r = 0.f, M0i = 0.f, Mar[3] = {0.f, 0.f, 0.f}, Mai[3] = {0.f, 0.f, 0.f}, Mbr[3] = {0.f, 0.f, 0.f},
+        Mbi[3] = {0.f, 0.f, 0.f}, Mabr = 0.f, Mabi = 0.f, dkF = 0.f;
+#pragma unroll 1
+  for (int a = 0; a < M; ++a) {
+    const float4 al = g.pts32[(size_t)a * g.nt + p];
+    const float alv[3] = {al.x, al.y, al.z};
+    const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+    // K_ab = Ka + Kb . beta_b with Ka = A0 + Aa . alpha_a, Kb = Ab + Aab alpha_a
+    const float Kar = A0r + Aar[0] * al.x + Aar[1] * al.y + Aar[2] * al.z;
+    const float Kai = A0i + Aai[0] * al.x + Aai[1] * al.y + Aai[2] * al.z;
+    float Kbr[3], Kbi[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      Kbr[x] = Abr[x] + Aabr * alv[x];
+      Kbi[x] = Abi[x] + Aabi * alv[x];
+    }
+    float ga[3] = {0.f, 0.f, 0.f}, gA[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      const float R = R2 * rs;
+      float Fr, Fi;
+      if (TABLE) {
+        const float2 f = lookup32<3>(T, R);
+        Fr = f.x;
+        Fi = f.y;
+      } else {
+        float sn, cs;
+        sincospif(R * k * 0.318309886183790672f, &sn, &cs);
+        Fr = cs * rs;
+        Fi = -sn * rs;
+      }
+      const float ww = al.w * beta[b].w;
+      const float bv[3] = {beta[b].x, beta[b].y, beta[b].z};
+      const float Kr = Kar + Kbr[0] * bv[0] + Kbr[1] * bv[1] + Kbr[2] * bv[2];
+      const float Ki = Kai + Kbi[0] * bv[0] + Kbi[1] * bv[1] + Kbi[2] * bv[2];
+      // F' = -(jk + 1/R) F
+      const float Fpr = -Fr * rs + k * Fi, Fpi = -Fi * rs - k * Fr;
+      const float t1 = ww * re_mul(Kr, Ki, Fpr, Fpi) * rs;  // times r/R below
+      const float gR[3] = {t1 * rx, t1 * ry, t1 * rz};
+      const float wFr = ww * Fr, wFi = ww * Fi;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        ga[x] += gR[x];
+        gqb[b][x] -= gR[x];
+        gA[x] += re_mul(wFr, wFi, Aar[x] + Aabr * bv[x], Aai[x] + Aabi * bv[x]);
+        gB[b][x] += re_mul(wFr, wFi, Kbr[x], Kbi[x]);
+      }
+      dkF += R * im_mul(Kr, Ki, wFr, wFi);
+      const float ab = alv[0] * bv[0] + alv[1] * bv[1] + alv[2] * bv[2];
+      M0r += wFr;
+      M0i += wFi;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        Mar[x] += alv[x] * wFr;
+        Mai[x] += alv[x] * wFi;
+        Mbr[x] += bv[x] * wFr;
+        Mbi[x] += bv[x] * wFi;
+      }
+      Mabr += ab * wFr;
+      Mabi += ab * wFi;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float lc = bw.l[a][c];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dp[c][x] += lc * ga[x] + (lc - (1.f / 3.f)) * gA[x];
+    }
+  }
+  float dq[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int b = 0; b < M; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float lc = bw.l[b][c];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dq[c][x] += lc * gqb[b][x] + (lc - (1.f / 3.f)) * gB[b][x];
+    }
+  // through delta_i, eps_j, the signed lengths and k explicitly
+  float dd[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float de_[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  float dsp[3] = {0.f, 0.f, 0.f}, dsq[3] = {0.f, 0.f, 0.f}, dkx = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float hr, hi;
+      h_of(i, j, &hr, &hi);
+      if (hr == 0.f && hi == 0.f) continue;
+      const float di[3] = {gp[i].x, gp[i].y, gp[i].z}, ej[3] = {gq[j].x, gq[j].y, gq[j].z};
+      const float de = di[0] * ej[0] + di[1] * ej[1] + di[2] * ej[2];
+      const float eMar = ej[0] * Mar[0] + ej[1] * Mar[1] + ej[2] * Mar[2];
+      const float eMai = ej[0] * Mai[0] + ej[1] * Mai[1] + ej[2] * Mai[2];
+      const float dMbr = di[0] * Mbr[0] + di[1] * Mbr[1] + di[2] * Mbr[2];
+      const float dMbi = di[0] * Mbi[0] + di[1] * Mbi[1] + di[2] * Mbi[2];
+      const float Btr = 0.25f * (Mabr + eMar + dMbr + de * M0r) - M0r * inv_k2;
+      const float Bti = 0.25f * (Mabi + eMai + dMbi + de * M0i) - M0i * inv_k2;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        dd[i][x] += 0.25f * re_mul(hr, hi, Mbr[x] + ej[x] * M0r, Mbi[x] + ej[x] * M0i);
+        de_[j][x] += 0.25f * re_mul(hr, hi, Mar[x] + di[x] * M0r, Mai[x] + di[x] * M0i);
+      }
+      const float hB = re_mul(hr, hi, Btr, Bti);
+      dsp[i] += hB / gp[i].w;
+      dsq[j] += hB / gq[j].w;
+      dkx += hB / k + 2.f * inv_k2 / k * re_mul(hr, hi, M0r, M0i);
+    }
+  // delta_i = c - v_i; sigma_i = s_i |v_{i+1} - v_{i+2}|, v_{i+1} - v_{i+2} = delta_{i+2} - delta_{i+1}
+  auto edge_terms = [&](float dv[3][3], const float4 gv[3], const float dd_[3][3], const float ds[3]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dv[c][x] += (dd_[0][x] + dd_[1][x] + dd_[2][x]) * (1.f / 3.f) - dd_[c][x];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (gv[i].w == 0.f) continue;
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+      const float s = ds[i] / gv[i].w;
+      const float e[3] = {gv[i2].x - gv[i1].x, gv[i2].y - gv[i1].y, gv[i2].z - gv[i1].z};
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        dv[i1][x] += s * e[x];
+        dv[i2][x] -= s * e[x];
+      }
+    }
+  };
+  edge_terms(dp, gp, dd, dsp);
+  edge_terms(dq, gq, de_, dsq);
+  float dkl = ok ? dkF + dkx : 0.f;
+  if (!ok) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int x = 0; x < 3; ++x) dp[c][x] = dq[c][x] = 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      float v = dp[c][x];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) atomicAdd(&dtri[9 * (size_t)p + 3 * c + x], (double)v);
+      if (ok) atomicAdd(&dtri[9 * (size_t)q + 3 * c + x], (double)dq[c][x]);
+    }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) dkl += __shfl_xor_sync(0xffffffffu, dkl, off);
+  if (lane == 0) atomicAdd(dkacc, (double)dkl);
+}
+
+template <int M, bool TABLE>
+__global__ void __launch_bounds__(256) k_adjoint_regular32(GeoView g, TabView tv, float k, float kappa, float inv_k2,
+                                                           BaryF bw, const float2* __restrict__ gZ, int64_t ldg,
+                                                           double* dtri, double* dkacc) {
+  const Tab32 T = tab32(tv);
+  const int lane = threadIdx.x & 31;
+  const int64_t nchunk = (g.nt + 31) / 32;
+  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp)
+    regular_adjoint_task32<M, TABLE>(g, T, k, kappa, inv_k2, bw, gZ, ldg, dtri, dkacc, (int)(task / nchunk),
+                                     (int)(task % nchunk) * 32, lane);
+}
+
+// ---- near pairs: forward-mode dual numbers (one direction per thread group)
+struct D1 {
+  double v, d;
+};
+__device__ __forceinline__ D1 operator+(D1 a, D1 b) { return D1{a.v + b.v, a.d + b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, D1 b) { return D1{a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ D1 operator-(D1 a) { return D1{-a.v, -a.d}; }
+__device__ __forceinline__ D1 operator*(D1 a, D1 b) { return D1{a.v * b.v, a.d * b.v + a.v * b.d}; }
+__device__ __forceinline__ D1 operator/(D1 a, D1 b) {
+  const double iv = 1.0 / b.v;
+  return D1{a.v * iv, (a.d - a.v * iv * b.d) * iv};
+}
+__device__ __forceinline__ D1 operator*(D1 a, double s) { return D1{a.v * s, a.d * s}; }
+__device__ __forceinline__ D1 operator*(double s, D1 a) { return D1{a.v * s, a.d * s}; }
+__device__ __forceinline__ D1 operator+(D1 a, double s) { return D1{a.v + s, a.d}; }
+__device__ __forceinline__ D1 operator-(D1 a, double s) { return D1{a.v - s, a.d}; }
+__device__ __forceinline__ D1 dsqrt(D1 a) {
+  const double r = sqrt(a.v);
+  return D1{r, a.d / (2.0 * r)};
+}
+__device__ __forceinline__ D1 dlog(D1 a) { return D1{log(a.v), a.d / a.v}; }
+__device__ __forceinline__ D1 dasinh(D1 a) { return D1{asinh(a.v), a.d / sqrt(1.0 + a.v * a.v)}; }
+__device__ __forceinline__ D1 dcosh(D1 a) { return D1{cosh(a.v), sinh(a.v) * a.d}; }
+__device__ __forceinline__ D1 dabs(D1 a) { return a.v < 0 ? -a : a; }
+
+struct DC {  // complex over D1
+  D1 re, im;
+};
+__device__ __forceinline__ DC operator+(DC a, DC b) { return DC{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ DC operator-(DC a, DC b) { return DC{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ DC operator*(DC a, D1 s) { return DC{a.re * s, a.im * s}; }
+
+// e^{-jkR} with its derivative: from the Exp table when R is in range (the
+// derivative then uses -j e^{-jkR} d(kR) with the table value), else direct.
+__device__ __forceinline__ DC exp_mjkr_d(D1 k, D1 R, const TabView* te, bool use_table) {
+  const D1 ph = k * R;
+  double c, s;
+  if (use_table && R.v >= te->r_lo && R.v <= te->r_hi) {
+    const double2 f = lookup64<1>(*te, R.v);
+    c = f.x;
+    s = -f.y;
+  } else {
+    sincos(ph.v, &s, &c);
+  }
+  // d/dph (c - j s) = -s - j c
+  return DC{D1{c, -s * ph.d}, D1{-s, -c * ph.d}};
+}
+
+struct V3D {
+  D1 x, y, z;
+};
+__device__ __forceinline__ V3D vsub(V3D a, V3D b) { return V3D{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D1 vdot(V3D a, V3D b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3D vcross(V3D a, V3D b) {
+  return V3D{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3D vscale(V3D a, D1 s) { return V3D{a.x * s, a.y * s, a.z * s}; }
+
+// The near-pair inner integrals of inner_integrals() in dual numbers.
+__device__ void inner_integrals_d(const V3D& r, const V3D v[3], const NearArgs& A, D1 k, const TabView* te,
+                                  bool use_table, DC* I0, DC I1[3], V3D* rho0_out) {
+  V3D n = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
+  const D1 inv = D1{1.0, 0.0} / dsqrt(vdot(n, n));
+  n = vscale(n, inv);
+  const D1 h = vdot(n, vsub(r, v[0]));
+  const D1 d = dabs(h);
+  const V3D rho0 = vsub(r, vscale(n, h));
+  *rho0_out = rho0;
+  const DC ed = exp_mjkr_d(k, d, te, use_table);
+  DC sacc{D1{0, 0}, D1{0, 0}};
+  DC vacc[3] = {{D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}};
+  D1 vst[3] = {D1{0, 0}, D1{0, 0}, D1{0, 0}};
+  for (int e = 0; e < 3; ++e) {
+    const V3D a = v[e], b = v[(e + 1) % 3];
+    V3D t = vsub(b, a);
+    const D1 len = dsqrt(vdot(t, t));
+    t = vscale(t, D1{1.0, 0.0} / len);
+    const V3D mh = vcross(t, n);
+    const V3D ar = vsub(a, rho0), br = vsub(b, rho0);
+    const D1 P0 = vdot(ar, mh), lm = vdot(ar, t), lp = vdot(br, t);
+    if (fabs(P0.v) > 1e-12 * len.v) {
+      const D1 aP = dabs(P0);
+      const D1 um = dasinh(lm / aP), up = dasinh(lp / aP);
+      const D1 half = (up - um) * 0.5, mid = (up + um) * 0.5;
+      DC sec{D1{0, 0}, D1{0, 0}};
+      for (int i = 0; i < A.nphi; ++i) {
+        const D1 u = mid + half * A.gx_phi[i];
+        const D1 ch = dcosh(u);
+        const D1 rho = aP * ch;
+        const D1 Re = dsqrt(rho * rho + d * d);
+        const DC eR = exp_mjkr_d(k, Re, te, use_table);
+        sec = sec + (ed - eR) * (D1{A.gw_phi[i], 0.0} / ch);
+      }
+      sec = sec * (P0.v > 0 ? half : -half);
+      sacc = sacc + sec;
+    }
+    DC li{D1{0, 0}, D1{0, 0}};
+    for (int i = 0; i < A.nl; ++i) {
+      const D1 sp = len * (0.5 * (A.gx_l[i] + 1.0));
+      const V3D x = vsub(V3D{a.x + t.x * sp, a.y + t.y * sp, a.z + t.z * sp}, r);
+      const D1 R = dsqrt(vdot(x, x));
+      const DC eR = exp_mjkr_d(k, R, te, use_table);
+      li = li + DC{eR.re - 1.0, eR.im + k * R} * D1{A.gw_l[i], 0.0};
+    }
+    li = li * (len * 0.5);
+    const D1 R02 = P0 * P0 + d * d;
+    const D1 Rm = dsqrt(lm * lm + R02), Rp = dsqrt(lp * lp + R02);
+    D1 st = (lp * Rp - lm * Rm) * 0.5;
+    if (R02.v > 0) {
+      const D1 fp = lp.v >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const D1 fm = lm.v >= 0 ? lm + Rm : R02 / (Rm - lm);
+      st = st + R02 * (dlog(fp) - dlog(fm)) * 0.5;
+    }
+    const D1 mhv[3] = {mh.x, mh.y, mh.z};
+    for (int x = 0; x < 3; ++x) {
+      vacc[x] = vacc[x] + li * mhv[x];
+      vst[x] = vst[x] + mhv[x] * st;
+    }
+  }
+  const double c4 = 1.0 / (4.0 * kPi);
+  const D1 ik = D1{1.0, 0.0} / k;
+  // I0 = (-j/k) s / (4 pi); I1 = ((j/k) v + v_static) / (4 pi)
+  I0->re = sacc.im * ik * c4;
+  I0->im = -(sacc.re * ik) * c4;
+  for (int x = 0; x < 3; ++x) {
+    I1[x].re = (vst[x] - vacc[x].im * ik) * c4;
+    I1[x].im = vacc[x].re * ik * c4;
+  }
+}
+
+// One (near pair, direction) on 8 lanes, one test point per lane. Direction
+// 0..8: p's vertex coordinates, 9..17: q's, 18: k. The derivative of the
+// pair's share of L is reduced over the points and added to dtri / dk.
+__global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, bool use_table, NearArgs A, double k,
+                                                      double eta, BaryF bw, const float2* __restrict__ gZ, int64_t ldg,
+                                                      double* dtri, double* dkacc) {
+  const int64_t n_near = g.near_ptr[g.nt];
+  const int64_t njobs = n_near * 19;
+  const int sub = threadIdx.x & 7;
+  const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t job = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; job < njobs; job += ngroups) {
+    const int64_t idx = job / 19;
+    const int dir = (int)(job % 19);
+    int lo = 0, hi = g.nt - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (g.near_ptr[mid] <= idx) lo = mid;
+      else hi = mid - 1;
+    }
+    const int p = lo, q = g.near_idx[idx];
+    double dL = 0.0;
+    if (sub < g.m) {
+      V3D vp[3], vq[3];
+      for (int c = 0; c < 3; ++c) {
+        const double* xp = g.v64 + 9 * (size_t)p + 3 * c;
+        const double* xq = g.v64 + 9 * (size_t)q + 3 * c;
+        vp[c] = V3D{D1{xp[0], dir == 3 * c ? 1.0 : 0.0}, D1{xp[1], dir == 3 * c + 1 ? 1.0 : 0.0},
+                    D1{xp[2], dir == 3 * c + 2 ? 1.0 : 0.0}};
+        vq[c] = V3D{D1{xq[0], dir == 9 + 3 * c ? 1.0 : 0.0}, D1{xq[1], dir == 10 + 3 * c ? 1.0 : 0.0},
+                    D1{xq[2], dir == 11 + 3 * c ? 1.0 : 0.0}};
+      }
+      const D1 kd{k, dir == 18 ? 1.0 : 0.0};
+      // test point r_a = sum_c l_ac v_c, weight w_a
+      const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
+      const double wa = al[3];
+      V3D ra{D1{0, 0}, D1{0, 0}, D1{0, 0}};
+      for (int c = 0; c < 3; ++c) {
+        const double l = (double)bw.l[sub][c];
+        ra = V3D{ra.x + vp[c].x * l, ra.y + vp[c].y * l, ra.z + vp[c].z * l};
+      }
+      DC I0, I1[3];
+      V3D rho0;
+      inner_integrals_d(ra, vq, A, kd, &te, use_table, &I0, I1, &rho0);
+      const V3D nq = vcross(vsub(vq[1], vq[0]), vsub(vq[2], vq[0]));
+      const D1 area_q = dsqrt(vdot(nq, nq)) * 0.5;
+      const int4 ep = g.tedge[p], eq = g.tedge[q];
+      const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+      const D1 inv_k2 = D1{1.0, 0.0} / (kd * kd);
+      for (int i = 0; i < 3; ++i) {
+        if (!edge_valid(ecp[i])) continue;
+        const V3D e_i = vsub(vp[(i + 2) % 3], vp[(i + 1) % 3]);
+        const D1 sl_i = dsqrt(vdot(e_i, e_i)) * ((ecp[i] & 1) ? -1.0 : 1.0);
+        const V3D f = vsub(ra, vp[i]);
+        for (int j = 0; j < 3; ++j) {
+          if (!edge_valid(ecq[j])) continue;
+          const V3D e_j = vsub(vq[(j + 2) % 3], vq[(j + 1) % 3]);
+          const D1 sl_j = dsqrt(vdot(e_j, e_j)) * ((ecq[j] & 1) ? -1.0 : 1.0);
+          const V3D dv = vsub(rho0, vq[j]);
+          // J = I1 + (rho0 - v_j) I0;  term = w_a (f . J / 4 - I0 / k^2)
+          const DC J[3] = {DC{I1[0].re + dv.x * I0.re, I1[0].im + dv.x * I0.im},
+                           DC{I1[1].re + dv.y * I0.re, I1[1].im + dv.y * I0.im},
+                           DC{I1[2].re + dv.z * I0.re, I1[2].im + dv.z * I0.im}};
+          const D1 tr = (f.x * J[0].re + f.y * J[1].re + f.z * J[2].re) * 0.25 - I0.re * inv_k2;
+          const D1 ti = (f.x * J[0].im + f.y * J[1].im + f.z * J[2].im) * 0.25 - I0.im * inv_k2;
+          // Z share = j k eta sl_i sl_j / A_q * w_a * (tr + j ti) = c (-ti + j tr)
+          const D1 c = kd * (eta * wa) * sl_i * sl_j / area_q;
+          const D1 zr = -(c * ti), zi = c * tr;
+          const float2 gz = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+          // dL = Re(conj(gZ) dZ) = gz.x dZr + gz.y dZi
+          dL += (double)gz.x * zr.d + (double)gz.y * zi.d;
+        }
+      }
+    }
+    for (int off = 1; off < 8; off <<= 1) dL += __shfl_xor_sync(gmask, dL, off);
+    if (sub == 0) {
+      if (dir == 18) atomicAdd(dkacc, dL);
+      else if (dir < 9) atomicAdd(&dtri[9 * (size_t)p + dir], dL);
+      else atomicAdd(&dtri[9 * (size_t)q + dir - 9], dL);
+    }
+  }
+}
+
+// dxyz[v] += sum over the corners of triangles at v (triangles in internal order)
+__global__ void k_adjoint_gather(int nt, const int4* __restrict__ tvert, const double* __restrict__ dtri, double* dxyz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const int4 v = tvert[t];
+  const int vs[3] = {v.x, v.y, v.z};
+  for (int c = 0; c < 3; ++c)
+    for (int x = 0; x < 3; ++x) atomicAdd(&dxyz[3 * (size_t)vs[c] + x], dtri[9 * (size_t)t + 3 * c + x]);
+}
+
 // ---------------------------------------------------------------- batched
 // Persistent kernels over the regular tasks and near pairs of many meshes:
 // warps pull chunks of a global task list (meshes with the most work first)
@@ -1134,6 +1600,66 @@ cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total,
   }
   if (mixed) k_batch_near<true><<<grid, 128, 0, s>>>(items, nitems, total, counter, A);
   else k_batch_near<false><<<grid, 128, 0, s>>>(items, nitems, total, counter, A);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_adjoint_regular_m(const GeoView& g, const TabView* green, double k, double eta, const BaryF& bw,
+                                     const float2* gZ, int64_t ldg, double* dtri, double* dk, cudaStream_t s) {
+  TabView tv{};
+  if (green) tv = *green;
+  const int64_t blocks = pair_grid(g, 4);
+  const float kappa = (float)(k * eta / (4.0 * kPi)), inv_k2 = (float)(1.0 / (k * k));
+  if (green)
+    k_adjoint_regular32<M, true><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ, ldg,
+                                                                       dtri, dk);
+  else
+    k_adjoint_regular32<M, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ, ldg,
+                                                                        dtri, dk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView* texp, double k, double eta,
+                           const double* bary, int nphi, int nl, const double* gl_phi, const double* gl_l,
+                           const void* gZ, int64_t ldg, double* dtri, double* dk, double* dxyz, int64_t nv,
+                           cudaStream_t s) {
+  BaryF bw;
+  for (int a = 0; a < kMaxRule; ++a)
+    for (int c = 0; c < 3; ++c) bw.l[a][c] = a < g.m ? (float)bary[3 * a + c] : 0.f;
+  cudaError_t e = cudaMemsetAsync(dtri, 0, 9 * sizeof(double) * (size_t)g.nt, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dk, 0, sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dxyz, 0, 3 * sizeof(double) * (size_t)nv, s);
+  if (e != cudaSuccess) return e;
+  const float2* gz = (const float2*)gZ;
+  switch (g.m) {
+    case 1: e = launch_adjoint_regular_m<1>(g, green, k, eta, bw, gz, ldg, dtri, dk, s); break;
+    case 3: e = launch_adjoint_regular_m<3>(g, green, k, eta, bw, gz, ldg, dtri, dk, s); break;
+    case 4: e = launch_adjoint_regular_m<4>(g, green, k, eta, bw, gz, ldg, dtri, dk, s); break;
+    case 6: e = launch_adjoint_regular_m<6>(g, green, k, eta, bw, gz, ldg, dtri, dk, s); break;
+    case 7: e = launch_adjoint_regular_m<7>(g, green, k, eta, bw, gz, ldg, dtri, dk, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  NearArgs A;
+  A.k = k;
+  A.scale = k * eta;
+  A.inv_k2 = 1.0 / (k * k);
+  A.nphi = nphi;
+  A.nl = nl;
+  for (int i = 0; i < 32; ++i) {
+    A.gx_phi[i] = gl_phi[i];
+    A.gw_phi[i] = gl_phi[32 + i];
+    A.gx_l[i] = gl_l[i];
+    A.gw_l[i] = gl_l[32 + i];
+    A.fx_phi[i] = (float)A.gx_phi[i];
+    A.fw_phi[i] = (float)A.gw_phi[i];
+    A.fx_l[i] = (float)A.gx_l[i];
+    A.fw_l[i] = (float)A.gw_l[i];
+  }
+  TabView te{};
+  if (texp) te = *texp;
+  k_adjoint_near<<<(unsigned)(sm_count() * 16), 128, 0, s>>>(g, te, texp != nullptr, A, k, eta, bw, gz, ldg, dtri, dk);
+  k_adjoint_gather<<<(g.nt + 127) / 128, 128, 0, s>>>(g.nt, g.tvert, dtri, dxyz);
   return cudaGetLastError();
 }
 

@@ -25,7 +25,7 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
-           "gf_batch_config", "gf_batch_destroy"]
+           "gf_batch_config", "gf_batch_destroy", "gf_fill_backward"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -81,6 +81,7 @@ def lib():
         L.gf_batch_launch.argtypes = [vp, vp]
         L.gf_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         L.gf_batch_destroy.argtypes = [vp]
+        L.gf_fill_backward.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
                 getattr(L, name).restype = C.c_int
@@ -355,3 +356,53 @@ class Batch:
         if h:
             lib().gf_batch_destroy(h)
             self.h = None
+
+
+def gf_fill_backward(mesh, k, params, table, gZ, stream=None):
+    """gZ: CUDA complex64 [ne, ldg] (dL = Re sum conj(gZ) dZ). Returns
+    (dxyz float64 [nv, 3], dk float64 [1]) CUDA tensors."""
+    import torch
+    _check_z(gZ, GF_FP32)
+    dxyz = torch.empty((mesh.nv, 3), dtype=torch.float64, device=gZ.device)
+    dk = torch.empty(1, dtype=torch.float64, device=gZ.device)
+    _check(lib().gf_fill_backward(mesh.h, float(k), C.byref(params), table.h if table is not None else None,
+                                  GF_FP32, C.c_void_p(gZ.data_ptr()), gZ.shape[-1], C.c_void_p(dxyz.data_ptr()),
+                                  C.c_void_p(dk.data_ptr()), _stream_ptr(stream)))
+    return dxyz, dk
+
+
+def _efie_function():
+    import torch
+
+    class EFIEFill(torch.autograd.Function):
+        """Z = fill(vertices, k) with a hand-written backward (gf_fill_backward)."""
+
+        @staticmethod
+        def forward(ctx, xyz, k, mesh, table, params):
+            mesh.set_vertices(xyz.detach().to("cpu", torch.float64).numpy())
+            kv = float(k)
+            Z = fill(mesh, kv, params, table, GF_FP32, device=xyz.device if xyz.is_cuda else None)
+            ctx.mesh, ctx.table, ctx.params, ctx.k = mesh, table, params, kv
+            ctx.xyz_dtype, ctx.k_tensor = xyz.dtype, torch.is_tensor(k)
+            return Z
+
+        @staticmethod
+        def backward(ctx, gZ):
+            dxyz, dk = gf_fill_backward(ctx.mesh, ctx.k, ctx.params, ctx.table, gZ.contiguous())
+            gk = dk.reshape(()).to(torch.float64) if ctx.k_tensor else None
+            return dxyz.to(ctx.xyz_dtype), gk, None, None, None
+
+    return EFIEFill
+
+
+_EFIE = None
+
+
+def efie_fill(xyz, k, mesh, table=None, params=None):
+    """Differentiable fill: xyz a (CUDA) float tensor [nv, 3] with the mesh's
+    topology, k a float or a 0-d tensor; returns complex64 Z on the GPU. The
+    table (if any) and the near-pair lists stay those of the first fill."""
+    global _EFIE
+    if _EFIE is None:
+        _EFIE = _efie_function()
+    return _EFIE.apply(xyz, k, mesh, table, params or gf_params_default())
