@@ -457,13 +457,85 @@ def run_batch(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, rank, world, local_rank):
+    """Backward of L = Re(a^H Z b) on the 2048-triangle sphere (6-point rule):
+    dL/d(vertex coordinates) and dL/dk from gZ = a conj(b)^T."""
+    import torch
+
+    import paper_1901_04162_gb300 as gf
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    wl = W.sphere_3072()
+    rule = wl.rule
+    p = gf.gf_params_default(rule=rule)
+    m = gf.Mesh(wl.xyz, wl.tri)
+    lo, hi = m.range(rule, gf.GF_FP32)
+    tab = gf.Table(wl.k, lo, hi, p)
+    a = W.complex_gaussian(m.ne, 7)
+    b = W.complex_gaussian(m.ne, 8)
+    gZ = torch.from_numpy(np.outer(a, np.conj(b)).astype(np.complex64)).to(dev)
+    Z = torch.empty((m.ne, m.ne), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / args.steps
+
+    with Clocks(local_rank) as clk:
+        bwd_ms = timed(lambda: gf.gf_fill_backward(m, wl.k, p, tab, gZ))
+    fwd_ms = timed(lambda: gf.gf_fill(m.h, wl.k, p, tab.h, gf.GF_FP32, Z))
+    bwd_direct_ms = timed(lambda: gf.gf_fill_backward(m, wl.k, p, None, gZ))
+    n_regular = m.nt * m.nt - m.n_near
+    line = {
+        "metric": "Z entries/s (adjoint fill)", "value": m.ne * m.ne / (bwd_ms / 1e3), "unit": "Z entries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": bwd_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "triangles": m.nt, "rwg_unknowns": m.ne, "rule_points": rule,
+                   "loss": "Re(a^H Z b), a, b seeded complex Gaussian", "regular_pairs": n_regular,
+                   "near_pairs": m.n_near, "parallelism": f"replicas x{world}"},
+        "gradient_evals_per_s": 1.0 / (bwd_ms / 1e3),
+        "forward_fill_ms": fwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
+        "direct_backward_ms": bwd_direct_ms,
+        "clocks": clk.summary(),
+        "e2e": {"value": None, "reason": "adjoint workload: device-resident gZ"},
+        "gpu_launches": 3 * args.steps,
+    }
+    if not args.skip_oracle:
+        import oracle as O
+        dxyz, dk = gf.gf_fill_backward(m, wl.k, p, tab, gZ)
+        g = dxyz.cpu().numpy()
+        om = O.Mesh(wl.xyz, wl.tri)
+        verts = [0, 517, 1000]
+        mask = np.isin(np.arange(len(wl.tri)), np.where(np.isin(wl.tri, verts).any(axis=1))[0]).astype(np.int32)
+        _, g_ref, _ = om.loss_grad(wl.k, rule, a, b, tri_mask=mask)
+        _, dk_ref = om.loss_dk(wl.k, rule, a, b)
+        line["accuracy"] = {
+            "sampled_vertices": verts,
+            "max_abs_err_over_max_abs_ref": float(np.abs(g[verts] - g_ref[verts]).max() / np.abs(g_ref[verts]).max()),
+            "dk_rel_err": abs(float(dk.cpu()[0]) - dk_ref) / abs(dk_ref), "reference": "oracle FP64 direct, dual numbers",
+            "tolerance": 1e-4}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere_7680", choices=sorted(WORKLOADS) + ["ellipsoid_batch"])
+    ap.add_argument("--workload", default="sphere_7680",
+                    choices=sorted(WORKLOADS) + ["ellipsoid_batch", "adjoint_3072"])
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
@@ -472,6 +544,12 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "adjoint_3072":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "reference arm runs the single-mesh workloads"}))
+            return
+        run_adjoint(args, rank, world, local_rank)
+        return
     if args.workload == "ellipsoid_batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "reference arm runs the single-mesh workloads"}))

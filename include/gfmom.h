@@ -177,8 +177,9 @@ gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf
  * (PyTorch's for a real loss). Writes dxyz (device float64 [nv][3], original
  * vertex ids) = dL/d(vertex coordinates) and *dk (device float64) = dL/dk.
  * Regular pairs: FP32 reverse mode with the Green values recomputed from
- * `table` (direct if NULL), F' = -(jk + 1/R) F, dF/dk = -jR F. Near pairs: FP64
- * forward mode (one dual direction per coordinate of the pair and k). The
+ * `table` (direct if NULL), F' = -(jk + 1/R) F, dF/dk = -jR F. Near pairs:
+ * forward mode (one dual direction per coordinate of the pair and k) with FP64
+ * geometry and FP32 edge sampling, or FP64 throughout if p->near_fp64. The
  * near / regular classification, the table range and its samples are held
  * fixed. precision must be GF_FP32. Asynchronous on `stream`; uses per-mesh
  * scratch, so backward calls on one mesh must not overlap. */

@@ -806,7 +806,8 @@ gf_status gf_fill_backward(const gf_mesh* mc, double k, const gf_params* p, cons
     tg = table->green.view();
     te = table->exp.view();
   }
-  GF_CUDA(launch_adjoint(geo_view_impl(m), table ? &tg : nullptr, table ? &te : nullptr, k, p->eta, &bary[0][0],
+  GF_CUDA(launch_adjoint(geo_view_impl(m), table ? &tg : nullptr, table ? &te : nullptr, !p->near_fp64, k, p->eta,
+                         &bary[0][0],
                          p->nphi, p->nl, glp, gll, gZ, ldg, m->d_dtri, m->d_dk, dxyz, m->nv, s));
   GF_CUDA(cudaMemcpyAsync(dk, m->d_dk, sizeof(double), cudaMemcpyDeviceToDevice, s));
   return GF_OK;

@@ -120,7 +120,7 @@ cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total,
                               bool mixed, int nphi, int nl, const double* gl_phi, const double* gl_l, int grid,
                               cudaStream_t s);
 int batch_regular_blocks_per_sm(int m, bool table, int block);
-cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView* texp, double k, double eta,
+cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView* texp, bool mixed, double k, double eta,
                            const double* bary, int nphi, int nl, const double* gl_phi, const double* gl_l,
                            const void* gZ, int64_t ldg, double* dtri, double* dk, double* dxyz, int64_t nv,
                            cudaStream_t s);

@@ -15,9 +15,9 @@ pytestmark = pytest.mark.gpu
 K = 2 * math.pi
 
 
-def gpu_grad(xyz, tri, rule, a, b, table=True):
+def gpu_grad(xyz, tri, rule, a, b, table=True, near_fp64=0):
     m = gf.Mesh(xyz, tri)
-    p = gf.gf_params_default(rule=rule)
+    p = gf.gf_params_default(rule=rule, near_fp64=near_fp64)
     tab = None
     if table:
         lo, hi = m.range(rule, gf.GF_FP32)
@@ -29,14 +29,15 @@ def gpu_grad(xyz, tri, rule, a, b, table=True):
 
 
 @pytest.mark.parametrize("table", [True, False])
-def test_small_sphere_vs_oracle_gradient(table):
+@pytest.mark.parametrize("near_fp64", [0, 1])
+def test_small_sphere_vs_oracle_gradient(table, near_fp64):
     xyz, tri = W.octasphere(2, 0.8)
     xyz = W.jitter(xyz, tri, 0.03, 8)
     om = O.Mesh(xyz, tri)
     a = W.complex_gaussian(om.ne, 1)
     b = W.complex_gaussian(om.ne, 2)
     _, g_ref, dk_ref = om.loss_grad(K, 6, a, b)
-    g, dk = gpu_grad(xyz, tri, 6, a, b, table)
+    g, dk = gpu_grad(xyz, tri, 6, a, b, table, near_fp64)
     assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
     assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
 
