@@ -56,6 +56,7 @@ WORKLOADS = {
     "plate_280": W.plate_280,
     "sphere_3072": W.sphere_3072,
     "cube_73728": W.cube_73728,
+    "cube_18432": lambda: W.cube_73728(32),
 }
 
 

@@ -268,9 +268,9 @@ gf_status check_device(int dev) {
 }
 
 void free_mesh_device(gf_mesh* m) {
-  void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_pts32,
+  void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_near_row, m->d_pts32,
                   m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
-                  m->d_dtri,  m->d_dk};
+                  m->d_dtri,  m->d_dk, m->d_bsph};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -298,6 +298,8 @@ gf_status upload_vertices(gf_mesh* m) {
 }
 
 // Builds (or reuses) the per-rule geometry on the device.
+GeoView geo_view_impl(const gf_mesh* m);
+
 gf_status prepare_rule_impl(gf_mesh* m, int rule, cudaStream_t s) {
   if (m->rule == rule) return GF_OK;
   double bary[kMaxRule][3], w[kMaxRule];
@@ -315,9 +317,16 @@ gf_status prepare_rule_impl(gf_mesh* m, int rule, cudaStream_t s) {
     e = launch_prep_geometry(m->d_v64, (int)m->nt, rule, d_bw, d_bw + 3 * kMaxRule, m->d_tedge, m->d_elen,
                              m->d_pts32, m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64, m->d_rad32,
                              s);
+  if (e == cudaSuccess) {
+    m->rule = rule;  // views below read the new geometry
+    e = launch_block_spheres(geo_view_impl(m), m->d_bsph, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_bw);
-  if (e != cudaSuccess) return cuda_fail(e, "prepare geometry");
+  if (e != cudaSuccess) {
+    m->rule = 0;
+    return cuda_fail(e, "prepare geometry");
+  }
   m->rule = rule;
   return GF_OK;
 }
@@ -337,8 +346,10 @@ GeoView geo_view_impl(const gf_mesh* m) {
   g.tedge = m->d_tedge;
   g.near_ptr = m->d_near_ptr;
   g.near_idx = m->d_near_idx;
+  g.near_row = m->d_near_row;
   g.near_dist32 = (float)m->near_dist;
   g.rad32 = m->d_rad32;
+  g.bsph = m->d_bsph;
   return g;
 }
 
@@ -514,11 +525,11 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   gf_status st;
   if ((st = dev_alloc(&m->d_v64, 9 * nt)) || (st = dev_alloc(&m->d_tvert, nt)) || (st = dev_alloc(&m->d_tedge, nt)) ||
       (st = dev_alloc(&m->d_elen, m->ne)) || (st = dev_alloc(&m->d_near_ptr, nt + 1)) ||
-      (st = dev_alloc(&m->d_near_idx, m->near_idx.size())) || (st = dev_alloc(&m->d_pts32, kMaxRule * nt)) ||
+      (st = dev_alloc(&m->d_near_idx, m->near_idx.size())) || (st = dev_alloc(&m->d_near_row, m->near_idx.size())) || (st = dev_alloc(&m->d_pts32, kMaxRule * nt)) ||
       (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
       (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
       (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_minmax, 4)) ||
-      (st = dev_alloc(&m->d_rad32, nt))) {
+      (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32))) {
     free_mesh_device(m.get());
     return st;
   }
@@ -531,8 +542,13 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   cudaError_t e = cudaMemcpy(m->d_tvert, tv.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->d_tedge, te.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m->d_near_ptr, m->near_ptr.data(), (nt + 1) * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !m->near_idx.empty())
+  if (e == cudaSuccess && !m->near_idx.empty()) {
     e = cudaMemcpy(m->d_near_idx, m->near_idx.data(), m->near_idx.size() * 4, cudaMemcpyHostToDevice);
+    std::vector<int32_t> rows(m->near_idx.size());
+    for (int64_t pi = 0; pi < nt; ++pi)
+      for (int64_t j = m->near_ptr[pi]; j < m->near_ptr[pi + 1]; ++j) rows[j] = (int32_t)pi;
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_near_row, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     free_mesh_device(m.get());
     return cuda_fail(e, "gf_mesh_create upload");

@@ -46,8 +46,10 @@ struct GeoView {
   const int4* tedge;     // [nt]: RWG edge id of local edge i, or -1
   const int64_t* near_ptr;  // [nt + 1]
   const int32_t* near_idx;  // sorted per row
+  const int32_t* near_row;  // row (test triangle) of every near_idx entry
   float near_dist32;        // > 0: centroid criterion present (FP32 screen)
   const float* rad32;       // [nt]: largest |point - centroid| of the rule, rounded up
+  const float4* bsph;       // [ceil(nt/32)]: bounding sphere of each block of 32 triangles (with points)
 };
 
 // FP64 cell record: every x in the cell lies in interval j0 if x < split,
@@ -105,6 +107,7 @@ cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, cons
                                int32_t* hash, int n_cells32, float lo32c, float inv32c, float4* cells32,
                                int n_cells64, double lo64c, double inv64c, Cell64* cells64, int* flag,
                                cudaStream_t s);
+cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s);
@@ -152,6 +155,7 @@ struct gf_mesh {
   double* d_elen = nullptr;
   int64_t* d_near_ptr = nullptr;
   int32_t* d_near_idx = nullptr;
+  int32_t* d_near_row = nullptr;
   // per-rule geometry cache
   int rule = 0;
   float4* d_pts32 = nullptr;
@@ -161,6 +165,7 @@ struct gf_mesh {
   double* d_cen64 = nullptr;
   double* d_geo64 = nullptr;
   float* d_rad32 = nullptr;
+  float4* d_bsph = nullptr;
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
   double* d_dk = nullptr;                   // adjoint scratch [1]
   unsigned long long* d_minmax = nullptr;  // range scratch [4]

@@ -178,16 +178,16 @@ __global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, do
 }
 
 // ---------------------------------------------------------------- lookups
-struct Tab32 {  // FP32 view (shared or global memory)
-  const float4* cells;
-  const float4* ca;
+struct Tab32 {  // FP32 view (shared or global memory; possibly a window)
+  const float4* cells;  // indexed by the global cell number
+  const float4* ca;     // indexed by the global interval number
   const float4* cb;
-  int n_cells;
+  int c_min, c_max;     // cells present (the whole table, or a window)
   float lo, inv;
 };
 
 __device__ __forceinline__ Tab32 tab32(const TabView& t) {
-  return Tab32{t.cells32, t.c32a, t.c32b, t.n_cells32, t.lo32c, t.inv32c};
+  return Tab32{t.cells32, t.c32a, t.c32b, 0, t.n_cells32 - 1, t.lo32c, t.inv32c};
 }
 
 // FP32 cell of x; the table builder uses the same two rounded operations
@@ -200,7 +200,7 @@ __device__ __forceinline__ int cell32_of(float x, float lo, float inv) {
 // two records give the polynomial about the interval's anchor.
 template <int DEG>
 __device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
-  const int c = min(max(cell32_of(R, T.lo, T.inv), 0), T.n_cells - 1);
+  const int c = min(max(cell32_of(R, T.lo, T.inv), T.c_min), T.c_max);
   const float4 rec = T.cells[c];
   const bool up = R >= rec.y;
   const int j = __float_as_int(rec.x) + (up ? 1 : 0);
@@ -903,13 +903,7 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
                                           unsigned gmask) {
   if (!valid_pair) return;  // uniform over the 8-lane group
   const int64_t pidx = idx;
-  int lo = 0, hi = g.nt - 1;  // p = row containing pidx
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (g.near_ptr[mid] <= pidx) lo = mid;
-    else hi = mid - 1;
-  }
-  const int p = lo, q = g.near_idx[pidx];
+  const int p = g.near_row[pidx], q = g.near_idx[pidx];
   double accr[3][3], acci[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -994,6 +988,116 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
     const int64_t idx = g0 + it * ngroups;
     near_task<Out, MIXED>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2}, Z, ldz, n_near, idx,
                           idx < n_near, sub, gmask);
+  }
+}
+
+// ---------------------------------------------------------------- windowed table
+// Tables larger than shared memory: the fill runs over tiles of 32 test
+// triangles x 512 source triangles (consecutive in the Morton order, so
+// spatially compact); the bounding spheres of the two sets bound every point
+// distance of the tile, and only the cells and interval records of that
+// distance window are staged into shared memory. A tile whose window does not
+// fit reads the table through L1.
+constexpr int kTileQBlocks = 16;
+constexpr int kWinBytes = 200 * 1024;
+
+__global__ void k_block_spheres(GeoView g, float4* bsph) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nb = (g.nt + 31) / 32;
+  if (b >= nb) return;
+  const int t0 = 32 * b, t1 = min(t0 + 32, g.nt);
+  double cx = 0, cy = 0, cz = 0;
+  for (int t = t0; t < t1; ++t) {
+    cx += g.cen64[4 * (size_t)t];
+    cy += g.cen64[4 * (size_t)t + 1];
+    cz += g.cen64[4 * (size_t)t + 2];
+  }
+  cx /= (t1 - t0);
+  cy /= (t1 - t0);
+  cz /= (t1 - t0);
+  double r = 0;
+  for (int t = t0; t < t1; ++t) {
+    const double dx = g.cen64[4 * (size_t)t] - cx, dy = g.cen64[4 * (size_t)t + 1] - cy,
+                 dz = g.cen64[4 * (size_t)t + 2] - cz;
+    r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz) + (double)g.rad32[t]);
+  }
+  bsph[b] = make_float4((float)cx, (float)cy, (float)cz, (float)(r * (1.0 + 1e-6)));
+}
+
+template <int M>
+__global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView tv, const float4* __restrict__ bsph,
+                                                            float kpi, float scale, float inv_k2, float2* Z,
+                                                            int64_t ldz) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int win[5];  // c_lo, c_hi, j_lo, j_hi, fits
+  const int nb = (g.nt + 31) / 32;
+  const int nqg = (nb + kTileQBlocks - 1) / kTileQBlocks;
+  const int64_t ntiles = (int64_t)nb * nqg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const Tab32 G = tab32(tv);
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int bp = (int)(tile / nqg), bqg = (int)(tile % nqg);
+    const int qb0 = bqg * kTileQBlocks, qb1 = min(qb0 + kTileQBlocks, nb);
+    if (threadIdx.x == 0) {
+      const float4 P = bsph[bp];
+      float qx = 0.f, qy = 0.f, qz = 0.f;
+      for (int b = qb0; b < qb1; ++b) {
+        qx += bsph[b].x;
+        qy += bsph[b].y;
+        qz += bsph[b].z;
+      }
+      const float inv_n = 1.f / (float)(qb1 - qb0);
+      qx *= inv_n;
+      qy *= inv_n;
+      qz *= inv_n;
+      float rq = 0.f;
+      for (int b = qb0; b < qb1; ++b) {
+        const float dx = bsph[b].x - qx, dy = bsph[b].y - qy, dz = bsph[b].z - qz;
+        rq = fmaxf(rq, sqrtf(dx * dx + dy * dy + dz * dz) + bsph[b].w);
+      }
+      const float dx = P.x - qx, dy = P.y - qy, dz = P.z - qz;
+      const float D = sqrtf(dx * dx + dy * dy + dz * dz);
+      const float mag = fmaxf(fmaxf(fabsf(P.x), fabsf(P.y)), fmaxf(fabsf(P.z), fmaxf(fmaxf(fabsf(qx), fabsf(qy)), fabsf(qz))));
+      const float slack = 1e-5f * (D + P.w + rq + mag);
+      const float lo = D - P.w - rq - slack, hi = D + P.w + rq + slack;
+      const int c_lo = max(min(max(cell32_of(lo, G.lo, G.inv), 0), G.c_max) - 2, 0);
+      const int c_hi = min(min(max(cell32_of(hi, G.lo, G.inv), 0), G.c_max) + 2, G.c_max);
+      const int j_lo = __float_as_int(G.cells[c_lo].x);
+      const int j_hi = min(__float_as_int(G.cells[c_hi].x) + 1, tv.n_nodes - 2);
+      const int64_t bytes = (int64_t)(c_hi - c_lo + 1) * 16 + (int64_t)(j_hi - j_lo + 1) * 32;
+      win[0] = c_lo;
+      win[1] = c_hi;
+      win[2] = j_lo;
+      win[3] = j_hi;
+      win[4] = bytes <= kWinBytes;
+    }
+    __syncthreads();
+    Tab32 T = G;
+    if (win[4]) {
+      const int c_lo = win[0], c_hi = win[1], j_lo = win[2], j_hi = win[3];
+      const int nc = c_hi - c_lo + 1, nj = j_hi - j_lo + 1;
+      float4* sc = reinterpret_cast<float4*>(smem);
+      float4* sa = sc + nc;
+      float4* sb = sa + nj;
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) sc[i] = G.cells[c_lo + i];
+      for (int i = threadIdx.x; i < nj; i += blockDim.x) {
+        sa[i] = G.ca[j_lo + i];
+        sb[i] = G.cb[j_lo + i];
+      }
+      __syncthreads();
+      T.cells = sc - c_lo;
+      T.ca = sa - j_lo;
+      T.cb = sb - j_lo;
+      T.c_min = c_lo;
+      T.c_max = c_hi;
+    }
+    const int ntask = 32 * (qb1 - qb0);
+    for (int task = warp; task < ntask; task += nw) {
+      const int p = bp * 32 + task / (qb1 - qb0);
+      const int q0 = (qb0 + task % (qb1 - qb0)) * 32;
+      if (p < g.nt) regular_task32<M, true>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
+    }
+    __syncthreads();
   }
 }
 
@@ -1506,13 +1610,7 @@ __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, boo
   for (int64_t job = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; job < njobs; job += ngroups) {
     const int64_t idx = job / 19;
     const int dir = (int)(job % 19);
-    int lo = 0, hi = g.nt - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (g.near_ptr[mid] <= idx) lo = mid;
-      else hi = mid - 1;
-    }
-    const int p = lo, q = g.near_idx[idx];
+    const int p = g.near_row[idx], q = g.near_idx[idx];
     double dL = 0.0;
     if (sub < g.m) {
       V3D vp[3], vq[3];
@@ -1791,6 +1889,12 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
   return cudaGetLastError();
 }
 
+cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s) {
+  const int nb = (g.nt + 31) / 32;
+  k_block_spheres<<<(nb + 127) / 128, 128, 0, s>>>(g, bsph);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
@@ -1861,6 +1965,11 @@ cudaError_t launch_regular32(const GeoView& g, const TabView* green, float kpi, 
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_regular32<M, true, true>, 512, smem);
     int64_t blocks = std::min<int64_t>(pair_grid(g, 2 * std::max(per_sm, 1)), (int64_t)sm_count() * std::max(per_sm, 1));
     k_fill_regular32<M, true, true><<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+  } else if (g.bsph) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fill_regular32_win<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinBytes);
+    if (e != cudaSuccess) return e;
+    k_fill_regular32_win<M><<<(unsigned)sm_count(), 512, kWinBytes, s>>>(g, tv, g.bsph, kpi, scale, inv_k2, Z, ldz);
   } else {
     int64_t blocks = pair_grid(g, 4);
     k_fill_regular32<M, true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
