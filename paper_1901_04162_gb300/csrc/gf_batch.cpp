@@ -249,14 +249,14 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
   }
   // longest first, so the tail of the persistent loop holds the small meshes
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-    return items[a].g.nt * items[a].nchunk > items[c].g.nt * items[c].nchunk;
+    return items[a].g.nt > items[c].g.nt;
   });
   int64_t reg = 0, nr = 0;
   for (int i : order) {
     BatchItem it = items[i];
     it.reg_begin = reg;
     it.near_begin = nr;
-    reg += (int64_t)it.g.nt * it.nchunk;
+    reg += gf::regular_units(it.g.nt);
     nr += it.n_near;
     b->items.push_back(it);
     b->z.push_back(Z[i]);

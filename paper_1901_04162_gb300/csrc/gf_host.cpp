@@ -239,10 +239,14 @@ gf::TabView gf_table::One::view() const {
   v.node32 = d_node32;
   v.c32a = d_c32a;
   v.c32b = d_c32b;
-  v.n_cells32 = n_cells32;
-  v.lo32c = lo32c;
-  v.inv32c = inv32c;
-  v.cells32 = d_cells32;
+  v.n_lat = n_lat;
+  v.n_sub = n_sub;
+  v.lat_lo = lat_lo;
+  v.lat_inv = lat_inv;
+  v.lat_h = lat_h;
+  v.lat_a = d_lat_a;
+  v.lat_b = d_lat_b;
+  v.lat_sub = d_lat_sub;
   v.n_cells64 = n_cells64;
   v.lo64c = lo64c;
   v.inv64c = inv64c;
@@ -615,6 +619,119 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
   return GF_OK;
 }
 
+namespace {
+
+// FP32 lattice image of a table (the device lookups repeat these float
+// operations exactly): cell of x and sub-cell of x inside cell i.
+int lattice_cell(float x, float lo, float inv) {
+  const float d = x - lo;
+  const float u = d * inv;
+  return (int)u;
+}
+
+int lattice_sub(float x, float anchor, float inv_w, int nsub) {
+  const float d = x - anchor;
+  const float u = d * inv_w;
+  const int c = (int)u;
+  return c < 0 ? 0 : (c > nsub - 1 ? nsub - 1 : c);
+}
+
+float bits_float(int32_t v) {
+  float f;
+  std::memcpy(&f, &v, 4);
+  return f;
+}
+
+struct Lattice {
+  int n = 0;
+  float lo = 0.f, inv = 0.f, h = 0.f;
+  std::vector<int32_t> j;    // interval of a sample-free cell, -1 for a cell holding samples
+  std::vector<float4> a;     // sub-cell headers (cells holding samples), zero elsewhere
+  std::vector<float4> sub;   // sub-cell records
+};
+
+// Cells of width t from r_min (the uniform samples of Eq. 2 sit on their ends).
+// A cell is sample-free when every interior sample lies within a margin of
+// its ends (FP32 rounding of the map and of the samples); R inside such a cell
+// but past a sample at its end is evaluated with the neighbour interval's
+// polynomial, an extrapolation by at most the margin. Cells holding samples
+// get sub-cells narrower than the local spacing, so each holds one sample at
+// most and the bracketing against the FP32 samples is exact.
+gf_status build_lattice(const std::vector<double>& r, double t, Lattice* L) {
+  const size_t n = r.size();
+  L->lo = (float)r.front();
+  L->h = (float)t;
+  L->inv = (float)(1.0 / t);
+  const float hi32 = (float)r.back();
+  if (!((double)(hi32 - L->lo) * L->inv < (double)(1 << 24))) return fail(GF_ERR_RANGE, "table: FP32 lattice too large");
+  L->n = lattice_cell(hi32, L->lo, L->inv) + 1;
+  std::vector<float> x32(n);
+  for (size_t j = 0; j < n; ++j) x32[j] = (float)r[j];
+  std::vector<int> cell(n, 0);
+  for (size_t j = 0; j < n; ++j) cell[j] = lattice_cell(x32[j], L->lo, L->inv);
+  const double eps = 1e-3 + 8.0 * L->n / 16777216.0;  // margin in cells
+  std::vector<char> busy(L->n, 0);
+  for (size_t j = 1; j + 1 < n; ++j) {
+    const double v = ((double)x32[j] - (double)L->lo) * (double)L->inv;
+    const double fl = std::floor(v), fr = v - fl;
+    const int64_t i = (int64_t)fl;
+    if (fr > eps && fr < 1.0 - eps && i >= 0 && i < L->n) busy[i] = 1;
+  }
+  L->j.assign(L->n, -1);
+  L->a.assign(L->n, make_float4(0.f, 0.f, 0.f, 0.f));
+  L->sub.clear();
+  for (int i = 0; i < L->n; ++i) {
+    if (!busy[i]) {
+      const double mid = (double)L->lo + (i + 0.5) / (double)L->inv;
+      int64_t j = (int64_t)(std::upper_bound(r.begin(), r.end(), mid) - r.begin()) - 1;
+      L->j[i] = (int32_t)std::min<int64_t>(std::max<int64_t>(j, 0), (int64_t)n - 2);
+      continue;
+    }
+    // interior samples whose FP32 cell is i: [ja, jb)
+    size_t ja = 1;
+    {
+      size_t lo = 1, hi = n - 1;
+      while (lo < hi) {
+        const size_t mid = (lo + hi) / 2;
+        if (cell[mid] >= i) hi = mid;
+        else lo = mid + 1;
+      }
+      ja = lo;
+    }
+    size_t jb = ja;
+    while (jb < n - 1 && cell[jb] == i) ++jb;
+    const float anchor = std::fmaf((float)i, L->h, L->lo);
+    double w = t;
+    for (size_t jj = (ja > 0 ? ja - 1 : 0); jj <= jb && jj + 1 < n; ++jj) w = std::min(w, r[jj + 1] - r[jj]);
+    w *= 0.9;
+    int nsub = 0;
+    float inv_w = 0.f;
+    bool ok = false;
+    for (int attempt = 0; attempt < 30 && !ok; ++attempt, w *= 0.5) {
+      inv_w = (float)(1.0 / w);
+      nsub = (int)(1.1 * t / w) + 2;
+      if (nsub > 65536) break;
+      ok = true;
+      for (size_t jj = ja; jj + 1 < jb; ++jj)
+        if (lattice_sub(x32[jj], anchor, inv_w, nsub) >= lattice_sub(x32[jj + 1], anchor, inv_w, nsub)) ok = false;
+    }
+    if (!ok) return fail(GF_ERR_RANGE, "table: samples closer than the FP32 resolution");
+    const int first = (int)L->sub.size();
+    size_t jj = ja;
+    for (int c = 0; c < nsub; ++c) {
+      while (jj < jb && lattice_sub(x32[jj], anchor, inv_w, nsub) < c) ++jj;
+      const int j0 = (int)jj - 1;  // interval below every sample of sub-cell c and later
+      const bool has = jj < jb && lattice_sub(x32[jj], anchor, inv_w, nsub) == c;
+      L->sub.push_back(make_float4(bits_float(j0), has ? x32[jj] : INFINITY, x32[j0], 0.f));
+    }
+    L->a[i] = make_float4(bits_float(kLatticeSubMark), bits_float(first), inv_w, bits_float(nsub - 1));
+  }
+  if (L->sub.empty()) L->sub.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+  return GF_OK;
+}
+
+}  // namespace
+
 gf_status gf_table_create(double k, double r_min, double r_max, const gf_params* p, void* stream, gf_table** out) {
   if (!out || !params_ok(p)) return fail(GF_ERR_ARG, "gf_table_create: bad params");
   if (!(k > 0) || !(r_min > 0) || !(r_max > r_min) || !std::isfinite(r_max))
@@ -647,23 +764,25 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o.dr = pl.dr;
     o.n_hash = pl.n_hash;
     const size_t n = o.r.size();
-    // FP32 cell map (the same float operations as the device lookups)
-    o.lo32c = (float)r_min;
-    o.inv32c = (float)(1.0 / (0.99 * o.dr));
-    const float span = ((float)r_max - o.lo32c) * o.inv32c;
-    if (!(span < (float)(1 << 26))) {
+    Lattice lat;
+    if ((st = build_lattice(o.r, t, &lat))) {
       gf_table_destroy(T.release());
-      return fail(GF_ERR_RANGE, "table: FP32 cell array too large");
+      return st;
     }
-    o.n_cells32 = (int)span + 1;
+    o.n_lat = lat.n;
+    o.n_sub = (int)lat.sub.size();
+    o.lat_lo = lat.lo;
+    o.lat_inv = lat.inv;
+    o.lat_h = lat.h;
     o.lo64c = r_min;
     o.inv64c = 1.0 / (0.99 * o.dr);
     o.n_cells64 = (int)std::floor((r_max - r_min) * o.inv64c) + 1;
     if ((st = dev_alloc(&o.d_node64, n)) || (st = dev_alloc(&o.d_zflag, n)) || (st = dev_alloc(&o.d_fval, 2 * n)) ||
         (st = dev_alloc(&o.d_c64, 4 * n)) || (st = dev_alloc(&o.d_node32, n)) || (st = dev_alloc(&o.d_c32a, n)) ||
         (st = dev_alloc(&o.d_c32b, n)) || (st = dev_alloc(&o.d_hash, (size_t)o.n_hash)) ||
-        (st = dev_alloc(&o.d_cells32, (size_t)o.n_cells32)) || (st = dev_alloc(&o.d_cells64, (size_t)o.n_cells64)) ||
-        (st = dev_alloc(&o.d_flag, 1))) {
+        (st = dev_alloc(&o.d_lat_j, (size_t)o.n_lat)) || (st = dev_alloc(&o.d_lat_a, (size_t)o.n_lat)) ||
+        (st = dev_alloc(&o.d_lat_b, (size_t)o.n_lat)) || (st = dev_alloc(&o.d_lat_sub, (size_t)o.n_sub)) ||
+        (st = dev_alloc(&o.d_cells64, (size_t)o.n_cells64)) || (st = dev_alloc(&o.d_flag, 1))) {
       gf_table_destroy(T.release());
       return st;
     }
@@ -671,9 +790,19 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     if (e == cudaSuccess) e = cudaMemcpyAsync(o.d_zflag, o.zflag.data(), n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(o.d_flag, 0, sizeof(int), s);
     if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o.d_lat_j, lat.j.data(), (size_t)o.n_lat * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o.d_lat_a, lat.a.data(), (size_t)o.n_lat * 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(o.d_lat_b, 0, (size_t)o.n_lat * 16, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(o.d_lat_sub, lat.sub.data(), (size_t)o.n_sub * 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
       e = launch_table_image(o.kind, k, o.degree, (int)n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a,
-                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells32, o.lo32c,
-                             o.inv32c, o.d_cells32, o.n_cells64, o.lo64c, o.inv64c, o.d_cells64, o.d_flag, s);
+                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells64, o.lo64c,
+                             o.inv64c, o.d_cells64, o.d_flag, s);
+    if (e == cudaSuccess)
+      e = launch_table_lattice(o.degree, (int)n, o.d_node64, o.d_fval, o.n_lat, o.lat_lo, o.lat_h, o.d_lat_j,
+                               o.d_lat_a, o.d_lat_b, s);
     int flag = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, o.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -683,7 +812,7 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     }
     if (flag) {
       gf_table_destroy(T.release());
-      return fail(GF_ERR_RANGE, "table: two samples in one hash cell (spacing below FP32 resolution)");
+      return fail(GF_ERR_RANGE, "table: two samples in one FP64 hash cell");
     }
   }
   *out = T.release();
@@ -733,8 +862,8 @@ gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* 
 gf_status gf_table_destroy(gf_table* t) {
   if (!t) return GF_OK;
   for (gf_table::One* o : {&t->green, &t->exp}) {
-    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval,    o->d_c64,     o->d_node32, o->d_c32a,
-                    o->d_c32b,   o->d_hash,  o->d_cells32, o->d_cells64, o->d_flag};
+    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval,    o->d_c64,     o->d_node32,    o->d_c32a,  o->d_c32b,
+                    o->d_hash,   o->d_lat_j, o->d_lat_a,   o->d_lat_b,   o->d_lat_sub,   o->d_cells64, o->d_flag};
     for (void* p : ptrs)
       if (p) cudaFree(p);
   }

@@ -70,18 +70,37 @@ struct TabView {
   const float* node32;     // [n_nodes]: FP32 anchors
   const float4* c32a;      // [n_nodes-1]: (c0re, c0im, c1re, c1im) about node32[j]
   const float4* c32b;      // [n_nodes-1]: (c2re, c2im, c3re, c3im)
-  // FP32 image of the hash: cells of width 0.99 dr in the FP32 map
-  // c(x) = trunc((x - lo32c) * inv32c); record c = (j0 as int bits, split,
-  // node32[j0], 0): every x in cell c lies in interval j0 if x < split, else in
-  // j0 + 1 whose anchor is split (at most one sample falls inside a cell).
-  int n_cells32;
-  float lo32c, inv32c;
-  const float4* cells32;
-  int n_cells64;  // FP64 cell image, same construction in FP64
+  // FP32 lattice image. Cells of the base spacing t on the map
+  // i(x) = trunc((x - lat_lo) * lat_inv), aligned with the uniform samples
+  // r_min + i t (Eq. 2). A cell with no sample inside (farther than a rounding
+  // margin from its ends) lies in one interval: lat_a/lat_b hold that
+  // interval's polynomial about A_i = fma(i, lat_h, lat_lo), so one lookup is
+  // two 16-byte records. A cell holding samples (refinement near zeros,
+  // grading, r_max) has lat_a = (kLatticeSubMark, first sub-cell, 1/w, count-1):
+  // sub-cell c = trunc((x - A_i) / w) holds (j0 as int bits, split, node32[j0],
+  // 0), x lies in interval j0 if x < split, else in j0 + 1 (anchor split), and
+  // the coefficients come from c32a/c32b.
+  int n_lat, n_sub;
+  float lat_lo, lat_inv, lat_h;
+  const float4* lat_a;     // [n_lat]: (c0re, c0im, c1re, c1im) about A_i, or a sub-cell header
+  const float4* lat_b;     // [n_lat]: (c2re, c2im, c3re, c3im)
+  const float4* lat_sub;   // [n_sub]
+  int n_cells64;  // FP64 image of the Eq. (6) hash: cells of width 0.99 dr, one sample at most each
   double lo64c, inv64c;
   const Cell64* cells64;
-  size_t smem32_bytes() const { return (size_t)n_cells32 * 16 + (size_t)(n_nodes - 1) * 32; }
+  size_t smem32_bytes() const { return (size_t)n_lat * 32 + (size_t)n_sub * 16; }
 };
+
+// Marker (a quiet-NaN bit pattern) of a lattice cell that holds samples.
+constexpr int32_t kLatticeSubMark = 0x7FC00001;
+
+// Regular work units of a mesh of nt triangles: (p, 32 consecutive q) over the
+// 32 x 32 triangle block pairs bp <= bq, 32 units per block pair; each
+// unordered regular pair {p, q} is evaluated once, for Z[m][n] and Z[n][m].
+__host__ __device__ inline int64_t regular_units(int nt) {
+  const int64_t nb = (nt + 31) / 32;
+  return 32 * (nb * (nb + 1) / 2);
+}
 
 // One mesh of a batched fill (device-resident descriptor).
 struct BatchItem {
@@ -92,7 +111,7 @@ struct BatchItem {
   double k, scale, inv_k2;        // k, k eta, 1/k^2 for the near kernel
   void* Z;
   int64_t ldz;
-  int64_t reg_begin, nchunk;      // first global regular task, 32-wide chunks per test triangle
+  int64_t reg_begin, nchunk;      // first global regular work unit, 32-wide triangle blocks
   int64_t near_begin, n_near;     // first global near pair, near pairs
 };
 
@@ -104,9 +123,12 @@ cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double*
 cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, const double* node64,
                                const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
                                float4* c32b, double* fval, int n_hash, double r_lo, double dr,
-                               int32_t* hash, int n_cells32, float lo32c, float inv32c, float4* cells32,
-                               int n_cells64, double lo64c, double inv64c, Cell64* cells64, int* flag,
-                               cudaStream_t s);
+                               int32_t* hash, int n_cells64, double lo64c, double inv64c, Cell64* cells64,
+                               int* flag, cudaStream_t s);
+// Coefficients of the sample-free lattice cells (lat_j[i] >= 0: interval of cell i).
+cudaError_t launch_table_lattice(int degree, int n_nodes, const double* node64, const double* fval, int n_lat,
+                                 float lat_lo, float lat_h, const int32_t* lat_j, float4* lat_a, float4* lat_b,
+                                 cudaStream_t s);
 cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
@@ -188,9 +210,12 @@ struct gf_table {
     float4* d_c32a = nullptr;
     float4* d_c32b = nullptr;
     int32_t* d_hash = nullptr;
-    int n_cells32 = 0;
-    float lo32c = 0.f, inv32c = 0.f;
-    float4* d_cells32 = nullptr;
+    int n_lat = 0, n_sub = 0;
+    float lat_lo = 0.f, lat_inv = 0.f, lat_h = 0.f;
+    int32_t* d_lat_j = nullptr;
+    float4* d_lat_a = nullptr;
+    float4* d_lat_b = nullptr;
+    float4* d_lat_sub = nullptr;
     int n_cells64 = 0;
     double lo64c = 0, inv64c = 0;
     gf::Cell64* d_cells64 = nullptr;

@@ -178,36 +178,46 @@ __global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, do
 }
 
 // ---------------------------------------------------------------- lookups
-struct Tab32 {  // FP32 view (shared or global memory; possibly a window)
-  const float4* cells;  // indexed by the global cell number
-  const float4* ca;     // indexed by the global interval number
-  const float4* cb;
-  int c_min, c_max;     // cells present (the whole table, or a window)
-  float lo, inv;
+struct Tab32 {  // FP32 view (shared or global memory; possibly a window of the lattice)
+  const float4* la;   // lattice records, indexed by the global cell number
+  const float4* lb;
+  const float4* sub;  // sub-cells of the cells holding samples
+  const float4* ga;   // interval records about node32 (cells holding samples)
+  const float4* gb;
+  int i_min, i_max;   // cells present (the whole lattice, or a window)
+  float lo, inv, h;
 };
 
 __device__ __forceinline__ Tab32 tab32(const TabView& t) {
-  return Tab32{t.cells32, t.c32a, t.c32b, 0, t.n_cells32 - 1, t.lo32c, t.inv32c};
+  return Tab32{t.lat_a, t.lat_b, t.lat_sub, t.c32a, t.c32b, 0, t.n_lat - 1, t.lat_lo, t.lat_inv, t.lat_h};
 }
 
-// FP32 cell of x; the table builder uses the same two rounded operations
+// lattice cell of x; the table builder uses the same rounded operations
 __device__ __forceinline__ int cell32_of(float x, float lo, float inv) {
   return __float2int_rz(__fmul_rn(__fsub_rn(x, lo), inv));
 }
 
-// e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 image: one cell record
-// gives the interval (Eq. 6 hash with the bracketing sample inlined), one or
-// two records give the polynomial about the interval's anchor.
+// e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 lattice image: the
+// lattice cell of R (the Eq. 6 hash on the uniform samples) gives the
+// polynomial directly; a cell that holds samples adds one sub-cell record
+// (exact bracketing) and the interval's own record.
 template <int DEG>
 __device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
-  const int c = min(max(cell32_of(R, T.lo, T.inv), T.c_min), T.c_max);
-  const float4 rec = T.cells[c];
-  const bool up = R >= rec.y;
-  const int j = __float_as_int(rec.x) + (up ? 1 : 0);
-  const float s = R - (up ? rec.y : rec.z);
-  const float4 a = T.ca[j];
+  const int i = min(max(cell32_of(R, T.lo, T.inv), T.i_min), T.i_max);
+  float4 a = T.la[i];
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DEG > 1) b = T.lb[i];
+  float s = __fsub_rn(R, __fmaf_rn((float)i, T.h, T.lo));
+  if (__float_as_int(a.x) == kLatticeSubMark) {
+    const int c = __float_as_int(a.y) + min(max(__float2int_rz(__fmul_rn(s, a.z)), 0), __float_as_int(a.w));
+    const float4 rec = T.sub[c];
+    const bool up = R >= rec.y;
+    const int j = __float_as_int(rec.x) + (up ? 1 : 0);
+    s = R - (up ? rec.y : rec.z);
+    a = T.ga[j];
+    if (DEG > 1) b = T.gb[j];
+  }
   if (DEG == 1) return make_float2(fmaf(s, a.z, a.x), fmaf(s, a.w, a.y));
-  const float4 b = T.cb[j];
   float re = fmaf(s, b.z, b.x), im = fmaf(s, b.w, b.y);
   re = fmaf(s, re, a.z);
   im = fmaf(s, im, a.w);
@@ -266,29 +276,19 @@ __global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_
   cells[c] = rec;
 }
 
-// Cell records of the FP32 image. Samples 1..n-2 may split a cell; with cells
-// 1 % narrower than the smallest spacing at most one sample falls in a cell
-// (checked: flag set otherwise). j0 = last sample whose cell is below c.
-__device__ __forceinline__ int first_sample_at_or_after(const float* node32, int n, float lo, float inv, int c) {
-  int a = 1, b = n - 1;  // search samples 1..n-2; result in [1, n-1]
-  while (a < b) {
-    const int mid = (a + b) >> 1;
-    if (cell32_of(node32[mid], lo, inv) >= c) b = mid;
-    else a = mid + 1;
-  }
-  return a;
-}
-
-__global__ void k_table_cells32(int n, const float* __restrict__ node32, int n_cells, float lo, float inv,
-                                float4* cells, int* flag) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
-  const int a = first_sample_at_or_after(node32, n, lo, inv, c);
-  const int b = first_sample_at_or_after(node32, n, lo, inv, c + 1);
-  if (b - a > 1) atomicOr(flag, 1);
-  const int j0 = a - 1;
-  const float split = (a < n - 1 && cell32_of(node32[a], lo, inv) == c) ? node32[a] : INFINITY;
-  cells[c] = make_float4(__int_as_float(j0), split, node32[j0], 0.f);
+// Lattice records of the sample-free cells: the interval's polynomial about
+// A_i = fma(i, h, lo), the anchor the lookups recompute.
+__global__ void k_table_lattice(int deg, int n, const double* __restrict__ r, const double* __restrict__ f, int n_lat,
+                                float lo, float h, const int32_t* __restrict__ lat_j, float4* la, float4* lb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_lat) return;
+  const int j = lat_j[i];
+  if (j < 0) return;
+  const float A = __fmaf_rn((float)i, h, lo);
+  double cre[4], cim[4];
+  interval_poly(deg, n, r, f, j, (double)A, cre, cim);
+  la[i] = make_float4((float)cre[0], (float)cim[0], (float)cre[1], (float)cim[1]);
+  lb[i] = make_float4((float)cre[2], (float)cim[2], (float)cre[3], (float)cim[3]);
 }
 
 template <int DEG>
@@ -328,6 +328,24 @@ __device__ __forceinline__ bool pair_is_near(const GeoView& g, int p, int q, int
   return false;
 }
 
+// Regular pairs are enumerated once per unordered pair {p, q}, p < q: the
+// Galerkin block of (q, p) is the transpose of that of (p, q) (the moments
+// swap alpha and beta, the bracket is unchanged), so one evaluation serves
+// Z[m][n] and Z[n][m]. Work unit = (p, 32 consecutive q) inside a 32 x 32 block
+// pair (bp <= bq); block pairs run column by column, u = bq (bq + 1) / 2 + bp,
+// 32 units (one per p of block bp) each; regular_units(nt) counts them.
+
+__device__ __forceinline__ bool sym_task(int64_t task, int nt, int* p, int* q0) {
+  const int64_t u = task >> 5;
+  int64_t bq = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+  while (bq > 0 && bq * (bq + 1) / 2 > u) --bq;
+  while ((bq + 1) * (bq + 2) / 2 <= u) ++bq;
+  const int64_t bp = u - bq * (bq + 1) / 2;
+  *p = (int)(bp * 32 + (task & 31));
+  *q0 = (int)(bq * 32);
+  return *p < nt;
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 __global__ void k_range_init(unsigned long long* mm) {
@@ -356,17 +374,16 @@ __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, floa
 
 __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm) {
   const int lane = threadIdx.x & 31;
-  const int64_t nchunk = (g.nt + 31) / 32;
-  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float min_ub = INFINITY, max_lb = 0.f;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
-    const int p = (int)(task / nchunk);
-    const int q0 = (int)(task % nchunk) * 32;
+    int p, q0;
+    if (!sym_task(task, g.nt, &p, &q0)) continue;
     const int q = min(q0 + lane, g.nt - 1);
     const float4 cp = g.cen32[p], cq = g.cen32[q];
     const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-    if (!((q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
+    if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
     float lb, ub;
     pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
     min_ub = fminf(min_ub, ub);
@@ -390,20 +407,19 @@ __global__ void __launch_bounds__(kThreads) k_range(GeoView g, unsigned long lon
   const int lane = threadIdx.x & 31;
   const float u_min = (float)__longlong_as_double((long long)mm[2]);
   const float l_max = (float)__longlong_as_double((long long)mm[3]);
-  const int64_t nchunk = (g.nt + 31) / 32;
-  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t ntask = regular_units(g.nt);
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double best_lo = INFINITY, best_hi = 0.0;
   float lo32 = INFINITY, hi32 = -1.f;
   int lo_p = 0, lo_q = 0, lo_ab = 0, hi_p = 0, hi_q = 0, hi_ab = 0;
   for (int64_t task = warp0; task < ntask; task += nwarp) {
-    const int p = (int)(task / nchunk);
-    const int q0 = (int)(task % nchunk) * 32;
+    int p, q0;
+    if (!sym_task(task, g.nt, &p, &q0)) continue;
     const int q = min(q0 + lane, g.nt - 1);
     const float4 cp = g.cen32[p], cq = g.cen32[q];
     float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-    bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+    bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
     if (!ok) continue;
     if (!FP64) {
       float lb, ub;
@@ -484,7 +500,7 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
   const int q = min(q0 + lane, g.nt - 1);
   const float4 cp = g.cen32[p], cq = g.cen32[q];
   const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-  const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
   if (!__any_sync(0xffffffffu, ok)) return;
   float4 beta[M];
 #pragma unroll
@@ -556,8 +572,10 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
       const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
       const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
       const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
-      // j * c * (br + j bi) = c * (-bi + j br)
-      atomicAdd(zrow + edge_of(ecq[j]), make_float2(-c * bi, c * br));
+      // j * c * (br + j bi) = c * (-bi + j br), into Z[m][n] and Z[n][m]
+      const float2 v = make_float2(-c * bi, c * br);
+      atomicAdd(zrow + edge_of(ecq[j]), v);
+      atomicAdd(Z + (int64_t)edge_of(ecq[j]) * ldz + edge_of(ecp[i]), v);
     }
   }
 }
@@ -569,26 +587,26 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoVie
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
   if (TABLE && SMEM) {
-    const int ni = tv.n_nodes - 1;
+    const int nl = tv.n_lat;
     float4* sa = reinterpret_cast<float4*>(smem);
-    float4* sb = sa + ni;
-    float4* sc = sb + ni;
-    for (int i = threadIdx.x; i < ni; i += blockDim.x) {
-      sa[i] = tv.c32a[i];
-      sb[i] = tv.c32b[i];
+    float4* sb = sa + nl;
+    float4* ss = sb + nl;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      sa[i] = tv.lat_a[i];
+      sb[i] = tv.lat_b[i];
     }
-    for (int i = threadIdx.x; i < tv.n_cells32; i += blockDim.x) sc[i] = tv.cells32[i];
+    for (int i = threadIdx.x; i < tv.n_sub; i += blockDim.x) ss[i] = tv.lat_sub[i];
     __syncthreads();
-    T.ca = sa;
-    T.cb = sb;
-    T.cells = sc;
+    T.la = sa;
+    T.lb = sb;
+    T.sub = ss;
   }
   const int lane = threadIdx.x & 31;
-  const int64_t nchunk = (g.nt + 31) / 32;
-  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
-    regular_task32<M, TABLE>(g, T, kpi, scale, inv_k2, Z, ldz, (int)(task / nchunk), (int)(task % nchunk) * 32, lane);
+    int p, q0;
+    if (sym_task(task, g.nt, &p, &q0)) regular_task32<M, TABLE>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
   }
 }
 
@@ -597,16 +615,15 @@ __global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView 
                                                              double inv_k2, double2* Z, int64_t ldz) {
   const int lane = threadIdx.x & 31;
   const int m = g.m;
-  const int64_t nchunk = (g.nt + 31) / 32;
-  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
-    const int p = (int)(task / nchunk);
-    const int q0 = (int)(task % nchunk) * 32;
+    int p, q0;
+    if (!sym_task(task, g.nt, &p, &q0)) continue;
     const int q = min(q0 + lane, g.nt - 1);
     const float4 cp32 = g.cen32[p], cq32 = g.cen32[q];
     const float3 dc32 = make_float3(cp32.x - cq32.x, cp32.y - cq32.y, cp32.z - cq32.z);
-    const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc32);
+    const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc32);
     if (!ok) continue;
     const double* cp = g.cen64 + 4 * (size_t)p;
     const double* cq = g.cen64 + 4 * (size_t)q;
@@ -672,6 +689,9 @@ __global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView 
         double* z = zrow + 2 * edge_of(ecq[j]);
         atomicAdd(z, -c * bi);
         atomicAdd(z + 1, c * br);
+        double* zt = reinterpret_cast<double*>(Z + (int64_t)edge_of(ecq[j]) * ldz + edge_of(ecp[i]));
+        atomicAdd(zt, -c * bi);
+        atomicAdd(zt + 1, c * br);
       }
     }
   }
@@ -995,9 +1015,10 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
 // Tables larger than shared memory: the fill runs over tiles of 32 test
 // triangles x 512 source triangles (consecutive in the Morton order, so
 // spatially compact); the bounding spheres of the two sets bound every point
-// distance of the tile, and only the cells and interval records of that
-// distance window are staged into shared memory. A tile whose window does not
-// fit reads the table through L1.
+// distance of the tile, and only the lattice records of that distance window
+// are staged into shared memory (sub-cells and the interval records of cells
+// holding samples stay in global memory). A tile whose window does not fit
+// reads the table through L1.
 constexpr int kTileQBlocks = 16;
 constexpr int kWinBytes = 200 * 1024;
 
@@ -1029,7 +1050,7 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
                                                             float kpi, float scale, float inv_k2, float2* Z,
                                                             int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int win[5];  // c_lo, c_hi, j_lo, j_hi, fits
+  __shared__ int win[5];  // c_lo, c_hi, unused, unused, fits
   const int nb = (g.nt + 31) / 32;
   const int nqg = (nb + kTileQBlocks - 1) / kTileQBlocks;
   const int64_t ntiles = (int64_t)nb * nqg;
@@ -1037,7 +1058,9 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
   const Tab32 G = tab32(tv);
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int bp = (int)(tile / nqg), bqg = (int)(tile % nqg);
-    const int qb0 = bqg * kTileQBlocks, qb1 = min(qb0 + kTileQBlocks, nb);
+    const int qb1 = min((bqg + 1) * kTileQBlocks, nb);
+    if (qb1 <= bp) continue;  // only source blocks bq >= bp (one evaluation per unordered pair)
+    const int qb0 = max(bqg * kTileQBlocks, bp);
     if (threadIdx.x == 0) {
       const float4 P = bsph[bp];
       float qx = 0.f, qy = 0.f, qz = 0.f;
@@ -1060,36 +1083,28 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
       const float mag = fmaxf(fmaxf(fabsf(P.x), fabsf(P.y)), fmaxf(fabsf(P.z), fmaxf(fmaxf(fabsf(qx), fabsf(qy)), fabsf(qz))));
       const float slack = 1e-5f * (D + P.w + rq + mag);
       const float lo = D - P.w - rq - slack, hi = D + P.w + rq + slack;
-      const int c_lo = max(min(max(cell32_of(lo, G.lo, G.inv), 0), G.c_max) - 2, 0);
-      const int c_hi = min(min(max(cell32_of(hi, G.lo, G.inv), 0), G.c_max) + 2, G.c_max);
-      const int j_lo = __float_as_int(G.cells[c_lo].x);
-      const int j_hi = min(__float_as_int(G.cells[c_hi].x) + 1, tv.n_nodes - 2);
-      const int64_t bytes = (int64_t)(c_hi - c_lo + 1) * 16 + (int64_t)(j_hi - j_lo + 1) * 32;
+      const int c_lo = max(min(max(cell32_of(lo, G.lo, G.inv), 0), G.i_max) - 2, 0);
+      const int c_hi = min(min(max(cell32_of(hi, G.lo, G.inv), 0), G.i_max) + 2, G.i_max);
       win[0] = c_lo;
       win[1] = c_hi;
-      win[2] = j_lo;
-      win[3] = j_hi;
-      win[4] = bytes <= kWinBytes;
+      win[4] = (int64_t)(c_hi - c_lo + 1) * 32 <= kWinBytes;
     }
     __syncthreads();
     Tab32 T = G;
     if (win[4]) {
-      const int c_lo = win[0], c_hi = win[1], j_lo = win[2], j_hi = win[3];
-      const int nc = c_hi - c_lo + 1, nj = j_hi - j_lo + 1;
-      float4* sc = reinterpret_cast<float4*>(smem);
-      float4* sa = sc + nc;
-      float4* sb = sa + nj;
-      for (int i = threadIdx.x; i < nc; i += blockDim.x) sc[i] = G.cells[c_lo + i];
-      for (int i = threadIdx.x; i < nj; i += blockDim.x) {
-        sa[i] = G.ca[j_lo + i];
-        sb[i] = G.cb[j_lo + i];
+      const int c_lo = win[0], c_hi = win[1];
+      const int nc = c_hi - c_lo + 1;
+      float4* sa = reinterpret_cast<float4*>(smem);
+      float4* sb = sa + nc;
+      for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+        sa[i] = G.la[c_lo + i];
+        sb[i] = G.lb[c_lo + i];
       }
       __syncthreads();
-      T.cells = sc - c_lo;
-      T.ca = sa - j_lo;
-      T.cb = sb - j_lo;
-      T.c_min = c_lo;
-      T.c_max = c_hi;
+      T.la = sa - c_lo;
+      T.lb = sb - c_lo;
+      T.i_min = c_lo;
+      T.i_max = c_hi;
     }
     const int ntask = 32 * (qb1 - qb0);
     for (int task = warp; task < ntask; task += nw) {
@@ -1127,7 +1142,7 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
   const int q = min(q0 + lane, g.nt - 1);
   const float4 cp = g.cen32[p], cq = g.cen32[q];
   const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-  const bool ok = (q0 + lane < g.nt) && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
   if (!__any_sync(0xffffffffu, ok)) return;
   const int4 ep = g.tedge[p], eq = g.tedge[q];
   const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
@@ -1137,11 +1152,14 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
     gp[i] = g.geo32[3 * (size_t)p + i];
     gq[i] = g.geo32[3 * (size_t)q + i];
   }
-  // h_ij = j kappa sigma_i sigma_j conj(gZ_ij) = c (Im gZ + j Re gZ)
+  // The block value B_ij feeds Z[m][n] and Z[n][m], so its cotangent is
+  // g = gZ[m][n] + gZ[n][m]; h_ij = j kappa sigma_i sigma_j conj(g) = c (Im g + j Re g)
   auto h_of = [&](int i, int j, float* hr, float* hi) {
     *hr = *hi = 0.f;
     if (ok && edge_valid(ecp[i]) && edge_valid(ecq[j])) {
-      const float2 z = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+      const float2 z1 = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+      const float2 z2 = gZ[(int64_t)edge_of(ecq[j]) * ldg + edge_of(ecp[i])];
+      const float2 z = make_float2(z1.x + z2.x, z1.y + z2.y);
       const float c = kappa * gp[i].w * gq[j].w;
       *hr = c * z.y;
       *hi = c * z.x;
@@ -1336,12 +1354,13 @@ __global__ void __launch_bounds__(256) k_adjoint_regular32(GeoView g, TabView tv
                                                            double* dtri, double* dkacc) {
   const Tab32 T = tab32(tv);
   const int lane = threadIdx.x & 31;
-  const int64_t nchunk = (g.nt + 31) / 32;
-  const int64_t ntask = (int64_t)g.nt * nchunk;
+  const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp)
-    regular_adjoint_task32<M, TABLE>(g, T, k, kappa, inv_k2, bw, gZ, ldg, dtri, dkacc, (int)(task / nchunk),
-                                     (int)(task % nchunk) * 32, lane);
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
+    int p, q0;
+    if (sym_task(task, g.nt, &p, &q0))
+      regular_adjoint_task32<M, TABLE>(g, T, k, kappa, inv_k2, bw, gZ, ldg, dtri, dkacc, p, q0, lane);
+  }
 }
 
 // ---- near pairs: forward-mode dual numbers (one direction per thread group)
@@ -1712,10 +1731,11 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
     const int64_t end = min((int64_t)base + chunk, total);
     for (int64_t t = (int64_t)base; t < end; ++t) {
       const BatchItem& it = items[batch_item_of(items, nitems, t, false)];
-      const int64_t local = t - it.reg_begin;
       const Tab32 T = tab32(it.green);
-      regular_task32<M, TABLE>(it.g, T, it.kpi, it.scale32, it.inv_k2_32, reinterpret_cast<float2*>(it.Z), it.ldz,
-                               (int)(local / it.nchunk), (int)(local % it.nchunk) * 32, lane);
+      int p, q0;
+      if (sym_task(t - it.reg_begin, it.g.nt, &p, &q0))
+        regular_task32<M, TABLE>(it.g, T, it.kpi, it.scale32, it.inv_k2_32, reinterpret_cast<float2*>(it.Z), it.ldz,
+                                 p, q0, lane);
     }
   }
 }
@@ -1754,7 +1774,7 @@ int sm_count() {
 }
 
 int64_t pair_grid(const GeoView& g, int blocks_per_sm) {
-  const int64_t ntask = (int64_t)g.nt * ((g.nt + 31) / 32);
+  const int64_t ntask = regular_units(g.nt);
   int64_t blocks = (ntask + kWarps - 1) / kWarps;
   return std::min<int64_t>(blocks, (int64_t)sm_count() * blocks_per_sm);
 }
@@ -1906,14 +1926,19 @@ cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double*
 
 cudaError_t launch_table_image(int kind, double k, int degree, int n, const double* node64, const int8_t* zflag,
                                float* node32, double2* c64, float4* c32a, float4* c32b, double* fval, int n_hash,
-                               double r_lo, double dr, int32_t* hash, int n_cells32, float lo32c, float inv32c,
-                               float4* cells32, int n_cells64, double lo64c, double inv64c, Cell64* cells64,
-                               int* flag, cudaStream_t s) {
+                               double r_lo, double dr, int32_t* hash, int n_cells64, double lo64c,
+                               double inv64c, Cell64* cells64, int* flag, cudaStream_t s) {
   k_table_values<<<(n + 255) / 256, 256, 0, s>>>(kind, k, n, node64, zflag, fval);
   k_table_coef<<<(n + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, c64, node32, c32a, c32b);
   k_table_hash<<<(n_hash + 255) / 256, 256, 0, s>>>(n, node64, n_hash, r_lo, dr, hash);
-  k_table_cells32<<<(n_cells32 + 255) / 256, 256, 0, s>>>(n, node32, n_cells32, lo32c, inv32c, cells32, flag);
   k_table_cells64<<<(n_cells64 + 255) / 256, 256, 0, s>>>(n, node64, n_cells64, lo64c, inv64c, cells64, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_lattice(int degree, int n, const double* node64, const double* fval, int n_lat, float lat_lo,
+                                 float lat_h, const int32_t* lat_j, float4* lat_a, float4* lat_b, cudaStream_t s) {
+  k_table_lattice<<<(n_lat + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, n_lat, lat_lo, lat_h, lat_j, lat_a,
+                                                       lat_b);
   return cudaGetLastError();
 }
 
