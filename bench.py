@@ -61,12 +61,18 @@ WORKLOADS = {
 
 
 def regular_ops_per_pair(m):
-    """FP32 lane operations of the algorithm per regular triangle pair:
-    28 per Green evaluation (distance 7, table lookup + cubic 11, weight 2,
-    moment sums 8), 92 per test point (offset 3, 16 compensated moment
-    updates 80, weighted offsets 3, alpha . S_beta 6), 210 for the 3 x 3 RWG
-    block of the pair."""
-    return 28 * m * m + 92 * m + 210
+    """FP32 lane operations of the algorithm per evaluated regular triangle
+    pair (each unordered pair {p, q} is evaluated once and its 3 x 3 block is
+    written to Z[m][n] and Z[n][m]): 28 per Green evaluation (distance 7,
+    table lookup + cubic 11, weight 2, moment sums 8), 92 per test point
+    (offset 3, 16 compensated moment updates 80, weighted offsets 3,
+    alpha . S_beta 6), 250 for the 3 x 3 RWG block and its two scatters."""
+    return 28 * m * m + 92 * m + 250
+
+
+def evaluated_pairs(nt, n_near):
+    """Unordered regular triangle pairs: (ordered regular pairs) / 2."""
+    return (nt * nt - n_near) // 2
 
 
 # ----------------------------------------------------------------------------
@@ -253,6 +259,8 @@ def run_ours(args, wl, rank, world, local_rank):
         tt = timed(False, args.steps, args.warmup)
     clocks = clk.summary()
     td = timed(True, args.steps, args.warmup)
+    px = gf.gf_params_default(rule=wl.rule, green_from_exp=1)
+    tx = timed(False, args.steps, args.warmup, px)
     p64 = gf.gf_params_default(rule=wl.rule, near_fp64=1)
     t64 = timed(False, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
     d64 = timed(True, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
@@ -292,15 +300,16 @@ def run_ours(args, wl, rank, world, local_rank):
     # ---- roofline of the regular-pair kernel (table), CUDA events on its stream
     m = wl.rule
     n_regular = nt * nt - n_near
+    n_eval = evaluated_pairs(nt, n_near)
     reg_ms = statistics.mean(tt["regular_ms"])
-    ops = n_regular * regular_ops_per_pair(m)
+    ops = n_eval * regular_ops_per_pair(m)
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     achieved = ops / (reg_ms / 1e3) / 1e12
     khash = kernel_source_hash()
     traffic = TRAFFIC.get((wl.name, khash))
-    evals_regular = n_regular * m * m
+    evals_regular = n_eval * m * m
     evals_near = n_near * m * (3 * (p.nphi + p.nl) + 1)
 
     line = {
@@ -310,7 +319,7 @@ def run_ours(args, wl, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": wl.name, "triangles": nt, "rwg_unknowns": ne, "rule_points": m, "k": wl.k,
                    "table_tol": p.table_tol, "near_pairs": n_near, "regular_pairs": n_regular,
-                   "precision": "fp32 regular (Kahan outer sums), fp64 near" if prec == gf.GF_FP32 else "fp64",
+                   "regular_pairs_evaluated": n_eval, "precision": "fp32 regular (Kahan outer sums), fp64 near" if prec == gf.GF_FP32 else "fp64",
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "green_evals_per_s": world * (evals_regular + evals_near) * args.steps / (total_ms / 1e3),
         "step_breakdown_ms": {"range_and_tables": statistics.mean(tt["range_table_ms"]),
@@ -322,6 +331,12 @@ def run_ours(args, wl, rank, world, local_rank):
             "ms_per_step": statistics.mean(t64["step_ms"]), "near_kernel_ms": statistics.mean(t64["near_ms"]),
             "direct_near_kernel_ms": statistics.mean(d64["near_ms"]),
             "note": "near pairs sampled in FP64 too (near_fp64=1)"},
+        "exp_over_r_variant": {
+            "ms_per_step": statistics.mean(tx["step_ms"]), "regular_kernel_ms": statistics.mean(tx["regular_ms"]),
+            "range_and_tables_ms": statistics.mean(tx["range_table_ms"]),
+            "regular_speedup_vs_direct": statistics.mean(td["regular_ms"]) / statistics.mean(tx["regular_ms"]),
+            "note": "green_from_exp=1: regular-pair e^{-jkR} from the linear Exp table (one 16-byte record), "
+                    "times 1/R; near pairs unchanged"},
         "table_speedup_vs_direct": {"step": direct_ms / ms_step,
                                     "regular_kernel": statistics.mean(td["regular_ms"]) / reg_ms,
                                     "near_kernel": statistics.mean(td["near_ms"]) / statistics.mean(tt["near_ms"])},
@@ -330,12 +345,13 @@ def run_ours(args, wl, rank, world, local_rank):
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                     f"({src} max SM clock)",
                      "ops_per_launch": ops, "traffic": traffic,
-                     "mufu_frac": n_regular * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6)},
+                     "mufu_frac": n_eval * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6)},
         "clocks": clocks,
         "e2e": ({"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3} if e2e_s else
                 {"value": None, "reason": "Z larger than 8 GiB: no pinned host copy per step"}),
-        "gpu_launches": 10 * args.steps,
+        # per step: range 3 (FP32; 2 in FP64), 5 per table x 2 tables, regular 1, near 1
+        "gpu_launches": (15 if prec == gf.GF_FP32 else 14) * args.steps,
     }
 
     # ---- accuracy vs the FP64 oracle on sampled rows (outside the timed region)
@@ -348,14 +364,20 @@ def run_ours(args, wl, rank, world, local_rank):
         tab = gf.Table(wl.k, lo, hi, p)
         gf.gf_fill(mesh.h, wl.k, p, tab.h, prec, Z)
         zt = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        gf.gf_fill(mesh.h, wl.k, px, tab.h, prec, Z)
+        zx = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
         gf.gf_fill(mesh.h, wl.k, p, None, prec, Z)
         zd = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        ref_t = om.z_rows(wl.k, wl.rule, rows, mode="table", tables=O.make_tables(wl.k, olo, ohi))
+        otabs = O.make_tables(wl.k, olo, ohi)
+        ref_t = om.z_rows(wl.k, wl.rule, rows, mode="table", tables=otabs)
+        ref_x = om.z_rows(wl.k, wl.rule, rows, mode="exp_over_r", tables=otabs)
         ref_d = om.z_rows(wl.k, wl.rule, rows)
         rf = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
         line["accuracy"] = {"rows_sampled": 8, "gpu_table_vs_oracle_table": rf(zt, ref_t),
                             "gpu_direct_vs_oracle_direct": rf(zd, ref_d),
-                            "gpu_table_vs_oracle_direct": rf(zt, ref_d), "tolerance": 1e-5}
+                            "gpu_table_vs_oracle_direct": rf(zt, ref_d),
+                            "gpu_exp_over_r_vs_oracle_exp_over_r": rf(zx, ref_x),
+                            "gpu_exp_over_r_vs_oracle_direct": rf(zx, ref_d), "tolerance": 1e-5}
     if rank == 0 and not args.skip_cpu_baseline:
         t_full, desc, cores, _ = oracle_baseline(wl)
         line["cpu_baseline"] = {"value": ne * ne / t_full, "unit": "Z entries/s", "cores": cores,
@@ -412,7 +434,7 @@ def run_batch(args, rank, world, local_rank):
     clocks = clk.summary()
     direct_ms = timed(direct)
     entries = sum(m.ne * m.ne for m in meshes)
-    n_regular = sum(m.nt * m.nt - m.n_near for m in meshes)
+    n_regular = sum(evaluated_pairs(m.nt, m.n_near) for m in meshes)
     n_near = sum(m.n_near for m in meshes)
     evals = n_regular * rule * rule + n_near * rule * (3 * (p.nphi + p.nl) + 1)
     ms = total_ms / args.steps
@@ -504,7 +526,7 @@ def run_adjoint(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl.name, "triangles": m.nt, "rwg_unknowns": m.ne, "rule_points": rule,
                    "loss": "Re(a^H Z b), a, b seeded complex Gaussian", "regular_pairs": n_regular,
-                   "near_pairs": m.n_near, "parallelism": f"replicas x{world}"},
+                   "regular_pairs_evaluated": evaluated_pairs(m.nt, m.n_near), "near_pairs": m.n_near, "parallelism": f"replicas x{world}"},
         "gradient_evals_per_s": 1.0 / (bwd_ms / 1e3),
         "forward_fill_ms": fwd_ms, "backward_over_forward": bwd_ms / fwd_ms,
         "direct_backward_ms": bwd_direct_ms,

@@ -75,6 +75,11 @@ typedef struct {
   int near_fp64;              /* GF_FP32 fills: 0 = near pairs with FP64 geometry, static
                                  parts and sums and FP32 sampling on the source edges;
                                  1 = FP64 throughout (GF_FP64 fills always are) (0)       */
+  int green_from_exp;         /* regular pairs of gf_fill / gf_fill_parts with a table:
+                                 0 = e^{-jkR}/R from the Lagrange Green table (Section
+                                 II.C); 1 = e^{-jkR} from the linear Exp table times 1/R
+                                 (one 16-byte record per evaluation in FP32). gf_batch_*
+                                 and gf_fill_backward accept 0 only (0)                   */
 } gf_params;
 
 /* Fills *p with the defaults listed above. */
@@ -124,9 +129,13 @@ gf_status gf_range(const gf_mesh* m, int rule, int precision, double* r_min, dou
  * the host in FP64 (uniform t from r_min, refinement near the zeros of the
  * real and imaginary parts, forced zeros, Eq. (11) grading), then sample
  * values, per-interval polynomial coefficients (FP64 and FP32 images) and the
- * hash array of Eq. (6) by kernels on `stream` (the call synchronizes it).
+ * hash array of Eq. (6) by kernels queued on `stream`. The call returns once
+ * the uploads and kernels are queued (it does not wait for them): the table is
+ * ready for work later on `stream`; other streams must wait for `stream`.
+ * The device memory is one allocation owned by the table.
  * Errors: GF_ERR_ARG (k <= 0, r_min <= 0, r_max <= r_min, bad params),
- * GF_ERR_RANGE (more than 2^26 samples or hash cells). */
+ * GF_ERR_RANGE (more than 2^26 samples or hash cells, samples closer than the
+ * FP32 / FP64 images resolve), GF_ERR_CUDA / GF_ERR_ALLOC. */
 gf_status gf_table_create(double k, double r_min, double r_max, const gf_params* p, void* stream,
                           gf_table** out);
 

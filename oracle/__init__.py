@@ -219,7 +219,7 @@ class Mesh:
         ni = np.ascontiguousarray(ni, dtype=np.int32)
         zr = np.zeros(mi.size)
         zi = np.zeros(mi.size)
-        fp = FillParams(k, eta, rule, nphi, nl, 1 if mode == "table" else 0)
+        fp = FillParams(k, eta, rule, nphi, nl, {"direct": 0, "table": 1, "exp_over_r": 2}[mode])
         tg = tables[0].h if tables else None
         te = tables[1].h if tables else None
         rc = lib().or_z_entries(self.h, C.byref(fp), tg, te, mi.size, _ip(mi), _ip(ni), _dp(zr),

@@ -249,9 +249,12 @@ TriGeo<T> tri_geo(const V3<T> v[3]) {
 // Contribution of triangle pair (p, q) to Z_mn where m is the edge opposite
 // local vertex i of p with sign sp, n the edge opposite local vertex j of q
 // with sign sq. Without the jk eta factor.
+// texp_regular != NULL: regular-pair Green values are e^{-jkR} from that
+// (linear Exp) table times 1/(4 pi R), in place of the Green table.
 template <class T>
 Cx<T> pair_term(const TriGeo<T>& P, int i, int sp, const TriGeo<T>& Qg, int j, int sq, bool near, T k,
-                const Quad& Q, const or_table* tgreen, const or_table* texp) {
+                const Quad& Q, const or_table* tgreen, const or_table* texp,
+                const or_table* texp_regular = nullptr) {
   // RWG on p: f = sp * l/(2A) (r - v_i), div f = sp * l / A
   T lm = norm(P.v[(i + 2) % 3] - P.v[(i + 1) % 3]);
   T ln = norm(Qg.v[(j + 2) % 3] - Qg.v[(j + 1) % 3]);
@@ -271,7 +274,7 @@ Cx<T> pair_term(const TriGeo<T>& P, int i, int sp, const TriGeo<T>& Qg, int j, i
         V3<T> fn = (rb - Qg.v[j]) * cn;
         T wb = Qg.area * Q.w[b];
         T R = norm(ra - rb);
-        Cx<T> G = green(k, R, tgreen);
+        Cx<T> G = texp_regular ? exp_mjkr(k, R, texp_regular) * (T(1.0 / (4.0 * kPi)) / R) : green(k, R, tgreen);
         T kern = dot(fm, fn) - divm * divn * inv_k2;
         sum += G * (wa * wb * kern);
       }
@@ -481,9 +484,12 @@ int or_z_entries(const or_mesh* m, const or_fill_params* fp, const or_table* tgr
                  long nent, const int* mi, const int* ni, double* zre, double* zim, int nthreads) {
   Quad Q;
   if (!m || !fp || !make_quad(fp->rule, fp->nphi, fp->nl, &Q)) return -1;
+  if (fp->green_mode < 0 || fp->green_mode > 2) return -1;
   if (fp->green_mode == 1 && (!tgreen || !texp)) return -1;
+  if (fp->green_mode == 2 && !texp) return -1;
   const or_table* tg = fp->green_mode == 1 ? tgreen : nullptr;
-  const or_table* te = fp->green_mode == 1 ? texp : nullptr;
+  const or_table* te = fp->green_mode >= 1 ? texp : nullptr;
+  const or_table* ter = fp->green_mode == 2 ? texp : nullptr;
   for (long e = 0; e < nent; ++e)
     if (mi[e] < 0 || mi[e] >= m->ne || ni[e] < 0 || ni[e] >= m->ne) return -1;
   double k = fp->k;
@@ -508,7 +514,7 @@ int or_z_entries(const or_mesh* m, const or_fill_params* fp, const or_table* tgr
           if (m->tedge[3 * q + c] == en) iq = c;
         V3<double> qv[3] = {vtx(m, m->tri[3 * q]), vtx(m, m->tri[3 * q + 1]), vtx(m, m->tri[3 * q + 2])};
         TriGeo<double> Qg = tri_geo(qv);
-        z += pair_term<double>(P, ip, sp, Qg, iq, sq, is_near(m, p, q), k, Q, tg, te);
+        z += pair_term<double>(P, ip, sp, Qg, iq, sq, is_near(m, p, q), k, Q, tg, te, ter);
       }
     }
     // times j k eta

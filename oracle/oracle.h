@@ -92,7 +92,9 @@ int or_range(const or_mesh* m, int rule, double* r_min, double* r_max, int nthre
 int or_range_ex(const or_mesh* m, int rule, int prune, double* r_min, double* r_max, int nthreads);
 
 /* Z entries (m_i, n_i), i < nent. green_mode 0: direct; 1: tables (tgreen for
- * regular pairs, texp for the near-pair line integrals). */
+ * regular pairs, texp for the near-pair line integrals); 2: texp for both, the
+ * regular-pair Green value being e^{-jkR} from the Exp table times 1/(4 pi R)
+ * (tgreen unused). */
 typedef struct {
   double k;
   double eta;

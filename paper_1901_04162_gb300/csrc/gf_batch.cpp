@@ -195,6 +195,7 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
   if (nmesh < 1 || !meshes || !k || !p || !Z || !ldz || !out)
     return fail(GF_ERR_ARG, "gf_batch_create: bad arguments");
   if (precision != GF_FP32) return fail(GF_ERR_ARG, "gf_batch_create: batched fills are GF_FP32");
+  if (p->green_from_exp) return fail(GF_ERR_ARG, "gf_batch_create: green_from_exp must be 0");
   std::unique_ptr<gf_batch> b(new (std::nothrow) gf_batch);
   if (!b) return fail(GF_ERR_ALLOC, "gf_batch_create: out of host memory");
   GF_CUDA(cudaGetDevice(&b->device));

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <tuple>
@@ -130,6 +131,40 @@ static double eq11_rel(const std::vector<double>& r, int j, int deg, int kind, d
   return kind == GF_GREEN ? b * r[j + 1] : b;
 }
 
+// The same bound with the powers formed by products (equal to eq11_rel up to
+// a few ulps): a screen, so that eq11_rel runs only on intervals whose bound
+// is within a factor 2 of the tolerance and the grading decisions do not
+// depend on the screen.
+struct Eq11Screen {
+  int deg, kind, q;
+  double kq, inv_fq, kp[8], cf[8];
+  Eq11Screen(int deg_, int kind_, double k) : deg(deg_), kind(kind_), q(deg_ + 1) {
+    kp[0] = 1.0;
+    for (int i = 1; i < 8; ++i) kp[i] = kp[i - 1] * k;
+    kq = kp[q < 8 ? q : 7];
+    inv_fq = 1.0 / fact(q);
+    for (int i = 0; i <= q && i < 8; ++i) cf[i] = fact(q) / (fact(i) * fact(q - i)) * fact(i);
+  }
+  double operator()(const std::vector<double>& r, int j) const {
+    const int n = (int)r.size();
+    const int s0 = deg <= 1 ? j : std::min(std::max(j - (deg - 1) / 2, 0), n - 1 - deg);
+    const double h = r[j + 1] - r[j];
+    double om = h * h / 4.0;
+    for (int s = s0; s <= s0 + deg; ++s)
+      if (s != j && s != j + 1) om *= std::max(std::fabs(r[j] - r[s]), std::fabs(r[j + 1] - r[s]));
+    double mq = 0.0;
+    if (kind == GF_EXP) {
+      mq = kq;
+    } else {
+      const double inv_r = 1.0 / r[s0];
+      double ir = inv_r;
+      for (int i = 0; i <= q; ++i, ir *= inv_r) mq += cf[i] * kp[q - i] * ir;
+    }
+    const double b = om * mq * inv_fq;
+    return kind == GF_GREEN ? b * r[j + 1] : b;
+  }
+};
+
 static gf_status place_samples(int kind, int deg, double k, double lo, double hi, double t,
                                const gf_params& p, Placement* out) {
   const double merge = p.merge_t * t;
@@ -156,6 +191,7 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
       if (z > lo) zeros.push_back(z);
     }
     const int nsub = (int)std::lround(1.0 / p.refine_factor);
+    std::vector<double> extra;
     for (double z : zeros) {
       // base intervals meeting the window [z - hw, z + hw] are subdivided
       auto it = std::lower_bound(base.begin(), base.end(), z - hw);
@@ -163,15 +199,19 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
       for (size_t i = i0; i + 1 < base.size() && base[i] < z + hw; ++i) {
         const double a = base[i], b = base[i + 1];
         if (b > z - hw)
-          for (int s = 1; s < nsub; ++s) all.push_back(a + (b - a) * s / nsub);
+          for (int s = 1; s < nsub; ++s) extra.push_back(a + (b - a) * s / nsub);
       }
     }
+    // sorted union of the (sorted) base samples and the refinement samples
+    std::sort(extra.begin(), extra.end());
+    all.resize(base.size() + extra.size());
+    std::merge(base.begin(), base.end(), extra.begin(), extra.end(), all.begin());
     // forced zeros: keep z, drop other samples within `merge` of it
     std::vector<double> kept_zeros;
     for (double z : zeros)
       if (z - lo >= merge && hi - z >= merge) kept_zeros.push_back(z);
     std::vector<double> tmp;
-    tmp.reserve(all.size() + kept_zeros.size());
+    tmp.reserve(all.size());
     for (double x : all) {
       bool drop = false;
       if (x != lo && x != hi) {
@@ -181,10 +221,11 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
       }
       if (!drop) tmp.push_back(x);
     }
-    for (double z : kept_zeros) tmp.push_back(z);
-    all.swap(tmp);
+    all.resize(tmp.size() + kept_zeros.size());
+    std::merge(tmp.begin(), tmp.end(), kept_zeros.begin(), kept_zeros.end(), all.begin());
   }
-  std::sort(all.begin(), all.end());
+  // `all` is sorted here (merges of sorted lists); the sample set is the same
+  // as sorting the union
   all.erase(std::unique(all.begin(), all.end()), all.end());
   while ((int)all.size() < deg + 1) {
     const size_t n = all.size();
@@ -192,10 +233,13 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
     std::sort(all.begin(), all.end());
   }
   if (p.grade) {
+    const Eq11Screen screen(deg, kind, k);
+    const bool exact_only = deg + 1 >= 8;
     for (int pass = 0; pass < 200; ++pass) {
       std::vector<double> add;
       for (int j = 0; j + 1 < (int)all.size(); ++j)
-        if (eq11_rel(all, j, deg, kind, k) > p.table_tol) add.push_back(0.5 * (all[j] + all[j + 1]));
+        if ((exact_only || screen(all, j) > 0.5 * p.table_tol) && eq11_rel(all, j, deg, kind, k) > p.table_tol)
+          add.push_back(0.5 * (all[j] + all[j + 1]));
       if (add.empty()) break;
       all.insert(all.end(), add.begin(), add.end());
       std::sort(all.begin(), all.end());
@@ -241,12 +285,15 @@ gf::TabView gf_table::One::view() const {
   v.c32b = d_c32b;
   v.n_lat = n_lat;
   v.n_sub = n_sub;
-  v.lat_lo = lat_lo;
   v.lat_inv = lat_inv;
+  v.lat_nc = lat_nc;
   v.lat_h = lat_h;
+  v.lat_lo = lat_lo;
   v.lat_a = d_lat_a;
+  v.lat_blob = d_lat_blob;
+  v.n_busy = n_busy;
+  v.n_cmp = n_cmp;
   v.lat_b = d_lat_b;
-  v.lat_sub = d_lat_sub;
   v.n_cells64 = n_cells64;
   v.lo64c = lo64c;
   v.inv64c = inv64c;
@@ -361,7 +408,8 @@ bool params_ok(const gf_params* p) {
   return p && p->table_tol > 0 && p->green_n_per_lambda >= 0 && p->exp_n_per_lambda >= 0 &&
          p->lagrange_degree >= 1 && p->lagrange_degree <= 3 && p->refine_factor > 0 && p->refine_factor <= 1 &&
          p->refine_halfwidth_t >= 0 && p->merge_t >= 0 && p->nphi >= 1 && p->nphi <= 32 && p->nl >= 1 &&
-         p->nl <= 32 && p->eta > 0 && (p->near_fp64 == 0 || p->near_fp64 == 1);
+         p->nl <= 32 && p->eta > 0 && (p->near_fp64 == 0 || p->near_fp64 == 1) &&
+         (p->green_from_exp == 0 || p->green_from_exp == 1);
 }
 
 }  // namespace
@@ -390,6 +438,7 @@ void gf_params_default(gf_params* p) {
   p->nl = 8;
   p->eta = 376.730313668;
   p->near_fp64 = 0;
+  p->green_from_exp = 0;
 }
 
 const char* gf_last_error(void) { return gf::g_err.c_str(); }
@@ -621,19 +670,74 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
 
 namespace {
 
-// FP32 lattice image of a table (the device lookups repeat these float
-// operations exactly): cell of x and sub-cell of x inside cell i.
-int lattice_cell(float x, float lo, float inv) {
-  const float d = x - lo;
-  const float u = d * inv;
-  return (int)u;
+// Device memory of destroyed tables kept for the next table of a similar
+// size on the same device (a table is rebuilt for every range / k; cudaMalloc
+// costs as much as building it). At most kPoolBlocks blocks, kPoolBytes bytes.
+constexpr int kPoolBlocks = 8;
+constexpr size_t kPoolBytes = size_t(1) << 30;
+
+struct ArenaPool {
+  std::mutex mu;
+  struct Block {
+    int device;
+    void* ptr;
+    size_t bytes;
+  };
+  std::vector<Block> blocks;
+  size_t held = 0;
+};
+
+ArenaPool& arena_pool() {
+  static ArenaPool* p = new ArenaPool;  // never destroyed: blocks live until the process exits
+  return *p;
 }
 
-int lattice_sub(float x, float anchor, float inv_w, int nsub) {
-  const float d = x - anchor;
-  const float u = d * inv_w;
-  const int c = (int)u;
-  return c < 0 ? 0 : (c > nsub - 1 ? nsub - 1 : c);
+// A pooled block of at least `bytes` (and at most twice that) on `device`, or null.
+void* arena_take(int device, size_t bytes, size_t* got) {
+  ArenaPool& P = arena_pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  int best = -1;
+  for (int i = 0; i < (int)P.blocks.size(); ++i) {
+    const ArenaPool::Block& b = P.blocks[i];
+    if (b.device == device && b.bytes >= bytes && b.bytes <= 2 * bytes + (1 << 20) &&
+        (best < 0 || b.bytes < P.blocks[best].bytes))
+      best = i;
+  }
+  if (best < 0) return nullptr;
+  void* ptr = P.blocks[best].ptr;
+  *got = P.blocks[best].bytes;
+  P.held -= *got;
+  P.blocks.erase(P.blocks.begin() + best);
+  return ptr;
+}
+
+// Called with no work in flight on the block (the caller synchronized the device).
+void arena_give(int device, void* ptr, size_t bytes) {
+  ArenaPool& P = arena_pool();
+  {
+    std::lock_guard<std::mutex> lock(P.mu);
+    if ((int)P.blocks.size() < kPoolBlocks && P.held + bytes <= kPoolBytes) {
+      P.blocks.push_back(ArenaPool::Block{device, ptr, bytes});
+      P.held += bytes;
+      return;
+    }
+  }
+  cudaFree(ptr);
+}
+
+// FP32 lattice image of a table (the device lookups repeat these float
+// operations exactly): u = fma(x, inv, nc); v = clamp(u + kLatMagic); the
+// cell i is the integer in v, and s = x - fma(i, h, lo) the offset from its
+// anchor.
+struct LatPos {
+  int i;
+  float s;
+};
+
+int32_t float_bits(float f) {
+  int32_t v;
+  std::memcpy(&v, &f, 4);
+  return v;
 }
 
 float bits_float(int32_t v) {
@@ -642,51 +746,85 @@ float bits_float(int32_t v) {
   return f;
 }
 
-struct Lattice {
-  int n = 0;
-  float lo = 0.f, inv = 0.f, h = 0.f;
-  std::vector<int32_t> j;    // interval of a sample-free cell, -1 for a cell holding samples
-  std::vector<float4> a;     // sub-cell headers (cells holding samples), zero elsewhere
-  std::vector<float4> sub;   // sub-cell records
+struct LatMap {
+  float inv, nc, h, lo;
 };
 
-// Cells of width t from r_min (the uniform samples of Eq. 2 sit on their ends).
-// A cell is sample-free when every interior sample lies within a margin of
-// its ends (FP32 rounding of the map and of the samples); R inside such a cell
-// but past a sample at its end is evaluated with the neighbour interval's
-// polynomial, an extrapolation by at most the margin. Cells holding samples
-// get sub-cells narrower than the local spacing, so each holds one sample at
-// most and the bracketing against the FP32 samples is exact.
-gf_status build_lattice(const std::vector<double>& r, double t, Lattice* L) {
+LatPos lattice_pos(float x, const LatMap& M, float vmin, float vmax) {
+  const float u = std::fmaf(x, M.inv, M.nc);
+  float v = u + kLatMagic;
+  v = std::fmin(std::fmax(v, vmin), vmax);
+  const float fi = v - kLatMagic;
+  return LatPos{float_bits(v) - float_bits(kLatMagic), x - std::fmaf(fi, M.h, M.lo)};
+}
+
+// sub-cell of an offset s inside a cell holding samples
+int lattice_sub(float s, float inv_w, int nsub) {
+  const float u = s * inv_w;
+  const int c = (int)u;
+  return c < 0 ? 0 : (c > nsub - 1 ? nsub - 1 : c);
+}
+
+struct Lattice {
+  int n = 0;
+  LatMap map{};
+  std::vector<int32_t> j;     // interval containing the middle of each cell; bit 31: the cell holds samples
+  std::vector<int32_t> busy;  // cells holding samples, ascending
+  std::vector<float4> hdr;    // per busy cell: (first sub-cell, 1/w, count - 1, 0)
+  std::vector<float4> sub;    // sub-cell records (compact interval j0, split, node32[j0], 0)
+  std::vector<int32_t> cmp;   // interval of each compact interval record
+  // the device blob: busy (int32, padded to 16 bytes), hdr, sub, then the
+  // compact interval records (a, b), filled on the device from cmp
+  size_t blob_vec4() const { return (busy.size() + 3) / 4 + busy.size() + sub.size() + 2 * cmp.size(); }
+};
+
+// Shared-memory budget of a lattice image for choosing the finer step.
+constexpr int64_t kLatticeSmemBudget = 192 * 1024;
+
+// Cells of width `step` (t or t / 2) from r_min (the uniform samples of Eq. 2,
+// and the refined ones for t / 2, sit on their ends). A cell is sample-free
+// when every interior sample lies within a margin of its ends (FP32 rounding
+// of the map and of the samples); R inside such a cell but past a sample at
+// its end is evaluated with the neighbour interval's polynomial, an
+// extrapolation by at most the margin. Cells holding samples get sub-cells
+// narrower than the local spacing, so each holds one sample at most and the
+// bracketing against the FP32 samples is exact.
+gf_status build_lattice(const std::vector<double>& r, double step, Lattice* L) {
   const size_t n = r.size();
-  L->lo = (float)r.front();
-  L->h = (float)t;
-  L->inv = (float)(1.0 / t);
+  LatMap& M = L->map;
+  M.lo = (float)r.front();
+  M.h = (float)step;
+  M.inv = (float)(1.0 / step);
+  const float c = (float)((double)M.lo * (double)M.inv + 0.5);
+  M.nc = -c;
   const float hi32 = (float)r.back();
-  if (!((double)(hi32 - L->lo) * L->inv < (double)(1 << 24))) return fail(GF_ERR_RANGE, "table: FP32 lattice too large");
-  L->n = lattice_cell(hi32, L->lo, L->inv) + 1;
+  const double span = ((double)hi32 - (double)M.lo) * (double)M.inv;
+  if (!(span < (double)(1 << 21))) return fail(GF_ERR_RANGE, "table: FP32 lattice too large");
+  const float wide_lo = kLatMagic - (float)(1 << 21), wide_hi = kLatMagic + (float)(1 << 21);
+  L->n = std::max(lattice_pos(hi32, M, wide_lo, wide_hi).i, 0) + 1;
   std::vector<float> x32(n);
   for (size_t j = 0; j < n; ++j) x32[j] = (float)r[j];
   std::vector<int> cell(n, 0);
-  for (size_t j = 0; j < n; ++j) cell[j] = lattice_cell(x32[j], L->lo, L->inv);
+  for (size_t j = 0; j < n; ++j) cell[j] = lattice_pos(x32[j], M, wide_lo, wide_hi).i;
   const double eps = 1e-3 + 8.0 * L->n / 16777216.0;  // margin in cells
   std::vector<char> busy(L->n, 0);
   for (size_t j = 1; j + 1 < n; ++j) {
-    const double v = ((double)x32[j] - (double)L->lo) * (double)L->inv;
-    const double fl = std::floor(v), fr = v - fl;
-    const int64_t i = (int64_t)fl;
-    if (fr > eps && fr < 1.0 - eps && i >= 0 && i < L->n) busy[i] = 1;
+    const double v = (double)x32[j] * (double)M.inv - (double)c;
+    const double ci = std::floor(v + 0.5), d = v - ci;  // d in [-1/2, 1/2)
+    const int64_t i = (int64_t)ci;
+    if (std::fabs(d) < 0.5 - eps && i >= 0 && i < L->n) busy[i] = 1;
   }
-  L->j.assign(L->n, -1);
-  L->a.assign(L->n, make_float4(0.f, 0.f, 0.f, 0.f));
+  L->j.assign(L->n, 0);
+  L->busy.clear();
+  L->hdr.clear();
   L->sub.clear();
+  L->cmp.clear();
+  size_t jm = 0;  // last sample <= the cell's middle (the middles increase with i)
   for (int i = 0; i < L->n; ++i) {
-    if (!busy[i]) {
-      const double mid = (double)L->lo + (i + 0.5) / (double)L->inv;
-      int64_t j = (int64_t)(std::upper_bound(r.begin(), r.end(), mid) - r.begin()) - 1;
-      L->j[i] = (int32_t)std::min<int64_t>(std::max<int64_t>(j, 0), (int64_t)n - 2);
-      continue;
-    }
+    const double mid = ((double)i + (double)c) / (double)M.inv;
+    while (jm + 1 < n && r[jm + 1] <= mid) ++jm;
+    L->j[i] = (int32_t)std::min<size_t>(jm, n - 2);
+    if (!busy[i]) continue;
     // interior samples whose FP32 cell is i: [ja, jb)
     size_t ja = 1;
     {
@@ -700,33 +838,38 @@ gf_status build_lattice(const std::vector<double>& r, double t, Lattice* L) {
     }
     size_t jb = ja;
     while (jb < n - 1 && cell[jb] == i) ++jb;
-    const float anchor = std::fmaf((float)i, L->h, L->lo);
-    double w = t;
+    const float vmin = kLatMagic + (float)i, vmax = vmin;
+    double w = step;
     for (size_t jj = (ja > 0 ? ja - 1 : 0); jj <= jb && jj + 1 < n; ++jj) w = std::min(w, r[jj + 1] - r[jj]);
     w *= 0.9;
     int nsub = 0;
     float inv_w = 0.f;
     bool ok = false;
+    auto sub_of = [&](size_t jj) { return lattice_sub(lattice_pos(x32[jj], M, vmin, vmax).s, inv_w, nsub); };
     for (int attempt = 0; attempt < 30 && !ok; ++attempt, w *= 0.5) {
       inv_w = (float)(1.0 / w);
-      nsub = (int)(1.1 * t / w) + 2;
+      nsub = (int)(1.1 * step / w) + 2;
       if (nsub > 65536) break;
       ok = true;
       for (size_t jj = ja; jj + 1 < jb; ++jj)
-        if (lattice_sub(x32[jj], anchor, inv_w, nsub) >= lattice_sub(x32[jj + 1], anchor, inv_w, nsub)) ok = false;
+        if (sub_of(jj) >= sub_of(jj + 1)) ok = false;
     }
     if (!ok) return fail(GF_ERR_RANGE, "table: samples closer than the FP32 resolution");
+    // intervals this cell can reach: ja - 1 .. jb - 1, stored as a compact run
     const int first = (int)L->sub.size();
+    const int cbase = (int)L->cmp.size() - ((int)ja - 1);
+    for (size_t jv = ja - 1; jv < jb; ++jv) L->cmp.push_back((int32_t)jv);
     size_t jj = ja;
-    for (int c = 0; c < nsub; ++c) {
-      while (jj < jb && lattice_sub(x32[jj], anchor, inv_w, nsub) < c) ++jj;
-      const int j0 = (int)jj - 1;  // interval below every sample of sub-cell c and later
-      const bool has = jj < jb && lattice_sub(x32[jj], anchor, inv_w, nsub) == c;
-      L->sub.push_back(make_float4(bits_float(j0), has ? x32[jj] : INFINITY, x32[j0], 0.f));
+    for (int cc = 0; cc < nsub; ++cc) {
+      while (jj < jb && sub_of(jj) < cc) ++jj;
+      const int j0 = (int)jj - 1;  // interval below every sample of sub-cell cc and later
+      const bool has = jj < jb && sub_of(jj) == cc;
+      L->sub.push_back(make_float4(bits_float(cbase + j0), has ? x32[jj] : INFINITY, x32[j0], 0.f));
     }
-    L->a[i] = make_float4(bits_float(kLatticeSubMark), bits_float(first), inv_w, bits_float(nsub - 1));
+    L->j[i] |= (int32_t)0x80000000u;
+    L->busy.push_back(i);
+    L->hdr.push_back(make_float4(bits_float(first), inv_w, bits_float(nsub - 1), 0.f));
   }
-  if (L->sub.empty()) L->sub.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
   return GF_OK;
 }
 
@@ -751,6 +894,8 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
   const int n_green = p->green_n_per_lambda ? p->green_n_per_lambda : 1000;
   cudaStream_t s = (cudaStream_t)stream;
   gf_table::One* ones[2] = {&T->green, &T->exp};
+  Lattice lat[2];
+  // ---- host: samples (Section II.B) and the FP32 lattice image of both tables
   for (int which = 0; which < 2; ++which) {
     gf_table::One& o = *ones[which];
     o.kind = which == 0 ? GF_GREEN : GF_EXP;
@@ -759,61 +904,124 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     Placement pl;
     gf_status st = place_samples(o.kind, o.degree, k, r_min, r_max, t, *p, &pl);
     if (st) return st;
-    o.r = pl.r;
-    o.zflag = pl.zflag;
+    o.r = std::move(pl.r);
+    o.zflag = std::move(pl.zflag);
     o.dr = pl.dr;
     o.n_hash = pl.n_hash;
-    const size_t n = o.r.size();
-    Lattice lat;
-    if ((st = build_lattice(o.r, t, &lat))) {
-      gf_table_destroy(T.release());
-      return st;
-    }
-    o.n_lat = lat.n;
-    o.n_sub = (int)lat.sub.size();
-    o.lat_lo = lat.lo;
-    o.lat_inv = lat.inv;
-    o.lat_h = lat.h;
+    // lattice step: t / 2 (the refined spacing, so refinement windows hold no
+    // sample inside a cell) when that image fits the shared-memory budget,
+    // else t
+    const double rec = o.degree > 1 ? 32.0 : 16.0;
+    const double h = p->refine && (r_max - r_min) / (0.5 * t) * rec <= (double)kLatticeSmemBudget &&
+                             std::fabs(p->refine_factor - 0.5) < 1e-12
+                         ? 0.5 * t
+                         : t;
+    if ((st = build_lattice(o.r, h, &lat[which]))) return st;
+    o.n_lat = lat[which].n;
+    o.n_busy = (int)lat[which].busy.size();
+    o.n_sub = (int)lat[which].sub.size();
+    o.n_cmp = (int)lat[which].cmp.size();
+    o.lat_inv = lat[which].map.inv;
+    o.lat_nc = lat[which].map.nc;
+    o.lat_h = lat[which].map.h;
+    o.lat_lo = lat[which].map.lo;
     o.lo64c = r_min;
     o.inv64c = 1.0 / (0.99 * o.dr);
     o.n_cells64 = (int)std::floor((r_max - r_min) * o.inv64c) + 1;
-    if ((st = dev_alloc(&o.d_node64, n)) || (st = dev_alloc(&o.d_zflag, n)) || (st = dev_alloc(&o.d_fval, 2 * n)) ||
-        (st = dev_alloc(&o.d_c64, 4 * n)) || (st = dev_alloc(&o.d_node32, n)) || (st = dev_alloc(&o.d_c32a, n)) ||
-        (st = dev_alloc(&o.d_c32b, n)) || (st = dev_alloc(&o.d_hash, (size_t)o.n_hash)) ||
-        (st = dev_alloc(&o.d_lat_j, (size_t)o.n_lat)) || (st = dev_alloc(&o.d_lat_a, (size_t)o.n_lat)) ||
-        (st = dev_alloc(&o.d_lat_b, (size_t)o.n_lat)) || (st = dev_alloc(&o.d_lat_sub, (size_t)o.n_sub)) ||
-        (st = dev_alloc(&o.d_cells64, (size_t)o.n_cells64)) || (st = dev_alloc(&o.d_flag, 1))) {
-      gf_table_destroy(T.release());
-      return st;
-    }
-    cudaError_t e = cudaMemcpyAsync(o.d_node64, o.r.data(), n * 8, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(o.d_zflag, o.zflag.data(), n, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(o.d_flag, 0, sizeof(int), s);
+    // the FP64 cell image holds one interior sample per cell at most (the
+    // device cell map, repeated here: no contraction in this file)
+    for (size_t j = 1; j + 2 < o.r.size(); ++j)
+      if ((int)((o.r[j] - o.lo64c) * o.inv64c) == (int)((o.r[j + 1] - o.lo64c) * o.inv64c))
+        return fail(GF_ERR_RANGE, "table: two samples in one FP64 hash cell");
+  }
+  // ---- one device allocation: the uploaded arrays of both tables first (one
+  // host-to-device copy), then the arrays the kernels compute
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    return o;
+  };
+  size_t o_node64[2], o_zflag[2], o_lat_j[2], o_lat_cmp[2], o_lat_blob[2];
+  for (int w = 0; w < 2; ++w) {
+    const gf_table::One& o = *ones[w];
+    o_node64[w] = take(o.r.size() * 8);
+    o_zflag[w] = take(o.r.size());
+    o_lat_j[w] = take((size_t)o.n_lat * 4);
+    o_lat_cmp[w] = take((size_t)o.n_cmp * 4);
+    o_lat_blob[w] = take(lat[w].blob_vec4() * 16);
+  }
+  const size_t upload = off;
+  size_t o_fval[2], o_c64[2], o_node32[2], o_c32a[2], o_c32b[2], o_hash[2], o_lat_a[2], o_lat_b[2], o_cells64[2];
+  for (int w = 0; w < 2; ++w) {
+    const gf_table::One& o = *ones[w];
+    const size_t n = o.r.size();
+    o_fval[w] = take(2 * n * 8);
+    o_c64[w] = take(4 * n * sizeof(double2));
+    o_node32[w] = take(n * 4);
+    o_c32a[w] = take(n * 16);
+    o_c32b[w] = take(n * 16);
+    o_hash[w] = take((size_t)o.n_hash * 4);
+    o_lat_a[w] = take((size_t)o.n_lat * 16);
+    o_lat_b[w] = take((size_t)o.n_lat * 16);
+    o_cells64[w] = take((size_t)o.n_cells64 * sizeof(Cell64));
+  }
+  std::vector<unsigned char> hbuf(upload, 0);
+  for (int w = 0; w < 2; ++w) {
+    const gf_table::One& o = *ones[w];
+    std::memcpy(&hbuf[o_node64[w]], o.r.data(), o.r.size() * 8);
+    std::memcpy(&hbuf[o_zflag[w]], o.zflag.data(), o.r.size());
+    std::memcpy(&hbuf[o_lat_j[w]], lat[w].j.data(), (size_t)o.n_lat * 4);
+    std::memcpy(&hbuf[o_lat_cmp[w]], lat[w].cmp.data(), (size_t)o.n_cmp * 4);
+    unsigned char* blob = &hbuf[o_lat_blob[w]];
+    std::memcpy(blob, lat[w].busy.data(), (size_t)o.n_busy * 4);
+    blob += ((size_t)o.n_busy + 3) / 4 * 16;
+    std::memcpy(blob, lat[w].hdr.data(), (size_t)o.n_busy * 16);
+    blob += (size_t)o.n_busy * 16;
+    std::memcpy(blob, lat[w].sub.data(), (size_t)o.n_sub * 16);  // compact records follow, filled on the device
+  }
+  size_t got = 0;
+  unsigned char* base = static_cast<unsigned char*>(arena_take(T->device, off, &got));
+  cudaError_t e = cudaSuccess;
+  if (!base) {
+    e = cudaMalloc((void**)&base, off);
+    if (e != cudaSuccess) return cuda_fail(e, "gf_table_create: cudaMalloc");
+    got = off;
+  }
+  T->d_arena = base;
+  T->arena_bytes = got;
+  for (int w = 0; w < 2; ++w) {
+    gf_table::One& o = *ones[w];
+    o.d_node64 = reinterpret_cast<double*>(base + o_node64[w]);
+    o.d_zflag = reinterpret_cast<int8_t*>(base + o_zflag[w]);
+    o.d_lat_j = reinterpret_cast<int32_t*>(base + o_lat_j[w]);
+    o.d_lat_cmp = reinterpret_cast<int32_t*>(base + o_lat_cmp[w]);
+    o.d_lat_blob = reinterpret_cast<float4*>(base + o_lat_blob[w]);
+    o.d_lat_a = reinterpret_cast<float4*>(base + o_lat_a[w]);
+    o.d_fval = reinterpret_cast<double*>(base + o_fval[w]);
+    o.d_c64 = reinterpret_cast<double2*>(base + o_c64[w]);
+    o.d_node32 = reinterpret_cast<float*>(base + o_node32[w]);
+    o.d_c32a = reinterpret_cast<float4*>(base + o_c32a[w]);
+    o.d_c32b = reinterpret_cast<float4*>(base + o_c32b[w]);
+    o.d_hash = reinterpret_cast<int32_t*>(base + o_hash[w]);
+    o.d_lat_b = reinterpret_cast<float4*>(base + o_lat_b[w]);
+    o.d_cells64 = reinterpret_cast<Cell64*>(base + o_cells64[w]);
+  }
+  // ---- device: values, coefficients, hash and images of both tables
+  e = cudaMemcpyAsync(base, hbuf.data(), upload, cudaMemcpyHostToDevice, s);
+  for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+    gf_table::One& o = *ones[w];
+    const int n = (int)o.r.size();
+    e = launch_table_image(o.kind, k, o.degree, n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a, o.d_c32b,
+                           o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells64, o.lo64c, o.inv64c,
+                           o.d_cells64, s);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(o.d_lat_j, lat.j.data(), (size_t)o.n_lat * 4, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(o.d_lat_a, lat.a.data(), (size_t)o.n_lat * 16, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(o.d_lat_b, 0, (size_t)o.n_lat * 16, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(o.d_lat_sub, lat.sub.data(), (size_t)o.n_sub * 16, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = launch_table_image(o.kind, k, o.degree, (int)n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a,
-                             o.d_c32b, o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells64, o.lo64c,
-                             o.inv64c, o.d_cells64, o.d_flag, s);
-    if (e == cudaSuccess)
-      e = launch_table_lattice(o.degree, (int)n, o.d_node64, o.d_fval, o.n_lat, o.lat_lo, o.lat_h, o.d_lat_j,
+      e = launch_table_lattice(o.view(), o.degree, o.d_fval, o.d_lat_j, o.d_lat_cmp, o.kind == GF_GREEN,
                                o.d_lat_a, o.d_lat_b, s);
-    int flag = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, o.d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      gf_table_destroy(T.release());
-      return cuda_fail(e, "gf_table_create");
-    }
-    if (flag) {
-      gf_table_destroy(T.release());
-      return fail(GF_ERR_RANGE, "table: two samples in one FP64 hash cell");
-    }
+  }
+  if (e != cudaSuccess) {
+    gf_table_destroy(T.release());
+    return cuda_fail(e, "gf_table_create");
   }
   *out = T.release();
   return GF_OK;
@@ -834,6 +1042,7 @@ gf_status gf_table_nodes(const gf_table* t, int kind, double* r, double* fre, do
   if (st) return st;
   const gf_table::One& o = t->get(kind);
   const size_t n = o.r.size();
+  GF_CUDA(cudaDeviceSynchronize());  // the table's kernels may still run on the creation stream
   if (r) std::memcpy(r, o.r.data(), n * 8);
   if (fre || fim) {
     std::vector<double> f(2 * n);
@@ -861,11 +1070,15 @@ gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* 
 
 gf_status gf_table_destroy(gf_table* t) {
   if (!t) return GF_OK;
-  for (gf_table::One* o : {&t->green, &t->exp}) {
-    void* ptrs[] = {o->d_node64, o->d_zflag, o->d_fval,    o->d_c64,     o->d_node32,    o->d_c32a,  o->d_c32b,
-                    o->d_hash,   o->d_lat_j, o->d_lat_a,   o->d_lat_b,   o->d_lat_sub,   o->d_cells64, o->d_flag};
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
+  if (t->d_arena) {
+    // like cudaFree, wait for work that may still read the table; then keep
+    // the memory for the next table
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != t->device) cudaSetDevice(t->device);
+    cudaDeviceSynchronize();
+    arena_give(t->device, t->d_arena, t->arena_bytes);
+    if (cur >= 0 && cur != t->device) cudaSetDevice(cur);
   }
   delete t;
   return GF_OK;
@@ -901,7 +1114,8 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
     te = table->exp.view();
   }
   if (parts & GF_PART_REGULAR)
-    GF_CUDA(launch_fill_regular(g, table ? &tg : nullptr, precision, k, p->eta, Z, ldz, s));
+    GF_CUDA(launch_fill_regular(g, table ? (p->green_from_exp ? &te : &tg) : nullptr, p->green_from_exp != 0,
+                                precision, k, p->eta, Z, ldz, s));
   if (!(parts & GF_PART_NEAR)) return GF_OK;
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
   gauss_legendre(p->nphi, gx_phi, gw_phi);
@@ -924,6 +1138,7 @@ gf_status gf_fill_backward(const gf_mesh* mc, double k, const gf_params* p, cons
                            const void* gZ, int64_t ldg, double* dxyz, double* dk, void* stream) {
   if (!mc || !params_ok(p) || !gZ || !dxyz || !dk) return fail(GF_ERR_ARG, "gf_fill_backward: bad argument");
   if (precision != GF_FP32) return fail(GF_ERR_ARG, "gf_fill_backward: GF_FP32 only");
+  if (p->green_from_exp) return fail(GF_ERR_ARG, "gf_fill_backward: green_from_exp must be 0");
   if (!(k > 0) || ldg < mc->ne) return fail(GF_ERR_ARG, "gf_fill_backward: need k > 0 and ldg >= ne");
   gf_mesh* m = const_cast<gf_mesh*>(mc);
   gf_status st = check_device(m->device);

@@ -70,29 +70,39 @@ struct TabView {
   const float* node32;     // [n_nodes]: FP32 anchors
   const float4* c32a;      // [n_nodes-1]: (c0re, c0im, c1re, c1im) about node32[j]
   const float4* c32b;      // [n_nodes-1]: (c2re, c2im, c3re, c3im)
-  // FP32 lattice image. Cells of the base spacing t on the map
-  // i(x) = trunc((x - lat_lo) * lat_inv), aligned with the uniform samples
-  // r_min + i t (Eq. 2). A cell with no sample inside (farther than a rounding
-  // margin from its ends) lies in one interval: lat_a/lat_b hold that
-  // interval's polynomial about A_i = fma(i, lat_h, lat_lo), so one lookup is
-  // two 16-byte records. A cell holding samples (refinement near zeros,
-  // grading, r_max) has lat_a = (kLatticeSubMark, first sub-cell, 1/w, count-1):
-  // sub-cell c = trunc((x - A_i) / w) holds (j0 as int bits, split, node32[j0],
-  // 0), x lies in interval j0 if x < split, else in j0 + 1 (anchor split), and
-  // the coefficients come from c32a/c32b.
-  int n_lat, n_sub;
-  float lat_lo, lat_inv, lat_h;
-  const float4* lat_a;     // [n_lat]: (c0re, c0im, c1re, c1im) about A_i, or a sub-cell header
+  // FP32 lattice image. Cells of step h (the base spacing t of Eq. 2, or the
+  // refined t / 2) from r_min, aligned with the samples r_min + i h: cell i
+  // holds the x with rint(fma(x, lat_inv, lat_nc)) = i (lat_nc = -(r_min / h +
+  // 1/2)), found without a conversion instruction (kLatMagic), and its anchor
+  // is A_i = fma(i, lat_h, lat_lo). lat_a/lat_b hold, for every cell, the
+  // polynomial (in s = x - A_i) of the interval that contains the cell's
+  // middle, so one lookup is two 16-byte records (one for the linear Exp
+  // table). A cell with no sample inside (farther than a rounding margin from
+  // its ends) lies in that interval. A cell holding samples (a forced zero,
+  // grading, r_max) is flagged by the lowest mantissa bit of its last record
+  // word (c3im of the Green table, c1im of the Exp table; clear elsewhere);
+  // the blob lists those cells (ascending), a header per cell (first
+  // sub-cell, 1/w, count - 1), sub-cells trunc(s / w) = (compact interval j0,
+  // split, node32[j0], 0) -- x lies in j0 if x < split, else in j0 + 1 whose
+  // anchor is split -- and the compact interval records about node32 (a, b).
+  int n_lat, n_busy, n_sub, n_cmp;
+  float lat_inv, lat_nc, lat_h, lat_lo;
+  const float4* lat_a;     // [n_lat]: (c0re, c0im, c1re, c1im) about A_i
   const float4* lat_b;     // [n_lat]: (c2re, c2im, c3re, c3im)
-  const float4* lat_sub;   // [n_sub]
+  const float4* lat_blob;  // [blob_vec4()]
+  __host__ __device__ size_t blob_vec4() const { return ((size_t)n_busy + 3) / 4 + n_busy + n_sub + 2 * (size_t)n_cmp; }
   int n_cells64;  // FP64 image of the Eq. (6) hash: cells of width 0.99 dr, one sample at most each
   double lo64c, inv64c;
   const Cell64* cells64;
-  size_t smem32_bytes() const { return (size_t)n_lat * 32 + (size_t)n_sub * 16; }
+  // shared-memory image of the lattice for a lookup of degree deg (lat_b only for deg > 1)
+  size_t smem32_bytes(int deg) const { return (size_t)n_lat * (deg > 1 ? 32 : 16) + blob_vec4() * 16; }
 };
 
 // Marker (a quiet-NaN bit pattern) of a lattice cell that holds samples.
 constexpr int32_t kLatticeSubMark = 0x7FC00001;
+// 1.5 * 2^23: for |u| < 2^22, u + kLatMagic rounds u to an integer held in
+// the low mantissa bits (the lattice index without a conversion instruction).
+constexpr float kLatMagic = 12582912.0f;
 
 // Regular work units of a mesh of nt triangles: (p, 32 consecutive q) over the
 // 32 x 32 triangle block pairs bp <= bq, 32 units per block pair; each
@@ -124,16 +134,19 @@ cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, cons
                                const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
                                float4* c32b, double* fval, int n_hash, double r_lo, double dr,
                                int32_t* hash, int n_cells64, double lo64c, double inv64c, Cell64* cells64,
-                               int* flag, cudaStream_t s);
-// Coefficients of the sample-free lattice cells (lat_j[i] >= 0: interval of cell i).
-cudaError_t launch_table_lattice(int degree, int n_nodes, const double* node64, const double* fval, int n_lat,
-                                 float lat_lo, float lat_h, const int32_t* lat_j, float4* lat_a, float4* lat_b,
-                                 cudaStream_t s);
+                               cudaStream_t s);
+// Lattice records (lat_j[i]: interval of cell i's middle, bit 31 set for a
+// cell holding samples) and the compact interval records of the blob (cmp);
+// flag_in_b: the flag bit sits in lat_b (Green) or lat_a (Exp).
+cudaError_t launch_table_lattice(const TabView& v, int degree, const double* fval, const int32_t* lat_j,
+                                 const int32_t* cmp, bool flag_in_b, float4* lat_a, float4* lat_b, cudaStream_t s);
 cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s);
-cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int precision, double k,
+// table: the Green table view, or with from_exp the Exp table view (e^{-jkR}
+// from the linear table times 1/R); NULL = direct evaluation.
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
                                 double eta, void* Z, int64_t ldz, cudaStream_t s);
 cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k,
                              double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
@@ -196,13 +209,15 @@ struct gf_mesh {
 struct gf_table {
   int device;
   double k, r_lo, r_hi;
+  void* d_arena = nullptr;  // one device allocation holding every array of both tables
+  size_t arena_bytes = 0;
   struct One {
     int kind, degree;
     std::vector<double> r;        // host sample positions
     std::vector<int8_t> zflag;    // 1: real part is an exact zero, 2: imaginary part
     double dr;
     int64_t n_hash;
-    double* d_node64 = nullptr;
+    double* d_node64 = nullptr;   // device arrays: views into the table's arena
     int8_t* d_zflag = nullptr;
     double* d_fval = nullptr;     // [n][2] sample values
     double2* d_c64 = nullptr;
@@ -210,16 +225,16 @@ struct gf_table {
     float4* d_c32a = nullptr;
     float4* d_c32b = nullptr;
     int32_t* d_hash = nullptr;
-    int n_lat = 0, n_sub = 0;
-    float lat_lo = 0.f, lat_inv = 0.f, lat_h = 0.f;
+    int n_lat = 0, n_busy = 0, n_sub = 0, n_cmp = 0;
+    float lat_inv = 0.f, lat_nc = 0.f, lat_h = 0.f, lat_lo = 0.f;
     int32_t* d_lat_j = nullptr;
     float4* d_lat_a = nullptr;
     float4* d_lat_b = nullptr;
-    float4* d_lat_sub = nullptr;
+    int32_t* d_lat_cmp = nullptr;
+    float4* d_lat_blob = nullptr;
     int n_cells64 = 0;
     double lo64c = 0, inv64c = 0;
     gf::Cell64* d_cells64 = nullptr;
-    int* d_flag = nullptr;
     gf::TabView view() const;
   } green, exp;
   const One& get(int kind) const { return kind == GF_GREEN ? green : exp; }

@@ -181,20 +181,53 @@ __global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, do
 struct Tab32 {  // FP32 view (shared or global memory; possibly a window of the lattice)
   const float4* la;   // lattice records, indexed by the global cell number
   const float4* lb;
-  const float4* sub;  // sub-cells of the cells holding samples
-  const float4* ga;   // interval records about node32 (cells holding samples)
-  const float4* gb;
-  int i_min, i_max;   // cells present (the whole lattice, or a window)
-  float lo, inv, h;
+  const int* busy;    // the blob: cells holding samples (ascending), their headers,
+  const float4* hdr;  // sub-cells and compact interval records
+  const float4* sub;
+  const float4* ca;
+  const float4* cb;
+  int n_busy;
+  float vmin, vmax;   // kLatMagic + first / last cell present (the whole lattice, or a window)
+  float inv, nc, h, lo;
 };
 
-__device__ __forceinline__ Tab32 tab32(const TabView& t) {
-  return Tab32{t.lat_a, t.lat_b, t.lat_sub, t.c32a, t.c32b, 0, t.n_lat - 1, t.lat_lo, t.lat_inv, t.lat_h};
+// Points a view's blob pointers into a copy of the blob (global or shared).
+__device__ __forceinline__ void tab32_blob(Tab32& T, const TabView& t, const float4* blob) {
+  T.busy = reinterpret_cast<const int*>(blob);
+  T.hdr = blob + (t.n_busy + 3) / 4;
+  T.sub = T.hdr + t.n_busy;
+  T.ca = T.sub + t.n_sub;
+  T.cb = T.ca + t.n_cmp;
+  T.n_busy = t.n_busy;
 }
 
-// lattice cell of x; the table builder uses the same rounded operations
-__device__ __forceinline__ int cell32_of(float x, float lo, float inv) {
-  return __float2int_rz(__fmul_rn(__fsub_rn(x, lo), inv));
+__device__ __forceinline__ Tab32 tab32(const TabView& t) {
+  Tab32 T;
+  T.la = t.lat_a;
+  T.lb = t.lat_b;
+  tab32_blob(T, t, t.lat_blob);
+  T.vmin = kLatMagic;
+  T.vmax = kLatMagic + (float)(t.n_lat - 1);
+  T.inv = t.lat_inv;
+  T.nc = t.lat_nc;
+  T.h = t.lat_h;
+  T.lo = t.lat_lo;
+  return T;
+}
+
+// Lattice cell of R (without a conversion instruction) and the exact offset
+// s = R - A_i from its anchor; the table builder repeats these float
+// operations.
+struct LatPos {
+  int i;
+  float s;
+};
+
+__device__ __forceinline__ LatPos lat_pos(const Tab32& T, float R) {
+  const float u = __fmaf_rn(R, T.inv, T.nc);
+  const float v = fminf(fmaxf(__fadd_rn(u, kLatMagic), T.vmin), T.vmax);
+  const float fi = __fsub_rn(v, kLatMagic);
+  return LatPos{__float_as_int(v) - __float_as_int(kLatMagic), __fsub_rn(R, __fmaf_rn(fi, T.h, T.lo))};
 }
 
 // e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 lattice image: the
@@ -202,21 +235,7 @@ __device__ __forceinline__ int cell32_of(float x, float lo, float inv) {
 // polynomial directly; a cell that holds samples adds one sub-cell record
 // (exact bracketing) and the interval's own record.
 template <int DEG>
-__device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
-  const int i = min(max(cell32_of(R, T.lo, T.inv), T.i_min), T.i_max);
-  float4 a = T.la[i];
-  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (DEG > 1) b = T.lb[i];
-  float s = __fsub_rn(R, __fmaf_rn((float)i, T.h, T.lo));
-  if (__float_as_int(a.x) == kLatticeSubMark) {
-    const int c = __float_as_int(a.y) + min(max(__float2int_rz(__fmul_rn(s, a.z)), 0), __float_as_int(a.w));
-    const float4 rec = T.sub[c];
-    const bool up = R >= rec.y;
-    const int j = __float_as_int(rec.x) + (up ? 1 : 0);
-    s = R - (up ? rec.y : rec.z);
-    a = T.ga[j];
-    if (DEG > 1) b = T.gb[j];
-  }
+__device__ __forceinline__ float2 horner32(float s, float4 a, float4 b) {
   if (DEG == 1) return make_float2(fmaf(s, a.z, a.x), fmaf(s, a.w, a.y));
   float re = fmaf(s, b.z, b.x), im = fmaf(s, b.w, b.y);
   re = fmaf(s, re, a.z);
@@ -224,6 +243,56 @@ __device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
   re = fmaf(s, re, a.x);
   im = fmaf(s, im, a.y);
   return make_float2(re, im);
+}
+
+// Branch-free part: the cell's record (the polynomial of the interval at the
+// cell's middle); *slow is set when the cell holds samples, where this value
+// is exact only on the middle interval.
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_fast(const Tab32& T, float R, bool* slow) {
+  const LatPos q = lat_pos(T, R);
+  const float4 a = T.la[q.i];
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DEG > 1) b = T.lb[q.i];
+  *slow = (__float_as_int(DEG > 1 ? b.w : a.w) & 1) != 0;
+  return horner32<DEG>(q.s, a, b);
+}
+
+// Cells holding samples: the cell's place in the busy list (kept in the low
+// bits of c3re for the Green table, in lat_b.x for the Exp table; a binary
+// search for lists longer than kOrdinalMax), its header, the sub-cell, then
+// the compact interval record about node32.
+constexpr int kOrdinalMax = 0xFFF;
+
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float R) {
+  const LatPos q = lat_pos(T, R);
+  int lo = DEG > 1 ? (__float_as_int(T.lb[q.i].z) & kOrdinalMax) : __float_as_int(T.lb[q.i].x);
+  if (lo >= kOrdinalMax) {
+    lo = 0;
+    int hi = T.n_busy - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (T.busy[mid] < q.i) lo = mid + 1;
+      else hi = mid;
+    }
+  }
+  const float4 h = T.hdr[lo];
+  const int c = __float_as_int(h.x) + min(max(__float2int_rz(__fmul_rn(q.s, h.y)), 0), __float_as_int(h.z));
+  const float4 rec = T.sub[c];
+  const bool up = R >= rec.y;
+  const int j = __float_as_int(rec.x) + (up ? 1 : 0);
+  const float4 a = T.ca[j];
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DEG > 1) b = T.cb[j];
+  return horner32<DEG>(R - (up ? rec.y : rec.z), a, b);
+}
+
+template <int DEG>
+__device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
+  bool slow;
+  const float2 f = lookup32_fast<DEG>(T, R, &slow);
+  return slow ? lookup32_slow<DEG>(T, R) : f;
 }
 
 // FP64 lookup through the FP64 cell image (same construction as the FP32
@@ -253,7 +322,7 @@ __device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
 }
 
 __global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_cells, double lo, double inv,
-                                Cell64* cells, int* flag) {
+                                Cell64* cells) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= n_cells) return;
   auto first_at_or_after = [&](int cc) {
@@ -265,9 +334,7 @@ __global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_
     }
     return a;
   };
-  const int a = first_at_or_after(c);
-  const int b = first_at_or_after(c + 1);
-  if (b - a > 1) atomicOr(flag, 2);
+  const int a = first_at_or_after(c);  // cells hold one interior sample at most (checked on the host)
   Cell64 rec;
   rec.j0 = a - 1;
   rec.split = (a < n - 1 && cell64_of(node64[a], lo, inv) == c) ? node64[a] : INFINITY;
@@ -276,19 +343,45 @@ __global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_
   cells[c] = rec;
 }
 
-// Lattice records of the sample-free cells: the interval's polynomial about
-// A_i = fma(i, h, lo), the anchor the lookups recompute.
-__global__ void k_table_lattice(int deg, int n, const double* __restrict__ r, const double* __restrict__ f, int n_lat,
-                                float lo, float h, const int32_t* __restrict__ lat_j, float4* la, float4* lb) {
+// Lattice records: the polynomial of the interval at the cell's middle about
+// the cell anchor A_i = fma(i, h, lo) (the anchor the lookups recompute),
+// with the flag bit of the cells holding samples.
+__global__ void k_table_lattice(TabView v, int deg, const double* __restrict__ r, const double* __restrict__ f,
+                                const int32_t* __restrict__ lat_j, const int32_t* __restrict__ cmp, bool flag_in_b,
+                                float4* la, float4* lb) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_lat) return;
-  const int j = lat_j[i];
-  if (j < 0) return;
-  const float A = __fmaf_rn((float)i, h, lo);
+  if (i < v.n_cmp) {  // compact interval records of the blob
+    float4* ca = const_cast<float4*>(v.lat_blob) + (v.n_busy + 3) / 4 + v.n_busy + v.n_sub;
+    ca[i] = v.c32a[cmp[i]];
+    ca[v.n_cmp + i] = v.c32b[cmp[i]];
+  }
+  if (i >= v.n_lat) return;
+  const float A = __fmaf_rn((float)i, v.lat_h, v.lat_lo);
+  const int jb = lat_j[i];
   double cre[4], cim[4];
-  interval_poly(deg, n, r, f, j, (double)A, cre, cim);
-  la[i] = make_float4((float)cre[0], (float)cim[0], (float)cre[1], (float)cim[1]);
-  lb[i] = make_float4((float)cre[2], (float)cim[2], (float)cre[3], (float)cim[3]);
+  interval_poly(deg, v.n_nodes, r, f, jb & 0x7fffffff, (double)A, cre, cim);
+  float4 a = make_float4((float)cre[0], (float)cim[0], (float)cre[1], (float)cim[1]);
+  float4 b = make_float4((float)cre[2], (float)cim[2], (float)cre[3], (float)cim[3]);
+  // flag bit: the lowest mantissa bit of the last word (changes it by one ulp at most)
+  const int busy = (int)(((unsigned)jb) >> 31);
+  float& w = flag_in_b ? b.w : a.w;
+  w = __int_as_float((__float_as_int(w) & ~1) | busy);
+  if (busy) {  // the cell's place in the busy list, for the exact path
+    const int* list = reinterpret_cast<const int*>(v.lat_blob);
+    int lo = 0, hi = v.n_busy - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (list[mid] < i) lo = mid + 1;
+      else hi = mid;
+    }
+    const int ord = min(lo, kOrdinalMax);
+    if (flag_in_b)  // low 12 bits of c3re: a relative change below 2^-11 of the smallest term
+      b.z = __int_as_float((__float_as_int(b.z) & ~kOrdinalMax) | ord);
+    else  // lat_b is not part of a linear lookup
+      b.x = __int_as_float(ord);
+  }
+  la[i] = a;
+  lb[i] = b;
 }
 
 template <int DEG>
@@ -494,7 +587,17 @@ struct KSum {  // Kahan-compensated FP32 sum
 // per SM holds it), 256 otherwise.
 // One warp task of the regular-pair fill: test triangle p, source triangles
 // q0..q0+31 (one per lane).
-template <int M, bool TABLE>
+// Green value source of the regular-pair kernels.
+enum GreenMode : int {
+  kDirect = 0,    // sincospi of k R / pi, times 1/R
+  kLagrange = 1,  // e^{-jkR}/R from the Green table (Lagrange, Section II.C)
+  kExpOverR = 2,  // e^{-jkR} from the Exp table (linear), times 1/R
+};
+
+// DEFER: lookups in the hot loop are branch-free and the rare evaluations in
+// lattice cells holding samples are corrected after it (tables with few such
+// cells); otherwise each lookup branches to the exact path at once.
+template <int M, int MODE, bool DEFER = true>
 __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
                                                float2* Z, int64_t ldz, int p, int q0, int lane) {
   const int q = min(q0 + lane, g.nt - 1);
@@ -506,21 +609,37 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
 #pragma unroll
   for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
   KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
+  unsigned amask = 0;  // test points whose row met a lattice cell holding samples
+  float4 al_next = g.pts32[p];
 #pragma unroll 1
   for (int a = 0; a < M; ++a) {
-    const float4 al = g.pts32[(size_t)a * g.nt + p];
+    const float4 al = al_next;
+    if (a + 1 < M) al_next = g.pts32[(size_t)(a + 1) * g.nt + p];  // issued a whole iteration early
     const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+    // Green values of the M source points: branch-free lookups accumulated at
+    // once (every load of the row in flight together); a row that met a
+    // lattice cell holding samples is corrected after the loop
     float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
+    bool flagged = false;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
       const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
       const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
       const float rs = rsqrtf(R2);
       float gr, gi;
-      if (TABLE) {
-        const float2 f = lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
+      if (MODE == kLagrange) {
+        bool sl = false;
+        const float2 f = DEFER ? lookup32_fast<3>(T, R2 * rs, &sl) : lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
+        flagged |= sl;
         gr = f.x * beta[b].w;
         gi = f.y * beta[b].w;
+      } else if (MODE == kExpOverR) {
+        bool sl = false;
+        const float2 f = DEFER ? lookup32_fast<1>(T, R2 * rs, &sl) : lookup32<1>(T, R2 * rs);  // e^{-jkR}
+        flagged |= sl;
+        const float wr = beta[b].w * rs;
+        gr = f.x * wr;
+        gi = f.y * wr;
       } else {
         float sn, cs;
         sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
@@ -537,6 +656,7 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
       sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
       sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
     }
+    if (flagged) amask |= 1u << a;
     const float wa = al.w;
     M0r.add(wa * s0r);
     M0i.add(wa * s0i);
@@ -550,6 +670,42 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
     }
     Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
     Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
+  }
+  if (DEFER && MODE != kDirect && __any_sync(0xffffffffu, amask != 0)) {
+    // exact values where the lattice cell holds samples: add (exact - cell
+    // polynomial) to the moments of those point pairs
+    while (amask) {
+      const int a = __ffs(amask) - 1;
+      amask &= amask - 1;
+      const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float rs = rsqrtf(R2);
+        constexpr int D = MODE == kLagrange ? 3 : 1;
+        bool sl;
+        const float2 fa = lookup32_fast<D>(T, R2 * rs, &sl);
+        if (!sl) continue;
+        const float2 fe = lookup32_slow<D>(T, R2 * rs);
+        const float w = al.w * (MODE == kLagrange ? beta[b].w : beta[b].w * rs);
+        const float dr = (fe.x - fa.x) * w, di = (fe.y - fa.y) * w;
+        const float ab = al.x * beta[b].x + al.y * beta[b].y + al.z * beta[b].z;
+        const float alv[3] = {al.x, al.y, al.z}, bev[3] = {beta[b].x, beta[b].y, beta[b].z};
+        M0r.add(dr);
+        M0i.add(di);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          Mar[c].add(alv[c] * dr);
+          Mai[c].add(alv[c] * di);
+          Mbr[c].add(bev[c] * dr);
+          Mbi[c].add(bev[c] * di);
+        }
+        Mabr.add(ab * dr);
+        Mabi.add(ab * di);
+      }
+    }
   }
   if (!ok) return;
   const int4 ep = g.tedge[p], eq = g.tedge[q];
@@ -580,37 +736,38 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
   }
 }
 
-template <int M, bool TABLE, bool SMEM>
+template <int M, int MODE, bool SMEM, bool DEFER = true>
 __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoView g, TabView tv, float kpi,
                                                                           float scale, float inv_k2, float2* Z,
                                                                           int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
-  if (TABLE && SMEM) {
-    const int nl = tv.n_lat;
+  if (MODE != kDirect && SMEM) {  // the lattice image (lat_b only for the cubic Green table)
+    const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
     float4* sa = reinterpret_cast<float4*>(smem);
     float4* sb = sa + nl;
-    float4* ss = sb + nl;
+    float4* sblob = MODE == kLagrange ? sb + nl : sb;
     for (int i = threadIdx.x; i < nl; i += blockDim.x) {
       sa[i] = tv.lat_a[i];
-      sb[i] = tv.lat_b[i];
+      if (MODE == kLagrange) sb[i] = tv.lat_b[i];
     }
-    for (int i = threadIdx.x; i < tv.n_sub; i += blockDim.x) ss[i] = tv.lat_sub[i];
+    for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
     __syncthreads();
     T.la = sa;
-    T.lb = sb;
-    T.sub = ss;
+    if (MODE == kLagrange) T.lb = sb;  // the Exp table's lat_b (read only on the exact path) stays global
+    tab32_blob(T, tv, sblob);
   }
   const int lane = threadIdx.x & 31;
   const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
-    if (sym_task(task, g.nt, &p, &q0)) regular_task32<M, TABLE>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
+    if (sym_task(task, g.nt, &p, &q0))
+      regular_task32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
   }
 }
 
-template <bool TABLE>
+template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView tv, double k, double scale,
                                                              double inv_k2, double2* Z, int64_t ldz) {
   const int lane = threadIdx.x & 31;
@@ -639,10 +796,15 @@ __global__ void __launch_bounds__(kThreads) k_fill_regular64(GeoView g, TabView 
         const double rx = ux - be[0], ry = uy - be[1], rz = uz - be[2];
         const double R = sqrt(rx * rx + ry * ry + rz * rz);
         double gr, gi;
-        if (TABLE) {
+        if (MODE == kLagrange) {
           double2 f = lookup64<3>(tv, R);
           gr = f.x * be[3];
           gi = f.y * be[3];
+        } else if (MODE == kExpOverR) {
+          double2 f = lookup64<1>(tv, R);
+          const double wr = be[3] / R;
+          gr = f.x * wr;
+          gi = f.y * wr;
         } else {
           double sn, cs;
           sincos(k * R, &sn, &cs);
@@ -1083,8 +1245,9 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
       const float mag = fmaxf(fmaxf(fabsf(P.x), fabsf(P.y)), fmaxf(fabsf(P.z), fmaxf(fmaxf(fabsf(qx), fabsf(qy)), fabsf(qz))));
       const float slack = 1e-5f * (D + P.w + rq + mag);
       const float lo = D - P.w - rq - slack, hi = D + P.w + rq + slack;
-      const int c_lo = max(min(max(cell32_of(lo, G.lo, G.inv), 0), G.i_max) - 2, 0);
-      const int c_hi = min(min(max(cell32_of(hi, G.lo, G.inv), 0), G.i_max) + 2, G.i_max);
+      const int n_lat = tv.n_lat;
+      const int c_lo = max(lat_pos(G, lo).i - 2, 0);
+      const int c_hi = min(lat_pos(G, hi).i + 2, n_lat - 1);
       win[0] = c_lo;
       win[1] = c_hi;
       win[4] = (int64_t)(c_hi - c_lo + 1) * 32 <= kWinBytes;
@@ -1103,14 +1266,14 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
       __syncthreads();
       T.la = sa - c_lo;
       T.lb = sb - c_lo;
-      T.i_min = c_lo;
-      T.i_max = c_hi;
+      T.vmin = kLatMagic + (float)c_lo;
+      T.vmax = kLatMagic + (float)c_hi;
     }
     const int ntask = 32 * (qb1 - qb0);
     for (int task = warp; task < ntask; task += nw) {
       const int p = bp * 32 + task / (qb1 - qb0);
       const int q0 = (qb0 + task % (qb1 - qb0)) * 32;
-      if (p < g.nt) regular_task32<M, true>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
+      if (p < g.nt) regular_task32<M, kLagrange, false>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
     }
     __syncthreads();
   }
@@ -1734,8 +1897,8 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
       const Tab32 T = tab32(it.green);
       int p, q0;
       if (sym_task(t - it.reg_begin, it.g.nt, &p, &q0))
-        regular_task32<M, TABLE>(it.g, T, it.kpi, it.scale32, it.inv_k2_32, reinterpret_cast<float2*>(it.Z), it.ldz,
-                                 p, q0, lane);
+        regular_task32<M, TABLE ? kLagrange : kDirect>(it.g, T, it.kpi, it.scale32, it.inv_k2_32,
+                                                       reinterpret_cast<float2*>(it.Z), it.ldz, p, q0, lane);
     }
   }
 }
@@ -1927,18 +2090,18 @@ cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double*
 cudaError_t launch_table_image(int kind, double k, int degree, int n, const double* node64, const int8_t* zflag,
                                float* node32, double2* c64, float4* c32a, float4* c32b, double* fval, int n_hash,
                                double r_lo, double dr, int32_t* hash, int n_cells64, double lo64c,
-                               double inv64c, Cell64* cells64, int* flag, cudaStream_t s) {
+                               double inv64c, Cell64* cells64, cudaStream_t s) {
   k_table_values<<<(n + 255) / 256, 256, 0, s>>>(kind, k, n, node64, zflag, fval);
   k_table_coef<<<(n + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, c64, node32, c32a, c32b);
   k_table_hash<<<(n_hash + 255) / 256, 256, 0, s>>>(n, node64, n_hash, r_lo, dr, hash);
-  k_table_cells64<<<(n_cells64 + 255) / 256, 256, 0, s>>>(n, node64, n_cells64, lo64c, inv64c, cells64, flag);
+  k_table_cells64<<<(n_cells64 + 255) / 256, 256, 0, s>>>(n, node64, n_cells64, lo64c, inv64c, cells64);
   return cudaGetLastError();
 }
 
-cudaError_t launch_table_lattice(int degree, int n, const double* node64, const double* fval, int n_lat, float lat_lo,
-                                 float lat_h, const int32_t* lat_j, float4* lat_a, float4* lat_b, cudaStream_t s) {
-  k_table_lattice<<<(n_lat + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, n_lat, lat_lo, lat_h, lat_j, lat_a,
-                                                       lat_b);
+cudaError_t launch_table_lattice(const TabView& v, int degree, const double* fval, const int32_t* lat_j,
+                                 const int32_t* cmp, bool flag_in_b, float4* lat_a, float4* lat_b, cudaStream_t s) {
+  const int n = std::max(v.n_lat, v.n_cmp);
+  k_table_lattice<<<(n + 255) / 256, 256, 0, s>>>(v, degree, v.node64, fval, lat_j, cmp, flag_in_b, lat_a, lat_b);
   return cudaGetLastError();
 }
 
@@ -1968,60 +2131,71 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
   return cudaGetLastError();
 }
 
-template <int M>
-cudaError_t launch_regular32(const GeoView& g, const TabView* green, float kpi, float scale, float inv_k2, float2* Z,
-                             int64_t ldz, cudaStream_t s) {
-  TabView tv{};
-  if (!green) {
-    int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
-    return cudaGetLastError();
-  }
-  tv = *green;
-  const size_t smem = tv.smem32_bytes();
+template <int M, int MODE>
+cudaError_t launch_regular32_table(const TabView& tv, const GeoView& g, float kpi, float scale, float inv_k2,
+                                   float2* Z, int64_t ldz, cudaStream_t s) {
+  const size_t smem = tv.smem32_bytes(MODE == kLagrange ? 3 : 1);
   int dev = 0, max_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem <= (size_t)max_optin) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_fill_regular32<M, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // deferred corrections while at most 0.5 % of the lattice cells hold samples
+    auto kern = tv.n_busy * 200 <= tv.n_lat ? k_fill_regular32<M, MODE, true, true> : k_fill_regular32<M, MODE, true, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_regular32<M, true, true>, 512, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
     int64_t blocks = std::min<int64_t>(pair_grid(g, 2 * std::max(per_sm, 1)), (int64_t)sm_count() * std::max(per_sm, 1));
-    k_fill_regular32<M, true, true><<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
-  } else if (g.bsph) {
+    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+  } else if (MODE == kLagrange && g.bsph) {
     cudaError_t e =
         cudaFuncSetAttribute(k_fill_regular32_win<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinBytes);
     if (e != cudaSuccess) return e;
     k_fill_regular32_win<M><<<(unsigned)sm_count(), 512, kWinBytes, s>>>(g, tv, g.bsph, kpi, scale, inv_k2, Z, ldz);
   } else {
     int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+    k_fill_regular32<M, MODE, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_regular(const GeoView& g, const TabView* green, int precision, double k, double eta, void* Z,
-                                int64_t ldz, cudaStream_t s) {
-  const double scale = k * eta / (4.0 * kPi);
-  TabView tv{};
-  if (green) tv = *green;
-  if (precision == GF_FP64) {
+template <int M>
+cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_exp, float kpi, float scale,
+                             float inv_k2, float2* Z, int64_t ldz, cudaStream_t s) {
+  if (!table) {
+    TabView tv{};
     int64_t blocks = pair_grid(g, 4);
-    if (green)
-      k_fill_regular64<true><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, 1.0 / (k * k), (double2*)Z, ldz);
-    else
-      k_fill_regular64<false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, 1.0 / (k * k), (double2*)Z, ldz);
+    k_fill_regular32<M, kDirect, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
     return cudaGetLastError();
   }
-  const float kpi = (float)(k / kPi);
+  if (from_exp) return launch_regular32_table<M, kExpOverR>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
+  return launch_regular32_table<M, kLagrange>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
+}
+
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
+                                double eta, void* Z, int64_t ldz, cudaStream_t s) {
+  const double scale = k * eta / (4.0 * kPi);
+  TabView tv{};
+  if (table) tv = *table;
+  if (precision == GF_FP64) {
+    int64_t blocks = pair_grid(g, 4);
+    const double ik2 = 1.0 / (k * k);
+    if (!table)
+      k_fill_regular64<kDirect><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, ik2, (double2*)Z, ldz);
+    else if (from_exp)
+      k_fill_regular64<kExpOverR><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, ik2, (double2*)Z, ldz);
+    else
+      k_fill_regular64<kLagrange><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, ik2, (double2*)Z, ldz);
+    return cudaGetLastError();
+  }
+  const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
+  float2* Z32 = (float2*)Z;
   switch (g.m) {
-    case 1: return launch_regular32<1>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
-    case 3: return launch_regular32<3>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
-    case 4: return launch_regular32<4>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
-    case 6: return launch_regular32<6>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
-    case 7: return launch_regular32<7>(g, green, kpi, (float)scale, (float)(1.0 / (k * k)), (float2*)Z, ldz, s);
+    case 1: return launch_regular32<1>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
+    case 3: return launch_regular32<3>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
+    case 4: return launch_regular32<4>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
+    case 6: return launch_regular32<6>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
+    case 7: return launch_regular32<7>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -41,7 +41,7 @@ class gf_params(C.Structure):
                 ("exp_n_per_lambda", C.c_int), ("lagrange_degree", C.c_int), ("refine", C.c_int),
                 ("refine_factor", C.c_double), ("refine_halfwidth_t", C.c_double), ("merge_t", C.c_double),
                 ("grade", C.c_int), ("nphi", C.c_int), ("nl", C.c_int), ("eta", C.c_double),
-                ("near_fp64", C.c_int)]
+                ("near_fp64", C.c_int), ("green_from_exp", C.c_int)]
 
 
 _lib = None

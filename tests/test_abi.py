@@ -34,6 +34,7 @@ def test_params_default_values():
     assert p.exp_n_per_lambda == 0 and p.lagrange_degree == 3 and p.refine == 1
     assert p.refine_factor == 0.5 and p.refine_halfwidth_t == 2.0 and p.merge_t == 0.25
     assert p.grade == 1 and p.nphi == 8 and p.nl == 8 and p.eta == 376.730313668 and p.near_fp64 == 0
+    assert p.green_from_exp == 0
 
 
 def test_argument_errors_before_any_device_call():
@@ -51,6 +52,9 @@ def test_argument_errors_before_any_device_call():
     assert L.gf_table_create(0.0, 0.1, 1.0, C.byref(p), None, C.byref(h)) == -1
     assert L.gf_table_create(1.0, 0.5, 0.1, C.byref(p), None, C.byref(h)) == -1
     p.nphi = 0
+    assert L.gf_table_create(1.0, 0.1, 1.0, C.byref(p), None, C.byref(h)) == -1
+    p = gf.gf_params_default()
+    p.green_from_exp = 2
     assert L.gf_table_create(1.0, 0.1, 1.0, C.byref(p), None, C.byref(h)) == -1
     assert L.gf_fill(None, 1.0, C.byref(p), None, 32, None, 10, None) == -1
     assert L.gf_table_destroy(None) == 0 and L.gf_mesh_destroy(None) == 0

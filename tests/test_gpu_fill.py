@@ -65,6 +65,26 @@ def test_small_sphere_fp64_both_modes():
         assert rel_fro(z, ref) <= 1e-12
 
 
+def test_green_from_exp_matches_oracle():
+    # regular pairs through the linear Exp table times 1/R (green_from_exp = 1)
+    # against the oracle's "exp_over_r" mode: FP64 plate element-wise at 1e-12,
+    # FP32 jittered sphere (smem lattice of the Exp table) at 1e-5
+    wl = W.plate_280()
+    _, z, _ = gpu_fill(wl.xyz, wl.tri, wl.k, 3, gf.GF_FP64, True, green_from_exp=1)
+    om = O.Mesh(wl.xyz, wl.tri)
+    lo, hi = om.range(3)
+    ref = om.z_full(wl.k, 3, mode="exp_over_r", tables=O.make_tables(wl.k, lo, hi))
+    assert rel_fro(z, ref) <= 1e-12 and rel_max(z, ref) <= 1e-12
+    xyz, tri = W.octasphere(2, 1.0)
+    xyz = W.jitter(xyz, tri, 0.02, 3)
+    for rule in (4, 7):
+        _, z, _ = gpu_fill(xyz, tri, K, rule, gf.GF_FP32, True, green_from_exp=1)
+        om = O.Mesh(xyz, tri)
+        lo, hi = om.range(rule)
+        ref = om.z_full(K, rule, mode="exp_over_r", tables=O.make_tables(K, lo, hi))
+        assert rel_fro(z, ref) <= 1e-5 and rel_max(z, ref) <= 1e-5
+
+
 @pytest.mark.parametrize("which", ["plate", "sphere", "cube"])
 def test_range_matches_oracle(which):
     wl = {"plate": W.plate_280, "sphere": W.sphere_3072, "cube": lambda: W.cube_73728(6)}[which]()

@@ -116,6 +116,33 @@ def test_table_vs_direct_z_matches_paper_order():
     assert np.abs(Zt - Zd).max() < 1e-5 * np.abs(Zd).max()
 
 
+def test_exp_over_r_mode_within_exp_table_bound():
+    # green_mode 2: regular-pair Green values from the linear Exp table times
+    # 1/(4 pi R). Its relative error is the Exp table's Eq. (10) bound (1e-6),
+    # so the fill stays within the table-vs-direct order of Section IV.B, and
+    # it differs from the Lagrange-table fill only in the regular pairs.
+    wl = W.plate_280()
+    m = O.Mesh(wl.xyz, wl.tri)
+    lo, hi = m.range(3)
+    g, e = O.make_tables(K, lo, hi)
+    Zd = m.z_full(K, 3)
+    Zt = m.z_full(K, 3, mode="table", tables=(g, e))
+    Zx = m.z_full(K, 3, mode="exp_over_r", tables=(g, e))
+    rel = np.linalg.norm(Zx - Zd) / np.linalg.norm(Zd)
+    assert 1e-10 < rel < 1e-5
+    assert np.abs(Zx - Zd).max() < 1e-5 * np.abs(Zd).max()
+    assert np.abs(Zx - Zt).max() > 1e-12 * np.abs(Zd).max()  # another table for regular pairs
+    # an entry whose four triangle pairs are all near is the same in both modes
+    xyz, tri = diamonds(size=0.05, gap=0.02)
+    md = O.Mesh(xyz, tri)
+    assert all(md.is_near(p, q) for p in (0, 1) for q in (0, 1))
+    lo2, hi2 = 0.01, 1.0
+    g2, e2 = O.make_tables(K, lo2, hi2)
+    z1 = md.z_entries(K, 3, [0], [0], mode="table", tables=(g2, e2))
+    z2 = md.z_entries(K, 3, [0], [0], mode="exp_over_r", tables=(g2, e2))
+    assert z1[0] == z2[0]
+
+
 def test_range_is_brute_force_min_max():
     xyz, tri = W.octasphere(1, 1.0)
     m = O.Mesh(xyz, tri)
