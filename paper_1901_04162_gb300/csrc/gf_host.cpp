@@ -321,7 +321,7 @@ gf_status check_device(int dev) {
 void free_mesh_device(gf_mesh* m) {
   void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_near_row, m->d_pts32,
                   m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
-                  m->d_dtri,  m->d_dk, m->d_bsph};
+                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -582,7 +582,8 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
       (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
       (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_minmax, 4)) ||
-      (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32))) {
+      (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32)) ||
+      (st = dev_alloc(&m->d_range_bpb, (size_t)((nt + 31) / 32) * ((nt + 31) / 32 + 1) / 2))) {
     free_mesh_device(m.get());
     return st;
   }
@@ -655,7 +656,7 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, rule, s))) return st;
-  GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, s));
+  GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, m->d_range_bpb, s));
   unsigned long long mm[2];
   GF_CUDA(cudaMemcpyAsync(mm, m->d_minmax, 16, cudaMemcpyDeviceToHost, s));
   GF_CUDA(cudaStreamSynchronize(s));

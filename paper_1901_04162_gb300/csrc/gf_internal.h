@@ -143,7 +143,8 @@ cudaError_t launch_table_lattice(const TabView& v, int degree, const double* fva
 cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
-cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s);
+// bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}
 // from the linear table times 1/R); NULL = direct evaluation.
 cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
@@ -204,6 +205,7 @@ struct gf_mesh {
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
   double* d_dk = nullptr;                   // adjoint scratch [1]
   unsigned long long* d_minmax = nullptr;  // range scratch [4]
+  float2* d_range_bpb = nullptr;          // range scratch: bounds per 32 x 32 block pair
 };
 
 struct gf_table {

@@ -451,7 +451,7 @@ __global__ void k_range_init(unsigned long long* mm) {
 // Every point distance of a pair lies in [D - r_p - r_q, D + r_p + r_q]
 // (D = centroid distance, r = largest point offset from the centroid).
 // Pass 1 bounds the extremes: r_min <= min(D + r_p + r_q) = mm[2] and
-// r_max >= max(D - r_p - r_q) = mm[3]; pass 2 (k_range) evaluates the point
+// r_max >= max(D - r_p - r_q) = mm[3]; pass 2 (k_range32) evaluates the point
 // pairs only of triangle pairs that can reach below mm[2] or above mm[3].
 // FP32 bounds are widened by a slack that covers their rounding.
 __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, float3 dc, float4 cp, float4 cq,
@@ -465,22 +465,39 @@ __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, floa
   *ub = D + r + slack;
 }
 
-__global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm) {
+// Pass 1, one warp per 32 x 32 triangle block pair: the extremes of the pair
+// bounds (mm[2], mm[3]) and, per block pair, the smallest lower and largest
+// upper bound of its regular pairs (bpb), so that pass 2 skips block pairs
+// that cannot hold an extreme.
+__global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm, float2* bpb) {
   const int lane = threadIdx.x & 31;
-  const int64_t ntask = regular_units(g.nt);
+  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float min_ub = INFINITY, max_lb = 0.f;
-  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
-    int p, q0;
-    if (!sym_task(task, g.nt, &p, &q0)) continue;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
+    int p0, q0;
+    sym_task(u * 32, g.nt, &p0, &q0);
     const int q = min(q0 + lane, g.nt - 1);
-    const float4 cp = g.cen32[p], cq = g.cen32[q];
-    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-    if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
-    float lb, ub;
-    pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
-    min_ub = fminf(min_ub, ub);
-    max_lb = fmaxf(max_lb, lb);
+    const float4 cq = g.cen32[q];
+    const int4 vq = g.tvert[q];
+    float blk_lb = INFINITY, blk_ub = 0.f;
+    const int p1 = min(p0 + 32, g.nt);
+    for (int p = p0; p < p1; ++p) {
+      const float4 cp = g.cen32[p];
+      const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+      if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], vq, dc))) continue;
+      float lb, ub;
+      pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
+      min_ub = fminf(min_ub, ub);
+      max_lb = fmaxf(max_lb, lb);
+      blk_lb = fminf(blk_lb, lb);
+      blk_ub = fmaxf(blk_ub, ub);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      blk_lb = fminf(blk_lb, __shfl_xor_sync(0xffffffffu, blk_lb, off));
+      blk_ub = fmaxf(blk_ub, __shfl_xor_sync(0xffffffffu, blk_ub, off));
+    }
+    if (lane == 0) bpb[u] = make_float2(blk_lb, blk_ub);
   }
   for (int off = 16; off > 0; off >>= 1) {
     min_ub = fminf(min_ub, __shfl_xor_sync(0xffffffffu, min_ub, off));
@@ -492,75 +509,102 @@ __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned l
   }
 }
 
-// ---------------------------------------------------------------- range
-// One warp per (p, 32 consecutive q). FP32: each lane keeps the FP32 extremes
-// with their point pairs and re-evaluates those two pairs in FP64 at the end.
-template <bool FP64>
-__global__ void __launch_bounds__(kThreads) k_range(GeoView g, unsigned long long* mm) {
+// Pass 2 (FP32 screen): block pairs that can hold an extreme, then their
+// pairs that can, then their point pairs; each lane keeps its FP32 extremes
+// and re-evaluates those two point pairs in FP64 at the end.
+template <int M>
+__global__ void __launch_bounds__(kThreads) k_range32(GeoView g, unsigned long long* mm, const float2* bpb) {
   const int lane = threadIdx.x & 31;
   const float u_min = (float)__longlong_as_double((long long)mm[2]);
   const float l_max = (float)__longlong_as_double((long long)mm[3]);
-  const int64_t ntask = regular_units(g.nt);
-  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  double best_lo = INFINITY, best_hi = 0.0;
   float lo32 = INFINITY, hi32 = -1.f;
   int lo_p = 0, lo_q = 0, lo_ab = 0, hi_p = 0, hi_q = 0, hi_ab = 0;
-  for (int64_t task = warp0; task < ntask; task += nwarp) {
-    int p, q0;
-    if (!sym_task(task, g.nt, &p, &q0)) continue;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
+    const float2 bb = bpb[u];
+    if (!(bb.x <= u_min || bb.y >= l_max)) continue;  // no pair of the block pair can hold an extreme
+    int p0, q0;
+    sym_task(u * 32, g.nt, &p0, &q0);
     const int q = min(q0 + lane, g.nt - 1);
-    const float4 cp = g.cen32[p], cq = g.cen32[q];
-    float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-    bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
-    if (!ok) continue;
-    if (!FP64) {
+    const float4 cq = g.cen32[q];
+    const int4 vq = g.tvert[q];
+    float4 beta[M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
+    const int p1 = min(p0 + 32, g.nt);
+    for (int p = p0; p < p1; ++p) {
+      const float4 cp = g.cen32[p];
+      const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+      if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], vq, dc))) continue;
       float lb, ub;
       pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
       if (lb > u_min && ub < l_max) continue;  // cannot hold an extreme
-    }
-    if (FP64) {
-      const double* cp64 = g.cen64 + 4 * (size_t)p;
-      const double* cq64 = g.cen64 + 4 * (size_t)q;
-      double dx = cp64[0] - cq64[0], dy = cp64[1] - cq64[1], dz = cp64[2] - cq64[2];
-      for (int a = 0; a < g.m; ++a) {
-        const double* pa = g.pts64 + 4 * ((size_t)a * g.nt + p);
-        double ux = dx + pa[0], uy = dy + pa[1], uz = dz + pa[2];
-        for (int b = 0; b < g.m; ++b) {
-          const double* pb = g.pts64 + 4 * ((size_t)b * g.nt + q);
-          double rx = ux - pb[0], ry = uy - pb[1], rz = uz - pb[2];
-          double R = sqrt(rx * rx + ry * ry + rz * rz);
-          best_lo = fmin(best_lo, R);
-          best_hi = fmax(best_hi, R);
-        }
-      }
-    } else {
-      for (int a = 0; a < g.m; ++a) {
-        float4 pa = g.pts32[(size_t)a * g.nt + p];
-        float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
-        for (int b = 0; b < g.m; ++b) {
-          float4 pb = g.pts32[(size_t)b * g.nt + q];
-          float rx = ux - pb.x, ry = uy - pb.y, rz = uz - pb.z;
-          float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      for (int a = 0; a < M; ++a) {
+        const float4 pa = g.pts32[(size_t)a * g.nt + p];
+        const float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+          const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+          const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
           if (R2 < lo32) { lo32 = R2; lo_p = p; lo_q = q; lo_ab = a * 8 + b; }
           if (R2 > hi32) { hi32 = R2; hi_p = p; hi_q = q; hi_ab = a * 8 + b; }
         }
       }
     }
   }
-  if (!FP64) {
-    auto dist64 = [&](int p, int q, int ab) {
-      const double* cp64 = g.cen64 + 4 * (size_t)p;
-      const double* cq64 = g.cen64 + 4 * (size_t)q;
-      const double* pa = g.pts64 + 4 * ((size_t)(ab >> 3) * g.nt + p);
-      const double* pb = g.pts64 + 4 * ((size_t)(ab & 7) * g.nt + q);
-      double rx = (cp64[0] - cq64[0]) + pa[0] - pb[0];
-      double ry = (cp64[1] - cq64[1]) + pa[1] - pb[1];
-      double rz = (cp64[2] - cq64[2]) + pa[2] - pb[2];
-      return sqrt(rx * rx + ry * ry + rz * rz);
-    };
-    if (lo32 < INFINITY) best_lo = dist64(lo_p, lo_q, lo_ab);
-    if (hi32 >= 0.f) best_hi = dist64(hi_p, hi_q, hi_ab);
+  auto dist64 = [&](int p, int q, int ab) {
+    const double* cp64 = g.cen64 + 4 * (size_t)p;
+    const double* cq64 = g.cen64 + 4 * (size_t)q;
+    const double* pa = g.pts64 + 4 * ((size_t)(ab >> 3) * g.nt + p);
+    const double* pb = g.pts64 + 4 * ((size_t)(ab & 7) * g.nt + q);
+    double rx = (cp64[0] - cq64[0]) + pa[0] - pb[0];
+    double ry = (cp64[1] - cq64[1]) + pa[1] - pb[1];
+    double rz = (cp64[2] - cq64[2]) + pa[2] - pb[2];
+    return sqrt(rx * rx + ry * ry + rz * rz);
+  };
+  double best_lo = lo32 < INFINITY ? dist64(lo_p, lo_q, lo_ab) : INFINITY;
+  double best_hi = hi32 >= 0.f ? dist64(hi_p, hi_q, hi_ab) : 0.0;
+  for (int off = 16; off > 0; off >>= 1) {
+    best_lo = fmin(best_lo, __shfl_xor_sync(0xffffffffu, best_lo, off));
+    best_hi = fmax(best_hi, __shfl_xor_sync(0xffffffffu, best_hi, off));
+  }
+  if (lane == 0) {
+    if (best_lo < INFINITY) atomicMin(&mm[0], dbits(best_lo));
+    if (best_hi > 0.0) atomicMax(&mm[1], dbits(best_hi));
+  }
+}
+
+// ---------------------------------------------------------------- range
+// FP64: every point pair of every regular pair, one warp per (p, 32
+// consecutive q).
+__global__ void __launch_bounds__(kThreads) k_range64(GeoView g, unsigned long long* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ntask = regular_units(g.nt);
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double best_lo = INFINITY, best_hi = 0.0;
+  for (int64_t task = warp0; task < ntask; task += nwarp) {
+    int p, q0;
+    if (!sym_task(task, g.nt, &p, &q0)) continue;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
+    const double* cp64 = g.cen64 + 4 * (size_t)p;
+    const double* cq64 = g.cen64 + 4 * (size_t)q;
+    const double dx = cp64[0] - cq64[0], dy = cp64[1] - cq64[1], dz = cp64[2] - cq64[2];
+    for (int a = 0; a < g.m; ++a) {
+      const double* pa = g.pts64 + 4 * ((size_t)a * g.nt + p);
+      const double ux = dx + pa[0], uy = dy + pa[1], uz = dz + pa[2];
+      for (int b = 0; b < g.m; ++b) {
+        const double* pb = g.pts64 + 4 * ((size_t)b * g.nt + q);
+        const double rx = ux - pb[0], ry = uy - pb[1], rz = uz - pb[2];
+        const double R = sqrt(rx * rx + ry * ry + rz * rz);
+        best_lo = fmin(best_lo, R);
+        best_hi = fmax(best_hi, R);
+      }
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     best_lo = fmin(best_lo, __shfl_xor_sync(0xffffffffu, best_lo, off));
@@ -2119,14 +2163,23 @@ cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const v
   return cudaGetLastError();
 }
 
-cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, cudaStream_t s) {
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, cudaStream_t s) {
   k_range_init<<<1, 1, 0, s>>>(d_minmax);
-  int64_t blocks = pair_grid(g, 8);
   if (precision == GF_FP64) {
-    k_range<true><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
-  } else {
-    k_range_bounds<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
-    k_range<false><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
+    int64_t blocks = pair_grid(g, 8);
+    k_range64<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
+    return cudaGetLastError();
+  }
+  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
+  const int64_t blocks = std::min<int64_t>((nbp + kWarps - 1) / kWarps, (int64_t)sm_count() * 8);
+  k_range_bounds<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb);
+  switch (g.m) {
+    case 1: k_range32<1><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 3: k_range32<3><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 4: k_range32<4><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 6: k_range32<6><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 7: k_range32<7><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
