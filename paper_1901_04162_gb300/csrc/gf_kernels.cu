@@ -450,10 +450,10 @@ __global__ void k_range_init(unsigned long long* mm) {
 
 // Every point distance of a pair lies in [D - r_p - r_q, D + r_p + r_q]
 // (D = centroid distance, r = largest point offset from the centroid).
-// Pass 1 bounds the extremes: r_min <= min(D + r_p + r_q) = mm[2] and
-// r_max >= max(D - r_p - r_q) = mm[3]; pass 2 (k_range32) evaluates the point
-// pairs only of triangle pairs that can reach below mm[2] or above mm[3].
-// FP32 bounds are widened by a slack that covers their rounding.
+// Pass 1 finds thresholds mm[2] >= r_min and mm[3] <= r_max; pass 2
+// (k_range32) evaluates the point pairs only of triangle pairs whose interval
+// reaches below mm[2] or above mm[3]. FP32 bounds are widened by a slack that
+// covers their rounding.
 __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, float3 dc, float4 cp, float4 cq,
                                             float* lb, float* ub) {
   const float D = sqrtf(fmaf(dc.x, dc.x, fmaf(dc.y, dc.y, dc.z * dc.z)));
@@ -465,20 +465,22 @@ __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, floa
   *ub = D + r + slack;
 }
 
-// Pass 1, one warp per 32 x 32 triangle block pair: the extremes of the pair
-// bounds (mm[2], mm[3]) and, per block pair, the smallest lower and largest
-// upper bound of its regular pairs (bpb), so that pass 2 skips block pairs
-// that cannot hold an extreme.
+// Pass 1, one warp per 32 x 32 triangle block pair: thresholds from actual
+// point distances (the first rule point of each triangle of every regular
+// pair: their minimum is >= r_min, their maximum <= r_max), widened by a
+// relative 1e-5 for the FP32 rounding (mm[2], mm[3]), and, per block pair,
+// the smallest lower and largest upper bound of its regular pairs (bpb), so
+// that pass 2 skips block pairs that cannot hold an extreme.
 __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm, float2* bpb) {
   const int lane = threadIdx.x & 31;
   const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float min_ub = INFINITY, max_lb = 0.f;
+  float min_d = INFINITY, max_d = 0.f;
   for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
     int p0, q0;
     sym_task(u * 32, g.nt, &p0, &q0);
     const int q = min(q0 + lane, g.nt - 1);
-    const float4 cq = g.cen32[q];
+    const float4 cq = g.cen32[q], yq = g.pts32[q];
     const int4 vq = g.tvert[q];
     float blk_lb = INFINITY, blk_ub = 0.f;
     const int p1 = min(p0 + 32, g.nt);
@@ -488,8 +490,11 @@ __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned l
       if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], vq, dc))) continue;
       float lb, ub;
       pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
-      min_ub = fminf(min_ub, ub);
-      max_lb = fmaxf(max_lb, lb);
+      const float4 xp = g.pts32[p];
+      const float rx = (dc.x + xp.x) - yq.x, ry = (dc.y + xp.y) - yq.y, rz = (dc.z + xp.z) - yq.z;
+      const float d = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+      min_d = fminf(min_d, d);
+      max_d = fmaxf(max_d, d);
       blk_lb = fminf(blk_lb, lb);
       blk_ub = fmaxf(blk_ub, ub);
     }
@@ -500,18 +505,18 @@ __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned l
     if (lane == 0) bpb[u] = make_float2(blk_lb, blk_ub);
   }
   for (int off = 16; off > 0; off >>= 1) {
-    min_ub = fminf(min_ub, __shfl_xor_sync(0xffffffffu, min_ub, off));
-    max_lb = fmaxf(max_lb, __shfl_xor_sync(0xffffffffu, max_lb, off));
+    min_d = fminf(min_d, __shfl_xor_sync(0xffffffffu, min_d, off));
+    max_d = fmaxf(max_d, __shfl_xor_sync(0xffffffffu, max_d, off));
   }
   if (lane == 0) {
-    if (min_ub < INFINITY) atomicMin(&mm[2], dbits((double)min_ub));
-    if (max_lb > 0.f) atomicMax(&mm[3], dbits((double)max_lb));
+    if (min_d < INFINITY) atomicMin(&mm[2], dbits((double)min_d * (1.0 + 1e-5)));
+    if (max_d > 0.f) atomicMax(&mm[3], dbits((double)max_d * (1.0 - 1e-5)));
   }
 }
 
-// Pass 2 (FP32 screen): block pairs that can hold an extreme, then their
-// pairs that can, then their point pairs; each lane keeps its FP32 extremes
-// and re-evaluates those two point pairs in FP64 at the end.
+// Pass 2 (FP32 screen), one warp per block pair that can hold an extreme:
+// its pairs that can are evaluated point by point. Each lane keeps its FP32
+// extremes and re-evaluates those two point pairs in FP64 at the end.
 template <int M>
 __global__ void __launch_bounds__(kThreads) k_range32(GeoView g, unsigned long long* mm, const float2* bpb) {
   const int lane = threadIdx.x & 31;
@@ -2173,12 +2178,13 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
   const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
   const int64_t blocks = std::min<int64_t>((nbp + kWarps - 1) / kWarps, (int64_t)sm_count() * 8);
   k_range_bounds<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb);
+  const unsigned b2 = (unsigned)blocks;
   switch (g.m) {
-    case 1: k_range32<1><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 3: k_range32<3><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 4: k_range32<4><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 6: k_range32<6><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 7: k_range32<7><<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 1: k_range32<1><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 3: k_range32<3><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 4: k_range32<4><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 6: k_range32<6><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 7: k_range32<7><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
