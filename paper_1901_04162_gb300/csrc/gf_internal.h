@@ -42,6 +42,7 @@ struct GeoView {
   const double* cen64;   // [nt][4]
   const double* geo64;   // [nt][3][4]
   const double* v64;     // [nt][9] vertices
+  const double* frame64; // [nt][kFrame] near-pair source frames
   const int4* tvert;     // [nt]: vertex ids (x, y, z)
   const int4* tedge;     // [nt]: RWG edge id of local edge i, or -1
   const int64_t* near_ptr;  // [nt + 1]
@@ -126,10 +127,13 @@ struct BatchItem {
 };
 
 // ---------------------------------------------------------------- kernels (gf_kernels.cu)
+// Doubles per triangle of the near-pair source frames: unit normal [0..2],
+// edge lengths [3..5], unit edge tangents [6..14], in-plane edge normals [15..23].
+constexpr int kFrame = 24;
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
-                                 cudaStream_t s);
+                                 double* frame64, cudaStream_t s);
 cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, const double* node64,
                                const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
                                float4* c32b, double* fval, int n_hash, double r_lo, double dr,
@@ -200,6 +204,7 @@ struct gf_mesh {
   double* d_pts64 = nullptr;
   double* d_cen64 = nullptr;
   double* d_geo64 = nullptr;
+  double* d_frame64 = nullptr;
   float* d_rad32 = nullptr;
   float4* d_bsph = nullptr;
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]

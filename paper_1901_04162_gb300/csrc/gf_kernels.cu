@@ -39,12 +39,35 @@ __device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
 __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, const double* __restrict__ bary,
                                 const double* __restrict__ w, const int4* __restrict__ tedge,
                                 const double* __restrict__ elen, float4* pts32, float4* cen32, float4* geo32,
-                                double* pts64, double* cen64, double* geo64, float* rad32) {
+                                double* pts64, double* cen64, double* geo64, float* rad32, double* frame64) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double v[3][3];
   for (int c = 0; c < 3; ++c)
     for (int x = 0; x < 3; ++x) v[c][x] = v64[9 * (size_t)t + 3 * c + x];
+  {
+    // source-triangle frame of the near-pair integrals: unit normal, edge
+    // lengths, unit edge tangents (v_e -> v_{e+1}) and in-plane edge normals t x n
+    double* fr = frame64 + kFrame * (size_t)t;
+    const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+    const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int x = 0; x < 3; ++x) fr[x] = n[x] = n[x] * inv;
+    for (int e = 0; e < 3; ++e) {
+      const double* a = v[e];
+      const double* b = v[(e + 1) % 3];
+      double tt[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+      const double len = sqrt(tt[0] * tt[0] + tt[1] * tt[1] + tt[2] * tt[2]);
+      const double il = 1.0 / len;
+      for (int x = 0; x < 3; ++x) tt[x] *= il;
+      fr[3 + e] = len;
+      for (int x = 0; x < 3; ++x) fr[6 + 3 * e + x] = tt[x];
+      fr[15 + 3 * e + 0] = tt[1] * n[2] - tt[2] * n[1];
+      fr[15 + 3 * e + 1] = tt[2] * n[0] - tt[0] * n[2];
+      fr[15 + 3 * e + 2] = tt[0] * n[1] - tt[1] * n[0];
+    }
+  }
   double c0 = (v[0][0] + v[1][0] + v[2][0]) / 3.0;
   double c1 = (v[0][1] + v[1][1] + v[2][1]) / 3.0;
   double c2 = (v[0][2] + v[1][2] + v[2][2]) / 3.0;
@@ -1030,45 +1053,41 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 // frames), the closed-form static part and all accumulation in FP64; the
 // sampling of e^{-jkR} at the angular and line nodes of each edge in FP32
 // (relative quantities of the size of a triangle, FP32 Exp table).
-__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const NearArgs& A, double k,
-                                      const Tab32& te, bool use_table, float lo, float hi, C2* I0, C2 I1[3],
-                                      double rho0[3]) {
+// FP64 where the terms cancel (projection, in-plane distances, the static
+// closed form, all sums), FP32 sampling of e^{-jkR} on the edges. The source
+// frame (normal, edge tangents, lengths, edge normals) is precomputed per
+// triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
+// and the static log term is one log of a ratio per edge.
+__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
+                                      const NearArgs& A, double k, const Tab32& te, bool use_table, float lo,
+                                      float hi, C2* I0, C2 I1[3], double rho0[3]) {
   const float kpi = (float)(k / kPi), k32 = (float)k;
-  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
-  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
-  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  n[0] *= inv;
-  n[1] *= inv;
-  n[2] *= inv;
+  const double n[3] = {fr[0], fr[1], fr[2]};
   const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
   const double d = fabs(h);
   for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  double Rv[3];  // |r - v_c|
+  for (int c = 0; c < 3; ++c) {
+    const double dx = v[c][0] - r[0], dy = v[c][1] - r[1], dz = v[c][2] - r[2];
+    Rv[c] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
   const float d32 = (float)d;
   const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
   double sre = 0, sim = 0;
   double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0}, vst[3] = {0, 0, 0};
   for (int e = 0; e < 3; ++e) {
     const double* a = v[e];
-    const double* b = v[(e + 1) % 3];
-    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-    const double il = 1.0 / len;
-    t[0] *= il;
-    t[1] *= il;
-    t[2] *= il;
-    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
+    const double len = fr[3 + e];
+    const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
+    const double mh[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
     const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
     const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
     const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
-    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
+    const double lp = lm + len;
     if (fabs(P0) > 1e-12 * len) {
-      const double aP = fabs(P0);
-      const double iaP = 1.0 / aP;
-      const float um = asinhf((float)(lm * iaP)), up = asinhf((float)(lp * iaP));
+      const float aP32 = (float)fabs(P0);
+      const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
       const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
-      const float aP32 = (float)aP;
       float cr = 0.f, ci = 0.f;
       for (int i = 0; i < A.nphi; ++i) {
         const float u = fmaf(half, A.fx_phi[i], mid);
@@ -1099,13 +1118,14 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
       li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
     }
     const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
+    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|
     const double R02 = P0 * P0 + d * d;
-    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
+    const double Rm = Rv[e], Rp = Rv[(e + 1) % 3];
     double st = 0.5 * (lp * Rp - lm * Rm);
     if (R02 > 0) {
       const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
       const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st += 0.5 * R02 * (log(fp) - log(fm));
+      st += 0.5 * R02 * log(fp / fm);
     }
     for (int x = 0; x < 3; ++x) {
       vre[x] += mh[x] * lrd;
@@ -1113,12 +1133,12 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
       vst[x] += mh[x] * st;
     }
   }
-  const double c4 = 1.0 / (4.0 * kPi);
-  I0->re = sim / k * c4;
-  I0->im = -sre / k * c4;
+  const double c4 = 1.0 / (4.0 * kPi), ik = 1.0 / k;
+  I0->re = sim * ik * c4;
+  I0->im = -sre * ik * c4;
   for (int x = 0; x < 3; ++x) {
-    I1[x].re = (-vim[x] / k + vst[x]) * c4;
-    I1[x].im = (vre[x] / k) * c4;
+    I1[x].re = (-vim[x] * ik + vst[x]) * c4;
+    I1[x].im = (vre[x] * ik) * c4;
   }
 }
 
@@ -1127,7 +1147,8 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
 // to Z by the group's first lane.
 // One near pair (index idx of the CSR list; valid_pair false: padding) on a
 // group of 8 lanes, one test point per lane; every lane of the group must call.
-template <class Out, bool MIXED>
+// One near pair per group of G lanes (G >= the rule size; lane = test point).
+template <class Out, bool MIXED, int G = 8>
 __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
                                           float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
                                           int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
@@ -1149,7 +1170,9 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
     const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
     C2 I0, I1[3];
     double rho0[3];
-    if (MIXED) inner_integrals_mixed(ra, vq, A, ks.k, te32, use_table, lo32, hi32, &I0, I1, rho0);
+    if (MIXED)
+      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, A, ks.k, te32, use_table, lo32, hi32, &I0, I1,
+                            rho0);
     else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
     const double wa = al[3];
 #pragma unroll
@@ -1177,7 +1200,7 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int off = 1; off < 8; off <<= 1) {
+      for (int off = 1; off < G; off <<= 1) {
         accr[i][j] += __shfl_xor_sync(gmask, accr[i][j], off);
         acci[i][j] += __shfl_xor_sync(gmask, acci[i][j], off);
       }
@@ -1204,21 +1227,21 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
   }
 }
 
-template <class Out, bool MIXED>
+template <class Out, bool MIXED, int G>
 __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
                                                    int64_t ldz) {
   const Tab32 te32 = tab32(te);
   const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
   const int64_t n_near = g.near_ptr[g.nt];
-  const int sub = threadIdx.x & 7;
-  const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+  const int sub = threadIdx.x & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
   for (int64_t it = 0; it < iters; ++it) {
     const int64_t idx = g0 + it * ngroups;
-    near_task<Out, MIXED>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2}, Z, ldz, n_near, idx,
-                          idx < n_near, sub, gmask);
+    near_task<Out, MIXED, G>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2}, Z, ldz, n_near,
+                             idx, idx < n_near, sub, gmask);
   }
 }
 
@@ -2130,9 +2153,9 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
-                                 cudaStream_t s) {
+                                 double* frame64, cudaStream_t s) {
   k_prep_geometry<<<(nt + 127) / 128, 128, 0, s>>>(v64, nt, m, bary, w, tedge, edge_len, pts32, cen32, geo32,
-                                                   pts64, cen64, geo64, rad32);
+                                                   pts64, cen64, geo64, rad32, frame64);
   return cudaGetLastError();
 }
 
@@ -2283,12 +2306,23 @@ cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precisio
   const int64_t n_near = 0;  // read on the device
   (void)n_near;
   int64_t blocks = (int64_t)sm_count() * 16;
-  if (precision == GF_FP32 && mixed)
-    k_fill_near<float2, true><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
-  else if (precision == GF_FP32)
-    k_fill_near<float2, false><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (float2*)Z, ldz);
-  else
-    k_fill_near<double2, false><<<(unsigned)blocks, 128, 0, s>>>(g, te, texp != nullptr, A, (double2*)Z, ldz);
+  const bool t = texp != nullptr;
+  // groups of 4 lanes for rules of up to 4 points, else 8 (idle lanes still cost FP64 pipe time)
+  if (g.m <= 4) {
+    if (precision == GF_FP32 && mixed)
+      k_fill_near<float2, true, 4><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (float2*)Z, ldz);
+    else if (precision == GF_FP32)
+      k_fill_near<float2, false, 4><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (float2*)Z, ldz);
+    else
+      k_fill_near<double2, false, 4><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (double2*)Z, ldz);
+  } else {
+    if (precision == GF_FP32 && mixed)
+      k_fill_near<float2, true, 8><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (float2*)Z, ldz);
+    else if (precision == GF_FP32)
+      k_fill_near<float2, false, 8><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (float2*)Z, ldz);
+    else
+      k_fill_near<double2, false, 8><<<(unsigned)blocks, 128, 0, s>>>(g, te, t, A, (double2*)Z, ldz);
+  }
   return cudaGetLastError();
 }
 
