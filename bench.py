@@ -38,6 +38,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
+SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM (32 banks x 4 B)
+SMEM_BYTES_PER_EVAL = 32  # Lagrange lattice: two 16-byte records per Green evaluation
 FALLBACK_SM_MHZ = 2070.0
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
@@ -345,7 +347,16 @@ def run_ours(args, wl, rank, world, local_rank):
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                     f"({src} max SM clock)",
                      "ops_per_launch": ops, "traffic": traffic,
-                     "mufu_frac": n_eval * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6)},
+                     "mufu_frac": n_eval * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6),
+                     # the resource that binds the table kernel (see profiles/): shared-memory reads of
+                     # the lattice image, 32 B per evaluation (two 16-byte records at random addresses)
+                     "smem": {"bytes_per_eval": SMEM_BYTES_PER_EVAL,
+                              "achieved_tbs": n_eval * m * m * SMEM_BYTES_PER_EVAL / (reg_ms / 1e3) / 1e12,
+                              "peak_tbs": SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e12,
+                              "frac": n_eval * m * m * SMEM_BYTES_PER_EVAL / (reg_ms / 1e3)
+                              / (SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6),
+                              "note": "random 16-byte reads by 32 lanes: bank conflicts give ~2.6 wavefronts per "
+                                      "conflict-free one, so the pipe saturates near frac 0.35"}},
         "clocks": clocks,
         "e2e": ({"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3} if e2e_s else

@@ -96,7 +96,7 @@ struct TabView {
   double lo64c, inv64c;
   const Cell64* cells64;
   // shared-memory image of the lattice for a lookup of degree deg (lat_b only for deg > 1)
-  size_t smem32_bytes(int deg) const { return (size_t)n_lat * (deg > 1 ? 32 : 16) + blob_vec4() * 16; }
+  __host__ __device__ size_t smem32_bytes(int deg) const { return (size_t)n_lat * (deg > 1 ? 32 : 16) + blob_vec4() * 16; }
 };
 
 // Marker (a quiet-NaN bit pattern) of a lattice cell that holds samples.

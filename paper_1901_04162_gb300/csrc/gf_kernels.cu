@@ -1066,10 +1066,15 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
   const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
   const double d = fabs(h);
   for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
-  double Rv[3];  // |r - v_c|
-  for (int c = 0; c < 3; ++c) {
-    const double dx = v[c][0] - r[0], dy = v[c][1] - r[1], dz = v[c][2] - r[2];
-    Rv[c] = sqrt(dx * dx + dy * dy + dz * dz);
+  // |r - v_c| (scalars, so that the edge loop picks them without a local array)
+  double Rv0, Rv1, Rv2;
+  {
+    const double* w = v[0];
+    Rv0 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
+    w = v[1];
+    Rv1 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
+    w = v[2];
+    Rv2 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
   }
   const float d32 = (float)d;
   const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
@@ -1120,7 +1125,7 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
     const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
     // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|
     const double R02 = P0 * P0 + d * d;
-    const double Rm = Rv[e], Rp = Rv[(e + 1) % 3];
+    const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
     double st = 0.5 * (lp * Rp - lm * Rm);
     if (R02 > 0) {
       const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
@@ -1772,6 +1777,10 @@ __device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const Near
   const F1 k32 = f1(k), d32 = f1(d);
   F1 edr, edi;
   exp_mjkr_f(k32, d32, te, use_table, lo, hi, &edr, &edi);
+  // |r - v_c|: R at the ends of the two edges that meet at v_c (scalars, so
+  // that the edge loop can pick them without a local-memory array)
+  const V3D dv0 = vsub(v[0], r), dv1 = vsub(v[1], r), dv2 = vsub(v[2], r);
+  const D1 Rv0 = dsqrt(vdot(dv0, dv0)), Rv1 = dsqrt(vdot(dv1, dv1)), Rv2 = dsqrt(vdot(dv2, dv2));
   DC sacc{D1{0, 0}, D1{0, 0}};
   DC vacc[3] = {{D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}};
   D1 vst[3] = {D1{0, 0}, D1{0, 0}, D1{0, 0}};
@@ -1781,8 +1790,8 @@ __device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const Near
     const D1 len = dsqrt(vdot(t, t));
     t = vscale(t, D1{1.0, 0.0} / len);
     const V3D mh = vcross(t, n);
-    const V3D ar = vsub(a, rho0), br = vsub(b, rho0);
-    const D1 P0 = vdot(ar, mh), lm = vdot(ar, t), lp = vdot(br, t);
+    const V3D ar = vsub(a, rho0);
+    const D1 P0 = vdot(ar, mh), lm = vdot(ar, t), lp = lm + len;
     if (fabs(P0.v) > 1e-12 * len.v) {
       const D1 aP = dabs(P0);
       const D1 iaP = D1{1.0, 0.0} / aP;
@@ -1824,12 +1833,12 @@ __device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const Near
     }
     const D1 lrd = D1{(double)lr.v, (double)lr.d} * (len * 0.5), lid = D1{(double)li.v, (double)li.d} * (len * 0.5);
     const D1 R02 = P0 * P0 + d * d;
-    const D1 Rm = dsqrt(lm * lm + R02), Rp = dsqrt(lp * lp + R02);
+    const D1 Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
     D1 st = (lp * Rp - lm * Rm) * 0.5;
     if (R02.v > 0) {
       const D1 fp = lp.v >= 0 ? lp + Rp : R02 / (Rp - lp);
       const D1 fm = lm.v >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st = st + R02 * (dlog(fp) - dlog(fm)) * 0.5;
+      st = st + R02 * dlog(fp / fm) * 0.5;
     }
     const D1 mhv[3] = {mh.x, mh.y, mh.z};
     for (int x = 0; x < 3; ++x) {
@@ -1850,7 +1859,9 @@ __device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const Near
 // One (near pair, direction) on 8 lanes, one test point per lane. Direction
 // 0..8: p's vertex coordinates, 9..17: q's, 18: k. The derivative of the
 // pair's share of L is reduced over the points and added to dtri / dk.
-template <bool MIXED>
+// One (near pair, derivative direction) per group of G lanes (lane = test
+// point): directions 0..8 = p's vertex coordinates, 9..17 = q's, 18 = k.
+template <bool MIXED, int G>
 __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, bool use_table, NearArgs A, double k,
                                                       double eta, BaryF bw, const float2* __restrict__ gZ, int64_t ldg,
                                                       double* dtri, double* dkacc) {
@@ -1858,10 +1869,10 @@ __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, boo
   const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
   const int64_t n_near = g.near_ptr[g.nt];
   const int64_t njobs = n_near * 19;
-  const int sub = threadIdx.x & 7;
-  const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) >> 3;
-  for (int64_t job = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3; job < njobs; job += ngroups) {
+  const int sub = threadIdx.x & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  for (int64_t job = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; job < njobs; job += ngroups) {
     const int64_t idx = job / 19;
     const int dir = (int)(job % 19);
     const int p = g.near_row[idx], q = g.near_idx[idx];
@@ -1919,7 +1930,7 @@ __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, boo
         }
       }
     }
-    for (int off = 1; off < 8; off <<= 1) dL += __shfl_xor_sync(gmask, dL, off);
+    for (int off = 1; off < G; off <<= 1) dL += __shfl_xor_sync(gmask, dL, off);
     if (sub == 0) {
       if (dir == 18) atomicAdd(dkacc, dL);
       else if (dir < 9) atomicAdd(&dtri[9 * (size_t)p + dir], dL);
@@ -2134,12 +2145,15 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
   }
   TabView te{};
   if (texp) te = *texp;
-  if (mixed)
-    k_adjoint_near<true><<<(unsigned)(sm_count() * 16), 128, 0, s>>>(g, te, texp != nullptr, A, k, eta, bw, gz, ldg,
-                                                                     dtri, dk);
-  else
-    k_adjoint_near<false><<<(unsigned)(sm_count() * 16), 128, 0, s>>>(g, te, texp != nullptr, A, k, eta, bw, gz, ldg,
-                                                                      dtri, dk);
+  const unsigned nblk = (unsigned)(sm_count() * 16);
+  const bool t = texp != nullptr;
+  if (g.m <= 4) {
+    if (mixed) k_adjoint_near<true, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    else k_adjoint_near<false, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+  } else {
+    if (mixed) k_adjoint_near<true, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    else k_adjoint_near<false, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+  }
   k_adjoint_gather<<<(g.nt + 127) / 128, 128, 0, s>>>(g.nt, g.tvert, dtri, dxyz);
   return cudaGetLastError();
 }
