@@ -1859,6 +1859,474 @@ __device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const Near
 // One (near pair, direction) on 8 lanes, one test point per lane. Direction
 // 0..8: p's vertex coordinates, 9..17: q's, 18: k. The derivative of the
 // pair's share of L is reduced over the points and added to dtri / dk.
+// ---- near pairs, reverse mode (mixed precision): one pass per (near pair,
+// test point) gives the derivatives along all 19 directions. The values are
+// those of inner_integrals_mixed (FP64 frames, projection, static closed form
+// and sums; FP32 samples of e^{-jkR}); the adjoints follow the same split,
+// FP32 inside the sampled loops, FP64 elsewhere. Sample derivatives use
+// dE/dR = -jk E and dE/dk = -jR E on the interpolated E.
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Adds d(contribution to L)/d(vertices of p), d/d(vertices of q), d/dk of
+// one test point a of near pair (p, q): L = sum_ij Re(conj(gZ_ij) dZ_ij).
+__device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3], const float lb[3], double wa,
+                                   const NearArgs& A, double k, double eta, const Tab32& te, bool use_table, float lo,
+                                   float hi, const int ecp[3], const int ecq[3], const float2* __restrict__ gZ,
+                                   int64_t ldg, double gp[3][3], double gq[3][3], double* gk) {
+  const float kpi = (float)(k / kPi), k32 = (float)k;
+  double r[3];
+  for (int x = 0; x < 3; ++x) r[x] = (double)lb[0] * vp[0][x] + (double)lb[1] * vp[1][x] + (double)lb[2] * vp[2][x];
+  // ---- source frame
+  double e1[3], e2[3], nn[3], n[3];
+  for (int x = 0; x < 3; ++x) {
+    e1[x] = vq[1][x] - vq[0][x];
+    e2[x] = vq[2][x] - vq[0][x];
+  }
+  cross3(e1, e2, nn);
+  const double Ln = sqrt(dot3(nn, nn)), iL = 1.0 / Ln;
+  for (int x = 0; x < 3; ++x) n[x] = nn[x] * iL;
+  double len[3], t[3][3], m[3][3];
+  for (int e = 0; e < 3; ++e) {
+    const int e2i = e == 2 ? 0 : e + 1;
+    double tt[3] = {vq[e2i][0] - vq[e][0], vq[e2i][1] - vq[e][1], vq[e2i][2] - vq[e][2]};
+    len[e] = sqrt(dot3(tt, tt));
+    for (int x = 0; x < 3; ++x) t[e][x] = tt[x] / len[e];
+    cross3(t[e], n, m[e]);
+  }
+  // ---- projection, vertex distances, e^{-jkd}
+  double rv0[3] = {r[0] - vq[0][0], r[1] - vq[0][1], r[2] - vq[0][2]};
+  const double h = dot3(n, rv0), d = fabs(h);
+  double rho0[3];
+  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  double Rv[3];
+  for (int c = 0; c < 3; ++c) {
+    const double dx = vq[c][0] - r[0], dy = vq[c][1] - r[1], dz = vq[c][2] - r[2];
+    Rv[c] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  const float d32 = (float)d;
+  const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
+  // ---- forward: the per-edge sums
+  double sre = 0, sim = 0, vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0}, vst[3] = {0, 0, 0};
+  for (int e = 0; e < 3; ++e) {
+    const double* a = vq[e];
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double P0 = dot3(ar, m[e]), lm = dot3(ar, t[e]), lp = lm + len[e];
+    if (fabs(P0) > 1e-12 * len[e]) {
+      const float aP32 = (float)fabs(P0);
+      const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
+      const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
+      float cr = 0.f, ci = 0.f;
+      for (int i = 0; i < A.nphi; ++i) {
+        const float u = fmaf(half, A.fx_phi[i], mid);
+        const float E = expf(u);
+        const float ch = 0.5f * (E + __frcp_rn(E));
+        const float rho = aP32 * ch;
+        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
+        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        cr = fmaf(ed.x - eR.x, wt, cr);
+        ci = fmaf(ed.y - eR.y, wt, ci);
+      }
+      const double sg = P0 > 0 ? (double)half : -(double)half;
+      sre += (double)cr * sg;
+      sim += (double)ci * sg;
+    }
+    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    const float tx = (float)t[e][0], ty = (float)t[e][1], tz = (float)t[e][2];
+    const float hl = 0.5f * (float)len[e];
+    float lr = 0.f, li = 0.f;
+    for (int i = 0; i < A.nl; ++i) {
+      const float sp = hl * (A.fx_l[i] + 1.0f);
+      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
+      lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
+      li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
+    }
+    const double lrd = (double)lr * (0.5 * len[e]), lid = (double)li * (0.5 * len[e]);
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = Rv[e], Rp = Rv[e == 2 ? 0 : e + 1];
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    if (R02 > 0) {
+      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
+      st += 0.5 * R02 * log(fp / fm);
+    }
+    for (int x = 0; x < 3; ++x) {
+      vre[x] += m[e][x] * lrd;
+      vim[x] += m[e][x] * lid;
+      vst[x] += m[e][x] * st;
+    }
+  }
+  const double c4 = 1.0 / (4.0 * kPi), ik = 1.0 / k;
+  const double I0r = sim * ik * c4, I0i = -sre * ik * c4;
+  double I1r[3], I1i[3];
+  for (int x = 0; x < 3; ++x) {
+    I1r[x] = (vst[x] - vim[x] * ik) * c4;
+    I1i[x] = vre[x] * ik * c4;
+  }
+  // ---- assembly: values and adjoints of I0, I1, rho0, r, p's vertices, L = |nn|, k
+  double bI0r = 0, bI0i = 0, bI1r[3] = {0, 0, 0}, bI1i[3] = {0, 0, 0}, brho[3] = {0, 0, 0}, br[3] = {0, 0, 0};
+  double bk = 0, bik2 = 0, bA = 0;
+  const double Aq = 0.5 * Ln, ik2 = ik * ik;
+  for (int i = 0; i < 3; ++i) {
+    if (!edge_valid(ecp[i])) continue;
+    const int i1 = i == 2 ? 0 : i + 1, i2 = i1 == 2 ? 0 : i1 + 1;
+    const double ei[3] = {vp[i2][0] - vp[i1][0], vp[i2][1] - vp[i1][1], vp[i2][2] - vp[i1][2]};
+    const double li_ = sqrt(dot3(ei, ei)), si = (ecp[i] & 1) ? -1.0 : 1.0, sli = si * li_;
+    const double f[3] = {r[0] - vp[i][0], r[1] - vp[i][1], r[2] - vp[i][2]};
+    double bf[3] = {0, 0, 0}, bsli = 0;
+    for (int j = 0; j < 3; ++j) {
+      if (!edge_valid(ecq[j])) continue;
+      const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
+      const double ej[3] = {vq[j2][0] - vq[j1][0], vq[j2][1] - vq[j1][1], vq[j2][2] - vq[j1][2]};
+      const double lj = sqrt(dot3(ej, ej)), sj = (ecq[j] & 1) ? -1.0 : 1.0, slj = sj * lj;
+      const double dv[3] = {rho0[0] - vq[j][0], rho0[1] - vq[j][1], rho0[2] - vq[j][2]};
+      double Jr[3], Ji[3];
+      for (int x = 0; x < 3; ++x) {
+        Jr[x] = I1r[x] + dv[x] * I0r;
+        Ji[x] = I1i[x] + dv[x] * I0i;
+      }
+      const double tr = 0.25 * dot3(f, Jr) - I0r * ik2, ti = 0.25 * dot3(f, Ji) - I0i * ik2;
+      const double c = k * eta * wa * sli * slj / Aq;
+      const float2 gz = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+      // L = gz.x (-c ti) + gz.y (c tr)
+      const double btr = (double)gz.y * c, bti = -(double)gz.x * c;
+      const double bc = (double)gz.y * tr - (double)gz.x * ti;
+      double bdv[3];
+      for (int x = 0; x < 3; ++x) {
+        bf[x] += 0.25 * (btr * Jr[x] + bti * Ji[x]);
+        const double bJr = 0.25 * btr * f[x], bJi = 0.25 * bti * f[x];
+        bI1r[x] += bJr;
+        bI1i[x] += bJi;
+        bdv[x] = bJr * I0r + bJi * I0i;
+        bI0r += bJr * dv[x];
+        bI0i += bJi * dv[x];
+        brho[x] += bdv[x];
+        gq[j][x] -= bdv[x];
+      }
+      bI0r -= btr * ik2;
+      bI0i -= bti * ik2;
+      bik2 -= btr * I0r + bti * I0i;
+      // c = k eta wa sl_i sl_j / A_q
+      bk += bc * c / k;
+      bsli += bc * c / sli;
+      bA -= bc * c / Aq;
+      const double bslj = bc * c / slj;
+      for (int x = 0; x < 3; ++x) {
+        const double g = bslj * sj * ej[x] / lj;
+        gq[j2][x] += g;
+        gq[j1][x] -= g;
+      }
+    }
+    for (int x = 0; x < 3; ++x) {
+      br[x] += bf[x];
+      gp[i][x] -= bf[x];
+      const double g = bsli * si * ei[x] / li_;
+      gp[i2][x] += g;
+      gp[i1][x] -= g;
+    }
+  }
+  bk -= 2.0 * bik2 * ik2 * ik;
+  // ---- reverse of I0, I1 = f(sre, sim, vre, vim, vst, k)
+  const double bsim = bI0r * ik * c4, bsre = -bI0i * ik * c4;
+  double bvst[3], bvim[3], bvre[3];
+  double bik = c4 * (bI0r * sim - bI0i * sre);
+  for (int x = 0; x < 3; ++x) {
+    bvst[x] = bI1r[x] * c4;
+    bvim[x] = -bI1r[x] * ik * c4;
+    bvre[x] = bI1i[x] * ik * c4;
+    bik += c4 * (-bI1r[x] * vim[x] + bI1i[x] * vre[x]);
+  }
+  bk -= bik * ik * ik;
+  // ---- reverse of the edges (recomputing their forward values)
+  double bd = 0, bRv[3] = {0, 0, 0}, bt[3][3], bm[3][3], blen[3];
+  float bedr = 0.f, bedi = 0.f;
+  for (int e = 0; e < 3; ++e) {
+    const int en = e == 2 ? 0 : e + 1;
+    const double* a = vq[e];
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double P0 = dot3(ar, m[e]), lm = dot3(ar, t[e]), lp = lm + len[e];
+    double bP0 = 0, blm = 0, blp = 0, bR02 = 0;
+    blen[e] = 0;
+    // line integral: values then adjoints
+    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    const float tx = (float)t[e][0], ty = (float)t[e][1], tz = (float)t[e][2];
+    const float hl = 0.5f * (float)len[e];
+    float lr = 0.f, li = 0.f;
+    for (int i = 0; i < A.nl; ++i) {
+      const float sp = hl * (A.fx_l[i] + 1.0f);
+      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
+      lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
+      li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
+    }
+    const double blrd = dot3(bvre, m[e]), blid = dot3(bvim, m[e]);
+    const double lrd = (double)lr * (0.5 * len[e]), lid = (double)li * (0.5 * len[e]);
+    const float blr = (float)(blrd * 0.5 * len[e]), bli = (float)(blid * 0.5 * len[e]);
+    blen[e] += 0.5 * (blrd * (double)lr + blid * (double)li);
+    float bax = 0.f, bay = 0.f, baz = 0.f, btx = 0.f, bty = 0.f, btz = 0.f, bhl = 0.f, bk32 = 0.f;
+    for (int i = 0; i < A.nl; ++i) {
+      const float sp = hl * (A.fx_l[i] + 1.0f);
+      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
+      // lr += w (Er - 1); li += w (Ei + k R); dEr/dph = Ei, dEi/dph = -Er, ph = k R
+      const float bEr = blr * A.fw_l[i], bEi = bli * A.fw_l[i];
+      const float bph = bEr * eR.y - bEi * eR.x;
+      const float bR = bph * k32 + bEi * k32;
+      bk32 += bph * R + bEi * R;
+      const float iR = __frcp_rn(R);
+      const float gx = bR * x0 * iR, gy = bR * x1 * iR, gz_ = bR * x2 * iR;
+      bax += gx;
+      bay += gy;
+      baz += gz_;
+      btx += gx * sp;
+      bty += gy * sp;
+      btz += gz_ * sp;
+      bhl += (gx * tx + gy * ty + gz_ * tz) * (A.fx_l[i] + 1.0f);
+    }
+    bk += (double)bk32;
+    blen[e] += 0.5 * (double)bhl;
+    // (a - r): a = v_e
+    gq[e][0] += bax;
+    gq[e][1] += bay;
+    gq[e][2] += baz;
+    br[0] -= bax;
+    br[1] -= bay;
+    br[2] -= baz;
+    bt[e][0] = btx;
+    bt[e][1] = bty;
+    bt[e][2] = btz;
+    // static part
+    const double bst = dot3(bvst, m[e]);
+    for (int x = 0; x < 3; ++x) bm[e][x] = bvre[x] * lrd + bvim[x] * lid;
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = Rv[e], Rp = Rv[en];
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    blp += 0.5 * Rp * bst;
+    blm -= 0.5 * Rm * bst;
+    double bRp = 0.5 * lp * bst, bRm = -0.5 * lm * bst;
+    if (R02 > 0) {
+      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
+      const double Lg = log(fp / fm);
+      st += 0.5 * R02 * Lg;
+      bR02 += 0.5 * Lg * bst;
+      const double bL = 0.5 * R02 * bst;  // adjoint of log fp - log fm
+      if (lp >= 0) {
+        const double g = bL / fp;
+        blp += g;
+        bRp += g;
+      } else {  // log R02 - log(Rp - lp)
+        const double g = bL / (Rp - lp);
+        bR02 += bL / R02;
+        bRp -= g;
+        blp += g;
+      }
+      if (lm >= 0) {
+        const double g = bL / fm;
+        blm -= g;
+        bRm -= g;
+      } else {
+        const double g = bL / (Rm - lm);
+        bR02 -= bL / R02;
+        bRm += g;
+        blm -= g;
+      }
+    }
+    for (int x = 0; x < 3; ++x) bm[e][x] += bvst[x] * st;
+    bRv[e] += bRm;
+    bRv[en] += bRp;
+    // angular part
+    if (fabs(P0) > 1e-12 * len[e]) {
+      const float aP32 = (float)fabs(P0);
+      const float zm = (float)lm / aP32, zp = (float)lp / aP32;
+      const float um = asinhf(zm), up = asinhf(zp);
+      const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
+      float cr = 0.f, ci = 0.f;
+      for (int i = 0; i < A.nphi; ++i) {
+        const float u = fmaf(half, A.fx_phi[i], mid);
+        const float E = expf(u);
+        const float ch = 0.5f * (E + __frcp_rn(E));
+        const float rho = aP32 * ch;
+        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
+        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        cr = fmaf(ed.x - eR.x, wt, cr);
+        ci = fmaf(ed.y - eR.y, wt, ci);
+      }
+      const double sgn = P0 > 0 ? 1.0 : -1.0, sg = sgn * (double)half;
+      const float bcr = (float)(bsre * sg), bci = (float)(bsim * sg);
+      float bhalf = (float)(sgn * (bsre * (double)cr + bsim * (double)ci)), bmid = 0.f, baP = 0.f, bd32 = 0.f;
+      float bk32a = 0.f;
+      for (int i = 0; i < A.nphi; ++i) {
+        const float u = fmaf(half, A.fx_phi[i], mid);
+        const float E = expf(u), iE = __frcp_rn(E);
+        const float ch = 0.5f * (E + iE), sh = 0.5f * (E - iE);
+        const float rho = aP32 * ch;
+        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
+        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        bedr += bcr * wt;
+        bedi += bci * wt;
+        const float bEr = -bcr * wt, bEi = -bci * wt;
+        const float bph = bEr * eR.y - bEi * eR.x;
+        const float bRe = bph * k32;
+        bk32a += bph * Re;
+        const float bwt = bcr * (ed.x - eR.x) + bci * (ed.y - eR.y);
+        float bch = -bwt * wt / ch;
+        const float iRe = __frcp_rn(Re);
+        const float brho = bRe * rho * iRe;
+        bd32 += bRe * d32 * iRe;
+        baP += brho * ch;
+        bch += brho * aP32;
+        const float bu = bch * sh;
+        bhalf += bu * A.fx_phi[i];
+        bmid += bu;
+      }
+      bk += (double)bk32a;
+      bd += (double)bd32;
+      const float bup = 0.5f * (bhalf + bmid), bum = 0.5f * (bmid - bhalf);
+      const float bzp = bup * rsqrtf(1.f + zp * zp), bzm = bum * rsqrtf(1.f + zm * zm);
+      blp += (double)(bzp / aP32);
+      blm += (double)(bzm / aP32);
+      baP -= (bzp * zp + bzm * zm) / aP32;
+      bP0 += sgn * (double)baP;
+    }
+    bP0 += 2.0 * P0 * bR02;
+    bd += 2.0 * d * bR02;
+    blm += blp;
+    blen[e] += blp;
+    for (int x = 0; x < 3; ++x) {
+      const double bar = bP0 * m[e][x] + blm * t[e][x];
+      bm[e][x] += bP0 * ar[x];
+      bt[e][x] += blm * ar[x];
+      gq[e][x] += bar;
+      brho[x] -= bar;
+    }
+  }
+  // e^{-jkd}
+  {
+    const float bph = bedr * ed.y - bedi * ed.x;
+    bd += (double)(bph * k32);
+    bk += (double)(bph * d32);
+  }
+  // vertex distances
+  for (int c = 0; c < 3; ++c) {
+    for (int x = 0; x < 3; ++x) {
+      const double g = bRv[c] * (vq[c][x] - r[x]) / Rv[c];
+      gq[c][x] += g;
+      br[x] -= g;
+    }
+  }
+  // d = |h|, rho0 = r - h n, h = n . (r - v0)
+  double bh = (h >= 0 ? 1.0 : -1.0) * bd, bn[3];
+  for (int x = 0; x < 3; ++x) {
+    br[x] += brho[x];
+    bh -= brho[x] * n[x];
+    bn[x] = -h * brho[x];
+  }
+  for (int x = 0; x < 3; ++x) {
+    bn[x] += bh * rv0[x];
+    br[x] += bh * n[x];
+    gq[0][x] -= bh * n[x];
+  }
+  // frame: m_e = t_e x n, t_e = tt / |tt|, n = nn / |nn|, A_q = |nn| / 2
+  for (int e = 0; e < 3; ++e) {
+    const int en = e == 2 ? 0 : e + 1;
+    double c1[3], c2[3];
+    cross3(n, bm[e], c1);  // d/dt of (t x n) . bm
+    cross3(bm[e], t[e], c2);  // d/dn
+    for (int x = 0; x < 3; ++x) {
+      bt[e][x] += c1[x];
+      bn[x] += c2[x];
+    }
+    const double tb = dot3(t[e], bt[e]);
+    for (int x = 0; x < 3; ++x) {
+      const double btt = (bt[e][x] - t[e][x] * tb) / len[e] + blen[e] * t[e][x];
+      gq[en][x] += btt;
+      gq[e][x] -= btt;
+    }
+  }
+  {
+    const double nb = dot3(n, bn);
+    double bnn[3];
+    for (int x = 0; x < 3; ++x) bnn[x] = (bn[x] - n[x] * nb) * iL + 0.5 * bA * n[x];
+    double be1[3], be2[3];
+    cross3(e2, bnn, be1);
+    cross3(bnn, e1, be2);
+    for (int x = 0; x < 3; ++x) {
+      gq[1][x] += be1[x];
+      gq[2][x] += be2[x];
+      gq[0][x] -= be1[x] + be2[x];
+    }
+  }
+  // r = sum_c l_c v_c
+  for (int c = 0; c < 3; ++c)
+    for (int x = 0; x < 3; ++x) gp[c][x] += (double)lb[c] * br[x];
+  *gk += bk;
+}
+
+// One near pair per group of G lanes, lane = test point; all 19 derivatives
+// in one reverse pass, reduced over the group.
+template <int G>
+__global__ void __launch_bounds__(128) k_adjoint_near_rev(GeoView g, TabView te, bool use_table, NearArgs A, double k,
+                                                          double eta, BaryF bw, const float2* __restrict__ gZ,
+                                                          int64_t ldg, double* dtri, double* dkacc) {
+  const Tab32 te32 = tab32(te);
+  const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
+  const int64_t n_near = g.near_ptr[g.nt];
+  const int sub = threadIdx.x & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  for (int64_t itn = 0; itn < iters; ++itn) {
+    const int64_t idx = g0 + itn * ngroups;
+    if (idx >= n_near) continue;  // uniform over the group
+    const int p = g.near_row[idx], q = g.near_idx[idx];
+    double gp[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gk = 0;
+    if (sub < g.m) {
+      double vp[3][3], vq[3][3];
+      for (int c = 0; c < 3; ++c)
+        for (int x = 0; x < 3; ++x) {
+          vp[c][x] = g.v64[9 * (size_t)p + 3 * c + x];
+          vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
+        }
+      const int4 ep = g.tedge[p], eq = g.tedge[q];
+      const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+      const double wa = g.pts64[4 * ((size_t)sub * g.nt + p) + 3];
+      near_point_adjoint(vp, vq, bw.l[sub], wa, A, k, eta, te32, use_table, lo32, hi32, ecp, ecq, gZ, ldg, gp, gq,
+                         &gk);
+    }
+    for (int off = 1; off < G; off <<= 1) {
+      for (int c = 0; c < 3; ++c)
+        for (int x = 0; x < 3; ++x) {
+          gp[c][x] += __shfl_xor_sync(gmask, gp[c][x], off);
+          gq[c][x] += __shfl_xor_sync(gmask, gq[c][x], off);
+        }
+      gk += __shfl_xor_sync(gmask, gk, off);
+    }
+    if (sub == 0) {
+      for (int c = 0; c < 3; ++c)
+        for (int x = 0; x < 3; ++x) {
+          atomicAdd(&dtri[9 * (size_t)p + 3 * c + x], gp[c][x]);
+          atomicAdd(&dtri[9 * (size_t)q + 3 * c + x], gq[c][x]);
+        }
+      atomicAdd(dkacc, gk);
+    }
+  }
+}
+
 // One (near pair, derivative direction) per group of G lanes (lane = test
 // point): directions 0..8 = p's vertex coordinates, 9..17 = q's, 18 = k.
 template <bool MIXED, int G>
@@ -2147,11 +2615,13 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
   if (texp) te = *texp;
   const unsigned nblk = (unsigned)(sm_count() * 16);
   const bool t = texp != nullptr;
+  // mixed precision: reverse mode, one pass per near pair; FP64 throughout:
+  // forward-mode duals, one pass per (near pair, direction)
   if (g.m <= 4) {
-    if (mixed) k_adjoint_near<true, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    if (mixed) k_adjoint_near_rev<4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
     else k_adjoint_near<false, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   } else {
-    if (mixed) k_adjoint_near<true, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    if (mixed) k_adjoint_near_rev<8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
     else k_adjoint_near<false, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   }
   k_adjoint_gather<<<(g.nt + 127) / 128, 128, 0, s>>>(g.nt, g.tvert, dtri, dxyz);
