@@ -361,8 +361,8 @@ def run_ours(args, wl, rank, world, local_rank):
         "e2e": ({"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3} if e2e_s else
                 {"value": None, "reason": "Z larger than 8 GiB: no pinned host copy per step"}),
-        # per step: range 3 (FP32; 2 in FP64), 5 per table x 2 tables, regular 1, near 1
-        "gpu_launches": (15 if prec == gf.GF_FP32 else 14) * args.steps,
+        # per step: range 3 (FP32; 2 in FP64), both tables 3, regular 1, near 1
+        "gpu_launches": (8 if prec == gf.GF_FP32 else 7) * args.steps,
     }
 
     # ---- accuracy vs the FP64 oracle on sampled rows (outside the timed region)

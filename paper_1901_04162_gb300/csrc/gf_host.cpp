@@ -1012,16 +1012,36 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
   }
   // ---- device: values, coefficients, hash and images of both tables
   e = cudaMemcpyAsync(base, hbuf.data(), upload, cudaMemcpyHostToDevice, s);
-  for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
-    gf_table::One& o = *ones[w];
-    const int n = (int)o.r.size();
-    e = launch_table_image(o.kind, k, o.degree, n, o.d_node64, o.d_zflag, o.d_node32, o.d_c64, o.d_c32a, o.d_c32b,
-                           o.d_fval, (int)o.n_hash, r_min, o.dr, o.d_hash, o.n_cells64, o.lo64c, o.inv64c,
-                           o.d_cells64, s);
-    if (e == cudaSuccess)
-      e = launch_table_lattice(o.view(), o.degree, o.d_fval, o.d_lat_j, o.d_lat_cmp, o.kind == GF_GREEN,
-                               o.d_lat_a, o.d_lat_b, s);
+  TableBuild tb[2];
+  for (int w = 0; w < 2; ++w) {
+    const gf_table::One& o = *ones[w];
+    TableBuild& b = tb[w];
+    b.kind = o.kind;
+    b.deg = o.degree;
+    b.n = (int)o.r.size();
+    b.n_hash = (int)o.n_hash;
+    b.n_cells64 = o.n_cells64;
+    b.r_lo = r_min;
+    b.dr = o.dr;
+    b.lo64c = o.lo64c;
+    b.inv64c = o.inv64c;
+    b.node64 = o.d_node64;
+    b.zflag = o.d_zflag;
+    b.fval = o.d_fval;
+    b.c64 = o.d_c64;
+    b.node32 = o.d_node32;
+    b.c32a = o.d_c32a;
+    b.c32b = o.d_c32b;
+    b.hash = o.d_hash;
+    b.cells64 = o.d_cells64;
+    b.view = o.view();
+    b.lat_j = o.d_lat_j;
+    b.cmp = o.d_lat_cmp;
+    b.flag_in_b = o.kind == GF_GREEN;
+    b.lat_a = o.d_lat_a;
+    b.lat_b = o.d_lat_b;
   }
+  if (e == cudaSuccess) e = launch_tables(tb[0], tb[1], k, s);
   if (e != cudaSuccess) {
     gf_table_destroy(T.release());
     return cuda_fail(e, "gf_table_create");

@@ -134,16 +134,30 @@ cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double*
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
                                  double* frame64, cudaStream_t s);
-cudaError_t launch_table_image(int kind, double k, int degree, int n_nodes, const double* node64,
-                               const int8_t* zero_flag, float* node32, double2* c64, float4* c32a,
-                               float4* c32b, double* fval, int n_hash, double r_lo, double dr,
-                               int32_t* hash, int n_cells64, double lo64c, double inv64c, Cell64* cells64,
-                               cudaStream_t s);
-// Lattice records (lat_j[i]: interval of cell i's middle, bit 31 set for a
-// cell holding samples) and the compact interval records of the blob (cmp);
-// flag_in_b: the flag bit sits in lat_b (Green) or lat_a (Exp).
-cudaError_t launch_table_lattice(const TabView& v, int degree, const double* fval, const int32_t* lat_j,
-                                 const int32_t* cmp, bool flag_in_b, float4* lat_a, float4* lat_b, cudaStream_t s);
+// Device build of one table (arrays in its arena; view = its TabView, whose
+// lattice fields the lattice stage reads).
+struct TableBuild {
+  int kind, deg, n, n_hash, n_cells64;
+  double r_lo, dr, lo64c, inv64c;
+  const double* node64;
+  const int8_t* zflag;
+  double* fval;
+  double2* c64;
+  float* node32;
+  float4* c32a;
+  float4* c32b;
+  int32_t* hash;
+  Cell64* cells64;
+  TabView view;
+  const int32_t* lat_j;  // interval of each lattice cell's middle, bit 31: the cell holds samples
+  const int32_t* cmp;    // interval of each compact record of the blob
+  bool flag_in_b;        // the flag bit sits in lat_b (Green) or lat_a (Exp)
+  float4* lat_a;
+  float4* lat_b;
+};
+// Values, Eq. (6) hash, FP64 cells, coefficients and lattice images of two
+// tables in three launches on s.
+cudaError_t launch_tables(const TableBuild& a, const TableBuild& b, double k, cudaStream_t s);
 cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);

@@ -109,10 +109,8 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
 }
 
 // ---------------------------------------------------------------- table image
-__global__ void k_table_values(int kind, double k, int n, const double* __restrict__ r,
-                               const int8_t* __restrict__ zflag, double* fval) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__device__ void dev_table_values(int j, int kind, double k, const double* __restrict__ r,
+                                 const int8_t* __restrict__ zflag, double* fval) {
   double s, c;
   sincos(k * r[j], &s, &c);
   double re = c, im = -s;
@@ -165,10 +163,8 @@ __device__ void interval_poly(int deg, int n, const double* __restrict__ r, cons
   }
 }
 
-__global__ void k_table_coef(int deg, int n, const double* __restrict__ r, const double* __restrict__ f,
-                             double2* c64, float* node32, float4* c32a, float4* c32b) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__device__ void dev_table_coef(int j, int deg, int n, const double* __restrict__ r, const double* __restrict__ f,
+                               double2* c64, float* node32, float4* c32a, float4* c32b) {
   float a32 = (float)r[j];
   node32[j] = a32;
   if (j >= n - 1) return;
@@ -184,9 +180,7 @@ __global__ void k_table_coef(int deg, int n, const double* __restrict__ r, const
 
 // Hash of Eq. (6): cell c holds the largest sample index whose cell
 // floor((r_j - r_min)/dr) is <= c (the forward-filled array); cell 0 holds 0.
-__global__ void k_table_hash(int n, const double* __restrict__ r, int n_hash, double r_lo, double dr, int32_t* hash) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_hash) return;
+__device__ void dev_table_hash(int c, int n, const double* __restrict__ r, double r_lo, double dr, int32_t* hash) {
   if (c == 0) {
     hash[0] = 0;
     return;
@@ -344,10 +338,8 @@ __device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
   return make_double2(re, im);
 }
 
-__global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_cells, double lo, double inv,
-                                Cell64* cells) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n_cells) return;
+__device__ void dev_table_cells64(int c, int n, const double* __restrict__ node64, double lo, double inv,
+                                  Cell64* cells) {
   auto first_at_or_after = [&](int cc) {
     int a = 1, b = n - 1;
     while (a < b) {
@@ -369,10 +361,9 @@ __global__ void k_table_cells64(int n, const double* __restrict__ node64, int n_
 // Lattice records: the polynomial of the interval at the cell's middle about
 // the cell anchor A_i = fma(i, h, lo) (the anchor the lookups recompute),
 // with the flag bit of the cells holding samples.
-__global__ void k_table_lattice(TabView v, int deg, const double* __restrict__ r, const double* __restrict__ f,
-                                const int32_t* __restrict__ lat_j, const int32_t* __restrict__ cmp, bool flag_in_b,
-                                float4* la, float4* lb) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ void dev_table_lattice(int i, const TabView& v, int deg, const double* __restrict__ r,
+                                  const double* __restrict__ f, const int32_t* __restrict__ lat_j,
+                                  const int32_t* __restrict__ cmp, bool flag_in_b, float4* la, float4* lb) {
   if (i < v.n_cmp) {  // compact interval records of the blob
     float4* ca = const_cast<float4*>(v.lat_blob) + (v.n_busy + 3) / 4 + v.n_busy + v.n_sub;
     ca[i] = v.c32a[cmp[i]];
@@ -405,6 +396,44 @@ __global__ void k_table_lattice(TabView v, int deg, const double* __restrict__ r
   }
   la[i] = a;
   lb[i] = b;
+}
+
+// The table builds of both tables (Green and Exp) in three launches: sample
+// values, hash and FP64 cells; interval coefficients; lattice records.
+__global__ void k_tables_values(TableBuild a, TableBuild b, double k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TableBuild* t[2] = {&a, &b};
+  for (int w = 0; w < 2; ++w) {
+    const TableBuild& T = *t[w];
+    if (i < T.n) return dev_table_values(i, T.kind, k, T.node64, T.zflag, T.fval);
+    i -= T.n;
+    if (i < T.n_hash) return dev_table_hash(i, T.n, T.node64, T.r_lo, T.dr, T.hash);
+    i -= T.n_hash;
+    if (i < T.n_cells64) return dev_table_cells64(i, T.n, T.node64, T.lo64c, T.inv64c, T.cells64);
+    i -= T.n_cells64;
+  }
+}
+
+__global__ void k_tables_coef(TableBuild a, TableBuild b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TableBuild* t[2] = {&a, &b};
+  for (int w = 0; w < 2; ++w) {
+    const TableBuild& T = *t[w];
+    if (i < T.n) return dev_table_coef(i, T.deg, T.n, T.node64, T.fval, T.c64, T.node32, T.c32a, T.c32b);
+    i -= T.n;
+  }
+}
+
+__global__ void k_tables_lattice(TableBuild a, TableBuild b) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const TableBuild* t[2] = {&a, &b};
+  for (int w = 0; w < 2; ++w) {
+    const TableBuild& T = *t[w];
+    const int n = max(T.view.n_lat, T.view.n_cmp);
+    if (i < n)
+      return dev_table_lattice(i, T.view, T.deg, T.node64, T.fval, T.lat_j, T.cmp, T.flag_in_b, T.lat_a, T.lat_b);
+    i -= n;
+  }
 }
 
 template <int DEG>
@@ -2643,21 +2672,13 @@ cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_table_image(int kind, double k, int degree, int n, const double* node64, const int8_t* zflag,
-                               float* node32, double2* c64, float4* c32a, float4* c32b, double* fval, int n_hash,
-                               double r_lo, double dr, int32_t* hash, int n_cells64, double lo64c,
-                               double inv64c, Cell64* cells64, cudaStream_t s) {
-  k_table_values<<<(n + 255) / 256, 256, 0, s>>>(kind, k, n, node64, zflag, fval);
-  k_table_coef<<<(n + 255) / 256, 256, 0, s>>>(degree, n, node64, fval, c64, node32, c32a, c32b);
-  k_table_hash<<<(n_hash + 255) / 256, 256, 0, s>>>(n, node64, n_hash, r_lo, dr, hash);
-  k_table_cells64<<<(n_cells64 + 255) / 256, 256, 0, s>>>(n, node64, n_cells64, lo64c, inv64c, cells64);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_table_lattice(const TabView& v, int degree, const double* fval, const int32_t* lat_j,
-                                 const int32_t* cmp, bool flag_in_b, float4* lat_a, float4* lat_b, cudaStream_t s) {
-  const int n = std::max(v.n_lat, v.n_cmp);
-  k_table_lattice<<<(n + 255) / 256, 256, 0, s>>>(v, degree, v.node64, fval, lat_j, cmp, flag_in_b, lat_a, lat_b);
+cudaError_t launch_tables(const TableBuild& a, const TableBuild& b, double k, cudaStream_t s) {
+  const int n1 = a.n + a.n_hash + a.n_cells64 + b.n + b.n_hash + b.n_cells64;
+  const int n2 = a.n + b.n;
+  const int n3 = std::max(a.view.n_lat, a.view.n_cmp) + std::max(b.view.n_lat, b.view.n_cmp);
+  k_tables_values<<<(n1 + 255) / 256, 256, 0, s>>>(a, b, k);
+  k_tables_coef<<<(n2 + 127) / 128, 128, 0, s>>>(a, b);
+  k_tables_lattice<<<(n3 + 127) / 128, 128, 0, s>>>(a, b);
   return cudaGetLastError();
 }
 

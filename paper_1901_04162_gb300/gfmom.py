@@ -98,14 +98,20 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
+_torch_cuda = None  # torch.cuda if torch with CUDA is importable, else False (checked once)
+
+
 def _stream_ptr(stream):
+    global _torch_cuda
     if stream is None:
-        try:
-            import torch
-            if torch.cuda.is_available():
-                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
-        except ImportError:
-            pass
+        if _torch_cuda is None:
+            try:
+                import torch
+                _torch_cuda = torch.cuda if torch.cuda.is_available() else False
+            except ImportError:
+                _torch_cuda = False
+        if _torch_cuda:
+            return C.c_void_p(_torch_cuda.current_stream().cuda_stream)
         return None
     return C.c_void_p(getattr(stream, "cuda_stream", stream))
 
