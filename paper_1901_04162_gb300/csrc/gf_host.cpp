@@ -111,30 +111,40 @@ static double fact(int n) {
   return f;
 }
 
-// Eq. (11) bound of interval j relative to min |f| on it (see gf_table_create).
-static double eq11_rel(const std::vector<double>& r, int j, int deg, int kind, double k) {
-  const int n = (int)r.size();
-  int s0 = deg <= 1 ? j : std::min(std::max(j - (deg - 1) / 2, 0), n - 1 - deg);
-  const double h = r[j + 1] - r[j];
-  double om = h * h / 4.0;
-  for (int s = s0; s <= s0 + deg; ++s)
-    if (s != j && s != j + 1) om *= std::max(std::fabs(r[j] - r[s]), std::fabs(r[j + 1] - r[s]));
-  const int q = deg + 1;
-  double mq = 0.0;
-  if (kind == GF_EXP) {
-    mq = std::pow(k, q);
-  } else {
-    for (int i = 0; i <= q; ++i)
-      mq += fact(q) / (fact(i) * fact(q - i)) * std::pow(k, q - i) * fact(i) / std::pow(r[s0], i + 1);
+// Eq. (11) bound of interval j relative to min |f| on it (see
+// gf_table_create). The factors that do not depend on the interval (powers of
+// k, factorials, binomials) are formed once, by the same operations in the
+// same order as a per-interval evaluation, so the bound is the same number.
+struct Eq11 {
+  int deg, kind, q;
+  double fq, kq, c[8];
+  Eq11(int deg_, int kind_, double k) : deg(deg_), kind(kind_), q(deg_ + 1) {
+    fq = fact(q);
+    kq = std::pow(k, q);
+    for (int i = 0; i <= q && i < 8; ++i) c[i] = fact(q) / (fact(i) * fact(q - i)) * std::pow(k, q - i) * fact(i);
   }
-  double b = om * mq / fact(q);
-  return kind == GF_GREEN ? b * r[j + 1] : b;
-}
+  static int stencil(int j, int deg, int n) { return deg <= 1 ? j : std::min(std::max(j - (deg - 1) / 2, 0), n - 1 - deg); }
+  double operator()(const std::vector<double>& r, int j) const {
+    const int s0 = stencil(j, deg, (int)r.size());
+    const double h = r[j + 1] - r[j];
+    double om = h * h / 4.0;
+    for (int s = s0; s <= s0 + deg; ++s)
+      if (s != j && s != j + 1) om *= std::max(std::fabs(r[j] - r[s]), std::fabs(r[j + 1] - r[s]));
+    double mq = 0.0;
+    if (kind == GF_EXP) {
+      mq = kq;
+    } else {
+      for (int i = 0; i <= q; ++i) mq += c[i] / std::pow(r[s0], i + 1);
+    }
+    const double b = om * mq / fq;
+    return kind == GF_GREEN ? b * r[j + 1] : b;
+  }
+};
 
-// The same bound with the powers formed by products (equal to eq11_rel up to
-// a few ulps): a screen, so that eq11_rel runs only on intervals whose bound
-// is within a factor 2 of the tolerance and the grading decisions do not
-// depend on the screen.
+// The same bound with the powers of 1/r formed by products (equal to Eq11 up
+// to a few ulps): a screen, so that Eq11 runs only on intervals whose bound is
+// within a factor 2 of the tolerance and the grading decisions do not depend
+// on the screen.
 struct Eq11Screen {
   int deg, kind, q;
   double kq, inv_fq, kp[8], cf[8];
@@ -146,8 +156,7 @@ struct Eq11Screen {
     for (int i = 0; i <= q && i < 8; ++i) cf[i] = fact(q) / (fact(i) * fact(q - i)) * fact(i);
   }
   double operator()(const std::vector<double>& r, int j) const {
-    const int n = (int)r.size();
-    const int s0 = deg <= 1 ? j : std::min(std::max(j - (deg - 1) / 2, 0), n - 1 - deg);
+    const int s0 = Eq11::stencil(j, deg, (int)r.size());
     const double h = r[j + 1] - r[j];
     double om = h * h / 4.0;
     for (int s = s0; s <= s0 + deg; ++s)
@@ -171,6 +180,7 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
   const double hw = p.refine_halfwidth_t * t;
   // uniform samples from r_min with spacing t (Eq. 2); r_max is a sample
   std::vector<double> base;
+  if ((hi - lo) / t < (double)(1u << 26)) base.reserve((size_t)((hi - lo) / t) + 2);
   for (int64_t i = 0;; ++i) {
     const double x = lo + (double)i * t;
     if (x >= hi) break;
@@ -212,12 +222,13 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
       if (z - lo >= merge && hi - z >= merge) kept_zeros.push_back(z);
     std::vector<double> tmp;
     tmp.reserve(all.size());
+    size_t z0 = 0;  // first kept zero >= x - merge (x ascends)
     for (double x : all) {
       bool drop = false;
       if (x != lo && x != hi) {
-        auto it = std::lower_bound(kept_zeros.begin(), kept_zeros.end(), x - merge);
-        for (; it != kept_zeros.end() && *it <= x + merge; ++it)
-          if (std::fabs(x - *it) < merge) drop = true;
+        while (z0 < kept_zeros.size() && kept_zeros[z0] < x - merge) ++z0;
+        for (size_t zi = z0; zi < kept_zeros.size() && kept_zeros[zi] <= x + merge; ++zi)
+          if (std::fabs(x - kept_zeros[zi]) < merge) drop = true;
       }
       if (!drop) tmp.push_back(x);
     }
@@ -233,30 +244,54 @@ static gf_status place_samples(int kind, int deg, double k, double lo, double hi
     std::sort(all.begin(), all.end());
   }
   if (p.grade) {
+    // bisection passes; an interval is examined again only when a new sample
+    // lies within its stencil's reach (deg + 1 samples either side): the bound
+    // of any other interval is unchanged, so it passes again
     const Eq11Screen screen(deg, kind, k);
+    const Eq11 exact(deg, kind, k);
     const bool exact_only = deg + 1 >= 8;
+    std::vector<char> dirty(all.size(), 1), fresh;
+    std::vector<double> add, merged;
     for (int pass = 0; pass < 200; ++pass) {
-      std::vector<double> add;
+      add.clear();
       for (int j = 0; j + 1 < (int)all.size(); ++j)
-        if ((exact_only || screen(all, j) > 0.5 * p.table_tol) && eq11_rel(all, j, deg, kind, k) > p.table_tol)
+        if (dirty[j] && (exact_only || kind == GF_EXP || screen(all, j) > 0.5 * p.table_tol) &&
+            exact(all, j) > p.table_tol)
           add.push_back(0.5 * (all[j] + all[j + 1]));
       if (add.empty()) break;
-      all.insert(all.end(), add.begin(), add.end());
-      std::sort(all.begin(), all.end());
+      // sorted union (`add` ascends with j), marking the new samples
+      merged.resize(all.size() + add.size());
+      fresh.assign(merged.size(), 0);
+      size_t ia = 0, ib = 0, o = 0;
+      while (ia < all.size() || ib < add.size()) {
+        if (ib < add.size() && (ia == all.size() || add[ib] < all[ia])) {
+          fresh[o] = 1;
+          merged[o++] = add[ib++];
+        } else {
+          merged[o++] = all[ia++];
+        }
+      }
+      all.swap(merged);
       if (all.size() > (1u << 26)) return fail(GF_ERR_RANGE, "table: too many samples");
+      const int reach = deg + 2, n = (int)all.size();
+      dirty.assign(n, 0);
+      for (int i = 0; i < n; ++i)
+        if (fresh[i])
+          for (int j = std::max(i - reach, 0); j <= std::min(i + reach, n - 1); ++j) dirty[j] = 1;
     }
   }
-  out->r = all;
   out->zflag.assign(all.size(), 0);
   if (p.refine) {
+    const double inv_quarter = 1.0 / quarter;  // a multiple of quarter is recognised either way
     for (size_t j = 0; j < all.size(); ++j) {
-      const double q = std::nearbyint(all[j] / quarter);
+      const double q = std::nearbyint(all[j] * inv_quarter);
       if (q >= 1 && q * quarter == all[j]) out->zflag[j] = ((int64_t)q % 2) ? 1 : 2;
     }
   }
   double dr = INFINITY;
   for (size_t j = 0; j + 1 < all.size(); ++j) dr = std::min(dr, all[j + 1] - all[j]);
   out->dr = dr;
+  out->r = std::move(all);
   const double cells = std::floor((hi - lo) / dr) + 1.0;
   if (!(cells < (double)(1 << 26))) return fail(GF_ERR_RANGE, "table: hash array too large");
   out->n_hash = (int64_t)cells;
@@ -321,7 +356,7 @@ gf_status check_device(int dev) {
 void free_mesh_device(gf_mesh* m) {
   void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_near_row, m->d_pts32,
                   m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
-                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb, m->d_frame64};
+                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb, m->d_frame64, m->d_range_list};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -583,9 +618,10 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
       (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
       (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_frame64, (size_t)kFrame * nt)) ||
-      (st = dev_alloc(&m->d_minmax, 4)) ||
+      (st = dev_alloc(&m->d_minmax, 8)) ||
       (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32)) ||
-      (st = dev_alloc(&m->d_range_bpb, (size_t)((nt + 31) / 32) * ((nt + 31) / 32 + 1) / 2))) {
+      (st = dev_alloc(&m->d_range_bpb, (size_t)((nt + 31) / 32) * ((nt + 31) / 32 + 1) / 2)) ||
+      (st = dev_alloc(&m->d_range_list, range_list_ints(nt)))) {
     free_mesh_device(m.get());
     return st;
   }
@@ -658,7 +694,7 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, rule, s))) return st;
-  GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, m->d_range_bpb, s));
+  GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, m->d_range_bpb, m->d_range_list, s));
   unsigned long long mm[2];
   GF_CUDA(cudaMemcpyAsync(mm, m->d_minmax, 16, cudaMemcpyDeviceToHost, s));
   GF_CUDA(cudaStreamSynchronize(s));
@@ -823,8 +859,9 @@ gf_status build_lattice(const std::vector<double>& r, double step, Lattice* L) {
   L->sub.clear();
   L->cmp.clear();
   size_t jm = 0;  // last sample <= the cell's middle (the middles increase with i)
+  const double cell_w = 1.0 / (double)M.inv;
   for (int i = 0; i < L->n; ++i) {
-    const double mid = ((double)i + (double)c) / (double)M.inv;
+    const double mid = ((double)i + (double)c) * cell_w;
     while (jm + 1 < n && r[jm + 1] <= mid) ++jm;
     L->j[i] = (int32_t)std::min<size_t>(jm, n - 2);
     if (!busy[i]) continue;

@@ -12,6 +12,13 @@ namespace gf {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxRule = 7;
+// FP32 range scratch after the candidate list of block pairs: one record pair
+// (12 bytes each) per pass-2 block, at most kRangeMaxBlocks blocks.
+constexpr int kRangeMaxBlocks = 4096;
+inline size_t range_list_ints(int64_t nt) {
+  const int64_t nb = (nt + 31) / 32, nbp = nb * (nb + 1) / 2;
+  return (size_t)((nbp + 3) & ~int64_t(3)) + 6 * (size_t)kRangeMaxBlocks;
+}
 
 }  // namespace gf
 struct gf_mesh;
@@ -162,7 +169,8 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 // bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
-cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, cudaStream_t s);
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
+                         cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}
 // from the linear table times 1/R); NULL = direct evaluation.
 cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
@@ -223,8 +231,9 @@ struct gf_mesh {
   float4* d_bsph = nullptr;
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
   double* d_dk = nullptr;                   // adjoint scratch [1]
-  unsigned long long* d_minmax = nullptr;  // range scratch [4]
+  unsigned long long* d_minmax = nullptr;  // range scratch [8]
   float2* d_range_bpb = nullptr;          // range scratch: bounds per 32 x 32 block pair
+  int32_t* d_range_list = nullptr;        // range scratch: block pairs that can hold an extreme, count last
 };
 
 struct gf_table {

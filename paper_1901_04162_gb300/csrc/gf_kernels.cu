@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "gf_internal.h"
 
@@ -493,11 +494,19 @@ __device__ __forceinline__ bool sym_task(int64_t task, int nt, int* p, int* q0) 
 
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-__global__ void k_range_init(unsigned long long* mm) {
-  mm[0] = dbits(INFINITY);
-  mm[1] = 0ull;
-  mm[2] = dbits(INFINITY);
-  mm[3] = 0ull;
+// Range scratch: mm[0] r_min, mm[1] r_max (FP64 bits), mm[2] / mm[3] the
+// pass-1 thresholds, mm[4] candidate block pairs, mm[5] blocks of pass 2 done.
+__global__ void k_range_init(unsigned long long* mm, float2* bpb, int64_t nbp) {
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0) {
+    mm[0] = dbits(INFINITY);
+    mm[1] = 0ull;
+    mm[2] = dbits(INFINITY);
+    mm[3] = 0ull;
+    mm[4] = 0ull;
+    mm[5] = 0ull;
+  }
+  for (int64_t i = i0; i < nbp; i += (int64_t)gridDim.x * blockDim.x) bpb[i] = make_float2(INFINITY, 0.f);
 }
 
 // Every point distance of a pair lies in [D - r_p - r_q, D + r_p + r_q]
@@ -517,25 +526,31 @@ __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, floa
   *ub = D + r + slack;
 }
 
-// Pass 1, one warp per 32 x 32 triangle block pair: thresholds from actual
-// point distances (the first rule point of each triangle of every regular
-// pair: their minimum is >= r_min, their maximum <= r_max), widened by a
-// relative 1e-5 for the FP32 rounding (mm[2], mm[3]), and, per block pair,
-// the smallest lower and largest upper bound of its regular pairs (bpb), so
-// that pass 2 skips block pairs that cannot hold an extreme.
+constexpr int kRangeSplit = 4;          // pass-1 warps per 32 x 32 block pair (8 test triangles each)
+
+// Pass 1, one warp per 8 test triangles of a 32 x 32 block pair: thresholds
+// from actual point distances (the first rule point of each triangle of every
+// regular pair: their minimum is >= r_min, their maximum <= r_max), widened by
+// a relative 1e-5 for the FP32 rounding (mm[2], mm[3]), and, per block pair,
+// the smallest lower and largest upper bound of its regular pairs (bpb, merged
+// by integer atomics on the bits of these non-negative floats), so that pass 2
+// skips block pairs that cannot hold an extreme.
 __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm, float2* bpb) {
   const int lane = threadIdx.x & 31;
-  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
+  const int64_t nb = (g.nt + 31) / 32, ntask = nb * (nb + 1) / 2 * kRangeSplit;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   float min_d = INFINITY, max_d = 0.f;
-  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarp) {
+    const int64_t u = t / kRangeSplit;
     int p0, q0;
     sym_task(u * 32, g.nt, &p0, &q0);
+    p0 += (int)(t % kRangeSplit) * (32 / kRangeSplit);
     const int q = min(q0 + lane, g.nt - 1);
     const float4 cq = g.cen32[q], yq = g.pts32[q];
     const int4 vq = g.tvert[q];
     float blk_lb = INFINITY, blk_ub = 0.f;
-    const int p1 = min(p0 + 32, g.nt);
+    const int p1 = min(p0 + 32 / kRangeSplit, g.nt);
+#pragma unroll 2
     for (int p = p0; p < p1; ++p) {
       const float4 cp = g.cen32[p];
       const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
@@ -554,7 +569,11 @@ __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned l
       blk_lb = fminf(blk_lb, __shfl_xor_sync(0xffffffffu, blk_lb, off));
       blk_ub = fmaxf(blk_ub, __shfl_xor_sync(0xffffffffu, blk_ub, off));
     }
-    if (lane == 0) bpb[u] = make_float2(blk_lb, blk_ub);
+    if (lane == 0 && blk_lb < INFINITY) {
+      unsigned* b = reinterpret_cast<unsigned*>(bpb + u);
+      atomicMin(b, __float_as_uint(blk_lb) & 0x7fffffffu);  // +0 for a -0 bound
+      atomicMax(b + 1, __float_as_uint(blk_ub));
+    }
   }
   for (int off = 16; off > 0; off >>= 1) {
     min_d = fminf(min_d, __shfl_xor_sync(0xffffffffu, min_d, off));
@@ -566,69 +585,174 @@ __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned l
   }
 }
 
-// Pass 2 (FP32 screen), one warp per block pair that can hold an extreme:
-// its pairs that can are evaluated point by point. Each lane keeps its FP32
-// extremes and re-evaluates those two point pairs in FP64 at the end.
-template <int M>
-__global__ void __launch_bounds__(kThreads) k_range32(GeoView g, unsigned long long* mm, const float2* bpb) {
-  const int lane = threadIdx.x & 31;
+// The block pairs that can hold an extreme, appended to list (in any order:
+// the result of pass 2 does not depend on it); their count into mm[4].
+__global__ void k_range_list(unsigned long long* mm, const float2* bpb, int64_t nbp, int32_t* list) {
   const float u_min = (float)__longlong_as_double((long long)mm[2]);
   const float l_max = (float)__longlong_as_double((long long)mm[3]);
-  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
-  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  float lo32 = INFINITY, hi32 = -1.f;
-  int lo_p = 0, lo_q = 0, lo_ab = 0, hi_p = 0, hi_q = 0, hi_ab = 0;
-  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
-    const float2 bb = bpb[u];
-    if (!(bb.x <= u_min || bb.y >= l_max)) continue;  // no pair of the block pair can hold an extreme
-    int p0, q0;
-    sym_task(u * 32, g.nt, &p0, &q0);
-    const int q = min(q0 + lane, g.nt - 1);
-    const float4 cq = g.cen32[q];
-    const int4 vq = g.tvert[q];
-    float4 beta[M];
-#pragma unroll
-    for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
-    const int p1 = min(p0 + 32, g.nt);
-    for (int p = p0; p < p1; ++p) {
-      const float4 cp = g.cen32[p];
-      const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-      if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], vq, dc))) continue;
-      float lb, ub;
-      pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
-      if (lb > u_min && ub < l_max) continue;  // cannot hold an extreme
-      for (int a = 0; a < M; ++a) {
-        const float4 pa = g.pts32[(size_t)a * g.nt + p];
-        const float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
-#pragma unroll
-        for (int b = 0; b < M; ++b) {
-          const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-          const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-          if (R2 < lo32) { lo32 = R2; lo_p = p; lo_q = q; lo_ab = a * 8 + b; }
-          if (R2 > hi32) { hi32 = R2; hi_p = p; hi_q = q; hi_ab = a * 8 + b; }
-        }
+  const int lane = threadIdx.x & 31;
+  for (int64_t u0 = (int64_t)blockIdx.x * blockDim.x; u0 < nbp; u0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = u0 + threadIdx.x;
+    bool cand = false;
+    if (u < nbp) {
+      const float2 bb = bpb[u];
+      cand = bb.x <= u_min || bb.y >= l_max;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, cand);
+    if (!bal) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&mm[4], (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (cand) list[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)u;
+  }
+}
+
+// Extremes of pass 2: the FP32 value (squared distance) and the pair holding
+// it; ties go to the smaller (p, q), so that the result is the same in any
+// order of evaluation.
+struct RExt {
+  float v;
+  int p, q;
+};
+
+__device__ __forceinline__ bool rext_before(bool hi, const RExt& x, const RExt& y) {
+  if (x.v != y.v) return hi ? x.v > y.v : x.v < y.v;
+  return x.p != y.p ? x.p < y.p : x.q < y.q;
+}
+
+__device__ __forceinline__ RExt rext_warp(bool hi, RExt x) {
+  for (int off = 16; off > 0; off >>= 1) {
+    RExt o;
+    o.v = __shfl_xor_sync(0xffffffffu, x.v, off);
+    o.p = __shfl_xor_sync(0xffffffffu, x.p, off);
+    o.q = __shfl_xor_sync(0xffffffffu, x.q, off);
+    if (rext_before(hi, o, x)) x = o;
+  }
+  return x;
+}
+
+// The extremal point pair of triangle pair (p, q) (FP32 rescan, first in
+// (a, b) order), evaluated in FP64.
+template <int M>
+__device__ double range_point64(const GeoView& g, int p, int q, bool hi) {
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+  float best = hi ? -1.f : INFINITY;
+  int ia = 0, ib = 0;
+  for (int a = 0; a < M; ++a) {
+    const float4 pa = g.pts32[(size_t)a * g.nt + p];
+    const float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
+    for (int b = 0; b < M; ++b) {
+      const float4 pb = g.pts32[(size_t)b * g.nt + q];
+      const float rx = ux - pb.x, ry = uy - pb.y, rz = uz - pb.z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      if (hi ? R2 > best : R2 < best) {
+        best = R2;
+        ia = a;
+        ib = b;
       }
     }
   }
-  auto dist64 = [&](int p, int q, int ab) {
-    const double* cp64 = g.cen64 + 4 * (size_t)p;
-    const double* cq64 = g.cen64 + 4 * (size_t)q;
-    const double* pa = g.pts64 + 4 * ((size_t)(ab >> 3) * g.nt + p);
-    const double* pb = g.pts64 + 4 * ((size_t)(ab & 7) * g.nt + q);
-    double rx = (cp64[0] - cq64[0]) + pa[0] - pb[0];
-    double ry = (cp64[1] - cq64[1]) + pa[1] - pb[1];
-    double rz = (cp64[2] - cq64[2]) + pa[2] - pb[2];
-    return sqrt(rx * rx + ry * ry + rz * rz);
-  };
-  double best_lo = lo32 < INFINITY ? dist64(lo_p, lo_q, lo_ab) : INFINITY;
-  double best_hi = hi32 >= 0.f ? dist64(hi_p, hi_q, hi_ab) : 0.0;
-  for (int off = 16; off > 0; off >>= 1) {
-    best_lo = fmin(best_lo, __shfl_xor_sync(0xffffffffu, best_lo, off));
-    best_hi = fmax(best_hi, __shfl_xor_sync(0xffffffffu, best_hi, off));
+  const double* cp64 = g.cen64 + 4 * (size_t)p;
+  const double* cq64 = g.cen64 + 4 * (size_t)q;
+  const double* pa = g.pts64 + 4 * ((size_t)ia * g.nt + p);
+  const double* pb = g.pts64 + 4 * ((size_t)ib * g.nt + q);
+  const double rx = (cp64[0] - cq64[0]) + pa[0] - pb[0];
+  const double ry = (cp64[1] - cq64[1]) + pa[1] - pb[1];
+  const double rz = (cp64[2] - cq64[2]) + pa[2] - pb[2];
+  return sqrt(rx * rx + ry * ry + rz * rz);
+}
+
+// Pass 2 (FP32 screen), one warp per (test triangle, block of 32 source
+// triangles) of a listed block pair: per candidate pair the FP32 minimum and
+// maximum over its point pairs. Each block records its extremes; the last
+// block to finish reduces the records and re-evaluates the extremal point
+// pairs in FP64 (mm[0], mm[1]). The FP32 screen costs a few ulps: the point
+// pair it selects is within its rounding of the true extreme.
+template <int M>
+__global__ void __launch_bounds__(kThreads) k_range32(GeoView g, unsigned long long* mm, const int32_t* list,
+                                                      RExt* rec) {
+  __shared__ RExt s_ext[2][kWarps];
+  __shared__ bool s_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const float u_min = (float)__longlong_as_double((long long)mm[2]);
+  const float l_max = (float)__longlong_as_double((long long)mm[3]);
+  const int64_t ntask = (int64_t)mm[4] * 32;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  RExt lo = {INFINITY, INT_MAX, INT_MAX}, hi = {-1.f, INT_MAX, INT_MAX};
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarp) {
+    int p, q0;
+    if (!sym_task((int64_t)list[t >> 5] * 32 + (t & 31), g.nt, &p, &q0)) continue;
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
+    float lb, ub;
+    pair_bounds(g, p, q, dc, cp, cq, &lb, &ub);
+    if (lb > u_min && ub < l_max) continue;  // cannot hold an extreme
+    float4 beta[M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
+    float pmin = INFINITY, pmax = 0.f;
+    for (int a = 0; a < M; ++a) {
+      const float4 pa = g.pts32[(size_t)a * g.nt + p];
+      const float ux = dc.x + pa.x, uy = dc.y + pa.y, uz = dc.z + pa.z;
+#pragma unroll
+      for (int b = 0; b < M; ++b) {
+        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        pmin = fminf(pmin, R2);
+        pmax = fmaxf(pmax, R2);
+      }
+    }
+    const RExt xl = {pmin, p, q}, xh = {pmax, p, q};
+    if (rext_before(false, xl, lo)) lo = xl;
+    if (rext_before(true, xh, hi)) hi = xh;
   }
+  lo = rext_warp(false, lo);
+  hi = rext_warp(true, hi);
   if (lane == 0) {
-    if (best_lo < INFINITY) atomicMin(&mm[0], dbits(best_lo));
-    if (best_hi > 0.0) atomicMax(&mm[1], dbits(best_hi));
+    s_ext[0][warp] = lo;
+    s_ext[1][warp] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kWarps; ++w) {
+      if (rext_before(false, s_ext[0][w], lo)) lo = s_ext[0][w];
+      if (rext_before(true, s_ext[1][w], hi)) hi = s_ext[1][w];
+    }
+    rec[2 * blockIdx.x] = lo;
+    rec[2 * blockIdx.x + 1] = hi;
+    __threadfence();
+    s_last = atomicAdd(&mm[5], 1ull) == (unsigned long long)(gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // the last block: every record is visible (each was fenced before its count)
+  lo = {INFINITY, INT_MAX, INT_MAX};
+  hi = {-1.f, INT_MAX, INT_MAX};
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    const RExt a = {__ldcg(&rec[2 * i].v), __ldcg(&rec[2 * i].p), __ldcg(&rec[2 * i].q)};
+    const RExt b = {__ldcg(&rec[2 * i + 1].v), __ldcg(&rec[2 * i + 1].p), __ldcg(&rec[2 * i + 1].q)};
+    if (rext_before(false, a, lo)) lo = a;
+    if (rext_before(true, b, hi)) hi = b;
+  }
+  lo = rext_warp(false, lo);
+  hi = rext_warp(true, hi);
+  __syncthreads();
+  if (lane == 0) {
+    s_ext[0][warp] = lo;
+    s_ext[1][warp] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < kWarps; ++w) {
+      if (rext_before(false, s_ext[0][w], lo)) lo = s_ext[0][w];
+      if (rext_before(true, s_ext[1][w], hi)) hi = s_ext[1][w];
+    }
+    if (lo.v < INFINITY) mm[0] = dbits(range_point64<M>(g, lo.p, lo.q, false));
+    if (hi.v >= 0.f) mm[1] = dbits(range_point64<M>(g, hi.p, hi.q, true));
+    mm[5] = 0ull;
   }
 }
 
@@ -973,7 +1097,7 @@ struct C2 {
 };
 
 struct KScal {  // per-wavenumber scalars of the near-pair fill
-  double k, scale, inv_k2;
+  double k, scale, inv_k2, inv_k;
 };
 
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
@@ -1088,8 +1212,8 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 // triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
 // and the static log term is one log of a ratio per edge.
 __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
-                                      const NearArgs& A, double k, const Tab32& te, bool use_table, float lo,
-                                      float hi, C2* I0, C2 I1[3], double rho0[3]) {
+                                      const NearArgs& A, double k, double inv_k, const Tab32& te, bool use_table,
+                                      float lo, float hi, C2* I0, C2 I1[3], double rho0[3]) {
   const float kpi = (float)(k / kPi), k32 = (float)k;
   const double n[3] = {fr[0], fr[1], fr[2]};
   const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
@@ -1107,8 +1231,10 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
   }
   const float d32 = (float)d;
   const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
-  double sre = 0, sim = 0;
-  double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0}, vst[3] = {0, 0, 0};
+  // the sampled (dynamic) sums carry FP32 samples: FP32 accumulation; the
+  // static closed form stays in FP64
+  float sre = 0.f, sim = 0.f, vre[3] = {0.f, 0.f, 0.f}, vim[3] = {0.f, 0.f, 0.f};
+  double vst[3] = {0, 0, 0};
   for (int e = 0; e < 3; ++e) {
     const double* a = v[e];
     const double len = fr[3 + e];
@@ -1134,9 +1260,9 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
         cr = fmaf(ed.x - eR.x, wt, cr);
         ci = fmaf(ed.y - eR.y, wt, ci);
       }
-      const double sg = P0 > 0 ? (double)half : -(double)half;
-      sre += (double)cr * sg;
-      sim += (double)ci * sg;
+      const float sg = P0 > 0 ? half : -half;
+      sre = fmaf(cr, sg, sre);
+      sim = fmaf(ci, sg, sim);
     }
     // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
     const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
@@ -1151,50 +1277,74 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
       lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
       li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
     }
-    const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
-    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|
+    lr *= hl;
+    li *= hl;
+    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|;
+    // log(fp / fm) with fp = lp + Rp = R02 / (Rp - lp), fm = lm + Rm =
+    // R02 / (Rm - lm), each in its cancellation-free form (lp >= lm), as one
+    // quotient
     const double R02 = P0 * P0 + d * d;
     const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
     double st = 0.5 * (lp * Rp - lm * Rm);
     if (R02 > 0) {
-      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st += 0.5 * R02 * log(fp / fm);
+      double ratio;
+      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
+      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
+      else ratio = (Rm - lm) / (Rp - lp);
+      st += 0.5 * R02 * log(ratio);
     }
-    for (int x = 0; x < 3; ++x) {
-      vre[x] += mh[x] * lrd;
-      vim[x] += mh[x] * lid;
-      vst[x] += mh[x] * st;
-    }
+    const float mx = (float)mh[0], my = (float)mh[1], mz = (float)mh[2];
+    vre[0] = fmaf(mx, lr, vre[0]);
+    vre[1] = fmaf(my, lr, vre[1]);
+    vre[2] = fmaf(mz, lr, vre[2]);
+    vim[0] = fmaf(mx, li, vim[0]);
+    vim[1] = fmaf(my, li, vim[1]);
+    vim[2] = fmaf(mz, li, vim[2]);
+    for (int x = 0; x < 3; ++x) vst[x] += mh[x] * st;
   }
-  const double c4 = 1.0 / (4.0 * kPi), ik = 1.0 / k;
-  I0->re = sim * ik * c4;
-  I0->im = -sre * ik * c4;
+  const double c4 = 1.0 / (4.0 * kPi), ikc4 = inv_k * c4;
+  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
+  I0->re = (double)sim * ikc4;
+  I0->im = -(double)sre * ikc4;
   for (int x = 0; x < 3; ++x) {
-    I1[x].re = (-vim[x] * ik + vst[x]) * c4;
-    I1[x].im = (vre[x] * ik) * c4;
+    I1[x].re = fma(-(double)vim[x], inv_k, vst[x]) * c4;
+    I1[x].im = (double)vre[x] * ikc4;
   }
 }
 
-// One near pair per group of 8 lanes, one test point per lane (lanes >= m
-// idle); the 3 x 3 block is reduced across the group with shuffles and added
-// to Z by the group's first lane.
-// One near pair (index idx of the CSR list; valid_pair false: padding) on a
-// group of 8 lanes, one test point per lane; every lane of the group must call.
-// One near pair per group of G lanes (G >= the rule size; lane = test point).
+// Reduce-scatter of the nine complex entries of a 3 x 3 block over the G
+// lanes of a group (G = 4 or 8): at each halving step a lane keeps one half
+// of its entries and adds the partner's copy of that half, so that the group
+// sums end spread over the lanes (at most ceil(9 / G) + 1 entries each) with
+// no more additions than entries exchanged.
+template <int N>
+__device__ __forceinline__ void rs_halve(const C2 (&in)[N], C2 (&out)[(N + 1) / 2], bool upper, int off,
+                                         unsigned gmask) {
+  constexpr int H = (N + 1) / 2;
+#pragma unroll
+  for (int s = 0; s < H; ++s) {
+    const C2 lo_v = in[s];
+    const C2 hi_v = (H + s < N) ? in[H + s] : C2{0.0, 0.0};
+    const C2 keep = upper ? hi_v : lo_v, send = upper ? lo_v : hi_v;
+    out[s].re = keep.re + __shfl_xor_sync(gmask, send.re, off);
+    out[s].im = keep.im + __shfl_xor_sync(gmask, send.im, off);
+  }
+}
+
+// One near pair per group of G lanes (G >= the rule size; lane = test point;
+// lanes >= m idle); every lane of the group must call (valid_pair is uniform
+// over the group). The 3 x 3 block is reduce-scattered over the group and
+// each lane adds its entries to Z.
 template <class Out, bool MIXED, int G = 8>
 __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
                                           float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
                                           int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
                                           unsigned gmask) {
-  if (!valid_pair) return;  // uniform over the 8-lane group
-  const int64_t pidx = idx;
-  const int p = g.near_row[pidx], q = g.near_idx[pidx];
-  double accr[3][3], acci[3][3];
+  if (!valid_pair) return;
+  const int p = g.near_row[idx], q = g.near_idx[idx];
+  C2 acc[9];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) accr[i][j] = acci[i][j] = 0.0;
+  for (int u = 0; u < 9; ++u) acc[u] = C2{0.0, 0.0};
   if (sub < g.m) {
     double vq[3][3];
     for (int c = 0; c < 3; ++c)
@@ -1205,58 +1355,75 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
     C2 I0, I1[3];
     double rho0[3];
     if (MIXED)
-      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, A, ks.k, te32, use_table, lo32, hi32, &I0, I1,
-                            rho0);
+      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, A, ks.k, ks.inv_k, te32, use_table, lo32, hi32,
+                            &I0, I1, rho0);
     else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
-    const double wa = al[3];
+    // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
+    // w_a / 4 folded into I0, I1
+    const double w4 = 0.25 * al[3];
+    const C2 S = {w4 * I0.re, w4 * I0.im};
+    const C2 T[3] = {{w4 * I1[0].re, w4 * I1[0].im}, {w4 * I1[1].re, w4 * I1[1].im}, {w4 * I1[2].re, w4 * I1[2].im}};
+    const double q4 = 4.0 * ks.inv_k2;
+    const C2 Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
+    double f[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
+      f[i][0] = ra[0] - vpi[0];
+      f[i][1] = ra[1] - vpi[1];
+      f[i][2] = ra[2] - vpi[2];
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      // J_j = I1 + (rho0 - v_j) I0
       C2 J[3];
+#pragma unroll
       for (int x = 0; x < 3; ++x) {
         const double dv = rho0[x] - vq[j][x];
-        J[x].re = I1[x].re + dv * I0.re;
-        J[x].im = I1[x].im + dv * I0.im;
+        J[x].re = fma(dv, S.re, T[x].re);
+        J[x].im = fma(dv, S.im, T[x].im);
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
-        const double f0 = ra[0] - vpi[0], f1 = ra[1] - vpi[1], f2 = ra[2] - vpi[2];
-        const double dr = f0 * J[0].re + f1 * J[1].re + f2 * J[2].re;
-        const double di = f0 * J[0].im + f1 * J[1].im + f2 * J[2].im;
-        accr[i][j] = wa * (0.25 * dr - I0.re * ks.inv_k2);
-        acci[i][j] = wa * (0.25 * di - I0.im * ks.inv_k2);
+        acc[3 * i + j].re = fma(f[i][0], J[0].re, fma(f[i][1], J[1].re, fma(f[i][2], J[2].re, -Q.re)));
+        acc[3 * i + j].im = fma(f[i][0], J[0].im, fma(f[i][1], J[1].im, fma(f[i][2], J[2].im, -Q.im)));
       }
     }
   }
+  // reduce-scatter: 9 -> 5 -> 3 (-> 2 for G = 8) entries per lane
+  C2 r5[5], r3[3];
+  constexpr int L1 = G / 2, L2 = G / 4;
+  rs_halve<9>(acc, r5, (sub & L1) != 0, L1, gmask);
+  rs_halve<5>(r5, r3, (sub & L2) != 0, L2, gmask);
+  int first = ((sub & L1) ? 5 : 0) + ((sub & L2) ? 3 : 0);  // entry of slot 0
+  int count = (sub & L1) ? ((sub & L2) ? 1 : 3) : ((sub & L2) ? 2 : 3);  // 9 = 5 + 4; 5 = 3 + 2; 4 = 3 + 1
+  constexpr int NS = G == 8 ? 2 : 3;
+  C2 fin[NS];
+  if constexpr (G == 8) {
+    rs_halve<3>(r3, fin, (sub & 1) != 0, 1, gmask);
+    const bool up = (sub & 1) != 0;
+    first += up ? 2 : 0;
+    count = up ? max(count - 2, 0) : min(count, 2);
+  } else {
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-      for (int off = 1; off < G; off <<= 1) {
-        accr[i][j] += __shfl_xor_sync(gmask, accr[i][j], off);
-        acci[i][j] += __shfl_xor_sync(gmask, acci[i][j], off);
-      }
-  if (sub != 0) return;
-  const double area_q = g.cen64[4 * (size_t)q + 3];
+    for (int u = 0; u < 3; ++u) fin[u] = r3[u];
+  }
+  const double inv_area_q = 1.0 / g.cen64[4 * (size_t)q + 3];
   const int4 ep = g.tedge[p], eq = g.tedge[q];
-  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-  for (int i = 0; i < 3; ++i) {
-    if (!edge_valid(ecp[i])) continue;
-    const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3];
-    for (int j = 0; j < 3; ++j) {
-      if (!edge_valid(ecq[j])) continue;
-      const double slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
-      const double c = ks.scale * slp * slq / area_q;  // k eta s_i l_i s_j l_j / A_q
-      const double zr = -c * acci[i][j], zi = c * accr[i][j];
-      Out* z = Z + (int64_t)edge_of(ecp[i]) * ldz + edge_of(ecq[j]);
-      if constexpr (sizeof(Out) == 8) {
-        atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
-      } else {
-        atomicAdd(reinterpret_cast<double*>(z), zr);
-        atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
-      }
+#pragma unroll
+  for (int u = 0; u < NS; ++u) {
+    if (u >= count) break;
+    const int e = first + u, i = e / 3, j = e - 3 * (e / 3);
+    const int ci = i == 0 ? ep.x : (i == 1 ? ep.y : ep.z), cj = j == 0 ? eq.x : (j == 1 ? eq.y : eq.z);
+    if (!edge_valid(ci) || !edge_valid(cj)) continue;
+    const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
+    const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
+    const double zr = -c * fin[u].im, zi = c * fin[u].re;
+    Out* z = Z + (int64_t)edge_of(ci) * ldz + edge_of(cj);
+    if constexpr (sizeof(Out) == 8) {
+      atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
+    } else {
+      atomicAdd(reinterpret_cast<double*>(z), zr);
+      atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
     }
   }
 }
@@ -1274,7 +1441,7 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
   const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
   for (int64_t it = 0; it < iters; ++it) {
     const int64_t idx = g0 + it * ngroups;
-    near_task<Out, MIXED, G>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2}, Z, ldz, n_near,
+    near_task<Out, MIXED, G>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2, 1.0 / A.k}, Z, ldz, n_near,
                              idx, idx < n_near, sub, gmask);
   }
 }
@@ -2499,7 +2666,7 @@ __global__ void __launch_bounds__(128) k_batch_near(const BatchItem* __restrict_
       const BatchItem& it = items[batch_item_of(items, nitems, t, true)];
       const Tab32 te32 = tab32(it.exp);
       near_task<float2, MIXED>(it.g, it.exp, te32, (float)it.exp.r_lo, (float)it.exp.r_hi, it.use_table != 0, A,
-                               KScal{it.k, it.scale, it.inv_k2}, reinterpret_cast<float2*>(it.Z), it.ldz, it.n_near,
+                               KScal{it.k, it.scale, it.inv_k2, 1.0 / it.k}, reinterpret_cast<float2*>(it.Z), it.ldz, it.n_near,
                                t - it.near_begin, true, sub, gmask);
     }
   }
@@ -2696,23 +2863,31 @@ cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const v
   return cudaGetLastError();
 }
 
-cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, cudaStream_t s) {
-  k_range_init<<<1, 1, 0, s>>>(d_minmax);
+cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
+                         cudaStream_t s) {
+  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
   if (precision == GF_FP64) {
+    k_range_init<<<1, 32, 0, s>>>(d_minmax, bpb, 0);
     int64_t blocks = pair_grid(g, 8);
     k_range64<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax);
     return cudaGetLastError();
   }
-  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
-  const int64_t blocks = std::min<int64_t>((nbp + kWarps - 1) / kWarps, (int64_t)sm_count() * 8);
-  k_range_bounds<<<(unsigned)blocks, kThreads, 0, s>>>(g, d_minmax, bpb);
-  const unsigned b2 = (unsigned)blocks;
+  const unsigned nsm = (unsigned)sm_count();
+  const unsigned b0 = (unsigned)std::min<int64_t>((nbp + kThreads - 1) / kThreads, (int64_t)nsm * 4);
+  k_range_init<<<b0, kThreads, 0, s>>>(d_minmax, bpb, nbp);
+  const int64_t b1 = std::min<int64_t>((nbp * kRangeSplit + kWarps - 1) / kWarps, (int64_t)nsm * 8);
+  k_range_bounds<<<(unsigned)b1, kThreads, 0, s>>>(g, d_minmax, bpb);
+  k_range_list<<<b0, kThreads, 0, s>>>(d_minmax, bpb, nbp, list);
+  // the pass-2 block records follow the list (sized for kRangeMaxBlocks)
+  RExt* rec = reinterpret_cast<RExt*>(list + ((nbp + 3) & ~int64_t(3)));
+  const unsigned b2 = (unsigned)std::min<int64_t>(std::min<int64_t>((nbp * 32 + kWarps - 1) / kWarps, (int64_t)nsm * 8),
+                                                  kRangeMaxBlocks);
   switch (g.m) {
-    case 1: k_range32<1><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 3: k_range32<3><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 4: k_range32<4><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 6: k_range32<6><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
-    case 7: k_range32<7><<<b2, kThreads, 0, s>>>(g, d_minmax, bpb); break;
+    case 1: k_range32<1><<<b2, kThreads, 0, s>>>(g, d_minmax, list, rec); break;
+    case 3: k_range32<3><<<b2, kThreads, 0, s>>>(g, d_minmax, list, rec); break;
+    case 4: k_range32<4><<<b2, kThreads, 0, s>>>(g, d_minmax, list, rec); break;
+    case 6: k_range32<6><<<b2, kThreads, 0, s>>>(g, d_minmax, list, rec); break;
+    case 7: k_range32<7><<<b2, kThreads, 0, s>>>(g, d_minmax, list, rec); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -96,6 +96,7 @@ def test_range_matches_oracle(which):
         g32 = m.range(rule, gf.GF_FP32)
         assert abs(g64[0] - lo) <= 1e-14 * lo and abs(g64[1] - hi) <= 1e-14 * hi
         assert abs(g32[0] - lo) <= 1e-6 * lo and abs(g32[1] - hi) <= 1e-6 * hi
+        assert m.range(rule, gf.GF_FP32) == g32  # independent of the order the device evaluates in
 
 
 def test_near_dist_criterion_matches_oracle():
