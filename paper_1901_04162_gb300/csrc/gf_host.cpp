@@ -356,7 +356,7 @@ gf_status check_device(int dev) {
 void free_mesh_device(gf_mesh* m) {
   void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_near_row, m->d_pts32,
                   m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
-                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb, m->d_frame64, m->d_range_list};
+                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb, m->d_frame64, m->d_range_list, m->d_frame32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -402,7 +402,7 @@ gf_status prepare_rule_impl(gf_mesh* m, int rule, cudaStream_t s) {
   if (e == cudaSuccess)
     e = launch_prep_geometry(m->d_v64, (int)m->nt, rule, d_bw, d_bw + 3 * kMaxRule, m->d_tedge, m->d_elen,
                              m->d_pts32, m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64, m->d_rad32,
-                             m->d_frame64, s);
+                             m->d_frame64, m->d_frame32, s);
   if (e == cudaSuccess) {
     m->rule = rule;  // views below read the new geometry
     e = launch_block_spheres(geo_view_impl(m), m->d_bsph, s);
@@ -429,6 +429,7 @@ GeoView geo_view_impl(const gf_mesh* m) {
   g.geo64 = m->d_geo64;
   g.v64 = m->d_v64;
   g.frame64 = m->d_frame64;
+  g.frame32 = m->d_frame32;
   g.tvert = m->d_tvert;
   g.tedge = m->d_tedge;
   g.near_ptr = m->d_near_ptr;
@@ -618,6 +619,7 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
       (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
       (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_frame64, (size_t)kFrame * nt)) ||
+      (st = dev_alloc(&m->d_frame32, (size_t)kFrame32 * nt)) ||
       (st = dev_alloc(&m->d_minmax, 8)) ||
       (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32)) ||
       (st = dev_alloc(&m->d_range_bpb, (size_t)((nt + 31) / 32) * ((nt + 31) / 32 + 1) / 2)) ||

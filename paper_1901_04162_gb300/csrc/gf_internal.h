@@ -50,6 +50,7 @@ struct GeoView {
   const double* geo64;   // [nt][3][4]
   const double* v64;     // [nt][9] vertices
   const double* frame64; // [nt][kFrame] near-pair source frames
+  const float* frame32;  // [nt][kFrame32]
   const int4* tvert;     // [nt]: vertex ids (x, y, z)
   const int4* tedge;     // [nt]: RWG edge id of local edge i, or -1
   const int64_t* near_ptr;  // [nt + 1]
@@ -136,11 +137,12 @@ struct BatchItem {
 // ---------------------------------------------------------------- kernels (gf_kernels.cu)
 // Doubles per triangle of the near-pair source frames: unit normal [0..2],
 // edge lengths [3..5], unit edge tangents [6..14], in-plane edge normals [15..23].
-constexpr int kFrame = 24;
+constexpr int kFrame = 25;    // FP64 source frame per triangle: n, len, t, m, 1/area
+constexpr int kFrame32 = 24;  // FP32 copy of len, t, m (the sampled integrals)
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
-                                 double* frame64, cudaStream_t s);
+                                 double* frame64, float* frame32, cudaStream_t s);
 // Device build of one table (arrays in its arena; view = its TabView, whose
 // lattice fields the lattice stage reads).
 struct TableBuild {
@@ -227,6 +229,7 @@ struct gf_mesh {
   double* d_cen64 = nullptr;
   double* d_geo64 = nullptr;
   double* d_frame64 = nullptr;
+  float* d_frame32 = nullptr;
   float* d_rad32 = nullptr;
   float4* d_bsph = nullptr;
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]

@@ -40,7 +40,8 @@ __device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
 __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, const double* __restrict__ bary,
                                 const double* __restrict__ w, const int4* __restrict__ tedge,
                                 const double* __restrict__ elen, float4* pts32, float4* cen32, float4* geo32,
-                                double* pts64, double* cen64, double* geo64, float* rad32, double* frame64) {
+                                double* pts64, double* cen64, double* geo64, float* rad32, double* frame64,
+                                float* frame32) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nt) return;
   double v[3][3];
@@ -48,13 +49,16 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
     for (int x = 0; x < 3; ++x) v[c][x] = v64[9 * (size_t)t + 3 * c + x];
   {
     // source-triangle frame of the near-pair integrals: unit normal, edge
-    // lengths, unit edge tangents (v_e -> v_{e+1}) and in-plane edge normals t x n
+    // lengths, unit edge tangents (v_e -> v_{e+1}), in-plane edge normals t x n
+    // and 1/area; an FP32 copy of the lengths, tangents and normals
     double* fr = frame64 + kFrame * (size_t)t;
+    float* f32 = frame32 + kFrame32 * (size_t)t;
     const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
     const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
     double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
     const double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     for (int x = 0; x < 3; ++x) fr[x] = n[x] = n[x] * inv;
+    fr[24] = 2.0 * inv;  // 1 / area
     for (int e = 0; e < 3; ++e) {
       const double* a = v[e];
       const double* b = v[(e + 1) % 3];
@@ -68,6 +72,8 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
       fr[15 + 3 * e + 1] = tt[2] * n[0] - tt[0] * n[2];
       fr[15 + 3 * e + 2] = tt[0] * n[1] - tt[1] * n[0];
     }
+    for (int i = 0; i < 21; ++i) f32[i] = (float)fr[3 + i];
+    for (int i = 21; i < kFrame32; ++i) f32[i] = 0.f;
   }
   double c0 = (v[0][0] + v[1][0] + v[2][0]) / 3.0;
   double c1 = (v[0][1] + v[1][1] + v[2][1]) / 3.0;
@@ -1212,8 +1218,9 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 // triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
 // and the static log term is one log of a ratio per edge.
 __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
-                                      const NearArgs& A, double k, double inv_k, const Tab32& te, bool use_table,
-                                      float lo, float hi, C2* I0, C2 I1[3], double rho0[3]) {
+                                      const float* __restrict__ fr32, const NearArgs& A, double k, double inv_k,
+                                      const Tab32& te, bool use_table, float lo, float hi, C2* I0, C2 I1[3],
+                                      double rho0[3]) {
   const float kpi = (float)(k / kPi), k32 = (float)k;
   const double n[3] = {fr[0], fr[1], fr[2]};
   const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
@@ -1266,8 +1273,8 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
     }
     // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
     const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
-    const float tx = (float)t[0], ty = (float)t[1], tz = (float)t[2];
-    const float hl = 0.5f * (float)len;
+    const float tx = fr32[3 + 3 * e], ty = fr32[4 + 3 * e], tz = fr32[5 + 3 * e];
+    const float hl = 0.5f * fr32[e];
     float lr = 0.f, li = 0.f;
     for (int i = 0; i < A.nl; ++i) {
       const float sp = hl * (A.fx_l[i] + 1.0f);
@@ -1293,7 +1300,7 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
       else ratio = (Rm - lm) / (Rp - lp);
       st += 0.5 * R02 * log(ratio);
     }
-    const float mx = (float)mh[0], my = (float)mh[1], mz = (float)mh[2];
+    const float mx = fr32[12 + 3 * e], my = fr32[13 + 3 * e], mz = fr32[14 + 3 * e];
     vre[0] = fmaf(mx, lr, vre[0]);
     vre[1] = fmaf(my, lr, vre[1]);
     vre[2] = fmaf(mz, lr, vre[2]);
@@ -1355,8 +1362,8 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
     C2 I0, I1[3];
     double rho0[3];
     if (MIXED)
-      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, A, ks.k, ks.inv_k, te32, use_table, lo32, hi32,
-                            &I0, I1, rho0);
+      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, g.frame32 + kFrame32 * (size_t)q, A, ks.k,
+                            ks.inv_k, te32, use_table, lo32, hi32, &I0, I1, rho0);
     else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
     // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
     // w_a / 4 folded into I0, I1
@@ -1407,7 +1414,7 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
 #pragma unroll
     for (int u = 0; u < 3; ++u) fin[u] = r3[u];
   }
-  const double inv_area_q = 1.0 / g.cen64[4 * (size_t)q + 3];
+  const double inv_area_q = g.frame64[kFrame * (size_t)q + 24];
   const int4 ep = g.tedge[p], eq = g.tedge[q];
 #pragma unroll
   for (int u = 0; u < NS; ++u) {
@@ -2833,9 +2840,9 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
-                                 double* frame64, cudaStream_t s) {
+                                 double* frame64, float* frame32, cudaStream_t s) {
   k_prep_geometry<<<(nt + 127) / 128, 128, 0, s>>>(v64, nt, m, bary, w, tedge, edge_len, pts32, cen32, geo32,
-                                                   pts64, cen64, geo64, rad32, frame64);
+                                                   pts64, cen64, geo64, rad32, frame64, frame32);
   return cudaGetLastError();
 }
 
