@@ -7,7 +7,6 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -338,6 +337,61 @@ gf::TabView gf_table::One::view() const {
 
 namespace {
 
+// Device memory of destroyed tables and meshes kept for the next one of a
+// similar size on the same device (a table is rebuilt for every range / k;
+// cudaMalloc costs as much as building it). At most kPoolBlocks blocks, kPoolBytes bytes.
+constexpr int kPoolBlocks = 8;
+constexpr size_t kPoolBytes = size_t(1) << 30;
+
+struct ArenaPool {
+  std::mutex mu;
+  struct Block {
+    int device;
+    void* ptr;
+    size_t bytes;
+  };
+  std::vector<Block> blocks;
+  size_t held = 0;
+};
+
+ArenaPool& arena_pool() {
+  static ArenaPool* p = new ArenaPool;  // never destroyed: blocks live until the process exits
+  return *p;
+}
+
+// A pooled block of at least `bytes` (and at most twice that) on `device`, or null.
+void* arena_take(int device, size_t bytes, size_t* got) {
+  ArenaPool& P = arena_pool();
+  std::lock_guard<std::mutex> lock(P.mu);
+  int best = -1;
+  for (int i = 0; i < (int)P.blocks.size(); ++i) {
+    const ArenaPool::Block& b = P.blocks[i];
+    if (b.device == device && b.bytes >= bytes && b.bytes <= 2 * bytes + (1 << 20) &&
+        (best < 0 || b.bytes < P.blocks[best].bytes))
+      best = i;
+  }
+  if (best < 0) return nullptr;
+  void* ptr = P.blocks[best].ptr;
+  *got = P.blocks[best].bytes;
+  P.held -= *got;
+  P.blocks.erase(P.blocks.begin() + best);
+  return ptr;
+}
+
+// Called with no work in flight on the block (the caller synchronized the device).
+void arena_give(int device, void* ptr, size_t bytes) {
+  ArenaPool& P = arena_pool();
+  {
+    std::lock_guard<std::mutex> lock(P.mu);
+    if ((int)P.blocks.size() < kPoolBlocks && P.held + bytes <= kPoolBytes) {
+      P.blocks.push_back(ArenaPool::Block{device, ptr, bytes});
+      P.held += bytes;
+      return;
+    }
+  }
+  cudaFree(ptr);
+}
+
 template <class T>
 gf_status dev_alloc(T** p, size_t n) {
   if (n == 0) n = 1;
@@ -354,21 +408,28 @@ gf_status check_device(int dev) {
 }
 
 void free_mesh_device(gf_mesh* m) {
-  void* ptrs[] = {m->d_v64,   m->d_tvert, m->d_tedge, m->d_elen,  m->d_near_ptr, m->d_near_idx, m->d_near_row, m->d_pts32,
-                  m->d_cen32, m->d_geo32, m->d_pts64, m->d_cen64, m->d_geo64,    m->d_minmax, m->d_rad32,
-                  m->d_dtri,  m->d_dk, m->d_bsph, m->d_range_bpb, m->d_frame64, m->d_range_list, m->d_frame32};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  if (m->d_arena) {
+    cudaDeviceSynchronize();  // no work in flight on the arena when it goes back to the pool
+    arena_give(m->device, m->d_arena, m->arena_bytes);
+    m->d_arena = nullptr;
+  }
+  if (m->d_dtri) cudaFree(m->d_dtri);
+  if (m->d_dk) cudaFree(m->d_dk);
+  m->d_dtri = nullptr;
+  m->d_dk = nullptr;
 }
 
-gf_status upload_vertices(gf_mesh* m) {
-  std::vector<double> v64(9 * (size_t)m->nt);  // internal (Morton) triangle order
+// Triangle corners (internal order) and RWG edge lengths, laid out as on the
+// device (elen follows v64 at a 256-byte aligned offset).
+void vertex_arrays(const gf_mesh* m, unsigned char* dst) {
+  double* v64 = reinterpret_cast<double*>(dst);
   for (int64_t i = 0; i < m->nt; ++i) {
     const int64_t t = m->perm[i];
     for (int c = 0; c < 3; ++c)
       for (int x = 0; x < 3; ++x) v64[9 * i + 3 * c + x] = m->xyz[3 * (size_t)m->tri[3 * t + c] + x];
   }
-  std::vector<double> elen(m->ne);
+  double* elen = reinterpret_cast<double*>(dst + (reinterpret_cast<unsigned char*>(m->d_elen) -
+                                                  reinterpret_cast<unsigned char*>(m->d_v64)));
   for (int64_t e = 0; e < m->ne; ++e) {
     double s = 0;
     for (int x = 0; x < 3; ++x) {
@@ -377,10 +438,52 @@ gf_status upload_vertices(gf_mesh* m) {
     }
     elen[e] = std::sqrt(s);
   }
-  GF_CUDA(cudaMemcpy(m->d_v64, v64.data(), v64.size() * 8, cudaMemcpyHostToDevice));
-  GF_CUDA(cudaMemcpy(m->d_elen, elen.data(), elen.size() * 8 + 8 * (m->ne == 0), cudaMemcpyHostToDevice));
+}
+
+size_t vertex_bytes(const gf_mesh* m) {
+  return (size_t)(reinterpret_cast<unsigned char*>(m->d_elen) - reinterpret_cast<unsigned char*>(m->d_v64)) +
+         (size_t)std::max<int64_t>(m->ne, 1) * 8;
+}
+
+gf_status upload_vertices(gf_mesh* m) {
+  std::vector<unsigned char> h(vertex_bytes(m), 0);
+  vertex_arrays(m, h.data());
+  GF_CUDA(cudaMemcpy(m->d_v64, h.data(), h.size(), cudaMemcpyHostToDevice));
   m->rule = 0;  // geometry cache invalid
   return GF_OK;
+}
+
+// Stable LSD radix sort (8-bit digits over the low `bits` bits): the order of
+// the keys, equal keys in input order.
+std::vector<int32_t> radix_order(const std::vector<uint64_t>& key, int bits) {
+  const size_t n = key.size();
+  std::vector<int32_t> a(n), b(n);
+  std::vector<uint64_t> k(key), kb(n);  // keys carried along with the order
+  for (size_t i = 0; i < n; ++i) a[i] = (int32_t)i;
+  uint32_t cnt[257];
+  for (int sh = 0; sh < bits; sh += 8) {
+    std::fill(cnt, cnt + 257, 0u);
+    for (size_t i = 0; i < n; ++i) ++cnt[((k[i] >> sh) & 0xFF) + 1];
+    if (cnt[1] == n) continue;  // every digit 0
+    for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
+    for (size_t i = 0; i < n; ++i) {
+      const uint32_t o = cnt[(k[i] >> sh) & 0xFF]++;
+      b[o] = a[i];
+      kb[o] = k[i];
+    }
+    a.swap(b);
+    k.swap(kb);
+  }
+  return a;
+}
+
+int bit_width(uint64_t v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 1;
+  }
+  return b;
 }
 
 // Builds (or reuses) the per-rule geometry on the device.
@@ -495,36 +598,41 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   m->near_dist = near_dist;
   m->xyz.assign(xyz, xyz + 3 * nv);
   m->tri.assign(tri, tri + 3 * nt);
-  // ---- RWG edges: sort (lower, higher, triangle, local index) records
-  std::vector<std::tuple<int32_t, int32_t, int32_t, int32_t>> rec;
-  rec.reserve(3 * nt);
+  // ---- RWG edges: records (lower, higher vertex) in (triangle, local index)
+  // order, sorted stably by the vertex pair (radix)
   for (int64_t t = 0; t < nt; ++t) {
     const int32_t* v = &tri[3 * t];
     for (int c = 0; c < 3; ++c) {
       if (v[c] < 0 || v[c] >= nv) return fail(GF_ERR_MESH, "gf_mesh_create: vertex index out of range");
     }
     if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) return fail(GF_ERR_MESH, "gf_mesh_create: repeated vertex");
-    for (int i = 0; i < 3; ++i) {  // local edge i is opposite local vertex i
-      int32_t a = v[(i + 1) % 3], b = v[(i + 2) % 3];
-      rec.emplace_back(std::min(a, b), std::max(a, b), (int32_t)t, i);
-    }
   }
-  std::sort(rec.begin(), rec.end());
+  const int vb = std::max(bit_width((uint64_t)(nv - 1)), 1);
+  std::vector<uint64_t> ekey(3 * nt);
+  for (int64_t t = 0; t < nt; ++t)
+    for (int i = 0; i < 3; ++i) {  // local edge i is opposite local vertex i
+      const int32_t a = tri[3 * t + (i + 1) % 3], b = tri[3 * t + (i + 2) % 3];
+      ekey[3 * t + i] = ((uint64_t)std::min(a, b) << vb) | (uint64_t)std::max(a, b);
+    }
+  const std::vector<int32_t> eorder = radix_order(ekey, 2 * vb);
   m->tedge.assign(3 * nt, -1);
-  for (size_t i = 0; i < rec.size();) {
+  m->ev.reserve(3 * nt);
+  m->et.reserve(3 * nt);
+  for (size_t i = 0; i < eorder.size();) {
     size_t j = i;
-    while (j < rec.size() && std::get<0>(rec[j]) == std::get<0>(rec[i]) && std::get<1>(rec[j]) == std::get<1>(rec[i])) ++j;
+    while (j < eorder.size() && ekey[eorder[j]] == ekey[eorder[i]]) ++j;
     if (j - i > 2) return fail(GF_ERR_MESH, "gf_mesh_create: edge shared by more than two triangles");
     if (j - i == 2) {
       const int32_t e = (int32_t)m->ev.size() / 2;
-      const int32_t tp = std::get<2>(rec[i]), tm = std::get<2>(rec[i + 1]);  // sorted: T+ first
+      const int32_t r0 = eorder[i], r1 = eorder[i + 1];  // input order: T+ first
+      const int32_t tp = r0 / 3, tm = r1 / 3;
       if (tp == tm) return fail(GF_ERR_MESH, "gf_mesh_create: degenerate triangle");
-      m->ev.push_back(std::get<0>(rec[i]));
-      m->ev.push_back(std::get<1>(rec[i]));
+      m->ev.push_back((int32_t)(ekey[r0] >> vb));
+      m->ev.push_back((int32_t)(ekey[r0] & ((uint64_t(1) << vb) - 1)));
       m->et.push_back(tp);
       m->et.push_back(tm);
-      m->tedge[3 * tp + std::get<3>(rec[i])] = 2 * e;          // even: T+ side
-      m->tedge[3 * tm + std::get<3>(rec[i + 1])] = 2 * e + 1;  // odd: T- side
+      m->tedge[r0] = 2 * e;      // even: T+ side
+      m->tedge[r1] = 2 * e + 1;  // odd: T- side
     }
     i = j;
   }
@@ -554,26 +662,27 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       v = (v | (v << 2)) & 0x1249249249249249ULL;
       return v;
     };
-    std::vector<std::pair<uint64_t, int32_t>> key(nt);
+    std::vector<uint64_t> code(nt);
     for (int64_t t = 0; t < nt; ++t) {
-      uint64_t code = 0;
-      for (int x = 0; x < 3; ++x) code |= spread((uint64_t)((cen[3 * t + x] - lo[x]) * scale)) << x;
-      key[t] = std::make_pair(code, (int32_t)t);
+      uint64_t c = 0;
+      for (int x = 0; x < 3; ++x) c |= spread((uint64_t)((cen[3 * t + x] - lo[x]) * scale)) << x;
+      code[t] = c;
     }
-    std::sort(key.begin(), key.end());
-    m->perm.resize(nt);
-    std::vector<int32_t> inv(nt);
-    for (int64_t i = 0; i < nt; ++i) {
-      m->perm[i] = key[i].second;
-      inv[key[i].second] = (int32_t)i;
-    }
-    m->inv_perm = inv;
+    m->perm = radix_order(code, 63);  // ties in triangle order
+    m->inv_perm.resize(nt);
+    for (int64_t i = 0; i < nt; ++i) m->inv_perm[m->perm[i]] = (int32_t)i;
   }
   // ---- near pairs (internal ids): vertex sharing, plus centroids closer
   // than near_dist
-  std::vector<std::vector<int32_t>> vt(nv);
-  for (int64_t t = 0; t < nt; ++t)
-    for (int c = 0; c < 3; ++c) vt[tri[3 * t + c]].push_back((int32_t)t);
+  // vertex stars: the triangles (internal ids, ascending) of each vertex
+  std::vector<int32_t> vptr(nv + 1, 0), vtri(3 * nt);
+  for (int64_t i = 0; i < 3 * nt; ++i) ++vptr[tri[i] + 1];
+  for (int64_t v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+  {
+    std::vector<int32_t> fillp(vptr.begin(), vptr.end() - 1);
+    for (int64_t pi = 0; pi < nt; ++pi)
+      for (int c = 0; c < 3; ++c) vtri[fillp[tri[3 * (size_t)m->perm[pi] + c]]++] = (int32_t)pi;
+  }
   std::unordered_map<int64_t, std::vector<int32_t>> grid;
   double cell = near_dist;
   auto key = [](int64_t a, int64_t b, int64_t c) { return ((a & 0x1FFFFF) << 42) | ((b & 0x1FFFFF) << 21) | (c & 0x1FFFFF); };
@@ -583,14 +692,31 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
                (int64_t)std::floor(cen[3 * t + 2] / cell))]
           .push_back((int32_t)t);
   }
+  // union of ascending lists, without repeats
+  auto merge_into = [](const int32_t* a, int na, const int32_t* b, int nb, std::vector<int32_t>& out) {
+    out.clear();
+    int i = 0, j = 0;
+    while (i < na || j < nb) {
+      int32_t x;
+      if (j >= nb || (i < na && a[i] < b[j])) x = a[i++];
+      else if (i >= na || b[j] < a[i]) x = b[j++];
+      else {
+        x = a[i++];
+        ++j;
+      }
+      out.push_back(x);
+    }
+  };
   m->near_ptr.assign(nt + 1, 0);
-  std::vector<int32_t> row;
+  m->near_idx.reserve(16 * (size_t)nt);
+  std::vector<int32_t> ab, row, close;
   for (int64_t pi = 0; pi < nt; ++pi) {
     const int64_t p = m->perm[pi];  // original id
-    row.clear();
-    for (int c = 0; c < 3; ++c)
-      for (int32_t q : vt[tri[3 * p + c]]) row.push_back(q);
+    const int32_t* v = &tri[3 * p];
+    merge_into(&vtri[vptr[v[0]]], vptr[v[0] + 1] - vptr[v[0]], &vtri[vptr[v[1]]], vptr[v[1] + 1] - vptr[v[1]], ab);
+    merge_into(ab.data(), (int)ab.size(), &vtri[vptr[v[2]]], vptr[v[2] + 1] - vptr[v[2]], row);
     if (near_dist > 0) {
+      close.clear();
       int64_t gx = (int64_t)std::floor(cen[3 * p] / cell), gy = (int64_t)std::floor(cen[3 * p + 1] / cell),
               gz = (int64_t)std::floor(cen[3 * p + 2] / cell);
       for (int dx = -1; dx <= 1; ++dx)
@@ -601,56 +727,85 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
             for (int32_t q : it->second) {
               double ax = cen[3 * p] - cen[3 * (size_t)q], ay = cen[3 * p + 1] - cen[3 * (size_t)q + 1],
                      az = cen[3 * p + 2] - cen[3 * (size_t)q + 2];
-              if (std::sqrt(ax * ax + ay * ay + az * az) < near_dist) row.push_back(q);
+              if (std::sqrt(ax * ax + ay * ay + az * az) < near_dist) close.push_back(m->inv_perm[q]);
             }
           }
+      std::sort(close.begin(), close.end());
+      close.erase(std::unique(close.begin(), close.end()), close.end());
+      ab.swap(row);
+      merge_into(ab.data(), (int)ab.size(), close.data(), (int)close.size(), row);
     }
-    for (int32_t& q : row) q = m->inv_perm[q];  // internal ids
-    std::sort(row.begin(), row.end());
-    row.erase(std::unique(row.begin(), row.end()), row.end());
     m->near_idx.insert(m->near_idx.end(), row.begin(), row.end());
     m->near_ptr[pi + 1] = (int64_t)m->near_idx.size();
   }
-  // ---- device upload
-  gf_status st;
-  if ((st = dev_alloc(&m->d_v64, 9 * nt)) || (st = dev_alloc(&m->d_tvert, nt)) || (st = dev_alloc(&m->d_tedge, nt)) ||
-      (st = dev_alloc(&m->d_elen, m->ne)) || (st = dev_alloc(&m->d_near_ptr, nt + 1)) ||
-      (st = dev_alloc(&m->d_near_idx, m->near_idx.size())) || (st = dev_alloc(&m->d_near_row, m->near_idx.size())) || (st = dev_alloc(&m->d_pts32, kMaxRule * nt)) ||
-      (st = dev_alloc(&m->d_cen32, nt)) || (st = dev_alloc(&m->d_geo32, 3 * nt)) ||
-      (st = dev_alloc(&m->d_pts64, 4 * kMaxRule * nt)) || (st = dev_alloc(&m->d_cen64, 4 * nt)) ||
-      (st = dev_alloc(&m->d_geo64, 12 * nt)) || (st = dev_alloc(&m->d_frame64, (size_t)kFrame * nt)) ||
-      (st = dev_alloc(&m->d_frame32, (size_t)kFrame32 * nt)) ||
-      (st = dev_alloc(&m->d_minmax, 8)) ||
-      (st = dev_alloc(&m->d_rad32, nt)) || (st = dev_alloc(&m->d_bsph, (nt + 31) / 32)) ||
-      (st = dev_alloc(&m->d_range_bpb, (size_t)((nt + 31) / 32) * ((nt + 31) / 32 + 1) / 2)) ||
-      (st = dev_alloc(&m->d_range_list, range_list_ints(nt)))) {
-    free_mesh_device(m.get());
-    return st;
+  // ---- device: one pooled allocation; the arrays built here are uploaded
+  // with one copy (they lead the arena, in this order)
+  const size_t nn = m->near_idx.size();
+  const int64_t nb = (nt + 31) / 32;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_tvert = take(16 * nt), o_tedge = take(16 * nt), o_near_ptr = take(8 * (nt + 1)),
+               o_near_idx = take(4 * nn), o_near_row = take(4 * nn), o_v64 = take(72 * nt),
+               o_elen = take(8 * std::max<int64_t>(m->ne, 1));
+  const size_t upload = off;
+  const size_t o_pts32 = take(16 * kMaxRule * nt), o_cen32 = take(16 * nt), o_geo32 = take(48 * nt),
+               o_pts64 = take(32 * kMaxRule * nt), o_cen64 = take(32 * nt), o_geo64 = take(96 * nt),
+               o_frame64 = take(8 * kFrame * nt), o_frame32 = take(4 * kFrame32 * nt), o_minmax = take(64),
+               o_rad32 = take(4 * nt), o_bsph = take(16 * nb), o_bpb = take(8 * (size_t)(nb * (nb + 1) / 2)),
+               o_list = take(4 * range_list_ints(nt));
+  size_t got = 0;
+  unsigned char* base = static_cast<unsigned char*>(arena_take(m->device, off, &got));
+  if (!base) {
+    cudaError_t e = cudaMalloc((void**)&base, off);
+    if (e != cudaSuccess) return cuda_fail(e, "gf_mesh_create: cudaMalloc");
+    got = off;
   }
-  std::vector<int4> tv(nt), te(nt);
+  m->d_arena = base;
+  m->arena_bytes = got;
+  m->d_tvert = reinterpret_cast<int4*>(base + o_tvert);
+  m->d_tedge = reinterpret_cast<int4*>(base + o_tedge);
+  m->d_near_ptr = reinterpret_cast<int64_t*>(base + o_near_ptr);
+  m->d_near_idx = reinterpret_cast<int32_t*>(base + o_near_idx);
+  m->d_near_row = reinterpret_cast<int32_t*>(base + o_near_row);
+  m->d_v64 = reinterpret_cast<double*>(base + o_v64);
+  m->d_elen = reinterpret_cast<double*>(base + o_elen);
+  m->d_pts32 = reinterpret_cast<float4*>(base + o_pts32);
+  m->d_cen32 = reinterpret_cast<float4*>(base + o_cen32);
+  m->d_geo32 = reinterpret_cast<float4*>(base + o_geo32);
+  m->d_pts64 = reinterpret_cast<double*>(base + o_pts64);
+  m->d_cen64 = reinterpret_cast<double*>(base + o_cen64);
+  m->d_geo64 = reinterpret_cast<double*>(base + o_geo64);
+  m->d_frame64 = reinterpret_cast<double*>(base + o_frame64);
+  m->d_frame32 = reinterpret_cast<float*>(base + o_frame32);
+  m->d_minmax = reinterpret_cast<unsigned long long*>(base + o_minmax);
+  m->d_rad32 = reinterpret_cast<float*>(base + o_rad32);
+  m->d_bsph = reinterpret_cast<float4*>(base + o_bsph);
+  m->d_range_bpb = reinterpret_cast<float2*>(base + o_bpb);
+  m->d_range_list = reinterpret_cast<int32_t*>(base + o_list);
+  std::vector<unsigned char> h(upload, 0);
+  int4* tv = reinterpret_cast<int4*>(&h[o_tvert]);
+  int4* te = reinterpret_cast<int4*>(&h[o_tedge]);
   for (int64_t i = 0; i < nt; ++i) {
     const int64_t t = m->perm[i];
     tv[i] = make_int4(tri[3 * t], tri[3 * t + 1], tri[3 * t + 2], 0);
     te[i] = make_int4(m->tedge[3 * t], m->tedge[3 * t + 1], m->tedge[3 * t + 2], 0);
   }
-  cudaError_t e = cudaMemcpy(m->d_tvert, tv.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->d_tedge, te.data(), nt * sizeof(int4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(m->d_near_ptr, m->near_ptr.data(), (nt + 1) * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !m->near_idx.empty()) {
-    e = cudaMemcpy(m->d_near_idx, m->near_idx.data(), m->near_idx.size() * 4, cudaMemcpyHostToDevice);
-    std::vector<int32_t> rows(m->near_idx.size());
-    for (int64_t pi = 0; pi < nt; ++pi)
-      for (int64_t j = m->near_ptr[pi]; j < m->near_ptr[pi + 1]; ++j) rows[j] = (int32_t)pi;
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_near_row, rows.data(), rows.size() * 4, cudaMemcpyHostToDevice);
-  }
+  std::memcpy(&h[o_near_ptr], m->near_ptr.data(), (nt + 1) * 8);
+  if (nn) std::memcpy(&h[o_near_idx], m->near_idx.data(), nn * 4);
+  int32_t* rows = reinterpret_cast<int32_t*>(&h[o_near_row]);
+  for (int64_t pi = 0; pi < nt; ++pi)
+    for (int64_t j = m->near_ptr[pi]; j < m->near_ptr[pi + 1]; ++j) rows[j] = (int32_t)pi;
+  vertex_arrays(m.get(), &h[o_v64]);
+  cudaError_t e = cudaMemcpy(base, h.data(), upload, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_mesh_device(m.get());
     return cuda_fail(e, "gf_mesh_create upload");
   }
-  if ((st = upload_vertices(m.get()))) {
-    free_mesh_device(m.get());
-    return st;
-  }
+  m->rule = 0;
   *out = m.release();
   return GF_OK;
 }
@@ -710,61 +865,6 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
 }
 
 namespace {
-
-// Device memory of destroyed tables kept for the next table of a similar
-// size on the same device (a table is rebuilt for every range / k; cudaMalloc
-// costs as much as building it). At most kPoolBlocks blocks, kPoolBytes bytes.
-constexpr int kPoolBlocks = 8;
-constexpr size_t kPoolBytes = size_t(1) << 30;
-
-struct ArenaPool {
-  std::mutex mu;
-  struct Block {
-    int device;
-    void* ptr;
-    size_t bytes;
-  };
-  std::vector<Block> blocks;
-  size_t held = 0;
-};
-
-ArenaPool& arena_pool() {
-  static ArenaPool* p = new ArenaPool;  // never destroyed: blocks live until the process exits
-  return *p;
-}
-
-// A pooled block of at least `bytes` (and at most twice that) on `device`, or null.
-void* arena_take(int device, size_t bytes, size_t* got) {
-  ArenaPool& P = arena_pool();
-  std::lock_guard<std::mutex> lock(P.mu);
-  int best = -1;
-  for (int i = 0; i < (int)P.blocks.size(); ++i) {
-    const ArenaPool::Block& b = P.blocks[i];
-    if (b.device == device && b.bytes >= bytes && b.bytes <= 2 * bytes + (1 << 20) &&
-        (best < 0 || b.bytes < P.blocks[best].bytes))
-      best = i;
-  }
-  if (best < 0) return nullptr;
-  void* ptr = P.blocks[best].ptr;
-  *got = P.blocks[best].bytes;
-  P.held -= *got;
-  P.blocks.erase(P.blocks.begin() + best);
-  return ptr;
-}
-
-// Called with no work in flight on the block (the caller synchronized the device).
-void arena_give(int device, void* ptr, size_t bytes) {
-  ArenaPool& P = arena_pool();
-  {
-    std::lock_guard<std::mutex> lock(P.mu);
-    if ((int)P.blocks.size() < kPoolBlocks && P.held + bytes <= kPoolBytes) {
-      P.blocks.push_back(ArenaPool::Block{device, ptr, bytes});
-      P.held += bytes;
-      return;
-    }
-  }
-  cudaFree(ptr);
-}
 
 // FP32 lattice image of a table (the device lookups repeat these float
 // operations exactly): u = fma(x, inv, nc); v = clamp(u + kLatMagic); the

@@ -212,7 +212,9 @@ struct gf_mesh {
   std::vector<int32_t> inv_perm;  // original -> internal
   std::vector<int64_t> near_ptr;  // [nt + 1], internal ids
   std::vector<int32_t> near_idx;
-  // device
+  // device: one allocation (d_arena) holds every array but the adjoint scratch
+  void* d_arena = nullptr;
+  size_t arena_bytes = 0;
   double* d_v64 = nullptr;
   int4* d_tvert = nullptr;
   int4* d_tedge = nullptr;

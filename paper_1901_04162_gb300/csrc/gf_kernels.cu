@@ -1464,27 +1464,27 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
 constexpr int kTileQBlocks = 16;
 constexpr int kWinBytes = 200 * 1024;
 
+// One warp per block of 32 triangles (lane = triangle): mean of the
+// centroids, then the largest centroid distance plus point radius.
 __global__ void k_block_spheres(GeoView g, float4* bsph) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nb = (g.nt + 31) / 32;
-  if (b >= nb) return;
-  const int t0 = 32 * b, t1 = min(t0 + 32, g.nt);
-  double cx = 0, cy = 0, cz = 0;
-  for (int t = t0; t < t1; ++t) {
-    cx += g.cen64[4 * (size_t)t];
-    cy += g.cen64[4 * (size_t)t + 1];
-    cz += g.cen64[4 * (size_t)t + 2];
+  if (b >= nb) return;  // uniform over the warp
+  const int t0 = 32 * b, n = min(32, g.nt - t0), t = t0 + min(lane, n - 1);
+  const double x = g.cen64[4 * (size_t)t], y = g.cen64[4 * (size_t)t + 1], z = g.cen64[4 * (size_t)t + 2];
+  double cx = lane < n ? x : 0.0, cy = lane < n ? y : 0.0, cz = lane < n ? z : 0.0;
+  for (int off = 16; off > 0; off >>= 1) {
+    cx += __shfl_xor_sync(0xffffffffu, cx, off);
+    cy += __shfl_xor_sync(0xffffffffu, cy, off);
+    cz += __shfl_xor_sync(0xffffffffu, cz, off);
   }
-  cx /= (t1 - t0);
-  cy /= (t1 - t0);
-  cz /= (t1 - t0);
-  double r = 0;
-  for (int t = t0; t < t1; ++t) {
-    const double dx = g.cen64[4 * (size_t)t] - cx, dy = g.cen64[4 * (size_t)t + 1] - cy,
-                 dz = g.cen64[4 * (size_t)t + 2] - cz;
-    r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz) + (double)g.rad32[t]);
-  }
-  bsph[b] = make_float4((float)cx, (float)cy, (float)cz, (float)(r * (1.0 + 1e-6)));
+  cx /= n;
+  cy /= n;
+  cz /= n;
+  const double dx = x - cx, dy = y - cy, dz = z - cz;
+  double r = sqrt(dx * dx + dy * dy + dz * dz) + (double)g.rad32[t];
+  for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
+  if (lane == 0) bsph[b] = make_float4((float)cx, (float)cy, (float)cz, (float)(r * (1.0 + 1e-6)));
 }
 
 template <int M>
@@ -2833,7 +2833,7 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
 
 cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s) {
   const int nb = (g.nt + 31) / 32;
-  k_block_spheres<<<(nb + 127) / 128, 128, 0, s>>>(g, bsph);
+  k_block_spheres<<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(g, bsph);
   return cudaGetLastError();
 }
 

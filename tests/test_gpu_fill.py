@@ -174,3 +174,19 @@ def test_cube_73728_sampled_rows():
     ref = om.z_rows(wl.k, 4, rows, mode="table", tables=O.make_tables(wl.k, olo, ohi))
     assert rel_fro(z, ref) <= 1e-5
     assert rel_max(z, ref) <= 1e-5
+
+
+def test_mesh_edges_and_near_count_match_oracle():
+    # RWG numbering (sorted vertex pairs, T+ = the first triangle in input
+    # order) and the number of ordered near pairs, on meshes with and without
+    # a centroid criterion
+    for wl in (W.plate_280(), W.sphere_3072(), W.cube_73728(8)):
+        m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+        om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
+        ev, et = m.edges()
+        oev, oet = om.edges()
+        np.testing.assert_array_equal(ev, oev)
+        np.testing.assert_array_equal(et, oet)
+        nt = len(wl.tri)
+        if nt <= 1000:
+            assert m.n_near == sum(om.is_near(p, q) for p in range(nt) for q in range(nt))
