@@ -48,6 +48,22 @@ FALLBACK_SM_MHZ = 2070.0
 TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "67e1a6b659a43fd1"): 925523200}
 
 
+def reduce_max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks (a job takes as long as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each process
+    `units_per_rank` units in `seconds` (the max over ranks)."""
+    return world * units_per_rank / seconds
+
+
 def kernel_source_hash():
     path = os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", "gf_kernels.cu")
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
@@ -272,15 +288,11 @@ def run_ours(args, wl, rank, world, local_rank):
     d64 = timed(True, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
 
     def reduce_max(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max_over_ranks(x, dist, dev)
 
     total_ms = reduce_max(sum(tt["step_ms"]))
     ms_step = total_ms / args.steps
-    value = world * ne * ne * args.steps / (total_ms / 1e3)
+    value = job_throughput(world, ne * ne * args.steps, total_ms / 1e3)
     direct_ms = reduce_max(sum(td["step_ms"])) / args.steps
 
     # ---- end to end: host arrays in, host copy of Z out, through the C ABI
