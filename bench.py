@@ -45,7 +45,7 @@ FALLBACK_SM_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "67e1a6b659a43fd1"): 925523200}
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "baa1247fe0f5ce17"): 550877696 + 536157696}
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
@@ -410,8 +410,53 @@ def run_ours(args, wl, rank, world, local_rank):
         t_full, desc, cores, _ = oracle_baseline(wl)
         line["cpu_baseline"] = {"value": ne * ne / t_full, "unit": "Z entries/s", "cores": cores,
                                 "kind": "oracle", "sample": desc}
+    if rank == 0 and "sphere_radius" in wl.extra and not args.skip_oracle:
+        line["rcs"] = sphere_rcs(gf, torch, mesh, wl, p, prec, stream, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def sphere_rcs(gf, torch, mesh, wl, p, prec, stream, dev):
+    """Plane-wave scattering by the sphere (outside the timed region): fill,
+    excitation, dense solve, far field; bistatic sigma in the E- and H-planes
+    against the Mie series, table fill against direct fill, and the times of
+    the scattering kernels (CUDA events on the launching stream)."""
+    from oracle import rcs
+    a = wl.extra["sphere_radius"]
+    th = np.linspace(0, math.pi, 181)
+    dirs = {pl: torch.from_numpy(rcs.plane_directions(th, pl)).to(dev) for pl in "EH"}
+    mie = dict(zip("EH", rcs.mie_bistatic(wl.k, a, th)))
+    lo, hi = mesh.range(wl.rule, prec)
+    tab = gf.Table(wl.k, lo, hi, p)
+    zdt = torch.complex64 if prec == gf.GF_FP32 else torch.complex128
+    out, sig = {}, {}
+    for name, table in (("table", tab), ("direct", None)):
+        Z = gf.fill(mesh, wl.k, p, table, prec)
+        V = torch.empty(mesh.ne, dtype=zdt, device=dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        gf.gf_excitation(mesh.h, wl.k, p, (0.0, 0.0, 1.0), (1.0, 0.0, 0.0), prec, V)
+        ev[1].record(stream)
+        I = torch.linalg.solve(Z, V)
+        ev[2].record(stream)
+        for pl in "EH":
+            sig[(name, pl)] = gf.gf_far_field(mesh.h, wl.k, p, prec, I, dirs[pl])[1].cpu().numpy()
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        del Z
+        if name == "table":
+            out["excitation_ms"] = ev[0].elapsed_time(ev[1])
+            out["solve_ms (torch.linalg.solve, LU)"] = ev[1].elapsed_time(ev[2])
+            out["far_field_ms"] = ev[2].elapsed_time(ev[3])
+    rl = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    for pl in "EH":
+        out[f"table_vs_mie_rel_l2_{pl}"] = rl(sig[("table", pl)], mie[pl])
+        out[f"direct_vs_mie_rel_l2_{pl}"] = rl(sig[("direct", pl)], mie[pl])
+        out[f"table_vs_direct_rel_l2_{pl}"] = rl(sig[("table", pl)], sig[("direct", pl)])
+    out["backscatter_over_pi_a2"] = {"table": float(sig[("table", "E")][-1] / (math.pi * a * a)),
+                                     "mie": float(mie["E"][-1] / (math.pi * a * a))}
+    out["angles"] = "181 per plane, theta 0..180 deg; x-polarised plane wave along +z"
+    return out
 
 
 def run_batch(args, rank, world, local_rank):

@@ -196,6 +196,33 @@ gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const
                            int precision, const void* gZ, int64_t ldg, double* dxyz, double* dk,
                            void* stream);
 
+/* ---------------------------------------------------------------- scattering
+ * Plane-wave excitation and far field of an RWG current: with a solve of
+ * Z I = V (any dense solver) they turn the filled EFIE matrix into the
+ * bistatic radar cross section, the quantity the paper compares between the
+ * table and the direct fill (Section IV.B). Not part of the fill's hot path;
+ * FP64 arithmetic. Both use the rule p->rule on every triangle and the RWG
+ * convention of gf_fill (f_n = +-l_n/(2A)(r - v_opp) on T+ / T-).
+ *
+ * gf_excitation: V_m = <f_m, p e^{-jk khat.r}> for every RWG function m, the
+ * right side of Z I = V for the Z of gf_fill (e^{jwt} convention; the
+ * incident field p e^{-jk khat.r} travels along khat). khat: host [3], a unit
+ * vector (GF_ERR_ARG otherwise); pol: host [3][2] float64, the complex
+ * polarisation (re, im per component); V: device [ne] complex64 (GF_FP32) or
+ * complex128 (GF_FP64), overwritten. k >= 0. Asynchronous on `stream`.
+ *
+ * gf_far_field: for each of n_dir directions d (device float64 [n_dir][3],
+ * unit vectors), F(d) = -(j k eta / 4 pi)(N - (d.N) d) with
+ * N = sum_n I_n int f_n e^{jk d.r'} dS' (the scattered field is
+ * F e^{-jkr} / r far away), written to F (device float64 [n_dir][3][2],
+ * complex128), and sigma (device float64 [n_dir]) = 4 pi |F|^2, the bistatic
+ * radar cross section for a unit incident field. I: device [ne] complex64
+ * (GF_FP32) or complex128 (GF_FP64). eta = p->eta. Asynchronous on `stream`. */
+gf_status gf_excitation(const gf_mesh* m, double k, const gf_params* p, const double* khat, const double* pol,
+                        int precision, void* V, void* stream);
+gf_status gf_far_field(const gf_mesh* m, double k, const gf_params* p, int precision, const void* I,
+                       int64_t n_dir, const double* dirs, double* F, double* sigma, void* stream);
+
 /* ---------------------------------------------------------------- batched --
  * Many meshes in one launch per kernel: each mesh i has its own wavenumber
  * k[i], tables[i] (built for k[i] over that mesh's gf_range; tables == NULL:

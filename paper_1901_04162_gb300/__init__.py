@@ -6,14 +6,16 @@ does (and fails loudly if it cannot).
 """
 from .gfmom import (GF_EXP, GF_FP32, GF_FP64, GF_GREEN, GF_PART_NEAR, GF_PART_REGULAR, GF_PART_ZERO,
                     Batch, GfError, Mesh, Table, fill, gf_batch_config, gf_batch_create, gf_batch_destroy,
-                    gf_batch_launch, efie_fill, gf_fill, gf_fill_backward, gf_fill_parts,
+                    gf_batch_launch, efie_fill, gf_excitation, gf_far_field, gf_fill, gf_fill_backward,
+                    gf_fill_parts, planewave_rcs,
                     gf_last_error, gf_mesh_create, gf_mesh_destroy, gf_mesh_edges, gf_mesh_info,
                     gf_mesh_set_vertices, gf_params, gf_params_default, gf_range, gf_table_create,
                     gf_table_destroy, gf_table_eval, gf_table_info, gf_table_nodes, lib)
 
 __all__ = ["GF_EXP", "GF_FP32", "GF_FP64", "GF_GREEN", "GF_PART_NEAR", "GF_PART_REGULAR", "GF_PART_ZERO",
            "Batch", "GfError", "Mesh", "Table", "fill", "gf_batch_config", "gf_batch_create", "gf_batch_destroy",
-           "gf_batch_launch", "efie_fill", "gf_fill", "gf_fill_backward", "gf_fill_parts",
+           "gf_batch_launch", "efie_fill", "gf_excitation", "gf_far_field", "gf_fill", "gf_fill_backward",
+           "gf_fill_parts", "planewave_rcs",
            "gf_last_error", "gf_mesh_create", "gf_mesh_destroy", "gf_mesh_edges", "gf_mesh_info",
            "gf_mesh_set_vertices", "gf_params", "gf_params_default", "gf_range", "gf_table_create",
            "gf_table_destroy", "gf_table_eval", "gf_table_info", "gf_table_nodes", "lib"]

@@ -25,7 +25,7 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
-           "gf_batch_config", "gf_batch_destroy", "gf_fill_backward"]
+           "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -375,6 +375,51 @@ def gf_fill_backward(mesh, k, params, table, gZ, stream=None):
                                   GF_FP32, C.c_void_p(gZ.data_ptr()), gZ.shape[-1], C.c_void_p(dxyz.data_ptr()),
                                   C.c_void_p(dk.data_ptr()), _stream_ptr(stream)))
     return dxyz, dk
+
+
+def gf_excitation(mesh, k, params, khat, pol, precision, V, stream=None):
+    """V: CUDA [ne] complex64 (GF_FP32) or complex128 (GF_FP64), overwritten with
+    <f_m, p e^{-jk khat.r}>; khat a unit 3-vector, pol a complex 3-vector."""
+    _check_z(V, precision)
+    kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(3)
+    pc = np.asarray(pol, dtype=np.complex128).reshape(3)
+    pl = np.ascontiguousarray(np.stack([pc.real, pc.imag], axis=1), dtype=np.float64)
+    _check(lib().gf_excitation(mesh, float(k), C.byref(params), _ptr(kh), _ptr(pl), int(precision),
+                               C.c_void_p(V.data_ptr()), _stream_ptr(stream)))
+    return V
+
+
+def gf_far_field(mesh, k, params, precision, I, dirs, stream=None):
+    """I: CUDA [ne] complex (as precision); dirs: CUDA float64 [n, 3] unit
+    vectors. Returns (F complex128 [n, 3], sigma float64 [n]) CUDA tensors."""
+    import torch
+    _check_z(I, precision)
+    if not dirs.is_cuda or dirs.dtype != torch.float64 or not dirs.is_contiguous() or dirs.shape[-1] != 3:
+        raise ValueError("dirs must be a contiguous CUDA float64 [n, 3] tensor")
+    n = dirs.shape[0]
+    F = torch.empty((n, 3), dtype=torch.complex128, device=I.device)
+    sigma = torch.empty(n, dtype=torch.float64, device=I.device)
+    _check(lib().gf_far_field(mesh, float(k), C.byref(params), int(precision), C.c_void_p(I.data_ptr()), int(n),
+                              C.c_void_p(dirs.data_ptr()), C.c_void_p(F.data_ptr()),
+                              C.c_void_p(sigma.data_ptr()), _stream_ptr(stream)))
+    return F, sigma
+
+
+def planewave_rcs(mesh: "Mesh", k, dirs, params=None, table: "Table | None" = None, precision=GF_FP32,
+                  khat=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), stream=None):
+    """EFIE scattering of a plane wave by the PEC surface `mesh`: fill Z (this
+    library), V (gf_excitation), solve Z I = V (a dense LU from the linear
+    algebra library: torch.linalg.solve), then the far field. Returns
+    (sigma [n] float64, I [ne]) CUDA tensors."""
+    import torch
+    params = params or gf_params_default()
+    Z = fill(mesh, k, params, table, precision, stream=stream)
+    V = torch.empty(mesh.ne, dtype=Z.dtype, device=Z.device)
+    gf_excitation(mesh.h, k, params, khat, pol, precision, V, stream=stream)
+    I = torch.linalg.solve(Z, V)
+    del Z
+    _, sigma = gf_far_field(mesh.h, k, params, precision, I.contiguous(), dirs, stream=stream)
+    return sigma, I
 
 
 def _efie_function():

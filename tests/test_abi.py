@@ -60,3 +60,22 @@ def test_argument_errors_before_any_device_call():
     assert L.gf_table_destroy(None) == 0 and L.gf_mesh_destroy(None) == 0
     with pytest.raises(gf.GfError):
         gf.gf_table_create(-1.0, 0.1, 1.0)
+
+
+def test_scattering_argument_errors_before_any_device_call():
+    L = gf.lib()
+    p = gf.gf_params_default()
+    one = C.c_double(1.0)
+    fake = C.c_void_p(1)  # never dereferenced: the argument checks come first
+    kh = np.array([2.0, 0.0, 0.0])
+    pol = np.zeros((3, 2))
+    v = C.c_void_p(8)
+    assert L.gf_excitation(None, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1
+    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1  # |khat| != 1
+    kh[0] = 1.0
+    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 7, v, None) == -1
+    assert L.gf_excitation(fake, C.c_double(-1.0), C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1
+    d = C.c_void_p(16)
+    assert L.gf_far_field(fake, one, C.byref(p), 32, v, C.c_int64(-1), d, d, d, None) == -1
+    assert L.gf_far_field(fake, one, C.byref(p), 7, v, C.c_int64(3), d, d, d, None) == -1
+    assert L.gf_far_field(None, one, C.byref(p), 32, v, C.c_int64(3), d, d, d, None) == -1

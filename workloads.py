@@ -208,7 +208,7 @@ def sphere_7680():
     vertices jittered by U[+-2%] of the mean edge length, 7-point rule."""
     xyz, tri = icosphere(4, 1.0)
     xyz = jitter(xyz, tri, 0.02, 20190114)
-    return Workload("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", xyz, tri, TWO_PI, 7)
+    return Workload("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", xyz, tri, TWO_PI, 7, extra={"sphere_radius": 1.0})
 
 
 def sphere_3072():
@@ -216,7 +216,8 @@ def sphere_3072():
     jittered as above, 6-point rule (adjoint workload)."""
     xyz, tri = octasphere(4, 1.0)
     xyz = jitter(xyz, tri, 0.02, 20190115)
-    return Workload("sphere_r1lambda_2048tri_3072rwg_6pt_adjoint", xyz, tri, TWO_PI, 6)
+    return Workload("sphere_r1lambda_2048tri_3072rwg_6pt_adjoint", xyz, tri, TWO_PI, 6,
+                    extra={"sphere_radius": 1.0})
 
 
 def cube_73728(n: int = 64):
