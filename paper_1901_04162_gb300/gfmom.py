@@ -82,6 +82,8 @@ def lib():
         L.gf_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         L.gf_batch_destroy.argtypes = [vp]
         L.gf_fill_backward.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp, vp, vp]
+        L.gf_excitation.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, vp, C.c_int, vp, vp]
+        L.gf_far_field.argtypes = [vp, C.c_double, C.POINTER(gf_params), C.c_int, vp, i64, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
                 getattr(L, name).restype = C.c_int

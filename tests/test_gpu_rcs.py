@@ -80,9 +80,10 @@ def test_fp64_chain_matches_oracle_chain():
 
 def test_sphere_rcs_table_and_direct_vs_mie():
     # the 1 lambda sphere of the benchmark (5120 triangles, 7-point rule), FP32
-    # fills: bistatic sigma in the E- and H-planes against Mie (discretisation
-    # error of a lambda/13 mesh, ~1 %), and the table fill against the direct
-    # fill (the table's own error, far below the discretisation's)
+    # fills: bistatic sigma in the E- and H-planes against Mie (the lambda/13
+    # mesh's discretisation error; measured 0.23 %), and the table fill against
+    # the direct fill (the table's own error; measured 1.5e-6, the paper's
+    # Section IV.B order of magnitude)
     wl = W.sphere_7680()
     a = wl.extra["sphere_radius"]
     m = gf.Mesh(wl.xyz, wl.tri)
@@ -96,5 +97,5 @@ def test_sphere_rcs_table_and_direct_vs_mie():
         st, _ = gf.planewave_rcs(m, wl.k, d, p, tab, gf.GF_FP32)
         sd, _ = gf.planewave_rcs(m, wl.k, d, p, None, gf.GF_FP32)
         st, sd = st.cpu().numpy(), sd.cpu().numpy()
-        assert _rel(st, ref) < 0.03, plane
-        assert _rel(st, sd) < 1e-4, plane
+        assert _rel(st, ref) < 0.01, plane
+        assert _rel(st, sd) < 1e-5, plane
