@@ -448,7 +448,31 @@ def sphere_rcs(gf, torch, mesh, wl, p, prec, stream, dev):
             out["excitation_ms"] = ev[0].elapsed_time(ev[1])
             out["solve_ms (torch.linalg.solve, LU)"] = ev[1].elapsed_time(ev[2])
             out["far_field_ms"] = ev[2].elapsed_time(ev[3])
+    # MFIE (K operator) on the same closed surface: fill time, and its solution's sigma
+    for name, table in (("mfie_table", tab), ("mfie_direct", None)):
+        Z = torch.empty((mesh.ne, mesh.ne), dtype=zdt, device=dev)
+        for _ in range(2):
+            gf.gf_fill_mfie(mesh.h, wl.k, p, table.h if table else None, prec, Z)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        reps = 5
+        ev[0].record(stream)
+        for _ in range(reps):
+            gf.gf_fill_mfie(mesh.h, wl.k, p, table.h if table else None, prec, Z)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out[f"{name}_fill_ms"] = ev[0].elapsed_time(ev[1]) / reps
+        V = torch.empty(mesh.ne, dtype=zdt, device=dev)
+        gf.gf_excitation(mesh.h, wl.k, p, (0.0, 0.0, 1.0), (1.0, 0.0, 0.0), prec, V, op=gf.GF_OP_MFIE)
+        I = torch.linalg.solve(Z, V)
+        del Z
+        for pl in "EH":
+            sig[(name, pl)] = gf.gf_far_field(mesh.h, wl.k, p, prec, I, dirs[pl])[1].cpu().numpy()
     rl = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    for pl in "EH":
+        out[f"mfie_table_vs_mie_rel_l2_{pl}"] = rl(sig[("mfie_table", pl)], mie[pl])
+        out[f"mfie_vs_efie_rel_l2_{pl}"] = rl(sig[("mfie_table", pl)], sig[("table", pl)])
+        out[f"mfie_table_vs_direct_rel_l2_{pl}"] = rl(sig[("mfie_table", pl)], sig[("mfie_direct", pl)])
+    out["mfie_z_entries_per_s"] = mesh.ne * mesh.ne / (out["mfie_table_fill_ms"] / 1e3)
     for pl in "EH":
         out[f"table_vs_mie_rel_l2_{pl}"] = rl(sig[("table", pl)], mie[pl])
         out[f"direct_vs_mie_rel_l2_{pl}"] = rl(sig[("direct", pl)], mie[pl])

@@ -196,6 +196,25 @@ gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const
                            int precision, const void* gZ, int64_t ldg, double* dxyz, double* dk,
                            void* stream);
 
+/* ---------------------------------------------------------------- MFIE -----
+ * The magnetic-field integral equation matrix (the paper's second formulation,
+ * Section IV.B: its K operator uses the gradient of the same Green function,
+ * so the same tables serve it) for a CLOSED PEC surface whose triangles are
+ * wound counter-clockwise seen from outside (outward normals), e^{jwt}:
+ *   Z_mn = 1/2 <f_m, f_n> - <f_m, n x PV int grad G x f_n dS'>,
+ *   grad G = -(r - r') (1 + jkR) e^{-jkR} / (4 pi R^3).
+ * Regular pairs: the m-point rule on both triangles, every ordered pair,
+ * e^{-jkR}/R from the table's Green (Lagrange) table (or direct sincos with
+ * table == NULL), FP32 with Kahan outer sums (GF_FP32) or FP64. Pairs sharing
+ * a vertex and the self pair: FP64, the inner integral of grad G x (r' - v)
+ * as three edge line integrals (static part in closed form, e^{-jkR} - 1 by
+ * p->nl Gauss points) plus a solid-angle term (angles by p->nphi Gauss points),
+ * e^{-jkR} from the Exp table when a table is given. Z (device, row-major,
+ * ld = ldz, complex64 / complex128) is overwritten. Asynchronous on `stream`.
+ * The right side for a plane wave is gf_excitation with GF_OP_MFIE. */
+gf_status gf_fill_mfie(const gf_mesh* m, double k, const gf_params* p, const gf_table* table, int precision,
+                       void* Z_dev, int64_t ldz, void* stream);
+
 /* ---------------------------------------------------------------- scattering
  * Plane-wave excitation and far field of an RWG current: with a solve of
  * Z I = V (any dense solver) they turn the filled EFIE matrix into the
@@ -204,12 +223,14 @@ gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const
  * FP64 arithmetic. Both use the rule p->rule on every triangle and the RWG
  * convention of gf_fill (f_n = +-l_n/(2A)(r - v_opp) on T+ / T-).
  *
- * gf_excitation: V_m = <f_m, p e^{-jk khat.r}> for every RWG function m, the
- * right side of Z I = V for the Z of gf_fill (e^{jwt} convention; the
- * incident field p e^{-jk khat.r} travels along khat). khat: host [3], a unit
- * vector (GF_ERR_ARG otherwise); pol: host [3][2] float64, the complex
- * polarisation (re, im per component); V: device [ne] complex64 (GF_FP32) or
- * complex128 (GF_FP64), overwritten. k >= 0. Asynchronous on `stream`.
+ * gf_excitation: the right side of Z I = V for the incident plane wave
+ * E_inc = p e^{-jk khat.r} (e^{jwt}; it travels along khat): with op =
+ * GF_OP_EFIE, V_m = <f_m, E_inc> (the Z of gf_fill); with GF_OP_MFIE,
+ * V_m = <f_m, n x H_inc>, H_inc = (khat x p) e^{-jk khat.r} / eta (the Z of
+ * gf_fill_mfie; eta = p->eta). khat: host [3], a unit vector (GF_ERR_ARG
+ * otherwise); pol: host [3][2] float64, the complex polarisation (re, im per
+ * component); V: device [ne] complex64 (GF_FP32) or complex128 (GF_FP64),
+ * overwritten. k >= 0. Asynchronous on `stream`.
  *
  * gf_far_field: for each of n_dir directions d (device float64 [n_dir][3],
  * unit vectors), F(d) = -(j k eta / 4 pi)(N - (d.N) d) with
@@ -218,8 +239,10 @@ gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const
  * complex128), and sigma (device float64 [n_dir]) = 4 pi |F|^2, the bistatic
  * radar cross section for a unit incident field. I: device [ne] complex64
  * (GF_FP32) or complex128 (GF_FP64). eta = p->eta. Asynchronous on `stream`. */
+#define GF_OP_EFIE 0
+#define GF_OP_MFIE 1
 gf_status gf_excitation(const gf_mesh* m, double k, const gf_params* p, const double* khat, const double* pol,
-                        int precision, void* V, void* stream);
+                        int op, int precision, void* V, void* stream);
 gf_status gf_far_field(const gf_mesh* m, double k, const gf_params* p, int precision, const void* I,
                        int64_t n_dir, const double* dirs, double* F, double* sigma, void* stream);
 

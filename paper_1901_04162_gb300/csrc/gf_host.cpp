@@ -1296,6 +1296,44 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   return GF_OK;
 }
 
+gf_status gf_fill_mfie(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision, void* Z,
+                       int64_t ldz, void* stream) {
+  if (!mc || !params_ok(p) || !Z) return fail(GF_ERR_ARG, "gf_fill_mfie: bad argument");
+  if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_fill_mfie: bad precision");
+  if (!(k > 0) || ldz < mc->ne) return fail(GF_ERR_ARG, "gf_fill_mfie: need k > 0 and ldz >= ne");
+  gf_mesh* m = const_cast<gf_mesh*>(mc);
+  gf_status st = check_device(m->device);
+  if (st) return st;
+  if (table && (table->device != m->device)) return fail(GF_ERR_DEVICE, "gf_fill_mfie: table on another device");
+  if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill_mfie: table built for another k");
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = prepare_rule_impl(m, p->rule, s))) return st;
+  if (m->ne == 0) return GF_OK;
+  const size_t esz = precision == GF_FP32 ? 8 : 16;
+  GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
+  GeoView g = geo_view_impl(m);
+  TabView tg, te;
+  if (table) {
+    tg = table->green.view();
+    te = table->exp.view();
+  }
+  double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
+  gauss_legendre(p->nphi, gx_phi, gw_phi);
+  gauss_legendre(p->nl, gx_l, gw_l);
+  double glp[64], gll[64];
+  for (int i = 0; i < p->nphi; ++i) {
+    glp[i] = gx_phi[i];
+    glp[32 + i] = gw_phi[i];
+  }
+  for (int i = 0; i < p->nl; ++i) {
+    gll[i] = gx_l[i];
+    gll[32 + i] = gw_l[i];
+  }
+  GF_CUDA(launch_fill_mfie(g, table ? &tg : nullptr, table ? &te : nullptr, precision, k, p->nphi, p->nl, glp, gll, Z,
+                           ldz, s));
+  return GF_OK;
+}
+
 gf_status gf_fill_backward(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision,
                            const void* gZ, int64_t ldg, double* dxyz, double* dk, void* stream) {
   if (!mc || !params_ok(p) || !gZ || !dxyz || !dk) return fail(GF_ERR_ARG, "gf_fill_backward: bad argument");

@@ -138,7 +138,7 @@ struct BatchItem {
 // Doubles per triangle of the near-pair source frames: unit normal [0..2],
 // edge lengths [3..5], unit edge tangents [6..14], in-plane edge normals [15..23].
 constexpr int kFrame = 25;    // FP64 source frame per triangle: n, len, t, m, 1/area
-constexpr int kFrame32 = 24;  // FP32 copy of len, t, m (the sampled integrals)
+constexpr int kFrame32 = 24;  // FP32 copy of len, t, m (the sampled integrals) and n
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,
                                  float4* geo32, double* pts64, double* cen64, double* geo64, float* rad32,
@@ -171,6 +171,9 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 // bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
+cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, double k,
+                             int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
+                             cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
                          cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}

@@ -39,7 +39,8 @@ struct CplxIO<double2> {
 
 struct PlaneWave {
   double khat[3];
-  double pre[3], pim[3];  // complex polarisation
+  double pre[3], pim[3];  // complex polarisation (EFIE) or H_inc amplitude khat x p / eta (MFIE)
+  int mfie;               // test n x H_inc instead of E_inc
 };
 
 // V_m += <f_m, p e^{-jk khat.r}> over triangle t for each of its RWG edges:
@@ -51,6 +52,16 @@ __global__ void k_excitation(GeoView g, double k, PlaneWave w, T* V) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= g.nt) return;
   const double* c = g.cen64 + 4 * (size_t)t;
+  if (w.mfie) {  // the tested field is n x H_inc: replace the amplitude by n x (khat x p) / eta
+    const double* n = g.frame64 + kFrame * (size_t)t;
+    const double hr[3] = {w.pre[0], w.pre[1], w.pre[2]}, hi[3] = {w.pim[0], w.pim[1], w.pim[2]};
+    w.pre[0] = n[1] * hr[2] - n[2] * hr[1];
+    w.pre[1] = n[2] * hr[0] - n[0] * hr[2];
+    w.pre[2] = n[0] * hr[1] - n[1] * hr[0];
+    w.pim[0] = n[1] * hi[2] - n[2] * hi[1];
+    w.pim[1] = n[2] * hi[0] - n[0] * hi[2];
+    w.pim[2] = n[0] * hi[1] - n[1] * hi[0];
+  }
   double er[8], ei[8], ap[8][2], wa[8];  // per point: phase, alpha . p (complex), weight
   for (int a = 0; a < g.m; ++a) {
     const double* pa = g.pts64 + 4 * ((size_t)a * g.nt + t);
@@ -163,9 +174,10 @@ gf_status mesh_ready(gf_mesh* m, int rule, cudaStream_t s) {
 extern "C" {
 
 gf_status gf_excitation(const gf_mesh* mc, double k, const gf_params* p, const double* khat, const double* pol,
-                        int precision, void* V, void* stream) {
+                        int op, int precision, void* V, void* stream) {
   using namespace gf;
   if (!mc || !p || !khat || !pol || !V) return fail(GF_ERR_ARG, "gf_excitation: null argument");
+  if (op != GF_OP_EFIE && op != GF_OP_MFIE) return fail(GF_ERR_ARG, "gf_excitation: bad operator");
   if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_excitation: bad precision");
   if (!(k >= 0) || !std::isfinite(k)) return fail(GF_ERR_ARG, "gf_excitation: need k >= 0");
   const double kn = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
@@ -180,6 +192,16 @@ gf_status gf_excitation(const gf_mesh* mc, double k, const gf_params* p, const d
     w.khat[x] = khat[x];
     w.pre[x] = pol[2 * x];
     w.pim[x] = pol[2 * x + 1];
+  }
+  w.mfie = op == GF_OP_MFIE;
+  if (w.mfie) {  // H_inc amplitude (khat x p) / eta
+    if (!(p->eta > 0)) return fail(GF_ERR_ARG, "gf_excitation: need eta > 0");
+    const double pr[3] = {w.pre[0], w.pre[1], w.pre[2]}, pi[3] = {w.pim[0], w.pim[1], w.pim[2]};
+    for (int x = 0; x < 3; ++x) {
+      const int y = (x + 1) % 3, z = (x + 2) % 3;
+      w.pre[x] = (khat[y] * pr[z] - khat[z] * pr[y]) / p->eta;
+      w.pim[x] = (khat[y] * pi[z] - khat[z] * pi[y]) / p->eta;
+    }
   }
   const size_t esz = precision == GF_FP32 ? 8 : 16;
   GF_CUDA(cudaMemsetAsync(V, 0, (size_t)m->ne * esz, s));

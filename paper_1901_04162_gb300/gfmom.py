@@ -25,7 +25,8 @@ _STATUS = {-1: "GF_ERR_ARG", -2: "GF_ERR_MESH", -3: "GF_ERR_RANGE", -4: "GF_ERR_
 EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info", "gf_mesh_edges",
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
-           "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field"]
+           "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field",
+           "gf_fill_mfie"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -82,7 +83,8 @@ def lib():
         L.gf_batch_config.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
         L.gf_batch_destroy.argtypes = [vp]
         L.gf_fill_backward.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp, vp, vp]
-        L.gf_excitation.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, vp, C.c_int, vp, vp]
+        L.gf_excitation.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, vp, C.c_int, C.c_int, vp, vp]
+        L.gf_fill_mfie.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
         L.gf_far_field.argtypes = [vp, C.c_double, C.POINTER(gf_params), C.c_int, vp, i64, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
@@ -379,16 +381,30 @@ def gf_fill_backward(mesh, k, params, table, gZ, stream=None):
     return dxyz, dk
 
 
-def gf_excitation(mesh, k, params, khat, pol, precision, V, stream=None):
+GF_OP_EFIE, GF_OP_MFIE = 0, 1
+
+
+def gf_excitation(mesh, k, params, khat, pol, precision, V, op=GF_OP_EFIE, stream=None):
     """V: CUDA [ne] complex64 (GF_FP32) or complex128 (GF_FP64), overwritten with
-    <f_m, p e^{-jk khat.r}>; khat a unit 3-vector, pol a complex 3-vector."""
+    <f_m, p e^{-jk khat.r}> (EFIE) or <f_m, n x H_inc> (MFIE); khat a unit
+    3-vector, pol a complex 3-vector."""
     _check_z(V, precision)
     kh = np.ascontiguousarray(khat, dtype=np.float64).reshape(3)
     pc = np.asarray(pol, dtype=np.complex128).reshape(3)
     pl = np.ascontiguousarray(np.stack([pc.real, pc.imag], axis=1), dtype=np.float64)
-    _check(lib().gf_excitation(mesh, float(k), C.byref(params), _ptr(kh), _ptr(pl), int(precision),
+    _check(lib().gf_excitation(mesh, float(k), C.byref(params), _ptr(kh), _ptr(pl), int(op), int(precision),
                                C.c_void_p(V.data_ptr()), _stream_ptr(stream)))
     return V
+
+
+def gf_fill_mfie(mesh, k, params, table, precision, Z, ldz=None, stream=None):
+    """MFIE matrix of a closed, outward-wound surface into Z (CUDA complex64 for
+    GF_FP32, complex128 for GF_FP64, at least [ne, ldz] row-major; overwritten)."""
+    _check_z(Z, precision)
+    ldz = Z.shape[-1] if ldz is None else ldz
+    _check(lib().gf_fill_mfie(mesh, float(k), C.byref(params), table, int(precision), C.c_void_p(Z.data_ptr()),
+                              int(ldz), _stream_ptr(stream)))
+    return Z
 
 
 def gf_far_field(mesh, k, params, precision, I, dirs, stream=None):
@@ -408,16 +424,22 @@ def gf_far_field(mesh, k, params, precision, I, dirs, stream=None):
 
 
 def planewave_rcs(mesh: "Mesh", k, dirs, params=None, table: "Table | None" = None, precision=GF_FP32,
-                  khat=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), stream=None):
-    """EFIE scattering of a plane wave by the PEC surface `mesh`: fill Z (this
-    library), V (gf_excitation), solve Z I = V (a dense LU from the linear
-    algebra library: torch.linalg.solve), then the far field. Returns
-    (sigma [n] float64, I [ne]) CUDA tensors."""
+                  khat=(0.0, 0.0, 1.0), pol=(1.0, 0.0, 0.0), op=GF_OP_EFIE, stream=None):
+    """Scattering of a plane wave by the PEC surface `mesh` (EFIE, or MFIE for a
+    closed outward-wound surface): fill Z (this library), V (gf_excitation),
+    solve Z I = V (a dense LU from the linear algebra library:
+    torch.linalg.solve), then the far field. Returns (sigma [n] float64, I [ne])
+    CUDA tensors."""
     import torch
     params = params or gf_params_default()
-    Z = fill(mesh, k, params, table, precision, stream=stream)
+    if op == GF_OP_MFIE:
+        dt = torch.complex64 if precision == GF_FP32 else torch.complex128
+        Z = torch.empty((mesh.ne, mesh.ne), dtype=dt, device="cuda")
+        gf_fill_mfie(mesh.h, k, params, table.h if table is not None else None, precision, Z, stream=stream)
+    else:
+        Z = fill(mesh, k, params, table, precision, stream=stream)
     V = torch.empty(mesh.ne, dtype=Z.dtype, device=Z.device)
-    gf_excitation(mesh.h, k, params, khat, pol, precision, V, stream=stream)
+    gf_excitation(mesh.h, k, params, khat, pol, precision, V, op=op, stream=stream)
     I = torch.linalg.solve(Z, V)
     del Z
     _, sigma = gf_far_field(mesh.h, k, params, precision, I.contiguous(), dirs, stream=stream)

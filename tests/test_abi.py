@@ -70,11 +70,12 @@ def test_scattering_argument_errors_before_any_device_call():
     kh = np.array([2.0, 0.0, 0.0])
     pol = np.zeros((3, 2))
     v = C.c_void_p(8)
-    assert L.gf_excitation(None, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1
-    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1  # |khat| != 1
+    assert L.gf_excitation(None, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 0, 32, v, None) == -1
+    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 0, 32, v, None) == -1  # |khat| != 1
     kh[0] = 1.0
-    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 7, v, None) == -1
-    assert L.gf_excitation(fake, C.c_double(-1.0), C.byref(p), kh.ctypes.data, pol.ctypes.data, 32, v, None) == -1
+    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 0, 7, v, None) == -1
+    assert L.gf_excitation(fake, C.c_double(-1.0), C.byref(p), kh.ctypes.data, pol.ctypes.data, 0, 32, v, None) == -1
+    assert L.gf_excitation(fake, one, C.byref(p), kh.ctypes.data, pol.ctypes.data, 5, 32, v, None) == -1  # operator
     d = C.c_void_p(16)
     assert L.gf_far_field(fake, one, C.byref(p), 32, v, C.c_int64(-1), d, d, d, None) == -1
     assert L.gf_far_field(fake, one, C.byref(p), 7, v, C.c_int64(3), d, d, d, None) == -1
