@@ -29,7 +29,11 @@ the first term in closed form, the second by Gauss-Legendre. In polar
 coordinates about rho0 the radial integral of Phi rho is exact,
 (1/4 pi)(e^{-jkd}/d - e^{-jkR_e}/R_e), so
     h I_0 = (1/4 pi) sum_e sgn(P0_e) int dphi (sgn(h) e^{-jkd} - h e^{-jkR_e}/R_e)
-with the angle of each edge integrated as in the EFIE scheme (u = asinh(tan phi)).
+          = -Omega / (4 pi) + (1/4 pi) sum_e sgn(P0_e) int dphi
+              (sgn(h)(e^{-jkd} - 1) - h (e^{-jkR_e} - 1)/R_e),
+Omega the solid angle of q seen from r (closed form, `solid_angle`), the
+smooth remainder with the angle of each edge integrated as in the EFIE scheme
+(u = asinh(tan phi)).
 For the self pair h = 0 exactly (the principal value; the jump is the 1/2 J
 term) and T_j is normal to q, so the self pair's K part vanishes.
 """
@@ -96,8 +100,24 @@ def inner_T(r, q, F, k, nphi=8, nl=8, self_pair=False):
     return T
 
 
-def inner_parts(r, q, F, k, nphi=8, nl=8, self_pair=False):
-    """(h, rho0, I_u, h I_0) of the source triangle q for the point r."""
+def solid_angle(r, v):
+    """Signed solid angle of the triangle v seen from r, closed form of Van
+    Oosterom & Strackee (IEEE Trans. Biomed. Eng. 30 (1983) 125):
+    tan(Omega / 2) = R1.(R2 x R3) / (R1 R2 R3 + (R1.R2) R3 + (R1.R3) R2 + (R2.R3) R1),
+    R_i = v_i - r."""
+    R = np.asarray(v, dtype=np.float64) - r
+    n = np.linalg.norm(R, axis=1)
+    num = R[0] @ np.cross(R[1], R[2])
+    den = n[0] * n[1] * n[2] + (R[0] @ R[1]) * n[2] + (R[0] @ R[2]) * n[1] + (R[1] @ R[2]) * n[0]
+    return 2 * math.atan2(num, den)
+
+
+def inner_parts(r, q, F, k, nphi=8, nl=8, self_pair=False, static="closed"):
+    """(h, rho0, I_u, h I_0) of the source triangle q for the point r. The
+    static part of h I_0, sum_e sgn(P0) int dphi (sgn(h) - h / R_e), is the
+    solid angle -Omega / (4 pi) (static="closed", the closed form) or is
+    integrated with the angles (static="quadrature"); the remainder
+    sgn(h)(e^{-jkd} - 1) - h (e^{-jkR_e} - 1) / R_e always is."""
     v, n, area, c, t, length, m = F
     vq, nq = v[q], n[q]
     h = 0.0 if self_pair else float(nq @ (r - vq[0]))
@@ -136,8 +156,12 @@ def inner_parts(r, q, F, k, nphi=8, nl=8, self_pair=False):
             u = 0.5 * (up + um) + 0.5 * (up - um) * xphi
             ch = np.cosh(u)
             Re = np.sqrt((aP * ch) ** 2 + d * d)
-            f = sgn_h * np.exp(-1j * k * d) - h * np.exp(-1j * k * Re) / Re
+            f = sgn_h * (np.exp(-1j * k * d) - 1.0) - h * (np.exp(-1j * k * Re) - 1.0) / Re
+            if static == "quadrature":
+                f = f + sgn_h - h / Re
             hI0 += math.copysign(1.0, P0) * 0.5 * (up - um) * np.sum(wphi * f / ch) / FOUR_PI
+    if static == "closed" and h != 0.0:
+        hI0 += -solid_angle(r, vq) / FOUR_PI
     return h, rho0, Iu, hI0
 
 

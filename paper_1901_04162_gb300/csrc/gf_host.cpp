@@ -1329,8 +1329,8 @@ gf_status gf_fill_mfie(const gf_mesh* mc, double k, const gf_params* p, const gf
     gll[i] = gx_l[i];
     gll[32 + i] = gw_l[i];
   }
-  GF_CUDA(launch_fill_mfie(g, table ? &tg : nullptr, table ? &te : nullptr, precision, k, p->nphi, p->nl, glp, gll, Z,
-                           ldz, s));
+  GF_CUDA(launch_fill_mfie(g, table ? &tg : nullptr, table ? &te : nullptr, precision,
+                           precision == GF_FP32 && !p->near_fp64, k, p->nphi, p->nl, glp, gll, Z, ldz, s));
   return GF_OK;
 }
 

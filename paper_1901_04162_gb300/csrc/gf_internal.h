@@ -171,8 +171,8 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 // bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
-cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, double k,
-                             int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
+cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, bool mixed,
+                             double k, int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
                              cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
                          cudaStream_t s);

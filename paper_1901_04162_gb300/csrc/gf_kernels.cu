@@ -1762,9 +1762,19 @@ __global__ void k_mfie_identity(GeoView g, Out* Z, int64_t ldz) {
 // (exact radial integral of Phi rho); h = 0 for the self pair (principal value).
 // One near pair per group of G lanes, lane = test point; the 3x3 block is
 // reduce-scattered over the group.
-template <class Out, int G>
+// The static part of h I_0 is the solid angle, -Omega / (4 pi), in closed form
+// (Van Oosterom & Strackee, IEEE Trans. Biomed. Eng. 30 (1983) 125:
+// tan(Omega / 2) = R1.(R2 x R3) / (R1 R2 R3 + (R1.R2) R3 + (R1.R3) R2 +
+// (R2.R3) R1), R_i = v_i - r); the angles carry only the smooth remainder.
+// MIXED (FP32 fills): the geometry, the closed-form static parts and the
+// assembly in FP64; the remainders e^{-jkR} - 1 on the edge lines and in the
+// angle integrals sampled in FP32 (the FP32 Exp table), as for the EFIE near
+// pairs.
+template <class Out, int G, bool MIXED>
 __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
                                                    int64_t ldz) {
+  const Tab32 te32 = tab32(te);
+  const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi, kpi = (float)(A.k / kPi);
   const int64_t n_near = g.near_ptr[g.nt];
   const int sub = threadIdx.x & (G - 1);
   const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
@@ -1808,37 +1818,95 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
         else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
         else ratio = (Rm - lm) / (Rp - lp);
         double lr = log(ratio), li = 0.0;
-        for (int i = 0; i < A.nl; ++i) {
-          const double s = 0.5 * le * (A.gx_l[i] + 1.0);
-          const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
-          const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
-          const C2 eR = exp_mjkr(k, R, &te, use_table);
-          const double w = 0.5 * le * A.gw_l[i] / R;
-          lr += (eR.re - 1.0) * w;
-          li += eR.im * w;
+        if (MIXED) {
+          const float* f32 = g.frame32 + kFrame32 * (size_t)q;
+          const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+          const float tx = f32[3 + 3 * e], ty = f32[4 + 3 * e], tz = f32[5 + 3 * e], hl = 0.5f * f32[e];
+          float sr = 0.f, si = 0.f;
+          for (int i = 0; i < A.nl; ++i) {
+            const float sp = hl * (A.fx_l[i] + 1.0f);
+            const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+            const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+            const float2 eR = exp32(kpi, R, te32, use_table, lo32, hi32);
+            const float w = A.fw_l[i] * __frcp_rn(R);
+            sr = fmaf(eR.x - 1.0f, w, sr);
+            si = fmaf(eR.y, w, si);
+          }
+          lr += (double)(sr * hl);
+          li += (double)(si * hl);
+        } else {
+          for (int i = 0; i < A.nl; ++i) {
+            const double s = 0.5 * le * (A.gx_l[i] + 1.0);
+            const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
+            const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+            const C2 eR = exp_mjkr(k, R, &te, use_table);
+            const double w = 0.5 * le * A.gw_l[i] / R;
+            lr += (eR.re - 1.0) * w;
+            li += eR.im * w;
+          }
         }
         for (int x = 0; x < 3; ++x) {
           Iu[x][0] -= m[x] * lr * c4;
           Iu[x][1] -= m[x] * li * c4;
         }
-        if (fabs(P0) > 1e-12 * le) {
+        if (fabs(P0) > 1e-12 * le && h != 0.0) {
           const double aP = fabs(P0);
-          const double um = asinh(lm / aP), up = asinh(lp / aP);
-          const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
-          double sr = 0, si = 0;
-          for (int i = 0; i < A.nphi; ++i) {
-            const double u = mid + half * A.gx_phi[i];
-            const double ch = cosh(u);
-            const double Re = sqrt(aP * aP * ch * ch + d * d);
-            const C2 eR = exp_mjkr(k, Re, &te, use_table);
-            const double w = A.gw_phi[i] / ch;
-            sr += (sgh * ed.re - h * eR.re / Re) * w;
-            si += (sgh * ed.im - h * eR.im / Re) * w;
+          if (MIXED) {  // the remainder sgn(h)(e^{-jkd} - 1) - h (e^{-jkR_e} - 1)/R_e; the static part below
+            const float aP32 = (float)aP, d32 = (float)d, h32 = (float)h, sg32 = (float)sgh;
+            const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
+            const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
+            const float2 ed32 = exp32(kpi, d32, te32, use_table, lo32, hi32);
+            const float er0 = sg32 * (ed32.x - 1.0f), ei0 = sg32 * ed32.y;
+            float sr = 0.f, si = 0.f;
+            for (int i = 0; i < A.nphi; ++i) {
+              const float u = fmaf(half, A.fx_phi[i], mid);
+              const float E = expf(u);
+              const float ch = 0.5f * (E + __frcp_rn(E));
+              const float rho = aP32 * ch;
+              const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+              const float2 eR = exp32(kpi, Re, te32, use_table, lo32, hi32);
+              const float w = A.fw_phi[i] * __frcp_rn(ch), hr = h32 * __frcp_rn(Re);
+              sr = fmaf(fmaf(-hr, eR.x - 1.0f, er0), w, sr);
+              si = fmaf(fmaf(-hr, eR.y, ei0), w, si);
+            }
+            const double sg = P0 > 0 ? (double)half * c4 : -(double)half * c4;
+            hI0[0] += (double)sr * sg;
+            hI0[1] += (double)si * sg;
+          } else {
+            const double um = asinh(lm / aP), up = asinh(lp / aP);
+            const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
+            double sr = 0, si = 0;
+            for (int i = 0; i < A.nphi; ++i) {
+              const double u = mid + half * A.gx_phi[i];
+              const double ch = cosh(u);
+              const double Re = sqrt(aP * aP * ch * ch + d * d);
+              const C2 eR = exp_mjkr(k, Re, &te, use_table);
+              const double w = A.gw_phi[i] / ch;
+              sr += (sgh * (ed.re - 1.0) - h * (eR.re - 1.0) / Re) * w;
+              si += (sgh * ed.im - h * eR.im / Re) * w;
+            }
+            const double sg = P0 > 0 ? half * c4 : -half * c4;
+            hI0[0] += sr * sg;
+            hI0[1] += si * sg;
           }
-          const double sg = P0 > 0 ? half * c4 : -half * c4;
-          hI0[0] += sr * sg;
-          hI0[1] += si * sg;
         }
+      }
+      if (h != 0.0) {  // static part of h I_0: -Omega / (4 pi)
+        double R1[3], R2[3], R3[3];
+        for (int x = 0; x < 3; ++x) {
+          R1[x] = v[x] - r[x];
+          R2[x] = v[3 + x] - r[x];
+          R3[x] = v[6 + x] - r[x];
+        }
+        const double n1 = sqrt(R1[0] * R1[0] + R1[1] * R1[1] + R1[2] * R1[2]);
+        const double n2 = sqrt(R2[0] * R2[0] + R2[1] * R2[1] + R2[2] * R2[2]);
+        const double n3 = sqrt(R3[0] * R3[0] + R3[1] * R3[1] + R3[2] * R3[2]);
+        const double num = R1[0] * (R2[1] * R3[2] - R2[2] * R3[1]) + R1[1] * (R2[2] * R3[0] - R2[0] * R3[2]) +
+                           R1[2] * (R2[0] * R3[1] - R2[1] * R3[0]);
+        const double den = n1 * n2 * n3 + (R1[0] * R2[0] + R1[1] * R2[1] + R1[2] * R2[2]) * n3 +
+                           (R1[0] * R3[0] + R1[1] * R3[1] + R1[2] * R3[2]) * n2 +
+                           (R2[0] * R3[0] + R2[1] * R3[1] + R2[2] * R3[2]) * n1;
+        hI0[0] -= 2.0 * atan2(num, den) * c4;
       }
       // n x I_u
       double nIu[3][2];
@@ -3462,8 +3530,8 @@ cudaError_t launch_mfie32(const GeoView& g, const TabView* table, float kpi, flo
   return launch_mfie32_table<M, false>(*table, g, kpi, k32, scale, Z, ldz, s);
 }
 
-cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, double k,
-                             int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
+cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, bool mixed,
+                             double k, int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
                              cudaStream_t s) {
   const unsigned tb = (unsigned)((g.nt + 127) / 128);
   if (precision == GF_FP64) k_mfie_identity<double2><<<tb, 128, 0, s>>>(g, (double2*)Z, ldz);
@@ -3513,11 +3581,13 @@ cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabVi
   const bool use_table = texp != nullptr;
   const unsigned nblk = (unsigned)(sm_count() * 16);
   if (g.m <= 4) {
-    if (precision == GF_FP64) k_mfie_near<double2, 4><<<nblk, 128, 0, s>>>(g, te, use_table, A, (double2*)Z, ldz);
-    else k_mfie_near<float2, 4><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
+    if (precision == GF_FP64) k_mfie_near<double2, 4, false><<<nblk, 128, 0, s>>>(g, te, use_table, A, (double2*)Z, ldz);
+    else if (mixed) k_mfie_near<float2, 4, true><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
+    else k_mfie_near<float2, 4, false><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
   } else {
-    if (precision == GF_FP64) k_mfie_near<double2, 8><<<nblk, 128, 0, s>>>(g, te, use_table, A, (double2*)Z, ldz);
-    else k_mfie_near<float2, 8><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
+    if (precision == GF_FP64) k_mfie_near<double2, 8, false><<<nblk, 128, 0, s>>>(g, te, use_table, A, (double2*)Z, ldz);
+    else if (mixed) k_mfie_near<float2, 8, true><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
+    else k_mfie_near<float2, 8, false><<<nblk, 128, 0, s>>>(g, te, use_table, A, (float2*)Z, ldz);
   }
   return cudaGetLastError();
 }

@@ -51,13 +51,17 @@ def test_static_parts_solid_angle_and_gradient_integral(r):
     xyz, tri = _tri()
     F = mfie.frames(xyz, tri)
     r = np.asarray(r)
-    # h I_0 at k -> 0 is the solid angle of q seen from r over 4 pi, int_q h / R^3 dS';
-    # with R_i = v_i - r the closed form's sign is opposite to h's convention here
-    om = _solid_angle(r, xyz)
-    _, _, _, hI0_32 = mfie.inner_parts(r, 0, F, 1e-9, nphi=32)
-    assert abs(hI0_32.real + om / (4 * math.pi)) < 1e-13
-    h, rho0, Iu, hI0 = mfie.inner_parts(r, 0, F, 1e-9)  # default 8-point angles
-    assert abs(hI0.real + om / (4 * math.pi)) < 1e-6
+    # h I_0 at k -> 0 is -Omega / (4 pi), Omega = int_q h / R^3 dS' the solid angle:
+    # the closed form used by the scheme against the angle integral of the static
+    # integrand (sgn(h) - h / R_e), converged, and at the default 8 angles
+    om = mfie.solid_angle(r, xyz)
+    assert abs(om - _solid_angle(r, xyz)) < 1e-15
+    _, _, _, q32 = mfie.inner_parts(r, 0, F, 1e-9, nphi=32, static="quadrature")
+    assert abs(q32.real + om / (4 * math.pi)) < 1e-13
+    _, _, _, q8 = mfie.inner_parts(r, 0, F, 1e-9, static="quadrature")
+    assert abs(q8.real + om / (4 * math.pi)) < 1e-6
+    h, rho0, Iu, hI0 = mfie.inner_parts(r, 0, F, 1e-9)
+    assert abs(hI0.real + om / (4 * math.pi)) < 1e-15
     # I_u at k -> 0: int_q (r' - rho0) / (4 pi R^3) dS' by a dense rule (the line
     # integrals are exact there; the tolerance is the dense rule's own error for
     # the point 0.004 off the plane)
