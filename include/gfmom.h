@@ -196,6 +196,32 @@ gf_status gf_fill_backward(const gf_mesh* m, double k, const gf_params* p, const
                            int precision, const void* gZ, int64_t ldg, double* dxyz, double* dk,
                            void* stream);
 
+/* ---------------------------------------------------------------- near field
+ * Z restricted to a sparsity pattern: the near-field matrix a fast solver
+ * keeps (the paper's "3mnNC" count, Section II.A, for the regime of large N).
+ * The pattern holds the RWG pairs (m, n) with some triangle of m and some
+ * triangle of n whose centroids are closer than `radius`; its values are the
+ * full Z_mn of gf_fill (all four triangle pairs), so on the pattern they equal
+ * the dense fill's entries.
+ *
+ * gf_sparse_create: builds the pattern (host) and the work list of triangle
+ * pairs; `m` must outlive the handle. GF_ERR_ARG for radius <= 0.
+ * gf_sparse_info: nnz of the pattern and the number of regular triangle pairs
+ * evaluated by a fill. gf_sparse_pattern: the CSR pattern on the host
+ * (row_ptr [ne + 1] int64, cols [nnz] int32 sorted per row; either may be NULL).
+ * gf_fill_sparse: vals (device complex64 [nnz], pattern order) overwritten
+ * with Z_mn; FP32 only (GF_ERR_ARG otherwise), the same kernels and options as
+ * gf_fill (Green table for regular pairs, Exp table and p->near_fp64 for near
+ * pairs; table == NULL: direct). Asynchronous on `stream`.
+ * gf_sparse_destroy: synchronizes the device, frees the handle. */
+typedef struct gf_sparse gf_sparse;
+gf_status gf_sparse_create(const gf_mesh* m, double radius, gf_sparse** out);
+gf_status gf_sparse_info(const gf_sparse* s, int64_t* nnz, int64_t* n_pairs);
+gf_status gf_sparse_pattern(const gf_sparse* s, int64_t* row_ptr, int32_t* cols);
+gf_status gf_fill_sparse(const gf_sparse* s, double k, const gf_params* p, const gf_table* table, int precision,
+                         void* vals_dev, void* stream);
+gf_status gf_sparse_destroy(gf_sparse* s);
+
 /* ---------------------------------------------------------------- MFIE -----
  * The magnetic-field integral equation matrix (the paper's second formulation,
  * Section IV.B: its K operator uses the gradient of the same Green function,

@@ -174,6 +174,14 @@ cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const v
 cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, bool mixed,
                              double k, int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
                              cudaStream_t s);
+// Near-field sparse fill (FP32): tasks = SparseTask records {int p, int n, int64 off}
+// (sparse_task_bytes() each), widx the work list of source triangles, the CSR
+// pattern (row_ptr [ne + 1], cols) and its complex64 values.
+cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, bool mixed, double k,
+                               double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
+                               const void* tasks, int64_t ntask, const int32_t* widx, const int64_t* row_ptr,
+                               const int32_t* cols, void* vals, cudaStream_t s);
+int sparse_task_bytes();
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
                          cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}

@@ -828,6 +828,52 @@ enum GreenMode : int {
 // DEFER: lookups in the hot loop are branch-free and the rare evaluations in
 // lattice cells holding samples are corrected after it (tables with few such
 // cells); otherwise each lookup branches to the exact path at once.
+// Where the regular fill's 3x3 blocks go. DenseSym: Z[m][n] and Z[n][m] (one
+// evaluation per unordered pair); CsrSink (near-field sparse fill): Z[m][n] at
+// its position in the CSR pattern, dropped where (m, n) is not in it.
+struct DenseSym {
+  float2* Z;
+  int64_t ldz;
+  __device__ __forceinline__ void operator()(int m, int n, float2 v) const {
+    atomicAdd(Z + (int64_t)m * ldz + n, v);
+    atomicAdd(Z + (int64_t)n * ldz + m, v);
+  }
+};
+
+template <class T>
+struct CsrSink {
+  const int64_t* row_ptr;  // [ne + 1]
+  const int32_t* cols;     // sorted per row
+  T* vals;
+  __device__ __forceinline__ int64_t find(int m, int n) const {
+    int64_t lo = row_ptr[m], hi = row_ptr[m + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cols[mid] < n) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo < row_ptr[m + 1] && cols[lo] == n ? lo : -1;
+  }
+  __device__ __forceinline__ void operator()(int m, int n, float2 v) const {
+    const int64_t i = find(m, n);
+    if (i >= 0) atomicAdd(reinterpret_cast<float2*>(vals + i), v);
+  }
+  __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
+    const int64_t i = find(m, n);
+    if (i < 0) return;
+    if constexpr (sizeof(T) == 8) {
+      atomicAdd(reinterpret_cast<float2*>(vals + i), make_float2((float)zr, (float)zi));
+    } else {
+      atomicAdd(reinterpret_cast<double*>(vals + i), zr);
+      atomicAdd(reinterpret_cast<double*>(vals + i) + 1, zi);
+    }
+  }
+};
+
+template <int M, int MODE, bool DEFER = true, class Sink = DenseSym>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               int p, int q, bool ok, const Sink& sink);
+
 template <int M, int MODE, bool DEFER = true>
 __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
                                                float2* Z, int64_t ldz, int p, int q0, int lane) {
@@ -835,6 +881,16 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
   const float4 cp = g.cen32[p], cq = g.cen32[q];
   const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
   const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, p, q, ok, DenseSym{Z, ldz});
+}
+
+// The 3x3 block of regular pair (p, q) (q per lane; lanes with ok == false
+// take part in the warp's work but write nothing), handed to `sink`.
+template <int M, int MODE, bool DEFER, class Sink>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               int p, int q, bool ok, const Sink& sink) {
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
   if (!__any_sync(0xffffffffu, ok)) return;
   float4 beta[M];
 #pragma unroll
@@ -948,7 +1004,6 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
     const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
     const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
     const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
-    float2* zrow = Z + (int64_t)edge_of(ecp[i]) * ldz;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       if (!edge_valid(ecq[j])) continue;
@@ -959,10 +1014,8 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
       const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
       const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
       const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
-      // j * c * (br + j bi) = c * (-bi + j br), into Z[m][n] and Z[n][m]
-      const float2 v = make_float2(-c * bi, c * br);
-      atomicAdd(zrow + edge_of(ecq[j]), v);
-      atomicAdd(Z + (int64_t)edge_of(ecq[j]) * ldz + edge_of(ecp[i]), v);
+      // j * c * (br + j bi) = c * (-bi + j br)
+      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bi, c * br));
     }
   }
 }
@@ -1342,11 +1395,40 @@ __device__ __forceinline__ void rs_halve(const C2 (&in)[N], C2 (&out)[(N + 1) / 
 // lanes >= m idle); every lane of the group must call (valid_pair is uniform
 // over the group). The 3 x 3 block is reduce-scattered over the group and
 // each lane adds its entries to Z.
+template <class Out>
+struct DenseOut {  // Z[m][n] += z (row-major, ld = ldz)
+  Out* Z;
+  int64_t ldz;
+  __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
+    Out* z = Z + (int64_t)m * ldz + n;
+    if constexpr (sizeof(Out) == 8) {
+      atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
+    } else {
+      atomicAdd(reinterpret_cast<double*>(z), zr);
+      atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
+    }
+  }
+};
+
+template <bool MIXED, int G, class Sink>
+__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
+                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask);
+
 template <class Out, bool MIXED, int G = 8>
 __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
                                           float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
                                           int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
                                           unsigned gmask) {
+  near_pair<MIXED, G>(g, te, te32, lo32, hi32, use_table, A, ks, DenseOut<Out>{Z, ldz}, idx, valid_pair, sub, gmask);
+}
+
+// The 3x3 block of near pair idx (of the mesh's near list) on a group of G
+// lanes, handed to `sink` (sink.add(m, n, re, im)).
+template <bool MIXED, int G, class Sink>
+__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
+                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask) {
   if (!valid_pair) return;
   const int p = g.near_row[idx], q = g.near_idx[idx];
   C2 acc[9];
@@ -1424,14 +1506,7 @@ __device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, c
     if (!edge_valid(ci) || !edge_valid(cj)) continue;
     const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
     const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
-    const double zr = -c * fin[u].im, zi = c * fin[u].re;
-    Out* z = Z + (int64_t)edge_of(ci) * ldz + edge_of(cj);
-    if constexpr (sizeof(Out) == 8) {
-      atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
-    } else {
-      atomicAdd(reinterpret_cast<double*>(z), zr);
-      atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
-    }
+    sink.add(edge_of(ci), edge_of(cj), -c * fin[u].im, c * fin[u].re);
   }
 }
 
@@ -1974,6 +2049,70 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
         atomicAdd(reinterpret_cast<double*>(z) + 1, c * fin[u].im);
       }
     }
+  }
+}
+
+// ---------------------------------------------------------------- near-field sparse fill
+// Z restricted to a sparsity pattern (the near field of fast solvers, the
+// paper's "3mnNC" regime): the same pair computations, each block handed to a
+// CsrSink that keeps the entries of the pattern. Regular pairs come from a
+// work list of (test triangle, up to 32 source triangles) tasks; every ordered
+// pair is listed (no symmetric second write).
+struct SparseTask {
+  int p;         // internal test triangle
+  int n;         // source triangles in this task (1..32)
+  int64_t off;   // first source triangle in the work list
+};
+
+template <int M, int MODE, bool SMEM, bool DEFER>
+__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_sparse_regular32(GeoView g, TabView tv, float kpi,
+                                                                            float scale, float inv_k2,
+                                                                            const SparseTask* __restrict__ tasks,
+                                                                            int64_t ntask, const int32_t* __restrict__ widx,
+                                                                            CsrSink<float2> sink) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  Tab32 T = tab32(tv);
+  if (MODE != kDirect && SMEM) {
+    const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
+    float4* sa = reinterpret_cast<float4*>(smem);
+    float4* sb = sa + nl;
+    float4* sblob = sb + nl;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
+      sa[i] = tv.lat_a[i];
+      sb[i] = tv.lat_b[i];
+    }
+    for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
+    __syncthreads();
+    T.la = sa;
+    T.lb = sb;
+    tab32_blob(T, tv, sblob);
+  }
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarp) {
+    const SparseTask tk = tasks[t];
+    const bool ok = lane < tk.n;
+    const int q = ok ? widx[tk.off + lane] : tk.p;
+    regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, tk.p, q, ok, sink);
+  }
+}
+
+// Near pairs of the mesh's near list into the pattern.
+template <bool MIXED, int G>
+__global__ void __launch_bounds__(128) k_sparse_near(GeoView g, TabView te, bool use_table, NearArgs A,
+                                                     CsrSink<float2> sink) {
+  const Tab32 te32 = tab32(te);
+  const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
+  const int64_t n_near = g.near_ptr[g.nt];
+  const int sub = threadIdx.x & (G - 1);
+  const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
+  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
+  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int64_t iters = (n_near + ngroups - 1) / ngroups;
+  for (int64_t it = 0; it < iters; ++it) {
+    const int64_t idx = g0 + it * ngroups;
+    near_pair<MIXED, G>(g, te, te32, lo32, hi32, use_table, A, KScal{A.k, A.scale, A.inv_k2, 1.0 / A.k}, sink, idx,
+                        idx < n_near, sub, gmask);
   }
 }
 
@@ -3591,6 +3730,88 @@ cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabVi
   }
   return cudaGetLastError();
 }
+
+template <int M>
+cudaError_t launch_sparse32(const GeoView& g, const TabView* table, float kpi, float scale, float inv_k2,
+                            const SparseTask* tasks, int64_t ntask, const int32_t* widx, CsrSink<float2> sink,
+                            cudaStream_t s) {
+  if (ntask == 0) return cudaSuccess;
+  if (!table) {
+    TabView tv{};
+    const int64_t blocks = std::min<int64_t>((ntask + kWarps - 1) / kWarps, (int64_t)sm_count() * 4);
+    k_sparse_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2,
+                                                                                      tasks, ntask, widx, sink);
+    return cudaGetLastError();
+  }
+  const TabView& tv = *table;
+  const size_t smem = tv.smem32_bytes(3);
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem <= (size_t)max_optin) {
+    auto kern = tv.n_busy * 200 <= tv.n_lat ? k_sparse_regular32<M, kLagrange, true, true>
+                                            : k_sparse_regular32<M, kLagrange, true, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>((ntask + 15) / 16, (int64_t)sm_count());
+    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, tasks, ntask, widx, sink);
+  } else {
+    const int64_t blocks = std::min<int64_t>((ntask + kWarps - 1) / kWarps, (int64_t)sm_count() * 4);
+    k_sparse_regular32<M, kLagrange, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2,
+                                                                                        tasks, ntask, widx, sink);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, bool mixed, double k,
+                               double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
+                               const void* tasks_v, int64_t ntask, const int32_t* widx, const int64_t* row_ptr,
+                               const int32_t* cols, void* vals, cudaStream_t s) {
+  const SparseTask* tasks = static_cast<const SparseTask*>(tasks_v);
+  CsrSink<float2> sink{row_ptr, cols, static_cast<float2*>(vals)};
+  const double scale = k * eta / (4.0 * kPi);
+  const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
+  cudaError_t e;
+  switch (g.m) {
+    case 1: e = launch_sparse32<1>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    case 3: e = launch_sparse32<3>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    case 4: e = launch_sparse32<4>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    case 6: e = launch_sparse32<6>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    case 7: e = launch_sparse32<7>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  NearArgs A;
+  A.k = k;
+  A.scale = k * eta;
+  A.inv_k2 = 1.0 / (k * k);
+  A.nphi = nphi;
+  A.nl = nl;
+  for (int i = 0; i < 32; ++i) {
+    A.gx_phi[i] = gl_phi[i];
+    A.gw_phi[i] = gl_phi[32 + i];
+    A.gx_l[i] = gl_l[i];
+    A.gw_l[i] = gl_l[32 + i];
+    A.fx_phi[i] = (float)A.gx_phi[i];
+    A.fw_phi[i] = (float)A.gw_phi[i];
+    A.fx_l[i] = (float)A.gx_l[i];
+    A.fw_l[i] = (float)A.gw_l[i];
+  }
+  TabView te{};
+  if (texp) te = *texp;
+  const bool use_table = texp != nullptr;
+  const unsigned nblk = (unsigned)(sm_count() * 16);
+  if (g.m <= 4) {
+    if (mixed) k_sparse_near<true, 4><<<nblk, 128, 0, s>>>(g, te, use_table, A, sink);
+    else k_sparse_near<false, 4><<<nblk, 128, 0, s>>>(g, te, use_table, A, sink);
+  } else {
+    if (mixed) k_sparse_near<true, 8><<<nblk, 128, 0, s>>>(g, te, use_table, A, sink);
+    else k_sparse_near<false, 8><<<nblk, 128, 0, s>>>(g, te, use_table, A, sink);
+  }
+  return cudaGetLastError();
+}
+
+int sparse_task_bytes() { return (int)sizeof(SparseTask); }
 
 cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k, double eta,
                              int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,

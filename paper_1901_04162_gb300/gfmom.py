@@ -26,7 +26,8 @@ EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info
            "gf_mesh_set_vertices", "gf_mesh_destroy", "gf_range", "gf_table_create", "gf_table_info",
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
            "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field",
-           "gf_fill_mfie"]
+           "gf_fill_mfie", "gf_sparse_create", "gf_sparse_info", "gf_sparse_pattern", "gf_fill_sparse",
+           "gf_sparse_destroy"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -85,6 +86,11 @@ def lib():
         L.gf_fill_backward.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp, vp, vp]
         L.gf_excitation.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, vp, C.c_int, C.c_int, vp, vp]
         L.gf_fill_mfie.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
+        L.gf_sparse_create.argtypes = [vp, C.c_double, C.POINTER(vp)]
+        L.gf_sparse_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+        L.gf_sparse_pattern.argtypes = [vp, vp, vp]
+        L.gf_fill_sparse.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, vp]
+        L.gf_sparse_destroy.argtypes = [vp]
         L.gf_far_field.argtypes = [vp, C.c_double, C.POINTER(gf_params), C.c_int, vp, i64, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
@@ -444,6 +450,43 @@ def planewave_rcs(mesh: "Mesh", k, dirs, params=None, table: "Table | None" = No
     del Z
     _, sigma = gf_far_field(mesh.h, k, params, precision, I.contiguous(), dirs, stream=stream)
     return sigma, I
+
+
+class Sparse:
+    """Owns a gf_sparse handle: the near-field pattern of `mesh` for `radius`
+    (the mesh must outlive it)."""
+
+    def __init__(self, mesh: "Mesh", radius):
+        self.mesh = mesh
+        h = C.c_void_p()
+        _check(lib().gf_sparse_create(mesh.h, float(radius), C.byref(h)))
+        self.h = h
+        nnz, npairs = C.c_int64(), C.c_int64()
+        _check(lib().gf_sparse_info(h, C.byref(nnz), C.byref(npairs)))
+        self.nnz, self.n_pairs = nnz.value, npairs.value
+
+    def pattern(self):
+        row_ptr = np.zeros(self.mesh.ne + 1, dtype=np.int64)
+        cols = np.zeros(max(self.nnz, 1), dtype=np.int32)
+        _check(lib().gf_sparse_pattern(self.h, _ptr(row_ptr), _ptr(cols)))
+        return row_ptr, cols[:self.nnz]
+
+    def fill(self, k, params=None, table: "Table | None" = None, vals=None, stream=None):
+        """Returns vals (CUDA complex64 [nnz]) with Z_mn on the pattern."""
+        import torch
+        params = params or gf_params_default()
+        if vals is None:
+            vals = torch.empty(max(self.nnz, 1), dtype=torch.complex64, device="cuda")
+        _check_z(vals, GF_FP32)
+        _check(lib().gf_fill_sparse(self.h, float(k), C.byref(params), table.h if table is not None else None,
+                                    GF_FP32, C.c_void_p(vals.data_ptr()), _stream_ptr(stream)))
+        return vals
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().gf_sparse_destroy(h)
+            self.h = None
 
 
 def _efie_function():
