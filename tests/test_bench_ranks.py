@@ -66,7 +66,7 @@ def test_reference_arm_runs_on_rank0_only():
                           "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     assert out.stdout.strip() == ""
-    for wl in ("ellipsoid_batch", "adjoint_3072"):  # single-mesh arm only: one line, rank 0
+    for wl in ("ellipsoid_batch", "adjoint_3072", "cube_near_field"):  # single-mesh arm only: one line
         out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", wl],
                              capture_output=True, text=True, timeout=300)
         assert out.returncode == 0
