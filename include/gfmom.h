@@ -139,6 +139,16 @@ gf_status gf_range(const gf_mesh* m, int rule, int precision, double* r_min, dou
 gf_status gf_table_create(double k, double r_min, double r_max, const gf_params* p, void* stream,
                           gf_table** out);
 
+/* The same tables in u = kR, for frequency sweeps: one table serves every
+ * wavenumber k with [k r_min, k r_max] inside [u_min, u_max] (e^{-jkR} =
+ * e^{-ju}, e^{-jkR}/R = k e^{-ju}/u; the tables are those of gf_table_create
+ * with k = 1 over [u_min, u_max]). The fills (gf_fill, gf_fill_parts,
+ * gf_fill_mfie, gf_fill_sparse, gf_batch_create) read it at x = kR for their
+ * own k; the caller keeps [k r_min, k r_max] of each mesh inside [u_min,
+ * u_max]. gf_fill_backward rejects it (GF_ERR_ARG). Errors as above. This is a
+ * variant of the method, not in the paper. */
+gf_status gf_table_create_kr(double u_min, double u_max, const gf_params* p, void* stream, gf_table** out);
+
 /* kind = GF_GREEN or GF_EXP: number of samples, hash cells, hash cell width
  * (= smallest sample spacing); any output may be NULL. */
 gf_status gf_table_info(const gf_table* t, int kind, int64_t* n_nodes, int64_t* n_hash, double* dr);

@@ -224,20 +224,19 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
     gf_mesh* m = const_cast<gf_mesh*>(meshes[i]);
     if (!m || !Z[i] || !(k[i] > 0) || ldz[i] < m->ne) return fail(GF_ERR_ARG, "gf_batch_create: bad mesh entry");
     if (m->device != b->device) return fail(GF_ERR_DEVICE, "gf_batch_create: mesh on another device");
-    if (tables && (!tables[i] || tables[i]->device != b->device || tables[i]->k != k[i]))
-      return fail(GF_ERR_ARG, "gf_batch_create: table missing, on another device or for another k");
+    if (tables && (!tables[i] || tables[i]->device != b->device))
+      return fail(GF_ERR_ARG, "gf_batch_create: table missing or on another device");
     gf_status st = prepare_rule(m, p->rule, s);
     if (st) return st;
     BatchItem& it = items[i];
     std::memset(&it, 0, sizeof it);
     it.g = geo_view(m);
-    if (tables) {
-      it.green = tables[i]->green.view();
-      it.exp = tables[i]->exp.view();
-    }
+    double gscale = 1.0;
+    if (tables && !table_views(tables[i], k[i], &it.green, &it.exp, &gscale))
+      return fail(GF_ERR_ARG, "gf_batch_create: table built for another k");
     it.use_table = tables ? 1 : 0;
     it.kpi = (float)(k[i] / kPi);
-    it.scale32 = (float)(k[i] * p->eta / (4.0 * kPi));
+    it.scale32 = (float)(k[i] * p->eta / (4.0 * kPi) * gscale);
     it.inv_k2_32 = (float)(1.0 / (k[i] * k[i]));
     it.k = k[i];
     it.scale = k[i] * p->eta;

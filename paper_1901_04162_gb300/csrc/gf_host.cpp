@@ -1189,6 +1189,13 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
   return GF_OK;
 }
 
+gf_status gf_table_create_kr(double u_min, double u_max, const gf_params* p, void* stream, gf_table** out) {
+  gf_status st = gf_table_create(1.0, u_min, u_max, p, stream, out);
+  if (st) return st;
+  (*out)->kr = true;
+  return GF_OK;
+}
+
 gf_status gf_table_info(const gf_table* t, int kind, int64_t* n_nodes, int64_t* n_hash, double* dr) {
   if (!t || (kind != GF_GREEN && kind != GF_EXP)) return fail(GF_ERR_ARG, "gf_table_info: bad argument");
   const gf_table::One& o = t->get(kind);
@@ -1262,7 +1269,9 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   gf_status st = check_device(m->device);
   if (st) return st;
   if (table && (table->device != m->device)) return fail(GF_ERR_DEVICE, "gf_fill: table on another device");
-  if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill: table built for another k");
+  TabView tg, te;
+  double gscale = 1.0;
+  if (table && !table_views(table, k, &tg, &te, &gscale)) return fail(GF_ERR_ARG, "gf_fill: table built for another k");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, p->rule, s))) return st;
   if (m->ne == 0) return GF_OK;
@@ -1270,13 +1279,8 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   if (parts & GF_PART_ZERO)
     GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
   GeoView g = geo_view_impl(m);
-  TabView tg, te;
-  if (table) {
-    tg = table->green.view();
-    te = table->exp.view();
-  }
   if (parts & GF_PART_REGULAR)
-    GF_CUDA(launch_fill_regular(g, table ? (p->green_from_exp ? &te : &tg) : nullptr, p->green_from_exp != 0,
+    GF_CUDA(launch_fill_regular(g, table ? (p->green_from_exp ? &te : &tg) : nullptr, p->green_from_exp != 0, gscale,
                                 precision, k, p->eta, Z, ldz, s));
   if (!(parts & GF_PART_NEAR)) return GF_OK;
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
@@ -1305,18 +1309,16 @@ gf_status gf_fill_mfie(const gf_mesh* mc, double k, const gf_params* p, const gf
   gf_status st = check_device(m->device);
   if (st) return st;
   if (table && (table->device != m->device)) return fail(GF_ERR_DEVICE, "gf_fill_mfie: table on another device");
-  if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill_mfie: table built for another k");
+  TabView tg, te;
+  double gscale = 1.0;
+  if (table && !table_views(table, k, &tg, &te, &gscale))
+    return fail(GF_ERR_ARG, "gf_fill_mfie: table built for another k");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, p->rule, s))) return st;
   if (m->ne == 0) return GF_OK;
   const size_t esz = precision == GF_FP32 ? 8 : 16;
   GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
   GeoView g = geo_view_impl(m);
-  TabView tg, te;
-  if (table) {
-    tg = table->green.view();
-    te = table->exp.view();
-  }
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
   gauss_legendre(p->nphi, gx_phi, gw_phi);
   gauss_legendre(p->nl, gx_l, gw_l);
@@ -1329,7 +1331,7 @@ gf_status gf_fill_mfie(const gf_mesh* mc, double k, const gf_params* p, const gf
     gll[i] = gx_l[i];
     gll[32 + i] = gw_l[i];
   }
-  GF_CUDA(launch_fill_mfie(g, table ? &tg : nullptr, table ? &te : nullptr, precision,
+  GF_CUDA(launch_fill_mfie(g, table ? &tg : nullptr, table ? &te : nullptr, gscale, precision,
                            precision == GF_FP32 && !p->near_fp64, k, p->nphi, p->nl, glp, gll, Z, ldz, s));
   return GF_OK;
 }
@@ -1343,8 +1345,8 @@ gf_status gf_fill_backward(const gf_mesh* mc, double k, const gf_params* p, cons
   gf_mesh* m = const_cast<gf_mesh*>(mc);
   gf_status st = check_device(m->device);
   if (st) return st;
-  if (table && (table->device != m->device || table->k != k))
-    return fail(GF_ERR_ARG, "gf_fill_backward: table on another device or for another k");
+  if (table && (table->device != m->device || table->kr || table->k != k))
+    return fail(GF_ERR_ARG, "gf_fill_backward: table on another device, for another k or in kR");
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, p->rule, s))) return st;
   if (!m->d_dtri && ((st = dev_alloc(&m->d_dtri, 9 * (size_t)m->nt)) || (st = dev_alloc(&m->d_dk, 1)))) return st;

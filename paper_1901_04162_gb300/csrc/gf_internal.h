@@ -105,6 +105,10 @@ struct TabView {
   const Cell64* cells64;
   // shared-memory image of the lattice for a lookup of degree deg (lat_b only for deg > 1)
   __host__ __device__ size_t smem32_bytes(int deg) const { return (size_t)n_lat * (deg > 1 ? 32 : 16) + blob_vec4() * 16; }
+  // lookups at x = xscale * R: 1 for a table in R, k for a table in u = kR
+  // (a frequency-sweep table, one for every k; r_lo, r_hi then bound u)
+  float xscale32 = 1.f;
+  double xscale64 = 1.0;
 };
 
 // Marker (a quiet-NaN bit pattern) of a lattice cell that holds samples.
@@ -171,13 +175,14 @@ cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s)
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 // bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
-cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, bool mixed,
-                             double k, int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
-                             cudaStream_t s);
+cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, double green_scale,
+                             int precision, bool mixed, double k, int nphi, int nl, const double* gl_phi,
+                             const double* gl_l, void* Z, int64_t ldz, cudaStream_t s);
 // Near-field sparse fill (FP32): tasks = SparseTask records {int p, int n, int64 off}
 // (sparse_task_bytes() each), widx the work list of source triangles, the CSR
 // pattern (row_ptr [ne + 1], cols) and its complex64 values.
-cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, bool mixed, double k,
+cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, double green_scale,
+                               bool mixed, double k,
                                double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
                                const void* tasks, int64_t ntask, const int32_t* widx, const int64_t* row_ptr,
                                const int32_t* cols, void* vals, cudaStream_t s);
@@ -186,7 +191,8 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
                          cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}
 // from the linear table times 1/R); NULL = direct evaluation.
-cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, double green_scale,
+                                int precision, double k,
                                 double eta, void* Z, int64_t ldz, cudaStream_t s);
 cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k,
                              double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
@@ -255,6 +261,7 @@ struct gf_mesh {
 struct gf_table {
   int device;
   double k, r_lo, r_hi;
+  bool kr = false;  // built in u = kR (k = 1): serves every k (frequency sweeps)
   void* d_arena = nullptr;  // one device allocation holding every array of both tables
   size_t arena_bytes = 0;
   struct One {
@@ -285,3 +292,20 @@ struct gf_table {
   } green, exp;
   const One& get(int kind) const { return kind == GF_GREEN ? green : exp; }
 };
+namespace gf {
+// Views of `t` for a fill at wavenumber k. A table in u = kR is read at
+// x = kR, and e^{-jkR}/R = k e^{-ju}/u: its Green values carry the factor
+// *green_scale = k (1 for a table built for this k). False if t is an
+// R-table for another k.
+inline bool table_views(const gf_table* t, double k, TabView* green, TabView* exp, double* green_scale) {
+  if (!t->kr && t->k != k) return false;
+  *green = t->green.view();
+  *exp = t->exp.view();
+  const double x = t->kr ? k : 1.0;
+  green->xscale32 = exp->xscale32 = (float)x;
+  green->xscale64 = exp->xscale64 = x;
+  *green_scale = x;
+  return true;
+}
+}  // namespace gf
+

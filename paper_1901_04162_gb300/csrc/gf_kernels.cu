@@ -213,6 +213,7 @@ struct Tab32 {  // FP32 view (shared or global memory; possibly a window of the 
   int n_busy;
   float vmin, vmax;   // kLatMagic + first / last cell present (the whole lattice, or a window)
   float inv, nc, h, lo;
+  float xscale;       // lookups at x = xscale * R (1, or k for a table in u = kR)
 };
 
 // Points a view's blob pointers into a copy of the blob (global or shared).
@@ -227,6 +228,7 @@ __device__ __forceinline__ void tab32_blob(Tab32& T, const TabView& t, const flo
 
 __device__ __forceinline__ Tab32 tab32(const TabView& t) {
   Tab32 T;
+  T.xscale = t.xscale32;
   T.la = t.lat_a;
   T.lb = t.lat_b;
   tab32_blob(T, t, t.lat_blob);
@@ -274,7 +276,7 @@ __device__ __forceinline__ float2 horner32(float s, float4 a, float4 b) {
 // is exact only on the middle interval.
 template <int DEG>
 __device__ __forceinline__ float2 lookup32_fast(const Tab32& T, float R, bool* slow) {
-  const LatPos q = lat_pos(T, R);
+  const LatPos q = lat_pos(T, R * T.xscale);
   const float4 a = T.la[q.i];
   float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
   if (DEG > 1) b = T.lb[q.i];
@@ -289,7 +291,8 @@ __device__ __forceinline__ float2 lookup32_fast(const Tab32& T, float R, bool* s
 constexpr int kOrdinalMax = 0xFFF;
 
 template <int DEG>
-__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float R) {
+__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float Rr) {
+  const float R = Rr * T.xscale;  // table units
   const LatPos q = lat_pos(T, R);
   int lo = DEG > 1 ? (__float_as_int(T.lb[q.i].z) & kOrdinalMax) : __float_as_int(T.lb[q.i].x);
   if (lo >= kOrdinalMax) {
@@ -327,7 +330,8 @@ __device__ __forceinline__ int cell64_of(double x, double lo, double inv) {
 }
 
 template <int DEG>
-__device__ __forceinline__ double2 lookup64(const TabView& T, double R) {
+__device__ __forceinline__ double2 lookup64(const TabView& T, double Rr) {
+  const double R = Rr * T.xscale64;  // table units
   const int c = min(max(cell64_of(R, T.lo64c, T.inv64c), 0), T.n_cells64 - 1);
   const Cell64 rec = T.cells64[c];
   const bool up = R >= rec.split;
@@ -1160,7 +1164,8 @@ struct KScal {  // per-wavenumber scalars of the near-pair fill
 };
 
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
-  if (use_table && R >= te->r_lo && R <= te->r_hi) {
+  const double x = use_table ? R * te->xscale64 : R;  // table units
+  if (use_table && x >= te->r_lo && x <= te->r_hi) {
     double2 f = lookup64<1>(*te, R);
     return C2{f.x, f.y};
   }
@@ -1255,7 +1260,8 @@ __device__ void inner_integrals(const double r[3], const double v[3][3], const N
 }
 
 __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, bool use_table, float lo, float hi) {
-  if (use_table && R >= lo && R <= hi) return lookup32<1>(te, R);
+  const float x = R * te.xscale;  // lo, hi in table units
+  if (use_table && x >= lo && x <= hi) return lookup32<1>(te, R);
   float sn, cs;
   sincospif(R * kpi, &sn, &cs);
   return make_float2(cs, -sn);
@@ -2189,8 +2195,8 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
       const float slack = 1e-5f * (D + P.w + rq + mag);
       const float lo = D - P.w - rq - slack, hi = D + P.w + rq + slack;
       const int n_lat = tv.n_lat;
-      const int c_lo = max(lat_pos(G, lo).i - 2, 0);
-      const int c_hi = min(lat_pos(G, hi).i + 2, n_lat - 1);
+      const int c_lo = max(lat_pos(G, lo * G.xscale).i - 2, 0);
+      const int c_hi = min(lat_pos(G, hi * G.xscale).i + 2, n_lat - 1);
       win[0] = c_lo;
       win[1] = c_hi;
       win[4] = (int64_t)(c_hi - c_lo + 1) * 32 <= kWinBytes;
@@ -3604,9 +3610,9 @@ cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_e
   return launch_regular32_table<M, kLagrange>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
 }
 
-cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, int precision, double k,
-                                double eta, void* Z, int64_t ldz, cudaStream_t s) {
-  const double scale = k * eta / (4.0 * kPi);
+cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, double green_scale,
+                                int precision, double k, double eta, void* Z, int64_t ldz, cudaStream_t s) {
+  const double scale = k * eta / (4.0 * kPi) * (table && !from_exp ? green_scale : 1.0);
   TabView tv{};
   if (table) tv = *table;
   if (precision == GF_FP64) {
@@ -3669,15 +3675,16 @@ cudaError_t launch_mfie32(const GeoView& g, const TabView* table, float kpi, flo
   return launch_mfie32_table<M, false>(*table, g, kpi, k32, scale, Z, ldz, s);
 }
 
-cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, int precision, bool mixed,
-                             double k, int nphi, int nl, const double* gl_phi, const double* gl_l, void* Z, int64_t ldz,
-                             cudaStream_t s) {
+cudaError_t launch_fill_mfie(const GeoView& g, const TabView* green, const TabView* texp, double green_scale,
+                             int precision, bool mixed, double k, int nphi, int nl, const double* gl_phi,
+                             const double* gl_l, void* Z, int64_t ldz, cudaStream_t s) {
   const unsigned tb = (unsigned)((g.nt + 127) / 128);
   if (precision == GF_FP64) k_mfie_identity<double2><<<tb, 128, 0, s>>>(g, (double2*)Z, ldz);
   else k_mfie_identity<float2><<<tb, 128, 0, s>>>(g, (float2*)Z, ldz);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const double scale = 1.0 / (16.0 * kPi);  // (s l / 2)^2 of the two RWG functions and the 1/(4 pi) of Phi
+  // (s l / 2)^2 of the two RWG functions and the 1/(4 pi) of Phi (times k for a table in kR)
+  const double scale = 1.0 / (16.0 * kPi) * (green ? green_scale : 1.0);
   if (precision == GF_FP64) {
     TabView tv{};
     if (green) tv = *green;
@@ -3763,13 +3770,13 @@ cudaError_t launch_sparse32(const GeoView& g, const TabView* table, float kpi, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, bool mixed, double k,
-                               double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
-                               const void* tasks_v, int64_t ntask, const int32_t* widx, const int64_t* row_ptr,
-                               const int32_t* cols, void* vals, cudaStream_t s) {
+cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, double green_scale,
+                               bool mixed, double k, double eta, int nphi, int nl, const double* gl_phi,
+                               const double* gl_l, const void* tasks_v, int64_t ntask, const int32_t* widx,
+                               const int64_t* row_ptr, const int32_t* cols, void* vals, cudaStream_t s) {
   const SparseTask* tasks = static_cast<const SparseTask*>(tasks_v);
   CsrSink<float2> sink{row_ptr, cols, static_cast<float2*>(vals)};
-  const double scale = k * eta / (4.0 * kPi);
+  const double scale = k * eta / (4.0 * kPi) * (green ? green_scale : 1.0);
   const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
   cudaError_t e;
   switch (g.m) {

@@ -210,7 +210,10 @@ gf_status gf_fill_sparse(const gf_sparse* s, double k, const gf_params* p, const
   int cur = -1;
   GF_CUDA(cudaGetDevice(&cur));
   if (cur != s->device) return fail(GF_ERR_DEVICE, "gf_fill_sparse: handle on another device");
-  if (table && table->k != k) return fail(GF_ERR_ARG, "gf_fill_sparse: table built for another k");
+  gf::TabView tg, te;
+  double gscale = 1.0;
+  if (table && !gf::table_views(table, k, &tg, &te, &gscale))
+    return fail(GF_ERR_ARG, "gf_fill_sparse: table built for another k");
   cudaStream_t st = (cudaStream_t)stream;
   gf_status r = gf::prepare_rule(m, p->rule, st);
   if (r) return r;
@@ -229,12 +232,7 @@ gf_status gf_fill_sparse(const gf_sparse* s, double k, const gf_params* p, const
     gll[32 + i] = gw_l[i];
   }
   const gf::GeoView g = gf::geo_view(m);
-  gf::TabView tg, te;
-  if (table) {
-    tg = table->green.view();
-    te = table->exp.view();
-  }
-  GF_CUDA(gf::launch_fill_sparse(g, table ? &tg : nullptr, table ? &te : nullptr, !p->near_fp64, k, p->eta, p->nphi,
+  GF_CUDA(gf::launch_fill_sparse(g, table ? &tg : nullptr, table ? &te : nullptr, gscale, !p->near_fp64, k, p->eta, p->nphi,
                                  p->nl, glp, gll, s->d_tasks, s->ntask, s->d_widx, s->d_row_ptr, s->d_cols, vals, st));
   return GF_OK;
 }

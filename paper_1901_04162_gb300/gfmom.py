@@ -27,7 +27,7 @@ EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
            "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field",
            "gf_fill_mfie", "gf_sparse_create", "gf_sparse_info", "gf_sparse_pattern", "gf_fill_sparse",
-           "gf_sparse_destroy"]
+           "gf_sparse_destroy", "gf_table_create_kr"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
 
@@ -91,6 +91,7 @@ def lib():
         L.gf_sparse_pattern.argtypes = [vp, vp, vp]
         L.gf_fill_sparse.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, vp]
         L.gf_sparse_destroy.argtypes = [vp]
+        L.gf_table_create_kr.argtypes = [C.c_double, C.c_double, C.POINTER(gf_params), vp, C.POINTER(vp)]
         L.gf_far_field.argtypes = [vp, C.c_double, C.POINTER(gf_params), C.c_int, vp, i64, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("gf_params_default", "gf_last_error"):
@@ -282,6 +283,19 @@ class Table:
         if h:
             lib().gf_table_destroy(h)
             self.h = None
+
+    @classmethod
+    def kr(cls, u_min, u_max, params=None, stream=None):
+        """Tables in u = kR over [u_min, u_max]: one table for every k of a
+        frequency sweep (see include/gfmom.h)."""
+        t = cls.__new__(cls)
+        t.k = None
+        params = params or gf_params_default()
+        h = C.c_void_p()
+        _check(lib().gf_table_create_kr(float(u_min), float(u_max), C.byref(params), _stream_ptr(stream),
+                                        C.byref(h)))
+        t.h = h
+        return t
 
     def info(self, kind=GF_GREEN):
         return gf_table_info(self.h, kind)

@@ -174,3 +174,15 @@ def test_near_dist_criterion():
         share = bool(set(wl.tri[p]) & set(wl.tri[q]))
         assert m0.is_near(p, q) == share
         assert m1.is_near(p, q) == (share or np.linalg.norm(cen[p] - cen[q]) < 0.8)
+
+
+def test_wavenumber_scaling_identity():
+    # Z_k(mesh) = Z_1(k mesh) / k^2: RWG functions are scale-free, div f scales
+    # as 1/k, dS dS' as k^4 and G as 1/k (the identity behind tables in u = kR)
+    xyz, tri = W.icosphere(1)
+    xyz = W.jitter(xyz * 0.4, tri, 0.05, 2)
+    k = 3.7
+    for rule in (3, 6):
+        za = O.Mesh(xyz, tri).z_full(k, rule)
+        zb = O.Mesh(xyz * k, tri).z_full(1.0, rule) / k ** 2
+        assert np.linalg.norm(za - zb) <= 1e-12 * np.linalg.norm(za)
