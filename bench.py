@@ -45,7 +45,7 @@ FALLBACK_SM_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "baa1247fe0f5ce17"): 550877696 + 536157696}
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "1bd02c469e9e9bd4"): 550934272 + 537756928}
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
@@ -430,6 +430,8 @@ def sphere_rcs(gf, torch, mesh, wl, p, prec, stream, dev):
     tab = gf.Table(wl.k, lo, hi, p)
     zdt = torch.complex64 if prec == gf.GF_FP32 else torch.complex128
     out, sig = {}, {}
+    torch.linalg.solve(torch.eye(8, dtype=zdt, device=dev), torch.ones(8, dtype=zdt, device=dev))  # loads the solver
+    torch.cuda.synchronize()
     for name, table in (("table", tab), ("direct", None)):
         Z = gf.fill(mesh, wl.k, p, table, prec)
         V = torch.empty(mesh.ne, dtype=zdt, device=dev)
@@ -530,6 +532,16 @@ def run_batch(args, rank, world, local_rank):
         total_ms = timed(batch)
     clocks = clk.summary()
     direct_ms = timed(direct)
+    # variant: one table in u = kR for all 64 meshes (built once over the union of their k R ranges)
+    t0 = time.perf_counter()
+    rngs = [m.range(rule, gf.GF_FP32) for m in meshes]
+    umin = min(wl.k * lo for wl, (lo, _) in zip(wls, rngs)) * (1 - 1e-6)
+    umax = max(wl.k * hi for wl, (_, hi) in zip(wls, rngs)) * (1 + 1e-6)
+    tkr = gf.Table.kr(umin, umax, p)
+    torch.cuda.synchronize()
+    t_kr = time.perf_counter() - t0
+    kr_batch = gf.Batch(meshes, [wl.k for wl in wls], p, [tkr] * len(meshes), Zs, autotune=True)
+    kr_ms = timed(kr_batch)
     entries = sum(m.ne * m.ne for m in meshes)
     n_regular = sum(evaluated_pairs(m.nt, m.n_near) for m in meshes)
     n_near = sum(m.n_near for m in meshes)
@@ -553,6 +565,10 @@ def run_batch(args, rank, world, local_rank):
         "setup_s": {"meshes": t_mesh, "ranges_and_tables": t_tables, "batch_create_and_autotune": t_create},
         "direct": {"value": entries / (direct_ms / args.steps / 1e3), "ms_per_step": direct_ms / args.steps,
                    "autotuned": direct.config()},
+        "kr_table_variant": {"ms_per_step": kr_ms / args.steps, "value": entries / (kr_ms / args.steps / 1e3),
+                             "u_range": [umin, umax], "green_samples": tkr.info(gf.GF_GREEN)[0],
+                             "ranges_and_one_table_s": t_kr,
+                             "note": "one table in u = kR shared by all meshes (gf_table_create_kr)"},
         "roofline": {"kernel": "batched graph (regular + near)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tops, "unit": "Tops/s (FP32 lane ops, regular pairs only, whole graph time)",
                      "frac": achieved / peak_tops, "traffic": None},
