@@ -732,6 +732,61 @@ def run_near_field(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_mfie(args, rank, world, local_rank):
+    """MFIE (K operator) fill of the 1 lambda sphere (5120 triangles, 7680 RWG,
+    7-point rule): identity term, every ordered regular pair, near pairs with
+    the singular scheme; table and direct Green function."""
+    import torch
+
+    import paper_1901_04162_gb300 as gf
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    wl = W.sphere_7680()
+    m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    p = gf.gf_params_default(rule=wl.rule)
+    lo, hi = m.range(wl.rule, gf.GF_FP32)
+    tab = gf.Table(wl.k, lo, hi, p)
+    Z = torch.empty((m.ne, m.ne), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(table):
+        h = table.h if table else None
+        for _ in range(args.warmup):
+            gf.gf_fill_mfie(m.h, wl.k, p, h, gf.GF_FP32, Z)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            evs[i][0].record(stream)
+            gf.gf_fill_mfie(m.h, wl.k, p, h, gf.GF_FP32, Z)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(x.elapsed_time(y) for x, y in evs) / args.steps
+
+    with Clocks(local_rank) as clk:
+        ms = timed(tab)
+    zt = Z.clone()
+    ms_direct = timed(None)
+    entries = m.ne * m.ne
+    line = {
+        "metric": "MFIE Z entries/s (table fill)", "value": world * entries / (ms / 1e3),
+        "unit": "Z entries/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name + "_mfie", "triangles": m.nt, "rwg_unknowns": m.ne, "rule_points": wl.rule,
+                   "near_pairs": m.n_near, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "direct": {"ms_per_step": ms_direct, "value": world * entries / (ms_direct / 1e3)},
+        "table_vs_direct_rel_l2": float(torch.linalg.vector_norm(zt - Z) / torch.linalg.vector_norm(Z)),
+        "clocks": clk.summary(),
+        "e2e": {"value": None, "reason": "MFIE workload: device-resident mesh and Z"},
+        # identity, regular, near
+        "gpu_launches": 3 * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,7 +794,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sphere_7680",
-                    choices=sorted(WORKLOADS) + ["ellipsoid_batch", "adjoint_3072", "cube_near_field"])
+                    choices=sorted(WORKLOADS) + ["ellipsoid_batch", "adjoint_3072", "cube_near_field",
+                                                   "sphere_mfie"])
     ap.add_argument("--skip-oracle", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
@@ -753,6 +809,12 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "reference arm runs the single-mesh workloads"}))
             return
         run_adjoint(args, rank, world, local_rank)
+        return
+    if args.workload == "sphere_mfie":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "reference arm runs the single-mesh workloads"}))
+            return
+        run_mfie(args, rank, world, local_rank)
         return
     if args.workload == "cube_near_field":
         if args.impl == "reference":
