@@ -900,7 +900,8 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
 #pragma unroll
   for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
   KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
-  unsigned amask = 0;  // test points whose row met a lattice cell holding samples
+  static_assert(M <= 8, "point pairs are flagged in 8 bits per test point");
+  unsigned long long emask = 0;  // point pairs (bit 8 a + b) whose lattice cell holds samples
   float4 al_next = g.pts32[p];
 #pragma unroll 1
   for (int a = 0; a < M; ++a) {
@@ -911,7 +912,7 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
     // once (every load of the row in flight together); a row that met a
     // lattice cell holding samples is corrected after the loop
     float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
-    bool flagged = false;
+    unsigned rowbits = 0;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
       const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
@@ -921,13 +922,13 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
       if (MODE == kLagrange) {
         bool sl = false;
         const float2 f = DEFER ? lookup32_fast<3>(T, R2 * rs, &sl) : lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
-        flagged |= sl;
+        if (sl) rowbits |= 1u << b;
         gr = f.x * beta[b].w;
         gi = f.y * beta[b].w;
       } else if (MODE == kExpOverR) {
         bool sl = false;
         const float2 f = DEFER ? lookup32_fast<1>(T, R2 * rs, &sl) : lookup32<1>(T, R2 * rs);  // e^{-jkR}
-        flagged |= sl;
+        if (sl) rowbits |= 1u << b;
         const float wr = beta[b].w * rs;
         gr = f.x * wr;
         gi = f.y * wr;
@@ -947,7 +948,7 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
       sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
       sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
     }
-    if (flagged) amask |= 1u << a;
+    emask |= (unsigned long long)rowbits << (8 * a);
     const float wa = al.w;
     M0r.add(wa * s0r);
     M0i.add(wa * s0i);
@@ -962,40 +963,39 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
     Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
     Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
   }
-  if (DEFER && MODE != kDirect && __any_sync(0xffffffffu, amask != 0)) {
+  if (DEFER && MODE != kDirect && __any_sync(0xffffffffu, emask != 0ull)) {
     // exact values where the lattice cell holds samples: add (exact - cell
-    // polynomial) to the moments of those point pairs
-    while (amask) {
-      const int a = __ffs(amask) - 1;
-      amask &= amask - 1;
+    // polynomial) to the moments of those point pairs only, in row order,
+    // with the same float operations for R as the loop above
+    while (emask) {
+      const int bit = __ffsll((long long)emask) - 1;
+      emask &= emask - 1;
+      const int a = bit >> 3, b = bit & 7;
       const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float4 be = g.pts32[(size_t)b * g.nt + q];
       const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+      const float rx = ux - be.x, ry = uy - be.y, rz = uz - be.z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      constexpr int D = MODE == kLagrange ? 3 : 1;
+      bool sl;
+      const float2 fa = lookup32_fast<D>(T, R2 * rs, &sl);
+      const float2 fe = lookup32_slow<D>(T, R2 * rs);
+      const float w = al.w * (MODE == kLagrange ? be.w : be.w * rs);
+      const float dr = (fe.x - fa.x) * w, di = (fe.y - fa.y) * w;
+      const float ab = al.x * be.x + al.y * be.y + al.z * be.z;
+      const float alv[3] = {al.x, al.y, al.z}, bev[3] = {be.x, be.y, be.z};
+      M0r.add(dr);
+      M0i.add(di);
 #pragma unroll
-      for (int b = 0; b < M; ++b) {
-        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float rs = rsqrtf(R2);
-        constexpr int D = MODE == kLagrange ? 3 : 1;
-        bool sl;
-        const float2 fa = lookup32_fast<D>(T, R2 * rs, &sl);
-        if (!sl) continue;
-        const float2 fe = lookup32_slow<D>(T, R2 * rs);
-        const float w = al.w * (MODE == kLagrange ? beta[b].w : beta[b].w * rs);
-        const float dr = (fe.x - fa.x) * w, di = (fe.y - fa.y) * w;
-        const float ab = al.x * beta[b].x + al.y * beta[b].y + al.z * beta[b].z;
-        const float alv[3] = {al.x, al.y, al.z}, bev[3] = {beta[b].x, beta[b].y, beta[b].z};
-        M0r.add(dr);
-        M0i.add(di);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          Mar[c].add(alv[c] * dr);
-          Mai[c].add(alv[c] * di);
-          Mbr[c].add(bev[c] * dr);
-          Mbi[c].add(bev[c] * di);
-        }
-        Mabr.add(ab * dr);
-        Mabi.add(ab * di);
+      for (int c = 0; c < 3; ++c) {
+        Mar[c].add(alv[c] * dr);
+        Mai[c].add(alv[c] * di);
+        Mbr[c].add(bev[c] * dr);
+        Mbi[c].add(bev[c] * di);
       }
+      Mabr.add(ab * dr);
+      Mabi.add(ab * di);
     }
   }
   if (!ok) return;
@@ -1607,13 +1607,14 @@ __device__ __forceinline__ void mfie_task32(const GeoView& g, const Tab32& T, fl
   const float* fp = g.frame32 + kFrame32 * (size_t)p;
   const float nx = fp[21], ny = fp[22], nz = fp[23];
   MfieSums S;
-  unsigned amask = 0;
+  static_assert(M <= 8, "point pairs are flagged in 8 bits per test point");
+  unsigned long long emask = 0;  // point pairs (bit 8 a + b) whose lattice cell holds samples
 #pragma unroll 1
   for (int a = 0; a < M; ++a) {
     const float4 al = g.pts32[(size_t)a * g.nt + p];
     const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
     float Pr[3] = {0.f, 0.f, 0.f}, Pi[3] = {0.f, 0.f, 0.f}, Qr[3] = {0.f, 0.f, 0.f}, Qi[3] = {0.f, 0.f, 0.f};
-    bool flagged = false;
+    unsigned rowbits = 0;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
       const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
@@ -1624,7 +1625,7 @@ __device__ __forceinline__ void mfie_task32(const GeoView& g, const Tab32& T, fl
       if (MODE == kLagrange) {
         bool sl = false;
         const float2 f = DEFER ? lookup32_fast<3>(T, R, &sl) : lookup32<3>(T, R);
-        flagged |= sl;
+        if (sl) rowbits |= 1u << b;
         gr = f.x;
         gi = f.y;
       } else {
@@ -1636,31 +1637,31 @@ __device__ __forceinline__ void mfie_task32(const GeoView& g, const Tab32& T, fl
       const float kR = k32 * R, w2 = beta[b].w * rs * rs;
       mfie_point(fmaf(-kR, gi, gr) * w2, fmaf(kR, gr, gi) * w2, rx, ry, rz, beta[b], Pr, Pi, Qr, Qi);
     }
-    if (flagged) amask |= 1u << a;
+    emask |= (unsigned long long)rowbits << (8 * a);
     mfie_outer(S, al.w, al, nx, ny, nz, Pr, Pi, Qr, Qi);
   }
-  if (DEFER && MODE == kLagrange && __any_sync(0xffffffffu, amask != 0)) {
-    // exact values where the lattice cell holds samples: the difference enters P, Q linearly
-    while (amask) {
-      const int a = __ffs(amask) - 1;
-      amask &= amask - 1;
+  if (DEFER && MODE == kLagrange && __any_sync(0xffffffffu, emask != 0ull)) {
+    // exact values where the lattice cell holds samples: the difference of
+    // each such point pair enters P, Q linearly (R from the same float
+    // operations as the loop above)
+    while (emask) {
+      const int bit = __ffsll((long long)emask) - 1;
+      emask &= emask - 1;
+      const int a = bit >> 3, b = bit & 7;
       const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float4 be = g.pts32[(size_t)b * g.nt + q];
       const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+      const float rx = ux - be.x, ry = uy - be.y, rz = uz - be.z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      const float R = R2 * rs;
+      bool sl;
+      const float2 fa = lookup32_fast<3>(T, R, &sl);
+      const float2 fe = lookup32_slow<3>(T, R);
+      const float gr = fe.x - fa.x, gi = fe.y - fa.y;
+      const float kR = k32 * R, w2 = be.w * rs * rs;
       float Pr[3] = {0.f, 0.f, 0.f}, Pi[3] = {0.f, 0.f, 0.f}, Qr[3] = {0.f, 0.f, 0.f}, Qi[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-      for (int b = 0; b < M; ++b) {
-        const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-        const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float rs = rsqrtf(R2);
-        const float R = R2 * rs;
-        bool sl;
-        const float2 fa = lookup32_fast<3>(T, R, &sl);
-        if (!sl) continue;
-        const float2 fe = lookup32_slow<3>(T, R);
-        const float gr = fe.x - fa.x, gi = fe.y - fa.y;
-        const float kR = k32 * R, w2 = beta[b].w * rs * rs;
-        mfie_point(fmaf(-kR, gi, gr) * w2, fmaf(kR, gr, gi) * w2, rx, ry, rz, beta[b], Pr, Pi, Qr, Qi);
-      }
+      mfie_point(fmaf(-kR, gi, gr) * w2, fmaf(kR, gr, gi) * w2, rx, ry, rz, be, Pr, Pi, Qr, Qi);
       mfie_outer(S, al.w, al, nx, ny, nz, Pr, Pi, Qr, Qi);
     }
   }
