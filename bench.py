@@ -234,7 +234,8 @@ def run_ours(args, wl, rank, world, local_rank):
     ne, nt, n_near = mesh.ne, mesh.nt, mesh.n_near
     Z = torch.empty((ne, ne), dtype=zdt, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
-    parts = (gf.GF_PART_ZERO, gf.GF_PART_REGULAR, gf.GF_PART_NEAR)
+    # clear, pair kernel, mirror (Z += Z^T), near kernel: events between them
+    parts = (gf.GF_PART_ZERO, gf.GF_PART_PAIRS, gf.GF_PART_MIRROR, gf.GF_PART_NEAR)
 
     def step(direct, ev, params=None):
         pp = params or p
@@ -250,16 +251,16 @@ def run_ours(args, wl, rank, world, local_rank):
         for i, part in enumerate(parts[1:]):
             ev[2 + i].record(stream)
             gf.gf_fill_parts(mesh.h, wl.k, pp, tab.h if tab else None, prec, Z, part)
-        ev[4].record(stream)
+        ev[5].record(stream)
         return tab
 
     def timed(direct, steps, warmup, params=None):
         keep = []
         for _ in range(warmup):
-            keep.append(step(direct, [torch.cuda.Event(enable_timing=True) for _ in range(5)], params))
+            keep.append(step(direct, [torch.cuda.Event(enable_timing=True) for _ in range(6)], params))
         torch.cuda.synchronize()
         keep.clear()
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(steps)]
         barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -269,12 +270,14 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         wall = time.perf_counter() - t0
-        st = [e[0].elapsed_time(e[4]) for e in evs]
+        st = [e[0].elapsed_time(e[5]) for e in evs]
         reg = [e[2].elapsed_time(e[3]) for e in evs]
-        near = [e[3].elapsed_time(e[4]) for e in evs]
+        mir = [e[3].elapsed_time(e[4]) for e in evs]
+        near = [e[4].elapsed_time(e[5]) for e in evs]
         pre = [e[0].elapsed_time(e[2]) for e in evs]
         keep.clear()
-        return {"step_ms": st, "regular_ms": reg, "near_ms": near, "range_table_ms": pre, "wall_s": wall}
+        return {"step_ms": st, "regular_ms": reg, "mirror_ms": mir, "near_ms": near, "range_table_ms": pre,
+                "wall_s": wall}
 
     # ---- table path (the method) with clocks sampled in the timed region
     with Clocks(local_rank) as clk:
@@ -342,9 +345,11 @@ def run_ours(args, wl, rank, world, local_rank):
                    "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
         "green_evals_per_s": world * (evals_regular + evals_near) * args.steps / (total_ms / 1e3),
         "step_breakdown_ms": {"range_tables_and_zero": statistics.mean(tt["range_table_ms"]),
-                              "regular_kernel": reg_ms, "near_kernel": statistics.mean(tt["near_ms"])},
+                              "regular_kernel": reg_ms, "mirror_z_plus_zt": statistics.mean(tt["mirror_ms"]),
+                              "near_kernel": statistics.mean(tt["near_ms"])},
         "direct": {"value": world * ne * ne / (direct_ms / 1e3), "unit": "Z entries/s", "ms_per_step": direct_ms,
                    "regular_kernel_ms": statistics.mean(td["regular_ms"]),
+                   "mirror_ms": statistics.mean(td["mirror_ms"]),
                    "near_kernel_ms": statistics.mean(td["near_ms"])},
         "near_fp64_variant": None if t64 is None else {
             "ms_per_step": statistics.mean(t64["step_ms"]), "near_kernel_ms": statistics.mean(t64["near_ms"]),
@@ -378,8 +383,8 @@ def run_ours(args, wl, rank, world, local_rank):
         "e2e": ({"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3} if e2e_s else
                 {"value": None, "reason": "Z larger than 8 GiB: no pinned host copy per step"}),
-        # per step: range 4 (FP32; 2 in FP64), both tables 3, regular 1, near 1
-        "gpu_launches": (9 if prec == gf.GF_FP32 else 7) * args.steps,
+        # per step: range 4 (FP32; 2 in FP64), both tables 3, regular pairs 1, mirror 1 (FP32 only), near 1
+        "gpu_launches": (10 if prec == gf.GF_FP32 else 7) * args.steps,
     }
 
     # ---- accuracy vs the FP64 oracle on sampled rows (outside the timed region)

@@ -179,13 +179,22 @@ gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table
                   int precision, void* Z_dev, int64_t ldz, void* stream);
 
 /* The stages of gf_fill, for callers that time or overlap them: GF_PART_ZERO
- * clears the ne x ne block of Z, GF_PART_REGULAR adds the regular-pair terms
- * (one kernel), GF_PART_NEAR adds the near-pair terms (one kernel). gf_fill is
- * gf_fill_parts with all three, in that order. parts = 0 or a bit outside the
- * three is GF_ERR_ARG. */
+ * clears the ne x ne block of Z, GF_PART_REGULAR adds the regular-pair terms,
+ * GF_PART_NEAR adds the near-pair terms (one kernel). gf_fill is
+ * gf_fill_parts with all three, in that order. GF_PART_REGULAR is the two
+ * stages GF_PART_PAIRS | GF_PART_MIRROR: in GF_FP32 the pair kernel adds each
+ * unordered triangle pair's terms to the rows of its test triangle's edges
+ * only, and the mirror kernel then sets Z <- Z + Z^T (one HBM pass); in
+ * GF_FP64 the pair kernel writes both halves and the mirror stage does
+ * nothing. So the regular stage expects the block cleared (GF_PART_ZERO in
+ * the same or an earlier call on the stream) and no near terms yet: the
+ * mirror doubles whatever the block held before. parts = 0 or a bit outside
+ * the five is GF_ERR_ARG. */
 #define GF_PART_ZERO 1u
 #define GF_PART_REGULAR 2u
 #define GF_PART_NEAR 4u
+#define GF_PART_PAIRS 8u
+#define GF_PART_MIRROR 16u
 gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                         int precision, void* Z_dev, int64_t ldz, unsigned parts, void* stream);
 

@@ -4,8 +4,8 @@ of Moment". The work is done by libgfmom (C-ABI, include/gfmom.h); this
 package only binds it. Importing does not load the library; the first call
 does (and fails loudly if it cannot).
 """
-from .gfmom import (GF_EXP, GF_FP32, GF_FP64, GF_GREEN, GF_OP_EFIE, GF_OP_MFIE, GF_PART_NEAR, GF_PART_REGULAR,
-                    GF_PART_ZERO, Sparse, gf_fill_mfie,
+from .gfmom import (GF_EXP, GF_FP32, GF_FP64, GF_GREEN, GF_OP_EFIE, GF_OP_MFIE, GF_PART_MIRROR, GF_PART_NEAR,
+                    GF_PART_PAIRS, GF_PART_REGULAR, GF_PART_ZERO, Sparse, gf_fill_mfie,
                     Batch, GfError, Mesh, Table, fill, gf_batch_config, gf_batch_create, gf_batch_destroy,
                     gf_batch_launch, efie_fill, gf_excitation, gf_far_field, gf_fill, gf_fill_backward,
                     gf_fill_parts, planewave_rcs,
@@ -13,7 +13,8 @@ from .gfmom import (GF_EXP, GF_FP32, GF_FP64, GF_GREEN, GF_OP_EFIE, GF_OP_MFIE, 
                     gf_mesh_set_vertices, gf_params, gf_params_default, gf_range, gf_table_create,
                     gf_table_destroy, gf_table_eval, gf_table_info, gf_table_nodes, lib)
 
-__all__ = ["GF_EXP", "GF_FP32", "GF_FP64", "GF_GREEN", "GF_OP_EFIE", "GF_OP_MFIE", "GF_PART_NEAR", "GF_PART_REGULAR",
+__all__ = ["GF_EXP", "GF_FP32", "GF_FP64", "GF_GREEN", "GF_OP_EFIE", "GF_OP_MFIE", "GF_PART_MIRROR", "GF_PART_NEAR",
+           "GF_PART_PAIRS", "GF_PART_REGULAR",
            "GF_PART_ZERO", "Sparse", "gf_fill_mfie",
            "Batch", "GfError", "Mesh", "Table", "fill", "gf_batch_config", "gf_batch_create", "gf_batch_destroy",
            "gf_batch_launch", "efie_fill", "gf_excitation", "gf_far_field", "gf_fill", "gf_fill_backward",

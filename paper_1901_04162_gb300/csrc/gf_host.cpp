@@ -1261,8 +1261,9 @@ gf_status gf_fill(const gf_mesh* mc, double k, const gf_params* p, const gf_tabl
 gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const gf_table* table, int precision,
                         void* Z, int64_t ldz, unsigned parts, void* stream) {
   if (!mc || !params_ok(p) || !Z) return fail(GF_ERR_ARG, "gf_fill: bad argument");
-  if (parts == 0 || (parts & ~(GF_PART_ZERO | GF_PART_REGULAR | GF_PART_NEAR)))
+  if (parts == 0 || (parts & ~(GF_PART_ZERO | GF_PART_REGULAR | GF_PART_NEAR | GF_PART_PAIRS | GF_PART_MIRROR)))
     return fail(GF_ERR_ARG, "gf_fill_parts: bad parts mask");
+  if (parts & GF_PART_REGULAR) parts |= GF_PART_PAIRS | GF_PART_MIRROR;
   if (precision != GF_FP32 && precision != GF_FP64) return fail(GF_ERR_ARG, "gf_fill: bad precision");
   if (!(k > 0) || ldz < mc->ne) return fail(GF_ERR_ARG, "gf_fill: need k > 0 and ldz >= ne");
   gf_mesh* m = const_cast<gf_mesh*>(mc);
@@ -1279,9 +1280,10 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   if (parts & GF_PART_ZERO)
     GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
   GeoView g = geo_view_impl(m);
-  if (parts & GF_PART_REGULAR)
+  if (parts & GF_PART_PAIRS)
     GF_CUDA(launch_fill_regular(g, table ? (p->green_from_exp ? &te : &tg) : nullptr, p->green_from_exp != 0, gscale,
                                 precision, k, p->eta, Z, ldz, s));
+  if ((parts & GF_PART_MIRROR) && precision == GF_FP32) GF_CUDA(launch_mirror32(Z, ldz, m->ne, s));
   if (!(parts & GF_PART_NEAR)) return GF_OK;
   double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
   gauss_legendre(p->nphi, gx_phi, gw_phi);

@@ -194,6 +194,9 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
 cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, double green_scale,
                                 int precision, double k,
                                 double eta, void* Z, int64_t ldz, cudaStream_t s);
+// Z <- Z + Z^T on the ne x ne FP32 block (the second half of the FP32
+// regular part, whose pair kernel writes the test triangle's rows only).
+cudaError_t launch_mirror32(void* Z, int64_t ldz, int64_t ne, cudaStream_t s);
 cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precision, bool mixed, double k,
                              double eta, int nphi, int nl, const double* gl_phi, const double* gl_l,
                              void* Z, int64_t ldz, cudaStream_t s);

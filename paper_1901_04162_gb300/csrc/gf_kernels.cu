@@ -832,9 +832,19 @@ enum GreenMode : int {
 // DEFER: lookups in the hot loop are branch-free and the rare evaluations in
 // lattice cells holding samples are corrected after it (tables with few such
 // cells); otherwise each lookup branches to the exact path at once.
-// Where the regular fill's 3x3 blocks go. DenseSym: Z[m][n] and Z[n][m] (one
-// evaluation per unordered pair); CsrSink (near-field sparse fill): Z[m][n] at
-// its position in the CSR pattern, dropped where (m, n) is not in it.
+// Where the regular fill's 3x3 blocks go (one evaluation per unordered
+// pair). DenseUpper: Z[m][n] only, the rows of the test triangle's edges;
+// k_symmetrize32 then adds the transpose (Z <- Z + Z^T on a block that held
+// zero), so that a warp's atomics hit three rows instead of 3 + 32.
+// DenseSym: Z[m][n] and Z[n][m] at once (the batched fill). CsrSink
+// (near-field sparse fill): Z[m][n] at its position in the CSR pattern,
+// dropped where (m, n) is not in it.
+struct DenseUpper {
+  float2* Z;
+  int64_t ldz;
+  __device__ __forceinline__ void operator()(int m, int n, float2 v) const { atomicAdd(Z + (int64_t)m * ldz + n, v); }
+};
+
 struct DenseSym {
   float2* Z;
   int64_t ldz;
@@ -878,14 +888,14 @@ template <int M, int MODE, bool DEFER = true, class Sink = DenseSym>
 __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
                                                int p, int q, bool ok, const Sink& sink);
 
-template <int M, int MODE, bool DEFER = true>
+template <int M, int MODE, bool DEFER, class Sink>
 __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
-                                               float2* Z, int64_t ldz, int p, int q0, int lane) {
+                                               const Sink& sink, int p, int q0, int lane) {
   const int q = min(q0 + lane, g.nt - 1);
   const float4 cp = g.cen32[p], cq = g.cen32[q];
   const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
   const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
-  regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, p, q, ok, DenseSym{Z, ldz});
+  regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, p, q, ok, sink);
 }
 
 // The 3x3 block of regular pair (p, q) (q per lane; lanes with ok == false
@@ -1051,7 +1061,7 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoVie
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
     if (sym_task(task, g.nt, &p, &q0))
-      regular_task32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
+      regular_task32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, DenseUpper{Z, ldz}, p, q0, lane);
   }
 }
 
@@ -2223,7 +2233,7 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
     for (int task = warp; task < ntask; task += nw) {
       const int p = bp * 32 + task / (qb1 - qb0);
       const int q0 = (qb0 + task % (qb1 - qb0)) * 32;
-      if (p < g.nt) regular_task32<M, kLagrange, false>(g, T, kpi, scale, inv_k2, Z, ldz, p, q0, lane);
+      if (p < g.nt) regular_task32<M, kLagrange, false>(g, T, kpi, scale, inv_k2, DenseUpper{Z, ldz}, p, q0, lane);
     }
     __syncthreads();
   }
@@ -3321,8 +3331,8 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
       const Tab32 T = tab32(it.green);
       int p, q0;
       if (sym_task(t - it.reg_begin, it.g.nt, &p, &q0))
-        regular_task32<M, TABLE ? kLagrange : kDirect>(it.g, T, it.kpi, it.scale32, it.inv_k2_32,
-                                                       reinterpret_cast<float2*>(it.Z), it.ldz, p, q0, lane);
+        regular_task32<M, TABLE ? kLagrange : kDirect, true>(
+            it.g, T, it.kpi, it.scale32, it.inv_k2_32, DenseSym{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
     }
   }
 }
@@ -3611,6 +3621,40 @@ cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_e
   return launch_regular32_table<M, kLagrange>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
 }
 
+// Z <- Z + Z^T on the ne x ne block (row-major, leading dimension ldz): the
+// regular fill leaves each unordered pair's block in its test triangle's rows
+// only. Per pair of 32 x 32 tiles (I, J), I <= J (a grid-stride walk over all
+// (I, J) that skips I > J): both tiles read through shared memory, both
+// written; a diagonal tile is its own partner. HBM-bound: 2 x 8 ne^2 bytes.
+__global__ void __launch_bounds__(256) k_symmetrize32(float2* __restrict__ Z, int64_t ldz, int ne) {
+  __shared__ float2 ta[32][33];
+  __shared__ float2 tb[32][33];
+  const int nb = (ne + 31) >> 5;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < (int64_t)nb * nb; t += gridDim.x) {
+    const int I = (int)(t / nb), J = (int)(t % nb);
+    if (I > J) continue;  // uniform over the block
+    for (int r = ty; r < 32; r += 8) {
+      const int gr = I * 32 + r, gc = J * 32 + tx;
+      ta[r][tx] = (gr < ne && gc < ne) ? Z[(int64_t)gr * ldz + gc] : make_float2(0.f, 0.f);
+      const int hr = J * 32 + r, hc = I * 32 + tx;
+      tb[r][tx] = (hr < ne && hc < ne) ? Z[(int64_t)hr * ldz + hc] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int gr = I * 32 + r, gc = J * 32 + tx;
+      const float2 a = ta[r][tx], b = tb[tx][r];
+      if (gr < ne && gc < ne) Z[(int64_t)gr * ldz + gc] = make_float2(a.x + b.x, a.y + b.y);
+      if (I != J) {
+        const int hr = J * 32 + r, hc = I * 32 + tx;
+        const float2 c = tb[r][tx], d = ta[tx][r];
+        if (hr < ne && hc < ne) Z[(int64_t)hr * ldz + hc] = make_float2(c.x + d.x, c.y + d.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool from_exp, double green_scale,
                                 int precision, double k, double eta, void* Z, int64_t ldz, cudaStream_t s) {
   const double scale = k * eta / (4.0 * kPi) * (table && !from_exp ? green_scale : 1.0);
@@ -3629,14 +3673,26 @@ cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool fro
   }
   const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
   float2* Z32 = (float2*)Z;
+  // each unordered pair into its test triangle's rows (launch_mirror32 adds
+  // the transpose)
+  cudaError_t e;
   switch (g.m) {
-    case 1: return launch_regular32<1>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
-    case 3: return launch_regular32<3>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
-    case 4: return launch_regular32<4>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
-    case 6: return launch_regular32<6>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
-    case 7: return launch_regular32<7>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s);
+    case 1: e = launch_regular32<1>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
+    case 3: e = launch_regular32<3>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
+    case 4: e = launch_regular32<4>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
+    case 6: e = launch_regular32<6>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
+    case 7: e = launch_regular32<7>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
     default: return cudaErrorInvalidValue;
   }
+  return e;
+}
+
+cudaError_t launch_mirror32(void* Z, int64_t ldz, int64_t ne, cudaStream_t s) {
+  if (ne == 0) return cudaSuccess;
+  const int64_t nb = (ne + 31) / 32;
+  const int64_t blocks = std::min<int64_t>(nb * nb, (int64_t)sm_count() * 8);
+  k_symmetrize32<<<(unsigned)blocks, 256, 0, s>>>((float2*)Z, ldz, (int)ne);
+  return cudaGetLastError();
 }
 
 template <int M, bool DEFER>

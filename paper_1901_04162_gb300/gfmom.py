@@ -29,7 +29,7 @@ EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info
            "gf_fill_mfie", "gf_sparse_create", "gf_sparse_info", "gf_sparse_pattern", "gf_fill_sparse",
            "gf_sparse_destroy", "gf_table_create_kr"]
 GF_NOALLOC_MAX_POINTS = 131072
-GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR = 1, 2, 4
+GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR, GF_PART_PAIRS, GF_PART_MIRROR = 1, 2, 4, 8, 16
 
 
 class GfError(RuntimeError):

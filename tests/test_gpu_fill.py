@@ -170,10 +170,17 @@ def test_cube_73728_sampled_rows():
     gf.gf_fill(m.h, wl.k, p, tab.h, gf.GF_FP32, Z)
     rows = np.random.default_rng(17).choice(m.ne, 6, replace=False)
     z = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
+    # direct evaluation into the same Z (each unordered pair into one
+    # triangle, then Z + Z^T, as for every Z of 4 GiB and more)
+    gf.gf_fill(m.h, wl.k, p, None, gf.GF_FP32, Z)
+    zd = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
     del Z
     ref = om.z_rows(wl.k, 4, rows, mode="table", tables=O.make_tables(wl.k, olo, ohi))
     assert rel_fro(z, ref) <= 1e-5
     assert rel_max(z, ref) <= 1e-5
+    refd = om.z_rows(wl.k, 4, rows)
+    assert rel_fro(zd, refd) <= 1e-5
+    assert rel_max(zd, refd) <= 1e-5
 
 
 def test_mesh_edges_and_near_count_match_oracle():
@@ -190,3 +197,40 @@ def test_mesh_edges_and_near_count_match_oracle():
         nt = len(wl.tri)
         if nt <= 1000:
             assert m.n_near == sum(om.is_near(p, q) for p in range(nt) for q in range(nt))
+
+
+@pytest.mark.parametrize("table", [False, True])
+def test_fp32_parts_padding_and_ragged_tiles(table):
+    # 280 unknowns: nine 32 x 32 tiles, the last ragged. The FP32 fill through
+    # a padded leading dimension leaves the padding alone and matches the
+    # oracle; the regular part alone is symmetric (Galerkin), and ZERO +
+    # REGULAR followed by NEAR in a second call gives gf_fill's matrix
+    wl = W.plate_280()
+    m = gf.Mesh(wl.xyz, wl.tri)
+    p = gf.gf_params_default(rule=3)
+    tab = None
+    if table:
+        lo, hi = m.range(3, gf.GF_FP32)
+        tab = gf.Table(wl.k, lo, hi, p)
+    th = tab.h if tab else None
+    Z = torch.full((m.ne, m.ne + 5), 3.0 - 1.0j, dtype=torch.complex64, device="cuda")
+    gf.gf_fill(m.h, wl.k, p, th, gf.GF_FP32, Z, ldz=m.ne + 5)
+    Zc = Z.cpu().numpy()
+    assert np.all(Zc[:, m.ne:] == 3.0 - 1.0j)
+    ref = oracle_full(wl.xyz, wl.tri, wl.k, 3, table)
+    assert rel_fro(Zc[:, :m.ne], ref) <= 1e-5 and rel_max(Zc[:, :m.ne], ref) <= 1e-5
+    R = torch.empty((m.ne, m.ne), dtype=torch.complex64, device="cuda")
+    gf.gf_fill_parts(m.h, wl.k, p, th, gf.GF_FP32, R, gf.GF_PART_ZERO | gf.GF_PART_REGULAR)
+    r = R.cpu().numpy()
+    assert np.abs(r).max() > 0
+    assert np.array_equal(r, r.T)  # Z + Z^T of the pair kernel's half, both entries from the same two floats
+    # the regular stage as its two halves: the pair kernel fills one triangle's rows per pair
+    gf.gf_fill_parts(m.h, wl.k, p, th, gf.GF_FP32, R, gf.GF_PART_ZERO | gf.GF_PART_PAIRS)
+    half = R.cpu().numpy()
+    assert np.linalg.norm(half - half.T) > 0.1 * np.linalg.norm(half)
+    assert rel_fro(half + half.T, r) <= 1e-6
+    gf.gf_fill_parts(m.h, wl.k, p, th, gf.GF_FP32, R, gf.GF_PART_MIRROR)
+    gf.gf_fill_parts(m.h, wl.k, p, th, gf.GF_FP32, R, gf.GF_PART_NEAR)
+    assert rel_fro(R.cpu().numpy(), Zc[:, :m.ne]) <= 1e-6
+    with pytest.raises(gf.GfError):
+        gf.gf_fill_parts(m.h, wl.k, p, th, gf.GF_FP32, R, 32)
