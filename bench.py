@@ -45,7 +45,7 @@ FALLBACK_SM_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "1bd02c469e9e9bd4"): 550934272 + 537756928}
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "5e720aab75da42db"): 296958464 + 257752064}
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
