@@ -564,7 +564,7 @@ def run_batch(args, rank, world, local_rank):
                                f"{rule}-point rule, k in [pi, 4pi], one table per mesh",
                    "meshes": len(wls), "rwg_unknowns_total": sum(m.ne for m in meshes),
                    "z_bytes": entries * 8, "l2": "flushed between steps (256 MiB write)",
-                   "launch": "one CUDA graph (zero Z, persistent regular kernel, persistent near kernel)",
+                   "launch": "one CUDA graph (zero Z, persistent regular kernel, Z += Z^T per mesh, persistent near kernel)",
                    "autotuned": batch.config(), "parallelism": f"replicas x{world}"},
         "green_evals_per_s": evals / (ms / 1e3),
         "setup_s": {"meshes": t_mesh, "ranges_and_tables": t_tables, "batch_create_and_autotune": t_create},
@@ -574,12 +574,13 @@ def run_batch(args, rank, world, local_rank):
                              "u_range": [umin, umax], "green_samples": tkr.info(gf.GF_GREEN)[0],
                              "ranges_and_one_table_s": t_kr,
                              "note": "one table in u = kR shared by all meshes (gf_table_create_kr)"},
-        "roofline": {"kernel": "batched graph (regular + near)", "bound": "alu", "achieved": achieved,
+        "roofline": {"kernel": "batched graph (regular + mirrors + near)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tops, "unit": "Tops/s (FP32 lane ops, regular pairs only, whole graph time)",
                      "frac": achieved / peak_tops, "traffic": None},
         "clocks": clocks,
         "e2e": {"value": None, "reason": "batched workload: fill-only; see setup_s"},
-        "gpu_launches": 2 * args.steps,
+        # per graph launch: the regular kernel, one mirror pass per mesh, the near kernel
+        "gpu_launches": (2 + len(wls)) * args.steps,
     }
     if not args.skip_oracle:
         import oracle as O

@@ -46,8 +46,9 @@ void release_graph(gf_batch* b) {
   b->graph = nullptr;
 }
 
-// Captures zeroing of every Z, the counter reset and the two persistent
-// kernels on the batch's own stream.
+// Captures zeroing of every Z, the counter reset, the persistent regular
+// kernel, one mirror pass per Z and the persistent near kernel on the batch's
+// own stream.
 gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
   release_graph(b);
   int sms = 1;
@@ -60,6 +61,9 @@ gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
   if (e == cudaSuccess && b->total_regular > 0)
     e = launch_batch_regular(b->d_items, (int)b->items.size(), b->total_regular, b->d_counters, b->m, b->table, block,
                              sms * ctas, chunk, b->cs);
+  // the regular kernel leaves each pair in its test triangle's rows: Z += Z^T per mesh
+  for (size_t i = 0; i < b->z.size() && e == cudaSuccess && b->total_regular > 0; ++i)
+    e = launch_mirror32(b->z[i], b->ldz[i], b->ne[i], b->cs);
   if (e == cudaSuccess && b->total_near > 0)
     e = launch_batch_near(b->d_items, (int)b->items.size(), b->total_near, b->d_counters + 1, b->mixed, b->nphi,
                           b->nl, b->glp, b->gll, sms * 16, b->cs);

@@ -833,25 +833,15 @@ enum GreenMode : int {
 // lattice cells holding samples are corrected after it (tables with few such
 // cells); otherwise each lookup branches to the exact path at once.
 // Where the regular fill's 3x3 blocks go (one evaluation per unordered
-// pair). DenseUpper: Z[m][n] only, the rows of the test triangle's edges;
-// k_symmetrize32 then adds the transpose (Z <- Z + Z^T on a block that held
-// zero), so that a warp's atomics hit three rows instead of 3 + 32.
-// DenseSym: Z[m][n] and Z[n][m] at once (the batched fill). CsrSink
-// (near-field sparse fill): Z[m][n] at its position in the CSR pattern,
-// dropped where (m, n) is not in it.
+// pair). DenseUpper (dense and batched fills): Z[m][n] only, the rows of the
+// test triangle's edges; k_symmetrize32 then adds the transpose (Z <- Z + Z^T
+// on a block that held zero), so that a warp's atomics hit three rows
+// instead of 3 + 32. CsrSink (near-field sparse fill): Z[m][n] at its
+// position in the CSR pattern, dropped where (m, n) is not in it.
 struct DenseUpper {
   float2* Z;
   int64_t ldz;
   __device__ __forceinline__ void operator()(int m, int n, float2 v) const { atomicAdd(Z + (int64_t)m * ldz + n, v); }
-};
-
-struct DenseSym {
-  float2* Z;
-  int64_t ldz;
-  __device__ __forceinline__ void operator()(int m, int n, float2 v) const {
-    atomicAdd(Z + (int64_t)m * ldz + n, v);
-    atomicAdd(Z + (int64_t)n * ldz + m, v);
-  }
 };
 
 template <class T>
@@ -884,7 +874,7 @@ struct CsrSink {
   }
 };
 
-template <int M, int MODE, bool DEFER = true, class Sink = DenseSym>
+template <int M, int MODE, bool DEFER = true, class Sink = DenseUpper>
 __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
                                                int p, int q, bool ok, const Sink& sink);
 
@@ -3332,7 +3322,7 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
       int p, q0;
       if (sym_task(t - it.reg_begin, it.g.nt, &p, &q0))
         regular_task32<M, TABLE ? kLagrange : kDirect, true>(
-            it.g, T, it.kpi, it.scale32, it.inv_k2_32, DenseSym{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
+            it.g, T, it.kpi, it.scale32, it.inv_k2_32, DenseUpper{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
     }
   }
 }
