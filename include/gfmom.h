@@ -72,8 +72,9 @@ typedef struct {
   int nphi;                   /* angular points per source edge, near pairs (8)         */
   int nl;                     /* line points per source edge, near pairs (8)            */
   double eta;                 /* wave impedance (376.730313668)                         */
-  int near_fp64;              /* GF_FP32 fills: 0 = near pairs with FP64 geometry, static
-                                 parts and sums and FP32 sampling on the source edges;
+  int near_fp64;              /* GF_FP32 fills: 0 = near pairs with FP64 geometry and
+                                 static parts, FP32 sampling on the source edges and FP32
+                                 assembly of the 3x3 block from the inner integrals;
                                  1 = FP64 throughout (GF_FP64 fills always are) (0)       */
   int green_from_exp;         /* regular pairs of gf_fill / gf_fill_parts with a table:
                                  0 = e^{-jkR}/R from the Lagrange Green table (Section

@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 
 #include "gf_internal.h"
 
@@ -1159,6 +1160,10 @@ struct C2 {
   double re, im;
 };
 
+struct C2f {  // FP32 complex of the mixed-precision near-block assembly
+  float re, im;
+};
+
 struct KScal {  // per-wavenumber scalars of the near-pair fill
   double k, scale, inv_k2, inv_k;
 };
@@ -1268,9 +1273,10 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 }
 
 // Mixed precision: the geometry (normal, projection, foot distances, edge
-// frames), the closed-form static part and all accumulation in FP64; the
-// sampling of e^{-jkR} at the angular and line nodes of each edge in FP32
-// (relative quantities of the size of a triangle, FP32 Exp table).
+// frames) and the closed-form static part in FP64; the sampling of e^{-jkR}
+// at the angular and line nodes of each edge and its sums in FP32 (relative
+// quantities of the size of a triangle, FP32 Exp table). The caller assembles
+// the 3x3 block from I0, I1 in FP32.
 // FP64 where the terms cancel (projection, in-plane distances, the static
 // closed form, all sums), FP32 sampling of e^{-jkR} on the edges. The source
 // frame (normal, edge tangents, lengths, edge normals) is precomputed per
@@ -1383,15 +1389,15 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
 // of its entries and adds the partner's copy of that half, so that the group
 // sums end spread over the lanes (at most ceil(9 / G) + 1 entries each) with
 // no more additions than entries exchanged.
-template <int N>
-__device__ __forceinline__ void rs_halve(const C2 (&in)[N], C2 (&out)[(N + 1) / 2], bool upper, int off,
+template <int N, class CT>
+__device__ __forceinline__ void rs_halve(const CT (&in)[N], CT (&out)[(N + 1) / 2], bool upper, int off,
                                          unsigned gmask) {
   constexpr int H = (N + 1) / 2;
 #pragma unroll
   for (int s = 0; s < H; ++s) {
-    const C2 lo_v = in[s];
-    const C2 hi_v = (H + s < N) ? in[H + s] : C2{0.0, 0.0};
-    const C2 keep = upper ? hi_v : lo_v, send = upper ? lo_v : hi_v;
+    const CT lo_v = in[s];
+    const CT hi_v = (H + s < N) ? in[H + s] : CT{0, 0};
+    const CT keep = upper ? hi_v : lo_v, send = upper ? lo_v : hi_v;
     out[s].re = keep.re + __shfl_xor_sync(gmask, send.re, off);
     out[s].im = keep.im + __shfl_xor_sync(gmask, send.im, off);
   }
@@ -1437,9 +1443,13 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
                                           const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask) {
   if (!valid_pair) return;
   const int p = g.near_row[idx], q = g.near_idx[idx];
-  C2 acc[9];
+  // MIXED: the 3x3 block is assembled from the FP64 inner integrals in FP32
+  // (products and sums of smooth quantities, added into an FP32 Z); else FP64
+  using CT = typename std::conditional<MIXED, C2f, C2>::type;
+  using RT = typename std::conditional<MIXED, float, double>::type;
+  CT acc[9];
 #pragma unroll
-  for (int u = 0; u < 9; ++u) acc[u] = C2{0.0, 0.0};
+  for (int u = 0; u < 9; ++u) acc[u] = CT{0, 0};
   if (sub < g.m) {
     double vq[3][3];
     for (int c = 0; c < 3; ++c)
@@ -1455,25 +1465,27 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
     else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
     // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
     // w_a / 4 folded into I0, I1
-    const double w4 = 0.25 * al[3];
-    const C2 S = {w4 * I0.re, w4 * I0.im};
-    const C2 T[3] = {{w4 * I1[0].re, w4 * I1[0].im}, {w4 * I1[1].re, w4 * I1[1].im}, {w4 * I1[2].re, w4 * I1[2].im}};
-    const double q4 = 4.0 * ks.inv_k2;
-    const C2 Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
-    double f[3][3];
+    const RT w4 = (RT)(0.25 * al[3]);
+    const CT S = {w4 * (RT)I0.re, w4 * (RT)I0.im};
+    const CT T[3] = {{w4 * (RT)I1[0].re, w4 * (RT)I1[0].im},
+                     {w4 * (RT)I1[1].re, w4 * (RT)I1[1].im},
+                     {w4 * (RT)I1[2].re, w4 * (RT)I1[2].im}};
+    const RT q4 = (RT)(4.0 * ks.inv_k2);
+    const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
+    RT f[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
-      f[i][0] = ra[0] - vpi[0];
-      f[i][1] = ra[1] - vpi[1];
-      f[i][2] = ra[2] - vpi[2];
+      f[i][0] = (RT)(ra[0] - vpi[0]);
+      f[i][1] = (RT)(ra[1] - vpi[1]);
+      f[i][2] = (RT)(ra[2] - vpi[2]);
     }
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      C2 J[3];
+      CT J[3];
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        const double dv = rho0[x] - vq[j][x];
+        const RT dv = (RT)(rho0[x] - vq[j][x]);
         J[x].re = fma(dv, S.re, T[x].re);
         J[x].im = fma(dv, S.im, T[x].im);
       }
@@ -1485,14 +1497,14 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
     }
   }
   // reduce-scatter: 9 -> 5 -> 3 (-> 2 for G = 8) entries per lane
-  C2 r5[5], r3[3];
+  CT r5[5], r3[3];
   constexpr int L1 = G / 2, L2 = G / 4;
   rs_halve<9>(acc, r5, (sub & L1) != 0, L1, gmask);
   rs_halve<5>(r5, r3, (sub & L2) != 0, L2, gmask);
   int first = ((sub & L1) ? 5 : 0) + ((sub & L2) ? 3 : 0);  // entry of slot 0
   int count = (sub & L1) ? ((sub & L2) ? 1 : 3) : ((sub & L2) ? 2 : 3);  // 9 = 5 + 4; 5 = 3 + 2; 4 = 3 + 1
   constexpr int NS = G == 8 ? 2 : 3;
-  C2 fin[NS];
+  CT fin[NS];
   if constexpr (G == 8) {
     rs_halve<3>(r3, fin, (sub & 1) != 0, 1, gmask);
     const bool up = (sub & 1) != 0;
@@ -1512,7 +1524,7 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
     if (!edge_valid(ci) || !edge_valid(cj)) continue;
     const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
     const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
-    sink.add(edge_of(ci), edge_of(cj), -c * fin[u].im, c * fin[u].re);
+    sink.add(edge_of(ci), edge_of(cj), -c * (double)fin[u].im, c * (double)fin[u].re);
   }
 }
 
@@ -1848,10 +1860,10 @@ __global__ void k_mfie_identity(GeoView g, Out* Z, int64_t ldz) {
 // (Van Oosterom & Strackee, IEEE Trans. Biomed. Eng. 30 (1983) 125:
 // tan(Omega / 2) = R1.(R2 x R3) / (R1 R2 R3 + (R1.R2) R3 + (R1.R3) R2 +
 // (R2.R3) R1), R_i = v_i - r); the angles carry only the smooth remainder.
-// MIXED (FP32 fills): the geometry, the closed-form static parts and the
-// assembly in FP64; the remainders e^{-jkR} - 1 on the edge lines and in the
-// angle integrals sampled in FP32 (the FP32 Exp table), as for the EFIE near
-// pairs.
+// MIXED (FP32 fills): the geometry and the closed-form static parts in FP64;
+// the remainders e^{-jkR} - 1 on the edge lines and in the angle integrals
+// sampled in FP32 (the FP32 Exp table), and the 3x3 block assembled from the
+// integrals in FP32, as for the EFIE near pairs.
 template <class Out, int G, bool MIXED>
 __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool use_table, NearArgs A, Out* Z,
                                                    int64_t ldz) {
@@ -1868,8 +1880,11 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
     const int64_t idx = g0 + it * ngroups;
     if (idx >= n_near) continue;  // uniform over the group
     const int p = g.near_row[idx], q = g.near_idx[idx];
-    C2 acc[9];
-    for (int u = 0; u < 9; ++u) acc[u] = C2{0.0, 0.0};
+    // MIXED: the 3x3 block is assembled from the FP64 integrals in FP32
+    using CT = typename std::conditional<MIXED, C2f, C2>::type;
+    using RT = typename std::conditional<MIXED, float, double>::type;
+    CT acc[9];
+    for (int u = 0; u < 9; ++u) acc[u] = CT{0, 0};
     if (sub < g.m) {
       const double* fr = g.frame64 + kFrame * (size_t)q;  // n, len, t, m of q
       const double* v = g.v64 + 9 * (size_t)q;
@@ -1990,47 +2005,50 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
                            (R2[0] * R3[0] + R2[1] * R3[1] + R2[2] * R3[2]) * n1;
         hI0[0] -= 2.0 * atan2(num, den) * c4;
       }
-      // n x I_u
-      double nIu[3][2];
+      // n x I_u, and the assembly below in RT
+      RT nIu[3][2], Iur[3][2], hI0r[2] = {(RT)hI0[0], (RT)hI0[1]};
+      const RT nr[3] = {(RT)n[0], (RT)n[1], (RT)n[2]}, hr = (RT)h;
       for (int hh = 0; hh < 2; ++hh) {
-        nIu[0][hh] = n[1] * Iu[2][hh] - n[2] * Iu[1][hh];
-        nIu[1][hh] = n[2] * Iu[0][hh] - n[0] * Iu[2][hh];
-        nIu[2][hh] = n[0] * Iu[1][hh] - n[1] * Iu[0][hh];
+        nIu[0][hh] = (RT)(n[1] * Iu[2][hh] - n[2] * Iu[1][hh]);
+        nIu[1][hh] = (RT)(n[2] * Iu[0][hh] - n[0] * Iu[2][hh]);
+        nIu[2][hh] = (RT)(n[0] * Iu[1][hh] - n[1] * Iu[0][hh]);
+        for (int x = 0; x < 3; ++x) Iur[x][hh] = (RT)Iu[x][hh];
       }
-      const double* np = g.frame64 + kFrame * (size_t)p;  // n_p
-      const double wa = al[3];
+      const double* np64 = g.frame64 + kFrame * (size_t)p;  // n_p
+      const RT np[3] = {(RT)np64[0], (RT)np64[1], (RT)np64[2]};
+      const RT wa = (RT)al[3];
       const double* vp = g.v64 + 9 * (size_t)p;
       for (int j = 0; j < 3; ++j) {
-        const double w[3] = {rho0[0] - v[3 * j], rho0[1] - v[3 * j + 1], rho0[2] - v[3 * j + 2]};
-        const double nw[3] = {n[1] * w[2] - n[2] * w[1], n[2] * w[0] - n[0] * w[2], n[0] * w[1] - n[1] * w[0]};
-        double T[3][2];
+        const RT w[3] = {(RT)(rho0[0] - v[3 * j]), (RT)(rho0[1] - v[3 * j + 1]), (RT)(rho0[2] - v[3 * j + 2])};
+        const RT nw[3] = {nr[1] * w[2] - nr[2] * w[1], nr[2] * w[0] - nr[0] * w[2], nr[0] * w[1] - nr[1] * w[0]};
+        RT T[3][2];
         for (int hh = 0; hh < 2; ++hh) {
-          const double Iw[3] = {Iu[1][hh] * w[2] - Iu[2][hh] * w[1], Iu[2][hh] * w[0] - Iu[0][hh] * w[2],
-                                Iu[0][hh] * w[1] - Iu[1][hh] * w[0]};  // I_u x w
-          for (int x = 0; x < 3; ++x) T[x][hh] = -(h * nIu[x][hh] + nw[x] * hI0[hh] - Iw[x]);
+          const RT Iw[3] = {Iur[1][hh] * w[2] - Iur[2][hh] * w[1], Iur[2][hh] * w[0] - Iur[0][hh] * w[2],
+                            Iur[0][hh] * w[1] - Iur[1][hh] * w[0]};  // I_u x w
+          for (int x = 0; x < 3; ++x) T[x][hh] = -(hr * nIu[x][hh] + nw[x] * hI0r[hh] - Iw[x]);
         }
         // n_p x T_j
-        double NT[3][2];
+        RT NT[3][2];
         for (int hh = 0; hh < 2; ++hh) {
           NT[0][hh] = np[1] * T[2][hh] - np[2] * T[1][hh];
           NT[1][hh] = np[2] * T[0][hh] - np[0] * T[2][hh];
           NT[2][hh] = np[0] * T[1][hh] - np[1] * T[0][hh];
         }
         for (int i = 0; i < 3; ++i) {
-          const double f[3] = {r[0] - vp[3 * i], r[1] - vp[3 * i + 1], r[2] - vp[3 * i + 2]};  // r_a - v_i
+          const RT f[3] = {(RT)(r[0] - vp[3 * i]), (RT)(r[1] - vp[3 * i + 1]), (RT)(r[2] - vp[3 * i + 2])};  // r_a - v_i
           acc[3 * i + j].re = -wa * (f[0] * NT[0][0] + f[1] * NT[1][0] + f[2] * NT[2][0]);
           acc[3 * i + j].im = -wa * (f[0] * NT[0][1] + f[1] * NT[1][1] + f[2] * NT[2][1]);
         }
       }
     }
-    C2 r5[5], r3[3];
+    CT r5[5], r3[3];
     constexpr int L1 = G / 2, L2 = G / 4;
     rs_halve<9>(acc, r5, (sub & L1) != 0, L1, gmask);
     rs_halve<5>(r5, r3, (sub & L2) != 0, L2, gmask);
     int first = ((sub & L1) ? 5 : 0) + ((sub & L2) ? 3 : 0);
     int count = (sub & L1) ? ((sub & L2) ? 1 : 3) : ((sub & L2) ? 2 : 3);
     constexpr int NS = G == 8 ? 2 : 3;
-    C2 fin[NS];
+    CT fin[NS];
     if constexpr (G == 8) {
       rs_halve<3>(r3, fin, (sub & 1) != 0, 1, gmask);
       const bool upper = (sub & 1) != 0;
@@ -2050,10 +2068,11 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
       const double c = 0.25 * slp * slq * inv_area_q;  // A_p (s l / 2A)_i (s l / 2A)_j
       Out* z = Z + (int64_t)edge_of(ci) * ldz + edge_of(cj);
       if constexpr (sizeof(Out) == 8) {
-        atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)(c * fin[u].re), (float)(c * fin[u].im)));
+        atomicAdd(reinterpret_cast<float2*>(z),
+                  make_float2((float)(c * (double)fin[u].re), (float)(c * (double)fin[u].im)));
       } else {
-        atomicAdd(reinterpret_cast<double*>(z), c * fin[u].re);
-        atomicAdd(reinterpret_cast<double*>(z) + 1, c * fin[u].im);
+        atomicAdd(reinterpret_cast<double*>(z), c * (double)fin[u].re);
+        atomicAdd(reinterpret_cast<double*>(z) + 1, c * (double)fin[u].im);
       }
     }
   }
