@@ -2784,12 +2784,13 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   cross3(e1, e2, nn);
   const double Ln = sqrt(dot3(nn, nn)), iL = 1.0 / Ln;
   for (int x = 0; x < 3; ++x) n[x] = nn[x] * iL;
-  double len[3], t[3][3], m[3][3];
+  double len[3], ilen[3], t[3][3], m[3][3];
   for (int e = 0; e < 3; ++e) {
     const int e2i = e == 2 ? 0 : e + 1;
     double tt[3] = {vq[e2i][0] - vq[e][0], vq[e2i][1] - vq[e][1], vq[e2i][2] - vq[e][2]};
     len[e] = sqrt(dot3(tt, tt));
-    for (int x = 0; x < 3; ++x) t[e][x] = tt[x] / len[e];
+    ilen[e] = 1.0 / len[e];
+    for (int x = 0; x < 3; ++x) t[e][x] = tt[x] * ilen[e];
     cross3(t[e], n, m[e]);
   }
   // ---- projection, vertex distances, e^{-jkd}
@@ -2867,27 +2868,37 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   // ---- assembly: values and adjoints of I0, I1, rho0, r, p's vertices, L = |nn|, k
   double bI0r = 0, bI0i = 0, bI1r[3] = {0, 0, 0}, bI1i[3] = {0, 0, 0}, brho[3] = {0, 0, 0}, br[3] = {0, 0, 0};
   double bk = 0, bik2 = 0, bA = 0;
-  const double Aq = 0.5 * Ln, ik2 = ik * ik;
+  const double Aq = 0.5 * Ln, ik2 = ik * ik, iAq = 1.0 / Aq;
+  // per source edge j: s_j l_j, s_j / l_j and rho0 - v_j (reciprocals once: the
+  // FP64 divide costs a dozen FP64 operations); the adjoint of s_j l_j is
+  // summed over i and applied once
+  double slj[3], sjl[3], dvj[3][3], bslj[3] = {0, 0, 0};
+  for (int j = 0; j < 3; ++j) {
+    const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
+    const double ej[3] = {vq[j2][0] - vq[j1][0], vq[j2][1] - vq[j1][1], vq[j2][2] - vq[j1][2]};
+    const double lj = sqrt(dot3(ej, ej)), sj = (ecq[j] & 1) ? -1.0 : 1.0;
+    slj[j] = sj * lj;
+    sjl[j] = sj / lj;
+    for (int x = 0; x < 3; ++x) dvj[j][x] = rho0[x] - vq[j][x];
+  }
+  const double kewa = k * eta * wa * iAq;
   for (int i = 0; i < 3; ++i) {
     if (!edge_valid(ecp[i])) continue;
     const int i1 = i == 2 ? 0 : i + 1, i2 = i1 == 2 ? 0 : i1 + 1;
     const double ei[3] = {vp[i2][0] - vp[i1][0], vp[i2][1] - vp[i1][1], vp[i2][2] - vp[i1][2]};
     const double li_ = sqrt(dot3(ei, ei)), si = (ecp[i] & 1) ? -1.0 : 1.0, sli = si * li_;
     const double f[3] = {r[0] - vp[i][0], r[1] - vp[i][1], r[2] - vp[i][2]};
-    double bf[3] = {0, 0, 0}, bsli = 0;
+    double bf[3] = {0, 0, 0}, bcsum = 0;
     for (int j = 0; j < 3; ++j) {
       if (!edge_valid(ecq[j])) continue;
-      const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
-      const double ej[3] = {vq[j2][0] - vq[j1][0], vq[j2][1] - vq[j1][1], vq[j2][2] - vq[j1][2]};
-      const double lj = sqrt(dot3(ej, ej)), sj = (ecq[j] & 1) ? -1.0 : 1.0, slj = sj * lj;
-      const double dv[3] = {rho0[0] - vq[j][0], rho0[1] - vq[j][1], rho0[2] - vq[j][2]};
+      const double* dv = dvj[j];
       double Jr[3], Ji[3];
       for (int x = 0; x < 3; ++x) {
         Jr[x] = I1r[x] + dv[x] * I0r;
         Ji[x] = I1i[x] + dv[x] * I0i;
       }
       const double tr = 0.25 * dot3(f, Jr) - I0r * ik2, ti = 0.25 * dot3(f, Ji) - I0i * ik2;
-      const double c = k * eta * wa * sli * slj / Aq;
+      const double c = kewa * sli * slj[j];
       const float2 gz = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
       // L = gz.x (-c ti) + gz.y (c tr)
       const double btr = (double)gz.y * c, bti = -(double)gz.x * c;
@@ -2907,23 +2918,32 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
       bI0r -= btr * ik2;
       bI0i -= bti * ik2;
       bik2 -= btr * I0r + bti * I0i;
-      // c = k eta wa sl_i sl_j / A_q
-      bk += bc * c / k;
-      bsli += bc * c / sli;
-      bA -= bc * c / Aq;
-      const double bslj = bc * c / slj;
-      for (int x = 0; x < 3; ++x) {
-        const double g = bslj * sj * ej[x] / lj;
-        gq[j2][x] += g;
-        gq[j1][x] -= g;
-      }
+      // c = k eta wa sl_i sl_j / A_q: bc c is the adjoint of log c, shared by its factors
+      const double bcc = bc * c;
+      bcsum += bcc;
+      bslj[j] += bcc;  // becomes the adjoint of s_j l_j below
     }
+    // log c = log k + log sl_i + log sl_j - log A_q + const
+    bk += bcsum * ik;
+    bA -= bcsum * iAq;
+    const double gsi = bcsum / sli * (si / li_);
     for (int x = 0; x < 3; ++x) {
       br[x] += bf[x];
       gp[i][x] -= bf[x];
-      const double g = bsli * si * ei[x] / li_;
+      const double g = gsi * ei[x];
       gp[i2][x] += g;
       gp[i1][x] -= g;
+    }
+  }
+  for (int j = 0; j < 3; ++j) {
+    if (!edge_valid(ecq[j])) continue;
+    const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
+    // d(s_j l_j)/d v_{j2} = s_j e_j / l_j; the adjoint of s_j l_j is (sum bc c) / (s_j l_j)
+    const double g0 = bslj[j] / slj[j] * sjl[j];
+    for (int x = 0; x < 3; ++x) {
+      const double g = g0 * (vq[j2][x] - vq[j1][x]);
+      gq[j2][x] += g;
+      gq[j1][x] -= g;
     }
   }
   bk -= 2.0 * bik2 * ik2 * ik;
@@ -3114,8 +3134,9 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   }
   // vertex distances
   for (int c = 0; c < 3; ++c) {
+    const double gr = bRv[c] / Rv[c];
     for (int x = 0; x < 3; ++x) {
-      const double g = bRv[c] * (vq[c][x] - r[x]) / Rv[c];
+      const double g = gr * (vq[c][x] - r[x]);
       gq[c][x] += g;
       br[x] -= g;
     }
@@ -3144,7 +3165,7 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
     }
     const double tb = dot3(t[e], bt[e]);
     for (int x = 0; x < 3; ++x) {
-      const double btt = (bt[e][x] - t[e][x] * tb) / len[e] + blen[e] * t[e][x];
+      const double btt = (bt[e][x] - t[e][x] * tb) * ilen[e] + blen[e] * t[e][x];
       gq[en][x] += btt;
       gq[e][x] -= btt;
     }
