@@ -65,8 +65,12 @@ def job_throughput(world, units_per_rank, seconds):
 
 
 def kernel_source_hash():
-    path = os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", "gf_kernels.cu")
-    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
+    """Hash of the sources that define the regular-pair table kernel (the
+    shared device code and the fill kernels)."""
+    h = hashlib.sha256()
+    for name in ("gf_device.cuh", "gf_fill.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
 
 
 WORKLOADS = {

@@ -1,0 +1,849 @@
+// Device code shared by the gfmom kernel files (sm_103a): the FP32 table
+// lookups of Section II.C on the lattice image, the near-pair test and the
+// symmetric task map, the regular-pair computation (moments of a triangle
+// pair and its 3x3 RWG block) with its sinks, and the near-pair computation
+// (singularity cancellation, Section II.A; mixed or FP64 precision).
+//
+// Regular pairs: one warp per (test triangle p, 32 source triangles q), one
+// source triangle per lane. For each test point a the lane runs over the
+// source points b: R = |(c_p - c_q) + alpha_a - beta_b|, Green value from the
+// Lagrange table (Eq. 6 hash on the lattice -> cubic in s, Eq. 3 + 5
+// re-expanded as monomials) or from sincospi, and four moments M0 = sum w w G,
+// Ma = sum w w alpha G, Mb = sum w w beta G, Mab = sum w w (alpha . beta) G (8
+// complex numbers; Kahan-compensated over a in FP32). The 3 x 3 RWG block:
+//   Z(e_i, e_j) += jk eta/(4 pi) s_i l_i s_j l_j
+//                  [ (Mab + eps_j . Ma + delta_i . Mb + (delta_i . eps_j) M0) / 4 - M0 / k^2 ]
+// with delta_i = c_p - v_i, eps_j = c_q - v_j (v = vertex opposite the edge).
+//
+// Near pairs: one pair per group of G lanes, lane = test point; the inner
+// integrals over q come from singularity cancellation (exact radial
+// integral) with the angular variable u = asinh(tan phi) for the scalar part,
+// and from the surface-gradient theorem (line integrals over q's edges, static
+// part in closed form) for the vector part. e^{-jkR} on those lines is the
+// linear Exp table when r_min <= R <= r_max (Section II.C), else sincos.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+#include <type_traits>
+
+#include "gf_internal.h"
+
+namespace gf {
+namespace {
+
+constexpr int kWarps = 8;              // warps per block of the pair kernels
+constexpr int kThreads = kWarps * 32;
+
+__device__ __forceinline__ int edge_of(int code) { return code >> 1; }
+__device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
+
+// ---------------------------------------------------------------- lookups
+struct Tab32 {  // FP32 view (shared or global memory; possibly a window of the lattice)
+  const float4* la;   // lattice records, indexed by the global cell number
+  const float4* lb;
+  const int* busy;    // the blob: cells holding samples (ascending), their headers,
+  const float4* hdr;  // sub-cells and compact interval records
+  const float4* sub;
+  const float4* ca;
+  const float4* cb;
+  int n_busy;
+  float vmin, vmax;   // kLatMagic + first / last cell present (the whole lattice, or a window)
+  float inv, nc, h, lo;
+  float xscale;       // lookups at x = xscale * R (1, or k for a table in u = kR)
+};
+
+// Points a view's blob pointers into a copy of the blob (global or shared).
+__device__ __forceinline__ void tab32_blob(Tab32& T, const TabView& t, const float4* blob) {
+  T.busy = reinterpret_cast<const int*>(blob);
+  T.hdr = blob + (t.n_busy + 3) / 4;
+  T.sub = T.hdr + t.n_busy;
+  T.ca = T.sub + t.n_sub;
+  T.cb = T.ca + t.n_cmp;
+  T.n_busy = t.n_busy;
+}
+
+__device__ __forceinline__ Tab32 tab32(const TabView& t) {
+  Tab32 T;
+  T.xscale = t.xscale32;
+  T.la = t.lat_a;
+  T.lb = t.lat_b;
+  tab32_blob(T, t, t.lat_blob);
+  T.vmin = kLatMagic;
+  T.vmax = kLatMagic + (float)(t.n_lat - 1);
+  T.inv = t.lat_inv;
+  T.nc = t.lat_nc;
+  T.h = t.lat_h;
+  T.lo = t.lat_lo;
+  return T;
+}
+
+// Lattice cell of R (without a conversion instruction) and the exact offset
+// s = R - A_i from its anchor; the table builder repeats these float
+// operations.
+struct LatPos {
+  int i;
+  float s;
+};
+
+__device__ __forceinline__ LatPos lat_pos(const Tab32& T, float R) {
+  const float u = __fmaf_rn(R, T.inv, T.nc);
+  const float v = fminf(fmaxf(__fadd_rn(u, kLatMagic), T.vmin), T.vmax);
+  const float fi = __fsub_rn(v, kLatMagic);
+  return LatPos{__float_as_int(v) - __float_as_int(kLatMagic), __fsub_rn(R, __fmaf_rn(fi, T.h, T.lo))};
+}
+
+// e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 lattice image: the
+// lattice cell of R (the Eq. 6 hash on the uniform samples) gives the
+// polynomial directly; a cell that holds samples adds one sub-cell record
+// (exact bracketing) and the interval's own record.
+template <int DEG>
+__device__ __forceinline__ float2 horner32(float s, float4 a, float4 b) {
+  if (DEG == 1) return make_float2(fmaf(s, a.z, a.x), fmaf(s, a.w, a.y));
+  float re = fmaf(s, b.z, b.x), im = fmaf(s, b.w, b.y);
+  re = fmaf(s, re, a.z);
+  im = fmaf(s, im, a.w);
+  re = fmaf(s, re, a.x);
+  im = fmaf(s, im, a.y);
+  return make_float2(re, im);
+}
+
+// Branch-free part: the cell's record (the polynomial of the interval at the
+// cell's middle); *slow is set when the cell holds samples, where this value
+// is exact only on the middle interval.
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_fast(const Tab32& T, float R, bool* slow) {
+  const LatPos q = lat_pos(T, R * T.xscale);
+  const float4 a = T.la[q.i];
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DEG > 1) b = T.lb[q.i];
+  *slow = (__float_as_int(DEG > 1 ? b.w : a.w) & 1) != 0;
+  return horner32<DEG>(q.s, a, b);
+}
+
+// Cells holding samples: the cell's place in the busy list (kept in the low
+// bits of c3re for the Green table, in lat_b.x for the Exp table; a binary
+// search for lists longer than kOrdinalMax), its header, the sub-cell, then
+// the compact interval record about node32.
+constexpr int kOrdinalMax = 0xFFF;
+
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float Rr) {
+  const float R = Rr * T.xscale;  // table units
+  const LatPos q = lat_pos(T, R);
+  int lo = DEG > 1 ? (__float_as_int(T.lb[q.i].z) & kOrdinalMax) : __float_as_int(T.lb[q.i].x);
+  if (lo >= kOrdinalMax) {
+    lo = 0;
+    int hi = T.n_busy - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (T.busy[mid] < q.i) lo = mid + 1;
+      else hi = mid;
+    }
+  }
+  const float4 h = T.hdr[lo];
+  const int c = __float_as_int(h.x) + min(max(__float2int_rz(__fmul_rn(q.s, h.y)), 0), __float_as_int(h.z));
+  const float4 rec = T.sub[c];
+  const bool up = R >= rec.y;
+  const int j = __float_as_int(rec.x) + (up ? 1 : 0);
+  const float4 a = T.ca[j];
+  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (DEG > 1) b = T.cb[j];
+  return horner32<DEG>(R - (up ? rec.y : rec.z), a, b);
+}
+
+template <int DEG>
+__device__ __forceinline__ float2 lookup32(const Tab32& T, float R) {
+  bool slow;
+  const float2 f = lookup32_fast<DEG>(T, R, &slow);
+  return slow ? lookup32_slow<DEG>(T, R) : f;
+}
+
+// FP64 lookup through the FP64 cell image (same construction as the FP32
+// one, in FP64): exact bracketing against the FP64 samples, then the FP64
+// polynomial about the interval's left sample.
+__device__ __forceinline__ int cell64_of(double x, double lo, double inv) {
+  return __double2int_rz(__dmul_rn(__dsub_rn(x, lo), inv));
+}
+
+template <int DEG>
+__device__ __forceinline__ double2 lookup64(const TabView& T, double Rr) {
+  const double R = Rr * T.xscale64;  // table units
+  const int c = min(max(cell64_of(R, T.lo64c, T.inv64c), 0), T.n_cells64 - 1);
+  const Cell64 rec = T.cells64[c];
+  const bool up = R >= rec.split;
+  const int j = rec.j0 + (up ? 1 : 0);
+  const double s = R - (up ? rec.split : rec.anchor);
+  const double2* cf = T.c64 + 4 * j;
+  const double2 c0 = cf[0], c1 = cf[1];
+  if (DEG == 1) return make_double2(fma(s, c1.x, c0.x), fma(s, c1.y, c0.y));
+  const double2 c2 = cf[2], c3 = cf[3];
+  double re = fma(s, c3.x, c2.x), im = fma(s, c3.y, c2.y);
+  re = fma(s, re, c1.x);
+  im = fma(s, im, c1.y);
+  re = fma(s, re, c0.x);
+  im = fma(s, im, c0.y);
+  return make_double2(re, im);
+}
+
+// ---------------------------------------------------------------- near test
+// A pair is near when it shares a vertex, or (centroid criterion) when q is in
+// p's sorted near list; the FP32 centroid distance only screens out pairs that
+// are clearly farther than near_dist.
+__device__ __forceinline__ bool pair_is_near(const GeoView& g, int p, int q, int4 vp, int4 vq, float3 dc) {
+  if (vp.x == vq.x || vp.x == vq.y || vp.x == vq.z || vp.y == vq.x || vp.y == vq.y || vp.y == vq.z ||
+      vp.z == vq.x || vp.z == vq.y || vp.z == vq.z)
+    return true;
+  if (g.near_dist32 > 0.f) {
+    float th = g.near_dist32 * 1.0001f + 1e-6f;
+    if (dc.x * dc.x + dc.y * dc.y + dc.z * dc.z < th * th) {
+      int64_t lo = g.near_ptr[p], hi = g.near_ptr[p + 1];
+      while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        int v = g.near_idx[mid];
+        if (v == q) return true;
+        if (v < q) lo = mid + 1;
+        else hi = mid;
+      }
+    }
+  }
+  return false;
+}
+
+// Regular pairs are enumerated once per unordered pair {p, q}, p < q: the
+// Galerkin block of (q, p) is the transpose of that of (p, q) (the moments
+// swap alpha and beta, the bracket is unchanged), so one evaluation serves
+// Z[m][n] and Z[n][m]. Work unit = (p, 32 consecutive q) inside a 32 x 32 block
+// pair (bp <= bq); block pairs run column by column, u = bq (bq + 1) / 2 + bp,
+// 32 units (one per p of block bp) each; regular_units(nt) counts them.
+
+__device__ __forceinline__ bool sym_task(int64_t task, int nt, int* p, int* q0) {
+  const int64_t u = task >> 5;
+  int64_t bq = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+  while (bq > 0 && bq * (bq + 1) / 2 > u) --bq;
+  while ((bq + 1) * (bq + 2) / 2 <= u) ++bq;
+  const int64_t bp = u - bq * (bq + 1) / 2;
+  *p = (int)(bp * 32 + (task & 31));
+  *q0 = (int)(bq * 32);
+  return *p < nt;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// ---------------------------------------------------------------- regular fill
+struct KSum {  // Kahan-compensated FP32 sum
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float y = x - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// Blocks of 512 threads when the table is staged in shared memory (one CTA
+// per SM holds it), 256 otherwise.
+// One warp task of the regular-pair fill: test triangle p, source triangles
+// q0..q0+31 (one per lane).
+// Green value source of the regular-pair kernels.
+enum GreenMode : int {
+  kDirect = 0,    // sincospi of k R / pi, times 1/R
+  kLagrange = 1,  // e^{-jkR}/R from the Green table (Lagrange, Section II.C)
+  kExpOverR = 2,  // e^{-jkR} from the Exp table (linear), times 1/R
+};
+
+// DEFER: lookups in the hot loop are branch-free and the rare evaluations in
+// lattice cells holding samples are corrected after it (tables with few such
+// cells); otherwise each lookup branches to the exact path at once.
+// Where the regular fill's 3x3 blocks go (one evaluation per unordered
+// pair). DenseUpper (dense and batched fills): Z[m][n] only, the rows of the
+// test triangle's edges; k_symmetrize32 then adds the transpose (Z <- Z + Z^T
+// on a block that held zero), so that a warp's atomics hit three rows
+// instead of 3 + 32. CsrSink (near-field sparse fill): Z[m][n] at its
+// position in the CSR pattern, dropped where (m, n) is not in it.
+struct DenseUpper {
+  float2* Z;
+  int64_t ldz;
+  __device__ __forceinline__ void operator()(int m, int n, float2 v) const { atomicAdd(Z + (int64_t)m * ldz + n, v); }
+};
+
+template <class T>
+struct CsrSink {
+  const int64_t* row_ptr;  // [ne + 1]
+  const int32_t* cols;     // sorted per row
+  T* vals;
+  __device__ __forceinline__ int64_t find(int m, int n) const {
+    int64_t lo = row_ptr[m], hi = row_ptr[m + 1];
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cols[mid] < n) lo = mid + 1;
+      else hi = mid;
+    }
+    return lo < row_ptr[m + 1] && cols[lo] == n ? lo : -1;
+  }
+  __device__ __forceinline__ void operator()(int m, int n, float2 v) const {
+    const int64_t i = find(m, n);
+    if (i >= 0) atomicAdd(reinterpret_cast<float2*>(vals + i), v);
+  }
+  __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
+    const int64_t i = find(m, n);
+    if (i < 0) return;
+    if constexpr (sizeof(T) == 8) {
+      atomicAdd(reinterpret_cast<float2*>(vals + i), make_float2((float)zr, (float)zi));
+    } else {
+      atomicAdd(reinterpret_cast<double*>(vals + i), zr);
+      atomicAdd(reinterpret_cast<double*>(vals + i) + 1, zi);
+    }
+  }
+};
+
+template <int M, int MODE, bool DEFER = true, class Sink = DenseUpper>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               int p, int q, bool ok, const Sink& sink);
+
+template <int M, int MODE, bool DEFER, class Sink>
+__device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               const Sink& sink, int p, int q0, int lane) {
+  const int q = min(q0 + lane, g.nt - 1);
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+  const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, p, q, ok, sink);
+}
+
+// The 3x3 block of regular pair (p, q) (q per lane; lanes with ok == false
+// take part in the warp's work but write nothing), handed to `sink`.
+template <int M, int MODE, bool DEFER, class Sink>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
+                                               int p, int q, bool ok, const Sink& sink) {
+  const float4 cp = g.cen32[p], cq = g.cen32[q];
+  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+  if (!__any_sync(0xffffffffu, ok)) return;
+  float4 beta[M];
+#pragma unroll
+  for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
+  KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
+  static_assert(M <= 8, "point pairs are flagged in 8 bits per test point");
+  unsigned long long emask = 0;  // point pairs (bit 8 a + b) whose lattice cell holds samples
+  float4 al_next = g.pts32[p];
+#pragma unroll 1
+  for (int a = 0; a < M; ++a) {
+    const float4 al = al_next;
+    if (a + 1 < M) al_next = g.pts32[(size_t)(a + 1) * g.nt + p];  // issued a whole iteration early
+    const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+    // Green values of the M source points: branch-free lookups accumulated at
+    // once (every load of the row in flight together); a row that met a
+    // lattice cell holding samples is corrected after the loop
+    float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
+    unsigned rowbits = 0;
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      float gr, gi;
+      if (MODE == kLagrange) {
+        bool sl = false;
+        const float2 f = DEFER ? lookup32_fast<3>(T, R2 * rs, &sl) : lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
+        if (sl) rowbits |= 1u << b;
+        gr = f.x * beta[b].w;
+        gi = f.y * beta[b].w;
+      } else if (MODE == kExpOverR) {
+        bool sl = false;
+        const float2 f = DEFER ? lookup32_fast<1>(T, R2 * rs, &sl) : lookup32<1>(T, R2 * rs);  // e^{-jkR}
+        if (sl) rowbits |= 1u << b;
+        const float wr = beta[b].w * rs;
+        gr = f.x * wr;
+        gi = f.y * wr;
+      } else {
+        float sn, cs;
+        sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
+        const float wr = beta[b].w * rs;
+        gr = cs * wr;
+        gi = -sn * wr;
+      }
+      s0r += gr;
+      s0i += gi;
+      sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
+      sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
+      sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
+      sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
+      sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
+      sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
+    }
+    emask |= (unsigned long long)rowbits << (8 * a);
+    const float wa = al.w;
+    M0r.add(wa * s0r);
+    M0i.add(wa * s0i);
+    const float wal[3] = {wa * al.x, wa * al.y, wa * al.z};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Mar[c].add(wal[c] * s0r);
+      Mai[c].add(wal[c] * s0i);
+      Mbr[c].add(wa * sbr[c]);
+      Mbi[c].add(wa * sbi[c]);
+    }
+    Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
+    Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
+  }
+  if (DEFER && MODE != kDirect && __any_sync(0xffffffffu, emask != 0ull)) {
+    // exact values where the lattice cell holds samples: add (exact - cell
+    // polynomial) to the moments of those point pairs only, in row order,
+    // with the same float operations for R as the loop above
+    while (emask) {
+      const int bit = __ffsll((long long)emask) - 1;
+      emask &= emask - 1;
+      const int a = bit >> 3, b = bit & 7;
+      const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float4 be = g.pts32[(size_t)b * g.nt + q];
+      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+      const float rx = ux - be.x, ry = uy - be.y, rz = uz - be.z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      constexpr int D = MODE == kLagrange ? 3 : 1;
+      bool sl;
+      const float2 fa = lookup32_fast<D>(T, R2 * rs, &sl);
+      const float2 fe = lookup32_slow<D>(T, R2 * rs);
+      const float w = al.w * (MODE == kLagrange ? be.w : be.w * rs);
+      const float dr = (fe.x - fa.x) * w, di = (fe.y - fa.y) * w;
+      const float ab = al.x * be.x + al.y * be.y + al.z * be.z;
+      const float alv[3] = {al.x, al.y, al.z}, bev[3] = {be.x, be.y, be.z};
+      M0r.add(dr);
+      M0i.add(di);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        Mar[c].add(alv[c] * dr);
+        Mai[c].add(alv[c] * di);
+        Mbr[c].add(bev[c] * dr);
+        Mbi[c].add(bev[c] * di);
+      }
+      Mabr.add(ab * dr);
+      Mabi.add(ab * di);
+    }
+  }
+  if (!ok) return;
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+  const float m0r = M0r.s, m0i = M0i.s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!edge_valid(ecp[i])) continue;
+    const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
+    const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
+    const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!edge_valid(ecq[j])) continue;
+      const float4 gq = g.geo32[3 * (size_t)q + j];  // eps_j, s_j l_j
+      const float eMar = gq.x * Mar[0].s + gq.y * Mar[1].s + gq.z * Mar[2].s;
+      const float eMai = gq.x * Mai[0].s + gq.y * Mai[1].s + gq.z * Mai[2].s;
+      const float de = gp.x * gq.x + gp.y * gq.y + gp.z * gq.z;
+      const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
+      const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
+      const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
+      // j * c * (br + j bi) = c * (-bi + j br)
+      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bi, c * br));
+    }
+  }
+}
+
+// ---------------------------------------------------------------- near pairs (FP64)
+struct NearArgs {
+  double k, scale, inv_k2;
+  int nphi, nl;
+  double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
+  float fx_phi[32], fw_phi[32], fx_l[32], fw_l[32];  // the same rules in FP32
+};
+
+struct C2 {
+  double re, im;
+};
+
+struct C2f {  // FP32 complex of the mixed-precision near-block assembly
+  float re, im;
+};
+
+struct KScal {  // per-wavenumber scalars of the near-pair fill
+  double k, scale, inv_k2, inv_k;
+};
+
+__device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
+  const double x = use_table ? R * te->xscale64 : R;  // table units
+  if (use_table && x >= te->r_lo && x <= te->r_hi) {
+    double2 f = lookup64<1>(*te, R);
+    return C2{f.x, f.y};
+  }
+  double s, c;
+  sincos(k * R, &s, &c);
+  return C2{c, -s};
+}
+
+// Inner integrals over triangle v for observation point r (1/(4 pi) included).
+__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, double k,
+                                const TabView* te, bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
+  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  n[0] *= inv;
+  n[1] *= inv;
+  n[2] *= inv;
+  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+  const double d = fabs(h);
+  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  const C2 ed = exp_mjkr(k, d, te, use_table);
+  double sre = 0, sim = 0;                       // scalar sector sums
+  double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0};  // vector remainder
+  double vst[3] = {0, 0, 0};                     // vector static part
+  for (int e = 0; e < 3; ++e) {
+    const double* a = v[e];
+    const double* b = v[(e + 1) % 3];
+    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    t[0] /= len;
+    t[1] /= len;
+    t[2] /= len;
+    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
+    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
+    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
+    if (fabs(P0) > 1e-12 * len) {
+      const double aP = fabs(P0);
+      const double um = asinh(lm / aP), up = asinh(lp / aP);
+      const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
+      double cr = 0, ci = 0;
+      for (int i = 0; i < A.nphi; ++i) {
+        const double u = mid + half * A.gx_phi[i];
+        const double ch = cosh(u);
+        const double rho = aP * ch;
+        const double Re = sqrt(rho * rho + d * d);
+        const C2 eR = exp_mjkr(k, Re, te, use_table);
+        const double wt = A.gw_phi[i] / ch;
+        cr += (ed.re - eR.re) * wt;
+        ci += (ed.im - eR.im) * wt;
+      }
+      const double sg = P0 > 0 ? half : -half;
+      sre += cr * sg;
+      sim += ci * sg;
+    }
+    double lr = 0, li = 0;
+    for (int i = 0; i < A.nl; ++i) {
+      const double s = 0.5 * len * (A.gx_l[i] + 1.0);
+      const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
+      const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
+      const C2 eR = exp_mjkr(k, R, te, use_table);
+      lr += (eR.re - 1.0) * A.gw_l[i];
+      li += (eR.im + k * R) * A.gw_l[i];
+    }
+    lr *= 0.5 * len;
+    li *= 0.5 * len;
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    if (R02 > 0) {
+      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
+      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
+      st += 0.5 * R02 * (log(fp) - log(fm));
+    }
+    for (int x = 0; x < 3; ++x) {
+      vre[x] += mh[x] * lr;
+      vim[x] += mh[x] * li;
+      vst[x] += mh[x] * st;
+    }
+  }
+  const double c4 = 1.0 / (4.0 * kPi);
+  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
+  I0->re = sim / k * c4;
+  I0->im = -sre / k * c4;
+  for (int x = 0; x < 3; ++x) {
+    I1[x].re = (-vim[x] / k + vst[x]) * c4;
+    I1[x].im = (vre[x] / k) * c4;
+  }
+}
+
+__device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, bool use_table, float lo, float hi) {
+  const float x = R * te.xscale;  // lo, hi in table units
+  if (use_table && x >= lo && x <= hi) return lookup32<1>(te, R);
+  float sn, cs;
+  sincospif(R * kpi, &sn, &cs);
+  return make_float2(cs, -sn);
+}
+
+// Mixed precision: the geometry (normal, projection, foot distances, edge
+// frames) and the closed-form static part in FP64; the sampling of e^{-jkR}
+// at the angular and line nodes of each edge and its sums in FP32 (relative
+// quantities of the size of a triangle, FP32 Exp table). The caller assembles
+// the 3x3 block from I0, I1 in FP32.
+// FP64 where the terms cancel (projection, in-plane distances, the static
+// closed form, all sums), FP32 sampling of e^{-jkR} on the edges. The source
+// frame (normal, edge tangents, lengths, edge normals) is precomputed per
+// triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
+// and the static log term is one log of a ratio per edge.
+__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
+                                      const float* __restrict__ fr32, const NearArgs& A, double k, double inv_k,
+                                      const Tab32& te, bool use_table, float lo, float hi, C2* I0, C2 I1[3],
+                                      double rho0[3]) {
+  const float kpi = (float)(k / kPi), k32 = (float)k;
+  const double n[3] = {fr[0], fr[1], fr[2]};
+  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+  const double d = fabs(h);
+  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  // |r - v_c| (scalars, so that the edge loop picks them without a local array)
+  double Rv0, Rv1, Rv2;
+  {
+    const double* w = v[0];
+    Rv0 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
+    w = v[1];
+    Rv1 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
+    w = v[2];
+    Rv2 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
+  }
+  const float d32 = (float)d;
+  const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
+  // the sampled (dynamic) sums carry FP32 samples: FP32 accumulation; the
+  // static closed form stays in FP64
+  float sre = 0.f, sim = 0.f, vre[3] = {0.f, 0.f, 0.f}, vim[3] = {0.f, 0.f, 0.f};
+  double vst[3] = {0, 0, 0};
+  for (int e = 0; e < 3; ++e) {
+    const double* a = v[e];
+    const double len = fr[3 + e];
+    const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
+    const double mh[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
+    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
+    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
+    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+    const double lp = lm + len;
+    if (fabs(P0) > 1e-12 * len) {
+      const float aP32 = (float)fabs(P0);
+      const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
+      const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
+      float cr = 0.f, ci = 0.f;
+      for (int i = 0; i < A.nphi; ++i) {
+        const float u = fmaf(half, A.fx_phi[i], mid);
+        const float E = expf(u);
+        const float ch = 0.5f * (E + __frcp_rn(E));
+        const float rho = aP32 * ch;
+        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
+        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
+        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        cr = fmaf(ed.x - eR.x, wt, cr);
+        ci = fmaf(ed.y - eR.y, wt, ci);
+      }
+      const float sg = P0 > 0 ? half : -half;
+      sre = fmaf(cr, sg, sre);
+      sim = fmaf(ci, sg, sim);
+    }
+    // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
+    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    const float tx = fr32[3 + 3 * e], ty = fr32[4 + 3 * e], tz = fr32[5 + 3 * e];
+    const float hl = 0.5f * fr32[e];
+    float lr = 0.f, li = 0.f;
+    for (int i = 0; i < A.nl; ++i) {
+      const float sp = hl * (A.fx_l[i] + 1.0f);
+      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
+      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
+      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
+      lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
+      li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
+    }
+    lr *= hl;
+    li *= hl;
+    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|;
+    // log(fp / fm) with fp = lp + Rp = R02 / (Rp - lp), fm = lm + Rm =
+    // R02 / (Rm - lm), each in its cancellation-free form (lp >= lm), as one
+    // quotient
+    const double R02 = P0 * P0 + d * d;
+    const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
+    double st = 0.5 * (lp * Rp - lm * Rm);
+    if (R02 > 0) {
+      double ratio;
+      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
+      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
+      else ratio = (Rm - lm) / (Rp - lp);
+      st += 0.5 * R02 * log(ratio);
+    }
+    const float mx = fr32[12 + 3 * e], my = fr32[13 + 3 * e], mz = fr32[14 + 3 * e];
+    vre[0] = fmaf(mx, lr, vre[0]);
+    vre[1] = fmaf(my, lr, vre[1]);
+    vre[2] = fmaf(mz, lr, vre[2]);
+    vim[0] = fmaf(mx, li, vim[0]);
+    vim[1] = fmaf(my, li, vim[1]);
+    vim[2] = fmaf(mz, li, vim[2]);
+    for (int x = 0; x < 3; ++x) vst[x] += mh[x] * st;
+  }
+  const double c4 = 1.0 / (4.0 * kPi), ikc4 = inv_k * c4;
+  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
+  I0->re = (double)sim * ikc4;
+  I0->im = -(double)sre * ikc4;
+  for (int x = 0; x < 3; ++x) {
+    I1[x].re = fma(-(double)vim[x], inv_k, vst[x]) * c4;
+    I1[x].im = (double)vre[x] * ikc4;
+  }
+}
+
+// Reduce-scatter of the nine complex entries of a 3 x 3 block over the G
+// lanes of a group (G = 4 or 8): at each halving step a lane keeps one half
+// of its entries and adds the partner's copy of that half, so that the group
+// sums end spread over the lanes (at most ceil(9 / G) + 1 entries each) with
+// no more additions than entries exchanged.
+template <int N, class CT>
+__device__ __forceinline__ void rs_halve(const CT (&in)[N], CT (&out)[(N + 1) / 2], bool upper, int off,
+                                         unsigned gmask) {
+  constexpr int H = (N + 1) / 2;
+#pragma unroll
+  for (int s = 0; s < H; ++s) {
+    const CT lo_v = in[s];
+    const CT hi_v = (H + s < N) ? in[H + s] : CT{0, 0};
+    const CT keep = upper ? hi_v : lo_v, send = upper ? lo_v : hi_v;
+    out[s].re = keep.re + __shfl_xor_sync(gmask, send.re, off);
+    out[s].im = keep.im + __shfl_xor_sync(gmask, send.im, off);
+  }
+}
+
+// One near pair per group of G lanes (G >= the rule size; lane = test point;
+// lanes >= m idle); every lane of the group must call (valid_pair is uniform
+// over the group). The 3 x 3 block is reduce-scattered over the group and
+// each lane adds its entries to Z.
+template <class Out>
+struct DenseOut {  // Z[m][n] += z (row-major, ld = ldz)
+  Out* Z;
+  int64_t ldz;
+  __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
+    Out* z = Z + (int64_t)m * ldz + n;
+    if constexpr (sizeof(Out) == 8) {
+      atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
+    } else {
+      atomicAdd(reinterpret_cast<double*>(z), zr);
+      atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
+    }
+  }
+};
+
+template <bool MIXED, int G, class Sink>
+__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
+                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask);
+
+template <class Out, bool MIXED, int G = 8>
+__device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
+                                          int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
+                                          unsigned gmask) {
+  near_pair<MIXED, G>(g, te, te32, lo32, hi32, use_table, A, ks, DenseOut<Out>{Z, ldz}, idx, valid_pair, sub, gmask);
+}
+
+// The 3x3 block of near pair idx (of the mesh's near list) on a group of G
+// lanes, handed to `sink` (sink.add(m, n, re, im)).
+template <bool MIXED, int G, class Sink>
+__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
+                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
+                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask) {
+  if (!valid_pair) return;
+  const int p = g.near_row[idx], q = g.near_idx[idx];
+  // MIXED: the 3x3 block is assembled from the FP64 inner integrals in FP32
+  // (products and sums of smooth quantities, added into an FP32 Z); else FP64
+  using CT = typename std::conditional<MIXED, C2f, C2>::type;
+  using RT = typename std::conditional<MIXED, float, double>::type;
+  CT acc[9];
+#pragma unroll
+  for (int u = 0; u < 9; ++u) acc[u] = CT{0, 0};
+  if (sub < g.m) {
+    double vq[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int x = 0; x < 3; ++x) vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
+    const double* cp = g.cen64 + 4 * (size_t)p;
+    const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
+    const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
+    C2 I0, I1[3];
+    double rho0[3];
+    if (MIXED)
+      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, g.frame32 + kFrame32 * (size_t)q, A, ks.k,
+                            ks.inv_k, te32, use_table, lo32, hi32, &I0, I1, rho0);
+    else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
+    // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
+    // w_a / 4 folded into I0, I1
+    const RT w4 = (RT)(0.25 * al[3]);
+    const CT S = {w4 * (RT)I0.re, w4 * (RT)I0.im};
+    const CT T[3] = {{w4 * (RT)I1[0].re, w4 * (RT)I1[0].im},
+                     {w4 * (RT)I1[1].re, w4 * (RT)I1[1].im},
+                     {w4 * (RT)I1[2].re, w4 * (RT)I1[2].im}};
+    const RT q4 = (RT)(4.0 * ks.inv_k2);
+    const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
+    RT f[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
+      f[i][0] = (RT)(ra[0] - vpi[0]);
+      f[i][1] = (RT)(ra[1] - vpi[1]);
+      f[i][2] = (RT)(ra[2] - vpi[2]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      CT J[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const RT dv = (RT)(rho0[x] - vq[j][x]);
+        J[x].re = fma(dv, S.re, T[x].re);
+        J[x].im = fma(dv, S.im, T[x].im);
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        acc[3 * i + j].re = fma(f[i][0], J[0].re, fma(f[i][1], J[1].re, fma(f[i][2], J[2].re, -Q.re)));
+        acc[3 * i + j].im = fma(f[i][0], J[0].im, fma(f[i][1], J[1].im, fma(f[i][2], J[2].im, -Q.im)));
+      }
+    }
+  }
+  // reduce-scatter: 9 -> 5 -> 3 (-> 2 for G = 8) entries per lane
+  CT r5[5], r3[3];
+  constexpr int L1 = G / 2, L2 = G / 4;
+  rs_halve<9>(acc, r5, (sub & L1) != 0, L1, gmask);
+  rs_halve<5>(r5, r3, (sub & L2) != 0, L2, gmask);
+  int first = ((sub & L1) ? 5 : 0) + ((sub & L2) ? 3 : 0);  // entry of slot 0
+  int count = (sub & L1) ? ((sub & L2) ? 1 : 3) : ((sub & L2) ? 2 : 3);  // 9 = 5 + 4; 5 = 3 + 2; 4 = 3 + 1
+  constexpr int NS = G == 8 ? 2 : 3;
+  CT fin[NS];
+  if constexpr (G == 8) {
+    rs_halve<3>(r3, fin, (sub & 1) != 0, 1, gmask);
+    const bool up = (sub & 1) != 0;
+    first += up ? 2 : 0;
+    count = up ? max(count - 2, 0) : min(count, 2);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) fin[u] = r3[u];
+  }
+  const double inv_area_q = g.frame64[kFrame * (size_t)q + 24];
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+#pragma unroll
+  for (int u = 0; u < NS; ++u) {
+    if (u >= count) break;
+    const int e = first + u, i = e / 3, j = e - 3 * (e / 3);
+    const int ci = i == 0 ? ep.x : (i == 1 ? ep.y : ep.z), cj = j == 0 ? eq.x : (j == 1 ? eq.y : eq.z);
+    if (!edge_valid(ci) || !edge_valid(cj)) continue;
+    const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
+    const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
+    sink.add(edge_of(ci), edge_of(cj), -c * (double)fin[u].im, c * (double)fin[u].re);
+  }
+}
+
+inline int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+inline int64_t pair_grid(const GeoView& g, int blocks_per_sm) {
+  const int64_t ntask = regular_units(g.nt);
+  int64_t blocks = (ntask + kWarps - 1) / kWarps;
+  return std::min<int64_t>(blocks, (int64_t)sm_count() * blocks_per_sm);
+}
+}  // namespace
+}  // namespace gf

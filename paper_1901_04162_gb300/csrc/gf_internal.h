@@ -138,7 +138,8 @@ struct BatchItem {
   int64_t near_begin, n_near;     // first global near pair, near pairs
 };
 
-// ---------------------------------------------------------------- kernels (gf_kernels.cu)
+// ---------------------------------------------------------------- kernels (gf_fill.cu, gf_mfie.cu,
+// gf_adjoint.cu, gf_sparse_kernels.cu, gf_batch_kernels.cu; shared device code in gf_device.cuh)
 // Doubles per triangle of the near-pair source frames: unit normal [0..2],
 // edge lengths [3..5], unit edge tangents [6..14], in-plane edge normals [15..23].
 constexpr int kFrame = 25;    // FP64 source frame per triangle: n, len, t, m, 1/area
