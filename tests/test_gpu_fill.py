@@ -106,6 +106,19 @@ def test_near_dist_criterion_matches_oracle():
     assert rel_fro(z, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("rule", [4, 7])
+def test_near_dist_fp32_matches_oracle(rule):
+    # FP32 fill of a mesh with a centroid criterion (near pairs that share no
+    # vertex, up to 0.6 lambda apart): mixed-precision near pairs against the
+    # oracle and against FP64 near pairs (near_fp64 = 1)
+    wl = W.cube_73728(3)
+    _, z, _ = gpu_fill(wl.xyz, wl.tri, wl.k, rule, gf.GF_FP32, True, near_dist=0.6)
+    _, z64, _ = gpu_fill(wl.xyz, wl.tri, wl.k, rule, gf.GF_FP32, True, near_dist=0.6, near_fp64=1)
+    ref = oracle_full(wl.xyz, wl.tri, wl.k, rule, True, near_dist=0.6)
+    assert rel_fro(z, ref) <= 1e-5 and rel_max(z, ref) <= 1e-5
+    assert rel_fro(z, z64) <= 1e-5
+
+
 @pytest.mark.parametrize("near_fp64", [0, 1])
 def test_sphere_7680_sampled_rows(near_fp64):
     wl = W.sphere_7680()
