@@ -467,6 +467,7 @@ struct C2f {  // FP32 complex of the mixed-precision near-block assembly
 
 struct KScal {  // per-wavenumber scalars of the near-pair fill
   double k, scale, inv_k2, inv_k;
+  float q4f;  // 4 / k^2 in FP32 (the mixed-precision block assembly)
 };
 
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
@@ -583,15 +584,22 @@ __device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, boo
 // frame (normal, edge tangents, lengths, edge normals) is precomputed per
 // triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
 // and the static log term is one log of a ratio per edge.
-__device__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
+// The results leave in FP32 (the caller assembles the 3x3 block in FP32):
+// I0, I1 and dvq[j] = rho0 - v_j, the latter from the FP32 edge vectors
+// v_j - r formed here anyway (each FP64 <-> FP32 conversion costs an FP64
+// pipe slot, as much as an FP64 operation).
+__device__ __forceinline__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
                                       const float* __restrict__ fr32, const NearArgs& A, double k, double inv_k,
-                                      const Tab32& te, bool use_table, float lo, float hi, C2* I0, C2 I1[3],
-                                      double rho0[3]) {
+                                      const Tab32& te, bool use_table, float lo, float hi, C2f* I0, C2f I1[3],
+                                      float dvq[3][3]) {
   const float kpi = (float)(k / kPi), k32 = (float)k;
   const double n[3] = {fr[0], fr[1], fr[2]};
   const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
   const double d = fabs(h);
+  double rho0[3];
   for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  const float h32 = (float)h, nx32 = fr32[21], ny32 = fr32[22], nz32 = fr32[23];
+  float d0x = 0.f, d0y = 0.f, d0z = 0.f, d1x = 0.f, d1y = 0.f, d1z = 0.f, d2x = 0.f, d2y = 0.f, d2z = 0.f;
   // |r - v_c| (scalars, so that the edge loop picks them without a local array)
   double Rv0, Rv1, Rv2;
   {
@@ -639,6 +647,15 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
     }
     // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
     const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    // rho0 - v_e = (r - v_e) - h n (scalars: the edge loop is not unrolled)
+    const float ux = fmaf(-h32, nx32, -ax), uy = fmaf(-h32, ny32, -ay), uz = fmaf(-h32, nz32, -az);
+    if (e == 0) {
+      d0x = ux, d0y = uy, d0z = uz;
+    } else if (e == 1) {
+      d1x = ux, d1y = uy, d1z = uz;
+    } else {
+      d2x = ux, d2y = uy, d2z = uz;
+    }
     const float tx = fr32[3 + 3 * e], ty = fr32[4 + 3 * e], tz = fr32[5 + 3 * e];
     const float hl = 0.5f * fr32[e];
     float lr = 0.f, li = 0.f;
@@ -675,13 +692,16 @@ __device__ void inner_integrals_mixed(const double r[3], const double v[3][3], c
     vim[2] = fmaf(mz, li, vim[2]);
     for (int x = 0; x < 3; ++x) vst[x] += mh[x] * st;
   }
-  const double c4 = 1.0 / (4.0 * kPi), ikc4 = inv_k * c4;
+  dvq[0][0] = d0x, dvq[0][1] = d0y, dvq[0][2] = d0z;
+  dvq[1][0] = d1x, dvq[1][1] = d1y, dvq[1][2] = d1z;
+  dvq[2][0] = d2x, dvq[2][1] = d2y, dvq[2][2] = d2z;
+  const float c4 = (float)(1.0 / (4.0 * kPi)), ik = (float)inv_k, ikc4 = ik * c4;
   // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
-  I0->re = (double)sim * ikc4;
-  I0->im = -(double)sre * ikc4;
+  I0->re = sim * ikc4;
+  I0->im = -sre * ikc4;
   for (int x = 0; x < 3; ++x) {
-    I1[x].re = fma(-(double)vim[x], inv_k, vst[x]) * c4;
-    I1[x].im = (double)vre[x] * ikc4;
+    I1[x].re = fmaf(-vim[x], ik, (float)vst[x]) * c4;
+    I1[x].im = vre[x] * ikc4;
   }
 }
 
@@ -758,35 +778,53 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
     const double* cp = g.cen64 + 4 * (size_t)p;
     const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
     const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
-    C2 I0, I1[3];
-    double rho0[3];
-    if (MIXED)
-      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, g.frame32 + kFrame32 * (size_t)q, A, ks.k,
-                            ks.inv_k, te32, use_table, lo32, hi32, &I0, I1, rho0);
-    else inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
     // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
     // w_a / 4 folded into I0, I1
-    const RT w4 = (RT)(0.25 * al[3]);
-    const CT S = {w4 * (RT)I0.re, w4 * (RT)I0.im};
-    const CT T[3] = {{w4 * (RT)I1[0].re, w4 * (RT)I1[0].im},
-                     {w4 * (RT)I1[1].re, w4 * (RT)I1[1].im},
-                     {w4 * (RT)I1[2].re, w4 * (RT)I1[2].im}};
-    const RT q4 = (RT)(4.0 * ks.inv_k2);
-    const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
-    RT f[3][3];
+    CT S, T[3];
+    RT f[3][3], dvq[3][3], q4;
+    if constexpr (MIXED) {
+      C2f I0, I1[3];
+      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, g.frame32 + kFrame32 * (size_t)q, A, ks.k,
+                            ks.inv_k, te32, use_table, lo32, hi32, &I0, I1, dvq);
+      // r_a - v_i = alpha_a + delta_i from the FP32 offsets (no conversions)
+      const float4 alf = g.pts32[(size_t)sub * g.nt + p];
+      const float w4 = 0.25f * alf.w;
+      S = CT{w4 * I0.re, w4 * I0.im};
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
-      f[i][0] = (RT)(ra[0] - vpi[0]);
-      f[i][1] = (RT)(ra[1] - vpi[1]);
-      f[i][2] = (RT)(ra[2] - vpi[2]);
+      for (int x = 0; x < 3; ++x) T[x] = CT{w4 * I1[x].re, w4 * I1[x].im};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float4 dl = g.geo32[3 * (size_t)p + i];  // c_p - v_i
+        f[i][0] = alf.x + dl.x;
+        f[i][1] = alf.y + dl.y;
+        f[i][2] = alf.z + dl.z;
+      }
+      q4 = ks.q4f;
+    } else {
+      C2 I0, I1[3];
+      double rho0[3];
+      inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
+      const RT w4 = (RT)(0.25 * al[3]);
+      S = CT{w4 * (RT)I0.re, w4 * (RT)I0.im};
+#pragma unroll
+      for (int x = 0; x < 3; ++x) T[x] = CT{w4 * (RT)I1[x].re, w4 * (RT)I1[x].im};
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
+        for (int x = 0; x < 3; ++x) f[i][x] = (RT)(ra[x] - vpi[x]);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        for (int x = 0; x < 3; ++x) dvq[j][x] = (RT)(rho0[x] - vq[j][x]);
+      q4 = (RT)(4.0 * ks.inv_k2);
     }
+    const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       CT J[3];
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        const RT dv = (RT)(rho0[x] - vq[j][x]);
+        const RT dv = dvq[j][x];
         J[x].re = fma(dv, S.re, T[x].re);
         J[x].im = fma(dv, S.im, T[x].im);
       }
