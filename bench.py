@@ -45,7 +45,7 @@ FALLBACK_SM_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "041b7adc8bcfc433"): 297102336 + 256780032}
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "d7eee9cb6472f272"): 296933888 + 257481472}
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
