@@ -594,22 +594,19 @@ __device__ __forceinline__ void inner_integrals_mixed(const double r[3], const d
                                       float dvq[3][3]) {
   const float kpi = (float)(k / kPi), k32 = (float)k;
   const double n[3] = {fr[0], fr[1], fr[2]};
-  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+  // v_c - r, once (scalars, so that the edge loop picks them without a local
+  // array): the vertex distances, h, and the edge offsets below all use them
+  const double w0x = v[0][0] - r[0], w0y = v[0][1] - r[1], w0z = v[0][2] - r[2];
+  const double w1x = v[1][0] - r[0], w1y = v[1][1] - r[1], w1z = v[1][2] - r[2];
+  const double w2x = v[2][0] - r[0], w2y = v[2][1] - r[1], w2z = v[2][2] - r[2];
+  const double h = -(n[0] * w0x + n[1] * w0y + n[2] * w0z);
   const double d = fabs(h);
-  double rho0[3];
-  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
   const float h32 = (float)h, nx32 = fr32[21], ny32 = fr32[22], nz32 = fr32[23];
   float d0x = 0.f, d0y = 0.f, d0z = 0.f, d1x = 0.f, d1y = 0.f, d1z = 0.f, d2x = 0.f, d2y = 0.f, d2z = 0.f;
-  // |r - v_c| (scalars, so that the edge loop picks them without a local array)
-  double Rv0, Rv1, Rv2;
-  {
-    const double* w = v[0];
-    Rv0 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
-    w = v[1];
-    Rv1 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
-    w = v[2];
-    Rv2 = sqrt((w[0] - r[0]) * (w[0] - r[0]) + (w[1] - r[1]) * (w[1] - r[1]) + (w[2] - r[2]) * (w[2] - r[2]));
-  }
+  // |r - v_c|
+  const double Rv0 = sqrt(w0x * w0x + w0y * w0y + w0z * w0z);
+  const double Rv1 = sqrt(w1x * w1x + w1y * w1y + w1z * w1z);
+  const double Rv2 = sqrt(w2x * w2x + w2y * w2y + w2z * w2z);
   const float d32 = (float)d;
   const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
   // the sampled (dynamic) sums carry FP32 samples: FP32 accumulation; the
@@ -617,13 +614,14 @@ __device__ __forceinline__ void inner_integrals_mixed(const double r[3], const d
   float sre = 0.f, sim = 0.f, vre[3] = {0.f, 0.f, 0.f}, vim[3] = {0.f, 0.f, 0.f};
   double vst[3] = {0, 0, 0};
   for (int e = 0; e < 3; ++e) {
-    const double* a = v[e];
     const double len = fr[3 + e];
     const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
     const double mh[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
-    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
-    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+    // v_e - r; its in-plane part v_e - rho0 differs by h n, normal to t and mh
+    const double arx = e == 0 ? w0x : (e == 1 ? w1x : w2x), ary = e == 0 ? w0y : (e == 1 ? w1y : w2y),
+                 arz = e == 0 ? w0z : (e == 1 ? w1z : w2z);
+    const double P0 = arx * mh[0] + ary * mh[1] + arz * mh[2];
+    const double lm = arx * t[0] + ary * t[1] + arz * t[2];
     const double lp = lm + len;
     if (fabs(P0) > 1e-12 * len) {
       const float aP32 = (float)fabs(P0);
@@ -646,7 +644,7 @@ __device__ __forceinline__ void inner_integrals_mixed(const double r[3], const d
       sim = fmaf(ci, sg, sim);
     }
     // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
-    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+    const float ax = (float)arx, ay = (float)ary, az = (float)arz;
     // rho0 - v_e = (r - v_e) - h n (scalars: the edge loop is not unrolled)
     const float ux = fmaf(-h32, nx32, -ax), uy = fmaf(-h32, ny32, -ay), uz = fmaf(-h32, nz32, -az);
     if (e == 0) {
