@@ -352,23 +352,29 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
       const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
       const double r[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
       const double n[3] = {fr[0], fr[1], fr[2]};
-      const double h = p == q ? 0.0 : n[0] * (r[0] - v[0]) + n[1] * (r[1] - v[1]) + n[2] * (r[2] - v[2]);
+      // v_c - r and |v_c - r|, once (scalars: the edge loop picks them by e)
+      const double w0x = v[0] - r[0], w0y = v[1] - r[1], w0z = v[2] - r[2];
+      const double w1x = v[3] - r[0], w1y = v[4] - r[1], w1z = v[5] - r[2];
+      const double w2x = v[6] - r[0], w2y = v[7] - r[1], w2z = v[8] - r[2];
+      const double Rv0 = sqrt(w0x * w0x + w0y * w0y + w0z * w0z), Rv1 = sqrt(w1x * w1x + w1y * w1y + w1z * w1z),
+                   Rv2 = sqrt(w2x * w2x + w2y * w2y + w2z * w2z);
+      const double h = p == q ? 0.0 : -(n[0] * w0x + n[1] * w0y + n[2] * w0z);
       const double d = fabs(h), sgh = h > 0 ? 1.0 : (h < 0 ? -1.0 : 0.0);
       const double rho0[3] = {r[0] - h * n[0], r[1] - h * n[1], r[2] - h * n[2]};
       const C2 ed = exp_mjkr(k, d, &te, use_table);
       double Iu[3][2] = {}, hI0[2] = {0, 0};
       for (int e = 0; e < 3; ++e) {
         const double* a = v + 3 * e;
-        const double* b = v + 3 * ((e + 1) % 3);
         const double le = fr[3 + e];
         const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
         const double m[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
-        const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-        const double P0 = ar[0] * m[0] + ar[1] * m[1] + ar[2] * m[2];
-        const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
+        // a - r; its in-plane part a - rho0 differs by h n, normal to t and m
+        const double arx = e == 0 ? w0x : (e == 1 ? w1x : w2x), ary = e == 0 ? w0y : (e == 1 ? w1y : w2y),
+                     arz = e == 0 ? w0z : (e == 1 ? w1z : w2z);
+        const double P0 = arx * m[0] + ary * m[1] + arz * m[2];
+        const double lm = arx * t[0] + ary * t[1] + arz * t[2];
         const double lp = lm + le;
-        const double Rm = sqrt((r[0] - a[0]) * (r[0] - a[0]) + (r[1] - a[1]) * (r[1] - a[1]) + (r[2] - a[2]) * (r[2] - a[2]));
-        const double Rp = sqrt((r[0] - b[0]) * (r[0] - b[0]) + (r[1] - b[1]) * (r[1] - b[1]) + (r[2] - b[2]) * (r[2] - b[2]));
+        const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
         const double R02 = P0 * P0 + d * d;
         double ratio;
         if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
@@ -377,7 +383,7 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
         double lr = log(ratio), li = 0.0;
         if (MIXED) {
           const float* f32 = g.frame32 + kFrame32 * (size_t)q;
-          const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
+          const float ax = (float)arx, ay = (float)ary, az = (float)arz;
           const float tx = f32[3 + 3 * e], ty = f32[4 + 3 * e], tz = f32[5 + 3 * e], hl = 0.5f * f32[e];
           float sr = 0.f, si = 0.f;
           for (int i = 0; i < A.nl; ++i) {
@@ -449,15 +455,8 @@ __global__ void __launch_bounds__(128) k_mfie_near(GeoView g, TabView te, bool u
         }
       }
       if (h != 0.0) {  // static part of h I_0: -Omega / (4 pi)
-        double R1[3], R2[3], R3[3];
-        for (int x = 0; x < 3; ++x) {
-          R1[x] = v[x] - r[x];
-          R2[x] = v[3 + x] - r[x];
-          R3[x] = v[6 + x] - r[x];
-        }
-        const double n1 = sqrt(R1[0] * R1[0] + R1[1] * R1[1] + R1[2] * R1[2]);
-        const double n2 = sqrt(R2[0] * R2[0] + R2[1] * R2[1] + R2[2] * R2[2]);
-        const double n3 = sqrt(R3[0] * R3[0] + R3[1] * R3[1] + R3[2] * R3[2]);
+        const double R1[3] = {w0x, w0y, w0z}, R2[3] = {w1x, w1y, w1z}, R3[3] = {w2x, w2y, w2z};
+        const double n1 = Rv0, n2 = Rv1, n3 = Rv2;
         const double num = R1[0] * (R2[1] * R3[2] - R2[2] * R3[1]) + R1[1] * (R2[2] * R3[0] - R2[0] * R3[2]) +
                            R1[2] * (R2[0] * R3[1] - R2[1] * R3[0]);
         const double den = n1 * n2 * n3 + (R1[0] * R2[0] + R1[1] * R2[1] + R1[2] * R2[2]) * n3 +
