@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128) k_batch_near(const BatchItem* __restrict_
       const BatchItem& it = items[batch_item_of(items, nitems, t, true)];
       const Tab32 te32 = tab32(it.exp);
       near_task<float2, MIXED>(it.g, it.exp, te32, (float)it.exp.r_lo, (float)it.exp.r_hi, it.use_table != 0, A,
-                               KScal{it.k, it.scale, it.inv_k2, 1.0 / it.k, (float)(4.0 * it.inv_k2)}, reinterpret_cast<float2*>(it.Z), it.ldz, it.n_near,
+                               KScal{it.k, it.scale, it.inv_k2, 1.0 / it.k, (float)(4.0 * it.inv_k2), (float)it.scale}, reinterpret_cast<float2*>(it.Z), it.ldz, it.n_near,
                                t - it.near_begin, true, sub, gmask);
     }
   }

@@ -287,6 +287,10 @@ struct CsrSink {
     const int64_t i = find(m, n);
     if (i >= 0) atomicAdd(reinterpret_cast<float2*>(vals + i), v);
   }
+  __device__ __forceinline__ void add32(int m, int n, float zr, float zi) const {  // FP32 values only
+    const int64_t i = find(m, n);
+    if (i >= 0) atomicAdd(reinterpret_cast<float2*>(vals + i), make_float2(zr, zi));
+  }
   __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
     const int64_t i = find(m, n);
     if (i < 0) return;
@@ -467,7 +471,8 @@ struct C2f {  // FP32 complex of the mixed-precision near-block assembly
 
 struct KScal {  // per-wavenumber scalars of the near-pair fill
   double k, scale, inv_k2, inv_k;
-  float q4f;  // 4 / k^2 in FP32 (the mixed-precision block assembly)
+  float q4f;      // 4 / k^2 in FP32 (the mixed-precision block assembly)
+  float scale32;  // k eta in FP32 (the mixed-precision output stage)
 };
 
 __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
@@ -739,6 +744,9 @@ struct DenseOut {  // Z[m][n] += z (row-major, ld = ldz)
       atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
     }
   }
+  __device__ __forceinline__ void add32(int m, int n, float zr, float zi) const {  // FP32 Z only
+    atomicAdd(reinterpret_cast<float2*>(Z + (int64_t)m * ldz + n), make_float2(zr, zi));
+  }
 };
 
 template <bool MIXED, int G, class Sink>
@@ -851,7 +859,8 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
 #pragma unroll
     for (int u = 0; u < 3; ++u) fin[u] = r3[u];
   }
-  const double inv_area_q = g.frame64[kFrame * (size_t)q + 24];
+  const double inv_area_q = MIXED ? 0.0 : g.frame64[kFrame * (size_t)q + 24];
+  const float inv_area32 = MIXED ? __frcp_rn(g.cen32[q].w) : 0.f;
   const int4 ep = g.tedge[p], eq = g.tedge[q];
 #pragma unroll
   for (int u = 0; u < NS; ++u) {
@@ -859,9 +868,14 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
     const int e = first + u, i = e / 3, j = e - 3 * (e / 3);
     const int ci = i == 0 ? ep.x : (i == 1 ? ep.y : ep.z), cj = j == 0 ? eq.x : (j == 1 ? eq.y : eq.z);
     if (!edge_valid(ci) || !edge_valid(cj)) continue;
-    const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
-    const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
-    sink.add(edge_of(ci), edge_of(cj), -c * (double)fin[u].im, c * (double)fin[u].re);
+    if constexpr (MIXED) {  // FP32 output: no conversions on the FP64 pipe
+      const float c = ks.scale32 * g.geo32[3 * (size_t)p + i].w * g.geo32[3 * (size_t)q + j].w * inv_area32;
+      sink.add32(edge_of(ci), edge_of(cj), -c * (float)fin[u].im, c * (float)fin[u].re);
+    } else {
+      const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
+      const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
+      sink.add(edge_of(ci), edge_of(cj), -c * (double)fin[u].im, c * (double)fin[u].re);
+    }
   }
 }
 

@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(128) k_fill_near(GeoView g, TabView te, bool u
   const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
   const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
-  const KScal ks{A.k, A.scale, A.inv_k2, 1.0 / A.k, (float)(4.0 * A.inv_k2)};
+  const KScal ks{A.k, A.scale, A.inv_k2, 1.0 / A.k, (float)(4.0 * A.inv_k2), (float)A.scale};
   for (int64_t it = 0; it < iters; ++it) {
     const int64_t idx = g0 + it * ngroups;
     near_task<Out, MIXED, G>(g, te, te32, lo32, hi32, use_table, A, ks, Z, ldz, n_near, idx, idx < n_near, sub, gmask);
