@@ -45,7 +45,7 @@ FALLBACK_SM_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "4368da46df97c4c7"): 296850176 + 257120256}
+TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "c37c83d3a8b42f44"): 296839680 + 256931328}
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
