@@ -1,10 +1,12 @@
 #!/usr/bin/env python
 """Benchmark of the EFIE impedance-matrix fill with the adaptive Green table.
 
-Default workload: PEC sphere r = 1 lambda, icosphere with 5120 triangles
-(7680 RWG unknowns), vertices jittered by 2% of the mean edge length, 7-point
-rule on both triangles, FP32 table fill with Kahan outer sums, FP64 near
-terms, table tolerance 1e-6. Synthetic, seeded input.
+Default workload: PEC cube of side 3 lambda, 64 x 64 squares per face split
+into triangles (49152 triangles, 73728 RWG unknowns), 4-point rule on both
+triangles, near pairs = shared vertex or centroids closer than 0.2 lambda,
+FP32 table fill with Kahan outer sums into a 43.5 GB complex64 Z, table
+tolerance 1e-6. Synthetic, seeded input. `--workload sphere_7680` gives the
+1 lambda sphere (5120 triangles, 7680 RWG, 7-point rule).
 
 One step = the whole hot path on a device-resident mesh: R_min/R_max
 reduction, Green + Exp table construction, zeroing Z, the regular-pair fill
@@ -39,13 +41,29 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
 SMEM_BYTES_PER_CLK = 128  # shared-memory bandwidth per SM (32 banks x 4 B)
-SMEM_BYTES_PER_EVAL = 32  # Lagrange lattice: two 16-byte records per Green evaluation
 FALLBACK_SM_MHZ = 2070.0
+# Algorithmic FP32 lane operations per regular Green evaluation (the op model of
+# the roofline): distance 7 (3 differences, 3 squares / FMAs, R = R^2 rsqrt),
+# lookup and polynomial 10 (cell FFMA, conversion-free rint, anchor, offset,
+# Horner), moment accumulation 8 (M0 and the three beta-weighted moments, complex).
+OPS_PER_EVAL = 25
+# Shared-memory reads of the FP32 lattice per Green evaluation, as
+# (bytes, vector width in bytes) per read: the Lagrange record is a 16-byte
+# read of (c0, c1) and a 16-byte read of (c2, c3).
+SMEM_READS = ((16, 16), (16, 16))
+# Expected shared-memory wavefronts of one warp-wide read at independent random
+# addresses: lanes are served in phases of 128 bytes (8 lanes for 16-byte reads,
+# 16 for 8-byte, 32 for 4-byte), and a phase takes as many wavefronts as the
+# largest number of distinct addresses that fall on one bank group (the
+# expected maximum load of 8 balls in 8 bins, 16 in 16, 32 in 32).
+RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
 # table kernel, from the ncu capture summarised in profiles/; valid only while
 # the kernel source hash matches.
 TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "c37c83d3a8b42f44"): 296839680 + 256931328}
+TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
+                "(ncu, --clock-control none); null when the kernel sources changed since the capture")
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
@@ -82,6 +100,20 @@ WORKLOADS = {
 }
 
 
+def smem_model(evals, ms, mhz):
+    """Shared-memory side of the table kernel: bytes per evaluation, the
+    wavefronts a warp evaluation costs at random addresses, and the time those
+    wavefronts take at one wavefront per clock per SM."""
+    wf = sum(RANDOM_WAVEFRONTS[w] for _, w in SMEM_READS)
+    t_wf = evals / 32 * wf / (SM_COUNT * mhz * 1e6)
+    return {"bytes_per_eval": sum(b for b, _ in SMEM_READS),
+            "random_wavefronts_per_warp_eval": wf,
+            "conflict_free_wavefronts_per_warp_eval": sum(b * 32 / 128 for b, _ in SMEM_READS),
+            "wavefront_time_ms": t_wf * 1e3, "frac_of_kernel_time": t_wf / (ms / 1e3),
+            "note": "one wavefront per clock per SM; random lattice cells make bank conflicts (model: "
+                    "expected largest bank-group load per 128-byte phase)"}
+
+
 def regular_ops_per_pair(m):
     """FP32 lane operations of the algorithm per evaluated regular triangle
     pair (each unordered pair {p, q} is evaluated once and its 3 x 3 block is
@@ -99,7 +131,7 @@ def evaluated_pairs(nt, n_near):
 
 # ----------------------------------------------------------------------------
 class Clocks:
-    """nvidia-smi sampler (200 ms) for the timed region."""
+    """nvidia-smi sampler (100 ms) for the timed region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -113,7 +145,7 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -162,48 +194,114 @@ def peaks():
 
 
 # ----------------------------------------------------------------------------
-def oracle_baseline(wl, target_s=12.0, reference=False):
-    """The FP64 CPU oracle as it stands on the host cores: range reduction,
-    tables and a sample of Z rows; returns seconds per full fill projected
-    from the sample, and a description."""
-    import oracle as O
-    om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
-    t0 = time.perf_counter()
-    lo, hi = om.range(wl.rule, prune=len(wl.tri) > 10000)
-    t_range = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    tabs = O.make_tables(wl.k, lo, hi)
-    t_table = time.perf_counter() - t0
-    rng = np.random.default_rng(123)
-    rows = 1
-    t0 = time.perf_counter()
-    om.z_rows(wl.k, wl.rule, rng.choice(om.ne, rows, replace=False), mode="table", tables=tabs)
-    t1 = time.perf_counter() - t0
-    rows = int(max(1, min(om.ne, round(target_s / max(t1, 1e-3)))))
-    sel = rng.choice(om.ne, rows, replace=False)
-    t0 = time.perf_counter()
-    om.z_rows(wl.k, wl.rule, sel, mode="table", tables=tabs)
-    t_rows = time.perf_counter() - t0
-    t_full = t_range + t_table + t_rows * om.ne / rows
+def cpu_model():
+    """Host CPU model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def panel_rows(ne, seed=256, size=256):
+    """The rows of one seeded panel of `size` consecutive RWG unknowns."""
+    npan = max(1, ne // size)
+    p = int(np.random.default_rng(seed).integers(npan))
+    return np.arange(p * size, min(ne, (p + 1) * size))
+
+
+class OracleRun:
+    """The FP64 CPU oracle as it stands (table mode) on one workload: its
+    range reduction and tables once, then timed samples of Z rows."""
+
+    def __init__(self, wl):
+        import oracle as O
+        self.O = O
+        self.wl = wl
+        self.om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
+        self.ne = self.om.ne
+        t0 = time.perf_counter()
+        self.lo, self.hi = self.om.range(wl.rule, prune=len(wl.tri) > 10000)
+        self.t_range = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.tabs = O.make_tables(wl.k, self.lo, self.hi)
+        self.t_tables = time.perf_counter() - t0
+
+    def rows(self, rows, nthreads=0):
+        """Seconds to compute the given Z rows."""
+        rows = np.asarray(rows)
+        t0 = time.perf_counter()
+        self.om.z_rows(self.wl.k, self.wl.rule, rows, mode="table", tables=self.tabs, nthreads=nthreads)
+        return time.perf_counter() - t0
+
+    def sized_rows(self, panel, target_s, nthreads=0):
+        """A prefix of `panel` sized to about target_s seconds (one row timed first)."""
+        t1 = self.rows(panel[:1], nthreads)
+        n = int(max(1, min(len(panel), round(target_s / max(t1, 1e-4)))))
+        return panel[:n]
+
+
+def oracle_baseline(wl, target_s=8.0, run=None):
+    """CPU baseline: the oracle (table mode) on the host cores, on rows of a
+    seeded 256-row panel, one thread and all threads; entries/s extrapolated
+    to the full matrix (range reduction and tables timed once on all
+    threads)."""
+    run = run or OracleRun(wl)
+    panel = panel_rows(run.ne)
     cores = os.cpu_count()
-    desc = (f"oracle table-mode fill: full R range ({t_range:.2f} s) + tables ({t_table:.3f} s) + "
-            f"{rows} of {om.ne} Z rows ({t_rows:.2f} s), projected to the full matrix; "
-            f"OpenMP over Z entries on {cores} threads")
-    return t_full, desc, cores, om.ne
+    r1 = run.sized_rows(panel, target_s / 2, nthreads=1)
+    t1 = run.rows(r1, nthreads=1)
+    ra = run.sized_rows(panel, target_s, nthreads=0)
+    ta = run.rows(ra, nthreads=0)
+    rate1 = len(r1) * run.ne / t1
+    ratea = len(ra) * run.ne / ta
+    setup = run.t_range + run.t_tables
+    full_a = setup + run.ne * run.ne / ratea
+    full_1 = setup + run.ne * run.ne / rate1
+    desc = (f"extrapolated: oracle table-mode Z rows of the seeded 256-row panel starting at row {panel[0]} "
+            f"({len(ra)} rows on {cores} threads in {ta:.2f} s; {len(r1)} rows on 1 thread in {t1:.2f} s), "
+            f"scaled by entry count to all {run.ne} rows, plus the full range reduction ({run.t_range:.2f} s) "
+            f"and tables ({run.t_tables:.3f} s) on {cores} threads; CPU: {cpu_model()}")
+    out = {"value": run.ne * run.ne / full_a, "unit": "Z entries/s", "cores": cores, "kind": "oracle",
+           "sample": desc, "cpu_model": cpu_model(),
+           "single_thread": {"value": run.ne * run.ne / full_1, "unit": "Z entries/s", "cores": 1,
+                             "rows": int(len(r1)), "rows_s": t1},
+           "all_threads_rows": int(len(ra)), "all_threads_rows_s": ta,
+           "setup_s": {"range": run.t_range, "tables": run.t_tables}}
+    return out
 
 
 # ----------------------------------------------------------------------------
 def run_reference(args, wl, rank):
+    """The oracle as the reference arm: each step computes a bounded sample of
+    Z rows (a seeded 256-row panel) on all host threads; the value is the
+    sample's entries over its measured time. The range and tables are built
+    once before the steps (their time is reported)."""
     if rank != 0:
         return
+    run = OracleRun(wl)
+    panel = panel_rows(run.ne)
+    rows = run.sized_rows(panel, args.ref_seconds)
     times = []
-    desc = cores = ne = None
     for i in range(args.warmup + args.steps):
-        t_full, desc, cores, ne = oracle_baseline(wl, target_s=args.ref_seconds, reference=True)
+        t = run.rows(rows)
         if i >= args.warmup:
-            times.append(t_full)
+            times.append(t)
     t = statistics.median(times)
-    value = ne * ne / t
+    value = len(rows) * run.ne / t
+    cores = os.cpu_count()
+    desc = (f"oracle table-mode fill of {len(rows)} Z rows ({len(rows) * run.ne} entries) of the seeded "
+            f"256-row panel at row {panel[0]} per step, on {cores} threads; range reduction "
+            f"({run.t_range:.2f} s) and tables ({run.t_tables:.3f} s) once before the steps; CPU: {cpu_model()}")
     line = {"impl": "reference", "metric": "Z entries/s (table fill)", "value": value, "unit": "Z entries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -215,6 +313,42 @@ def run_reference(args, wl, rank):
 
 
 # ----------------------------------------------------------------------------
+def sample_blocks(ne, count=64, size=256, seed=64):
+    """`count` seeded (row block, column block) pairs of size x size blocks;
+    the whole matrix as one block when it is small."""
+    if ne <= 4 * size:
+        return [(0, 0)], ne
+    nb = ne // size
+    rng = np.random.default_rng(seed)
+    return [(int(i), int(j)) for i, j in zip(rng.integers(nb, size=count), rng.integers(nb, size=count))], size
+
+
+def gather_blocks(torch, Z, blocks, size):
+    return np.stack([Z[i * size:(i + 1) * size, j * size:(j + 1) * size].cpu().numpy() for i, j in blocks])
+
+
+def oracle_blocks(run, blocks, size, mode):
+    ii = np.arange(size)
+    mi = np.concatenate([np.repeat(i * size + ii, size) for i, _ in blocks])
+    ni = np.concatenate([np.tile(j * size + ii, size) for _, j in blocks])
+    kw = {"mode": "table", "tables": run.tabs} if mode == "table" else {}
+    z = run.om.z_entries(run.wl.k, run.wl.rule, mi, ni, **kw)
+    return z.reshape(len(blocks), size, size)
+
+
+def err_stats(z, ref, floor=1e-3):
+    """Relative Frobenius error, max |error| / max |ref|, and the per-entry
+    relative error |z - ref| / |ref| over entries with |ref| >= floor * max|ref|."""
+    d = np.abs(z - ref)
+    a = np.abs(ref)
+    big = a >= floor * a.max()
+    rel = d[big] / a[big]
+    return {"rel_fro": float(np.linalg.norm(z - ref) / np.linalg.norm(ref)),
+            "max_abs_err_over_max_abs_ref": float(d.max() / a.max()),
+            "entry_rel_max": float(rel.max()), "entry_rel_p999": float(np.quantile(rel, 0.999)),
+            "entry_floor": f"|ref| >= {floor:g} max|ref| ({int(big.sum())} of {big.size} entries)"}
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
 
@@ -237,7 +371,8 @@ def run_ours(args, wl, rank, world, local_rank):
     mesh = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
     ne, nt, n_near = mesh.ne, mesh.nt, mesh.n_near
     Z = torch.empty((ne, ne), dtype=zdt, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    zbytes = Z.numel() * Z.element_size()
+    flush = None if zbytes > (1 << 30) else torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2
     # clear, pair kernel, mirror (Z += Z^T), near kernel: events between them
     parts = (gf.GF_PART_ZERO, gf.GF_PART_PAIRS, gf.GF_PART_MIRROR, gf.GF_PART_NEAR)
 
@@ -269,7 +404,8 @@ def run_ours(args, wl, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(steps):
-            flush.fill_(i & 0xFF)  # evict Z and the geometry from L2 between steps
+            if flush is not None:
+                flush.fill_(i & 0xFF)  # evict Z and the geometry from L2 between steps
             keep.append(step(direct, evs[i], params))
         torch.cuda.synchronize()
         barrier()
@@ -283,60 +419,93 @@ def run_ours(args, wl, rank, world, local_rank):
         return {"step_ms": st, "regular_ms": reg, "mirror_ms": mir, "near_ms": near, "range_table_ms": pre,
                 "wall_s": wall}
 
+    def spread(x):
+        return {"mean": statistics.mean(x), "min": min(x), "max": max(x)}
+
+    def reduce_max(x):
+        return reduce_max_over_ranks(x, dist, dev)
+
     # ---- table path (the method) with clocks sampled in the timed region
     with Clocks(local_rank) as clk:
         tt = timed(False, args.steps, args.warmup)
     clocks = clk.summary()
-    td = timed(True, args.steps, args.warmup)
+    with Clocks(local_rank) as clkd:
+        td = timed(True, args.steps, args.warmup)
+    clocks_direct = clkd.summary()
     px = gf.gf_params_default(rule=wl.rule, green_from_exp=1)
     tx = timed(False, args.steps, args.warmup, px)
     p64 = gf.gf_params_default(rule=wl.rule, near_fp64=1)
-    t64 = timed(False, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
-    d64 = timed(True, max(2, args.steps // 2), 1, p64) if prec == gf.GF_FP32 else None
-
-    def reduce_max(x):
-        return reduce_max_over_ranks(x, dist, dev)
+    n64 = max(3, args.steps // 2)
+    t64 = timed(False, n64, 1, p64) if prec == gf.GF_FP32 else None
+    d64 = timed(True, n64, 1, p64) if prec == gf.GF_FP32 else None
 
     total_ms = reduce_max(sum(tt["step_ms"]))
     ms_step = total_ms / args.steps
     value = job_throughput(world, ne * ne * args.steps, total_ms / 1e3)
     direct_ms = reduce_max(sum(td["step_ms"])) / args.steps
 
-    # ---- end to end: host arrays in, host copy of Z out, through the C ABI
-    big = Z.numel() * Z.element_size() > (8 << 30)
-    zhost = torch.empty((1, 1) if big else (ne, ne), dtype=zdt, pin_memory=True)
-    e2e = []
-    for i in range(0 if big else args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        m2 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
-        lo, hi = m2.range(wl.rule, prec)
-        gf.gf_fill_parts(m2.h, wl.k, p, None, prec, Z, gf.GF_PART_ZERO)  # overlaps the host table stage
-        tab = gf.Table(wl.k, lo, hi, p)
-        gf.gf_fill_parts(m2.h, wl.k, p, tab.h, prec, Z, gf.GF_PART_REGULAR | gf.GF_PART_NEAR)
-        zhost.copy_(Z, non_blocking=True)
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            e2e.append(time.perf_counter() - t0)
-        del tab, m2
-    e2e_s = reduce_max(statistics.median(e2e)) if e2e else None
-    h2d = wl.xyz.nbytes + wl.tri.nbytes
-    d2h = Z.numel() * Z.element_size()
+    # ---- end to end through the C ABI: host arrays in (mesh creation, range,
+    # tables, fill) and the whole Z copied to page-locked host memory, per step
+    e2e = {"value": None}
+    zhost = None
+    host_bytes = 0
+    try:
+        avail = int(next(ln.split()[1] for ln in open("/proc/meminfo") if ln.startswith("MemAvailable"))) * 1024
+    except (OSError, StopIteration, ValueError):
+        avail = 0
+    # every rank copies its own Z: all of them need the room, or none times e2e
+    fits = zbytes * 1.3 * world + (8 << 30) < avail
+    if reduce_max(0.0 if fits else 1.0) == 0.0:
+        host = np.empty(ne * ne, dtype=np.complex64 if prec == gf.GF_FP32 else np.complex128)
+        host.view(np.uint8)[:: 1 << 16] = 0  # touch every page before registering
+        rc = torch.cuda.cudart().cudaHostRegister(host.ctypes.data, zbytes, 0)
+        if int(rc) == 0:
+            zhost = torch.from_numpy(host).view(ne, ne)
+            host_bytes = zbytes
+        else:
+            e2e["reason"] = f"cudaHostRegister of {zbytes} bytes returned {int(rc)}"
+    else:
+        e2e["reason"] = f"host memory: {avail} bytes available for {world} x {zbytes}-byte Z copies"
+    if reduce_max(0.0 if zhost is not None else 1.0) != 0.0:
+        zhost = None
+    if zhost is not None:
+        times = []
+        n_e2e = args.steps if zbytes < (4 << 30) else min(args.steps, 5)
+        for i in range(args.warmup + n_e2e if zbytes < (4 << 30) else 1 + n_e2e):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+            lo, hi = m2.range(wl.rule, prec)
+            gf.gf_fill_parts(m2.h, wl.k, p, None, prec, Z, gf.GF_PART_ZERO)  # overlaps the host table stage
+            tab = gf.Table(wl.k, lo, hi, p)
+            gf.gf_fill_parts(m2.h, wl.k, p, tab.h, prec, Z, gf.GF_PART_REGULAR | gf.GF_PART_NEAR)
+            zhost.copy_(Z, non_blocking=True)
+            torch.cuda.synchronize()
+            if i >= (args.warmup if zbytes < (4 << 30) else 1):
+                times.append(time.perf_counter() - t0)
+            del tab, m2
+        e2e_s = reduce_max(statistics.median(times))
+        e2e = {"value": world * ne * ne / e2e_s, "unit": "Z entries/s",
+               "h2d_bytes_per_step": wl.xyz.nbytes + wl.tri.nbytes, "d2h_bytes_per_step": zbytes,
+               "ms_per_step": e2e_s * 1e3, "steps": len(times),
+               "path": "host xyz/tri -> gf_mesh_create -> gf_range -> gf_table_create -> gf_fill_parts -> "
+                       "cudaMemcpyAsync of all of Z to page-locked (registered) host memory"}
 
     # ---- roofline of the regular-pair kernel (table), CUDA events on its stream
     m = wl.rule
     n_regular = nt * nt - n_near
     n_eval = evaluated_pairs(nt, n_near)
+    evals_regular = n_eval * m * m
+    evals_near = n_near * m * (3 * (p.nphi + p.nl) + 1)
     reg_ms = statistics.mean(tt["regular_ms"])
-    ops = n_eval * regular_ops_per_pair(m)
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    ops = evals_regular * OPS_PER_EVAL
     achieved = ops / (reg_ms / 1e3) / 1e12
-    khash = kernel_source_hash()
-    traffic = TRAFFIC.get((wl.name, khash))
-    evals_regular = n_eval * m * m
-    evals_near = n_near * m * (3 * (p.nphi + p.nl) + 1)
+    traffic = TRAFFIC.get((wl.name, kernel_source_hash()))
+    mhz = clocks.get("sm_mhz") or sm_mhz
+    mhz_d = clocks_direct.get("sm_mhz") or sm_mhz
 
     line = {
         "metric": "Z entries/s (table fill)", "value": value, "unit": "Z entries/s", "n_gpus": world,
@@ -344,21 +513,38 @@ def run_ours(args, wl, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == gf.GF_FP32 else "f64",
         "data": "synthetic",
         "config": {"workload": wl.name, "triangles": nt, "rwg_unknowns": ne, "rule_points": m, "k": wl.k,
+                   "near_criterion": (f"shared vertex or centroid distance < {wl.near_dist} lambda"
+                                      if wl.near_dist > 0 else "shared vertex"),
                    "table_tol": p.table_tol, "near_pairs": n_near, "regular_pairs": n_regular,
-                   "regular_pairs_evaluated": n_eval, "precision": "fp32 regular (Kahan outer sums), fp64 near" if prec == gf.GF_FP32 else "fp64",
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
+                   "regular_pairs_evaluated": n_eval, "z_bytes": zbytes,
+                   "precision": ("fp32 regular pairs (Kahan outer sums); mixed near pairs (near_fp64=0: FP64 "
+                                 "geometry, projections and closed-form static parts, FP32 sampling of e^-jkR "
+                                 "on the source edges and FP32 3x3 assembly); the all-FP64 near variant is "
+                                 "near_fp64_variant" if prec == gf.GF_FP32 else "fp64 throughout"),
+                   "l2": ("inputs larger than L2: Z is written every step" if flush is None
+                          else "flushed between steps (256 MiB write)"),
+                   "parallelism": f"replicas x{world}"},
         "green_evals_per_s": world * (evals_regular + evals_near) * args.steps / (total_ms / 1e3),
+        "green_evals": {"regular_per_step": evals_regular, "near_per_step": evals_near},
         "step_breakdown_ms": {"range_tables_and_zero": statistics.mean(tt["range_table_ms"]),
                               "regular_kernel": reg_ms, "mirror_z_plus_zt": statistics.mean(tt["mirror_ms"]),
                               "near_kernel": statistics.mean(tt["near_ms"])},
+        "spread_ms": {"table_step": spread(tt["step_ms"]), "table_regular": spread(tt["regular_ms"]),
+                      "direct_step": spread(td["step_ms"]), "direct_regular": spread(td["regular_ms"])},
+        "clock_normalised": {"table_regular_ms_x_mhz": reg_ms * mhz,
+                             "direct_regular_ms_x_mhz": statistics.mean(td["regular_ms"]) * mhz_d,
+                             "table_sm_mhz": mhz, "direct_sm_mhz": mhz_d},
         "direct": {"value": world * ne * ne / (direct_ms / 1e3), "unit": "Z entries/s", "ms_per_step": direct_ms,
                    "regular_kernel_ms": statistics.mean(td["regular_ms"]),
                    "mirror_ms": statistics.mean(td["mirror_ms"]),
-                   "near_kernel_ms": statistics.mean(td["near_ms"])},
+                   "near_kernel_ms": statistics.mean(td["near_ms"]), "clocks": clocks_direct},
         "near_fp64_variant": None if t64 is None else {
-            "ms_per_step": statistics.mean(t64["step_ms"]), "near_kernel_ms": statistics.mean(t64["near_ms"]),
+            "ms_per_step": statistics.mean(t64["step_ms"]), "value": ne * ne / (statistics.mean(t64["step_ms"]) / 1e3),
+            "near_kernel_ms": statistics.mean(t64["near_ms"]),
+            "direct_ms_per_step": statistics.mean(d64["step_ms"]),
             "direct_near_kernel_ms": statistics.mean(d64["near_ms"]),
-            "note": "near pairs sampled in FP64 too (near_fp64=1)"},
+            "note": "near pairs in FP64 throughout (near_fp64=1): the configuration's 'FP64 near-singular "
+                    "correction' as written"},
         "exp_over_r_variant": {
             "ms_per_step": statistics.mean(tx["step_ms"]), "regular_kernel_ms": statistics.mean(tx["regular_ms"]),
             "range_tables_and_zero_ms": statistics.mean(tx["range_table_ms"]),
@@ -370,55 +556,54 @@ def run_ours(args, wl, rank, world, local_rank):
                                     "near_kernel": statistics.mean(td["near_ms"]) / statistics.mean(tt["near_ms"])},
         "roofline": {"kernel": "k_fill_regular32<table>", "bound": "alu", "achieved": achieved,
                      "peak": peak_tops, "unit": "Tops/s (FP32 lane ops)", "frac": achieved / peak_tops,
+                     "op_model": f"{OPS_PER_EVAL} FP32 lane operations per regular Green evaluation "
+                                 "(distance 7, lookup and polynomial 10, moment accumulation 8); per-point "
+                                 "Kahan updates and the per-pair 3x3 block not counted",
                      "peak_source": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
                                     f"({src} max SM clock)",
-                     "ops_per_launch": ops, "traffic": traffic,
-                     "mufu_frac": n_eval * m * m / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6),
-                     # the resource that binds the table kernel (see profiles/): shared-memory reads of
-                     # the lattice image, 32 B per evaluation (two 16-byte records at random addresses)
-                     "smem": {"bytes_per_eval": SMEM_BYTES_PER_EVAL,
-                              "achieved_tbs": n_eval * m * m * SMEM_BYTES_PER_EVAL / (reg_ms / 1e3) / 1e12,
-                              "peak_tbs": SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6 / 1e12,
-                              "frac": n_eval * m * m * SMEM_BYTES_PER_EVAL / (reg_ms / 1e3)
-                              / (SM_COUNT * SMEM_BYTES_PER_CLK * sm_mhz * 1e6),
-                              "note": "random 16-byte reads by 32 lanes: bank conflicts give ~2.6 wavefronts per "
-                                      "conflict-free one, so the pipe saturates near frac 0.35"}},
+                     "ops_per_launch": ops, "evals_per_launch": evals_regular, "traffic": traffic,
+                     "traffic_note": TRAFFIC_NOTE,
+                     "mufu_frac": evals_regular / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6),
+                     "hbm_frac_z": zbytes / (reg_ms / 1e3) / (float(pk.get("hbm_gbs", 6800.0)) * 1e9),
+                     "smem": smem_model(evals_regular, reg_ms, sm_mhz)},
         "clocks": clocks,
-        "e2e": ({"value": world * ne * ne / e2e_s, "unit": "Z entries/s", "h2d_bytes_per_step": h2d,
-                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3} if e2e_s else
-                {"value": None, "reason": "Z larger than 8 GiB: no pinned host copy per step"}),
+        "e2e": e2e,
         # per step: range 4 (FP32; 2 in FP64), both tables 3, regular pairs 1, mirror 1 (FP32 only), near 1
         "gpu_launches": (10 if prec == gf.GF_FP32 else 7) * args.steps,
     }
-
-    # ---- accuracy vs the FP64 oracle on sampled rows (outside the timed region)
+    if zhost is not None:
+        torch.cuda.cudart().cudaHostUnregister(zhost.data_ptr())
+        del zhost
+    # ---- accuracy vs the FP64 oracle on 64 seeded 256 x 256 blocks (outside the timed region)
+    run = None
     if rank == 0 and not args.skip_oracle:
-        import oracle as O
-        om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
-        olo, ohi = om.range(wl.rule, prune=len(wl.tri) > 10000)
+        run = OracleRun(wl)
         lo, hi = mesh.range(wl.rule, prec)
-        rows = np.random.default_rng(5).choice(ne, 8, replace=False)
+        blocks, bs = sample_blocks(ne)
         tab = gf.Table(wl.k, lo, hi, p)
         gf.gf_fill(mesh.h, wl.k, p, tab.h, prec, Z)
-        zt = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        zt = gather_blocks(torch, Z, blocks, bs)
         gf.gf_fill(mesh.h, wl.k, px, tab.h, prec, Z)
-        zx = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
+        zx = gather_blocks(torch, Z, blocks, bs)
         gf.gf_fill(mesh.h, wl.k, p, None, prec, Z)
-        zd = Z[torch.from_numpy(rows).to(dev)].cpu().numpy()
-        otabs = O.make_tables(wl.k, olo, ohi)
-        ref_t = om.z_rows(wl.k, wl.rule, rows, mode="table", tables=otabs)
-        ref_x = om.z_rows(wl.k, wl.rule, rows, mode="exp_over_r", tables=otabs)
-        ref_d = om.z_rows(wl.k, wl.rule, rows)
-        rf = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
-        line["accuracy"] = {"rows_sampled": 8, "gpu_table_vs_oracle_table": rf(zt, ref_t),
-                            "gpu_direct_vs_oracle_direct": rf(zd, ref_d),
-                            "gpu_table_vs_oracle_direct": rf(zt, ref_d),
-                            "gpu_exp_over_r_vs_oracle_exp_over_r": rf(zx, ref_x),
-                            "gpu_exp_over_r_vs_oracle_direct": rf(zx, ref_d), "tolerance": 1e-5}
+        zd = gather_blocks(torch, Z, blocks, bs)
+        z64 = None
+        if prec == gf.GF_FP32:
+            gf.gf_fill(mesh.h, wl.k, p64, tab.h, prec, Z)
+            z64 = gather_blocks(torch, Z, blocks, bs)
+        ref_t = oracle_blocks(run, blocks, bs, "table")
+        ref_d = oracle_blocks(run, blocks, bs, "direct")
+        line["accuracy"] = {
+            "blocks": f"{len(blocks)} seeded {bs} x {bs} blocks ({len(blocks) * bs * bs} entries)",
+            "gpu_table_vs_oracle_table": err_stats(zt, ref_t),
+            "gpu_direct_vs_oracle_direct": err_stats(zd, ref_d),
+            "gpu_table_vs_oracle_direct": err_stats(zt, ref_d),
+            "gpu_exp_over_r_vs_oracle_direct": err_stats(zx, ref_d),
+            "tolerance_rel_fro": 1e-5}
+        if z64 is not None:
+            line["accuracy"]["gpu_table_near_fp64_vs_oracle_table"] = err_stats(z64, ref_t)
     if rank == 0 and not args.skip_cpu_baseline:
-        t_full, desc, cores, _ = oracle_baseline(wl)
-        line["cpu_baseline"] = {"value": ne * ne / t_full, "unit": "Z entries/s", "cores": cores,
-                                "kind": "oracle", "sample": desc}
+        line["cpu_baseline"] = oracle_baseline(wl, run=run)
     if rank == 0 and "sphere_radius" in wl.extra and not args.skip_oracle:
         line["rcs"] = sphere_rcs(gf, torch, mesh, wl, p, prec, stream, dev)
     if rank == 0:
@@ -800,10 +985,10 @@ def run_mfie(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere_7680",
+    ap.add_argument("--workload", default="cube_73728",
                     choices=sorted(WORKLOADS) + ["ellipsoid_batch", "adjoint_3072", "cube_near_field",
                                                    "sphere_mfie"])
     ap.add_argument("--skip-oracle", action="store_true")
