@@ -49,8 +49,8 @@ FALLBACK_SM_MHZ = 2070.0
 OPS_PER_EVAL = 25
 # Shared-memory reads of the FP32 lattice per Green evaluation, as
 # (bytes, vector width in bytes) per read: the Lagrange record is a 16-byte
-# read of (c0, c1) and a 16-byte read of (c2, c3).
-SMEM_READS = ((16, 16), (16, 16))
+# read of (c0, c1) and a 4-byte read of c2 (two halves).
+SMEM_READS = ((16, 16), (4, 4))
 # Expected shared-memory wavefronts of one warp-wide read at independent random
 # addresses: lanes are served in phases of 128 bytes (8 lanes for 16-byte reads,
 # 16 for 8-byte, 32 for 4-byte), and a phase takes as many wavefronts as the

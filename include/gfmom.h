@@ -166,6 +166,23 @@ gf_status gf_table_nodes(const gf_table* t, int kind, double* r, double* fre, do
 gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* r_dev, int64_t n,
                         void* out_dev, void* stream);
 
+/* Host FP64 lookup of n points x (host [n], table units: R, or u = kR for a
+ * table of gf_table_create_kr) through the FP64 cell image of the Eq. (6)
+ * hash: exact bracketing against the samples, then the interval's FP64
+ * polynomial (Eq. 4 for GF_EXP, Eq. 5 for GF_GREEN). out: host [n][2]
+ * float64 (re, im) of e^{-jkr}/r or e^{-jkr} (without 1/(4 pi)).
+ * Synchronous (copies the FP64 image from the device). GF_ERR_RANGE if some
+ * x lies outside [r_min, r_max] (below r_min the fills evaluate directly). */
+gf_status gf_table_eval_host(const gf_table* t, int kind, const double* x, int64_t n, double* out);
+
+/* gf_table_create over the range of a mesh: r_min < 0 or r_max < 0 are
+ * replaced by gf_range(m, p->rule, precision) (which synchronizes `stream`).
+ * The paper builds its tables over "the maximum and minimum distance between
+ * any two integration points" (abstract); errors as gf_range and
+ * gf_table_create. */
+gf_status gf_table_create_for_mesh(const gf_mesh* m, double k, const gf_params* p, int precision, double r_min,
+                                   double r_max, void* stream, gf_table** out);
+
 gf_status gf_table_destroy(gf_table* t);
 
 /* ---------------------------------------------------------------- fill ---
@@ -207,8 +224,10 @@ gf_status gf_fill_parts(const gf_mesh* m, double k, const gf_params* p, const gf
  * vertex ids) = dL/d(vertex coordinates) and *dk (device float64) = dL/dk.
  * Regular pairs: FP32 reverse mode with the Green values recomputed from
  * `table` (direct if NULL), F' = -(jk + 1/R) F, dF/dk = -jR F. Near pairs:
- * forward mode (one dual direction per coordinate of the pair and k) with FP64
- * geometry and FP32 edge sampling, or FP64 throughout if p->near_fp64. The
+ * reverse mode (all 19 directions of the pair's coordinates and k in one
+ * pass) with FP64 geometry and static parts and FP32 edge sampling; with
+ * p->near_fp64, forward mode with FP64 dual numbers (one pass per
+ * direction). The
  * near / regular classification, the table range and its samples are held
  * fixed. precision must be GF_FP32. Asynchronous on `stream`; uses per-mesh
  * scratch, so backward calls on one mesh must not overlap. */
@@ -303,8 +322,8 @@ gf_status gf_far_field(const gf_mesh* m, double k, const gf_params* p, int preci
  * (Section II.A fill; the batching is this library's, not the paper's).
  * autotune != 0 times the launch shapes (block size, CTAs per SM, task
  * chunk) on the batch and keeps the fastest; choices are cached in the file
- * named by $GF_AUTOTUNE_CACHE (default ~/.cache/gfmom_autotune.txt, "off"
- * disables the cache). precision must be GF_FP32. Meshes, tables and Z must
+ * named by $GF_AUTOTUNE_CACHE when it is set (unset, empty or "off": no
+ * cache file; the library writes no other host file). precision must be GF_FP32. Meshes, tables and Z must
  * outlive the batch; the batch stores their device pointers. gf_batch_create
  * synchronizes `stream`. */
 typedef struct gf_batch gf_batch;
@@ -319,6 +338,13 @@ gf_status gf_batch_launch(const gf_batch* b, void* stream);
 gf_status gf_batch_config(const gf_batch* b, int* block, int* ctas_per_sm, int* chunk, double* tuned_ms);
 
 gf_status gf_batch_destroy(gf_batch* b);
+
+/* One-shot batched fill: gf_batch_create (no tuning) + gf_batch_launch on
+ * `stream` + gf_batch_destroy. Returns after the fill has completed (it
+ * synchronizes `stream`); keep a gf_batch to refill the same meshes again
+ * without the set-up. Arguments and errors as gf_batch_create (GF_FP32). */
+gf_status gf_fill_batched(int nmesh, const gf_mesh* const* meshes, const double* k, const gf_params* p,
+                          const gf_table* const* tables, void* const* Z, const int64_t* ldz, void* stream);
 
 /* ---------------------------------------------------------------- no-alloc -
  * gf_range for callers that cannot allocate device memory (for example code

@@ -11,7 +11,8 @@ from .gfmom import (GF_EXP, GF_FP32, GF_FP64, GF_GREEN, GF_OP_EFIE, GF_OP_MFIE, 
                     gf_fill_parts, planewave_rcs,
                     gf_last_error, gf_mesh_create, gf_mesh_destroy, gf_mesh_edges, gf_mesh_info,
                     gf_mesh_set_vertices, gf_params, gf_params_default, gf_range, gf_table_create,
-                    gf_table_destroy, gf_table_eval, gf_table_info, gf_table_nodes, lib)
+                    gf_table_destroy, gf_table_eval, gf_table_info, gf_table_nodes, lib, gf_table_eval_host,
+                    gf_table_create_for_mesh, gf_fill_batched)
 
 __all__ = ["GF_EXP", "GF_FP32", "GF_FP64", "GF_GREEN", "GF_OP_EFIE", "GF_OP_MFIE", "GF_PART_MIRROR", "GF_PART_NEAR",
            "GF_PART_PAIRS", "GF_PART_REGULAR",
@@ -21,4 +22,5 @@ __all__ = ["GF_EXP", "GF_FP32", "GF_FP64", "GF_GREEN", "GF_OP_EFIE", "GF_OP_MFIE
            "gf_fill_parts", "planewave_rcs",
            "gf_last_error", "gf_mesh_create", "gf_mesh_destroy", "gf_mesh_edges", "gf_mesh_info",
            "gf_mesh_set_vertices", "gf_params", "gf_params_default", "gf_range", "gf_table_create",
-           "gf_table_destroy", "gf_table_eval", "gf_table_info", "gf_table_nodes", "lib"]
+           "gf_table_destroy", "gf_table_eval", "gf_table_info", "gf_table_nodes", "lib", "gf_table_eval_host",
+           "gf_table_create_for_mesh", "gf_fill_batched"]

@@ -82,11 +82,11 @@ gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
   return GF_OK;
 }
 
+// The tuner's cache file: only where $GF_AUTOTUNE_CACHE names one (the
+// library writes nothing else on the host); "" or "off" = no cache.
 std::string cache_path() {
   const char* p = std::getenv("GF_AUTOTUNE_CACHE");
-  if (p) return std::string(p);
-  const char* home = std::getenv("HOME");
-  return std::string(home ? home : "/tmp") + "/.cache/gfmom_autotune.txt";
+  return p ? std::string(p) : std::string();
 }
 
 std::string tune_key(const gf_batch* b) {
@@ -105,7 +105,7 @@ std::string tune_key(const gf_batch* b) {
 
 bool cache_lookup(const std::string& key, int* block, int* ctas, int* chunk, double* ms) {
   std::string path = cache_path();
-  if (path == "off") return false;
+  if (path.empty() || path == "off") return false;
   FILE* f = std::fopen(path.c_str(), "r");
   if (!f) return false;
   char k[512];
@@ -127,7 +127,7 @@ bool cache_lookup(const std::string& key, int* block, int* ctas, int* chunk, dou
 
 void cache_store(const std::string& key, int block, int ctas, int chunk, double ms) {
   std::string path = cache_path();
-  if (path == "off") return;
+  if (path.empty() || path == "off") return;
   for (size_t i = 1; i < path.size(); ++i)  // parent directories, errors ignored
     if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
   FILE* f = std::fopen(path.c_str(), "a");
@@ -239,9 +239,7 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
     if (tables && !table_views(tables[i], k[i], &it.green, &it.exp, &gscale))
       return fail(GF_ERR_ARG, "gf_batch_create: table built for another k");
     it.use_table = tables ? 1 : 0;
-    it.kpi = (float)(k[i] / kPi);
-    it.scale32 = (float)(k[i] * p->eta / (4.0 * kPi) * gscale);
-    it.inv_k2_32 = (float)(1.0 / (k[i] * k[i]));
+    it.rk = reg_consts(k[i], k[i] * p->eta / (4.0 * kPi) * gscale);
     it.k = k[i];
     it.scale = k[i] * p->eta;
     it.inv_k2 = 1.0 / (k[i] * k[i]);
@@ -313,6 +311,19 @@ gf_status gf_batch_destroy(gf_batch* b) {
   if (b->d_items) cudaFree(b->d_items);
   if (b->d_counters) cudaFree(b->d_counters);
   delete b;
+  return GF_OK;
+}
+
+gf_status gf_fill_batched(int nmesh, const gf_mesh* const* meshes, const double* k, const gf_params* p,
+                          const gf_table* const* tables, void* const* Z, const int64_t* ldz, void* stream) {
+  gf_batch* b = nullptr;
+  gf_status st = gf_batch_create(nmesh, meshes, k, p, tables, GF_FP32, Z, ldz, 0, stream, &b);
+  if (st) return st;
+  st = gf_batch_launch(b, stream);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  gf_batch_destroy(b);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "gf_fill_batched");
   return GF_OK;
 }
 

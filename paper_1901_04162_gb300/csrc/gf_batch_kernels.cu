@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
       const Tab32 T = tab32(it.green);
       int p, q0;
       if (sym_task(t - it.reg_begin, it.g.nt, &p, &q0))
-        regular_task32<M, TABLE ? kLagrange : kDirect, true>(
-            it.g, T, it.kpi, it.scale32, it.inv_k2_32, DenseUpper{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
+        regular_task32<M, TABLE ? kLagrange : kDirect, TABLE, false>(
+            it.g, T, it.rk, DenseUpper{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
     }
   }
 }

@@ -22,6 +22,7 @@
 // part in closed form) for the vector part. e^{-jkR} on those lines is the
 // linear Exp table when r_min <= R <= r_max (Section II.C), else sincos.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -42,17 +43,20 @@ __device__ __forceinline__ bool edge_valid(int code) { return code >= 0; }
 
 // ---------------------------------------------------------------- lookups
 struct Tab32 {  // FP32 view (shared or global memory; possibly a window of the lattice)
-  const float4* la;   // lattice records, indexed by the global cell number
-  const float4* lb;
+  const float4* la;   // lattice records (c0, c1), indexed by the global cell number
+  const uint32_t* lc; // c2 as half2 (Green) or the busy ordinal
   const int* busy;    // the blob: cells holding samples (ascending), their headers,
-  const float4* hdr;  // sub-cells and compact interval records
+  const float4* hdr;  // sub-cells and full interval records
   const float4* sub;
   const float4* ca;
   const float4* cb;
   int n_busy;
   float vmin, vmax;   // kLatMagic + first / last cell present (the whole lattice, or a window)
-  float inv, nc, h, lo;
+  float inv, nc, h, lo, amid, c2d;
   float xscale;       // lookups at x = xscale * R (1, or k for a table in u = kR)
+  // shared-memory copies: address of cell i's record = (bits of kLatMagic + i)
+  // * 16 + sa_off, of its lat_c word = (bits) * 4 + sc_off (mod 2^32)
+  uint32_t sa_off = 0u, sc_off = 0u;
 };
 
 // Points a view's blob pointers into a copy of the blob (global or shared).
@@ -69,7 +73,7 @@ __device__ __forceinline__ Tab32 tab32(const TabView& t) {
   Tab32 T;
   T.xscale = t.xscale32;
   T.la = t.lat_a;
-  T.lb = t.lat_b;
+  T.lc = t.lat_c;
   tab32_blob(T, t, t.lat_blob);
   T.vmin = kLatMagic;
   T.vmax = kLatMagic + (float)(t.n_lat - 1);
@@ -77,22 +81,45 @@ __device__ __forceinline__ Tab32 tab32(const TabView& t) {
   T.nc = t.lat_nc;
   T.h = t.lat_h;
   T.lo = t.lat_lo;
+  T.amid = t.lat_amid;
+  T.c2d = t.lat_c2d;
   return T;
 }
 
-// Lattice cell of R (without a conversion instruction) and the exact offset
-// s = R - A_i from its anchor; the table builder repeats these float
-// operations.
+// Copies a table's lattice image (records, the c2 plane for deg > 1, the
+// blob) into shared memory at `smem` (all threads of the block; the caller
+// synchronizes) and points T at the copy.
+__device__ __forceinline__ void stage_tab32(Tab32& T, const TabView& tv, int deg, unsigned char* smem) {
+  const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
+  float4* sa = reinterpret_cast<float4*>(smem);
+  for (int i = threadIdx.x; i < nl; i += blockDim.x) sa[i] = tv.lat_a[i];
+  if (deg > 1) {
+    uint32_t* sc = reinterpret_cast<uint32_t*>(sa + nl);
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) sc[i] = tv.lat_c[i];
+    T.lc = sc;
+  }
+  float4* sblob = reinterpret_cast<float4*>(smem + tv.smem32_plane_bytes(deg));
+  for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
+  T.la = sa;
+  tab32_blob(T, tv, sblob);
+  const uint32_t mb = (uint32_t)__float_as_int(kLatMagic);
+  T.sa_off = (uint32_t)__cvta_generic_to_shared(sa) - mb * 16u;
+  T.sc_off = (uint32_t)__cvta_generic_to_shared(sa + nl) - mb * 4u;
+}
+
+// Lattice cell of R (without a conversion instruction), its index as a
+// float, and the exact offset s = R - A_i from its anchor; the table builder
+// repeats these float operations.
 struct LatPos {
   int i;
-  float s;
+  float s, fi;
 };
 
 __device__ __forceinline__ LatPos lat_pos(const Tab32& T, float R) {
   const float u = __fmaf_rn(R, T.inv, T.nc);
   const float v = fminf(fmaxf(__fadd_rn(u, kLatMagic), T.vmin), T.vmax);
   const float fi = __fsub_rn(v, kLatMagic);
-  return LatPos{__float_as_int(v) - __float_as_int(kLatMagic), __fsub_rn(R, __fmaf_rn(fi, T.h, T.lo))};
+  return LatPos{__float_as_int(v) - __float_as_int(kLatMagic), __fsub_rn(R, __fmaf_rn(fi, T.h, T.amid)), fi};
 }
 
 // e^{-jkR}/R (Green) or e^{-jkR} (Exp) from the FP32 lattice image: the
@@ -110,48 +137,61 @@ __device__ __forceinline__ float2 horner32(float s, float4 a, float4 b) {
   return make_float2(re, im);
 }
 
+// The cell record's value: c0 + s c1 (+ s^2 c2 for the Green table, c2 from
+// the half2 word scaled by c2d).
+template <int DEG>
+__device__ __forceinline__ float2 cell_value32(const Tab32& T, float s, float4 a, uint32_t c) {
+  if (DEG == 1) return make_float2(fmaf(s, a.z, a.x), fmaf(s, a.w, a.y));
+  __half2_raw hr;
+  hr.x = (unsigned short)(c & 0xFFFFu);
+  hr.y = (unsigned short)(c >> 16);
+  const float2 c2 = __half22float2(__half2(hr));
+  const float t = s * T.c2d;
+  return make_float2(fmaf(s, fmaf(t, c2.x, a.z), a.x), fmaf(s, fmaf(t, c2.y, a.w), a.y));
+}
+
 // Branch-free part: the cell's record (the polynomial of the interval at the
 // cell's middle); *slow is set when the cell holds samples, where this value
-// is exact only on the middle interval.
+// is not to be used.
 template <int DEG>
 __device__ __forceinline__ float2 lookup32_fast(const Tab32& T, float R, bool* slow) {
   const LatPos q = lat_pos(T, R * T.xscale);
   const float4 a = T.la[q.i];
-  float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (DEG > 1) b = T.lb[q.i];
-  *slow = (__float_as_int(DEG > 1 ? b.w : a.w) & 1) != 0;
-  return horner32<DEG>(q.s, a, b);
+  const uint32_t c = DEG > 1 ? T.lc[q.i] : 0u;
+  *slow = (__float_as_int(a.w) & 1) != 0;
+  return cell_value32<DEG>(T, q.s, a, c);
 }
 
-// Cells holding samples: the cell's place in the busy list (kept in the low
-// bits of c3re for the Green table, in lat_b.x for the Exp table; a binary
-// search for lists longer than kOrdinalMax), its header, the sub-cell, then
-// the compact interval record about node32.
-constexpr int kOrdinalMax = 0xFFF;
-
+// Cells holding samples: the cell's place in the busy list (its lat_c
+// word), its header, the sub-cell of the offset from the cell's left end,
+// then the full interval record about node32. x = x_hi + x_lo in table units
+// (x_lo = 0 for an FP32 distance); the bracketing compares x_hi (at a sample
+// both neighbouring polynomials take the sample value).
 template <int DEG>
-__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float Rr) {
-  const float R = Rr * T.xscale;  // table units
-  const LatPos q = lat_pos(T, R);
-  int lo = DEG > 1 ? (__float_as_int(T.lb[q.i].z) & kOrdinalMax) : __float_as_int(T.lb[q.i].x);
-  if (lo >= kOrdinalMax) {
-    lo = 0;
-    int hi = T.n_busy - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (T.busy[mid] < q.i) lo = mid + 1;
-      else hi = mid;
-    }
-  }
-  const float4 h = T.hdr[lo];
-  const int c = __float_as_int(h.x) + min(max(__float2int_rz(__fmul_rn(q.s, h.y)), 0), __float_as_int(h.z));
+__device__ __forceinline__ float2 lookup32_slow_x(const Tab32& T, float xh, float xl) {
+  const LatPos q = lat_pos(T, xh);
+  const int ord = min(max((int)T.lc[q.i], 0), T.n_busy - 1);  // called for flagged cells only
+  const float4 h = T.hdr[ord];
+  const float sl = __fadd_rn(__fsub_rn(xh, __fmaf_rn(q.fi, T.h, T.lo)), xl);
+  const int c = __float_as_int(h.x) + min(max(__float2int_rz(__fmul_rn(sl, h.y)), 0), __float_as_int(h.z));
   const float4 rec = T.sub[c];
-  const bool up = R >= rec.y;
+  const bool up = xh >= rec.y;
   const int j = __float_as_int(rec.x) + (up ? 1 : 0);
   const float4 a = T.ca[j];
   float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
   if (DEG > 1) b = T.cb[j];
-  return horner32<DEG>(R - (up ? rec.y : rec.z), a, b);
+  return horner32<DEG>(__fadd_rn(xh - (up ? rec.y : rec.z), xl), a, b);
+}
+
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float Rr) {
+  return lookup32_slow_x<DEG>(T, Rr * T.xscale, 0.f);
+}
+
+// The same at a split distance already in table units.
+template <int DEG>
+__device__ __forceinline__ float2 lookup32_slow(const Tab32& T, float xh, float xl) {
+  return lookup32_slow_x<DEG>(T, xh, xl);
 }
 
 template <int DEG>
@@ -303,150 +343,357 @@ struct CsrSink {
   }
 };
 
-template <int M, int MODE, bool DEFER = true, class Sink = DenseUpper>
-__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
-                                               int p, int q, bool ok, const Sink& sink);
+// ---------------------------------------------------------------- packed FP32 pairs
+// Two FP32 lanes (re, im) in one 64-bit register for the packed FP32
+// instructions of sm_100 and later (add / sub / mul / fma .f32x2, one issue
+// slot for both parts, IEEE round-to-nearest in each).
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 up2(f2x r) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x mul2(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x fma2(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
-template <int M, int MODE, bool DEFER, class Sink>
-__device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
-                                               const Sink& sink, int p, int q0, int lane) {
+struct KSum2 {  // Kahan-compensated sum of a complex number, both parts at once
+  f2x s = 0ull, c = 0ull;
+  __device__ __forceinline__ void add(f2x x) {
+    const f2x y = sub2(x, c);
+    const f2x t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+  }
+};
+
+// ---------------------------------------------------------------- split distances
+// The separation of the 32-triangle blocks of p and q. Block centres lie on
+// a grid of step u = 2^e (bgrid, in units of u), so B = C_p - C_q is exact in
+// FP32 and |B|^2 is an exact unsigned integer in units of u^2 (each
+// coordinate below 2^15 units), split into two exact FP32 parts.
+struct BlockSep {
+  float bx, by, bz, bbh, bbl;
+};
+
+__device__ __forceinline__ BlockSep block_sep(const GeoView& g, int p, int q) {
+  const int4 cp = g.bgrid[p >> 5], cq = g.bgrid[q >> 5];
+  const int dx = cp.x - cq.x, dy = cp.y - cq.y, dz = cp.z - cq.z;
+  const unsigned bb = (unsigned)(dx * dx) + (unsigned)(dy * dy) + (unsigned)(dz * dz);
+  BlockSep s;
+  s.bx = (float)dx * g.bunit;
+  s.by = (float)dy * g.bunit;
+  s.bz = (float)dz * g.bunit;
+  s.bbh = (float)(bb & 0xFFFFFF00u) * g.bunit2;
+  s.bbl = (float)(bb & 0xFFu) * g.bunit2;
+  return s;
+}
+
+// R = |B + r_a - r_b| (r: point offsets from their block centres, FP32) as
+// R_hi + R_lo: R^2 = |B|^2 + num with num = 2B.(r_a - r_b) + |r_a - r_b|^2 =
+// A_a + B_b - 2 r_a.r_b (A_a = 2B.r_a + |r_a|^2, B_b = |r_b|^2 - 2B.r_b), all
+// small terms; R_hi = FP32 sqrt of |B|_hi^2 + num, R_lo = (R^2 - R_hi^2) /
+// (2 R_hi) with R_hi^2 taken exactly by an FMA. So R carries about 1e-9 lambda
+// of absolute error where one FP32 number would carry ulp(R) / 2 (6e-8 at
+// R = 1), and kR keeps its phase across the electrically large workloads.
+struct SplitR {
+  float hi, lo, rs;  // R_hi, R_lo, 1 / R (FP32)
+};
+
+__device__ __forceinline__ SplitR split_r(const BlockSep& bs, float c, float m2x, float m2y, float m2z, float bx,
+                                         float by, float bz) {
+  const float num = fmaf(m2x, bx, fmaf(m2y, by, fmaf(m2z, bz, c)));
+  const float R2 = bs.bbh + num;
+  SplitR r;
+  r.rs = rsqrtf(R2);
+  r.hi = R2 * r.rs;
+  float e = fmaf(-r.hi, r.hi, bs.bbh);
+  e += num;
+  e += bs.bbl;
+  r.lo = e * (0.5f * r.rs);
+  // 1/R = 1/(R_hi + R_lo): rs is 1/R_hi to FP32 accuracy even where R2 lost
+  // digits to the cancellation in |B|^2 + num (R much smaller than |B|)
+  r.rs = fmaf(-r.lo * r.rs, r.rs, r.rs);
+  return r;
+}
+
+// Table units x = xscale R as x_hi + x_lo (xscale = 1 for tables in R).
+template <bool KR>
+__device__ __forceinline__ void table_x(const Tab32& T, const SplitR& r, float* xh, float* xl) {
+  if (!KR) {
+    *xh = r.hi;
+    *xl = r.lo;
+  } else {
+    *xh = r.hi * T.xscale;
+    *xl = fmaf(r.lo, T.xscale, fmaf(r.hi, T.xscale, -*xh));
+  }
+}
+
+// Fast lattice lookup at x = x_hi + x_lo: the cell from x_hi, the offset
+// s = (x_hi - A_i) + x_lo (the difference exact); SM: the lattice planes in
+// shared memory, addressed from the float bits of the cell index (one IMAD
+// per plane). *busy: the cell holds samples (the value is then corrected).
+template <int DEG, bool SM>
+__device__ __forceinline__ float2 lat_fast(const Tab32& T, float xh, float xl, bool* busy) {
+  const float u = __fmaf_rn(xh, T.inv, T.nc);
+  const float v = fminf(fmaxf(__fadd_rn(u, kLatMagic), T.vmin), T.vmax);
+  const float fi = __fsub_rn(v, kLatMagic);
+  const float s = __fadd_rn(__fsub_rn(xh, __fmaf_rn(fi, T.h, T.amid)), xl);
+  float4 a;
+  uint32_t c = 0u;
+  if (SM) {
+    const uint32_t bits = __float_as_uint(v);
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w)
+                 : "r"(bits * 16u + T.sa_off));
+    if (DEG > 1) asm("ld.shared.b32 %0, [%1];" : "=r"(c) : "r"(bits * 4u + T.sc_off));
+  } else {
+    const int i = __float_as_int(v) - __float_as_int(kLatMagic);
+    a = T.la[i];
+    if (DEG > 1) c = T.lc[i];
+  }
+  *busy = (__float_as_uint(a.w) & 1u) != 0u;
+  return cell_value32<DEG>(T, s, a, c);
+}
+
+// sincos(pi x) of x = k R / pi from the split R: the product carried exactly
+// (x_hi + x_err by an FMA, plus R_lo and the FP32 residue of k / pi), x_hi
+// reduced modulo 2 exactly, then CUDA's sincospif of the small argument.
+__device__ __forceinline__ void sincos_kr(const SplitR& r, float kpi, float kpi_lo, float* sn, float* cs) {
+  const float xh = r.hi * kpi;
+  const float xl = fmaf(r.lo, kpi, fmaf(r.hi, kpi_lo, fmaf(r.hi, kpi, -xh)));
+  const float n2 = __fsub_rn(__fmaf_rn(xh, 0.5f, kLatMagic), kLatMagic);
+  sincospif(fmaf(-2.f, n2, xh) + xl, sn, cs);
+}
+
+
+
+template <int M, int MODE, bool KR = false, bool SM = false, class Sink = DenseUpper>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p, int q,
+                                               bool ok, const Sink& sink);
+
+// No pair of the blocks of p and q0 is near when their centres are farther
+// apart than the two vertex radii plus the centroid criterion (then no two
+// triangles touch and no two centroids are within near_dist).
+__device__ __forceinline__ bool blocks_apart(const GeoView& g, int p, int q0) {
+  const int4 a = g.bgrid[p >> 5], b = g.bgrid[q0 >> 5];
+  const float dx = (float)(a.x - b.x) * g.bunit, dy = (float)(a.y - b.y) * g.bunit, dz = (float)(a.z - b.z) * g.bunit;
+  const float lim = __int_as_float(a.w) + __int_as_float(b.w) + g.near_dist32 * 1.0001f + 1e-6f;
+  return dx * dx + dy * dy + dz * dz > lim * lim * 1.0001f;
+}
+
+// One warp task: test triangle p, source triangles q0 .. q0 + 31 (q0 a
+// multiple of 32, one block).
+template <int M, int MODE, bool KR, bool SM, class Sink>
+__device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, const RegK& K, const Sink& sink,
+                                               int p, int q0, int lane) {
   const int q = min(q0 + lane, g.nt - 1);
-  const float4 cp = g.cen32[p], cq = g.cen32[q];
-  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
-  const bool ok = (q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
-  regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, p, q, ok, sink);
+  bool ok = (q0 + lane < g.nt) && q > p;
+  if (!blocks_apart(g, p, q0)) {
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    ok = ok && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  }
+  regular_pair32<M, MODE, KR, SM>(g, T, K, p, q, ok, sink);
 }
 
 // The 3x3 block of regular pair (p, q) (q per lane; lanes with ok == false
-// take part in the warp's work but write nothing), handed to `sink`.
-template <int M, int MODE, bool DEFER, class Sink>
-__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, float kpi, float scale, float inv_k2,
-                                               int p, int q, bool ok, const Sink& sink) {
-  const float4 cp = g.cen32[p], cq = g.cen32[q];
-  const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+// take part in the warp's work but write nothing), handed to `sink`. Source
+// points enter through their offsets r_b from q's block centre (rel32): the
+// source moments are taken about that centre, and the block formula uses
+// eps'_j = C_b(q) - v_j (geob32) in place of eps_j = c_q - v_j (the same sums:
+// r_b + eps'_j = beta_b + eps_j).
+template <int M, int MODE, bool KR, bool SM, class Sink>
+__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p, int q,
+                                               bool ok, const Sink& sink) {
   if (!__any_sync(0xffffffffu, ok)) return;
-  float4 beta[M];
+  const BlockSep bs = block_sep(g, p, q);
+  constexpr bool kWQ = M <= 4;  // keep w_b r_b in registers (small rules)
+  float rx[M], ry[M], rz[M], wb[M], bq[M];
 #pragma unroll
-  for (int b = 0; b < M; ++b) beta[b] = g.pts32[(size_t)b * g.nt + q];
-  KSum M0r, M0i, Mar[3], Mai[3], Mbr[3], Mbi[3], Mabr, Mabi;
+  for (int b = 0; b < M; ++b) {
+    const float4 r = g.rel32[(size_t)b * g.nt + q];
+    rx[b] = r.x;
+    ry[b] = r.y;
+    rz[b] = r.z;
+    wb[b] = r.w;
+    bq[b] = fmaf(r.x, r.x - 2.f * bs.bx, fmaf(r.y, r.y - 2.f * bs.by, r.z * (r.z - 2.f * bs.bz)));
+  }
+  float wqx[kWQ ? M : 1], wqy[kWQ ? M : 1], wqz[kWQ ? M : 1];
+  if (kWQ) {
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+      wqx[b] = wb[b] * rx[b];
+      wqy[b] = wb[b] * ry[b];
+      wqz[b] = wb[b] * rz[b];
+    }
+  }
+  KSum2 M0, Ma[3], Mb[3], Mab;
   static_assert(M <= 8, "point pairs are flagged in 8 bits per test point");
   unsigned long long emask = 0;  // point pairs (bit 8 a + b) whose lattice cell holds samples
-  float4 al_next = g.pts32[p];
 #pragma unroll 1
   for (int a = 0; a < M; ++a) {
-    const float4 al = al_next;
-    if (a + 1 < M) al_next = g.pts32[(size_t)(a + 1) * g.nt + p];  // issued a whole iteration early
-    const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
-    // Green values of the M source points: branch-free lookups accumulated at
-    // once (every load of the row in flight together); a row that met a
-    // lattice cell holding samples is corrected after the loop
-    float s0r = 0.f, s0i = 0.f, sbr[3] = {0.f, 0.f, 0.f}, sbi[3] = {0.f, 0.f, 0.f};
+    const float4 ra = g.rel32[(size_t)a * g.nt + p];  // test point: offset from p's block centre
+    const float4 al = g.pts32[(size_t)a * g.nt + p];  // offset from p's centroid, weight
+    const float Aa = fmaf(2.f * bs.bx, ra.x, fmaf(2.f * bs.by, ra.y, fmaf(2.f * bs.bz, ra.z,
+                                                                              fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, ra.z * ra.z)))));
+    const float m2x = -2.f * ra.x, m2y = -2.f * ra.y, m2z = -2.f * ra.z;
+    float s0r = 0.f, s0i = 0.f, sqr[3] = {0.f, 0.f, 0.f}, sqi[3] = {0.f, 0.f, 0.f};
     unsigned rowbits = 0;
 #pragma unroll
     for (int b = 0; b < M; ++b) {
-      const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
-      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-      const float rs = rsqrtf(R2);
-      float gr, gi;
-      if (MODE == kLagrange) {
-        bool sl = false;
-        const float2 f = DEFER ? lookup32_fast<3>(T, R2 * rs, &sl) : lookup32<3>(T, R2 * rs);  // e^{-jkR}/R
-        if (sl) rowbits |= 1u << b;
-        gr = f.x * beta[b].w;
-        gi = f.y * beta[b].w;
-      } else if (MODE == kExpOverR) {
-        bool sl = false;
-        const float2 f = DEFER ? lookup32_fast<1>(T, R2 * rs, &sl) : lookup32<1>(T, R2 * rs);  // e^{-jkR}
-        if (sl) rowbits |= 1u << b;
-        const float wr = beta[b].w * rs;
-        gr = f.x * wr;
-        gi = f.y * wr;
-      } else {
+      const SplitR R = split_r(bs, Aa + bq[b], m2x, m2y, m2z, rx[b], ry[b], rz[b]);
+      float gr, gi;  // e^{-jkR}/R
+      if (MODE == kDirect) {
         float sn, cs;
-        sincospif(R2 * rs * kpi, &sn, &cs);  // kR / pi
-        const float wr = beta[b].w * rs;
-        gr = cs * wr;
-        gi = -sn * wr;
+        sincos_kr(R, K.kpi, K.kpi_lo, &sn, &cs);
+        gr = cs * R.rs;
+        gi = -sn * R.rs;
+      } else {
+        float xh, xl;
+        table_x<KR>(T, R, &xh, &xl);
+        bool busy;
+        const float2 f = lat_fast<MODE == kLagrange ? 3 : 1, SM>(T, xh, xl, &busy);
+        if (busy) rowbits |= 1u << b;
+        if (MODE == kLagrange) {
+          gr = f.x;
+          gi = f.y;
+        } else {  // e^{-jkR} times 1/R
+          gr = f.x * R.rs;
+          gi = f.y * R.rs;
+        }
       }
-      s0r += gr;
-      s0i += gi;
-      sbr[0] = fmaf(beta[b].x, gr, sbr[0]);
-      sbi[0] = fmaf(beta[b].x, gi, sbi[0]);
-      sbr[1] = fmaf(beta[b].y, gr, sbr[1]);
-      sbi[1] = fmaf(beta[b].y, gi, sbi[1]);
-      sbr[2] = fmaf(beta[b].z, gr, sbr[2]);
-      sbi[2] = fmaf(beta[b].z, gi, sbi[2]);
+      if (kWQ) {
+        s0r = fmaf(wb[b], gr, s0r);
+        s0i = fmaf(wb[b], gi, s0i);
+        sqr[0] = fmaf(wqx[b], gr, sqr[0]);
+        sqi[0] = fmaf(wqx[b], gi, sqi[0]);
+        sqr[1] = fmaf(wqy[b], gr, sqr[1]);
+        sqi[1] = fmaf(wqy[b], gi, sqi[1]);
+        sqr[2] = fmaf(wqz[b], gr, sqr[2]);
+        sqi[2] = fmaf(wqz[b], gi, sqi[2]);
+      } else {
+        const float wr = wb[b] * gr, wi = wb[b] * gi;
+        s0r += wr;
+        s0i += wi;
+        sqr[0] = fmaf(rx[b], wr, sqr[0]);
+        sqi[0] = fmaf(rx[b], wi, sqi[0]);
+        sqr[1] = fmaf(ry[b], wr, sqr[1]);
+        sqi[1] = fmaf(ry[b], wi, sqi[1]);
+        sqr[2] = fmaf(rz[b], wr, sqr[2]);
+        sqi[2] = fmaf(rz[b], wi, sqi[2]);
+      }
     }
-    emask |= (unsigned long long)rowbits << (8 * a);
-    const float wa = al.w;
-    M0r.add(wa * s0r);
-    M0i.add(wa * s0i);
-    const float wal[3] = {wa * al.x, wa * al.y, wa * al.z};
+    if (MODE != kDirect) emask |= (unsigned long long)rowbits << (8 * a);
+    // outer sums over the test points, Kahan-compensated (both parts at once)
+    const f2x wa2 = pk2(al.w, al.w);
+    const f2x s0 = pk2(s0r, s0i);
+    M0.add(mul2(s0, wa2));
+    const float wal[3] = {al.w * al.x, al.w * al.y, al.w * al.z};
+    f2x xab = 0ull;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      Mar[c].add(wal[c] * s0r);
-      Mai[c].add(wal[c] * s0i);
-      Mbr[c].add(wa * sbr[c]);
-      Mbi[c].add(wa * sbi[c]);
+      const f2x wl = pk2(wal[c], wal[c]);
+      const f2x sq = pk2(sqr[c], sqi[c]);
+      Ma[c].add(mul2(s0, wl));
+      Mb[c].add(mul2(sq, wa2));
+      xab = fma2(sq, wl, xab);
     }
-    Mabr.add(wal[0] * sbr[0] + wal[1] * sbr[1] + wal[2] * sbr[2]);
-    Mabi.add(wal[0] * sbi[0] + wal[1] * sbi[1] + wal[2] * sbi[2]);
+    Mab.add(xab);
   }
-  if (DEFER && MODE != kDirect && __any_sync(0xffffffffu, emask != 0ull)) {
+  if (MODE != kDirect && __any_sync(0xffffffffu, emask != 0ull)) {
     // exact values where the lattice cell holds samples: add (exact - cell
-    // polynomial) to the moments of those point pairs only, in row order,
-    // with the same float operations for R as the loop above
+    // polynomial) to the moments of those point pairs only, with the same
+    // float operations for R as the loop above
     while (emask) {
       const int bit = __ffsll((long long)emask) - 1;
       emask &= emask - 1;
       const int a = bit >> 3, b = bit & 7;
+      const float4 ra = g.rel32[(size_t)a * g.nt + p];
       const float4 al = g.pts32[(size_t)a * g.nt + p];
-      const float4 be = g.pts32[(size_t)b * g.nt + q];
-      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
-      const float rx = ux - be.x, ry = uy - be.y, rz = uz - be.z;
-      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-      const float rs = rsqrtf(R2);
+      const float4 rb = g.rel32[(size_t)b * g.nt + q];
+      const float Aa = fmaf(2.f * bs.bx, ra.x, fmaf(2.f * bs.by, ra.y, fmaf(2.f * bs.bz, ra.z,
+                                                                                fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, ra.z * ra.z)))));
+      const float bqb = fmaf(rb.x, rb.x - 2.f * bs.bx, fmaf(rb.y, rb.y - 2.f * bs.by, rb.z * (rb.z - 2.f * bs.bz)));
+      const SplitR R = split_r(bs, Aa + bqb, -2.f * ra.x, -2.f * ra.y, -2.f * ra.z, rb.x, rb.y, rb.z);
+      float xh, xl;
+      table_x<KR>(T, R, &xh, &xl);
       constexpr int D = MODE == kLagrange ? 3 : 1;
-      bool sl;
-      const float2 fa = lookup32_fast<D>(T, R2 * rs, &sl);
-      const float2 fe = lookup32_slow<D>(T, R2 * rs);
-      const float w = al.w * (MODE == kLagrange ? be.w : be.w * rs);
-      const float dr = (fe.x - fa.x) * w, di = (fe.y - fa.y) * w;
-      const float ab = al.x * be.x + al.y * be.y + al.z * be.z;
-      const float alv[3] = {al.x, al.y, al.z}, bev[3] = {be.x, be.y, be.z};
-      M0r.add(dr);
-      M0i.add(di);
+      bool busy;
+      const float2 fa = lat_fast<D, SM>(T, xh, xl, &busy);
+      const float2 fe = busy ? lookup32_slow<D>(T, xh, xl) : fa;
+      const float w = al.w * (MODE == kLagrange ? rb.w : rb.w * R.rs);
+      const f2x d = pk2((fe.x - fa.x) * w, (fe.y - fa.y) * w);
+      M0.add(d);
+      const float alv[3] = {al.x, al.y, al.z}, rbv[3] = {rb.x, rb.y, rb.z};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        Mar[c].add(alv[c] * dr);
-        Mai[c].add(alv[c] * di);
-        Mbr[c].add(bev[c] * dr);
-        Mbi[c].add(bev[c] * di);
+        Ma[c].add(mul2(d, pk2(alv[c], alv[c])));
+        Mb[c].add(mul2(d, pk2(rbv[c], rbv[c])));
       }
-      Mabr.add(ab * dr);
-      Mabi.add(ab * di);
+      const float ab = al.x * rb.x + al.y * rb.y + al.z * rb.z;
+      Mab.add(mul2(d, pk2(ab, ab)));
     }
   }
   if (!ok) return;
+  // 3x3 block: Z(e_i, e_j) += j scale s_i l_i s_j l_j [X_j + delta_i . Y_j / 4] with
+  // X_j = (Mab + eps'_j . Ma) / 4 - M0 / k^2 and Y_j = Mb + eps'_j M0
   const int4 ep = g.tedge[p], eq = g.tedge[q];
   const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-  const float m0r = M0r.s, m0i = M0i.s;
+  const float2 m0 = up2(M0.s), mab = up2(Mab.s);
+  const float2 ma[3] = {up2(Ma[0].s), up2(Ma[1].s), up2(Ma[2].s)};
+  const float2 mb[3] = {up2(Mb[0].s), up2(Mb[1].s), up2(Mb[2].s)};
+  float xr[3], xi[3], yr[3][3], yi[3][3], sl[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float4 gq = g.geob32[3 * (size_t)q + j];  // eps'_j, s_j l_j
+    const float e[3] = {gq.x, gq.y, gq.z};
+    float er = mab.x, ei = mab.y;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      er = fmaf(e[c], ma[c].x, er);
+      ei = fmaf(e[c], ma[c].y, ei);
+      yr[j][c] = fmaf(e[c], m0.x, mb[c].x);
+      yi[j][c] = fmaf(e[c], m0.y, mb[c].y);
+    }
+    xr[j] = fmaf(0.25f, er, -m0.x * K.inv_k2);
+    xi[j] = fmaf(0.25f, ei, -m0.y * K.inv_k2);
+    sl[j] = gq.w;
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (!edge_valid(ecp[i])) continue;
     const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
-    const float dMbr = gp.x * Mbr[0].s + gp.y * Mbr[1].s + gp.z * Mbr[2].s;
-    const float dMbi = gp.x * Mbi[0].s + gp.y * Mbi[1].s + gp.z * Mbi[2].s;
+    const float d[3] = {0.25f * gp.x, 0.25f * gp.y, 0.25f * gp.z};
+    const float ci = K.scale * gp.w;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       if (!edge_valid(ecq[j])) continue;
-      const float4 gq = g.geo32[3 * (size_t)q + j];  // eps_j, s_j l_j
-      const float eMar = gq.x * Mar[0].s + gq.y * Mar[1].s + gq.z * Mar[2].s;
-      const float eMai = gq.x * Mai[0].s + gq.y * Mai[1].s + gq.z * Mai[2].s;
-      const float de = gp.x * gq.x + gp.y * gq.y + gp.z * gq.z;
-      const float br = 0.25f * (Mabr.s + eMar + dMbr + de * m0r) - m0r * inv_k2;
-      const float bi = 0.25f * (Mabi.s + eMai + dMbi + de * m0i) - m0i * inv_k2;
-      const float c = scale * gp.w * gq.w;  // k eta/(4 pi) s_i l_i s_j l_j
+      const float br = fmaf(d[0], yr[j][0], fmaf(d[1], yr[j][1], fmaf(d[2], yr[j][2], xr[j])));
+      const float bi = fmaf(d[0], yi[j][0], fmaf(d[1], yi[j][1], fmaf(d[2], yi[j][2], xi[j])));
+      const float c = ci * sl[j];
       // j * c * (br + j bi) = c * (-bi + j br)
       sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bi, c * br));
     }

@@ -194,27 +194,28 @@ __device__ void dev_table_cells64(int c, int n, const double* __restrict__ node6
 }
 
 // Lattice records: the polynomial of the interval at the cell's middle about
-// the cell anchor A_i = fma(i, h, lo) (the anchor the lookups recompute),
-// with the flag bit of the cells holding samples.
+// the cell anchor A_i = fma(i, h, lat_amid) (the anchor the lookups
+// recompute): (c0, c1) in FP32 with the flag bit of the cells holding samples
+// in c1im, and for the Green table c2 as a half2 scaled by 2^E; a flagged
+// cell's lat_c word is its place in the busy list instead.
 __device__ void dev_table_lattice(int i, const TabView& v, int deg, const double* __restrict__ r,
                                   const double* __restrict__ f, const int32_t* __restrict__ lat_j,
-                                  const int32_t* __restrict__ cmp, bool flag_in_b, float4* la, float4* lb) {
-  if (i < v.n_cmp) {  // compact interval records of the blob
+                                  const int32_t* __restrict__ cmp, float4* la, uint32_t* lc) {
+  if (i < v.n_cmp) {  // full interval records of the blob
     float4* ca = const_cast<float4*>(v.lat_blob) + (v.n_busy + 3) / 4 + v.n_busy + v.n_sub;
     ca[i] = v.c32a[cmp[i]];
     ca[v.n_cmp + i] = v.c32b[cmp[i]];
   }
   if (i >= v.n_lat) return;
-  const float A = __fmaf_rn((float)i, v.lat_h, v.lat_lo);
+  const float A = __fmaf_rn((float)i, v.lat_h, v.lat_amid);
   const int jb = lat_j[i];
   double cre[4], cim[4];
   interval_poly(deg, v.n_nodes, r, f, jb & 0x7fffffff, (double)A, cre, cim);
   float4 a = make_float4((float)cre[0], (float)cim[0], (float)cre[1], (float)cim[1]);
-  float4 b = make_float4((float)cre[2], (float)cim[2], (float)cre[3], (float)cim[3]);
-  // flag bit: the lowest mantissa bit of the last word (changes it by one ulp at most)
+  // flag bit: the lowest mantissa bit of c1im (changes it by one ulp at most)
   const int busy = (int)(((unsigned)jb) >> 31);
-  float& w = flag_in_b ? b.w : a.w;
-  w = __int_as_float((__float_as_int(w) & ~1) | busy);
+  a.w = __int_as_float((__float_as_int(a.w) & ~1) | busy);
+  uint32_t c = 0u;
   if (busy) {  // the cell's place in the busy list, for the exact path
     const int* list = reinterpret_cast<const int*>(v.lat_blob);
     int lo = 0, hi = v.n_busy - 1;
@@ -223,14 +224,15 @@ __device__ void dev_table_lattice(int i, const TabView& v, int deg, const double
       if (list[mid] < i) lo = mid + 1;
       else hi = mid;
     }
-    const int ord = min(lo, kOrdinalMax);
-    if (flag_in_b)  // low 12 bits of c3re: a relative change below 2^-11 of the smallest term
-      b.z = __int_as_float((__float_as_int(b.z) & ~kOrdinalMax) | ord);
-    else  // lat_b is not part of a linear lookup
-      b.x = __int_as_float(ord);
+    c = (uint32_t)lo;
+  } else if (deg > 1) {
+    const double e = 1.0 / (double)v.lat_c2d;  // 2^E
+    const __half2 hv = __floats2half2_rn((float)(cre[2] * e), (float)(cim[2] * e));
+    const __half2_raw hr = hv;
+    c = (uint32_t)hr.x | ((uint32_t)hr.y << 16);
   }
   la[i] = a;
-  lb[i] = b;
+  lc[i] = c;
 }
 
 // The table builds of both tables (Green and Exp) in three launches: sample
@@ -266,7 +268,7 @@ __global__ void k_tables_lattice(TableBuild a, TableBuild b) {
     const TableBuild& T = *t[w];
     const int n = max(T.view.n_lat, T.view.n_cmp);
     if (i < n)
-      return dev_table_lattice(i, T.view, T.deg, T.node64, T.fval, T.lat_j, T.cmp, T.flag_in_b, T.lat_a, T.lat_b);
+      return dev_table_lattice(i, T.view, T.deg, T.node64, T.fval, T.lat_j, T.cmp, T.lat_a, T.lat_c);
     i -= n;
   }
 }
@@ -587,26 +589,17 @@ __global__ void __launch_bounds__(kThreads) k_range64(GeoView g, unsigned long l
   }
 }
 
-template <int M, int MODE, bool SMEM, bool DEFER = true>
-__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoView g, TabView tv, float kpi,
-                                                                          float scale, float inv_k2, float2* Z,
+// One warp per (test triangle p, 32 source triangles) task over the 32 x 32
+// triangle block pairs; SMEM: the table's lattice image staged in shared
+// memory (one CTA of 512 threads per SM holds it), else read through L1.
+template <int M, int MODE, bool SMEM, bool KR>
+__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoView g, TabView tv, RegK K, float2* Z,
                                                                           int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
-  if (MODE != kDirect && SMEM) {  // the lattice image (lat_b only for the cubic Green table)
-    const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
-    float4* sa = reinterpret_cast<float4*>(smem);
-    float4* sb = sa + nl;
-    float4* sblob = MODE == kLagrange ? sb + nl : sb;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-      sa[i] = tv.lat_a[i];
-      if (MODE == kLagrange) sb[i] = tv.lat_b[i];
-    }
-    for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
+  if (MODE != kDirect && SMEM) {
+    stage_tab32(T, tv, MODE == kLagrange ? 3 : 1, smem);
     __syncthreads();
-    T.la = sa;
-    if (MODE == kLagrange) T.lb = sb;  // the Exp table's lat_b (read only on the exact path) stays global
-    tab32_blob(T, tv, sblob);
   }
   const int lane = threadIdx.x & 31;
   const int64_t ntask = regular_units(g.nt);
@@ -614,7 +607,7 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_fill_regular32(GeoVie
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
     if (sym_task(task, g.nt, &p, &q0))
-      regular_task32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, DenseUpper{Z, ldz}, p, q0, lane);
+      regular_task32<M, MODE, KR, SMEM && MODE != kDirect>(g, T, K, DenseUpper{Z, ldz}, p, q0, lane);
   }
 }
 
@@ -740,8 +733,10 @@ constexpr int kTileQBlocks = 16;
 constexpr int kWinBytes = 200 * 1024;
 
 // One warp per block of 32 triangles (lane = triangle): mean of the
-// centroids, then the largest centroid distance plus point radius.
-__global__ void k_block_spheres(GeoView g, float4* bsph) {
+// centroids, then the largest centroid distance plus point radius; the block
+// centre for the split distances is the mean rounded to the grid of step
+// g.bunit.
+__global__ void k_block_spheres(GeoView g, float4* bsph, int4* bgrid) {
   const int b = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nb = (g.nt + 31) / 32;
   if (b >= nb) return;  // uniform over the warp
@@ -758,14 +753,51 @@ __global__ void k_block_spheres(GeoView g, float4* bsph) {
   cz /= n;
   const double dx = x - cx, dy = y - cy, dz = z - cz;
   double r = sqrt(dx * dx + dy * dy + dz * dz) + (double)g.rad32[t];
-  for (int off = 16; off > 0; off >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
-  if (lane == 0) bsph[b] = make_float4((float)cx, (float)cy, (float)cz, (float)(r * (1.0 + 1e-6)));
+  // the farthest vertex from the block's centre (the near-pair screen of a task)
+  double rv = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    const double* gi = g.geo64 + 4 * (3 * (size_t)t + i);  // c - v_i
+    rv = fmax(rv, sqrt(gi[0] * gi[0] + gi[1] * gi[1] + gi[2] * gi[2]));
+  }
+  rv += sqrt(dx * dx + dy * dy + dz * dz);
+  for (int off = 16; off > 0; off >>= 1) {
+    r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
+    rv = fmax(rv, __shfl_xor_sync(0xffffffffu, rv, off));
+  }
+  if (lane == 0) {
+    bsph[b] = make_float4((float)cx, (float)cy, (float)cz, (float)(r * (1.0 + 1e-6)));
+    const double inv = 1.0 / (double)g.bunit;
+    // block centre on the grid; w: the vertex radius about it (bits of a float, rounded up)
+    bgrid[b] = make_int4((int)llrint(cx * inv), (int)llrint(cy * inv), (int)llrint(cz * inv),
+                         __float_as_int((float)((rv + (double)g.bunit) * (1.0 + 1e-6))));
+  }
 }
 
-template <int M>
+// Offsets from the block centres: the rule's points (with their weights) and
+// the vertices opposite each local edge (with s_i l_i), FP64 differences
+// rounded once to FP32.
+__global__ void k_block_offsets(GeoView g, const int4* __restrict__ bgrid, float4* rel32, float4* geob32) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.nt) return;
+  const int4 cb = bgrid[t >> 5];
+  const double u = (double)g.bunit;
+  const double C[3] = {cb.x * u, cb.y * u, cb.z * u};
+  const double* c = g.cen64 + 4 * (size_t)t;
+  for (int a = 0; a < g.m; ++a) {
+    const double* pa = g.pts64 + 4 * ((size_t)a * g.nt + t);
+    rel32[(size_t)a * g.nt + t] = make_float4((float)(c[0] + pa[0] - C[0]), (float)(c[1] + pa[1] - C[1]),
+                                              (float)(c[2] + pa[2] - C[2]), (float)pa[3]);
+  }
+  for (int i = 0; i < 3; ++i) {
+    const double* gi = g.geo64 + 4 * (3 * (size_t)t + i);  // c - v_i, s_i l_i
+    geob32[3 * (size_t)t + i] = make_float4((float)(C[0] - c[0] + gi[0]), (float)(C[1] - c[1] + gi[1]),
+                                            (float)(C[2] - c[2] + gi[2]), (float)gi[3]);
+  }
+}
+
+template <int M, bool KR>
 __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView tv, const float4* __restrict__ bsph,
-                                                            float kpi, float scale, float inv_k2, float2* Z,
-                                                            int64_t ldz) {
+                                                            RegK K, float2* Z, int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int win[5];  // c_lo, c_hi, unused, unused, fits
   const int nb = (g.nt + 31) / 32;
@@ -805,30 +837,36 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
       const int c_hi = min(lat_pos(G, hi * G.xscale).i + 2, n_lat - 1);
       win[0] = c_lo;
       win[1] = c_hi;
-      win[4] = (int64_t)(c_hi - c_lo + 1) * 32 <= kWinBytes;
+      win[4] = (int64_t)(c_hi - c_lo + 1) * 20 + 16 <= kWinBytes;
     }
     __syncthreads();
     Tab32 T = G;
-    if (win[4]) {
+    const bool staged = win[4] != 0;
+    if (staged) {  // the window's (c0, c1) records and c2 words
       const int c_lo = win[0], c_hi = win[1];
       const int nc = c_hi - c_lo + 1;
       float4* sa = reinterpret_cast<float4*>(smem);
-      float4* sb = sa + nc;
+      uint32_t* sc = reinterpret_cast<uint32_t*>(sa + nc);
       for (int i = threadIdx.x; i < nc; i += blockDim.x) {
         sa[i] = G.la[c_lo + i];
-        sb[i] = G.lb[c_lo + i];
+        sc[i] = G.lc[c_lo + i];
       }
       __syncthreads();
       T.la = sa - c_lo;
-      T.lb = sb - c_lo;
+      T.lc = sc - c_lo;
       T.vmin = kLatMagic + (float)c_lo;
       T.vmax = kLatMagic + (float)c_hi;
+      const uint32_t mb = (uint32_t)__float_as_int(kLatMagic) + (uint32_t)c_lo;
+      T.sa_off = (uint32_t)__cvta_generic_to_shared(sa) - mb * 16u;
+      T.sc_off = (uint32_t)__cvta_generic_to_shared(sc) - mb * 4u;
     }
     const int ntask = 32 * (qb1 - qb0);
     for (int task = warp; task < ntask; task += nw) {
       const int p = bp * 32 + task / (qb1 - qb0);
       const int q0 = (qb0 + task % (qb1 - qb0)) * 32;
-      if (p < g.nt) regular_task32<M, kLagrange, false>(g, T, kpi, scale, inv_k2, DenseUpper{Z, ldz}, p, q0, lane);
+      if (p >= g.nt) continue;
+      if (staged) regular_task32<M, kLagrange, KR, true>(g, T, K, DenseUpper{Z, ldz}, p, q0, lane);
+      else regular_task32<M, kLagrange, KR, false>(g, T, K, DenseUpper{Z, ldz}, p, q0, lane);
     }
     __syncthreads();
   }
@@ -836,9 +874,11 @@ __global__ void __launch_bounds__(512) k_fill_regular32_win(GeoView g, TabView t
 
 }  // namespace
 
-cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s) {
+cudaError_t launch_block_frames(const GeoView& g, float4* bsph, int4* bgrid, float4* rel32, float4* geob32,
+                                cudaStream_t s) {
   const int nb = (g.nt + 31) / 32;
-  k_block_spheres<<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(g, bsph);
+  k_block_spheres<<<(unsigned)((nb + 3) / 4), 128, 0, s>>>(g, bsph, bgrid);
+  k_block_offsets<<<(unsigned)((g.nt + 127) / 128), 128, 0, s>>>(g, bgrid, rel32, geob32);
   return cudaGetLastError();
 }
 
@@ -905,45 +945,48 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
   return cudaGetLastError();
 }
 
-template <int M, int MODE>
-cudaError_t launch_regular32_table(const TabView& tv, const GeoView& g, float kpi, float scale, float inv_k2,
-                                   float2* Z, int64_t ldz, cudaStream_t s) {
+template <int M, int MODE, bool KR>
+cudaError_t launch_regular32_table(const TabView& tv, const GeoView& g, const RegK& K, float2* Z, int64_t ldz,
+                                   cudaStream_t s) {
   const size_t smem = tv.smem32_bytes(MODE == kLagrange ? 3 : 1);
   int dev = 0, max_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem <= (size_t)max_optin) {
-    // deferred corrections while at most 0.5 % of the lattice cells hold samples
-    auto kern = tv.n_busy * 200 <= tv.n_lat ? k_fill_regular32<M, MODE, true, true> : k_fill_regular32<M, MODE, true, false>;
+    auto kern = k_fill_regular32<M, MODE, true, KR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 512, smem);
     int64_t blocks = std::min<int64_t>(pair_grid(g, 2 * std::max(per_sm, 1)), (int64_t)sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, K, Z, ldz);
   } else if (MODE == kLagrange && g.bsph) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_fill_regular32_win<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinBytes);
+        cudaFuncSetAttribute(k_fill_regular32_win<M, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinBytes);
     if (e != cudaSuccess) return e;
-    k_fill_regular32_win<M><<<(unsigned)sm_count(), 512, kWinBytes, s>>>(g, tv, g.bsph, kpi, scale, inv_k2, Z, ldz);
+    k_fill_regular32_win<M, KR><<<(unsigned)sm_count(), 512, kWinBytes, s>>>(g, tv, g.bsph, K, Z, ldz);
   } else {
     int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, MODE, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+    k_fill_regular32<M, MODE, false, KR><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
   }
   return cudaGetLastError();
 }
 
 template <int M>
-cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_exp, float kpi, float scale,
-                             float inv_k2, float2* Z, int64_t ldz, cudaStream_t s) {
+cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_exp, const RegK& K, float2* Z,
+                             int64_t ldz, cudaStream_t s) {
   if (!table) {
     TabView tv{};
     int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, kDirect, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2, Z, ldz);
+    k_fill_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
     return cudaGetLastError();
   }
-  if (from_exp) return launch_regular32_table<M, kExpOverR>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
-  return launch_regular32_table<M, kLagrange>(*table, g, kpi, scale, inv_k2, Z, ldz, s);
+  const bool kr = table->xscale32 != 1.f;
+  if (from_exp)
+    return kr ? launch_regular32_table<M, kExpOverR, true>(*table, g, K, Z, ldz, s)
+              : launch_regular32_table<M, kExpOverR, false>(*table, g, K, Z, ldz, s);
+  return kr ? launch_regular32_table<M, kLagrange, true>(*table, g, K, Z, ldz, s)
+            : launch_regular32_table<M, kLagrange, false>(*table, g, K, Z, ldz, s);
 }
 
 // Z <- Z + Z^T on the ne x ne block (row-major, leading dimension ldz): the
@@ -996,17 +1039,17 @@ cudaError_t launch_fill_regular(const GeoView& g, const TabView* table, bool fro
       k_fill_regular64<kLagrange><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, k, scale, ik2, (double2*)Z, ldz);
     return cudaGetLastError();
   }
-  const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
+  const RegK K = reg_consts(k, scale);
   float2* Z32 = (float2*)Z;
   // each unordered pair into its test triangle's rows (launch_mirror32 adds
   // the transpose)
   cudaError_t e;
   switch (g.m) {
-    case 1: e = launch_regular32<1>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
-    case 3: e = launch_regular32<3>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
-    case 4: e = launch_regular32<4>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
-    case 6: e = launch_regular32<6>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
-    case 7: e = launch_regular32<7>(g, table, from_exp, kpi, sc, ik2, Z32, ldz, s); break;
+    case 1: e = launch_regular32<1>(g, table, from_exp, K, Z32, ldz, s); break;
+    case 3: e = launch_regular32<3>(g, table, from_exp, K, Z32, ldz, s); break;
+    case 4: e = launch_regular32<4>(g, table, from_exp, K, Z32, ldz, s); break;
+    case 6: e = launch_regular32<6>(g, table, from_exp, K, Z32, ldz, s); break;
+    case 7: e = launch_regular32<7>(g, table, from_exp, K, Z32, ldz, s); break;
     default: return cudaErrorInvalidValue;
   }
   return e;

@@ -327,7 +327,9 @@ gf::TabView gf_table::One::view() const {
   v.lat_blob = d_lat_blob;
   v.n_busy = n_busy;
   v.n_cmp = n_cmp;
-  v.lat_b = d_lat_b;
+  v.lat_c = d_lat_c;
+  v.lat_amid = lat_amid;
+  v.lat_c2d = lat_c2d;
   v.n_cells64 = n_cells64;
   v.lo64c = lo64c;
   v.inv64c = inv64c;
@@ -440,6 +442,17 @@ void vertex_arrays(const gf_mesh* m, unsigned char* dst) {
   }
 }
 
+// Step 2^e of the block-centre grid: every coordinate of the mesh (and so of
+// every block centre) below 2^14 - 2 steps, so block separations stay below
+// 2^15 steps and |B|^2 fits an unsigned 32-bit integer.
+void set_block_grid(gf_mesh* m) {
+  double mx = 0.0;
+  for (double x : m->xyz) mx = std::max(mx, std::fabs(x));
+  int e = -60;
+  while (e < 100 && std::ldexp(16382.0, e) <= mx) ++e;
+  m->bgrid_e = e;
+}
+
 size_t vertex_bytes(const gf_mesh* m) {
   return (size_t)(reinterpret_cast<unsigned char*>(m->d_elen) - reinterpret_cast<unsigned char*>(m->d_v64)) +
          (size_t)std::max<int64_t>(m->ne, 1) * 8;
@@ -508,7 +521,7 @@ gf_status prepare_rule_impl(gf_mesh* m, int rule, cudaStream_t s) {
                              m->d_frame64, m->d_frame32, s);
   if (e == cudaSuccess) {
     m->rule = rule;  // views below read the new geometry
-    e = launch_block_spheres(geo_view_impl(m), m->d_bsph, s);
+    e = launch_block_frames(geo_view_impl(m), m->d_bsph, m->d_bgrid, m->d_rel32, m->d_geob32, s);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d_bw);
@@ -541,6 +554,11 @@ GeoView geo_view_impl(const gf_mesh* m) {
   g.near_dist32 = (float)m->near_dist;
   g.rad32 = m->d_rad32;
   g.bsph = m->d_bsph;
+  g.bgrid = m->d_bgrid;
+  g.rel32 = m->d_rel32;
+  g.geob32 = m->d_geob32;
+  g.bunit = std::ldexp(1.f, m->bgrid_e);
+  g.bunit2 = std::ldexp(1.f, 2 * m->bgrid_e);
   return g;
 }
 
@@ -597,6 +615,7 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   m->nt = nt;
   m->near_dist = near_dist;
   m->xyz.assign(xyz, xyz + 3 * nv);
+  set_block_grid(m.get());
   m->tri.assign(tri, tri + 3 * nt);
   // ---- RWG edges: records (lower, higher vertex) in (triangle, local index)
   // order, sorted stably by the vertex pair (radix)
@@ -756,6 +775,7 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
                o_pts64 = take(32 * kMaxRule * nt), o_cen64 = take(32 * nt), o_geo64 = take(96 * nt),
                o_frame64 = take(8 * kFrame * nt), o_frame32 = take(4 * kFrame32 * nt), o_minmax = take(64),
                o_rad32 = take(4 * nt), o_bsph = take(16 * nb), o_bpb = take(8 * (size_t)(nb * (nb + 1) / 2)),
+               o_bgrid = take(16 * nb), o_rel32 = take(16 * kMaxRule * nt), o_geob32 = take(48 * nt),
                o_list = take(4 * range_list_ints(nt));
   size_t got = 0;
   unsigned char* base = static_cast<unsigned char*>(arena_take(m->device, off, &got));
@@ -784,6 +804,9 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   m->d_minmax = reinterpret_cast<unsigned long long*>(base + o_minmax);
   m->d_rad32 = reinterpret_cast<float*>(base + o_rad32);
   m->d_bsph = reinterpret_cast<float4*>(base + o_bsph);
+  m->d_bgrid = reinterpret_cast<int4*>(base + o_bgrid);
+  m->d_rel32 = reinterpret_cast<float4*>(base + o_rel32);
+  m->d_geob32 = reinterpret_cast<float4*>(base + o_geob32);
   m->d_range_bpb = reinterpret_cast<float2*>(base + o_bpb);
   m->d_range_list = reinterpret_cast<int32_t*>(base + o_list);
   std::vector<unsigned char> h(upload, 0);
@@ -833,6 +856,7 @@ gf_status gf_mesh_set_vertices(gf_mesh* m, const double* xyz) {
   for (int64_t i = 0; i < 3 * m->nv; ++i)
     if (!std::isfinite(xyz[i])) return fail(GF_ERR_MESH, "gf_mesh_set_vertices: non-finite coordinate");
   m->xyz.assign(xyz, xyz + 3 * m->nv);
+  set_block_grid(m);
   return upload_vertices(m);
 }
 
@@ -869,7 +893,7 @@ namespace {
 // FP32 lattice image of a table (the device lookups repeat these float
 // operations exactly): u = fma(x, inv, nc); v = clamp(u + kLatMagic); the
 // cell i is the integer in v, and s = x - fma(i, h, lo) the offset from its
-// anchor.
+// left end (the sub-cells of a cell holding samples are counted from there).
 struct LatPos {
   int i;
   float s;
@@ -888,7 +912,7 @@ float bits_float(int32_t v) {
 }
 
 struct LatMap {
-  float inv, nc, h, lo;
+  float inv, nc, h, lo, amid;
 };
 
 LatPos lattice_pos(float x, const LatMap& M, float vmin, float vmax) {
@@ -909,6 +933,7 @@ int lattice_sub(float s, float inv_w, int nsub) {
 struct Lattice {
   int n = 0;
   LatMap map{};
+  float c2d = 0.f;            // 2^-E of the Green table's c2 halves
   std::vector<int32_t> j;     // interval containing the middle of each cell; bit 31: the cell holds samples
   std::vector<int32_t> busy;  // cells holding samples, ascending
   std::vector<float4> hdr;    // per busy cell: (first sub-cell, 1/w, count - 1, 0)
@@ -920,7 +945,25 @@ struct Lattice {
 };
 
 // Shared-memory budget of a lattice image for choosing the finer step.
-constexpr int64_t kLatticeSmemBudget = 192 * 1024;
+constexpr int64_t kLatticeSmemBudget = 210 * 1024;
+
+// Bound of |f^(n)| for f = e^{-jkr}/r at r (it decreases with r): the
+// Leibniz sum sum_i C(n, i) k^(n-i) i! / r^(i+1).
+double green_deriv_bound(int n, double k, double r) {
+  double s = 0.0, c = 1.0, fact = 1.0;
+  for (int i = 0; i <= n; ++i) {
+    if (i > 0) {
+      c = c * (n - i + 1) / i;
+      fact *= i;
+    }
+    s += c * std::pow(k, n - i) * fact / std::pow(r, i + 1);
+  }
+  return s;
+}
+
+// Relative size (to |f| on the cell) below which the cubic term of the Green
+// table's cell polynomial is left out of the lattice record.
+constexpr double kDropC3 = 4e-8;
 
 // Cells of width `step` (t or t / 2) from r_min (the uniform samples of Eq. 2,
 // and the refined ones for t / 2, sit on their ends). A cell is sample-free
@@ -930,12 +973,14 @@ constexpr int64_t kLatticeSmemBudget = 192 * 1024;
 // extrapolation by at most the margin. Cells holding samples get sub-cells
 // narrower than the local spacing, so each holds one sample at most and the
 // bracketing against the FP32 samples is exact.
-gf_status build_lattice(const std::vector<double>& r, double step, Lattice* L) {
+gf_status build_lattice(const std::vector<double>& r, double step, double t, int degree, double k,
+                        Lattice* L) {
   const size_t n = r.size();
   LatMap& M = L->map;
   M.lo = (float)r.front();
   M.h = (float)step;
   M.inv = (float)(1.0 / step);
+  M.amid = degree > 1 ? (float)(r.front() + 0.5 * step) : M.lo;
   const float c = (float)((double)M.lo * (double)M.inv + 0.5);
   M.nc = -c;
   const float hi32 = (float)r.back();
@@ -954,6 +999,32 @@ gf_status build_lattice(const std::vector<double>& r, double step, Lattice* L) {
     const double ci = std::floor(v + 0.5), d = v - ci;  // d in [-1/2, 1/2)
     const int64_t i = (int64_t)ci;
     if (std::fabs(d) < 0.5 - eps && i >= 0 && i < L->n) busy[i] = 1;
+  }
+  L->c2d = 0.f;
+  if (degree > 1) {
+    // Green table records hold c0, c1 and c2 (a half2 scaled by 2^E). A cell
+    // is treated as one holding samples where the left-out cubic term could
+    // exceed kDropC3 |f| (|c3| <= max |f'''| / 3! over the stencil, which
+    // starts at most one spacing t below the cell), or where c2 falls out of
+    // the half range: |c2| <= max |f''| / 2 + 3 |c3| 1.5 t (the expansion
+    // point lies within 1.5 t of the stencil's middle) and |c2| >= 0.9 k / r^2
+    // (|f''| >= 2 k / r^2).
+    const double hh = 0.51 * step, r0 = r.front();
+    double c2max = 0.0;
+    std::vector<double> lo_c2(L->n, 0.0);
+    for (int i = 0; i < L->n; ++i) {
+      const double rl = r0 + i * step, rh = rl + step, rs = std::max(rl - 1.01 * t, r0);
+      const double c3 = green_deriv_bound(3, k, rs) / 6.0;
+      if (c3 * hh * hh * hh > kDropC3 / rh) busy[i] = 1;
+      if (busy[i]) continue;
+      c2max = std::max(c2max, green_deriv_bound(2, k, rs) / 2.0 + 4.5 * t * c3);
+      lo_c2[i] = 0.9 * k / (rh * rh);
+    }
+    int E = c2max > 0.0 ? (int)std::floor(std::log2(32768.0 / c2max)) : 0;
+    E = std::min(std::max(E, -120), 120);
+    L->c2d = (float)std::ldexp(1.0, -E);
+    for (int i = 0; i < L->n; ++i)
+      if (!busy[i] && std::ldexp(lo_c2[i], E) < std::ldexp(1.0, -13)) busy[i] = 1;
   }
   L->j.assign(L->n, 0);
   L->busy.clear();
@@ -1053,12 +1124,12 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     // lattice step: t / 2 (the refined spacing, so refinement windows hold no
     // sample inside a cell) when that image fits the shared-memory budget,
     // else t
-    const double rec = o.degree > 1 ? 32.0 : 16.0;
+    const double rec = o.degree > 1 ? 20.0 : 16.0;
     const double h = p->refine && (r_max - r_min) / (0.5 * t) * rec <= (double)kLatticeSmemBudget &&
                              std::fabs(p->refine_factor - 0.5) < 1e-12
                          ? 0.5 * t
                          : t;
-    if ((st = build_lattice(o.r, h, &lat[which]))) return st;
+    if ((st = build_lattice(o.r, h, t, o.degree, k, &lat[which]))) return st;
     o.n_lat = lat[which].n;
     o.n_busy = (int)lat[which].busy.size();
     o.n_sub = (int)lat[which].sub.size();
@@ -1067,6 +1138,8 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o.lat_nc = lat[which].map.nc;
     o.lat_h = lat[which].map.h;
     o.lat_lo = lat[which].map.lo;
+    o.lat_amid = lat[which].map.amid;
+    o.lat_c2d = lat[which].c2d;
     o.lo64c = r_min;
     o.inv64c = 1.0 / (0.99 * o.dr);
     o.n_cells64 = (int)std::floor((r_max - r_min) * o.inv64c) + 1;
@@ -1094,7 +1167,7 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o_lat_blob[w] = take(lat[w].blob_vec4() * 16);
   }
   const size_t upload = off;
-  size_t o_fval[2], o_c64[2], o_node32[2], o_c32a[2], o_c32b[2], o_hash[2], o_lat_a[2], o_lat_b[2], o_cells64[2];
+  size_t o_fval[2], o_c64[2], o_node32[2], o_c32a[2], o_c32b[2], o_hash[2], o_lat_a[2], o_lat_c[2], o_cells64[2];
   for (int w = 0; w < 2; ++w) {
     const gf_table::One& o = *ones[w];
     const size_t n = o.r.size();
@@ -1105,7 +1178,7 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o_c32b[w] = take(n * 16);
     o_hash[w] = take((size_t)o.n_hash * 4);
     o_lat_a[w] = take((size_t)o.n_lat * 16);
-    o_lat_b[w] = take((size_t)o.n_lat * 16);
+    o_lat_c[w] = take((size_t)o.n_lat * 4);
     o_cells64[w] = take((size_t)o.n_cells64 * sizeof(Cell64));
   }
   std::vector<unsigned char> hbuf(upload, 0);
@@ -1146,7 +1219,7 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     o.d_c32a = reinterpret_cast<float4*>(base + o_c32a[w]);
     o.d_c32b = reinterpret_cast<float4*>(base + o_c32b[w]);
     o.d_hash = reinterpret_cast<int32_t*>(base + o_hash[w]);
-    o.d_lat_b = reinterpret_cast<float4*>(base + o_lat_b[w]);
+    o.d_lat_c = reinterpret_cast<uint32_t*>(base + o_lat_c[w]);
     o.d_cells64 = reinterpret_cast<Cell64*>(base + o_cells64[w]);
   }
   // ---- device: values, coefficients, hash and images of both tables
@@ -1176,9 +1249,8 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
     b.view = o.view();
     b.lat_j = o.d_lat_j;
     b.cmp = o.d_lat_cmp;
-    b.flag_in_b = o.kind == GF_GREEN;
     b.lat_a = o.d_lat_a;
-    b.lat_b = o.d_lat_b;
+    b.lat_c = o.d_lat_c;
   }
   if (e == cudaSuccess) e = launch_tables(tb[0], tb[1], k, s);
   if (e != cudaSuccess) {
@@ -1235,6 +1307,57 @@ gf_status gf_table_eval(const gf_table* t, int kind, int precision, const void* 
   if (n == 0) return GF_OK;
   GF_CUDA(launch_table_eval(t->get(kind).view(), kind, precision, r_dev, n, out_dev, (cudaStream_t)stream));
   return GF_OK;
+}
+
+gf_status gf_table_eval_host(const gf_table* t, int kind, const double* x, int64_t n, double* out) {
+  if (!t || (kind != GF_GREEN && kind != GF_EXP) || n < 0 || (n > 0 && (!x || !out)))
+    return fail(GF_ERR_ARG, "gf_table_eval_host: bad argument");
+  if (n == 0) return GF_OK;
+  gf_status st = check_device(t->device);
+  if (st) return st;
+  const gf_table::One& o = t->get(kind);
+  const size_t nn = o.r.size();
+  for (int64_t i = 0; i < n; ++i)
+    if (!(x[i] >= o.r.front() && x[i] <= o.r.back()))
+      return fail(GF_ERR_RANGE, "gf_table_eval_host: x outside the table's range");
+  // the FP64 interval polynomials and cell records of the device image
+  std::vector<double2> c64(4 * nn);
+  std::vector<Cell64> cells((size_t)o.n_cells64);
+  GF_CUDA(cudaDeviceSynchronize());  // the table's kernels may still run on the creation stream
+  GF_CUDA(cudaMemcpy(c64.data(), o.d_c64, c64.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+  GF_CUDA(cudaMemcpy(cells.data(), o.d_cells64, cells.size() * sizeof(Cell64), cudaMemcpyDeviceToHost));
+  const int deg = o.degree > 1 ? 3 : 1;
+  for (int64_t i = 0; i < n; ++i) {
+    // the FP64 cell of x brackets it exactly (one sample per cell at most)
+    int c = (int)((x[i] - o.lo64c) * o.inv64c);
+    c = std::min(std::max(c, 0), o.n_cells64 - 1);
+    const Cell64& rec = cells[c];
+    const bool up = x[i] >= rec.split;
+    const int j = rec.j0 + (up ? 1 : 0);
+    const double s = x[i] - (up ? rec.split : rec.anchor);
+    const double2* cf = &c64[4 * (size_t)j];
+    double re = cf[deg].x, im = cf[deg].y;
+    for (int q = deg - 1; q >= 0; --q) {
+      re = std::fma(s, re, cf[q].x);
+      im = std::fma(s, im, cf[q].y);
+    }
+    out[2 * i] = re;
+    out[2 * i + 1] = im;
+  }
+  return GF_OK;
+}
+
+gf_status gf_table_create_for_mesh(const gf_mesh* m, double k, const gf_params* p, int precision, double r_min,
+                                   double r_max, void* stream, gf_table** out) {
+  if (!m || !p || !out) return fail(GF_ERR_ARG, "gf_table_create_for_mesh: bad argument");
+  if (r_min < 0 || r_max < 0) {
+    double lo = 0, hi = 0;
+    gf_status st = gf_range(m, p->rule, precision, &lo, &hi, stream);
+    if (st) return st;
+    if (r_min < 0) r_min = lo;
+    if (r_max < 0) r_max = hi;
+  }
+  return gf_table_create(k, r_min, r_max, p, stream, out);
 }
 
 gf_status gf_table_destroy(gf_table* t) {

@@ -59,6 +59,13 @@ struct GeoView {
   float near_dist32;        // > 0: centroid criterion present (FP32 screen)
   const float* rad32;       // [nt]: largest |point - centroid| of the rule, rounded up
   const float4* bsph;       // [ceil(nt/32)]: bounding sphere of each block of 32 triangles (with points)
+  // Block frames of the FP32 regular pairs: the centre of each block of 32
+  // triangles on a grid of step bunit = 2^e (bgrid, in grid units; every
+  // coordinate below 2^14 units), and offsets from it.
+  const int4* bgrid;        // [ceil(nt/32)]
+  const float4* rel32;      // [m][nt]: point a minus its block's centre (FP32 of the FP64 difference), weight
+  const float4* geob32;     // [nt][3]: block centre minus v_i (the vertex opposite local edge i), s_i l_i
+  float bunit, bunit2;      // 2^e, 2^(2e)
 };
 
 // FP64 cell record: every x in the cell lies in interval j0 if x < split,
@@ -82,29 +89,41 @@ struct TabView {
   // FP32 lattice image. Cells of step h (the base spacing t of Eq. 2, or the
   // refined t / 2) from r_min, aligned with the samples r_min + i h: cell i
   // holds the x with rint(fma(x, lat_inv, lat_nc)) = i (lat_nc = -(r_min / h +
-  // 1/2)), found without a conversion instruction (kLatMagic), and its anchor
-  // is A_i = fma(i, lat_h, lat_lo). lat_a/lat_b hold, for every cell, the
-  // polynomial (in s = x - A_i) of the interval that contains the cell's
-  // middle, so one lookup is two 16-byte records (one for the linear Exp
-  // table). A cell with no sample inside (farther than a rounding margin from
-  // its ends) lies in that interval. A cell holding samples (a forced zero,
-  // grading, r_max) is flagged by the lowest mantissa bit of its last record
-  // word (c3im of the Green table, c1im of the Exp table; clear elsewhere);
-  // the blob lists those cells (ascending), a header per cell (first
-  // sub-cell, 1/w, count - 1), sub-cells trunc(s / w) = (compact interval j0,
-  // split, node32[j0], 0) -- x lies in j0 if x < split, else in j0 + 1 whose
-  // anchor is split -- and the compact interval records about node32 (a, b).
+  // 1/2)), found without a conversion instruction (kLatMagic). Its left end is
+  // L_i = fma(i, lat_h, lat_lo) and its anchor A_i = fma(i, lat_h, lat_amid):
+  // the middle of the cell for the Green table, L_i for the Exp table. For
+  // every cell, lat_a holds the polynomial (in s = x - A_i) of the interval
+  // that contains the cell's middle: (c0, c1) in FP32 for both tables; the
+  // Green table's c2 sits in lat_c as two halves scaled by 2^E (c2 =
+  // half * lat_c2d, lat_c2d = 2^-E), and its c3 is left out (the cells where
+  // |c3| (h/2)^3 could exceed 4e-8 of |f| are treated as cells holding
+  // samples). So one lookup is a 16-byte record plus a 4-byte one (Green) or
+  // one 16-byte record (Exp). A cell with no sample inside (farther than a
+  // rounding margin from its ends) lies in that interval. A cell holding
+  // samples (a forced zero, grading, r_max; for the Green table also the c3
+  // and c2-range tests) is flagged by the lowest mantissa bit of c1im, and
+  // its lat_c word is its place in the blob's busy list; the blob lists those
+  // cells (ascending), a header per cell (first sub-cell, 1/w, count - 1),
+  // sub-cells trunc((x - L_i) / w) = (compact interval j0, split, node32[j0],
+  // 0) -- x lies in j0 if x < split, else in j0 + 1 whose anchor is split --
+  // and the full FP32 interval records about node32 (a, b).
   int n_lat, n_busy, n_sub, n_cmp;
   float lat_inv, lat_nc, lat_h, lat_lo;
-  const float4* lat_a;     // [n_lat]: (c0re, c0im, c1re, c1im) about A_i
-  const float4* lat_b;     // [n_lat]: (c2re, c2im, c3re, c3im)
+  float lat_amid = 0.f;    // anchor base (see above)
+  float lat_c2d = 0.f;     // 2^-E: c2 = half value * lat_c2d (Green)
+  const float4* lat_a;     // [n_lat]: (c0re, c0im, c1re, c1im) about A_i; busy flag in c1im
+  const uint32_t* lat_c;   // [n_lat]: c2 as half2 scaled by 2^E (Green), or the busy ordinal
   const float4* lat_blob;  // [blob_vec4()]
   __host__ __device__ size_t blob_vec4() const { return ((size_t)n_busy + 3) / 4 + n_busy + n_sub + 2 * (size_t)n_cmp; }
+  // bytes of the lattice planes in shared memory for a lookup of degree deg
+  // (lat_c only for deg > 1, padded to 16 bytes), then the blob
+  __host__ __device__ size_t smem32_plane_bytes(int deg) const {
+    return (size_t)n_lat * 16 + (deg > 1 ? (((size_t)n_lat * 4 + 15) & ~(size_t)15) : 0);
+  }
+  __host__ __device__ size_t smem32_bytes(int deg) const { return smem32_plane_bytes(deg) + blob_vec4() * 16; }
   int n_cells64;  // FP64 image of the Eq. (6) hash: cells of width 0.99 dr, one sample at most each
   double lo64c, inv64c;
   const Cell64* cells64;
-  // shared-memory image of the lattice for a lookup of degree deg (lat_b only for deg > 1)
-  __host__ __device__ size_t smem32_bytes(int deg) const { return (size_t)n_lat * (deg > 1 ? 32 : 16) + blob_vec4() * 16; }
   // lookups at x = xscale * R: 1 for a table in R, k for a table in u = kR
   // (a frequency-sweep table, one for every k; r_lo, r_hi then bound u)
   float xscale32 = 1.f;
@@ -125,12 +144,28 @@ __host__ __device__ inline int64_t regular_units(int nt) {
   return 32 * (nb * (nb + 1) / 2);
 }
 
+// Per-fill constants of the FP32 regular-pair kernels.
+struct RegK {
+  float kpi, kpi_lo;  // k / pi and its FP32 residue
+  float scale;        // k eta / (4 pi) (times k for tables in u = kR)
+  float inv_k2;       // 1 / k^2
+};
+
+inline RegK reg_consts(double k, double scale) {
+  RegK K;
+  K.kpi = (float)(k / kPi);
+  K.kpi_lo = (float)(k / kPi - (double)K.kpi);
+  K.scale = (float)scale;
+  K.inv_k2 = (float)(1.0 / (k * k));
+  return K;
+}
+
 // One mesh of a batched fill (device-resident descriptor).
 struct BatchItem {
   GeoView g;
   TabView green, exp;
   int use_table;
-  float kpi, scale32, inv_k2_32;  // k/pi, k eta/(4 pi), 1/k^2 for the FP32 regular kernel
+  RegK rk;                        // constants of the FP32 regular kernel
   double k, scale, inv_k2;        // k, k eta, 1/k^2 for the near kernel
   void* Z;
   int64_t ldz;
@@ -165,14 +200,16 @@ struct TableBuild {
   TabView view;
   const int32_t* lat_j;  // interval of each lattice cell's middle, bit 31: the cell holds samples
   const int32_t* cmp;    // interval of each compact record of the blob
-  bool flag_in_b;        // the flag bit sits in lat_b (Green) or lat_a (Exp)
   float4* lat_a;
-  float4* lat_b;
+  uint32_t* lat_c;
 };
 // Values, Eq. (6) hash, FP64 cells, coefficients and lattice images of two
 // tables in three launches on s.
 cudaError_t launch_tables(const TableBuild& a, const TableBuild& b, double k, cudaStream_t s);
-cudaError_t launch_block_spheres(const GeoView& g, float4* bsph, cudaStream_t s);
+// Block spheres, block centres on the grid of step g.bunit, and the offsets
+// from them (rel32, geob32) of the current rule's geometry.
+cudaError_t launch_block_frames(const GeoView& g, float4* bsph, int4* bgrid, float4* rel32, float4* geob32,
+                                cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
                               void* out, cudaStream_t s);
 // bpb: scratch of nb (nb + 1) / 2 float2 (nb = ceil(nt / 32)) for the FP32 screen.
@@ -255,6 +292,10 @@ struct gf_mesh {
   float* d_frame32 = nullptr;
   float* d_rad32 = nullptr;
   float4* d_bsph = nullptr;
+  int4* d_bgrid = nullptr;
+  float4* d_rel32 = nullptr;
+  float4* d_geob32 = nullptr;
+  int bgrid_e = 0;                          // block-centre grid step 2^bgrid_e
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
   double* d_dk = nullptr;                   // adjoint scratch [1]
   unsigned long long* d_minmax = nullptr;  // range scratch [8]
@@ -283,10 +324,10 @@ struct gf_table {
     float4* d_c32b = nullptr;
     int32_t* d_hash = nullptr;
     int n_lat = 0, n_busy = 0, n_sub = 0, n_cmp = 0;
-    float lat_inv = 0.f, lat_nc = 0.f, lat_h = 0.f, lat_lo = 0.f;
+    float lat_inv = 0.f, lat_nc = 0.f, lat_h = 0.f, lat_lo = 0.f, lat_amid = 0.f, lat_c2d = 0.f;
     int32_t* d_lat_j = nullptr;
     float4* d_lat_a = nullptr;
-    float4* d_lat_b = nullptr;
+    uint32_t* d_lat_c = nullptr;
     int32_t* d_lat_cmp = nullptr;
     float4* d_lat_blob = nullptr;
     int n_cells64 = 0;

@@ -172,19 +172,8 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_mfie_regular32(GeoVie
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
   if (MODE == kLagrange && SMEM) {
-    const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
-    float4* sa = reinterpret_cast<float4*>(smem);
-    float4* sb = sa + nl;
-    float4* sblob = sb + nl;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-      sa[i] = tv.lat_a[i];
-      sb[i] = tv.lat_b[i];
-    }
-    for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
+    stage_tab32(T, tv, 3, smem);
     __syncthreads();
-    T.la = sa;
-    T.lb = sb;
-    tab32_blob(T, tv, sblob);
   }
   const int lane = threadIdx.x & 31;
   const int64_t nb = (g.nt + 31) / 32, ntask = (int64_t)g.nt * nb;

@@ -17,28 +17,16 @@ struct SparseTask {
   int64_t off;   // first source triangle in the work list
 };
 
-template <int M, int MODE, bool SMEM, bool DEFER>
-__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_sparse_regular32(GeoView g, TabView tv, float kpi,
-                                                                            float scale, float inv_k2,
+template <int M, int MODE, bool SMEM, bool KR>
+__global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_sparse_regular32(GeoView g, TabView tv, RegK K,
                                                                             const SparseTask* __restrict__ tasks,
                                                                             int64_t ntask, const int32_t* __restrict__ widx,
                                                                             CsrSink<float2> sink) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
   if (MODE != kDirect && SMEM) {
-    const int nl = tv.n_lat, nblob = (int)tv.blob_vec4();
-    float4* sa = reinterpret_cast<float4*>(smem);
-    float4* sb = sa + nl;
-    float4* sblob = sb + nl;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) {
-      sa[i] = tv.lat_a[i];
-      sb[i] = tv.lat_b[i];
-    }
-    for (int i = threadIdx.x; i < nblob; i += blockDim.x) sblob[i] = tv.lat_blob[i];
+    stage_tab32(T, tv, 3, smem);
     __syncthreads();
-    T.la = sa;
-    T.lb = sb;
-    tab32_blob(T, tv, sblob);
   }
   const int lane = threadIdx.x & 31;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -46,7 +34,7 @@ __global__ void __launch_bounds__(SMEM ? 512 : kThreads) k_sparse_regular32(GeoV
     const SparseTask tk = tasks[t];
     const bool ok = lane < tk.n;
     const int q = ok ? widx[tk.off + lane] : tk.p;
-    regular_pair32<M, MODE, DEFER>(g, T, kpi, scale, inv_k2, tk.p, q, ok, sink);
+    regular_pair32<M, MODE, KR, SMEM && MODE != kDirect>(g, T, K, tk.p, q, ok, sink);
   }
 }
 
@@ -71,16 +59,15 @@ __global__ void __launch_bounds__(128) k_sparse_near(GeoView g, TabView te, bool
 
 }  // namespace
 
-template <int M>
-cudaError_t launch_sparse32(const GeoView& g, const TabView* table, float kpi, float scale, float inv_k2,
-                            const SparseTask* tasks, int64_t ntask, const int32_t* widx, CsrSink<float2> sink,
-                            cudaStream_t s) {
+template <int M, bool KR>
+cudaError_t launch_sparse32(const GeoView& g, const TabView* table, const RegK& K, const SparseTask* tasks,
+                            int64_t ntask, const int32_t* widx, CsrSink<float2> sink, cudaStream_t s) {
   if (ntask == 0) return cudaSuccess;
   if (!table) {
     TabView tv{};
     const int64_t blocks = std::min<int64_t>((ntask + kWarps - 1) / kWarps, (int64_t)sm_count() * 4);
-    k_sparse_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2,
-                                                                                      tasks, ntask, widx, sink);
+    k_sparse_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, tasks, ntask, widx,
+                                                                                      sink);
     return cudaGetLastError();
   }
   const TabView& tv = *table;
@@ -89,18 +76,24 @@ cudaError_t launch_sparse32(const GeoView& g, const TabView* table, float kpi, f
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (smem <= (size_t)max_optin) {
-    auto kern = tv.n_busy * 200 <= tv.n_lat ? k_sparse_regular32<M, kLagrange, true, true>
-                                            : k_sparse_regular32<M, kLagrange, true, false>;
+    auto kern = k_sparse_regular32<M, kLagrange, true, KR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t blocks = std::min<int64_t>((ntask + 15) / 16, (int64_t)sm_count());
-    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, kpi, scale, inv_k2, tasks, ntask, widx, sink);
+    kern<<<(unsigned)blocks, 512, smem, s>>>(g, tv, K, tasks, ntask, widx, sink);
   } else {
     const int64_t blocks = std::min<int64_t>((ntask + kWarps - 1) / kWarps, (int64_t)sm_count() * 4);
-    k_sparse_regular32<M, kLagrange, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, kpi, scale, inv_k2,
-                                                                                        tasks, ntask, widx, sink);
+    k_sparse_regular32<M, kLagrange, false, KR><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, tasks, ntask, widx,
+                                                                                     sink);
   }
   return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t launch_sparse32_any(const GeoView& g, const TabView* table, const RegK& K, const SparseTask* tasks,
+                                int64_t ntask, const int32_t* widx, CsrSink<float2> sink, cudaStream_t s) {
+  if (table && table->xscale32 != 1.f) return launch_sparse32<M, true>(g, table, K, tasks, ntask, widx, sink, s);
+  return launch_sparse32<M, false>(g, table, K, tasks, ntask, widx, sink, s);
 }
 
 cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const TabView* texp, double green_scale,
@@ -110,14 +103,14 @@ cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const Tab
   const SparseTask* tasks = static_cast<const SparseTask*>(tasks_v);
   CsrSink<float2> sink{row_ptr, cols, static_cast<float2*>(vals)};
   const double scale = k * eta / (4.0 * kPi) * (green ? green_scale : 1.0);
-  const float kpi = (float)(k / kPi), sc = (float)scale, ik2 = (float)(1.0 / (k * k));
+  const RegK K = reg_consts(k, scale);
   cudaError_t e;
   switch (g.m) {
-    case 1: e = launch_sparse32<1>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
-    case 3: e = launch_sparse32<3>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
-    case 4: e = launch_sparse32<4>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
-    case 6: e = launch_sparse32<6>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
-    case 7: e = launch_sparse32<7>(g, green, kpi, sc, ik2, tasks, ntask, widx, sink, s); break;
+    case 1: e = launch_sparse32_any<1>(g, green, K, tasks, ntask, widx, sink, s); break;
+    case 3: e = launch_sparse32_any<3>(g, green, K, tasks, ntask, widx, sink, s); break;
+    case 4: e = launch_sparse32_any<4>(g, green, K, tasks, ntask, widx, sink, s); break;
+    case 6: e = launch_sparse32_any<6>(g, green, K, tasks, ntask, widx, sink, s); break;
+    case 7: e = launch_sparse32_any<7>(g, green, K, tasks, ntask, widx, sink, s); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;

@@ -27,7 +27,8 @@ EXPORTS = ["gf_params_default", "gf_last_error", "gf_mesh_create", "gf_mesh_info
            "gf_table_nodes", "gf_table_eval", "gf_table_destroy", "gf_fill", "gf_fill_parts", "gf_range_noalloc", "gf_batch_create", "gf_batch_launch",
            "gf_batch_config", "gf_batch_destroy", "gf_fill_backward", "gf_excitation", "gf_far_field",
            "gf_fill_mfie", "gf_sparse_create", "gf_sparse_info", "gf_sparse_pattern", "gf_fill_sparse",
-           "gf_sparse_destroy", "gf_table_create_kr"]
+           "gf_sparse_destroy", "gf_table_create_kr", "gf_table_eval_host", "gf_table_create_for_mesh",
+           "gf_fill_batched"]
 GF_NOALLOC_MAX_POINTS = 131072
 GF_PART_ZERO, GF_PART_REGULAR, GF_PART_NEAR, GF_PART_PAIRS, GF_PART_MIRROR = 1, 2, 4, 8, 16
 
@@ -73,6 +74,10 @@ def lib():
         L.gf_table_info.argtypes = [vp, C.c_int, C.POINTER(i64), C.POINTER(i64), dp]
         L.gf_table_nodes.argtypes = [vp, C.c_int, vp, vp, vp, vp]
         L.gf_table_eval.argtypes = [vp, C.c_int, C.c_int, vp, i64, vp, vp]
+        L.gf_table_eval_host.argtypes = [vp, C.c_int, vp, i64, vp]
+        L.gf_table_create_for_mesh.argtypes = [vp, C.c_double, C.POINTER(gf_params), C.c_int, C.c_double, C.c_double,
+                                               vp, C.POINTER(vp)]
+        L.gf_fill_batched.argtypes = [C.c_int, vp, vp, C.POINTER(gf_params), vp, vp, vp, vp]
         L.gf_table_destroy.argtypes = [vp]
         L.gf_fill.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, vp]
         L.gf_fill_parts.argtypes = [vp, C.c_double, C.POINTER(gf_params), vp, C.c_int, vp, i64, C.c_uint, vp]
@@ -216,6 +221,22 @@ def gf_table_eval(h, kind, r, stream=None):
     return out
 
 
+def gf_table_eval_host(h, kind, x):
+    """Host FP64 lookup (numpy float64 in table units) -> complex128 array."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(2 * x.size)
+    _check(lib().gf_table_eval_host(h, int(kind), _ptr(x), x.size, _ptr(out)))
+    return out[0::2] + 1j * out[1::2]
+
+
+def gf_table_create_for_mesh(mesh, k, params=None, precision=GF_FP32, r_min=-1.0, r_max=-1.0, stream=None):
+    params = params or gf_params_default()
+    h = C.c_void_p()
+    _check(lib().gf_table_create_for_mesh(mesh, float(k), C.byref(params), int(precision), float(r_min),
+                                          float(r_max), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
 def gf_table_destroy(h):
     _check(lib().gf_table_destroy(h))
 
@@ -352,6 +373,19 @@ def gf_batch_create(meshes, ks, params, tables, Zs, autotune=True, stream=None):
     _check(lib().gf_batch_create(n, mh, kk, C.byref(params), th, GF_FP32, zz, ld, int(bool(autotune)),
                                  _stream_ptr(stream), C.byref(h)))
     return h
+
+
+def gf_fill_batched(meshes, ks, params, tables, Zs, stream=None):
+    """One-shot batched fill (no tuning); returns when every Z is filled."""
+    n = len(meshes)
+    for Z in Zs:
+        _check_z(Z, GF_FP32)
+    mh = (C.c_void_p * n)(*[m.h.value for m in meshes])
+    kk = (C.c_double * n)(*[float(k) for k in ks])
+    th = (C.c_void_p * n)(*[t.h.value for t in tables]) if tables is not None else None
+    zz = (C.c_void_p * n)(*[Z.data_ptr() for Z in Zs])
+    ld = (C.c_int64 * n)(*[Z.shape[-1] for Z in Zs])
+    _check(lib().gf_fill_batched(n, mh, kk, C.byref(params), th, zz, ld, _stream_ptr(stream)))
 
 
 def gf_batch_launch(h, stream=None):

@@ -2,6 +2,7 @@
 gradient of the FP64 direct fill, central differences of the oracle, and the
 autograd wrapper. L = Re(a^H Z b), gZ = a conj(b)^T."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -42,30 +43,66 @@ def test_small_sphere_vs_oracle_gradient(table, near_fp64):
     assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
 
 
-def test_sphere_2048_sampled_vertices_fd_and_dk():
+def golden_grad_2048():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grad_sphere2048.txt")
+    rows = [list(map(float, ln.split())) for ln in open(path)]
+    L, dk = rows[0]
+    return L, np.array(rows[1:]), dk
+
+
+def test_sphere_2048_full_gradient_vs_oracle():
+    # every vertex coordinate and k against the oracle's dual-number gradient
+    # of its FP64 direct fill (tests/golden/make_grad_sphere2048.py)
+    wl = W.sphere_3072()
+    a = W.complex_gaussian(3072, 7)
+    b = W.complex_gaussian(3072, 8)
+    g, dk = gpu_grad(wl.xyz, wl.tri, 6, a, b, table=True)
+    _, g_ref, dk_ref = golden_grad_2048()
+    assert g.shape == g_ref.shape
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
+    assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
+
+
+def restricted_loss(xyz, tri, k, a, b, rows):
+    """Re(a^H Z b) over the entries of the given RWG rows and columns (the
+    oracle's FP64 direct fill): the part of L that moves with the vertices of
+    those unknowns' triangles."""
+    om = O.Mesh(xyz, tri)
+    rows = np.asarray(sorted(rows))
+    rest = np.setdiff1d(np.arange(om.ne), rows)
+    mi = np.concatenate([np.repeat(rows, om.ne), np.tile(rest, len(rows))])
+    ni = np.concatenate([np.tile(np.arange(om.ne), len(rows)), np.repeat(rows, len(rest))])
+    z = om.z_entries(k, 6, mi, ni)
+    return float(np.real(np.sum(np.conj(a[mi]) * z * b[ni])))
+
+
+def test_sphere_2048_central_differences():
+    # 64 seeded vertex coordinates and k: central differences (step 1e-4
+    # lambda, and 1e-4 k) of the oracle's FP64 direct loss
     wl = W.sphere_3072()
     om = O.Mesh(wl.xyz, wl.tri)
     a = W.complex_gaussian(om.ne, 7)
     b = W.complex_gaussian(om.ne, 8)
     g, dk = gpu_grad(wl.xyz, wl.tri, 6, a, b, table=True)
-    verts = [0, 517, 1000]
-    mask = np.isin(np.arange(len(wl.tri)), np.where(np.isin(wl.tri, verts).any(axis=1))[0]).astype(np.int32)
-    _, g_ref, _ = om.loss_grad(K, 6, a, b, tri_mask=mask)
-    scale = np.abs(g_ref[verts]).max()
-    assert np.abs(g[verts] - g_ref[verts]).max() <= 1e-4 * scale
-    # central differences (step 1e-4 lambda) of the oracle's loss restricted to
-    # the pairs that move
+    _, et = om.edges()
+    scale = np.abs(g).max()
+    rng = np.random.default_rng(64)
+    verts = rng.choice(len(wl.xyz), 64, replace=False)
+    coords = rng.integers(3, size=64)
     h = 1e-4
-    for v, c in [(517, 0), (1000, 2)]:
+    for v, c in zip(verts, coords):
+        tris = np.where((wl.tri == v).any(axis=1))[0]
+        rows = np.where(np.isin(et, tris).any(axis=1))[0]
         xp, xm = wl.xyz.copy(), wl.xyz.copy()
         xp[v, c] += h
         xm[v, c] -= h
-        Lp = O.Mesh(xp, wl.tri).loss_grad(K, 6, a, b, tri_mask=mask)[0]
-        Lm = O.Mesh(xm, wl.tri).loss_grad(K, 6, a, b, tri_mask=mask)[0]
-        fd = (Lp - Lm) / (2 * h)
+        fd = (restricted_loss(xp, wl.tri, K, a, b, rows) - restricted_loss(xm, wl.tri, K, a, b, rows)) / (2 * h)
         assert abs(g[v, c] - fd) <= 1e-3 * scale, (v, c, g[v, c], fd)
-    _, dk_ref = om.loss_dk(K, 6, a, b)
-    assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
+    hk = 1e-4 * K
+    Lp = float(np.real(np.conj(a) @ om.z_full(K + hk, 6) @ b))
+    Lm = float(np.real(np.conj(a) @ om.z_full(K - hk, 6) @ b))
+    assert abs(dk - (Lp - Lm) / (2 * hk)) <= 1e-3 * abs(dk)
 
 
 def test_autograd_wrapper():

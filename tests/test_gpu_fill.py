@@ -166,36 +166,6 @@ def test_errors():
         gf.fill(m, 2 * K, gf.gf_params_default(rule=3), t, gf.GF_FP64)
 
 
-def test_cube_73728_sampled_rows():
-    # 49152 triangles, 73728 unknowns, complex64 Z of 43.5 GB; near pairs are
-    # those with centroids closer than 0.2 lambda; the Green table is larger
-    # than shared memory, so the regular kernel reads it through L1
-    wl = W.cube_73728()
-    m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
-    assert m.ne == 73728 and m.nt == 49152
-    p = gf.gf_params_default(rule=4)
-    lo, hi = m.range(4, gf.GF_FP32)
-    om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
-    olo, ohi = om.range(4, prune=True)
-    assert abs(lo - olo) <= 1e-6 * olo and abs(hi - ohi) <= 1e-6 * ohi
-    tab = gf.Table(wl.k, lo, hi, p)
-    Z = torch.empty((m.ne, m.ne), dtype=torch.complex64, device="cuda")
-    gf.gf_fill(m.h, wl.k, p, tab.h, gf.GF_FP32, Z)
-    rows = np.random.default_rng(17).choice(m.ne, 6, replace=False)
-    z = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
-    # direct evaluation into the same Z (each unordered pair into one
-    # triangle, then Z + Z^T, as for every Z of 4 GiB and more)
-    gf.gf_fill(m.h, wl.k, p, None, gf.GF_FP32, Z)
-    zd = Z[torch.from_numpy(rows).cuda()].cpu().numpy()
-    del Z
-    ref = om.z_rows(wl.k, 4, rows, mode="table", tables=O.make_tables(wl.k, olo, ohi))
-    assert rel_fro(z, ref) <= 1e-5
-    assert rel_max(z, ref) <= 1e-5
-    refd = om.z_rows(wl.k, 4, rows)
-    assert rel_fro(zd, refd) <= 1e-5
-    assert rel_max(zd, refd) <= 1e-5
-
-
 def test_mesh_edges_and_near_count_match_oracle():
     # RWG numbering (sorted vertex pairs, T+ = the first triangle in input
     # order) and the number of ordered near pairs, on meshes with and without

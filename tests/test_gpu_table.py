@@ -8,6 +8,7 @@ import torch
 
 import oracle as O
 import paper_1901_04162_gb300 as gf
+import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -58,3 +59,24 @@ def test_device_table_vs_direct_1e6(k, lo, hi):
     assert np.max(np.abs(got - exact) / np.abs(exact)) <= 1e-6
     got = t(torch.from_numpy(r).cuda(), gf.GF_EXP).cpu().numpy()
     assert np.max(np.abs(got - np.exp(-1j * k * r))) <= 1e-6
+
+
+def test_host_fp64_lookup_and_table_for_mesh():
+    # gf_table_eval_host (host FP64 lookup) against the oracle's table on the
+    # same samples, and gf_table_create_for_mesh with the range computed
+    wl = W.sphere_3072()
+    m = gf.Mesh(wl.xyz, wl.tri)
+    p = gf.gf_params_default(rule=6)
+    h = gf.gf_table_create_for_mesh(m.h, wl.k, p, gf.GF_FP32)
+    lo, hi = m.range(6, gf.GF_FP32)
+    t = gf.Table(wl.k, lo, hi, p)
+    assert gf.gf_table_info(h, gf.GF_GREEN) == t.info(gf.GF_GREEN)
+    x = np.random.default_rng(3).uniform(lo, hi, 20000)
+    tabs = O.make_tables(wl.k, lo, hi)
+    for kind, ot in ((gf.GF_GREEN, tabs[0]), (gf.GF_EXP, tabs[1])):
+        f = gf.gf_table_eval_host(h, kind, x)
+        ref = ot(x)
+        assert np.abs(f - ref).max() <= 1e-13 * np.abs(ref).max()
+    with pytest.raises(gf.GfError):
+        gf.gf_table_eval_host(h, gf.GF_GREEN, np.array([0.5 * lo]))
+    gf.gf_table_destroy(h)
