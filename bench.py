@@ -84,9 +84,9 @@ def job_throughput(world, units_per_rank, seconds):
 
 def kernel_source_hash():
     """Hash of the sources that define the regular-pair table kernel (the
-    shared device code and the fill kernels)."""
+    shared device code and the regular-pair kernel file)."""
     h = hashlib.sha256()
-    for name in ("gf_device.cuh", "gf_fill.cu"):
+    for name in ("gf_device.cuh", "gf_regular.cu"):
         h.update(open(os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -448,7 +448,6 @@ def run_ours(args, wl, rank, world, local_rank):
     # tables, fill) and the whole Z copied to page-locked host memory, per step
     e2e = {"value": None}
     zhost = None
-    host_bytes = 0
     try:
         avail = int(next(ln.split()[1] for ln in open("/proc/meminfo") if ln.startswith("MemAvailable"))) * 1024
     except (OSError, StopIteration, ValueError):
@@ -456,40 +455,52 @@ def run_ours(args, wl, rank, world, local_rank):
     # every rank copies its own Z: all of them need the room, or none times e2e
     fits = zbytes * 1.3 * world + (8 << 30) < avail
     if reduce_max(0.0 if fits else 1.0) == 0.0:
-        host = np.empty(ne * ne, dtype=np.complex64 if prec == gf.GF_FP32 else np.complex128)
-        host.view(np.uint8)[:: 1 << 16] = 0  # touch every page before registering
-        rc = torch.cuda.cudart().cudaHostRegister(host.ctypes.data, zbytes, 0)
-        if int(rc) == 0:
-            zhost = torch.from_numpy(host).view(ne, ne)
-            host_bytes = zbytes
-        else:
-            e2e["reason"] = f"cudaHostRegister of {zbytes} bytes returned {int(rc)}"
+        try:
+            zhost = torch.empty((ne, ne), dtype=zdt, pin_memory=True)  # page-locked (cudaHostAlloc)
+        except RuntimeError as exc:
+            e2e["reason"] = f"page-locked host buffer of {zbytes} bytes: {exc}"[:200]
     else:
         e2e["reason"] = f"host memory: {avail} bytes available for {world} x {zbytes}-byte Z copies"
     if reduce_max(0.0 if zhost is not None else 1.0) != 0.0:
         zhost = None
     if zhost is not None:
-        times = []
-        n_e2e = args.steps if zbytes < (4 << 30) else min(args.steps, 5)
-        for i in range(args.warmup + n_e2e if zbytes < (4 << 30) else 1 + n_e2e):
+        times, parts_ms = [], []
+        big = zbytes >= (4 << 30)
+        zflat, zhost_flat = Z.view(-1), zhost.view(-1)
+        chunk = max(1, (1 << 30) // Z.element_size())
+        n_e2e = min(args.steps, 5) if big else args.steps
+        n_w = 1 if big else args.warmup
+        for i in range(n_w + n_e2e):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             m2 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+            t1 = time.perf_counter()
             lo, hi = m2.range(wl.rule, prec)
             gf.gf_fill_parts(m2.h, wl.k, p, None, prec, Z, gf.GF_PART_ZERO)  # overlaps the host table stage
             tab = gf.Table(wl.k, lo, hi, p)
+            ev[0].record(stream)
             gf.gf_fill_parts(m2.h, wl.k, p, tab.h, prec, Z, gf.GF_PART_REGULAR | gf.GF_PART_NEAR)
-            zhost.copy_(Z, non_blocking=True)
+            ev[1].record(stream)
+            for c0 in range(0, zflat.numel(), chunk):  # the copy in 1 GiB pieces
+                zhost_flat[c0:c0 + chunk].copy_(zflat[c0:c0 + chunk], non_blocking=True)
+            ev[2].record(stream)
             torch.cuda.synchronize()
-            if i >= (args.warmup if zbytes < (4 << 30) else 1):
-                times.append(time.perf_counter() - t0)
+            t2 = time.perf_counter()
+            if i >= n_w:
+                times.append(t2 - t0)
+                parts_ms.append(((t1 - t0) * 1e3, ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
             del tab, m2
         e2e_s = reduce_max(statistics.median(times))
+        cp = statistics.median(x[2] for x in parts_ms)
         e2e = {"value": world * ne * ne / e2e_s, "unit": "Z entries/s",
                "h2d_bytes_per_step": wl.xyz.nbytes + wl.tri.nbytes, "d2h_bytes_per_step": zbytes,
                "ms_per_step": e2e_s * 1e3, "steps": len(times),
+               "breakdown_ms": {"mesh_create_host": statistics.median(x[0] for x in parts_ms),
+                                "fill_after_tables": statistics.median(x[1] for x in parts_ms),
+                                "copy_z_to_host": cp, "copy_gb_per_s": zbytes / (cp / 1e3) / 1e9},
                "path": "host xyz/tri -> gf_mesh_create -> gf_range -> gf_table_create -> gf_fill_parts -> "
-                       "cudaMemcpyAsync of all of Z to page-locked (registered) host memory"}
+                       "cudaMemcpyAsync of all of Z (1 GiB pieces) to page-locked host memory"}
 
     # ---- roofline of the regular-pair kernel (table), CUDA events on its stream
     m = wl.rule
@@ -571,9 +582,7 @@ def run_ours(args, wl, rank, world, local_rank):
         # per step: range 4 (FP32; 2 in FP64), both tables 3, regular pairs 1, mirror 1 (FP32 only), near 1
         "gpu_launches": (10 if prec == gf.GF_FP32 else 7) * args.steps,
     }
-    if zhost is not None:
-        torch.cuda.cudart().cudaHostUnregister(zhost.data_ptr())
-        del zhost
+    del zhost
     # ---- accuracy vs the FP64 oracle on 64 seeded 256 x 256 blocks (outside the timed region)
     run = None
     if rank == 0 and not args.skip_oracle:
@@ -703,9 +712,9 @@ def run_batch(args, rank, world, local_rank):
     t_tables = time.perf_counter() - t0
     Zs = [torch.empty((m.ne, m.ne), dtype=torch.complex64, device=dev) for m in meshes]
     t0 = time.perf_counter()
-    batch = gf.Batch(meshes, [wl.k for wl in wls], p, tables, Zs, autotune=True)
+    batch = gf.Batch(meshes, [wl.k for wl in wls], p, tables, Zs, autotune=not args.no_autotune)
     t_create = time.perf_counter() - t0
-    direct = gf.Batch(meshes, [wl.k for wl in wls], p, None, Zs, autotune=True)
+    direct = gf.Batch(meshes, [wl.k for wl in wls], p, None, Zs, autotune=not args.no_autotune)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -734,7 +743,7 @@ def run_batch(args, rank, world, local_rank):
     tkr = gf.Table.kr(umin, umax, p)
     torch.cuda.synchronize()
     t_kr = time.perf_counter() - t0
-    kr_batch = gf.Batch(meshes, [wl.k for wl in wls], p, [tkr] * len(meshes), Zs, autotune=True)
+    kr_batch = gf.Batch(meshes, [wl.k for wl in wls], p, [tkr] * len(meshes), Zs, autotune=not args.no_autotune)
     kr_ms = timed(kr_batch)
     entries = sum(m.ne * m.ne for m in meshes)
     n_regular = sum(evaluated_pairs(m.nt, m.n_near) for m in meshes)
@@ -753,7 +762,8 @@ def run_batch(args, rank, world, local_rank):
                                f"{rule}-point rule, k in [pi, 4pi], one table per mesh",
                    "meshes": len(wls), "rwg_unknowns_total": sum(m.ne for m in meshes),
                    "z_bytes": entries * 8, "l2": "flushed between steps (256 MiB write)",
-                   "launch": "one CUDA graph (zero Z, persistent regular kernel, Z += Z^T per mesh, persistent near kernel)",
+                   "launch": "one CUDA graph (zero Z, persistent regular kernel, one Z += Z^T pass over every mesh, "
+                             "persistent near kernel)",
                    "autotuned": batch.config(), "parallelism": f"replicas x{world}"},
         "green_evals_per_s": evals / (ms / 1e3),
         "setup_s": {"meshes": t_mesh, "ranges_and_tables": t_tables, "batch_create_and_autotune": t_create},
@@ -768,8 +778,8 @@ def run_batch(args, rank, world, local_rank):
                      "frac": achieved / peak_tops, "traffic": None},
         "clocks": clocks,
         "e2e": {"value": None, "reason": "batched workload: fill-only; see setup_s"},
-        # per graph launch: the regular kernel, one mirror pass per mesh, the near kernel
-        "gpu_launches": (2 + len(wls)) * args.steps,
+        # per graph launch: the regular kernel, the mirror pass over every Z, the near kernel
+        "gpu_launches": 3 * args.steps,
     }
     if not args.skip_oracle:
         import oracle as O
@@ -995,6 +1005,7 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--batch-count", type=int, default=64)
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: the default launch shape")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

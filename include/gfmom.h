@@ -363,8 +363,9 @@ gf_status gf_fill_batched(int nmesh, const gf_mesh* const* meshes, const double*
  * `stream`. GF_ERR_ARG if nt * rule > GF_NOALLOC_MAX_POINTS, a pointer is
  * null, nt < 1 or the rule is not 1, 3, 4, 6 or 7.
  * The first call on a device looks up the scratch array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture. Every call on a device shares the one scratch array:
+ * (once per device and driver context, with that device current; after a
+ * cudaDeviceReset the next call looks it up again); make that first call
+ * before any stream capture. Every call on a device shares the one scratch array:
  * calls whose work overlaps on the GPU (other streams, other threads) race
  * and give wrong results; serialize them. */
 #define GF_NOALLOC_MAX_POINTS 131072

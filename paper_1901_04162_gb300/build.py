@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgfmom.so")
-SOURCES = ["gf_host.cpp", "gf_batch.cpp", "gf_fill.cu", "gf_mfie.cu", "gf_adjoint.cu", "gf_sparse_kernels.cu",
+SOURCES = ["gf_host.cpp", "gf_batch.cpp", "gf_fill.cu", "gf_regular.cu", "gf_mfie.cu", "gf_adjoint.cu", "gf_sparse_kernels.cu",
            "gf_batch_kernels.cu", "gf_noalloc.cu", "gf_rcs.cu", "gf_sparse.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

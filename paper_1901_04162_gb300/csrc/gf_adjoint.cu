@@ -2,7 +2,7 @@
 // L = Re(sum conj(gZ) Z) for regular pairs (reverse mode, table values
 // recomputed) and near pairs (reverse or forward mode through the singular
 // scheme), with their launcher.
-#include "gf_device.cuh"
+#include "gf_near.cuh"
 
 namespace gf {
 namespace {

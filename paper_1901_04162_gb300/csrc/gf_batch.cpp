@@ -29,8 +29,9 @@ struct gf_batch {
   unsigned long long* d_counters = nullptr;  // [0] regular, [1] near
   std::vector<void*> z;
   std::vector<int64_t> ldz, ne;
-  int64_t total_regular = 0, total_near = 0;
+  int64_t total_regular = 0, total_near = 0, total_mirror = 0;
   int block = 256, ctas = 2, chunk = 4;
+  int max_l1 = 0;  // 1: the regular kernel with all of the unified memory as L1 (the tables are read through it)
   double tuned_ms = 0.0;
   cudaStream_t cs = nullptr;
   cudaGraph_t graph = nullptr;
@@ -47,12 +48,13 @@ void release_graph(gf_batch* b) {
 }
 
 // Captures zeroing of every Z, the counter reset, the persistent regular
-// kernel, one mirror pass per Z and the persistent near kernel on the batch's
-// own stream.
-gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
+// kernel, one mirror pass over every Z and the persistent near kernel on the
+// batch's own stream.
+gf_status capture(gf_batch* b, int block, int ctas, int chunk, int max_l1) {
   release_graph(b);
   int sms = 1;
   GF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  GF_CUDA(set_batch_regular_l1(b->m, b->table, max_l1 != 0));
   GF_CUDA(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
   for (size_t i = 0; i < b->z.size() && e == cudaSuccess; ++i)
@@ -61,9 +63,9 @@ gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
   if (e == cudaSuccess && b->total_regular > 0)
     e = launch_batch_regular(b->d_items, (int)b->items.size(), b->total_regular, b->d_counters, b->m, b->table, block,
                              sms * ctas, chunk, b->cs);
-  // the regular kernel leaves each pair in its test triangle's rows: Z += Z^T per mesh
-  for (size_t i = 0; i < b->z.size() && e == cudaSuccess && b->total_regular > 0; ++i)
-    e = launch_mirror32(b->z[i], b->ldz[i], b->ne[i], b->cs);
+  // the regular kernel leaves each pair in its test triangle's rows: Z += Z^T for every mesh
+  if (e == cudaSuccess && b->total_regular > 0)
+    e = launch_batch_mirror(b->d_items, (int)b->items.size(), b->total_mirror, sms * 8, b->cs);
   if (e == cudaSuccess && b->total_near > 0)
     e = launch_batch_near(b->d_items, (int)b->items.size(), b->total_near, b->d_counters + 1, b->mixed, b->nphi,
                           b->nl, b->glp, b->gll, sms * 16, b->cs);
@@ -78,6 +80,7 @@ gf_status capture(gf_batch* b, int block, int ctas, int chunk) {
   GF_CUDA(cudaGraphInstantiate(&b->exec, b->graph, 0));
   b->block = block;
   b->ctas = ctas;
+  b->max_l1 = max_l1;
   b->chunk = chunk;
   return GF_OK;
 }
@@ -98,25 +101,26 @@ std::string tune_key(const gf_batch* b) {
   int lg = 0;
   for (int64_t t = b->total_regular; t > 1; t >>= 1) ++lg;
   char buf[256];
-  std::snprintf(buf, sizeof buf, "%s|sm%d|m%d|t%d|n%d|i%zu", name.c_str(),
+  std::snprintf(buf, sizeof buf, "v2|%s|sm%d|m%d|t%d|n%d|i%zu", name.c_str(),
                 prop.multiProcessorCount, b->m, (int)b->table, lg, b->items.size());
   return std::string(buf);
 }
 
-bool cache_lookup(const std::string& key, int* block, int* ctas, int* chunk, double* ms) {
+bool cache_lookup(const std::string& key, int* block, int* ctas, int* chunk, int* l1, double* ms) {
   std::string path = cache_path();
   if (path.empty() || path == "off") return false;
   FILE* f = std::fopen(path.c_str(), "r");
   if (!f) return false;
   char k[512];
-  int bl, ct, ch;
+  int bl, ct, ch, li;
   double t;
   bool found = false;
-  while (std::fscanf(f, "%511s %d %d %d %lf", k, &bl, &ct, &ch, &t) == 5) {
+  while (std::fscanf(f, "%511s %d %d %d %d %lf", k, &bl, &ct, &ch, &li, &t) == 6) {
     if (key == k) {  // the last entry for a key wins
       *block = bl;
       *ctas = ct;
       *chunk = ch;
+      *l1 = li;
       *ms = t;
       found = true;
     }
@@ -125,14 +129,14 @@ bool cache_lookup(const std::string& key, int* block, int* ctas, int* chunk, dou
   return found;
 }
 
-void cache_store(const std::string& key, int block, int ctas, int chunk, double ms) {
+void cache_store(const std::string& key, int block, int ctas, int chunk, int l1, double ms) {
   std::string path = cache_path();
   if (path.empty() || path == "off") return;
   for (size_t i = 1; i < path.size(); ++i)  // parent directories, errors ignored
     if (path[i] == '/') mkdir(path.substr(0, i).c_str(), 0755);
   FILE* f = std::fopen(path.c_str(), "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), block, ctas, chunk, ms);
+  std::fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), block, ctas, chunk, l1, ms);
   std::fclose(f);
 }
 
@@ -155,38 +159,55 @@ gf_status time_graph(gf_batch* b, int reps, double* ms) {
   return GF_OK;
 }
 
+// Tuning in two stages, each configuration timed over 5 graph replays: the
+// launch shape (block size, resident CTAs per SM) at task chunk 4, then at
+// the best shape the work granularity and tile order (a warp takes 1, 4 or 32
+// consecutive tasks; 32 = the 32 test triangles of one block pair in a row,
+// reusing the source block's data) and the table's cache (the regular kernel
+// with all of the unified memory as L1, which holds the meshes' lattice
+// images, or the driver's split).
 gf_status autotune(gf_batch* b) {
   const std::string key = tune_key(b);
-  int bl, ct, ch;
+  int bl, ct, ch, li;
   double ms;
-  if (cache_lookup(key, &bl, &ct, &ch, &ms)) {
+  if (cache_lookup(key, &bl, &ct, &ch, &li, &ms)) {
     b->tuned_ms = ms;
-    return capture(b, bl, ct, ch);
+    return capture(b, bl, ct, ch, li);
   }
   double best = INFINITY;
-  int best_bl = 256, best_ct = 2, best_ch = 4;
+  int best_bl = 256, best_ct = 2, best_ch = 4, best_l1 = 0;
   const int blocks[] = {128, 256, 512};
-  const int chunks[] = {1, 4};
   for (int block : blocks) {
     const int occ = batch_regular_blocks_per_sm(b->m, b->table, block);
     for (int ctas = 1; ctas <= std::min(occ, 4); ++ctas) {
-      for (int chunk : chunks) {
-        gf_status st = capture(b, block, ctas, chunk);
-        if (st) return st;
-        double t;
-        if ((st = time_graph(b, 2, &t))) return st;
-        if (t < best) {
-          best = t;
-          best_bl = block;
-          best_ct = ctas;
-          best_ch = chunk;
-        }
+      gf_status st = capture(b, block, ctas, 4, 0);
+      if (st) return st;
+      double t;
+      if ((st = time_graph(b, 5, &t))) return st;
+      if (t < best) {
+        best = t;
+        best_bl = block;
+        best_ct = ctas;
       }
     }
   }
+  const int chunks[] = {1, 4, 32};
+  for (int l1 = 0; l1 <= 1; ++l1)
+    for (int chunk : chunks) {
+      if (chunk == 4 && l1 == 0) continue;  // timed above
+      gf_status st = capture(b, best_bl, best_ct, chunk, l1);
+      if (st) return st;
+      double t;
+      if ((st = time_graph(b, 5, &t))) return st;
+      if (t < best) {
+        best = t;
+        best_ch = chunk;
+        best_l1 = l1;
+      }
+    }
   b->tuned_ms = best;
-  cache_store(key, best_bl, best_ct, best_ch, best);
-  return capture(b, best_bl, best_ct, best_ch);
+  cache_store(key, best_bl, best_ct, best_ch, best_l1, best);
+  return capture(b, best_bl, best_ct, best_ch, best_l1);
 }
 
 }  // namespace
@@ -253,13 +274,17 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
     return items[a].g.nt > items[c].g.nt;
   });
-  int64_t reg = 0, nr = 0;
+  int64_t reg = 0, nr = 0, mir = 0;
   for (int i : order) {
     BatchItem it = items[i];
     it.reg_begin = reg;
     it.near_begin = nr;
+    it.mir_begin = mir;
+    it.ne = (int)meshes[i]->ne;
     reg += gf::regular_units(it.g.nt);
     nr += it.n_near;
+    const int64_t nb = (it.ne + 31) / 32;
+    mir += nb * (nb + 1) / 2;
     b->items.push_back(it);
     b->z.push_back(Z[i]);
     b->ldz.push_back(ldz[i]);
@@ -267,6 +292,7 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
   }
   b->total_regular = reg;
   b->total_near = nr;
+  b->total_mirror = mir;
   cudaError_t e = cudaMalloc(&b->d_items, b->items.size() * sizeof(BatchItem));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, 2 * sizeof(unsigned long long));
   if (e == cudaSuccess)
@@ -276,7 +302,7 @@ gf_status gf_batch_create(int nmesh, const gf_mesh* const* meshes, const double*
     gf_batch_destroy(b.release());
     return cuda_fail(e, "gf_batch_create");
   }
-  gf_status st = autotune_flag ? autotune(b.get()) : capture(b.get(), 256, 2, 4);
+  gf_status st = autotune_flag ? autotune(b.get()) : capture(b.get(), 256, 2, 4, 0);
   if (st) {
     gf_batch_destroy(b.release());
     return st;

@@ -1,6 +1,8 @@
 // gfmom batched fill kernels for sm_103a: persistent regular and near
 // kernels over the work lists of many meshes, with their launchers.
-#include "gf_device.cuh"
+#include <algorithm>
+
+#include "gf_near.cuh"
 
 namespace gf {
 namespace {
@@ -39,6 +41,55 @@ __global__ void __launch_bounds__(512) k_batch_regular32(const BatchItem* __rest
         regular_task32<M, TABLE ? kLagrange : kDirect, TABLE, false>(
             it.g, T, it.rk, DenseUpper{reinterpret_cast<float2*>(it.Z), it.ldz}, p, q0, lane);
     }
+  }
+}
+
+// Z <- Z + Z^T per mesh over a global list of 32 x 32 tile pairs (I <= J)
+// of all meshes: both tiles through shared memory, both written (a diagonal
+// tile is its own partner). HBM-bound.
+__device__ __forceinline__ int batch_mirror_item(const BatchItem* items, int nitems, int64_t t) {
+  int lo = 0, hi = nitems - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].mir_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(256) k_batch_mirror(const BatchItem* __restrict__ items, int nitems, int64_t total) {
+  __shared__ float2 ta[32][33];
+  __shared__ float2 tb[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const BatchItem& it = items[batch_mirror_item(items, nitems, t)];
+    const int64_t u = t - it.mir_begin;
+    // tile pair u -> (I, J), I <= J, column by column: u = J (J + 1) / 2 + I
+    int64_t J = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+    while (J > 0 && J * (J + 1) / 2 > u) --J;
+    while ((J + 1) * (J + 2) / 2 <= u) ++J;
+    const int I = (int)(u - J * (J + 1) / 2);
+    const int ne = it.ne;
+    const int64_t ldz = it.ldz;
+    float2* Z = reinterpret_cast<float2*>(it.Z);
+    for (int r = ty; r < 32; r += 8) {
+      const int gr = I * 32 + r, gc = (int)J * 32 + tx;
+      ta[r][tx] = (gr < ne && gc < ne) ? Z[(int64_t)gr * ldz + gc] : make_float2(0.f, 0.f);
+      const int hr = (int)J * 32 + r, hc = I * 32 + tx;
+      tb[r][tx] = (hr < ne && hc < ne) ? Z[(int64_t)hr * ldz + hc] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const int gr = I * 32 + r, gc = (int)J * 32 + tx;
+      const float2 a = ta[r][tx], b = tb[tx][r];
+      if (gr < ne && gc < ne) Z[(int64_t)gr * ldz + gc] = make_float2(a.x + b.x, a.y + b.y);
+      if (I != J) {
+        const int hr = (int)J * 32 + r, hc = I * 32 + tx;
+        const float2 c = tb[r][tx], d = ta[tx][r];
+        if (hr < ne && hc < ne) Z[(int64_t)hr * ldz + hc] = make_float2(c.x + d.x, c.y + d.y);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -104,6 +155,31 @@ int batch_regular_blocks_per_sm(int m, bool table, int block) {
     case 6: return batch_blocks_m<6>(table, block);
     case 7: return batch_blocks_m<7>(table, block);
     default: return 0;
+  }
+}
+
+cudaError_t launch_batch_mirror(const BatchItem* items, int nitems, int64_t total, int grid, cudaStream_t s) {
+  if (total == 0) return cudaSuccess;
+  k_batch_mirror<<<(unsigned)std::min<int64_t>(total, grid), 256, 0, s>>>(items, nitems, total);
+  return cudaGetLastError();
+}
+
+template <int M>
+cudaError_t set_l1_m(bool table, bool max_l1) {
+  const int carve = max_l1 ? 0 : -1;  // 0: all of the unified memory as L1; -1: the driver's default
+  return table ? cudaFuncSetAttribute(k_batch_regular32<M, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve)
+               : cudaFuncSetAttribute(k_batch_regular32<M, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      carve);
+}
+
+cudaError_t set_batch_regular_l1(int m, bool table, bool max_l1) {
+  switch (m) {
+    case 1: return set_l1_m<1>(table, max_l1);
+    case 3: return set_l1_m<3>(table, max_l1);
+    case 4: return set_l1_m<4>(table, max_l1);
+    case 6: return set_l1_m<6>(table, max_l1);
+    case 7: return set_l1_m<7>(table, max_l1);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -1,26 +1,20 @@
 // Device code shared by the gfmom kernel files (sm_103a): the FP32 table
 // lookups of Section II.C on the lattice image, the near-pair test and the
-// symmetric task map, the regular-pair computation (moments of a triangle
-// pair and its 3x3 RWG block) with its sinks, and the near-pair computation
-// (singularity cancellation, Section II.A; mixed or FP64 precision).
+// symmetric task map, and the regular-pair computation (moments of a triangle
+// pair and its 3x3 RWG block) with its sinks. The near-pair computations are
+// in gf_near.cuh.
 //
 // Regular pairs: one warp per (test triangle p, 32 source triangles q), one
 // source triangle per lane. For each test point a the lane runs over the
-// source points b: R = |(c_p - c_q) + alpha_a - beta_b|, Green value from the
-// Lagrange table (Eq. 6 hash on the lattice -> cubic in s, Eq. 3 + 5
-// re-expanded as monomials) or from sincospi, and four moments M0 = sum w w G,
-// Ma = sum w w alpha G, Mb = sum w w beta G, Mab = sum w w (alpha . beta) G (8
-// complex numbers; Kahan-compensated over a in FP32). The 3 x 3 RWG block:
+// source points b: R = |(c_p - c_q) + alpha_a - beta_b| (taken in split form
+// from block frames), Green value from the Lagrange table (Eq. 6 hash on the
+// lattice -> polynomial in s, Eq. 3 + 5 re-expanded as monomials) or from
+// sincospi, and four moments M0 = sum w w G, Ma = sum w w alpha G,
+// Mb = sum w w beta G, Mab = sum w w (alpha . beta) G (8 complex numbers;
+// Kahan-compensated over a in FP32). The 3 x 3 RWG block:
 //   Z(e_i, e_j) += jk eta/(4 pi) s_i l_i s_j l_j
 //                  [ (Mab + eps_j . Ma + delta_i . Mb + (delta_i . eps_j) M0) / 4 - M0 / k^2 ]
 // with delta_i = c_p - v_i, eps_j = c_q - v_j (v = vertex opposite the edge).
-//
-// Near pairs: one pair per group of G lanes, lane = test point; the inner
-// integrals over q come from singularity cancellation (exact radial
-// integral) with the angular variable u = asinh(tan phi) for the scalar part,
-// and from the surface-gradient theorem (line integrals over q's edges, static
-// part in closed form) for the vector part. e^{-jkR} on those lines is the
-// linear Exp table when r_min <= R <= r_max (Section II.C), else sincos.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -551,9 +545,13 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
     }
   }
   KSum2 M0, Ma[3], Mb[3], Mab;
-  static_assert(M <= 8, "point pairs are flagged in 8 bits per test point");
-  unsigned long long emask = 0;  // point pairs (bit 8 a + b) whose lattice cell holds samples
-#pragma unroll 1
+  static_assert(M <= 8, "point pairs are flagged in one 64-bit word");
+  // point pairs (bit a M + b) whose lattice cell holds samples: 32 bits for
+  // rules of up to 5 points; the test-point loop unrolled for up to 4
+  using Mask = typename std::conditional<(M * M <= 32), unsigned, unsigned long long>::type;
+  constexpr int kUnrollA = M <= 4 ? M : 1;
+  Mask emask = 0;
+#pragma unroll kUnrollA
   for (int a = 0; a < M; ++a) {
     const float4 ra = g.rel32[(size_t)a * g.nt + p];  // test point: offset from p's block centre
     const float4 al = g.pts32[(size_t)a * g.nt + p];  // offset from p's centroid, weight
@@ -606,7 +604,7 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
         sqi[2] = fmaf(rz[b], wi, sqi[2]);
       }
     }
-    if (MODE != kDirect) emask |= (unsigned long long)rowbits << (8 * a);
+    if (MODE != kDirect) emask |= (Mask)rowbits << (M * a);
     // outer sums over the test points, Kahan-compensated (both parts at once)
     const f2x wa2 = pk2(al.w, al.w);
     const f2x s0 = pk2(s0r, s0i);
@@ -623,14 +621,14 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
     }
     Mab.add(xab);
   }
-  if (MODE != kDirect && __any_sync(0xffffffffu, emask != 0ull)) {
+  if (MODE != kDirect && __any_sync(0xffffffffu, emask != 0)) {
     // exact values where the lattice cell holds samples: add (exact - cell
     // polynomial) to the moments of those point pairs only, with the same
     // float operations for R as the loop above
     while (emask) {
-      const int bit = __ffsll((long long)emask) - 1;
+      const int bit = sizeof(Mask) == 4 ? __ffs((int)emask) - 1 : __ffsll((long long)emask) - 1;
       emask &= emask - 1;
-      const int a = bit >> 3, b = bit & 7;
+      const int a = bit / M, b = bit - M * (bit / M);
       const float4 ra = g.rel32[(size_t)a * g.nt + p];
       const float4 al = g.pts32[(size_t)a * g.nt + p];
       const float4 rb = g.rel32[(size_t)b * g.nt + q];
@@ -662,466 +660,38 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
   // X_j = (Mab + eps'_j . Ma) / 4 - M0 / k^2 and Y_j = Mb + eps'_j M0
   const int4 ep = g.tedge[p], eq = g.tedge[q];
   const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-  const float2 m0 = up2(M0.s), mab = up2(Mab.s);
-  const float2 ma[3] = {up2(Ma[0].s), up2(Ma[1].s), up2(Ma[2].s)};
-  const float2 mb[3] = {up2(Mb[0].s), up2(Mb[1].s), up2(Mb[2].s)};
-  float xr[3], xi[3], yr[3][3], yi[3][3], sl[3];
+  // (packed pairs: both parts of each complex number in one instruction)
+  const f2x m0k = mul2(M0.s, pk2(-K.inv_k2, -K.inv_k2));
+  f2x xj[3], yj[3][3];
+  float sl[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     const float4 gq = g.geob32[3 * (size_t)q + j];  // eps'_j, s_j l_j
     const float e[3] = {gq.x, gq.y, gq.z};
-    float er = mab.x, ei = mab.y;
+    f2x er = Mab.s;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      er = fmaf(e[c], ma[c].x, er);
-      ei = fmaf(e[c], ma[c].y, ei);
-      yr[j][c] = fmaf(e[c], m0.x, mb[c].x);
-      yi[j][c] = fmaf(e[c], m0.y, mb[c].y);
+      const f2x ec = pk2(e[c], e[c]);
+      er = fma2(ec, Ma[c].s, er);
+      yj[j][c] = fma2(ec, M0.s, Mb[c].s);
     }
-    xr[j] = fmaf(0.25f, er, -m0.x * K.inv_k2);
-    xi[j] = fmaf(0.25f, ei, -m0.y * K.inv_k2);
+    xj[j] = fma2(pk2(0.25f, 0.25f), er, m0k);
     sl[j] = gq.w;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (!edge_valid(ecp[i])) continue;
     const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
-    const float d[3] = {0.25f * gp.x, 0.25f * gp.y, 0.25f * gp.z};
+    const f2x d0 = pk2(0.25f * gp.x, 0.25f * gp.x), d1 = pk2(0.25f * gp.y, 0.25f * gp.y),
+              d2 = pk2(0.25f * gp.z, 0.25f * gp.z);
     const float ci = K.scale * gp.w;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       if (!edge_valid(ecq[j])) continue;
-      const float br = fmaf(d[0], yr[j][0], fmaf(d[1], yr[j][1], fmaf(d[2], yr[j][2], xr[j])));
-      const float bi = fmaf(d[0], yi[j][0], fmaf(d[1], yi[j][1], fmaf(d[2], yi[j][2], xi[j])));
+      const float2 bz = up2(fma2(d0, yj[j][0], fma2(d1, yj[j][1], fma2(d2, yj[j][2], xj[j]))));
       const float c = ci * sl[j];
       // j * c * (br + j bi) = c * (-bi + j br)
-      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bi, c * br));
-    }
-  }
-}
-
-// ---------------------------------------------------------------- near pairs (FP64)
-struct NearArgs {
-  double k, scale, inv_k2;
-  int nphi, nl;
-  double gx_phi[32], gw_phi[32], gx_l[32], gw_l[32];
-  float fx_phi[32], fw_phi[32], fx_l[32], fw_l[32];  // the same rules in FP32
-};
-
-struct C2 {
-  double re, im;
-};
-
-struct C2f {  // FP32 complex of the mixed-precision near-block assembly
-  float re, im;
-};
-
-struct KScal {  // per-wavenumber scalars of the near-pair fill
-  double k, scale, inv_k2, inv_k;
-  float q4f;      // 4 / k^2 in FP32 (the mixed-precision block assembly)
-  float scale32;  // k eta in FP32 (the mixed-precision output stage)
-};
-
-__device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bool use_table) {
-  const double x = use_table ? R * te->xscale64 : R;  // table units
-  if (use_table && x >= te->r_lo && x <= te->r_hi) {
-    double2 f = lookup64<1>(*te, R);
-    return C2{f.x, f.y};
-  }
-  double s, c;
-  sincos(k * R, &s, &c);
-  return C2{c, -s};
-}
-
-// Inner integrals over triangle v for observation point r (1/(4 pi) included).
-__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, double k,
-                                const TabView* te, bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
-  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
-  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
-  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  n[0] *= inv;
-  n[1] *= inv;
-  n[2] *= inv;
-  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
-  const double d = fabs(h);
-  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
-  const C2 ed = exp_mjkr(k, d, te, use_table);
-  double sre = 0, sim = 0;                       // scalar sector sums
-  double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0};  // vector remainder
-  double vst[3] = {0, 0, 0};                     // vector static part
-  for (int e = 0; e < 3; ++e) {
-    const double* a = v[e];
-    const double* b = v[(e + 1) % 3];
-    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-    t[0] /= len;
-    t[1] /= len;
-    t[2] /= len;
-    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
-    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
-    const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
-    const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
-    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
-    if (fabs(P0) > 1e-12 * len) {
-      const double aP = fabs(P0);
-      const double um = asinh(lm / aP), up = asinh(lp / aP);
-      const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
-      double cr = 0, ci = 0;
-      for (int i = 0; i < A.nphi; ++i) {
-        const double u = mid + half * A.gx_phi[i];
-        const double ch = cosh(u);
-        const double rho = aP * ch;
-        const double Re = sqrt(rho * rho + d * d);
-        const C2 eR = exp_mjkr(k, Re, te, use_table);
-        const double wt = A.gw_phi[i] / ch;
-        cr += (ed.re - eR.re) * wt;
-        ci += (ed.im - eR.im) * wt;
-      }
-      const double sg = P0 > 0 ? half : -half;
-      sre += cr * sg;
-      sim += ci * sg;
-    }
-    double lr = 0, li = 0;
-    for (int i = 0; i < A.nl; ++i) {
-      const double s = 0.5 * len * (A.gx_l[i] + 1.0);
-      const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
-      const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
-      const C2 eR = exp_mjkr(k, R, te, use_table);
-      lr += (eR.re - 1.0) * A.gw_l[i];
-      li += (eR.im + k * R) * A.gw_l[i];
-    }
-    lr *= 0.5 * len;
-    li *= 0.5 * len;
-    const double R02 = P0 * P0 + d * d;
-    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
-    double st = 0.5 * (lp * Rp - lm * Rm);
-    if (R02 > 0) {
-      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st += 0.5 * R02 * (log(fp) - log(fm));
-    }
-    for (int x = 0; x < 3; ++x) {
-      vre[x] += mh[x] * lr;
-      vim[x] += mh[x] * li;
-      vst[x] += mh[x] * st;
-    }
-  }
-  const double c4 = 1.0 / (4.0 * kPi);
-  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
-  I0->re = sim / k * c4;
-  I0->im = -sre / k * c4;
-  for (int x = 0; x < 3; ++x) {
-    I1[x].re = (-vim[x] / k + vst[x]) * c4;
-    I1[x].im = (vre[x] / k) * c4;
-  }
-}
-
-__device__ __forceinline__ float2 exp32(float kpi, float R, const Tab32& te, bool use_table, float lo, float hi) {
-  const float x = R * te.xscale;  // lo, hi in table units
-  if (use_table && x >= lo && x <= hi) return lookup32<1>(te, R);
-  float sn, cs;
-  sincospif(R * kpi, &sn, &cs);
-  return make_float2(cs, -sn);
-}
-
-// Mixed precision: the geometry (normal, projection, foot distances, edge
-// frames) and the closed-form static part in FP64; the sampling of e^{-jkR}
-// at the angular and line nodes of each edge and its sums in FP32 (relative
-// quantities of the size of a triangle, FP32 Exp table). The caller assembles
-// the 3x3 block from I0, I1 in FP32.
-// FP64 where the terms cancel (projection, in-plane distances, the static
-// closed form, all sums), FP32 sampling of e^{-jkR} on the edges. The source
-// frame (normal, edge tangents, lengths, edge normals) is precomputed per
-// triangle; |r - v_c| serves as R at the ends of both edges that meet at v_c,
-// and the static log term is one log of a ratio per edge.
-// The results leave in FP32 (the caller assembles the 3x3 block in FP32):
-// I0, I1 and dvq[j] = rho0 - v_j, the latter from the FP32 edge vectors
-// v_j - r formed here anyway (each FP64 <-> FP32 conversion costs an FP64
-// pipe slot, as much as an FP64 operation).
-__device__ __forceinline__ void inner_integrals_mixed(const double r[3], const double v[3][3], const double* __restrict__ fr,
-                                      const float* __restrict__ fr32, const NearArgs& A, double k, double inv_k,
-                                      const Tab32& te, bool use_table, float lo, float hi, C2f* I0, C2f I1[3],
-                                      float dvq[3][3]) {
-  const float kpi = (float)(k / kPi), k32 = (float)k;
-  const double n[3] = {fr[0], fr[1], fr[2]};
-  // v_c - r, once (scalars, so that the edge loop picks them without a local
-  // array): the vertex distances, h, and the edge offsets below all use them
-  const double w0x = v[0][0] - r[0], w0y = v[0][1] - r[1], w0z = v[0][2] - r[2];
-  const double w1x = v[1][0] - r[0], w1y = v[1][1] - r[1], w1z = v[1][2] - r[2];
-  const double w2x = v[2][0] - r[0], w2y = v[2][1] - r[1], w2z = v[2][2] - r[2];
-  const double h = -(n[0] * w0x + n[1] * w0y + n[2] * w0z);
-  const double d = fabs(h);
-  const float h32 = (float)h, nx32 = fr32[21], ny32 = fr32[22], nz32 = fr32[23];
-  float d0x = 0.f, d0y = 0.f, d0z = 0.f, d1x = 0.f, d1y = 0.f, d1z = 0.f, d2x = 0.f, d2y = 0.f, d2z = 0.f;
-  // |r - v_c|
-  const double Rv0 = sqrt(w0x * w0x + w0y * w0y + w0z * w0z);
-  const double Rv1 = sqrt(w1x * w1x + w1y * w1y + w1z * w1z);
-  const double Rv2 = sqrt(w2x * w2x + w2y * w2y + w2z * w2z);
-  const float d32 = (float)d;
-  const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
-  // the sampled (dynamic) sums carry FP32 samples: FP32 accumulation; the
-  // static closed form stays in FP64
-  float sre = 0.f, sim = 0.f, vre[3] = {0.f, 0.f, 0.f}, vim[3] = {0.f, 0.f, 0.f};
-  double vst[3] = {0, 0, 0};
-  for (int e = 0; e < 3; ++e) {
-    const double len = fr[3 + e];
-    const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
-    const double mh[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
-    // v_e - r; its in-plane part v_e - rho0 differs by h n, normal to t and mh
-    const double arx = e == 0 ? w0x : (e == 1 ? w1x : w2x), ary = e == 0 ? w0y : (e == 1 ? w1y : w2y),
-                 arz = e == 0 ? w0z : (e == 1 ? w1z : w2z);
-    const double P0 = arx * mh[0] + ary * mh[1] + arz * mh[2];
-    const double lm = arx * t[0] + ary * t[1] + arz * t[2];
-    const double lp = lm + len;
-    if (fabs(P0) > 1e-12 * len) {
-      const float aP32 = (float)fabs(P0);
-      const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
-      const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
-      float cr = 0.f, ci = 0.f;
-      for (int i = 0; i < A.nphi; ++i) {
-        const float u = fmaf(half, A.fx_phi[i], mid);
-        const float E = expf(u);
-        const float ch = 0.5f * (E + __frcp_rn(E));
-        const float rho = aP32 * ch;
-        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
-        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
-        const float wt = A.fw_phi[i] * __frcp_rn(ch);
-        cr = fmaf(ed.x - eR.x, wt, cr);
-        ci = fmaf(ed.y - eR.y, wt, ci);
-      }
-      const float sg = P0 > 0 ? half : -half;
-      sre = fmaf(cr, sg, sre);
-      sim = fmaf(ci, sg, sim);
-    }
-    // line integral of e^{-jkR} - 1 + jkR from r's position relative to a
-    const float ax = (float)arx, ay = (float)ary, az = (float)arz;
-    // rho0 - v_e = (r - v_e) - h n (scalars: the edge loop is not unrolled)
-    const float ux = fmaf(-h32, nx32, -ax), uy = fmaf(-h32, ny32, -ay), uz = fmaf(-h32, nz32, -az);
-    if (e == 0) {
-      d0x = ux, d0y = uy, d0z = uz;
-    } else if (e == 1) {
-      d1x = ux, d1y = uy, d1z = uz;
-    } else {
-      d2x = ux, d2y = uy, d2z = uz;
-    }
-    const float tx = fr32[3 + 3 * e], ty = fr32[4 + 3 * e], tz = fr32[5 + 3 * e];
-    const float hl = 0.5f * fr32[e];
-    float lr = 0.f, li = 0.f;
-    for (int i = 0; i < A.nl; ++i) {
-      const float sp = hl * (A.fx_l[i] + 1.0f);
-      const float x0 = fmaf(tx, sp, ax), x1 = fmaf(ty, sp, ay), x2 = fmaf(tz, sp, az);
-      const float R = sqrtf(fmaf(x0, x0, fmaf(x1, x1, x2 * x2)));
-      const float2 eR = exp32(kpi, R, te, use_table, lo, hi);
-      lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
-      li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
-    }
-    lr *= hl;
-    li *= hl;
-    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|;
-    // log(fp / fm) with fp = lp + Rp = R02 / (Rp - lp), fm = lm + Rm =
-    // R02 / (Rm - lm), each in its cancellation-free form (lp >= lm), as one
-    // quotient
-    const double R02 = P0 * P0 + d * d;
-    const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
-    double st = 0.5 * (lp * Rp - lm * Rm);
-    if (R02 > 0) {
-      double ratio;
-      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
-      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
-      else ratio = (Rm - lm) / (Rp - lp);
-      st += 0.5 * R02 * log(ratio);
-    }
-    const float mx = fr32[12 + 3 * e], my = fr32[13 + 3 * e], mz = fr32[14 + 3 * e];
-    vre[0] = fmaf(mx, lr, vre[0]);
-    vre[1] = fmaf(my, lr, vre[1]);
-    vre[2] = fmaf(mz, lr, vre[2]);
-    vim[0] = fmaf(mx, li, vim[0]);
-    vim[1] = fmaf(my, li, vim[1]);
-    vim[2] = fmaf(mz, li, vim[2]);
-    for (int x = 0; x < 3; ++x) vst[x] += mh[x] * st;
-  }
-  dvq[0][0] = d0x, dvq[0][1] = d0y, dvq[0][2] = d0z;
-  dvq[1][0] = d1x, dvq[1][1] = d1y, dvq[1][2] = d1z;
-  dvq[2][0] = d2x, dvq[2][1] = d2y, dvq[2][2] = d2z;
-  const float c4 = (float)(1.0 / (4.0 * kPi)), ik = (float)inv_k, ikc4 = ik * c4;
-  // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
-  I0->re = sim * ikc4;
-  I0->im = -sre * ikc4;
-  for (int x = 0; x < 3; ++x) {
-    I1[x].re = fmaf(-vim[x], ik, (float)vst[x]) * c4;
-    I1[x].im = vre[x] * ikc4;
-  }
-}
-
-// Reduce-scatter of the nine complex entries of a 3 x 3 block over the G
-// lanes of a group (G = 4 or 8): at each halving step a lane keeps one half
-// of its entries and adds the partner's copy of that half, so that the group
-// sums end spread over the lanes (at most ceil(9 / G) + 1 entries each) with
-// no more additions than entries exchanged.
-template <int N, class CT>
-__device__ __forceinline__ void rs_halve(const CT (&in)[N], CT (&out)[(N + 1) / 2], bool upper, int off,
-                                         unsigned gmask) {
-  constexpr int H = (N + 1) / 2;
-#pragma unroll
-  for (int s = 0; s < H; ++s) {
-    const CT lo_v = in[s];
-    const CT hi_v = (H + s < N) ? in[H + s] : CT{0, 0};
-    const CT keep = upper ? hi_v : lo_v, send = upper ? lo_v : hi_v;
-    out[s].re = keep.re + __shfl_xor_sync(gmask, send.re, off);
-    out[s].im = keep.im + __shfl_xor_sync(gmask, send.im, off);
-  }
-}
-
-// One near pair per group of G lanes (G >= the rule size; lane = test point;
-// lanes >= m idle); every lane of the group must call (valid_pair is uniform
-// over the group). The 3 x 3 block is reduce-scattered over the group and
-// each lane adds its entries to Z.
-template <class Out>
-struct DenseOut {  // Z[m][n] += z (row-major, ld = ldz)
-  Out* Z;
-  int64_t ldz;
-  __device__ __forceinline__ void add(int m, int n, double zr, double zi) const {
-    Out* z = Z + (int64_t)m * ldz + n;
-    if constexpr (sizeof(Out) == 8) {
-      atomicAdd(reinterpret_cast<float2*>(z), make_float2((float)zr, (float)zi));
-    } else {
-      atomicAdd(reinterpret_cast<double*>(z), zr);
-      atomicAdd(reinterpret_cast<double*>(z) + 1, zi);
-    }
-  }
-  __device__ __forceinline__ void add32(int m, int n, float zr, float zi) const {  // FP32 Z only
-    atomicAdd(reinterpret_cast<float2*>(Z + (int64_t)m * ldz + n), make_float2(zr, zi));
-  }
-};
-
-template <bool MIXED, int G, class Sink>
-__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
-                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
-                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask);
-
-template <class Out, bool MIXED, int G = 8>
-__device__ __forceinline__ void near_task(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
-                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks, Out* Z,
-                                          int64_t ldz, int64_t n_near, int64_t idx, bool valid_pair, int sub,
-                                          unsigned gmask) {
-  near_pair<MIXED, G>(g, te, te32, lo32, hi32, use_table, A, ks, DenseOut<Out>{Z, ldz}, idx, valid_pair, sub, gmask);
-}
-
-// The 3x3 block of near pair idx (of the mesh's near list) on a group of G
-// lanes, handed to `sink` (sink.add(m, n, re, im)).
-template <bool MIXED, int G, class Sink>
-__device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, const Tab32& te32, float lo32,
-                                          float hi32, bool use_table, const NearArgs& A, const KScal& ks,
-                                          const Sink& sink, int64_t idx, bool valid_pair, int sub, unsigned gmask) {
-  if (!valid_pair) return;
-  const int p = g.near_row[idx], q = g.near_idx[idx];
-  // MIXED: the 3x3 block is assembled from the FP64 inner integrals in FP32
-  // (products and sums of smooth quantities, added into an FP32 Z); else FP64
-  using CT = typename std::conditional<MIXED, C2f, C2>::type;
-  using RT = typename std::conditional<MIXED, float, double>::type;
-  CT acc[9];
-#pragma unroll
-  for (int u = 0; u < 9; ++u) acc[u] = CT{0, 0};
-  if (sub < g.m) {
-    double vq[3][3];
-    for (int c = 0; c < 3; ++c)
-      for (int x = 0; x < 3; ++x) vq[c][x] = g.v64[9 * (size_t)q + 3 * c + x];
-    const double* cp = g.cen64 + 4 * (size_t)p;
-    const double* al = g.pts64 + 4 * ((size_t)sub * g.nt + p);
-    const double ra[3] = {cp[0] + al[0], cp[1] + al[1], cp[2] + al[2]};
-    // entry (i, j): w_a ((r - v_i) . J_j / 4 - I0 / k^2), J_j = I1 + (rho0 - v_j) I0;
-    // w_a / 4 folded into I0, I1
-    CT S, T[3];
-    RT f[3][3], dvq[3][3], q4;
-    if constexpr (MIXED) {
-      C2f I0, I1[3];
-      inner_integrals_mixed(ra, vq, g.frame64 + kFrame * (size_t)q, g.frame32 + kFrame32 * (size_t)q, A, ks.k,
-                            ks.inv_k, te32, use_table, lo32, hi32, &I0, I1, dvq);
-      // r_a - v_i = alpha_a + delta_i from the FP32 offsets (no conversions)
-      const float4 alf = g.pts32[(size_t)sub * g.nt + p];
-      const float w4 = 0.25f * alf.w;
-      S = CT{w4 * I0.re, w4 * I0.im};
-#pragma unroll
-      for (int x = 0; x < 3; ++x) T[x] = CT{w4 * I1[x].re, w4 * I1[x].im};
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const float4 dl = g.geo32[3 * (size_t)p + i];  // c_p - v_i
-        f[i][0] = alf.x + dl.x;
-        f[i][1] = alf.y + dl.y;
-        f[i][2] = alf.z + dl.z;
-      }
-      q4 = ks.q4f;
-    } else {
-      C2 I0, I1[3];
-      double rho0[3];
-      inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
-      const RT w4 = (RT)(0.25 * al[3]);
-      S = CT{w4 * (RT)I0.re, w4 * (RT)I0.im};
-#pragma unroll
-      for (int x = 0; x < 3; ++x) T[x] = CT{w4 * (RT)I1[x].re, w4 * (RT)I1[x].im};
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double* vpi = g.v64 + 9 * (size_t)p + 3 * i;
-        for (int x = 0; x < 3; ++x) f[i][x] = (RT)(ra[x] - vpi[x]);
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j)
-        for (int x = 0; x < 3; ++x) dvq[j][x] = (RT)(rho0[x] - vq[j][x]);
-      q4 = (RT)(4.0 * ks.inv_k2);
-    }
-    const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      CT J[3];
-#pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        const RT dv = dvq[j][x];
-        J[x].re = fma(dv, S.re, T[x].re);
-        J[x].im = fma(dv, S.im, T[x].im);
-      }
-#pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        acc[3 * i + j].re = fma(f[i][0], J[0].re, fma(f[i][1], J[1].re, fma(f[i][2], J[2].re, -Q.re)));
-        acc[3 * i + j].im = fma(f[i][0], J[0].im, fma(f[i][1], J[1].im, fma(f[i][2], J[2].im, -Q.im)));
-      }
-    }
-  }
-  // reduce-scatter: 9 -> 5 -> 3 (-> 2 for G = 8) entries per lane
-  CT r5[5], r3[3];
-  constexpr int L1 = G / 2, L2 = G / 4;
-  rs_halve<9>(acc, r5, (sub & L1) != 0, L1, gmask);
-  rs_halve<5>(r5, r3, (sub & L2) != 0, L2, gmask);
-  int first = ((sub & L1) ? 5 : 0) + ((sub & L2) ? 3 : 0);  // entry of slot 0
-  int count = (sub & L1) ? ((sub & L2) ? 1 : 3) : ((sub & L2) ? 2 : 3);  // 9 = 5 + 4; 5 = 3 + 2; 4 = 3 + 1
-  constexpr int NS = G == 8 ? 2 : 3;
-  CT fin[NS];
-  if constexpr (G == 8) {
-    rs_halve<3>(r3, fin, (sub & 1) != 0, 1, gmask);
-    const bool up = (sub & 1) != 0;
-    first += up ? 2 : 0;
-    count = up ? max(count - 2, 0) : min(count, 2);
-  } else {
-#pragma unroll
-    for (int u = 0; u < 3; ++u) fin[u] = r3[u];
-  }
-  const double inv_area_q = MIXED ? 0.0 : g.frame64[kFrame * (size_t)q + 24];
-  const float inv_area32 = MIXED ? __frcp_rn(g.cen32[q].w) : 0.f;
-  const int4 ep = g.tedge[p], eq = g.tedge[q];
-#pragma unroll
-  for (int u = 0; u < NS; ++u) {
-    if (u >= count) break;
-    const int e = first + u, i = e / 3, j = e - 3 * (e / 3);
-    const int ci = i == 0 ? ep.x : (i == 1 ? ep.y : ep.z), cj = j == 0 ? eq.x : (j == 1 ? eq.y : eq.z);
-    if (!edge_valid(ci) || !edge_valid(cj)) continue;
-    if constexpr (MIXED) {  // FP32 output: no conversions on the FP64 pipe
-      const float c = ks.scale32 * g.geo32[3 * (size_t)p + i].w * g.geo32[3 * (size_t)q + j].w * inv_area32;
-      sink.add32(edge_of(ci), edge_of(cj), -c * (float)fin[u].im, c * (float)fin[u].re);
-    } else {
-      const double slp = g.geo64[4 * (3 * (size_t)p + i) + 3], slq = g.geo64[4 * (3 * (size_t)q + j) + 3];
-      const double c = ks.scale * slp * slq * inv_area_q;  // k eta s_i l_i s_j l_j / A_q
-      sink.add(edge_of(ci), edge_of(cj), -c * (double)fin[u].im, c * (double)fin[u].re);
+      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bz.y, c * bz.x));
     }
   }
 }

@@ -171,6 +171,8 @@ struct BatchItem {
   int64_t ldz;
   int64_t reg_begin, nchunk;      // first global regular work unit, 32-wide triangle blocks
   int64_t near_begin, n_near;     // first global near pair, near pairs
+  int64_t mir_begin;              // first global 32 x 32 tile pair of the mirror pass Z += Z^T
+  int ne;                         // RWG unknowns (rows and columns of Z)
 };
 
 // ---------------------------------------------------------------- kernels (gf_fill.cu, gf_mfie.cu,
@@ -241,6 +243,12 @@ cudaError_t launch_fill_near(const GeoView& g, const TabView* texp, int precisio
 
 cudaError_t launch_batch_regular(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter, int m,
                                  bool table, int block, int grid, int chunk, cudaStream_t s);
+// Z <- Z + Z^T of every mesh in one launch (total = all meshes' 32 x 32 tile
+// pairs I <= J).
+cudaError_t launch_batch_mirror(const BatchItem* items, int nitems, int64_t total, int grid, cudaStream_t s);
+// The batched regular kernel with the largest L1 (no shared memory carve-out)
+// or the default split.
+cudaError_t set_batch_regular_l1(int m, bool table, bool max_l1);
 cudaError_t launch_batch_near(const BatchItem* items, int nitems, int64_t total, unsigned long long* counter,
                               bool mixed, int nphi, int nl, const double* gl_phi, const double* gl_l, int grid,
                               cudaStream_t s);

@@ -1,7 +1,7 @@
 // gfmom MFIE (K operator) kernels for sm_103a: identity term, regular pairs
 // (FP32 with the Green table in shared memory, FP64) and near pairs, with
 // their launcher.
-#include "gf_device.cuh"
+#include "gf_near.cuh"
 
 namespace gf {
 namespace {

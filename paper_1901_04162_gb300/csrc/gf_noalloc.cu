@@ -16,6 +16,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "gf_internal.h"
 
@@ -32,12 +33,43 @@ struct __align__(32) P4 {
 // holds the min / max accumulator as two double bit patterns.
 static __device__ __align__(256) P4 g_noalloc_scratch[kMaxPoints + 1];
 
+// The scratch array's device address, per device and per context: a device
+// reset (cudaDeviceReset) or a new primary context reloads the module, and
+// the array may then sit elsewhere, so the address is looked up again when
+// the device's current context is not the one it was taken in (contexts are
+// told apart by their driver ID, unique for the life of the process).
 struct Slot {
   bool ready = false;
+  unsigned long long ctx_id = 0;
   P4* base = nullptr;
 };
 std::mutex g_mu;
 Slot g_slots[kMaxDevices];
+
+// The driver ID of the calling thread's current context (cuCtxGetCurrent and
+// cuCtxGetId, fetched through the runtime so the library links no driver
+// API); false if the driver does not provide them (then every call looks the
+// address up).
+bool current_context_id(unsigned long long* id) {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
+  static const std::pair<GetCurrent, GetId> fns = [] {
+    void* f = nullptr;
+    void* g = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      g = nullptr;
+    return std::make_pair(reinterpret_cast<GetCurrent>(f), reinterpret_cast<GetId>(g));
+  }();
+  if (!fns.first || !fns.second) return false;
+  void* ctx = nullptr;
+  if (fns.first(&ctx) != 0 || !ctx) return false;
+  return fns.second(ctx, id) == 0;
+}
 
 struct Bary {
   double v[3 * gf::kMaxRule];
@@ -125,17 +157,20 @@ extern "C" gf_status gf_range_noalloc(const double* tri_xyz, const int32_t* tri_
   if (dev < 0 || dev >= kMaxDevices) return gf::fail(GF_ERR_DEVICE, "gf_range_noalloc: device index too large");
   P4* base = nullptr;
   {
-    // set-up, once per device, with that device current: the device address
-    // of the scratch array (in host code the symbol is only a host-side
-    // stand-in, never a device address)
+    // set-up, once per device and context, with that device current: the
+    // device address of the scratch array (in host code the symbol is only a
+    // host-side stand-in, never a device address)
     std::lock_guard<std::mutex> lock(g_mu);
     Slot& slot = g_slots[dev];
-    if (!slot.ready) {
+    unsigned long long id = 0;
+    const bool known = current_context_id(&id);
+    if (!slot.ready || !known || slot.ctx_id != id) {
       void* ptr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess) return gf::cuda_fail(e, "gf_range_noalloc: cudaGetSymbolAddress");
       slot.base = static_cast<P4*>(ptr);
-      slot.ready = true;
+      slot.ctx_id = id;
+      slot.ready = known;
     }
     base = slot.base;
   }

@@ -1,6 +1,6 @@
 // gfmom near-field sparse fill kernels for sm_103a (regular pairs from a
 // work list and near pairs, into a CSR pattern), with their launcher.
-#include "gf_device.cuh"
+#include "gf_near.cuh"
 
 namespace gf {
 namespace {
