@@ -58,12 +58,32 @@ SMEM_READS = ((16, 16), (4, 4))
 # expected maximum load of 8 balls in 8 bins, 16 in 16, 32 in 32).
 RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the regular-pair
-# table kernel, from the ncu capture summarised in profiles/; valid only while
-# the kernel source hash matches.
-TRAFFIC = {("sphere_r1lambda_5120tri_7680rwg_7pt_fp32", "c37c83d3a8b42f44"): 296839680 + 256931328}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair
+# table kernel from ncu captures (summarised in profiles/), with the number of
+# unordered regular pairs that launch evaluated; valid only while the kernel
+# source hash matches. A workload without its own capture takes the bytes per
+# pair of the cube's smaller case (the kernel's DRAM traffic is the
+# read-modify-write of Z through the row atomics and the mirror-free half, and
+# Z grows with the pair count).
+TRAFFIC_HASH = "146254499157ed09"
+TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1939979264 + 2300862976, 75331278),
+           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298330624 + 285425152, 13073950)}
+TRAFFIC_SCALED_FROM = {"cube_3lambda_49152tri_73728rwg_4pt_fp32": "cube_3lambda_12288tri_18432rwg_4pt_fp32"}
 TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
-                "(ncu, --clock-control none); null when the kernel sources changed since the capture")
+                "(ncu, --clock-control none); the 73728-unknown cube's from the 18432-unknown cube's capture scaled "
+                "by the pair count; null when the kernel sources changed since the capture")
+
+
+def kernel_traffic(workload, n_pairs):
+    if kernel_source_hash() != TRAFFIC_HASH:
+        return None
+    if workload in TRAFFIC:
+        return TRAFFIC[workload][0]
+    src = TRAFFIC_SCALED_FROM.get(workload)
+    if src:
+        b, n = TRAFFIC[src]
+        return b * n_pairs / n
+    return None
 
 
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
@@ -514,7 +534,7 @@ def run_ours(args, wl, rank, world, local_rank):
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
     ops = evals_regular * OPS_PER_EVAL
     achieved = ops / (reg_ms / 1e3) / 1e12
-    traffic = TRAFFIC.get((wl.name, kernel_source_hash()))
+    traffic = kernel_traffic(wl.name, evaluated_pairs(nt, n_near))
     mhz = clocks.get("sm_mhz") or sm_mhz
     mhz_d = clocks_direct.get("sm_mhz") or sm_mhz
 

@@ -25,7 +25,7 @@ struct BaryF {
 __device__ __forceinline__ float re_mul(float ar, float ai, float br, float bi) { return ar * br - ai * bi; }
 __device__ __forceinline__ float im_mul(float ar, float ai, float br, float bi) { return ar * bi + ai * br; }
 
-template <int M, bool TABLE>
+template <int M, bool TABLE, bool SM>
 __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const Tab32& T, float k, float kappa,
                                                        float inv_k2, const BaryF& bw, const float2* __restrict__ gZ,
                                                        int64_t ldg, double* dtri, double* dkacc, int p, int q0,
@@ -45,16 +45,24 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
   }
   // The block value B_ij feeds Z[m][n] and Z[n][m], so its cotangent is
   // g = gZ[m][n] + gZ[n][m]; h_ij = j kappa sigma_i sigma_j conj(g) = c (Im g + j Re g)
-  auto h_of = [&](int i, int j, float* hr, float* hi) {
-    *hr = *hi = 0.f;
-    if (ok && edge_valid(ecp[i]) && edge_valid(ecq[j])) {
-      const float2 z1 = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
-      const float2 z2 = gZ[(int64_t)edge_of(ecq[j]) * ldg + edge_of(ecp[i])];
-      const float2 z = make_float2(z1.x + z2.x, z1.y + z2.y);
-      const float c = kappa * gp[i].w * gq[j].w;
-      *hr = c * z.y;
-      *hi = c * z.x;
+  // (gathered once: 18 scattered loads per pair)
+  float hr_[3][3], hi_[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      hr_[i][j] = hi_[i][j] = 0.f;
+      if (ok && edge_valid(ecp[i]) && edge_valid(ecq[j])) {
+        const float2 z1 = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
+        const float2 z2 = gZ[(int64_t)edge_of(ecq[j]) * ldg + edge_of(ecp[i])];
+        const float c = kappa * gp[i].w * gq[j].w;
+        hr_[i][j] = c * (z1.y + z2.y);
+        hi_[i][j] = c * (z1.x + z2.x);
+      }
     }
+  auto h_of = [&](int i, int j, float* hr, float* hi) {
+    *hr = hr_[i][j];
+    *hi = hi_[i][j];
   };
   float Aabr = 0.f, Aabi = 0.f, A0r = 0.f, A0i = 0.f, Aar[3] = {0.f, 0.f, 0.f}, Aai[3] = {0.f, 0.f, 0.f};
   float Abr[3] = {0.f, 0.f, 0.f}, Abi[3] = {0.f, 0.f, 0.f};
@@ -89,6 +97,9 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
   float dp[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float M0r = 0.f, M0i = 0.f, Mar[3] = {0.f, 0.f, 0.f}, Mai[3] = {0.f, 0.f, 0.f}, Mbr[3] = {0.f, 0.f, 0.f},
         Mbi[3] = {0.f, 0.f, 0.f}, Mabr = 0.f, Mabi = 0.f, dkF = 0.f;
+  // point pairs (bit a M + b) whose lattice cell holds samples
+  using Mask = typename std::conditional<(M * M <= 32), unsigned, unsigned long long>::type;
+  Mask emask = 0;
 #pragma unroll 1
   for (int a = 0; a < M; ++a) {
     const float4 al = g.pts32[(size_t)a * g.nt + p];
@@ -104,6 +115,7 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
       Kbi[x] = Abi[x] + Aabi * alv[x];
     }
     float ga[3] = {0.f, 0.f, 0.f}, gA[3] = {0.f, 0.f, 0.f};
+    unsigned rowbits = 0;  // flagged point pairs of this test point
 #pragma unroll
     for (int b = 0; b < M; ++b) {
       const float rx = ux - beta[b].x, ry = uy - beta[b].y, rz = uz - beta[b].z;
@@ -111,8 +123,10 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
       const float rs = rsqrtf(R2);
       const float R = R2 * rs;
       float Fr, Fi;
-      if (TABLE) {
-        const float2 f = lookup32<3>(T, R);
+      if (TABLE) {  // the lattice value; point pairs whose cell holds samples are corrected below
+        bool busy;
+        const float2 f = SM ? lat_fast<3, true>(T, R * T.xscale, 0.f, &busy) : lookup32_fast<3>(T, R, &busy);
+        if (busy) rowbits |= 1u << b;
         Fr = f.x;
         Fi = f.y;
       } else {
@@ -151,6 +165,7 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
       Mabr += ab * wFr;
       Mabi += ab * wFi;
     }
+    if (TABLE) emask |= (Mask)rowbits << (M * a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const float lc = bw.l[a][c];
@@ -167,6 +182,71 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
 #pragma unroll
       for (int x = 0; x < 3; ++x) dq[c][x] += lc * gqb[b][x] + (lc - (1.f / 3.f)) * gB[b][x];
     }
+  if (TABLE && __any_sync(0xffffffffu, emask != 0)) {
+    // every term above is linear in F (and F' = -(jk + 1/R) F): the flagged
+    // point pairs add the same terms for dF = exact - lattice value, with the
+    // same float operations for R as the loop above
+    while (emask) {
+      const int bit = sizeof(Mask) == 4 ? __ffs((int)emask) - 1 : __ffsll((long long)emask) - 1;
+      emask &= emask - 1;
+      const int a = bit / M, b = bit - M * (bit / M);
+      const float4 al = g.pts32[(size_t)a * g.nt + p];
+      const float4 bb = g.pts32[(size_t)b * g.nt + q];
+      const float alv[3] = {al.x, al.y, al.z}, bv[3] = {bb.x, bb.y, bb.z};
+      const float ux = dc.x + al.x, uy = dc.y + al.y, uz = dc.z + al.z;
+      const float rx = ux - bb.x, ry = uy - bb.y, rz = uz - bb.z;
+      const float R2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+      const float rs = rsqrtf(R2);
+      const float R = R2 * rs;
+      bool busy;
+      const float2 fa = SM ? lat_fast<3, true>(T, R * T.xscale, 0.f, &busy) : lookup32_fast<3>(T, R, &busy);
+      const float2 fe = lookup32_slow<3>(T, R * T.xscale, 0.f);
+      const float Fr = fe.x - fa.x, Fi = fe.y - fa.y;
+      const float Kar = A0r + Aar[0] * al.x + Aar[1] * al.y + Aar[2] * al.z;
+      const float Kai = A0i + Aai[0] * al.x + Aai[1] * al.y + Aai[2] * al.z;
+      float Kbr[3], Kbi[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        Kbr[x] = Abr[x] + Aabr * alv[x];
+        Kbi[x] = Abi[x] + Aabi * alv[x];
+      }
+      const float ww = al.w * bb.w;
+      const float Kr = Kar + Kbr[0] * bv[0] + Kbr[1] * bv[1] + Kbr[2] * bv[2];
+      const float Ki = Kai + Kbi[0] * bv[0] + Kbi[1] * bv[1] + Kbi[2] * bv[2];
+      const float Fpr = -Fr * rs + k * Fi, Fpi = -Fi * rs - k * Fr;
+      const float t1 = ww * re_mul(Kr, Ki, Fpr, Fpi) * rs;
+      const float wFr = ww * Fr, wFi = ww * Fi;
+      float gA[3], gBb[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        gA[x] = re_mul(wFr, wFi, Aar[x] + Aabr * bv[x], Aai[x] + Aabi * bv[x]);
+        gBb[x] = re_mul(wFr, wFi, Kbr[x], Kbi[x]);
+      }
+      const float gR[3] = {t1 * rx, t1 * ry, t1 * rz};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float la = bw.l[a][c], lb = bw.l[b][c];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          dp[c][x] += la * gR[x] + (la - (1.f / 3.f)) * gA[x];
+          dq[c][x] += -lb * gR[x] + (lb - (1.f / 3.f)) * gBb[x];
+        }
+      }
+      dkF += R * im_mul(Kr, Ki, wFr, wFi);
+      const float ab = alv[0] * bv[0] + alv[1] * bv[1] + alv[2] * bv[2];
+      M0r += wFr;
+      M0i += wFi;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        Mar[x] += alv[x] * wFr;
+        Mai[x] += alv[x] * wFi;
+        Mbr[x] += bv[x] * wFr;
+        Mbi[x] += bv[x] * wFi;
+      }
+      Mabr += ab * wFr;
+      Mabi += ab * wFi;
+    }
+  }
   // through delta_i, eps_j, the signed lengths and k explicitly
   float dd[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float de_[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
@@ -239,18 +319,23 @@ __device__ __forceinline__ void regular_adjoint_task32(const GeoView& g, const T
   if (lane == 0) atomicAdd(dkacc, (double)dkl);
 }
 
-template <int M, bool TABLE>
+template <int M, bool TABLE, bool SM>
 __global__ void __launch_bounds__(256) k_adjoint_regular32(GeoView g, TabView tv, float k, float kappa, float inv_k2,
                                                            BaryF bw, const float2* __restrict__ gZ, int64_t ldg,
                                                            double* dtri, double* dkacc) {
-  const Tab32 T = tab32(tv);
+  extern __shared__ __align__(16) unsigned char smem[];
+  Tab32 T = tab32(tv);
+  if (SM) {
+    stage_tab32(T, tv, 3, smem);
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31;
   const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
     if (sym_task(task, g.nt, &p, &q0))
-      regular_adjoint_task32<M, TABLE>(g, T, k, kappa, inv_k2, bw, gZ, ldg, dtri, dkacc, p, q0, lane);
+      regular_adjoint_task32<M, TABLE, SM>(g, T, k, kappa, inv_k2, bw, gZ, ldg, dtri, dkacc, p, q0, lane);
   }
 }
 
@@ -525,50 +610,50 @@ __device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
 
 // Adds d(contribution to L)/d(vertices of p), d/d(vertices of q), d/dk of
 // one test point a of near pair (p, q): L = sum_ij Re(conj(gZ_ij) dZ_ij).
-__device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3], const float lb[3], double wa,
-                                   const NearArgs& A, double k, double eta, const Tab32& te, bool use_table, float lo,
-                                   float hi, const int ecp[3], const int ecq[3], const float2* __restrict__ gZ,
-                                   int64_t ldg, double gp[3][3], double gq[3][3], double* gk) {
-  const float kpi = (float)(k / kPi), k32 = (float)k;
+// frp, frq: the triangles' source frames (unit normal, edge lengths, unit
+// tangents, in-plane edge normals, 1/area, 1/edge lengths); their values
+// enter the forward pass, and the reverse pass maps the frames' adjoints back
+// to the vertices. Reciprocals are formed once and shared by the forward
+// pass and the reverse one (an FP64 divide costs a dozen FP64 operations).
+__device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3], const double* __restrict__ frp,
+                                   const double* __restrict__ frq, const float lb[3], double wa, const NearArgs& A,
+                                   double k, double ik, float kpi, double eta, const Tab32& te, bool use_table,
+                                   float lo, float hi, const int ecp[3], const int ecq[3],
+                                   const float2* __restrict__ gZ, int64_t ldg, double gp[3][3], double gq[3][3],
+                                   double* gk) {
+  const float k32 = (float)k;
   double r[3];
   for (int x = 0; x < 3; ++x) r[x] = (double)lb[0] * vp[0][x] + (double)lb[1] * vp[1][x] + (double)lb[2] * vp[2][x];
-  // ---- source frame
-  double e1[3], e2[3], nn[3], n[3];
-  for (int x = 0; x < 3; ++x) {
-    e1[x] = vq[1][x] - vq[0][x];
-    e2[x] = vq[2][x] - vq[0][x];
-  }
-  cross3(e1, e2, nn);
-  const double Ln = sqrt(dot3(nn, nn)), iL = 1.0 / Ln;
-  for (int x = 0; x < 3; ++x) n[x] = nn[x] * iL;
-  double len[3], ilen[3], t[3][3], m[3][3];
-  for (int e = 0; e < 3; ++e) {
-    const int e2i = e == 2 ? 0 : e + 1;
-    double tt[3] = {vq[e2i][0] - vq[e][0], vq[e2i][1] - vq[e][1], vq[e2i][2] - vq[e][2]};
-    len[e] = sqrt(dot3(tt, tt));
-    ilen[e] = 1.0 / len[e];
-    for (int x = 0; x < 3; ++x) t[e][x] = tt[x] * ilen[e];
-    cross3(t[e], n, m[e]);
-  }
-  // ---- projection, vertex distances, e^{-jkd}
-  double rv0[3] = {r[0] - vq[0][0], r[1] - vq[0][1], r[2] - vq[0][2]};
+  const double n[3] = {frq[0], frq[1], frq[2]};
+  // ---- projection, vertex distances (with their reciprocals), e^{-jkd}
+  const double rv0[3] = {r[0] - vq[0][0], r[1] - vq[0][1], r[2] - vq[0][2]};
   const double h = dot3(n, rv0), d = fabs(h);
   double rho0[3];
   for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
-  double Rv[3];
+  double Rv[3], iRv[3];
   for (int c = 0; c < 3; ++c) {
     const double dx = vq[c][0] - r[0], dy = vq[c][1] - r[1], dz = vq[c][2] - r[2];
-    Rv[c] = sqrt(dx * dx + dy * dy + dz * dz);
+    const double s2 = dx * dx + dy * dy + dz * dz;  // > 0: r is inside p, off q's vertices
+    iRv[c] = rsqrt(s2);
+    Rv[c] = s2 * iRv[c];
   }
   const float d32 = (float)d;
   const float2 ed = exp32(kpi, d32, te, use_table, lo, hi);
-  // ---- forward: the per-edge sums
+  // ---- forward: the per-edge sums; the static part's value and its partial
+  // derivatives in (l+, l-, R+, R-, R0^2) kept for the reverse pass
   double sre = 0, sim = 0, vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0}, vst[3] = {0, 0, 0};
+  double st_[3], s_lp[3], s_lm[3], s_Rp[3], s_Rm[3], s_R02[3];
+  float cr_[3], ci_[3];
+#pragma unroll
   for (int e = 0; e < 3; ++e) {
-    const double* a = vq[e];
-    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double P0 = dot3(ar, m[e]), lm = dot3(ar, t[e]), lp = lm + len[e];
-    if (fabs(P0) > 1e-12 * len[e]) {
+    const int en = e == 2 ? 0 : e + 1;
+    const double len = frq[3 + e];
+    const double* t = frq + 6 + 3 * e;
+    const double* m = frq + 15 + 3 * e;
+    const double ar[3] = {vq[e][0] - rho0[0], vq[e][1] - rho0[1], vq[e][2] - rho0[2]};
+    const double P0 = dot3(ar, m), lm = dot3(ar, t), lp = lm + len;
+    cr_[e] = ci_[e] = 0.f;
+    if (fabs(P0) > 1e-12 * len) {
       const float aP32 = (float)fabs(P0);
       const float um = asinhf((float)lm / aP32), up = asinhf((float)lp / aP32);
       const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
@@ -584,13 +669,15 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
         cr = fmaf(ed.x - eR.x, wt, cr);
         ci = fmaf(ed.y - eR.y, wt, ci);
       }
+      cr_[e] = cr;
+      ci_[e] = ci;
       const double sg = P0 > 0 ? (double)half : -(double)half;
       sre += (double)cr * sg;
       sim += (double)ci * sg;
     }
-    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
-    const float tx = (float)t[e][0], ty = (float)t[e][1], tz = (float)t[e][2];
-    const float hl = 0.5f * (float)len[e];
+    const float ax = (float)(vq[e][0] - r[0]), ay = (float)(vq[e][1] - r[1]), az = (float)(vq[e][2] - r[2]);
+    const float tx = (float)t[0], ty = (float)t[1], tz = (float)t[2];
+    const float hl = 0.5f * (float)len;
     float lr = 0.f, li = 0.f;
     for (int i = 0; i < A.nl; ++i) {
       const float sp = hl * (A.fx_l[i] + 1.0f);
@@ -600,103 +687,144 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
       lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
       li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
     }
-    const double lrd = (double)lr * (0.5 * len[e]), lid = (double)li * (0.5 * len[e]);
+    const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
+    // static part st = (l+ R+ - l- R-) / 2 + R0^2 / 2 (log F+ - log F-), F = l + R
+    // (for l < 0 in its cancellation-free form R0^2 / (R - l)), one log of
+    // one quotient; d log F / d l = +-1 / (R +- l), d / dR likewise
     const double R02 = P0 * P0 + d * d;
-    const double Rm = Rv[e], Rp = Rv[e == 2 ? 0 : e + 1];
+    const double Rm = Rv[e], Rp = Rv[en];
     double st = 0.5 * (lp * Rp - lm * Rm);
+    double slp = 0.5 * Rp, slm = -0.5 * Rm, sRp = 0.5 * lp, sRm = -0.5 * lm, sR02 = 0.0;
     if (R02 > 0) {
-      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st += 0.5 * R02 * log(fp / fm);
+      const double Fp = lp >= 0 ? lp + Rp : Rp - lp, Fm = lm >= 0 ? lm + Rm : Rm - lm;
+      const double ip = 1.0 / Fp, im = 1.0 / Fm, hR = 0.5 * R02;
+      double ratio;
+      if (lm >= 0) {
+        ratio = Fp * im;
+      } else if (lp >= 0) {
+        ratio = Fp * Fm / R02;
+        sR02 = -0.5;  // R0^2 / 2 times d(-log R0^2)/d R0^2
+      } else {
+        ratio = Fm * ip;
+      }
+      const double Lg = log(ratio);
+      st += hR * Lg;
+      sR02 += 0.5 * Lg;
+      slp += hR * ip;
+      sRp += lp >= 0 ? hR * ip : -hR * ip;
+      slm -= hR * im;
+      sRm += lm >= 0 ? -hR * im : hR * im;
     }
+    st_[e] = st;
+    s_lp[e] = slp;
+    s_lm[e] = slm;
+    s_Rp[e] = sRp;
+    s_Rm[e] = sRm;
+    s_R02[e] = sR02;
     for (int x = 0; x < 3; ++x) {
-      vre[x] += m[e][x] * lrd;
-      vim[x] += m[e][x] * lid;
-      vst[x] += m[e][x] * st;
+      vre[x] += m[x] * lrd;
+      vim[x] += m[x] * lid;
+      vst[x] += m[x] * st;
     }
   }
-  const double c4 = 1.0 / (4.0 * kPi), ik = 1.0 / k;
+  const double c4 = 1.0 / (4.0 * kPi);
   const double I0r = sim * ik * c4, I0i = -sre * ik * c4;
   double I1r[3], I1i[3];
   for (int x = 0; x < 3; ++x) {
     I1r[x] = (vst[x] - vim[x] * ik) * c4;
     I1i[x] = vre[x] * ik * c4;
   }
-  // ---- assembly: values and adjoints of I0, I1, rho0, r, p's vertices, L = |nn|, k
+  // ---- assembly: values and adjoints of I0, I1, rho0, r, p's vertices, A_q, k.
+  // The 3x3 block and its adjoint are products and sums of smooth quantities
+  // of the size of a triangle: FP32 (as in the forward fill), with the FP64
+  // inputs converted once and the FP32 adjoints added back into the FP64
+  // accumulators once (every FP64 <-> FP32 conversion takes an FP64 pipe slot).
   double bI0r = 0, bI0i = 0, bI1r[3] = {0, 0, 0}, bI1i[3] = {0, 0, 0}, brho[3] = {0, 0, 0}, br[3] = {0, 0, 0};
   double bk = 0, bik2 = 0, bA = 0;
-  const double Aq = 0.5 * Ln, ik2 = ik * ik, iAq = 1.0 / Aq;
-  // per source edge j: s_j l_j, s_j / l_j and rho0 - v_j (reciprocals once: the
-  // FP64 divide costs a dozen FP64 operations); the adjoint of s_j l_j is
-  // summed over i and applied once
-  double slj[3], sjl[3], dvj[3][3], bslj[3] = {0, 0, 0};
+  const double ik2 = ik * ik, iAq = frq[24];
+  // per source edge j (from v_{j+1} to v_{j+2}: frame edge j + 1): s_j l_j and
+  // rho0 - v_j; the adjoint of s_j l_j is summed over i and applied once
+  float dvj[3][3], sljf[3], bslj[3] = {0.f, 0.f, 0.f};
   for (int j = 0; j < 3; ++j) {
-    const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
-    const double ej[3] = {vq[j2][0] - vq[j1][0], vq[j2][1] - vq[j1][1], vq[j2][2] - vq[j1][2]};
-    const double lj = sqrt(dot3(ej, ej)), sj = (ecq[j] & 1) ? -1.0 : 1.0;
-    slj[j] = sj * lj;
-    sjl[j] = sj / lj;
-    for (int x = 0; x < 3; ++x) dvj[j][x] = rho0[x] - vq[j][x];
+    const int j1 = j == 2 ? 0 : j + 1;
+    sljf[j] = (float)((ecq[j] & 1) ? -frq[3 + j1] : frq[3 + j1]);
+    for (int x = 0; x < 3; ++x) dvj[j][x] = (float)(rho0[x] - vq[j][x]);
   }
-  const double kewa = k * eta * wa * iAq;
+  const float I0rf = (float)I0r, I0if = (float)I0i, ik2f = (float)ik2;
+  const float I1rf[3] = {(float)I1r[0], (float)I1r[1], (float)I1r[2]};
+  const float I1if[3] = {(float)I1i[0], (float)I1i[1], (float)I1i[2]};
+  const float kewa = (float)(k * eta * wa * iAq);
+  float fbI0r = 0.f, fbI0i = 0.f, fbI1r[3] = {0.f, 0.f, 0.f}, fbI1i[3] = {0.f, 0.f, 0.f};
+  float fbrho[3] = {0.f, 0.f, 0.f}, fgq[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}}, fbik2 = 0.f;
   for (int i = 0; i < 3; ++i) {
     if (!edge_valid(ecp[i])) continue;
     const int i1 = i == 2 ? 0 : i + 1, i2 = i1 == 2 ? 0 : i1 + 1;
-    const double ei[3] = {vp[i2][0] - vp[i1][0], vp[i2][1] - vp[i1][1], vp[i2][2] - vp[i1][2]};
-    const double li_ = sqrt(dot3(ei, ei)), si = (ecp[i] & 1) ? -1.0 : 1.0, sli = si * li_;
-    const double f[3] = {r[0] - vp[i][0], r[1] - vp[i][1], r[2] - vp[i][2]};
-    double bf[3] = {0, 0, 0}, bcsum = 0;
+    const double li_ = frp[3 + i1], ili = frp[25 + i1];
+    const float f[3] = {(float)(r[0] - vp[i][0]), (float)(r[1] - vp[i][1]), (float)(r[2] - vp[i][2])};
+    const float slif = (float)((ecp[i] & 1) ? -li_ : li_);
+    float bf[3] = {0.f, 0.f, 0.f}, bcsum = 0.f;
     for (int j = 0; j < 3; ++j) {
       if (!edge_valid(ecq[j])) continue;
-      const double* dv = dvj[j];
-      double Jr[3], Ji[3];
+      const float* dv = dvj[j];
+      float Jr[3], Ji[3];
       for (int x = 0; x < 3; ++x) {
-        Jr[x] = I1r[x] + dv[x] * I0r;
-        Ji[x] = I1i[x] + dv[x] * I0i;
+        Jr[x] = fmaf(dv[x], I0rf, I1rf[x]);
+        Ji[x] = fmaf(dv[x], I0if, I1if[x]);
       }
-      const double tr = 0.25 * dot3(f, Jr) - I0r * ik2, ti = 0.25 * dot3(f, Ji) - I0i * ik2;
-      const double c = kewa * sli * slj[j];
+      const float tr = 0.25f * (f[0] * Jr[0] + f[1] * Jr[1] + f[2] * Jr[2]) - I0rf * ik2f;
+      const float ti = 0.25f * (f[0] * Ji[0] + f[1] * Ji[1] + f[2] * Ji[2]) - I0if * ik2f;
+      const float c = kewa * slif * sljf[j];
       const float2 gz = gZ[(int64_t)edge_of(ecp[i]) * ldg + edge_of(ecq[j])];
       // L = gz.x (-c ti) + gz.y (c tr)
-      const double btr = (double)gz.y * c, bti = -(double)gz.x * c;
-      const double bc = (double)gz.y * tr - (double)gz.x * ti;
-      double bdv[3];
+      const float btr = gz.y * c, bti = -gz.x * c;
+      const float bc = gz.y * tr - gz.x * ti;
       for (int x = 0; x < 3; ++x) {
-        bf[x] += 0.25 * (btr * Jr[x] + bti * Ji[x]);
-        const double bJr = 0.25 * btr * f[x], bJi = 0.25 * bti * f[x];
-        bI1r[x] += bJr;
-        bI1i[x] += bJi;
-        bdv[x] = bJr * I0r + bJi * I0i;
-        bI0r += bJr * dv[x];
-        bI0i += bJi * dv[x];
-        brho[x] += bdv[x];
-        gq[j][x] -= bdv[x];
+        bf[x] += 0.25f * (btr * Jr[x] + bti * Ji[x]);
+        const float bJr = 0.25f * btr * f[x], bJi = 0.25f * bti * f[x];
+        fbI1r[x] += bJr;
+        fbI1i[x] += bJi;
+        const float bdv = bJr * I0rf + bJi * I0if;
+        fbI0r += bJr * dv[x];
+        fbI0i += bJi * dv[x];
+        fbrho[x] += bdv;
+        fgq[j][x] -= bdv;
       }
-      bI0r -= btr * ik2;
-      bI0i -= bti * ik2;
-      bik2 -= btr * I0r + bti * I0i;
+      fbI0r -= btr * ik2f;
+      fbI0i -= bti * ik2f;
+      fbik2 -= btr * I0rf + bti * I0if;
       // c = k eta wa sl_i sl_j / A_q: bc c is the adjoint of log c, shared by its factors
-      const double bcc = bc * c;
+      const float bcc = bc * c;
       bcsum += bcc;
       bslj[j] += bcc;  // becomes the adjoint of s_j l_j below
     }
-    // log c = log k + log sl_i + log sl_j - log A_q + const
-    bk += bcsum * ik;
-    bA -= bcsum * iAq;
-    const double gsi = bcsum / sli * (si / li_);
+    // log c = log k + log sl_i + log sl_j - log A_q + const; d l_i / d v_{i2} = e_i / l_i
+    const double bcs = (double)bcsum;
+    bk += bcs * ik;
+    bA -= bcs * iAq;
+    const double gsi = bcs * ili * ili;
     for (int x = 0; x < 3; ++x) {
-      br[x] += bf[x];
-      gp[i][x] -= bf[x];
-      const double g = gsi * ei[x];
+      br[x] += (double)bf[x];
+      gp[i][x] -= (double)bf[x];
+      const double g = gsi * (vp[i2][x] - vp[i1][x]);
       gp[i2][x] += g;
       gp[i1][x] -= g;
     }
   }
+  bI0r = (double)fbI0r;
+  bI0i = (double)fbI0i;
+  bik2 = (double)fbik2;
+  for (int x = 0; x < 3; ++x) {
+    bI1r[x] = (double)fbI1r[x];
+    bI1i[x] = (double)fbI1i[x];
+    brho[x] = (double)fbrho[x];
+    for (int j = 0; j < 3; ++j) gq[j][x] += (double)fgq[j][x];
+  }
   for (int j = 0; j < 3; ++j) {
     if (!edge_valid(ecq[j])) continue;
     const int j1 = j == 2 ? 0 : j + 1, j2 = j1 == 2 ? 0 : j1 + 1;
-    // d(s_j l_j)/d v_{j2} = s_j e_j / l_j; the adjoint of s_j l_j is (sum bc c) / (s_j l_j)
-    const double g0 = bslj[j] / slj[j] * sjl[j];
+    // the adjoint of s_j l_j is (sum bc c) / (s_j l_j); d l_j / d v_{j2} = e_j / l_j
+    const double ilj = frq[25 + j1];
+    const double g0 = (double)bslj[j] * ilj * ilj;
     for (int x = 0; x < 3; ++x) {
       const double g = g0 * (vq[j2][x] - vq[j1][x]);
       gq[j2][x] += g;
@@ -715,20 +843,23 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
     bik += c4 * (-bI1r[x] * vim[x] + bI1i[x] * vre[x]);
   }
   bk -= bik * ik * ik;
-  // ---- reverse of the edges (recomputing their forward values)
+  // ---- reverse of the edges (the sampled sums recomputed)
   double bd = 0, bRv[3] = {0, 0, 0}, bt[3][3], bm[3][3], blen[3];
   float bedr = 0.f, bedi = 0.f;
+#pragma unroll
   for (int e = 0; e < 3; ++e) {
     const int en = e == 2 ? 0 : e + 1;
-    const double* a = vq[e];
-    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double P0 = dot3(ar, m[e]), lm = dot3(ar, t[e]), lp = lm + len[e];
-    double bP0 = 0, blm = 0, blp = 0, bR02 = 0;
+    const double len = frq[3 + e];
+    const double* t = frq + 6 + 3 * e;
+    const double* m = frq + 15 + 3 * e;
+    const double ar[3] = {vq[e][0] - rho0[0], vq[e][1] - rho0[1], vq[e][2] - rho0[2]};
+    const double P0 = dot3(ar, m), lm = dot3(ar, t), lp = lm + len;
+    double bP0 = 0, blm = 0, blp = 0;
     blen[e] = 0;
     // line integral: values then adjoints
-    const float ax = (float)(a[0] - r[0]), ay = (float)(a[1] - r[1]), az = (float)(a[2] - r[2]);
-    const float tx = (float)t[e][0], ty = (float)t[e][1], tz = (float)t[e][2];
-    const float hl = 0.5f * (float)len[e];
+    const float ax = (float)(vq[e][0] - r[0]), ay = (float)(vq[e][1] - r[1]), az = (float)(vq[e][2] - r[2]);
+    const float tx = (float)t[0], ty = (float)t[1], tz = (float)t[2];
+    const float hl = 0.5f * (float)len;
     float lr = 0.f, li = 0.f;
     for (int i = 0; i < A.nl; ++i) {
       const float sp = hl * (A.fx_l[i] + 1.0f);
@@ -738,9 +869,9 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
       lr = fmaf(eR.x - 1.0f, A.fw_l[i], lr);
       li = fmaf(fmaf(k32, R, eR.y), A.fw_l[i], li);
     }
-    const double blrd = dot3(bvre, m[e]), blid = dot3(bvim, m[e]);
-    const double lrd = (double)lr * (0.5 * len[e]), lid = (double)li * (0.5 * len[e]);
-    const float blr = (float)(blrd * 0.5 * len[e]), bli = (float)(blid * 0.5 * len[e]);
+    const double blrd = dot3(bvre, m), blid = dot3(bvim, m);
+    const double lrd = (double)lr * (0.5 * len), lid = (double)li * (0.5 * len);
+    const float blr = (float)(blrd * 0.5 * len), bli = (float)(blid * 0.5 * len);
     blen[e] += 0.5 * (blrd * (double)lr + blid * (double)li);
     float bax = 0.f, bay = 0.f, baz = 0.f, btx = 0.f, bty = 0.f, btz = 0.f, bhl = 0.f, bk32 = 0.f;
     for (int i = 0; i < A.nl; ++i) {
@@ -775,67 +906,24 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
     bt[e][0] = btx;
     bt[e][1] = bty;
     bt[e][2] = btz;
-    // static part
-    const double bst = dot3(bvst, m[e]);
-    for (int x = 0; x < 3; ++x) bm[e][x] = bvre[x] * lrd + bvim[x] * lid;
-    const double R02 = P0 * P0 + d * d;
-    const double Rm = Rv[e], Rp = Rv[en];
-    double st = 0.5 * (lp * Rp - lm * Rm);
-    blp += 0.5 * Rp * bst;
-    blm -= 0.5 * Rm * bst;
-    double bRp = 0.5 * lp * bst, bRm = -0.5 * lm * bst;
-    if (R02 > 0) {
-      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      const double Lg = log(fp / fm);
-      st += 0.5 * R02 * Lg;
-      bR02 += 0.5 * Lg * bst;
-      const double bL = 0.5 * R02 * bst;  // adjoint of log fp - log fm
-      if (lp >= 0) {
-        const double g = bL / fp;
-        blp += g;
-        bRp += g;
-      } else {  // log R02 - log(Rp - lp)
-        const double g = bL / (Rp - lp);
-        bR02 += bL / R02;
-        bRp -= g;
-        blp += g;
-      }
-      if (lm >= 0) {
-        const double g = bL / fm;
-        blm -= g;
-        bRm -= g;
-      } else {
-        const double g = bL / (Rm - lm);
-        bR02 -= bL / R02;
-        bRm += g;
-        blm -= g;
-      }
-    }
-    for (int x = 0; x < 3; ++x) bm[e][x] += bvst[x] * st;
-    bRv[e] += bRm;
-    bRv[en] += bRp;
+    // static part, from its partial derivatives
+    const double bst = dot3(bvst, m);
+    for (int x = 0; x < 3; ++x) bm[e][x] = bvre[x] * lrd + bvim[x] * lid + bvst[x] * st_[e];
+    blp += s_lp[e] * bst;
+    blm += s_lm[e] * bst;
+    bRv[en] += s_Rp[e] * bst;
+    bRv[e] += s_Rm[e] * bst;
+    const double bR02 = s_R02[e] * bst;
     // angular part
-    if (fabs(P0) > 1e-12 * len[e]) {
-      const float aP32 = (float)fabs(P0);
-      const float zm = (float)lm / aP32, zp = (float)lp / aP32;
+    if (fabs(P0) > 1e-12 * len) {
+      const float aP32 = (float)fabs(P0), iaP = __frcp_rn(aP32);
+      const float zm = (float)lm * iaP, zp = (float)lp * iaP;
       const float um = asinhf(zm), up = asinhf(zp);
       const float half = 0.5f * (up - um), mid = 0.5f * (up + um);
-      float cr = 0.f, ci = 0.f;
-      for (int i = 0; i < A.nphi; ++i) {
-        const float u = fmaf(half, A.fx_phi[i], mid);
-        const float E = expf(u);
-        const float ch = 0.5f * (E + __frcp_rn(E));
-        const float rho = aP32 * ch;
-        const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
-        const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
-        const float wt = A.fw_phi[i] * __frcp_rn(ch);
-        cr = fmaf(ed.x - eR.x, wt, cr);
-        ci = fmaf(ed.y - eR.y, wt, ci);
-      }
       const double sgn = P0 > 0 ? 1.0 : -1.0, sg = sgn * (double)half;
       const float bcr = (float)(bsre * sg), bci = (float)(bsim * sg);
-      float bhalf = (float)(sgn * (bsre * (double)cr + bsim * (double)ci)), bmid = 0.f, baP = 0.f, bd32 = 0.f;
+      float bhalf = (float)(sgn * (bsre * (double)cr_[e] + bsim * (double)ci_[e])), bmid = 0.f, baP = 0.f,
+            bd32 = 0.f;
       float bk32a = 0.f;
       for (int i = 0; i < A.nphi; ++i) {
         const float u = fmaf(half, A.fx_phi[i], mid);
@@ -844,7 +932,8 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
         const float rho = aP32 * ch;
         const float Re = sqrtf(fmaf(rho, rho, d32 * d32));
         const float2 eR = exp32(kpi, Re, te, use_table, lo, hi);
-        const float wt = A.fw_phi[i] * __frcp_rn(ch);
+        const float ich = __frcp_rn(ch);
+        const float wt = A.fw_phi[i] * ich;
         bedr += bcr * wt;
         bedi += bci * wt;
         const float bEr = -bcr * wt, bEi = -bci * wt;
@@ -852,7 +941,7 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
         const float bRe = bph * k32;
         bk32a += bph * Re;
         const float bwt = bcr * (ed.x - eR.x) + bci * (ed.y - eR.y);
-        float bch = -bwt * wt / ch;
+        float bch = -bwt * wt * ich;
         const float iRe = __frcp_rn(Re);
         const float brho = bRe * rho * iRe;
         bd32 += bRe * d32 * iRe;
@@ -866,9 +955,9 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
       bd += (double)bd32;
       const float bup = 0.5f * (bhalf + bmid), bum = 0.5f * (bmid - bhalf);
       const float bzp = bup * rsqrtf(1.f + zp * zp), bzm = bum * rsqrtf(1.f + zm * zm);
-      blp += (double)(bzp / aP32);
-      blm += (double)(bzm / aP32);
-      baP -= (bzp * zp + bzm * zm) / aP32;
+      blp += (double)(bzp * iaP);
+      blm += (double)(bzm * iaP);
+      baP -= (bzp * zp + bzm * zm) * iaP;
       bP0 += sgn * (double)baP;
     }
     bP0 += 2.0 * P0 * bR02;
@@ -876,7 +965,7 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
     blm += blp;
     blen[e] += blp;
     for (int x = 0; x < 3; ++x) {
-      const double bar = bP0 * m[e][x] + blm * t[e][x];
+      const double bar = bP0 * m[x] + blm * t[x];
       bm[e][x] += bP0 * ar[x];
       bt[e][x] += blm * ar[x];
       gq[e][x] += bar;
@@ -891,7 +980,7 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   }
   // vertex distances
   for (int c = 0; c < 3; ++c) {
-    const double gr = bRv[c] / Rv[c];
+    const double gr = bRv[c] * iRv[c];
     for (int x = 0; x < 3; ++x) {
       const double g = gr * (vq[c][x] - r[x]);
       gq[c][x] += g;
@@ -913,21 +1002,26 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   // frame: m_e = t_e x n, t_e = tt / |tt|, n = nn / |nn|, A_q = |nn| / 2
   for (int e = 0; e < 3; ++e) {
     const int en = e == 2 ? 0 : e + 1;
+    const double t[3] = {frq[6 + 3 * e], frq[7 + 3 * e], frq[8 + 3 * e]};
+    const double ilen = frq[25 + e];
     double c1[3], c2[3];
     cross3(n, bm[e], c1);  // d/dt of (t x n) . bm
-    cross3(bm[e], t[e], c2);  // d/dn
+    cross3(bm[e], t, c2);  // d/dn
     for (int x = 0; x < 3; ++x) {
       bt[e][x] += c1[x];
       bn[x] += c2[x];
     }
-    const double tb = dot3(t[e], bt[e]);
+    const double tb = dot3(t, bt[e]);
     for (int x = 0; x < 3; ++x) {
-      const double btt = (bt[e][x] - t[e][x] * tb) * ilen[e] + blen[e] * t[e][x];
+      const double btt = (bt[e][x] - t[x] * tb) * ilen + blen[e] * t[x];
       gq[en][x] += btt;
       gq[e][x] -= btt;
     }
   }
   {
+    const double iL = 0.5 * frq[24];  // 1 / |nn|, nn = e1 x e2
+    const double e1[3] = {vq[1][0] - vq[0][0], vq[1][1] - vq[0][1], vq[1][2] - vq[0][2]};
+    const double e2[3] = {vq[2][0] - vq[0][0], vq[2][1] - vq[0][1], vq[2][2] - vq[0][2]};
     const double nb = dot3(n, bn);
     double bnn[3];
     for (int x = 0; x < 3; ++x) bnn[x] = (bn[x] - n[x] * nb) * iL + 0.5 * bA * n[x];
@@ -946,26 +1040,29 @@ __device__ void near_point_adjoint(const double vp[3][3], const double vq[3][3],
   *gk += bk;
 }
 
-// One near pair per group of G lanes, lane = test point; all 19 derivatives
-// in one reverse pass, reduced over the group.
-template <int G>
+// Near pairs packed P = 32 / M to a warp, lane = (pair slot, test point); all
+// 19 derivatives of a pair in one reverse pass, summed over the pair's M
+// lanes (32 - P M lanes idle, against 8 - M of every 8 with groups of 8).
+template <int M>
 __global__ void __launch_bounds__(128) k_adjoint_near_rev(GeoView g, TabView te, bool use_table, NearArgs A, double k,
                                                           double eta, BaryF bw, const float2* __restrict__ gZ,
                                                           int64_t ldg, double* dtri, double* dkacc) {
+  constexpr int P = 32 / M;
   const Tab32 te32 = tab32(te);
   const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
+  const double ik = 1.0 / k;
+  const float kpi = (float)(k / kPi);
   const int64_t n_near = g.near_ptr[g.nt];
-  const int sub = threadIdx.x & (G - 1);
-  const unsigned gmask = ((1u << G) - 1u) << (threadIdx.x & (32 - G));
-  const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / G;
-  const int64_t iters = (n_near + ngroups - 1) / ngroups;  // same trip count in every group of a warp
-  const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int lane = threadIdx.x & 31, slot = lane / M, sub = lane - M * (lane / M);
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t iters = (n_near + nwarps * P - 1) / (nwarps * P);  // same trip count in every lane of a warp
   for (int64_t itn = 0; itn < iters; ++itn) {
-    const int64_t idx = g0 + itn * ngroups;
-    if (idx >= n_near) continue;  // uniform over the group
-    const int p = g.near_row[idx], q = g.near_idx[idx];
+    const int64_t idx = (w0 + itn * nwarps) * P + slot;
+    const bool valid = slot < P && idx < n_near;
+    const int p = valid ? g.near_row[idx] : 0, q = valid ? g.near_idx[idx] : 0;
     double gp[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, gk = 0;
-    if (sub < g.m) {
+    if (valid) {
       double vp[3][3], vq[3][3];
       for (int c = 0; c < 3; ++c)
         for (int x = 0; x < 3; ++x) {
@@ -975,18 +1072,29 @@ __global__ void __launch_bounds__(128) k_adjoint_near_rev(GeoView g, TabView te,
       const int4 ep = g.tedge[p], eq = g.tedge[q];
       const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
       const double wa = g.pts64[4 * ((size_t)sub * g.nt + p) + 3];
-      near_point_adjoint(vp, vq, bw.l[sub], wa, A, k, eta, te32, use_table, lo32, hi32, ecp, ecq, gZ, ldg, gp, gq,
-                         &gk);
+      near_point_adjoint(vp, vq, g.frame64 + kFrame * (size_t)p, g.frame64 + kFrame * (size_t)q, bw.l[sub], wa, A,
+                         k, ik, kpi, eta, te32, use_table, lo32, hi32, ecp, ecq, gZ, ldg, gp, gq, &gk);
     }
-    for (int off = 1; off < G; off <<= 1) {
+    // segmented sum over the M lanes of each slot: after the step with offset
+    // o, lane sub holds the sum over sub .. sub + 2o - 1 (within the slot)
+#pragma unroll
+    for (int off = 1; off < M; off <<= 1) {
+      const bool take = sub + off < M;
+#pragma unroll
       for (int c = 0; c < 3; ++c)
+#pragma unroll
         for (int x = 0; x < 3; ++x) {
-          gp[c][x] += __shfl_xor_sync(gmask, gp[c][x], off);
-          gq[c][x] += __shfl_xor_sync(gmask, gq[c][x], off);
+          const double a = __shfl_down_sync(0xffffffffu, gp[c][x], off);
+          const double b = __shfl_down_sync(0xffffffffu, gq[c][x], off);
+          if (take) {
+            gp[c][x] += a;
+            gq[c][x] += b;
+          }
         }
-      gk += __shfl_xor_sync(gmask, gk, off);
+      const double a = __shfl_down_sync(0xffffffffu, gk, off);
+      if (take) gk += a;
     }
-    if (sub == 0) {
+    if (valid && sub == 0) {
       for (int c = 0; c < 3; ++c)
         for (int x = 0; x < 3; ++x) {
           atomicAdd(&dtri[9 * (size_t)p + 3 * c + x], gp[c][x]);
@@ -1096,12 +1204,29 @@ cudaError_t launch_adjoint_regular_m(const GeoView& g, const TabView* green, dou
   if (green) tv = *green;
   const int64_t blocks = pair_grid(g, 4);
   const float kappa = (float)(k * eta / (4.0 * kPi)), inv_k2 = (float)(1.0 / (k * k));
-  if (green)
-    k_adjoint_regular32<M, true><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ, ldg,
-                                                                       dtri, dk);
-  else
-    k_adjoint_regular32<M, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ, ldg,
-                                                                        dtri, dk);
+  if (!green) {
+    k_adjoint_regular32<M, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ,
+                                                                              ldg, dtri, dk);
+    return cudaGetLastError();
+  }
+  // the Green lattice staged in shared memory where it fits (one CTA per SM
+  // at this register count: one staging per SM), else read through L1
+  const size_t smem = tv.smem32_bytes(3);
+  int dev = 0, max_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem <= (size_t)max_optin) {
+    auto kern = k_adjoint_regular32<M, true, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+    const int64_t b = std::min<int64_t>(blocks, (int64_t)sm_count() * std::max(per_sm, 1));
+    kern<<<(unsigned)b, kThreads, smem, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ, ldg, dtri, dk);
+  } else {
+    k_adjoint_regular32<M, true, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, (float)k, kappa, inv_k2, bw, gZ,
+                                                                             ldg, dtri, dk);
+  }
   return cudaGetLastError();
 }
 
@@ -1148,12 +1273,18 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
   const bool t = texp != nullptr;
   // mixed precision: reverse mode, one pass per near pair; FP64 throughout:
   // forward-mode duals, one pass per (near pair, direction)
-  if (g.m <= 4) {
-    if (mixed) k_adjoint_near_rev<4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
-    else k_adjoint_near<false, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+  if (mixed) {
+    switch (g.m) {
+      case 1: k_adjoint_near_rev<1><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
+      case 3: k_adjoint_near_rev<3><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
+      case 4: k_adjoint_near_rev<4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
+      case 6: k_adjoint_near_rev<6><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
+      default: k_adjoint_near_rev<7><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
+    }
+  } else if (g.m <= 4) {
+    k_adjoint_near<false, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   } else {
-    if (mixed) k_adjoint_near_rev<8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
-    else k_adjoint_near<false, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    k_adjoint_near<false, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   }
   k_adjoint_gather<<<(g.nt + 127) / 128, 128, 0, s>>>(g.nt, g.tvert, dtri, dxyz);
   return cudaGetLastError();

@@ -21,8 +21,9 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
     for (int x = 0; x < 3; ++x) v[c][x] = v64[9 * (size_t)t + 3 * c + x];
   {
     // source-triangle frame of the near-pair integrals: unit normal, edge
-    // lengths, unit edge tangents (v_e -> v_{e+1}), in-plane edge normals t x n
-    // and 1/area; an FP32 copy of the lengths, tangents and normals
+    // lengths, unit edge tangents (v_e -> v_{e+1}), in-plane edge normals t x n,
+    // 1/area and the reciprocal edge lengths; an FP32 copy of the lengths,
+    // tangents and normals
     double* fr = frame64 + kFrame * (size_t)t;
     float* f32 = frame32 + kFrame32 * (size_t)t;
     const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
@@ -39,6 +40,7 @@ __global__ void k_prep_geometry(const double* __restrict__ v64, int nt, int m, c
       const double il = 1.0 / len;
       for (int x = 0; x < 3; ++x) tt[x] *= il;
       fr[3 + e] = len;
+      fr[25 + e] = il;
       for (int x = 0; x < 3; ++x) fr[6 + 3 * e + x] = tt[x];
       fr[15 + 3 * e + 0] = tt[1] * n[2] - tt[2] * n[1];
       fr[15 + 3 * e + 1] = tt[2] * n[0] - tt[0] * n[2];

@@ -949,14 +949,20 @@ constexpr int64_t kLatticeSmemBudget = 210 * 1024;
 
 // Bound of |f^(n)| for f = e^{-jkr}/r at r (it decreases with r): the
 // Leibniz sum sum_i C(n, i) k^(n-i) i! / r^(i+1).
+// (powers by repeated products: it runs for every lattice cell)
 double green_deriv_bound(int n, double k, double r) {
-  double s = 0.0, c = 1.0, fact = 1.0;
-  for (int i = 0; i <= n; ++i) {
+  double kp[16];
+  kp[0] = 1.0;
+  for (int i = 1; i <= n && i < 16; ++i) kp[i] = kp[i - 1] * k;
+  const double ir = 1.0 / r;
+  double s = 0.0, c = 1.0, fact = 1.0, irp = ir;  // irp = 1 / r^(i+1)
+  for (int i = 0; i <= n && i < 16; ++i) {
     if (i > 0) {
       c = c * (n - i + 1) / i;
       fact *= i;
+      irp *= ir;
     }
-    s += c * std::pow(k, n - i) * fact / std::pow(r, i + 1);
+    s += c * kp[n - i] * fact * irp;
   }
   return s;
 }

@@ -179,7 +179,7 @@ struct BatchItem {
 // gf_adjoint.cu, gf_sparse_kernels.cu, gf_batch_kernels.cu; shared device code in gf_device.cuh)
 // Doubles per triangle of the near-pair source frames: unit normal [0..2],
 // edge lengths [3..5], unit edge tangents [6..14], in-plane edge normals [15..23].
-constexpr int kFrame = 25;    // FP64 source frame per triangle: n, len, t, m, 1/area
+constexpr int kFrame = 28;    // FP64 source frame per triangle: n, len, t, m, 1/area, 1/len
 constexpr int kFrame32 = 24;  // FP32 copy of len, t, m (the sampled integrals) and n
 cudaError_t launch_prep_geometry(const double* v64, int nt, int m, const double* bary, const double* w,
                                  const int4* tedge, const double* edge_len, float4* pts32, float4* cen32,

@@ -41,74 +41,106 @@ __device__ __forceinline__ C2 exp_mjkr(double k, double R, const TabView* te, bo
   return C2{c, -s};
 }
 
-// Inner integrals over triangle v for observation point r (1/(4 pi) included).
-__device__ void inner_integrals(const double r[3], const double v[3][3], const NearArgs& A, double k,
-                                const TabView* te, bool use_table, C2* I0, C2 I1[3], double rho0[3]) {
-  double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
-  double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
-  double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-  double inv = 1.0 / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  n[0] *= inv;
-  n[1] *= inv;
-  n[2] *= inv;
-  const double h = n[0] * (r[0] - v[0][0]) + n[1] * (r[1] - v[0][1]) + n[2] * (r[2] - v[0][2]);
+// Inner integrals over source triangle v (frame fr) for observation point r,
+// all in FP64 (1/(4 pi) included); dvq[c] = rho0 - v_c. The steps of the
+// mixed-precision version below with FP64 samples: the frame of the source
+// triangle precomputed, the vertex offsets and distances formed once and
+// shared by the two edges meeting at a vertex, the static part as one log of
+// one quotient per edge, the bounds of the angular substitution
+// u = asinh(l / |P0|) from the in-plane vertex distances (e^u = (l + rho) / |P0|),
+// and e^u at a symmetric pair of angular nodes from e^mid and e^{+-half x}.
+__device__ void inner_integrals64(const double r[3], const double v[3][3], const double* __restrict__ fr,
+                                  const NearArgs& A, double k, double inv_k, const TabView* te, bool use_table,
+                                  C2* I0, C2 I1[3], double dvq[3][3]) {
+  const double n[3] = {fr[0], fr[1], fr[2]};
+  double w[3][3];  // v_c - r
+  for (int c = 0; c < 3; ++c)
+    for (int x = 0; x < 3; ++x) w[c][x] = v[c][x] - r[x];
+  const double h = -(n[0] * w[0][0] + n[1] * w[0][1] + n[2] * w[0][2]);
   const double d = fabs(h);
-  for (int x = 0; x < 3; ++x) rho0[x] = r[x] - h * n[x];
+  double Rv[3], rv[3];  // |r - v_c| and the in-plane |rho0 - v_c|
+  for (int c = 0; c < 3; ++c) {
+    Rv[c] = sqrt(w[c][0] * w[c][0] + w[c][1] * w[c][1] + w[c][2] * w[c][2]);
+    double u[3];
+    for (int x = 0; x < 3; ++x) {
+      u[x] = fma(h, n[x], w[c][x]);  // v_c - rho0
+      dvq[c][x] = -u[x];
+    }
+    rv[c] = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  }
   const C2 ed = exp_mjkr(k, d, te, use_table);
-  double sre = 0, sim = 0;                       // scalar sector sums
+  double sre = 0, sim = 0;                        // scalar sector sums
   double vre[3] = {0, 0, 0}, vim[3] = {0, 0, 0};  // vector remainder
-  double vst[3] = {0, 0, 0};                     // vector static part
+  double vst[3] = {0, 0, 0};                      // vector static part
   for (int e = 0; e < 3; ++e) {
-    const double* a = v[e];
-    const double* b = v[(e + 1) % 3];
-    double t[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    const double len = sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
-    t[0] /= len;
-    t[1] /= len;
-    t[2] /= len;
-    const double mh[3] = {t[1] * n[2] - t[2] * n[1], t[2] * n[0] - t[0] * n[2], t[0] * n[1] - t[1] * n[0]};
-    const double ar[3] = {a[0] - rho0[0], a[1] - rho0[1], a[2] - rho0[2]};
-    const double br[3] = {b[0] - rho0[0], b[1] - rho0[1], b[2] - rho0[2]};
+    const int en = e == 2 ? 0 : e + 1;
+    const double len = fr[3 + e];
+    const double t[3] = {fr[6 + 3 * e], fr[7 + 3 * e], fr[8 + 3 * e]};
+    const double mh[3] = {fr[15 + 3 * e], fr[16 + 3 * e], fr[17 + 3 * e]};
+    const double* ar = w[e];  // its in-plane part differs by h n, normal to t and mh
     const double P0 = ar[0] * mh[0] + ar[1] * mh[1] + ar[2] * mh[2];
     const double lm = ar[0] * t[0] + ar[1] * t[1] + ar[2] * t[2];
-    const double lp = br[0] * t[0] + br[1] * t[1] + br[2] * t[2];
+    const double lp = lm + len;
     if (fabs(P0) > 1e-12 * len) {
-      const double aP = fabs(P0);
-      const double um = asinh(lm / aP), up = asinh(lp / aP);
-      const double half = 0.5 * (up - um), mid = 0.5 * (up + um);
+      const double aP = fabs(P0), iaP = 1.0 / aP;
+      // e^{asinh(l / aP)} = (l + rho) / aP, for l < 0 as aP / (rho - l)
+      const double Em = lm >= 0 ? (lm + rv[e]) * iaP : aP / (rv[e] - lm);
+      const double Ep = lp >= 0 ? (lp + rv[en]) * iaP : aP / (rv[en] - lp);
+      const double um = log(Em), up = log(Ep);
+      const double half = 0.5 * (up - um);
+      const double Emid = sqrt(Em * Ep), iEmid = 1.0 / Emid;  // e^{+-mid}
       double cr = 0, ci = 0;
-      for (int i = 0; i < A.nphi; ++i) {
-        const double u = mid + half * A.gx_phi[i];
-        const double ch = cosh(u);
-        const double rho = aP * ch;
-        const double Re = sqrt(rho * rho + d * d);
-        const C2 eR = exp_mjkr(k, Re, te, use_table);
-        const double wt = A.gw_phi[i] / ch;
-        cr += (ed.re - eR.re) * wt;
-        ci += (ed.im - eR.im) * wt;
+      // nodes i and nphi - 1 - i sit at mid +- half x_i (x_{n-1-i} = -x_i)
+      for (int i = 0; i < (A.nphi + 1) / 2; ++i) {
+        const int j = A.nphi - 1 - i;
+        const double ex = exp(half * A.gx_phi[i]), iex = 1.0 / ex;
+        const double chi = 0.5 * (Emid * ex + iEmid * iex), chj = 0.5 * (Emid * iex + iEmid * ex);  // cosh u
+        const double q = 1.0 / (chi * chj);
+        {
+          const double Re = sqrt(fma(aP * chi, aP * chi, d * d));
+          const C2 eR = exp_mjkr(k, Re, te, use_table);
+          const double wt = A.gw_phi[i] * (chj * q);
+          cr += (ed.re - eR.re) * wt;
+          ci += (ed.im - eR.im) * wt;
+        }
+        if (j != i) {
+          const double Re = sqrt(fma(aP * chj, aP * chj, d * d));
+          const C2 eR = exp_mjkr(k, Re, te, use_table);
+          const double wt = A.gw_phi[j] * (chi * q);
+          cr += (ed.re - eR.re) * wt;
+          ci += (ed.im - eR.im) * wt;
+        }
       }
       const double sg = P0 > 0 ? half : -half;
       sre += cr * sg;
       sim += ci * sg;
     }
+    // line integral of e^{-jkR} - 1 + jkR along the edge
     double lr = 0, li = 0;
+    const double hl = 0.5 * len;
     for (int i = 0; i < A.nl; ++i) {
-      const double s = 0.5 * len * (A.gx_l[i] + 1.0);
-      const double x0 = a[0] + t[0] * s - r[0], x1 = a[1] + t[1] * s - r[1], x2 = a[2] + t[2] * s - r[2];
+      const double s = hl * (A.gx_l[i] + 1.0);
+      const double x0 = fma(t[0], s, ar[0]), x1 = fma(t[1], s, ar[1]), x2 = fma(t[2], s, ar[2]);
       const double R = sqrt(x0 * x0 + x1 * x1 + x2 * x2);
       const C2 eR = exp_mjkr(k, R, te, use_table);
       lr += (eR.re - 1.0) * A.gw_l[i];
       li += (eR.im + k * R) * A.gw_l[i];
     }
-    lr *= 0.5 * len;
-    li *= 0.5 * len;
+    lr *= hl;
+    li *= hl;
+    // static part: int R dl along the edge, with Rm = |r - a|, Rp = |r - b|;
+    // log(fp / fm) with fp = lp + Rp = R02 / (Rp - lp), fm = lm + Rm =
+    // R02 / (Rm - lm), each in its cancellation-free form (lp >= lm), as one
+    // quotient
     const double R02 = P0 * P0 + d * d;
-    const double Rm = sqrt(lm * lm + R02), Rp = sqrt(lp * lp + R02);
+    const double Rm = Rv[e], Rp = Rv[en];
     double st = 0.5 * (lp * Rp - lm * Rm);
     if (R02 > 0) {
-      const double fp = lp >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const double fm = lm >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st += 0.5 * R02 * (log(fp) - log(fm));
+      double ratio;
+      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
+      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
+      else ratio = (Rm - lm) / (Rp - lp);
+      st += 0.5 * R02 * log(ratio);
     }
     for (int x = 0; x < 3; ++x) {
       vre[x] += mh[x] * lr;
@@ -116,13 +148,13 @@ __device__ void inner_integrals(const double r[3], const double v[3][3], const N
       vst[x] += mh[x] * st;
     }
   }
-  const double c4 = 1.0 / (4.0 * kPi);
+  const double c4 = 1.0 / (4.0 * kPi), ikc4 = inv_k * c4;
   // I0 = (-j/k) s / (4 pi);  I1 = ((j/k) v + v_static) / (4 pi)
-  I0->re = sim / k * c4;
-  I0->im = -sre / k * c4;
+  I0->re = sim * ikc4;
+  I0->im = -sre * ikc4;
   for (int x = 0; x < 3; ++x) {
-    I1[x].re = (-vim[x] / k + vst[x]) * c4;
-    I1[x].im = (vre[x] / k) * c4;
+    I1[x].re = (vst[x] - vim[x] * inv_k) * c4;
+    I1[x].im = vre[x] * ikc4;
   }
 }
 
@@ -363,8 +395,8 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
       q4 = ks.q4f;
     } else {
       C2 I0, I1[3];
-      double rho0[3];
-      inner_integrals(ra, vq, A, ks.k, &te, use_table, &I0, I1, rho0);
+      double dv64[3][3];
+      inner_integrals64(ra, vq, g.frame64 + kFrame * (size_t)q, A, ks.k, ks.inv_k, &te, use_table, &I0, I1, dv64);
       const RT w4 = (RT)(0.25 * al[3]);
       S = CT{w4 * (RT)I0.re, w4 * (RT)I0.im};
 #pragma unroll
@@ -376,7 +408,7 @@ __device__ __forceinline__ void near_pair(const GeoView& g, const TabView& te, c
       }
 #pragma unroll
       for (int j = 0; j < 3; ++j)
-        for (int x = 0; x < 3; ++x) dvq[j][x] = (RT)(rho0[x] - vq[j][x]);
+        for (int x = 0; x < 3; ++x) dvq[j][x] = (RT)dv64[j][x];
       q4 = (RT)(4.0 * ks.inv_k2);
     }
     const CT Q = {q4 * S.re, q4 * S.im};  // w_a I0 / k^2
