@@ -58,7 +58,7 @@ def build(force=False, verbose=False):
                 print(err, file=sys.stderr)
     objs = [o for o, _ in results]
     tmp = LIB + ".tmp"
-    cmd = [NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
+    cmd = [NVCC, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -288,6 +288,15 @@ __global__ void k_table_eval64(TabView t, const double* __restrict__ r, int64_t 
     out[i] = lookup64<DEG>(t, r[i]);
 }
 
+// Row (test triangle) of every near-list entry, expanded from the CSR row
+// pointers: one warp per row.
+__global__ void k_near_rows(const int64_t* __restrict__ near_ptr, int64_t nt, int32_t* near_row) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nt; r += nwarp)
+    for (int64_t j = near_ptr[r] + lane; j < near_ptr[r + 1]; j += 32) near_row[j] = (int32_t)r;
+}
+
 // Range scratch: mm[0] r_min, mm[1] r_max (FP64 bits), mm[2] / mm[3] the
 // pass-1 thresholds, mm[4] candidate block pairs, mm[5] blocks of pass 2 done.
 __global__ void k_range_init(unsigned long long* mm, float2* bpb, int64_t nbp) {
@@ -322,22 +331,80 @@ __device__ __forceinline__ void pair_bounds(const GeoView& g, int p, int q, floa
 
 constexpr int kRangeSplit = 4;          // pass-1 warps per 32 x 32 block pair (8 test triangles each)
 
-// Pass 1, one warp per 8 test triangles of a 32 x 32 block pair: thresholds
-// from actual point distances (the first rule point of each triangle of every
-// regular pair: their minimum is >= r_min, their maximum <= r_max), widened by
-// a relative 1e-5 for the FP32 rounding (mm[2], mm[3]), and, per block pair,
-// the smallest lower and largest upper bound of its regular pairs (bpb, merged
-// by integer atomics on the bits of these non-negative floats), so that pass 2
+// Every point distance of the triangles of blocks I and J lies in
+// [D - r_I - r_J, D + r_I + r_J] (D = distance of the blocks' bounding-sphere
+// centres), widened by the slack of pair_bounds.
+__device__ __forceinline__ void block_bounds(const float4* __restrict__ bsph, int I, int J, float* lb, float* ub) {
+  const float4 a = bsph[I], b = bsph[J];
+  const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  const float D = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  const float r = a.w + b.w;
+  const float mag = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fmaxf(fmaxf(fabsf(b.x), fabsf(b.y)),
+                                                                                  fabsf(b.z))));
+  const float slack = 1e-5f * (D + r + mag);
+  *lb = fmaxf(D - r - slack, 0.f);
+  *ub = D + r + slack;
+}
+
+// Pass 0, one warp per 32 x 32 block pair: first thresholds mm[2] >= r_min
+// and mm[3] <= r_max from actual distances (the first rule point of the test
+// block's first triangle and of each source triangle, regular pairs only),
+// so that pass 1 can skip the block pairs whose bounding spheres keep every
+// point distance inside (mm[2], mm[3]).
+__global__ void __launch_bounds__(kThreads) k_range_witness(GeoView g, unsigned long long* mm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  float min_d = INFINITY, max_d = 0.f;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nbp; u += nwarp) {
+    int p, q0;
+    sym_task(u * 32, g.nt, &p, &q0);
+    const int q = min(q0 + lane, g.nt - 1);
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    if (!((q0 + lane < g.nt) && q > p && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc))) continue;
+    const float4 xp = g.pts32[p], yq = g.pts32[q];
+    const float rx = (dc.x + xp.x) - yq.x, ry = (dc.y + xp.y) - yq.y, rz = (dc.z + xp.z) - yq.z;
+    const float d = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+    min_d = fminf(min_d, d);
+    max_d = fmaxf(max_d, d);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    min_d = fminf(min_d, __shfl_xor_sync(0xffffffffu, min_d, off));
+    max_d = fmaxf(max_d, __shfl_xor_sync(0xffffffffu, max_d, off));
+  }
+  if (lane == 0) {
+    if (min_d < INFINITY) atomicMin(&mm[2], dbits((double)min_d * (1.0 + 1e-5)));
+    if (max_d > 0.f) atomicMax(&mm[3], dbits((double)max_d * (1.0 - 1e-5)));
+  }
+}
+
+// Pass 1, one warp per 8 test triangles of a 32 x 32 block pair whose
+// bounding spheres reach below the pass-0 threshold mm[2] or above mm[3]
+// (the others hold no extreme and are skipped): thresholds from actual point
+// distances (the first rule point of each triangle of every regular pair:
+// their minimum is >= r_min, their maximum <= r_max), widened by a relative
+// 1e-5 for the FP32 rounding (mm[2], mm[3]), and, per block pair, the
+// smallest lower and largest upper bound of its regular pairs (bpb, merged by
+// integer atomics on the bits of these non-negative floats), so that pass 2
 // skips block pairs that cannot hold an extreme.
 __global__ void __launch_bounds__(kThreads) k_range_bounds(GeoView g, unsigned long long* mm, float2* bpb) {
   const int lane = threadIdx.x & 31;
   const int64_t nb = (g.nt + 31) / 32, ntask = nb * (nb + 1) / 2 * kRangeSplit;
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // the thresholds of pass 0 (any later, tighter value would serve as well)
+  const float u_min = (float)__longlong_as_double((long long)mm[2]);
+  const float l_max = (float)__longlong_as_double((long long)mm[3]);
   float min_d = INFINITY, max_d = 0.f;
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntask; t += nwarp) {
     const int64_t u = t / kRangeSplit;
     int p0, q0;
     sym_task(u * 32, g.nt, &p0, &q0);
+    {
+      float lb, ub;
+      block_bounds(g.bsph, p0 >> 5, q0 >> 5, &lb, &ub);
+      if (lb > u_min && ub < l_max) continue;  // no pair of this block pair can hold an extreme (uniform)
+    }
     p0 += (int)(t % kRangeSplit) * (32 / kRangeSplit);
     const int q = min(q0 + lane, g.nt - 1);
     const float4 cq = g.cen32[q], yq = g.pts32[q];
@@ -718,6 +785,13 @@ cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const v
   return cudaGetLastError();
 }
 
+cudaError_t launch_near_rows(const int64_t* near_ptr, int64_t nt, int32_t* near_row, cudaStream_t s) {
+  if (nt <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)std::min<int64_t>((nt + kWarps - 1) / kWarps, (int64_t)sm_count() * 8);
+  k_near_rows<<<blocks, kThreads, 0, s>>>(near_ptr, nt, near_row);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
                          cudaStream_t s) {
   const int64_t nb = (g.nt + 31) / 32, nbp = nb * (nb + 1) / 2;
@@ -730,6 +804,8 @@ cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_
   const unsigned nsm = (unsigned)sm_count();
   const unsigned b0 = (unsigned)std::min<int64_t>((nbp + kThreads - 1) / kThreads, (int64_t)nsm * 4);
   k_range_init<<<b0, kThreads, 0, s>>>(d_minmax, bpb, nbp);
+  const int64_t bw = std::min<int64_t>((nbp + kWarps - 1) / kWarps, (int64_t)nsm * 8);
+  k_range_witness<<<(unsigned)bw, kThreads, 0, s>>>(g, d_minmax);
   const int64_t b1 = std::min<int64_t>((nbp * kRangeSplit + kWarps - 1) / kWarps, (int64_t)nsm * 8);
   k_range_bounds<<<(unsigned)b1, kThreads, 0, s>>>(g, d_minmax, bpb);
   k_range_list<<<b0, kThreads, 0, s>>>(d_minmax, bpb, nbp, list);

@@ -7,7 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
-#include <unordered_map>
+#include <thread>
 #include <vector>
 
 #include "gf_internal.h"
@@ -702,14 +702,40 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
     for (int64_t pi = 0; pi < nt; ++pi)
       for (int c = 0; c < 3; ++c) vtri[fillp[tri[3 * (size_t)m->perm[pi] + c]]++] = (int32_t)pi;
   }
-  std::unordered_map<int64_t, std::vector<int32_t>> grid;
-  double cell = near_dist;
-  auto key = [](int64_t a, int64_t b, int64_t c) { return ((a & 0x1FFFFF) << 42) | ((b & 0x1FFFFF) << 21) | (c & 0x1FFFFF); };
+  // centroid grid of cell near_dist over the internal ids, as sorted cell
+  // keys with the ids of each cell (a pair closer than near_dist lies in
+  // neighbouring cells)
+  const double cell = near_dist;
+  auto key = [](int64_t a, int64_t b, int64_t c) {
+    return (uint64_t)(((a & 0x1FFFFF) << 42) | ((b & 0x1FFFFF) << 21) | (c & 0x1FFFFF));
+  };
+  auto cell_of = [&](int64_t t, int x) { return (int64_t)std::floor(cen[3 * t + x] / cell); };
+  struct CellPt {  // a centroid and its internal id, stored by cell
+    double x, y, z;
+    int32_t id;
+  };
+  std::vector<uint64_t> ckey, cells;  // key of each internal id; distinct keys, ascending
+  std::vector<int32_t> cell_ptr;     // offsets of the distinct keys' runs in cpts
+  std::vector<CellPt> cpts;
   if (near_dist > 0) {
-    for (int64_t t = 0; t < nt; ++t)
-      grid[key((int64_t)std::floor(cen[3 * t] / cell), (int64_t)std::floor(cen[3 * t + 1] / cell),
-               (int64_t)std::floor(cen[3 * t + 2] / cell))]
-          .push_back((int32_t)t);
+    ckey.resize(nt);
+    for (int64_t pi = 0; pi < nt; ++pi) {
+      const int64_t t = m->perm[pi];
+      ckey[pi] = key(cell_of(t, 0), cell_of(t, 1), cell_of(t, 2));
+    }
+    const std::vector<int32_t> by_cell = radix_order(ckey, 63);  // ascending key, ids ascending within a cell
+    cpts.resize(nt);
+    for (int64_t i = 0; i < nt; ++i) {
+      const int32_t qi = by_cell[i];
+      const size_t q = (size_t)m->perm[qi];
+      cpts[i] = CellPt{cen[3 * q], cen[3 * q + 1], cen[3 * q + 2], qi};
+      const uint64_t k = ckey[qi];
+      if (cells.empty() || cells.back() != k) {
+        cells.push_back(k);
+        cell_ptr.push_back((int32_t)i);
+      }
+    }
+    cell_ptr.push_back((int32_t)nt);
   }
   // union of ascending lists, without repeats
   auto merge_into = [](const int32_t* a, int na, const int32_t* b, int nb, std::vector<int32_t>& out) {
@@ -726,36 +752,86 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       out.push_back(x);
     }
   };
-  m->near_ptr.assign(nt + 1, 0);
-  m->near_idx.reserve(16 * (size_t)nt);
-  std::vector<int32_t> ab, row, close;
-  for (int64_t pi = 0; pi < nt; ++pi) {
-    const int64_t p = m->perm[pi];  // original id
-    const int32_t* v = &tri[3 * p];
-    merge_into(&vtri[vptr[v[0]]], vptr[v[0] + 1] - vptr[v[0]], &vtri[vptr[v[1]]], vptr[v[1] + 1] - vptr[v[1]], ab);
-    merge_into(ab.data(), (int)ab.size(), &vtri[vptr[v[2]]], vptr[v[2] + 1] - vptr[v[2]], row);
-    if (near_dist > 0) {
-      close.clear();
-      int64_t gx = (int64_t)std::floor(cen[3 * p] / cell), gy = (int64_t)std::floor(cen[3 * p + 1] / cell),
-              gz = (int64_t)std::floor(cen[3 * p + 2] / cell);
-      for (int dx = -1; dx <= 1; ++dx)
-        for (int dy = -1; dy <= 1; ++dy)
-          for (int dz = -1; dz <= 1; ++dz) {
-            auto it = grid.find(key(gx + dx, gy + dy, gz + dz));
-            if (it == grid.end()) continue;
-            for (int32_t q : it->second) {
-              double ax = cen[3 * p] - cen[3 * (size_t)q], ay = cen[3 * p + 1] - cen[3 * (size_t)q + 1],
-                     az = cen[3 * p + 2] - cen[3 * (size_t)q + 2];
-              if (std::sqrt(ax * ax + ay * ay + az * az) < near_dist) close.push_back(m->inv_perm[q]);
+  // rows of the near list (ascending internal ids): the vertex stars of the
+  // three vertices, plus the centroids closer than near_dist (the distance
+  // compared as sqrt(d2) < near_dist, decided on d2 where it is clear by a
+  // margin far above the rounding); built in chunks of rows on several host
+  // threads for large meshes, then concatenated in row order
+  const double lim_lo = near_dist * near_dist * (1.0 - 1e-9), lim_hi = near_dist * near_dist * (1.0 + 1e-9);
+  auto build_rows = [&](int64_t p0, int64_t p1, std::vector<int32_t>& idx, std::vector<int64_t>& cnt) {
+    std::vector<int32_t> ab, row, close;
+    for (int64_t pi = p0; pi < p1; ++pi) {
+      const int64_t p = m->perm[pi];  // original id
+      const int32_t* v = &tri[3 * p];
+      merge_into(&vtri[vptr[v[0]]], vptr[v[0] + 1] - vptr[v[0]], &vtri[vptr[v[1]]], vptr[v[1] + 1] - vptr[v[1]], ab);
+      merge_into(ab.data(), (int)ab.size(), &vtri[vptr[v[2]]], vptr[v[2] + 1] - vptr[v[2]], row);
+      if (near_dist > 0) {
+        close.clear();
+        const int64_t gx = cell_of(p, 0), gy = cell_of(p, 1), gz = cell_of(p, 2);
+        for (int dx = -1; dx <= 1; ++dx)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dz = -1; dz <= 1; ++dz) {
+              const uint64_t k = key(gx + dx, gy + dy, gz + dz);
+              const auto it = std::lower_bound(cells.begin(), cells.end(), k);
+              if (it == cells.end() || *it != k) continue;
+              const size_t c = (size_t)(it - cells.begin());
+              for (int32_t i = cell_ptr[c]; i < cell_ptr[c + 1]; ++i) {
+                const CellPt& cq = cpts[i];
+                const double ax = cen[3 * p] - cq.x, ay = cen[3 * p + 1] - cq.y, az = cen[3 * p + 2] - cq.z;
+                const double d2 = ax * ax + ay * ay + az * az;
+                if (d2 >= lim_hi) continue;
+                if (d2 < lim_lo || std::sqrt(d2) < near_dist) close.push_back(cq.id);
+              }
             }
-          }
-      std::sort(close.begin(), close.end());
-      close.erase(std::unique(close.begin(), close.end()), close.end());
-      ab.swap(row);
-      merge_into(ab.data(), (int)ab.size(), close.data(), (int)close.size(), row);
+        std::sort(close.begin(), close.end());
+        close.erase(std::unique(close.begin(), close.end()), close.end());
+        ab.swap(row);
+        merge_into(ab.data(), (int)ab.size(), close.data(), (int)close.size(), row);
+      }
+      idx.insert(idx.end(), row.begin(), row.end());
+      cnt.push_back((int64_t)row.size());
     }
-    m->near_idx.insert(m->near_idx.end(), row.begin(), row.end());
-    m->near_ptr[pi + 1] = (int64_t)m->near_idx.size();
+  };
+  int nthr = 1;
+  if (nt >= 8192) nthr = (int)std::min<unsigned>(std::max(std::thread::hardware_concurrency(), 1u), 16u);
+  std::vector<std::vector<int32_t>> part_idx(nthr);
+  std::vector<std::vector<int64_t>> part_cnt(nthr);
+  {
+    std::vector<std::thread> pool;
+    auto chunk = [&](int w) {
+      const int64_t p0 = nt * w / nthr, p1 = nt * (w + 1) / nthr;
+      part_cnt[w].reserve(p1 - p0);
+      part_idx[w].reserve(16 * (size_t)(p1 - p0));
+      build_rows(p0, p1, part_idx[w], part_cnt[w]);
+    };
+    for (int w = 1; w < nthr; ++w) {
+      try {
+        pool.emplace_back(chunk, w);
+      } catch (...) {  // no thread: this one builds the chunk afterwards
+        pool.emplace_back();
+      }
+    }
+    chunk(0);
+    for (int w = 1; w < nthr; ++w) {
+      if (pool[w - 1].joinable()) pool[w - 1].join();
+      else chunk(w);
+    }
+  }
+  m->near_ptr.assign(nt + 1, 0);
+  size_t total = 0;
+  for (int w = 0; w < nthr; ++w) total += part_idx[w].size();
+  m->near_idx.resize(total);
+  {
+    int64_t pi = 0;
+    size_t at = 0;
+    for (int w = 0; w < nthr; ++w) {
+      if (!part_idx[w].empty()) std::memcpy(&m->near_idx[at], part_idx[w].data(), part_idx[w].size() * 4);
+      at += part_idx[w].size();
+      for (int64_t c : part_cnt[w]) {
+        m->near_ptr[pi + 1] = m->near_ptr[pi] + c;
+        ++pi;
+      }
+    }
   }
   // ---- device: one pooled allocation; the arrays built here are uploaded
   // with one copy (they lead the arena, in this order)
@@ -768,10 +844,9 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
     return o;
   };
   const size_t o_tvert = take(16 * nt), o_tedge = take(16 * nt), o_near_ptr = take(8 * (nt + 1)),
-               o_near_idx = take(4 * nn), o_near_row = take(4 * nn), o_v64 = take(72 * nt),
-               o_elen = take(8 * std::max<int64_t>(m->ne, 1));
+               o_near_idx = take(4 * nn), o_v64 = take(72 * nt), o_elen = take(8 * std::max<int64_t>(m->ne, 1));
   const size_t upload = off;
-  const size_t o_pts32 = take(16 * kMaxRule * nt), o_cen32 = take(16 * nt), o_geo32 = take(48 * nt),
+  const size_t o_near_row = take(4 * nn), o_pts32 = take(16 * kMaxRule * nt), o_cen32 = take(16 * nt), o_geo32 = take(48 * nt),
                o_pts64 = take(32 * kMaxRule * nt), o_cen64 = take(32 * nt), o_geo64 = take(96 * nt),
                o_frame64 = take(8 * kFrame * nt), o_frame32 = take(4 * kFrame32 * nt), o_minmax = take(64),
                o_rad32 = take(4 * nt), o_bsph = take(16 * nb), o_bpb = take(8 * (size_t)(nb * (nb + 1) / 2)),
@@ -809,7 +884,11 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   m->d_geob32 = reinterpret_cast<float4*>(base + o_geob32);
   m->d_range_bpb = reinterpret_cast<float2*>(base + o_bpb);
   m->d_range_list = reinterpret_cast<int32_t*>(base + o_list);
-  std::vector<unsigned char> h(upload, 0);
+  std::unique_ptr<unsigned char[]> h(new (std::nothrow) unsigned char[upload]);
+  if (!h) {
+    free_mesh_device(m.get());
+    return fail(GF_ERR_ALLOC, "gf_mesh_create: out of host memory");
+  }
   int4* tv = reinterpret_cast<int4*>(&h[o_tvert]);
   int4* te = reinterpret_cast<int4*>(&h[o_tedge]);
   for (int64_t i = 0; i < nt; ++i) {
@@ -819,11 +898,10 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   }
   std::memcpy(&h[o_near_ptr], m->near_ptr.data(), (nt + 1) * 8);
   if (nn) std::memcpy(&h[o_near_idx], m->near_idx.data(), nn * 4);
-  int32_t* rows = reinterpret_cast<int32_t*>(&h[o_near_row]);
-  for (int64_t pi = 0; pi < nt; ++pi)
-    for (int64_t j = m->near_ptr[pi]; j < m->near_ptr[pi + 1]; ++j) rows[j] = (int32_t)pi;
   vertex_arrays(m.get(), &h[o_v64]);
-  cudaError_t e = cudaMemcpy(base, h.data(), upload, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(base, h.get(), upload, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_near_rows(m->d_near_ptr, nt, m->d_near_row, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
   if (e != cudaSuccess) {
     free_mesh_device(m.get());
     return cuda_fail(e, "gf_mesh_create upload");

@@ -210,6 +210,7 @@ struct TableBuild {
 cudaError_t launch_tables(const TableBuild& a, const TableBuild& b, double k, cudaStream_t s);
 // Block spheres, block centres on the grid of step g.bunit, and the offsets
 // from them (rel32, geob32) of the current rule's geometry.
+cudaError_t launch_near_rows(const int64_t* near_ptr, int64_t nt, int32_t* near_row, cudaStream_t s);
 cudaError_t launch_block_frames(const GeoView& g, float4* bsph, int4* bgrid, float4* rel32, float4* geob32,
                                 cudaStream_t s);
 cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const void* r, int64_t n,
