@@ -785,6 +785,18 @@ cudaError_t launch_table_eval(const TabView& t, int kind, int precision, const v
   return cudaGetLastError();
 }
 
+// r_min, r_max into page-locked host memory mapped into the device: the host
+// reads them after a stream synchronization, with no copy-engine transfer
+// (which would queue behind large copies of Z on other streams).
+__global__ void k_range_out(const unsigned long long* __restrict__ mm, unsigned long long* h) {
+  if (threadIdx.x < 2) h[threadIdx.x] = mm[threadIdx.x];
+}
+
+cudaError_t launch_range_out(const unsigned long long* d_minmax, unsigned long long* h_range, cudaStream_t s) {
+  k_range_out<<<1, 32, 0, s>>>(d_minmax, h_range);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_near_rows(const int64_t* near_ptr, int64_t nt, int32_t* near_row, cudaStream_t s) {
   if (nt <= 0) return cudaSuccess;
   const unsigned blocks = (unsigned)std::min<int64_t>((nt + kWarps - 1) / kWarps, (int64_t)sm_count() * 8);

@@ -417,8 +417,10 @@ void free_mesh_device(gf_mesh* m) {
   }
   if (m->d_dtri) cudaFree(m->d_dtri);
   if (m->d_dk) cudaFree(m->d_dk);
+  if (m->h_range) cudaFreeHost(m->h_range);
   m->d_dtri = nullptr;
   m->d_dk = nullptr;
+  m->h_range = nullptr;
 }
 
 // Triangle corners (internal order) and RWG edge lengths, laid out as on the
@@ -954,9 +956,14 @@ gf_status gf_range(const gf_mesh* mc, int rule, int precision, double* r_min, do
   cudaStream_t s = (cudaStream_t)stream;
   if ((st = prepare_rule_impl(m, rule, s))) return st;
   GF_CUDA(launch_range(geo_view_impl(m), precision, m->d_minmax, m->d_range_bpb, m->d_range_list, s));
-  unsigned long long mm[2];
-  GF_CUDA(cudaMemcpyAsync(mm, m->d_minmax, 16, cudaMemcpyDeviceToHost, s));
+  // the result through device-mapped page-locked memory, written by a kernel
+  if (!m->h_range) GF_CUDA(cudaHostAlloc((void**)&m->h_range, 16, cudaHostAllocMapped));
+  unsigned long long* h_dev = nullptr;
+  GF_CUDA(cudaHostGetDevicePointer((void**)&h_dev, m->h_range, 0));
+  GF_CUDA(launch_range_out(m->d_minmax, h_dev, s));
   GF_CUDA(cudaStreamSynchronize(s));
+  unsigned long long mm[2];
+  std::memcpy(mm, (const void*)m->h_range, 16);
   double lo, hi;
   std::memcpy(&lo, &mm[0], 8);
   std::memcpy(&hi, &mm[1], 8);

@@ -228,6 +228,7 @@ cudaError_t launch_fill_sparse(const GeoView& g, const TabView* green, const Tab
                                const void* tasks, int64_t ntask, const int32_t* widx, const int64_t* row_ptr,
                                const int32_t* cols, void* vals, cudaStream_t s);
 int sparse_task_bytes();
+cudaError_t launch_range_out(const unsigned long long* d_minmax, unsigned long long* h_range, cudaStream_t s);
 cudaError_t launch_range(const GeoView& g, int precision, unsigned long long* d_minmax, float2* bpb, int32_t* list,
                          cudaStream_t s);
 // table: the Green table view, or with from_exp the Exp table view (e^{-jkR}
@@ -308,6 +309,7 @@ struct gf_mesh {
   double* d_dtri = nullptr;                 // adjoint scratch [nt][9]
   double* d_dk = nullptr;                   // adjoint scratch [1]
   unsigned long long* d_minmax = nullptr;  // range scratch [8]
+  unsigned long long* h_range = nullptr;   // page-locked, device-mapped: r_min, r_max of the last gf_range
   float2* d_range_bpb = nullptr;          // range scratch: bounds per 32 x 32 block pair
   int32_t* d_range_list = nullptr;        // range scratch: block pairs that can hold an extreme, count last
 };
