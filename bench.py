@@ -10,15 +10,17 @@ tolerance 1e-6. Synthetic, seeded input. `--workload sphere_7680` gives the
 
 One step = the whole hot path on a device-resident mesh: R_min/R_max
 reduction, Green + Exp table construction, zeroing Z, the regular-pair fill
-kernel and the near-pair kernel. `value` is Z entries / s over all ranks.
-Alongside: the direct (sincospi) fill on the same mesh, the regular kernel's
-roofline fraction, an end-to-end number through the C ABI from host arrays to
-a host copy of Z, the oracle's accuracy check on sampled rows, and the FP64
-CPU oracle timed on a bounded sample (the CPU baseline).
+kernel, the Z + Z^T pass and the near-pair kernel. `value` is Z entries / s
+over all ranks. Alongside: the direct (sincospi) fill on the same mesh, the
+regular kernel's roofline fraction, an end-to-end number through the C ABI
+from host arrays to a host copy of Z, the oracle's accuracy check on seeded
+256 x 256 blocks, and the FP64 CPU oracle timed on a bounded sample of rows
+(the CPU baseline, extrapolated).
 
 python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--workload NAME]
 """
 import argparse
+import ctypes
 import hashlib
 import json
 import math
@@ -528,30 +530,67 @@ def run_ours(args, wl, rank, world, local_rank):
         except RuntimeError:
             Zb = None
         if reduce_max(0.0 if Zb is not None else 1.0) == 0.0:
-            copy_stream = torch.cuda.Stream()
+            # a non-blocking stream for the copies: work on the legacy default
+            # stream (the fill's stream here, the library's mesh upload) would
+            # otherwise wait for a copy in flight on a blocking stream
+            rt = ctypes.CDLL("libcudart.so.13")
+            handle = ctypes.c_void_p()
+            if rt.cudaStreamCreateWithFlags(ctypes.byref(handle), ctypes.c_uint(1)) != 0:
+                raise RuntimeError("cudaStreamCreateWithFlags failed")
+            copy_stream = torch.cuda.ExternalStream(handle.value)
+
+            piece = max(1, (256 << 20) // Z.element_size())
 
             def streamed(n):
-                keep, done = [], [None, None]
-                for i in range(n):
-                    zb = Zb[i % 2]
-                    m3 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
-                    lo3, hi3 = m3.range(wl.rule, prec)
-                    if done[i % 2] is not None:
-                        stream.wait_event(done[i % 2])  # the copy out of this buffer, two steps back
-                    gf.gf_fill_parts(m3.h, wl.k, p, None, prec, zb, gf.GF_PART_ZERO)
-                    tab3 = gf.Table(wl.k, lo3, hi3, p)
-                    gf.gf_fill_parts(m3.h, wl.k, p, tab3.h, prec, zb, gf.GF_PART_REGULAR | gf.GF_PART_NEAR)
-                    filled = torch.cuda.Event()
-                    filled.record(stream)
-                    copy_stream.wait_event(filled)
-                    zsrc = zb.view(-1)
-                    with torch.cuda.stream(copy_stream):
-                        for c0 in range(0, zsrc.numel(), chunk):
-                            zhost_flat[c0:c0 + chunk].copy_(zsrc[c0:c0 + chunk], non_blocking=True)
-                    ev = torch.cuda.Event()
-                    ev.record(copy_stream)
-                    done[i % 2] = ev
-                    keep.append((m3, tab3))  # freed after the timed loop (freeing waits for the device)
+                """n steps; the copies run on a host thread that keeps one 256 MiB
+                piece in flight, so that the next step's host-to-device uploads
+                (mesh, tables) are not queued behind a whole Z of copies."""
+                import queue
+                jobs, copied, keep = queue.Queue(), [threading.Event() for _ in range(n)], []
+
+                failed = []
+
+                def copier():
+                    try:
+                        while True:
+                            job = jobs.get()
+                            if job is None:
+                                return
+                            i, zsrc, filled = job
+                            filled.synchronize()
+                            with torch.cuda.stream(copy_stream):
+                                for c0 in range(0, zsrc.numel(), piece):
+                                    zhost_flat[c0:c0 + piece].copy_(zsrc[c0:c0 + piece], non_blocking=True)
+                                    copy_stream.synchronize()
+                            copied[i].set()
+                    except Exception as exc:  # noqa: BLE001 - reported by the main thread
+                        failed.append(exc)
+                        for ev in copied:
+                            ev.set()
+
+                th = threading.Thread(target=copier)
+                th.start()
+                try:
+                    for i in range(n):
+                        zb = Zb[i % 2]
+                        m3 = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+                        lo3, hi3 = m3.range(wl.rule, prec)
+                        if i >= 2:
+                            copied[i - 2].wait()  # the copy out of this buffer, two steps back
+                        if failed:
+                            raise failed[0]
+                        gf.gf_fill_parts(m3.h, wl.k, p, None, prec, zb, gf.GF_PART_ZERO)
+                        tab3 = gf.Table(wl.k, lo3, hi3, p)
+                        gf.gf_fill_parts(m3.h, wl.k, p, tab3.h, prec, zb, gf.GF_PART_REGULAR | gf.GF_PART_NEAR)
+                        filled = torch.cuda.Event()
+                        filled.record(stream)
+                        jobs.put((i, zb.view(-1), filled))
+                        keep.append((m3, tab3))  # freed after the timed loop (freeing waits for the device)
+                finally:
+                    jobs.put(None)
+                    th.join()
+                if failed:
+                    raise failed[0]
                 torch.cuda.synchronize()
                 return keep
 
@@ -562,7 +601,8 @@ def run_ours(args, wl, rank, world, local_rank):
             kept = streamed(n_e2e)
             pipe_s = reduce_max((time.perf_counter() - t0) / n_e2e)
             kept.clear()
-            del Zb
+            torch.cuda.synchronize()
+            del Zb  # (the copy stream lives until the process exits: torch may still query it)
         e2e_s = pipe_s if pipe_s is not None else serial_s
         e2e = {"value": world * ne * ne / e2e_s, "unit": "Z entries/s",
                "h2d_bytes_per_step": wl.xyz.nbytes + wl.tri.nbytes, "d2h_bytes_per_step": zbytes,
