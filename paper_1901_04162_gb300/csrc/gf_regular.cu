@@ -7,19 +7,20 @@
 namespace gf {
 namespace {
 
-// Threads of the CTA that holds the table in shared memory (one per SM): 20
-// warps for rules of up to 4 points (at most 96 registers a thread), 16 for
-// the larger rules.
+// Threads of the CTA that holds the table in shared memory (one per SM): 28
+// warps for rules of up to 4 points (at most 72 registers a thread; 7 warps per
+// scheduler), 16 for the larger rules (128 registers).
 template <int M>
 constexpr int smem_block() {
-  return M <= 4 ? 640 : 512;
+  return M <= 4 ? 896 : 512;
 }
 
 // One warp per (test triangle p, 32 source triangles) task over the 32 x 32
 // triangle block pairs; SMEM: the table's lattice image staged in shared
-// memory (one CTA per SM holds it), else read through L1.
+// memory (one CTA per SM holds it), else read through L1 (the direct kernel:
+// three 256-thread CTAs per SM for rules of up to 4 points).
 template <int M, int MODE, bool SMEM, bool KR>
-__global__ void __launch_bounds__(SMEM ? smem_block<M>() : kThreads) k_fill_regular32(GeoView g, TabView tv, RegK K,
+__global__ void __launch_bounds__(SMEM ? smem_block<M>() : kThreads, SMEM ? 1 : (M <= 4 ? 3 : 1)) k_fill_regular32(GeoView g, TabView tv, RegK K,
                                                                                       float2* Z, int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
