@@ -67,8 +67,9 @@ RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 # pair of the cube's smaller case (the kernel's DRAM traffic is the
 # read-modify-write of Z through the row atomics and the mirror-free half, and
 # Z grows with the pair count).
-TRAFFIC_HASH = "86f16cd9c092af3b"
-TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1965611520 + 2385367040, 75331278)}
+TRAFFIC_HASH = "2ebc2719d3f69dff"
+TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1966764544 + 2390544384, 75331278),
+           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298452224 + 283401984, 13073950)}
 TRAFFIC_SCALED_FROM = {"cube_3lambda_49152tri_73728rwg_4pt_fp32": "cube_3lambda_12288tri_18432rwg_4pt_fp32"}
 TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
                 "(ncu, --clock-control none); the 73728-unknown cube's from the 18432-unknown cube's capture scaled "

@@ -524,9 +524,10 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
                                                bool ok, const Sink& sink) {
   if (!__any_sync(0xffffffffu, ok)) return;
   const BlockSep bs = block_sep(g, p, q);
-  // w_b r_b kept in registers for small rules, except in the kernels that hold
-  // the lattice in shared memory: those spend the registers on resident warps
-  // (one CTA per SM; 28 warps at 72 registers for the 4-point rule)
+  // w_b r_b kept in registers for small rules in the kernels of 256-thread
+  // CTAs; SM (the lattice in shared memory, or in direct mode one wide CTA per
+  // SM) spends those registers on resident warps instead (28 warps at 72
+  // registers for the 4-point rule)
   constexpr bool kWQ = M <= 4 && !SM;
   float rx[M], ry[M], rz[M], wb[M], bq[M];
 #pragma unroll

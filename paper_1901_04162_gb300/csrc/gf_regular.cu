@@ -17,10 +17,13 @@ constexpr int smem_block() {
 
 // One warp per (test triangle p, 32 source triangles) task over the 32 x 32
 // triangle block pairs; SMEM: the table's lattice image staged in shared
-// memory (one CTA per SM holds it), else read through L1 (the direct kernel:
-// three 256-thread CTAs per SM for rules of up to 4 points).
+// memory (one CTA per SM holds it), else read through L1. The direct kernel
+// for rules of up to 4 points runs the same CTA shape (one CTA of 896
+// threads per SM at 72 registers), which measured faster than three
+// 256-thread CTAs per SM.
 template <int M, int MODE, bool SMEM, bool KR>
-__global__ void __launch_bounds__(SMEM ? smem_block<M>() : kThreads, SMEM ? 1 : (M <= 4 ? 3 : 1)) k_fill_regular32(GeoView g, TabView tv, RegK K,
+__global__ void __launch_bounds__((SMEM || (MODE == kDirect && M <= 4)) ? smem_block<M>() : kThreads, 1)
+    k_fill_regular32(GeoView g, TabView tv, RegK K,
                                                                                       float2* Z, int64_t ldz) {
   extern __shared__ __align__(16) unsigned char smem[];
   Tab32 T = tab32(tv);
@@ -34,7 +37,8 @@ __global__ void __launch_bounds__(SMEM ? smem_block<M>() : kThreads, SMEM ? 1 : 
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
     if (sym_task(task, g.nt, &p, &q0))
-      regular_task32<M, MODE, KR, SMEM && MODE != kDirect>(g, T, K, DenseUpper{Z, ldz}, p, q0, lane);
+      regular_task32<M, MODE, KR, (SMEM && MODE != kDirect) || (MODE == kDirect && M <= 4)>(g, T, K,
+                                                                                        DenseUpper{Z, ldz}, p, q0, lane);
   }
 }
 
@@ -252,8 +256,12 @@ cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_e
                              int64_t ldz, cudaStream_t s) {
   if (!table) {
     TabView tv{};
-    int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
+    if (M <= 4) {
+      k_fill_regular32<M, kDirect, false, false><<<(unsigned)sm_count(), smem_block<M>(), 0, s>>>(g, tv, K, Z, ldz);
+    } else {
+      int64_t blocks = pair_grid(g, 4);
+      k_fill_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
+    }
     return cudaGetLastError();
   }
   const bool kr = table->xscale32 != 1.f;
