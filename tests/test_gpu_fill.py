@@ -85,12 +85,15 @@ def test_green_from_exp_matches_oracle():
         assert rel_fro(z, ref) <= 1e-5 and rel_max(z, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("which", ["plate", "sphere", "cube"])
+@pytest.mark.parametrize("which", ["plate", "sphere", "cube", "cube16"])
 def test_range_matches_oracle(which):
-    wl = {"plate": W.plate_280, "sphere": W.sphere_3072, "cube": lambda: W.cube_73728(6)}[which]()
+    # cube16: 3072 triangles in 96 blocks with the centroid criterion, where
+    # most block pairs are skipped after the first-threshold pass
+    wl = {"plate": W.plate_280, "sphere": W.sphere_3072, "cube": lambda: W.cube_73728(6),
+          "cube16": lambda: W.cube_73728(16)}[which]()
     m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
     om = O.Mesh(wl.xyz, wl.tri, wl.near_dist)
-    for rule in (3, 7):
+    for rule in ((4,) if which == "cube16" else (3, 7)):
         lo, hi = om.range(rule)
         g64 = m.range(rule, gf.GF_FP64)
         g32 = m.range(rule, gf.GF_FP32)
@@ -180,6 +183,31 @@ def test_mesh_edges_and_near_count_match_oracle():
         nt = len(wl.tri)
         if nt <= 1000:
             assert m.n_near == sum(om.is_near(p, q) for p in range(nt) for q in range(nt))
+
+
+def test_near_count_large_mesh_brute_force():
+    # 12288 triangles with the centroid criterion: the near rows are built on
+    # several host threads from a cell-sorted centroid array; their number
+    # equals a brute-force count of the ordered pairs that share a vertex or
+    # whose centroids are closer than near_dist (distance compared as the
+    # library and the oracle do, sqrt(d2) < near_dist)
+    sp = pytest.importorskip("scipy.sparse")
+    wl = W.cube_73728(32)
+    m = gf.Mesh(wl.xyz, wl.tri, wl.near_dist)
+    tri = np.asarray(wl.tri)
+    cen = wl.xyz[tri].mean(axis=1)
+    nt = len(tri)
+    inc = sp.csr_matrix((np.ones(3 * nt), (np.repeat(np.arange(nt), 3), tri.ravel())), shape=(nt, len(wl.xyz)))
+    near = (inc @ inc.T).tocsr()  # pairs sharing a vertex (self included)
+    rows, cols = [], []
+    for a0 in range(0, nt, 1024):  # centroid distances by brute force
+        d = np.sqrt(((cen[a0:a0 + 1024, None, :] - cen[None, :, :]) ** 2).sum(-1))
+        r, c = np.nonzero(d < wl.near_dist)
+        rows.append(r + a0)
+        cols.append(c)
+    r, c = np.concatenate(rows), np.concatenate(cols)
+    near = near + sp.csr_matrix((np.ones(len(r)), (r, c)), shape=(nt, nt))
+    assert m.n_near == near.nnz
 
 
 @pytest.mark.parametrize("table", [False, True])
