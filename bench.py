@@ -691,7 +691,9 @@ def run_ours(args, wl, rank, world, local_rank):
         "clocks": clocks,
         "e2e": e2e,
         # per step: range 4 (FP32; 2 in FP64), both tables 3, regular pairs 1, mirror 1 (FP32 only), near 1
-        "gpu_launches": (10 if prec == gf.GF_FP32 else 7) * args.steps,
+        # per step: range (init, [pass 0, pass 1, list, pass 2] or FP64 pass, out),
+        # three table kernels, the pair kernel, [the mirror], the near kernel
+        "gpu_launches": (12 if prec == gf.GF_FP32 else 8) * args.steps,
     }
     del zhost
     # ---- accuracy vs the FP64 oracle on 64 seeded 256 x 256 blocks (outside the timed region)
