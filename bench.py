@@ -88,6 +88,38 @@ def kernel_traffic(workload, n_pairs):
     return None
 
 
+# FP64 arithmetic instructions (DADD + DFMA + DMUL, thread level) per (near pair,
+# test point) of the mixed-precision near kernel, from an ncu capture of the
+# 18432-unknown cube (profiles/); valid while the near kernel's sources match.
+NEAR_FP64_OPS_HASH = "c1e2fb1ff6a5b3d7"
+NEAR_FP64_OPS_PER_TASK = (59829840 + 165940896 + 64555955) / (332388 * 4)  # 218.4
+FP64_OPS_PER_SM_CLOCK = 2  # GB300: 304 DFMA thread instructions per clock on 152 SMs (ncu peak_sustained)
+
+
+def near_source_hash():
+    h = hashlib.sha256()
+    for name in ("gf_device.cuh", "gf_near.cuh", "gf_fill.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def other_kernel_rooflines(workload, zbytes, mirror_ms, near_ms, near_tasks, pk, sm_mhz):
+    """The mirror pass against the measured HBM copy bandwidth (it reads and
+    writes all of Z), and the mixed near kernel against the FP64 pipe."""
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    out = {"mirror": {"kernel": "k_symmetrize32", "bound": "hbm", "bytes": 2 * zbytes,
+                      "achieved": 2 * zbytes / (mirror_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}}
+    out["mirror"]["frac"] = out["mirror"]["achieved"] / hbm
+    near = {"kernel": "k_fill_near<mixed>", "bound": "fp64", "unit": "FP64 arithmetic instructions/s (thread)",
+            "peak": SM_COUNT * FP64_OPS_PER_SM_CLOCK * sm_mhz * 1e6, "achieved": None, "frac": None}
+    if NEAR_FP64_OPS_PER_TASK is not None and near_source_hash() == NEAR_FP64_OPS_HASH and near_ms > 0:
+        near["achieved"] = NEAR_FP64_OPS_PER_TASK * near_tasks / (near_ms / 1e3)
+        near["frac"] = near["achieved"] / near["peak"]
+        near["ops_per_task"] = NEAR_FP64_OPS_PER_TASK
+    out["near"] = near
+    return out
+
+
 def reduce_max_over_ranks(x, dist=None, device="cpu"):
     """The largest x over all ranks (a job takes as long as its slowest rank)."""
     if dist is None:
@@ -690,7 +722,8 @@ def run_ours(args, wl, rank, world, local_rank):
                      "smem": smem_model(evals_regular, reg_ms, sm_mhz)},
         "clocks": clocks,
         "e2e": e2e,
-        # per step: range 4 (FP32; 2 in FP64), both tables 3, regular pairs 1, mirror 1 (FP32 only), near 1
+        "other_kernels": other_kernel_rooflines(wl.name, zbytes, statistics.mean(tt["mirror_ms"]),
+                                                statistics.mean(tt["near_ms"]), n_near * m, pk, sm_mhz),
         # per step: range (init, [pass 0, pass 1, list, pass 2] or FP64 pass, out),
         # three table kernels, the pair kernel, [the mirror], the near kernel
         "gpu_launches": (12 if prec == gf.GF_FP32 else 8) * args.steps,
