@@ -255,9 +255,18 @@ __device__ __forceinline__ bool pair_is_near(const GeoView& g, int p, int q, int
 
 __device__ __forceinline__ bool sym_task(int64_t task, int nt, int* p, int* q0) {
   const int64_t u = task >> 5;
-  int64_t bq = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
-  while (bq > 0 && bq * (bq + 1) / 2 > u) --bq;
-  while ((bq + 1) * (bq + 2) / 2 <= u) ++bq;
+  int64_t bq;
+  if (u < (int64_t(1) << 29)) {  // 32-bit integers and conversions (the 64-bit ones take the FP64 pipe)
+    const int u32 = (int)u;
+    int b = (int)((sqrtf(8.f * (float)u32 + 1.f) - 1.f) * 0.5f);
+    while (b > 0 && b * (b + 1) / 2 > u32) --b;
+    while ((b + 1) * (b + 2) / 2 <= u32) ++b;
+    bq = b;
+  } else {
+    bq = (int64_t)((sqrtf(8.f * (float)u + 1.f) - 1.f) * 0.5f);
+    while (bq > 0 && bq * (bq + 1) / 2 > u) --bq;
+    while ((bq + 1) * (bq + 2) / 2 <= u) ++bq;
+  }
   const int64_t bp = u - bq * (bq + 1) / 2;
   *p = (int)(bp * 32 + (task & 31));
   *q0 = (int)(bq * 32);
