@@ -467,132 +467,6 @@ __device__ void inner_integrals_d(const V3D& r, const V3D v[3], const NearArgs& 
   }
 }
 
-// FP32 dual numbers for the edge sampling of the mixed-precision near pairs.
-struct F1 {
-  float v, d;
-};
-__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1{a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1{a.v - b.v, a.d - b.d}; }
-__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1{a.v * b.v, fmaf(a.d, b.v, a.v * b.d)}; }
-__device__ __forceinline__ F1 operator*(F1 a, float s) { return F1{a.v * s, a.d * s}; }
-__device__ __forceinline__ F1 f1(D1 a) { return F1{(float)a.v, (float)a.d}; }
-__device__ __forceinline__ F1 fsqrt1(F1 a) {
-  const float r = sqrtf(a.v);
-  return F1{r, a.d * 0.5f * __frcp_rn(r)};
-}
-
-// e^{-jk R} and its derivative in FP32 (table value when R is in range).
-__device__ __forceinline__ void exp_mjkr_f(F1 k, F1 R, const Tab32& te, bool use_table, float lo, float hi,
-                                           F1* re, F1* im) {
-  const F1 ph = k * R;
-  float c, s;
-  if (use_table && R.v >= lo && R.v <= hi) {
-    const float2 f = lookup32<1>(te, R.v);
-    c = f.x;
-    s = -f.y;
-  } else {
-    sincospif(ph.v * 0.318309886183790672f, &s, &c);
-  }
-  *re = F1{c, -s * ph.d};
-  *im = F1{-s, -c * ph.d};
-}
-
-// inner_integrals_d with the sampling of each edge in FP32 duals (geometry,
-// closed-form static part and accumulation in FP64 duals).
-__device__ void inner_integrals_d_mixed(const V3D& r, const V3D v[3], const NearArgs& A, D1 k, const Tab32& te,
-                                        bool use_table, float lo, float hi, DC* I0, DC I1[3], V3D* rho0_out) {
-  V3D n = vcross(vsub(v[1], v[0]), vsub(v[2], v[0]));
-  const D1 inv = D1{1.0, 0.0} / dsqrt(vdot(n, n));
-  n = vscale(n, inv);
-  const D1 h = vdot(n, vsub(r, v[0]));
-  const D1 d = dabs(h);
-  const V3D rho0 = vsub(r, vscale(n, h));
-  *rho0_out = rho0;
-  const F1 k32 = f1(k), d32 = f1(d);
-  F1 edr, edi;
-  exp_mjkr_f(k32, d32, te, use_table, lo, hi, &edr, &edi);
-  // |r - v_c|: R at the ends of the two edges that meet at v_c (scalars, so
-  // that the edge loop can pick them without a local-memory array)
-  const V3D dv0 = vsub(v[0], r), dv1 = vsub(v[1], r), dv2 = vsub(v[2], r);
-  const D1 Rv0 = dsqrt(vdot(dv0, dv0)), Rv1 = dsqrt(vdot(dv1, dv1)), Rv2 = dsqrt(vdot(dv2, dv2));
-  DC sacc{D1{0, 0}, D1{0, 0}};
-  DC vacc[3] = {{D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}, {D1{0, 0}, D1{0, 0}}};
-  D1 vst[3] = {D1{0, 0}, D1{0, 0}, D1{0, 0}};
-  for (int e = 0; e < 3; ++e) {
-    const V3D a = v[e], b = v[(e + 1) % 3];
-    V3D t = vsub(b, a);
-    const D1 len = dsqrt(vdot(t, t));
-    t = vscale(t, D1{1.0, 0.0} / len);
-    const V3D mh = vcross(t, n);
-    const V3D ar = vsub(a, rho0);
-    const D1 P0 = vdot(ar, mh), lm = vdot(ar, t), lp = lm + len;
-    if (fabs(P0.v) > 1e-12 * len.v) {
-      const D1 aP = dabs(P0);
-      const D1 iaP = D1{1.0, 0.0} / aP;
-      const F1 x1 = f1(lm * iaP), x2 = f1(lp * iaP);
-      const F1 um = F1{asinhf(x1.v), x1.d * rsqrtf(1.f + x1.v * x1.v)};
-      const F1 up = F1{asinhf(x2.v), x2.d * rsqrtf(1.f + x2.v * x2.v)};
-      const F1 half = (up - um) * 0.5f, mid = (up + um) * 0.5f;
-      const F1 aP32 = f1(aP);
-      F1 cr{0.f, 0.f}, ci{0.f, 0.f};
-      for (int i = 0; i < A.nphi; ++i) {
-        const F1 u = mid + half * A.fx_phi[i];
-        const float E = expf(u.v), iE = __frcp_rn(E);
-        const F1 ch{0.5f * (E + iE), 0.5f * (E - iE) * u.d};
-        const F1 rho = aP32 * ch;
-        const F1 Re = fsqrt1(rho * rho + d32 * d32);
-        F1 er, ei;
-        exp_mjkr_f(k32, Re, te, use_table, lo, hi, &er, &ei);
-        const float ich = __frcp_rn(ch.v);
-        const F1 wt{A.fw_phi[i] * ich, -A.fw_phi[i] * ich * ich * ch.d};
-        cr = cr + (edr - er) * wt;
-        ci = ci + (edi - ei) * wt;
-      }
-      const D1 hd{(double)half.v, (double)half.d};
-      const D1 sg = P0.v > 0 ? hd : -hd;
-      sacc = DC{sacc.re + D1{(double)cr.v, (double)cr.d} * sg, sacc.im + D1{(double)ci.v, (double)ci.d} * sg};
-    }
-    const V3D a_r = vsub(a, r);
-    const F1 ax = f1(a_r.x), ay = f1(a_r.y), az = f1(a_r.z), tx = f1(t.x), ty = f1(t.y), tz = f1(t.z);
-    const F1 hl = f1(len * 0.5);
-    F1 lr{0.f, 0.f}, li{0.f, 0.f};
-    for (int i = 0; i < A.nl; ++i) {
-      const F1 sp = hl * (A.fx_l[i] + 1.0f);
-      const F1 x0 = ax + tx * sp, x1v = ay + ty * sp, x2v = az + tz * sp;
-      const F1 R = fsqrt1(x0 * x0 + x1v * x1v + x2v * x2v);
-      F1 er, ei;
-      exp_mjkr_f(k32, R, te, use_table, lo, hi, &er, &ei);
-      lr = lr + F1{er.v - 1.f, er.d} * A.fw_l[i];
-      li = li + (ei + k32 * R) * A.fw_l[i];
-    }
-    const D1 lrd = D1{(double)lr.v, (double)lr.d} * (len * 0.5), lid = D1{(double)li.v, (double)li.d} * (len * 0.5);
-    const D1 R02 = P0 * P0 + d * d;
-    const D1 Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
-    D1 st = (lp * Rp - lm * Rm) * 0.5;
-    if (R02.v > 0) {
-      const D1 fp = lp.v >= 0 ? lp + Rp : R02 / (Rp - lp);
-      const D1 fm = lm.v >= 0 ? lm + Rm : R02 / (Rm - lm);
-      st = st + R02 * dlog(fp / fm) * 0.5;
-    }
-    const D1 mhv[3] = {mh.x, mh.y, mh.z};
-    for (int x = 0; x < 3; ++x) {
-      vacc[x] = DC{vacc[x].re + lrd * mhv[x], vacc[x].im + lid * mhv[x]};
-      vst[x] = vst[x] + mhv[x] * st;
-    }
-  }
-  const double c4 = 1.0 / (4.0 * kPi);
-  const D1 ik = D1{1.0, 0.0} / k;
-  I0->re = sacc.im * ik * c4;
-  I0->im = -(sacc.re * ik) * c4;
-  for (int x = 0; x < 3; ++x) {
-    I1[x].re = (vst[x] - vacc[x].im * ik) * c4;
-    I1[x].im = vacc[x].re * ik * c4;
-  }
-}
-
-// One (near pair, direction) on 8 lanes, one test point per lane. Direction
-// 0..8: p's vertex coordinates, 9..17: q's, 18: k. The derivative of the
-// pair's share of L is reduced over the points and added to dtri / dk.
 // ---- near pairs, reverse mode (mixed precision): one pass per (near pair,
 // test point) gives the derivatives along all 19 directions. The values are
 // those of inner_integrals_mixed (FP64 frames, projection, static closed form
@@ -1107,12 +981,10 @@ __global__ void __launch_bounds__(128) k_adjoint_near_rev(GeoView g, TabView te,
 
 // One (near pair, derivative direction) per group of G lanes (lane = test
 // point): directions 0..8 = p's vertex coordinates, 9..17 = q's, 18 = k.
-template <bool MIXED, int G>
+template <int G>
 __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, bool use_table, NearArgs A, double k,
                                                       double eta, BaryF bw, const float2* __restrict__ gZ, int64_t ldg,
                                                       double* dtri, double* dkacc) {
-  const Tab32 te32 = tab32(te);
-  const float lo32 = (float)te.r_lo, hi32 = (float)te.r_hi;
   const int64_t n_near = g.near_ptr[g.nt];
   const int64_t njobs = n_near * 19;
   const int sub = threadIdx.x & (G - 1);
@@ -1144,8 +1016,7 @@ __global__ void __launch_bounds__(128) k_adjoint_near(GeoView g, TabView te, boo
       }
       DC I0, I1[3];
       V3D rho0;
-      if (MIXED) inner_integrals_d_mixed(ra, vq, A, kd, te32, use_table, lo32, hi32, &I0, I1, &rho0);
-      else inner_integrals_d(ra, vq, A, kd, &te, use_table, &I0, I1, &rho0);
+      inner_integrals_d(ra, vq, A, kd, &te, use_table, &I0, I1, &rho0);
       const V3D nq = vcross(vsub(vq[1], vq[0]), vsub(vq[2], vq[0]));
       const D1 area_q = dsqrt(vdot(nq, nq)) * 0.5;
       const int4 ep = g.tedge[p], eq = g.tedge[q];
@@ -1282,9 +1153,9 @@ cudaError_t launch_adjoint(const GeoView& g, const TabView* green, const TabView
       default: k_adjoint_near_rev<7><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk); break;
     }
   } else if (g.m <= 4) {
-    k_adjoint_near<false, 4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    k_adjoint_near<4><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   } else {
-    k_adjoint_near<false, 8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
+    k_adjoint_near<8><<<nblk, 128, 0, s>>>(g, te, t, A, k, eta, bw, gz, ldg, dtri, dk);
   }
   k_adjoint_gather<<<(g.nt + 127) / 128, 128, 0, s>>>(g.nt, g.tvert, dtri, dxyz);
   return cudaGetLastError();
