@@ -798,13 +798,18 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
   if (nt >= 8192) nthr = (int)std::min<unsigned>(std::max(std::thread::hardware_concurrency(), 1u), 16u);
   std::vector<std::vector<int32_t>> part_idx(nthr);
   std::vector<std::vector<int64_t>> part_cnt(nthr);
+  std::vector<char> part_failed(nthr, 0);
   {
     std::vector<std::thread> pool;
     auto chunk = [&](int w) {
-      const int64_t p0 = nt * w / nthr, p1 = nt * (w + 1) / nthr;
-      part_cnt[w].reserve(p1 - p0);
-      part_idx[w].reserve(16 * (size_t)(p1 - p0));
-      build_rows(p0, p1, part_idx[w], part_cnt[w]);
+      try {  // (no exception may leave a thread)
+        const int64_t p0 = nt * w / nthr, p1 = nt * (w + 1) / nthr;
+        part_cnt[w].reserve(p1 - p0);
+        part_idx[w].reserve(16 * (size_t)(p1 - p0));
+        build_rows(p0, p1, part_idx[w], part_cnt[w]);
+      } catch (...) {
+        part_failed[w] = 1;
+      }
     };
     for (int w = 1; w < nthr; ++w) {
       try {
@@ -819,6 +824,8 @@ gf_status gf_mesh_create(const double* xyz, int64_t nv, const int32_t* tri, int6
       else chunk(w);
     }
   }
+  for (int w = 0; w < nthr; ++w)
+    if (part_failed[w]) return fail(GF_ERR_ALLOC, "gf_mesh_create: out of host memory (near rows)");
   m->near_ptr.assign(nt + 1, 0);
   size_t total = 0;
   for (int w = 0; w < nthr; ++w) total += part_idx[w].size();
