@@ -67,9 +67,9 @@ RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 # pair of the cube's smaller case (the kernel's DRAM traffic is the
 # read-modify-write of Z through the row atomics and the mirror-free half, and
 # Z grows with the pair count).
-TRAFFIC_HASH = "2ebc2719d3f69dff"
-TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1966764544 + 2390544384, 75331278),
-           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298452224 + 283401984, 13073950)}
+TRAFFIC_HASH = "a55c453e0485f63c"
+TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1966432768 + 2392417792, 75331278),
+           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298641152 + 283526656, 13073950)}
 TRAFFIC_SCALED_FROM = {"cube_3lambda_49152tri_73728rwg_4pt_fp32": "cube_3lambda_12288tri_18432rwg_4pt_fp32"}
 TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
                 "(ncu, --clock-control none); the 73728-unknown cube's from the 18432-unknown cube's capture scaled "
@@ -91,7 +91,7 @@ def kernel_traffic(workload, n_pairs):
 # FP64 arithmetic instructions (DADD + DFMA + DMUL, thread level) per (near pair,
 # test point) of the mixed-precision near kernel, from an ncu capture of the
 # 18432-unknown cube (profiles/); valid while the near kernel's sources match.
-NEAR_FP64_OPS_HASH = "c1e2fb1ff6a5b3d7"
+NEAR_FP64_OPS_HASH = "97ed97d47b14818e"
 NEAR_FP64_OPS_PER_TASK = (59829840 + 165940896 + 64555955) / (332388 * 4)  # 218.4
 FP64_OPS_PER_SM_CLOCK = 2  # GB300: 304 DFMA thread instructions per clock on 152 SMs (ncu peak_sustained)
 
@@ -581,8 +581,8 @@ def run_ours(args, wl, rank, world, local_rank):
             piece = max(1, (256 << 20) // Z.element_size())
 
             def streamed(n):
-                """n steps; the copies run on a host thread that keeps one 256 MiB
-                piece in flight, so that the next step's host-to-device uploads
+                """n steps; the copies run on a host thread that keeps two 256 MiB
+                pieces queued, so that the next step's host-to-device uploads
                 (mesh, tables) are not queued behind a whole Z of copies."""
                 import queue
                 jobs, copied, keep = queue.Queue(), [threading.Event() for _ in range(n)], []
@@ -598,9 +598,16 @@ def run_ours(args, wl, rank, world, local_rank):
                             i, zsrc, filled = job
                             filled.synchronize()
                             with torch.cuda.stream(copy_stream):
+                                inflight = []
                                 for c0 in range(0, zsrc.numel(), piece):
                                     zhost_flat[c0:c0 + piece].copy_(zsrc[c0:c0 + piece], non_blocking=True)
-                                    copy_stream.synchronize()
+                                    ev = torch.cuda.Event()
+                                    ev.record(copy_stream)
+                                    inflight.append(ev)
+                                    if len(inflight) == 2:  # two pieces queued: no gap between them
+                                        inflight.pop(0).synchronize()
+                                for ev in inflight:
+                                    ev.synchronize()
                             copied[i].set()
                     except Exception as exc:  # noqa: BLE001 - reported by the main thread
                         failed.append(exc)
