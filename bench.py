@@ -180,16 +180,6 @@ def smem_model(evals, ms, mhz):
                     "expected largest bank-group load per 128-byte phase)"}
 
 
-def regular_ops_per_pair(m):
-    """FP32 lane operations of the algorithm per evaluated regular triangle
-    pair (each unordered pair {p, q} is evaluated once and its 3 x 3 block is
-    written to Z[m][n] and Z[n][m]): 28 per Green evaluation (distance 7,
-    table lookup + cubic 11, weight 2, moment sums 8), 92 per test point
-    (offset 3, 16 compensated moment updates 80, weighted offsets 3,
-    alpha . S_beta 6), 250 for the 3 x 3 RWG block and its two scatters."""
-    return 28 * m * m + 92 * m + 250
-
-
 def evaluated_pairs(nt, n_near):
     """Unordered regular triangle pairs: (ordered regular pairs) / 2."""
     return (nt * nt - n_near) // 2
@@ -913,7 +903,7 @@ def run_batch(args, rank, world, local_rank):
     pk, src = peaks()
     sm_mhz = float(pk.get("sm_max_mhz", FALLBACK_SM_MHZ))
     peak_tops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = n_regular * regular_ops_per_pair(rule) / (ms / 1e3) / 1e12
+    achieved = n_regular * rule * rule * OPS_PER_EVAL / (ms / 1e3) / 1e12
     line = {
         "metric": "Z entries/s (table fill)", "value": entries / (ms / 1e3), "unit": "Z entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -935,7 +925,9 @@ def run_batch(args, rank, world, local_rank):
                              "note": "one table in u = kR shared by all meshes (gf_table_create_kr)"},
         "roofline": {"kernel": "batched graph (regular + mirrors + near)", "bound": "alu", "achieved": achieved,
                      "peak": peak_tops, "unit": "Tops/s (FP32 lane ops, regular pairs only, whole graph time)",
-                     "frac": achieved / peak_tops, "traffic": None},
+                     "frac": achieved / peak_tops, "traffic": None,
+                     "op_model": f"{OPS_PER_EVAL} FP32 lane operations per regular Green evaluation, as for "
+                                 "the single fill"},
         "clocks": clocks,
         "e2e": {"value": None, "reason": "batched workload: fill-only; see setup_s"},
         # per graph launch: the regular kernel, the mirror pass over every Z, the near kernel
