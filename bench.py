@@ -70,10 +70,29 @@ RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 TRAFFIC_HASH = "a55c453e0485f63c"
 TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1966432768 + 2392417792, 75331278),
            "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298641152 + 283526656, 13073950)}
+# The table kernel's instruction issue from the same `--set full` capture of
+# the 18432-unknown cube (warp instructions per warp evaluation, fraction of
+# cycles with an instruction issued): the kernel is issue-bound, and the
+# 25-operation model above counts about a quarter of the instructions it needs.
+ISSUE = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (3.869e9 / (75331278 * 16 / 32), 0.781)}
 TRAFFIC_SCALED_FROM = {"cube_3lambda_49152tri_73728rwg_4pt_fp32": "cube_3lambda_12288tri_18432rwg_4pt_fp32"}
 TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
                 "(ncu, --clock-control none); the 73728-unknown cube's from the 18432-unknown cube's capture scaled "
                 "by the pair count; null when the kernel sources changed since the capture")
+
+
+def kernel_issue(workload):
+    """Instruction issue of the table kernel from the ncu capture (the same
+    kernel at a quarter of the size for the 73728-unknown cube), or None when
+    the kernel sources changed since."""
+    if kernel_source_hash() != TRAFFIC_HASH:
+        return None
+    src = workload if workload in ISSUE else TRAFFIC_SCALED_FROM.get(workload)
+    if src not in ISSUE:
+        return None
+    per_eval, active = ISSUE[src]
+    return {"warp_instructions_per_warp_eval": per_eval, "issue_active": active,
+            "source": "ncu --set full of the 18432-unknown cube's table kernel (smsp__inst_executed, issue active)"}
 
 
 def kernel_traffic(workload, n_pairs):
@@ -723,7 +742,8 @@ def run_ours(args, wl, rank, world, local_rank):
                      "traffic_note": TRAFFIC_NOTE,
                      "mufu_frac": evals_regular / (reg_ms / 1e3) / (SM_COUNT * MUFU_PER_SM * sm_mhz * 1e6),
                      "hbm_frac_z": zbytes / (reg_ms / 1e3) / (float(pk.get("hbm_gbs", 6800.0)) * 1e9),
-                     "smem": smem_model(evals_regular, reg_ms, sm_mhz)},
+                     "smem": smem_model(evals_regular, reg_ms, sm_mhz),
+                     "issue": kernel_issue(wl.name)},
         "clocks": clocks,
         "e2e": e2e,
         "other_kernels": other_kernel_rooflines(wl.name, zbytes, statistics.mean(tt["mirror_ms"]),
