@@ -110,8 +110,8 @@ def kernel_traffic(workload, n_pairs):
 # FP64 arithmetic instructions (DADD + DFMA + DMUL, thread level) per (near pair,
 # test point) of the mixed-precision near kernel, from an ncu capture of the
 # 18432-unknown cube (profiles/); valid while the near kernel's sources match.
-NEAR_FP64_OPS_HASH = "97ed97d47b14818e"
-NEAR_FP64_OPS_PER_TASK = (59829840 + 165940896 + 64555955) / (332388 * 4)  # 218.4
+NEAR_FP64_OPS_HASH = "dfbefd861ef0f73f"
+NEAR_FP64_OPS_PER_TASK = (59829840 + 165940896 + 64560827) / (332388 * 4)  # 218.4
 FP64_OPS_PER_SM_CLOCK = 2  # GB300: 304 DFMA thread instructions per clock on 152 SMs (ncu peak_sustained)
 
 

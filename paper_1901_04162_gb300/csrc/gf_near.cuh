@@ -24,6 +24,12 @@ struct C2f {  // FP32 complex of the mixed-precision near-block assembly
   float re, im;
 };
 
+// Sign tests of FP64 values on their bits (integer compares; a DSETP takes an
+// FP64 pipe slot): x > 0 and x >= 0 for finite x (-0 counts as negative in
+// nonneg, which the callers' formulas for both signs agree on at zero).
+__device__ __forceinline__ bool pos64(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool nonneg64(double x) { return __double_as_longlong(x) >= 0; }
+
 struct KScal {  // per-wavenumber scalars of the near-pair fill
   double k, scale, inv_k2, inv_k;
   float q4f;      // 4 / k^2 in FP32 (the mixed-precision block assembly)
@@ -84,8 +90,8 @@ __device__ void inner_integrals64(const double r[3], const double v[3][3], const
     if (fabs(P0) > 1e-12 * len) {
       const double aP = fabs(P0), iaP = 1.0 / aP;
       // e^{asinh(l / aP)} = (l + rho) / aP, for l < 0 as aP / (rho - l)
-      const double Em = lm >= 0 ? (lm + rv[e]) * iaP : aP / (rv[e] - lm);
-      const double Ep = lp >= 0 ? (lp + rv[en]) * iaP : aP / (rv[en] - lp);
+      const double Em = nonneg64(lm) ? (lm + rv[e]) * iaP : aP / (rv[e] - lm);
+      const double Ep = nonneg64(lp) ? (lp + rv[en]) * iaP : aP / (rv[en] - lp);
       const double um = log(Em), up = log(Ep);
       const double half = 0.5 * (up - um);
       const double Emid = sqrt(Em * Ep), iEmid = 1.0 / Emid;  // e^{+-mid}
@@ -111,7 +117,7 @@ __device__ void inner_integrals64(const double r[3], const double v[3][3], const
           ci += (ed.im - eR.im) * wt;
         }
       }
-      const double sg = P0 > 0 ? half : -half;
+      const double sg = pos64(P0) ? half : -half;
       sre += cr * sg;
       sim += ci * sg;
     }
@@ -135,10 +141,10 @@ __device__ void inner_integrals64(const double r[3], const double v[3][3], const
     const double R02 = P0 * P0 + d * d;
     const double Rm = Rv[e], Rp = Rv[en];
     double st = 0.5 * (lp * Rp - lm * Rm);
-    if (R02 > 0) {
+    if (pos64(R02)) {
       double ratio;
-      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
-      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
+      if (nonneg64(lm)) ratio = (lp + Rp) / (lm + Rm);
+      else if (nonneg64(lp)) ratio = (lp + Rp) * (Rm - lm) / R02;
       else ratio = (Rm - lm) / (Rp - lp);
       st += 0.5 * R02 * log(ratio);
     }
@@ -231,7 +237,7 @@ __device__ __forceinline__ void inner_integrals_mixed(const double r[3], const d
         cr = fmaf(ed.x - eR.x, wt, cr);
         ci = fmaf(ed.y - eR.y, wt, ci);
       }
-      const float sg = P0 > 0 ? half : -half;
+      const float sg = pos64(P0) ? half : -half;
       sre = fmaf(cr, sg, sre);
       sim = fmaf(ci, sg, sim);
     }
@@ -266,10 +272,10 @@ __device__ __forceinline__ void inner_integrals_mixed(const double r[3], const d
     const double R02 = P0 * P0 + d * d;
     const double Rm = e == 0 ? Rv0 : (e == 1 ? Rv1 : Rv2), Rp = e == 0 ? Rv1 : (e == 1 ? Rv2 : Rv0);
     double st = 0.5 * (lp * Rp - lm * Rm);
-    if (R02 > 0) {
+    if (pos64(R02)) {
       double ratio;
-      if (lm >= 0) ratio = (lp + Rp) / (lm + Rm);
-      else if (lp >= 0) ratio = (lp + Rp) * (Rm - lm) / R02;
+      if (nonneg64(lm)) ratio = (lp + Rp) / (lm + Rm);
+      else if (nonneg64(lp)) ratio = (lp + Rp) * (Rm - lm) / R02;
       else ratio = (Rm - lm) / (Rp - lp);
       st += 0.5 * R02 * log(ratio);
     }
