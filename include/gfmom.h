@@ -192,7 +192,15 @@ gf_status gf_table_destroy(gf_table* t);
  * cover the range of gf_range for this mesh and rule; distances outside it
  * fall back to direct evaluation in the near-pair path). precision GF_FP32
  * (complex64 Z) or GF_FP64 (complex128 Z). Z is overwritten. Asynchronous on
- * `stream`. */
+ * `stream`. An FP32 fill with a table (green_from_exp = 0) keeps, in the
+ * mesh, a list of the point pairs whose Green lattice cell holds samples
+ * (corrected by a second kernel), sized from the table's share of such cells
+ * (at most 1 GiB) and allocated by the first fill that needs it (cudaMalloc,
+ * which synchronizes the device). So fills of one mesh must not overlap on
+ * different streams. The environment variable GF_FIX_ENTRIES, if set,
+ * replaces that size (0: no list, each pair corrected in the pair kernel; a
+ * list too small for some CTA makes that CTA scan its pairs again): the
+ * results are the same either way. */
 gf_status gf_fill(const gf_mesh* m, double k, const gf_params* p, const gf_table* table,
                   int precision, void* Z_dev, int64_t ldz, void* stream);
 

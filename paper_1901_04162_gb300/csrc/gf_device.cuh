@@ -493,9 +493,9 @@ __device__ __forceinline__ void sincos_kr(const SplitR& r, float kpi, float kpi_
 
 
 
-template <int M, int MODE, bool KR = false, bool SM = false, class Sink = DenseUpper>
-__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p, int q,
-                                               bool ok, const Sink& sink);
+template <int M, int MODE, bool KR = false, bool SM = false, bool QUEUE = false, class Sink = DenseUpper>
+__device__ __forceinline__ unsigned long long regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p,
+                                                             int q, bool ok, const Sink& sink);
 
 // No pair of the blocks of p and q0 is near when their centres are farther
 // apart than the two vertex radii plus the centroid criterion (then no two
@@ -508,10 +508,12 @@ __device__ __forceinline__ bool blocks_apart(const GeoView& g, int p, int q0) {
 }
 
 // One warp task: test triangle p, source triangles q0 .. q0 + 31 (q0 a
-// multiple of 32, one block).
-template <int M, int MODE, bool KR, bool SM, class Sink>
-__device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T, const RegK& K, const Sink& sink,
-                                               int p, int q0, int lane) {
+// multiple of 32, one block). QUEUE: returns the lane's flagged point pairs
+// (bit a M + b: the lattice cell of that distance holds samples) instead of
+// correcting them; the caller lists them for fix_entry32.
+template <int M, int MODE, bool KR, bool SM, bool QUEUE = false, class Sink>
+__device__ __forceinline__ unsigned long long regular_task32(const GeoView& g, const Tab32& T, const RegK& K,
+                                                             const Sink& sink, int p, int q0, int lane) {
   const int q = min(q0 + lane, g.nt - 1);
   bool ok = (q0 + lane < g.nt) && q > p;
   if (!blocks_apart(g, p, q0)) {
@@ -519,7 +521,78 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
     const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
     ok = ok && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
   }
-  regular_pair32<M, MODE, KR, SM>(g, T, K, p, q, ok, sink);
+  return regular_pair32<M, MODE, KR, SM, QUEUE>(g, T, K, p, q, ok, sink);
+}
+
+// The 3x3 block of pair (p, q) from its moments (packed complex pairs), handed
+// to `sink`: Z(e_i, e_j) += j scale s_i l_i s_j l_j [X_j + delta_i . Y_j / 4]
+// with X_j = (Mab + eps'_j . Ma) / 4 - M0 / k^2 and Y_j = Mb + eps'_j M0.
+template <class Sink>
+__device__ __forceinline__ void pair_block32(const GeoView& g, const RegK& K, int p, int q, f2x M0, const f2x* Ma,
+                                             const f2x* Mb, f2x Mab, const Sink& sink) {
+  const int4 ep = g.tedge[p], eq = g.tedge[q];
+  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
+  // (packed pairs: both parts of each complex number in one instruction)
+  const f2x m0k = mul2(M0, pk2(-K.inv_k2, -K.inv_k2));
+  f2x xj[3], yj[3][3];
+  float sl[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float4 gq = g.geob32[3 * (size_t)q + j];  // eps'_j, s_j l_j
+    const float e[3] = {gq.x, gq.y, gq.z};
+    f2x er = Mab;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const f2x ec = pk2(e[c], e[c]);
+      er = fma2(ec, Ma[c], er);
+      yj[j][c] = fma2(ec, M0, Mb[c]);
+    }
+    xj[j] = fma2(pk2(0.25f, 0.25f), er, m0k);
+    sl[j] = gq.w;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!edge_valid(ecp[i])) continue;
+    const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
+    const f2x d0 = pk2(0.25f * gp.x, 0.25f * gp.x), d1 = pk2(0.25f * gp.y, 0.25f * gp.y),
+              d2 = pk2(0.25f * gp.z, 0.25f * gp.z);
+    const float ci = K.scale * gp.w;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (!edge_valid(ecq[j])) continue;
+      const float2 bz = up2(fma2(d0, yj[j][0], fma2(d1, yj[j][1], fma2(d2, yj[j][2], xj[j]))));
+      const float c = ci * sl[j];
+      // j * c * (br + j bi) = c * (-bi + j br)
+      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bz.y, c * bz.x));
+    }
+  }
+}
+
+// Point pair (test point a of p, source point b of q) whose lattice cell holds
+// samples: the exact table value minus the cell polynomial the loop used (the
+// same float operations for R as the loop), times the weights: the increment
+// d of M0 (those of Ma, Mb, Mab are d alpha, d beta, d alpha.beta; everything
+// is linear in the Green value). al, rb: the two points (offsets, weights).
+template <int M, int MODE, bool KR, bool SM>
+__device__ __forceinline__ f2x flagged_value32(const GeoView& g, const Tab32& T, const BlockSep& bs, int p, int q,
+                                               int a, int b, float4* al_out, float4* rb_out) {
+  const float4 ra = g.rel32[(size_t)a * g.nt + p];
+  const float4 al = g.pts32[(size_t)a * g.nt + p];
+  const float4 rb = g.rel32[(size_t)b * g.nt + q];
+  const float Aa = fmaf(2.f * bs.bx, ra.x, fmaf(2.f * bs.by, ra.y, fmaf(2.f * bs.bz, ra.z,
+                                                                            fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, ra.z * ra.z)))));
+  const float bqb = fmaf(rb.x, rb.x - 2.f * bs.bx, fmaf(rb.y, rb.y - 2.f * bs.by, rb.z * (rb.z - 2.f * bs.bz)));
+  const SplitR R = split_r(bs, Aa + bqb, -2.f * ra.x, -2.f * ra.y, -2.f * ra.z, rb.x, rb.y, rb.z);
+  float xh, xl;
+  table_x<KR>(T, R, &xh, &xl);
+  constexpr int D = MODE == kLagrange ? 3 : 1;
+  bool busy;
+  const float2 fa = lat_fast<D, SM>(T, xh, xl, &busy);
+  const float2 fe = busy ? lookup32_slow<D>(T, xh, xl) : fa;
+  const float w = al.w * (MODE == kLagrange ? rb.w : rb.w * R.rs);
+  *al_out = al;
+  *rb_out = rb;
+  return pk2((fe.x - fa.x) * w, (fe.y - fa.y) * w);
 }
 
 // The 3x3 block of regular pair (p, q) (q per lane; lanes with ok == false
@@ -527,11 +600,13 @@ __device__ __forceinline__ void regular_task32(const GeoView& g, const Tab32& T,
 // points enter through their offsets r_b from q's block centre (rel32): the
 // source moments are taken about that centre, and the block formula uses
 // eps'_j = C_b(q) - v_j (geob32) in place of eps_j = c_q - v_j (the same sums:
-// r_b + eps'_j = beta_b + eps_j).
-template <int M, int MODE, bool KR, bool SM, class Sink>
-__device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p, int q,
-                                               bool ok, const Sink& sink) {
-  if (!__any_sync(0xffffffffu, ok)) return;
+// r_b + eps'_j = beta_b + eps_j). Point pairs in lattice cells holding
+// samples are corrected here after the loop, or (QUEUE) returned as a bit
+// mask (bit a M + b) for the caller to list.
+template <int M, int MODE, bool KR, bool SM, bool QUEUE, class Sink>
+__device__ __forceinline__ unsigned long long regular_pair32(const GeoView& g, const Tab32& T, const RegK& K, int p,
+                                                             int q, bool ok, const Sink& sink) {
+  if (!__any_sync(0xffffffffu, ok)) return 0ull;
   const BlockSep bs = block_sep(g, p, q);
   // w_b r_b kept in registers for small rules in the kernels of 256-thread
   // CTAs; SM (the lattice in shared memory, or in direct mode one wide CTA per
@@ -634,29 +709,15 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
     }
     Mab.add(xab);
   }
-  if (MODE != kDirect && __any_sync(0xffffffffu, emask != 0)) {
+  if (!QUEUE && MODE != kDirect && __any_sync(0xffffffffu, emask != 0)) {
     // exact values where the lattice cell holds samples: add (exact - cell
-    // polynomial) to the moments of those point pairs only, with the same
-    // float operations for R as the loop above
+    // polynomial) to the moments of those point pairs only
     while (emask) {
       const int bit = sizeof(Mask) == 4 ? __ffs((int)emask) - 1 : __ffsll((long long)emask) - 1;
       emask &= emask - 1;
       const int a = bit / M, b = bit - M * (bit / M);
-      const float4 ra = g.rel32[(size_t)a * g.nt + p];
-      const float4 al = g.pts32[(size_t)a * g.nt + p];
-      const float4 rb = g.rel32[(size_t)b * g.nt + q];
-      const float Aa = fmaf(2.f * bs.bx, ra.x, fmaf(2.f * bs.by, ra.y, fmaf(2.f * bs.bz, ra.z,
-                                                                                fmaf(ra.x, ra.x, fmaf(ra.y, ra.y, ra.z * ra.z)))));
-      const float bqb = fmaf(rb.x, rb.x - 2.f * bs.bx, fmaf(rb.y, rb.y - 2.f * bs.by, rb.z * (rb.z - 2.f * bs.bz)));
-      const SplitR R = split_r(bs, Aa + bqb, -2.f * ra.x, -2.f * ra.y, -2.f * ra.z, rb.x, rb.y, rb.z);
-      float xh, xl;
-      table_x<KR>(T, R, &xh, &xl);
-      constexpr int D = MODE == kLagrange ? 3 : 1;
-      bool busy;
-      const float2 fa = lat_fast<D, SM>(T, xh, xl, &busy);
-      const float2 fe = busy ? lookup32_slow<D>(T, xh, xl) : fa;
-      const float w = al.w * (MODE == kLagrange ? rb.w : rb.w * R.rs);
-      const f2x d = pk2((fe.x - fa.x) * w, (fe.y - fa.y) * w);
+      float4 al, rb;
+      const f2x d = flagged_value32<M, MODE, KR, SM>(g, T, bs, p, q, a, b, &al, &rb);
       M0.add(d);
       const float alv[3] = {al.x, al.y, al.z}, rbv[3] = {rb.x, rb.y, rb.z};
 #pragma unroll
@@ -668,45 +729,58 @@ __device__ __forceinline__ void regular_pair32(const GeoView& g, const Tab32& T,
       Mab.add(mul2(d, pk2(ab, ab)));
     }
   }
+  if (!ok) return 0ull;
+  const f2x ma[3] = {Ma[0].s, Ma[1].s, Ma[2].s}, mb[3] = {Mb[0].s, Mb[1].s, Mb[2].s};
+  pair_block32(g, K, p, q, M0.s, ma, mb, Mab.s, sink);
+  return QUEUE ? (unsigned long long)emask : 0ull;
+}
+
+// The 3x3 block of one flagged point pair's correction d (exact - cell
+// value, times the weights): moments d, d alpha, d beta, d alpha.beta.
+template <class Sink>
+__device__ __forceinline__ void fix_block32(const GeoView& g, const RegK& K, int p, int q, f2x d, float4 al,
+                                            float4 rb, const Sink& sink) {
+  const f2x ma[3] = {mul2(d, pk2(al.x, al.x)), mul2(d, pk2(al.y, al.y)), mul2(d, pk2(al.z, al.z))};
+  const f2x mb[3] = {mul2(d, pk2(rb.x, rb.x)), mul2(d, pk2(rb.y, rb.y)), mul2(d, pk2(rb.z, rb.z))};
+  const float ab = al.x * rb.x + al.y * rb.y + al.z * rb.z;
+  pair_block32(g, K, p, q, d, ma, mb, mul2(d, pk2(ab, ab)), sink);
+}
+
+// Flagged point pairs of the QUEUE kernels: entries (p, q << 6 | a M + b) in
+// per-CTA lists (GeoView::fix), corrected by a second kernel with every
+// thread busy, each as a pair block of its own added to Z (the loop's moments
+// are left as they are: everything is linear in the Green value).
+template <int M, int MODE, bool KR, bool SM, class Sink>
+__device__ __forceinline__ void fix_entry32(const GeoView& g, const Tab32& T, const RegK& K, const Sink& sink,
+                                            int2 e) {
+  const int p = e.x, q = e.y >> 6, bit = e.y & 63;
+  const int a = bit / M, b = bit - M * (bit / M);
+  const BlockSep bs = block_sep(g, p, q);
+  float4 al, rb;
+  const f2x d = flagged_value32<M, MODE, KR, SM>(g, T, bs, p, q, a, b, &al, &rb);
+  fix_block32(g, K, p, q, d, al, rb, sink);
+}
+
+// The tasks of a CTA whose list overflowed are scanned again: every point
+// pair's distance and cell as in the loop, the flagged ones corrected at once.
+template <int M, int MODE, bool KR, bool SM, class Sink>
+__device__ __forceinline__ void fix_rescan32(const GeoView& g, const Tab32& T, const RegK& K, const Sink& sink,
+                                             int p, int q0, int lane) {
+  const int q = min(q0 + lane, g.nt - 1);
+  bool ok = (q0 + lane < g.nt) && q > p;
+  if (!blocks_apart(g, p, q0)) {
+    const float4 cp = g.cen32[p], cq = g.cen32[q];
+    const float3 dc = make_float3(cp.x - cq.x, cp.y - cq.y, cp.z - cq.z);
+    ok = ok && !pair_is_near(g, p, q, g.tvert[p], g.tvert[q], dc);
+  }
   if (!ok) return;
-  // 3x3 block: Z(e_i, e_j) += j scale s_i l_i s_j l_j [X_j + delta_i . Y_j / 4] with
-  // X_j = (Mab + eps'_j . Ma) / 4 - M0 / k^2 and Y_j = Mb + eps'_j M0
-  const int4 ep = g.tedge[p], eq = g.tedge[q];
-  const int ecp[3] = {ep.x, ep.y, ep.z}, ecq[3] = {eq.x, eq.y, eq.z};
-  // (packed pairs: both parts of each complex number in one instruction)
-  const f2x m0k = mul2(M0.s, pk2(-K.inv_k2, -K.inv_k2));
-  f2x xj[3], yj[3][3];
-  float sl[3];
-#pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const float4 gq = g.geob32[3 * (size_t)q + j];  // eps'_j, s_j l_j
-    const float e[3] = {gq.x, gq.y, gq.z};
-    f2x er = Mab.s;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const f2x ec = pk2(e[c], e[c]);
-      er = fma2(ec, Ma[c].s, er);
-      yj[j][c] = fma2(ec, M0.s, Mb[c].s);
+  const BlockSep bs = block_sep(g, p, q);
+  for (int a = 0; a < M; ++a)
+    for (int b = 0; b < M; ++b) {
+      float4 al, rb;
+      const f2x d = flagged_value32<M, MODE, KR, SM>(g, T, bs, p, q, a, b, &al, &rb);
+      if (d != 0ull) fix_block32(g, K, p, q, d, al, rb, sink);
     }
-    xj[j] = fma2(pk2(0.25f, 0.25f), er, m0k);
-    sl[j] = gq.w;
-  }
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    if (!edge_valid(ecp[i])) continue;
-    const float4 gp = g.geo32[3 * (size_t)p + i];  // delta_i, s_i l_i
-    const f2x d0 = pk2(0.25f * gp.x, 0.25f * gp.x), d1 = pk2(0.25f * gp.y, 0.25f * gp.y),
-              d2 = pk2(0.25f * gp.z, 0.25f * gp.z);
-    const float ci = K.scale * gp.w;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (!edge_valid(ecq[j])) continue;
-      const float2 bz = up2(fma2(d0, yj[j][0], fma2(d1, yj[j][1], fma2(d2, yj[j][2], xj[j]))));
-      const float c = ci * sl[j];
-      // j * c * (br + j bi) = c * (-bi + j br)
-      sink(edge_of(ecp[i]), edge_of(ecq[j]), make_float2(-c * bz.y, c * bz.x));
-    }
-  }
 }
 
 inline int sm_count() {

@@ -105,45 +105,6 @@ __device__ void dev_table_values(int j, int kind, double k, const double* __rest
   fval[2 * j + 1] = im;
 }
 
-// Coefficients of the interpolant on interval j as a polynomial in u = x - x0:
-// linear (Eq. 4) or the Lagrange form (Eq. 5) on the stencil s0..s0+deg,
-// expanded by multiplying out prod_{m != i} (u - (r_m - x0)) / (r_i - r_m).
-__device__ void interval_poly(int deg, int n, const double* __restrict__ r, const double* __restrict__ f, int j,
-                              double x0, double cre[4], double cim[4]) {
-  for (int p = 0; p < 4; ++p) cre[p] = cim[p] = 0.0;
-  if (deg <= 1) {
-    double h = r[j + 1] - r[j];
-    double sre = (f[2 * j + 2] - f[2 * j]) / h, sim = (f[2 * j + 3] - f[2 * j + 1]) / h;
-    double u0 = x0 - r[j];
-    cre[0] = f[2 * j] + sre * u0;
-    cim[0] = f[2 * j + 1] + sim * u0;
-    cre[1] = sre;
-    cim[1] = sim;
-    return;
-  }
-  int s0 = j - (deg - 1) / 2;
-  if (s0 > n - 1 - deg) s0 = n - 1 - deg;
-  if (s0 < 0) s0 = 0;
-  for (int i = s0; i <= s0 + deg; ++i) {
-    double poly[4] = {1.0, 0.0, 0.0, 0.0};
-    double den = 1.0;
-    int len = 1;
-    for (int mm = s0; mm <= s0 + deg; ++mm) {
-      if (mm == i) continue;
-      double e = r[mm] - x0;
-      for (int p = len; p >= 1; --p) poly[p] = poly[p - 1] - e * poly[p];
-      poly[0] = -e * poly[0];
-      ++len;
-      den *= (r[i] - r[mm]);
-    }
-    for (int p = 0; p < len; ++p) {
-      double b = poly[p] / den;
-      cre[p] += f[2 * i] * b;
-      cim[p] += f[2 * i + 1] * b;
-    }
-  }
-}
-
 __device__ void dev_table_coef(int j, int deg, int n, const double* __restrict__ r, const double* __restrict__ f,
                                double2* c64, float* node32, float4* c32a, float4* c32b) {
   float a32 = (float)r[j];

@@ -2,6 +2,7 @@
 // pairs), table sample placement (FP64), and the C-ABI entry points.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -418,6 +419,9 @@ void free_mesh_device(gf_mesh* m) {
   if (m->d_dtri) cudaFree(m->d_dtri);
   if (m->d_dk) cudaFree(m->d_dk);
   if (m->h_range) cudaFreeHost(m->h_range);
+  if (m->d_fix) cudaFree(m->d_fix);
+  m->d_fix = nullptr;
+  m->fix_cap = 0;
   m->d_dtri = nullptr;
   m->d_dk = nullptr;
   m->h_range = nullptr;
@@ -1062,6 +1066,10 @@ double green_deriv_bound(int n, double k, double r) {
 // Relative size (to |f| on the cell) below which the cubic term of the Green
 // table's cell polynomial is left out of the lattice record.
 constexpr double kDropC3 = 4e-8;
+// Largest difference (relative to |f| on the cell) between the Green
+// polynomials of the intervals a cell holding samples spans for which the
+// cell keeps the plain record of the interval at its middle.
+constexpr double kAgree = 1e-8;
 
 // Cells of width `step` (t or t / 2) from r_min (the uniform samples of Eq. 2,
 // and the refined ones for t / 2, sit on their ends). A cell is sample-free
@@ -1071,8 +1079,8 @@ constexpr double kDropC3 = 4e-8;
 // extrapolation by at most the margin. Cells holding samples get sub-cells
 // narrower than the local spacing, so each holds one sample at most and the
 // bracketing against the FP32 samples is exact.
-gf_status build_lattice(const std::vector<double>& r, double step, double t, int degree, double k,
-                        Lattice* L) {
+gf_status build_lattice(const std::vector<double>& r, const std::vector<int8_t>& zflag, double step, double t,
+                        int degree, double k, Lattice* L) {
   const size_t n = r.size();
   LatMap& M = L->map;
   M.lo = (float)r.front();
@@ -1097,6 +1105,48 @@ gf_status build_lattice(const std::vector<double>& r, double step, double t, int
     const double ci = std::floor(v + 0.5), d = v - ci;  // d in [-1/2, 1/2)
     const int64_t i = (int64_t)ci;
     if (std::fabs(d) < 0.5 - eps && i >= 0 && i < L->n) busy[i] = 1;
+  }
+  const double cell_w = 1.0 / (double)M.inv;
+  if (degree > 1) {
+    // A Green cell holding samples whose intervals' polynomials all agree
+    // with that of the interval at its middle within kAgree |f| over the cell
+    // (the refinement samples and forced zeros of Section II.B, at spacings
+    // where the interpolant is far more accurate than FP32) keeps that one
+    // record, as a sample-free cell does: its value then differs from the
+    // piecewise interpolant by less than FP32 resolves.
+    std::vector<double> f(2 * n);
+    for (size_t j = 0; j < n; ++j) {
+      const double re = std::cos(k * r[j]) / r[j], im = -std::sin(k * r[j]) / r[j];
+      f[2 * j] = zflag[j] == 1 ? 0.0 : re;
+      f[2 * j + 1] = zflag[j] == 2 ? 0.0 : im;
+    }
+    auto interval_at = [&](double x) {  // last sample <= x, as an interval index
+      const size_t u = (size_t)(std::upper_bound(r.begin(), r.end(), x) - r.begin());
+      return (int)std::min<size_t>(u == 0 ? 0 : u - 1, n - 2);
+    };
+    for (int i = 0; i < L->n; ++i) {
+      if (!busy[i]) continue;
+      const double mid = ((double)i + (double)c) * cell_w;
+      const double a = mid - 0.5005 * cell_w, b = mid + 0.5005 * cell_w;
+      const int jm = interval_at(mid), j0 = interval_at(a), j1 = interval_at(b);
+      double pm[2][4], pj[2][4], worst = 0.0;
+      interval_poly(degree, (int)n, r.data(), f.data(), jm, mid, pm[0], pm[1]);
+      for (int j = j0; j <= j1; ++j) {
+        if (j == jm) continue;
+        interval_poly(degree, (int)n, r.data(), f.data(), j, mid, pj[0], pj[1]);
+        const double xa = std::max(a, j == 0 ? a : r[j]), xb = std::min(b, j == (int)n - 2 ? b : r[j + 1]);
+        for (int q = 0; q <= 32 && xb > xa; ++q) {
+          const double u = xa + (xb - xa) * q / 32.0 - mid;
+          double dre = 0.0, dim = 0.0;
+          for (int e = 3; e >= 0; --e) {
+            dre = dre * u + (pj[0][e] - pm[0][e]);
+            dim = dim * u + (pj[1][e] - pm[1][e]);
+          }
+          worst = std::max(worst, std::hypot(dre, dim));
+        }
+      }
+      if (worst <= kAgree / b) busy[i] = 0;
+    }
   }
   L->c2d = 0.f;
   if (degree > 1) {
@@ -1130,7 +1180,6 @@ gf_status build_lattice(const std::vector<double>& r, double step, double t, int
   L->sub.clear();
   L->cmp.clear();
   size_t jm = 0;  // last sample <= the cell's middle (the middles increase with i)
-  const double cell_w = 1.0 / (double)M.inv;
   for (int i = 0; i < L->n; ++i) {
     const double mid = ((double)i + (double)c) * cell_w;
     while (jm + 1 < n && r[jm + 1] <= mid) ++jm;
@@ -1227,7 +1276,7 @@ gf_status gf_table_create(double k, double r_min, double r_max, const gf_params*
                              std::fabs(p->refine_factor - 0.5) < 1e-12
                          ? 0.5 * t
                          : t;
-    if ((st = build_lattice(o.r, h, t, o.degree, k, &lat[which]))) return st;
+    if ((st = build_lattice(o.r, o.zflag, h, t, o.degree, k, &lat[which]))) return st;
     o.n_lat = lat[which].n;
     o.n_busy = (int)lat[which].busy.size();
     o.n_sub = (int)lat[which].sub.size();
@@ -1501,6 +1550,23 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
   if (parts & GF_PART_ZERO)
     GF_CUDA(cudaMemset2DAsync(Z, (size_t)ldz * esz, 0, (size_t)m->ne * esz, (size_t)m->ne, s));
   GeoView g = geo_view_impl(m);
+  if ((parts & GF_PART_PAIRS) && table && precision == GF_FP32 && !p->green_from_exp) {
+    // list of the point pairs in Green lattice cells holding samples (grown
+    // on demand); GF_FIX_ENTRIES replaces its size (0: no list, the
+    // corrections in the pair kernel's loop; small: lists overflow and their
+    // CTAs scan their tasks again)
+    int64_t need = fix_entries(m->nt, p->rule, tg.n_busy, tg.n_lat);
+    if (const char* ev = std::getenv("GF_FIX_ENTRIES")) need = std::max<int64_t>(0, std::atoll(ev));
+    if (m->fix_cap < need) {
+      if (m->d_fix) cudaFree(m->d_fix);
+      m->d_fix = nullptr;
+      m->fix_cap = 0;
+      if (cudaMalloc((void**)&m->d_fix, (size_t)need * sizeof(int2)) == cudaSuccess) m->fix_cap = need;
+      else (void)cudaGetLastError();
+    }
+    g.fix = need > 0 ? m->d_fix : nullptr;
+    g.fix_cap = std::min(m->fix_cap, need);
+  }
   if (parts & GF_PART_PAIRS)
     GF_CUDA(launch_fill_regular(g, table ? (p->green_from_exp ? &te : &tg) : nullptr, p->green_from_exp != 0, gscale,
                                 precision, k, p->eta, Z, ldz, s));

@@ -66,7 +66,24 @@ struct GeoView {
   const float4* rel32;      // [m][nt]: point a minus its block's centre (FP32 of the FP64 difference), weight
   const float4* geob32;     // [nt][3]: block centre minus v_i (the vertex opposite local edge i), s_i l_i
   float bunit, bunit2;      // 2^e, 2^(2e)
+  // FP32 Green-table fills: list of the point pairs whose lattice cell holds
+  // samples (fix_cap entries with the per-CTA counts first; mesh scratch)
+  int2* fix = nullptr;
+  int64_t fix_cap = 0;
 };
+
+// Entries to reserve for the flagged point pairs of an FP32 Green-table fill:
+// the pair evaluations (nt^2 / 2 unordered pairs, m^2 point pairs each) times
+// three times the share of lattice cells holding samples, plus a floor, at
+// most kFixMaxBytes. A CTA whose share overflows scans its tasks again.
+constexpr int64_t kFixMaxBytes = int64_t(1) << 30;
+inline int64_t fix_entries(int64_t nt, int m, int64_t n_busy, int64_t n_lat) {
+  const double evals = 0.5 * (double)nt * (double)nt * (double)m * (double)m;
+  double f = n_lat > 0 ? 3.0 * (double)n_busy / (double)n_lat + 2e-4 : 1.0;
+  if (f > 1.0) f = 1.0;
+  const double want = evals * f + 65536.0, most = (double)(kFixMaxBytes / 8);
+  return (int64_t)(want < most ? want : most);
+}
 
 // FP64 cell record: every x in the cell lies in interval j0 if x < split,
 // else in j0 + 1 whose left sample is split; anchor = sample j0.
@@ -74,6 +91,47 @@ struct __align__(32) Cell64 {
   double split, anchor;
   int j0, pad;
 };
+
+// Coefficients of the interpolant on interval j (samples r, values f as
+// (re, im) pairs) as a polynomial in u = x - x0:
+// linear (Eq. 4) or the Lagrange form (Eq. 5) on the stencil s0..s0+deg,
+// expanded by multiplying out prod_{m != i} (u - (r_m - x0)) / (r_i - r_m).
+__host__ __device__ inline void interval_poly(int deg, int n, const double* __restrict__ r,
+                                              const double* __restrict__ f, int j, double x0, double cre[4],
+                                              double cim[4]) {
+  for (int p = 0; p < 4; ++p) cre[p] = cim[p] = 0.0;
+  if (deg <= 1) {
+    double h = r[j + 1] - r[j];
+    double sre = (f[2 * j + 2] - f[2 * j]) / h, sim = (f[2 * j + 3] - f[2 * j + 1]) / h;
+    double u0 = x0 - r[j];
+    cre[0] = f[2 * j] + sre * u0;
+    cim[0] = f[2 * j + 1] + sim * u0;
+    cre[1] = sre;
+    cim[1] = sim;
+    return;
+  }
+  int s0 = j - (deg - 1) / 2;
+  if (s0 > n - 1 - deg) s0 = n - 1 - deg;
+  if (s0 < 0) s0 = 0;
+  for (int i = s0; i <= s0 + deg; ++i) {
+    double poly[4] = {1.0, 0.0, 0.0, 0.0};
+    double den = 1.0;
+    int len = 1;
+    for (int mm = s0; mm <= s0 + deg; ++mm) {
+      if (mm == i) continue;
+      double e = r[mm] - x0;
+      for (int p = len; p >= 1; --p) poly[p] = poly[p - 1] - e * poly[p];
+      poly[0] = -e * poly[0];
+      ++len;
+      den *= (r[i] - r[mm]);
+    }
+    for (int p = 0; p < len; ++p) {
+      double b = poly[p] / den;
+      cre[p] += f[2 * i] * b;
+      cim[p] += f[2 * i + 1] * b;
+    }
+  }
+}
 
 // One interpolation table as the kernels see it.
 struct TabView {
@@ -312,6 +370,8 @@ struct gf_mesh {
   unsigned long long* h_range = nullptr;   // page-locked, device-mapped: r_min, r_max of the last gf_range
   float2* d_range_bpb = nullptr;          // range scratch: bounds per 32 x 32 block pair
   int32_t* d_range_list = nullptr;        // range scratch: block pairs that can hold an extreme, count last
+  int2* d_fix = nullptr;                   // FP32 Green-table fill scratch: flagged point pairs (grown on demand)
+  int64_t fix_cap = 0;
 };
 
 struct gf_table {

@@ -20,25 +20,79 @@ constexpr int smem_block() {
 // memory (one CTA per SM holds it), else read through L1. The direct kernel
 // for rules of up to 4 points runs the same CTA shape (one CTA of 896
 // threads per SM at 72 registers), which measured faster than three
-// 256-thread CTAs per SM.
+// 256-thread CTAs per SM. With the Green lattice in shared memory the point
+// pairs whose cell holds samples (rare: cells whose polynomials agree count
+// as sample-free) are listed (fix_cap entries per CTA after the counts,
+// kFixCounts of them, in g.fix) and k_fix_regular32 corrects them; the Exp
+// lattice (Exp x 1/R), where such pairs are common, corrects them in the loop.
+constexpr int kFixCounts = 4096;  // CTAs of one launch at most (count words, as 2048 int2)
+
 template <int M, int MODE, bool SMEM, bool KR>
 __global__ void __launch_bounds__((SMEM || (MODE == kDirect && M <= 4)) ? smem_block<M>() : kThreads, 1)
-    k_fill_regular32(GeoView g, TabView tv, RegK K,
-                                                                                      float2* Z, int64_t ldz) {
+    k_fill_regular32(GeoView g, TabView tv, RegK K, float2* Z, int64_t ldz, unsigned fix_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
+  constexpr bool kList = SMEM && MODE == kLagrange;
+  __shared__ unsigned fix_n, fix_over;
   Tab32 T = tab32(tv);
-  if (MODE != kDirect && SMEM) {
+  if (SMEM && MODE != kDirect) {
     stage_tab32(T, tv, MODE == kLagrange ? 3 : 1, smem);
+    if (threadIdx.x == 0) fix_n = fix_over = 0u;
     __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
+  const DenseUpper sink{Z, ldz};
+  int2* const list = kList ? g.fix + kFixCounts / 2 + (size_t)blockIdx.x * fix_cap : nullptr;
+  const int64_t ntask = regular_units(g.nt);
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
+    int p, q0;
+    if (!sym_task(task, g.nt, &p, &q0)) continue;
+    unsigned long long emask =
+        regular_task32<M, MODE, KR, SMEM || (MODE == kDirect && M <= 4), kList>(g, T, K, sink, p, q0, lane);
+    if (kList && emask) {
+      const unsigned nb = (unsigned)__popcll(emask);
+      unsigned slot = atomicAdd(&fix_n, nb);
+      if (slot + nb > fix_cap || slot + nb < slot) fix_over = 1u;
+      const int qv = (q0 + lane) << 6;
+      while (emask) {
+        const int bit = __ffsll((long long)emask) - 1;
+        emask &= emask - 1ull;
+        if (slot < fix_cap) list[slot] = make_int2(p, qv | bit);
+        ++slot;
+      }
+    }
+  }
+  if (kList) {
+    __syncthreads();
+    if (threadIdx.x == 0) reinterpret_cast<unsigned*>(g.fix)[blockIdx.x] = fix_over ? 0xFFFFFFFFu : fix_n;
+  }
+}
+
+// The corrections of k_fill_regular32's flagged point pairs, launched with
+// its grid and CTA shape: CTA b corrects list b (one entry per thread), or,
+// where that list overflowed, scans CTA b's tasks again. (As a kernel of its
+// own it adds nothing to the pair kernel's registers.)
+template <int M, int MODE, bool KR>
+__global__ void __launch_bounds__(smem_block<M>(), 1)
+    k_fix_regular32(GeoView g, TabView tv, RegK K, float2* Z, int64_t ldz, unsigned fix_cap) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned n = reinterpret_cast<const unsigned*>(g.fix)[blockIdx.x];
+  if (n == 0u) return;
+  Tab32 T = tab32(tv);
+  stage_tab32(T, tv, MODE == kLagrange ? 3 : 1, smem);
+  __syncthreads();
+  const DenseUpper sink{Z, ldz};
+  if (n != 0xFFFFFFFFu) {
+    const int2* list = g.fix + kFixCounts / 2 + (size_t)blockIdx.x * fix_cap;
+    for (unsigned i = threadIdx.x; i < n; i += blockDim.x) fix_entry32<M, MODE, KR, true>(g, T, K, sink, list[i]);
+    return;
   }
   const int lane = threadIdx.x & 31;
   const int64_t ntask = regular_units(g.nt);
   const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; task < ntask; task += nwarp) {
     int p, q0;
-    if (sym_task(task, g.nt, &p, &q0))
-      regular_task32<M, MODE, KR, (SMEM && MODE != kDirect) || (MODE == kDirect && M <= 4)>(g, T, K,
-                                                                                        DenseUpper{Z, ldz}, p, q0, lane);
+    if (sym_task(task, g.nt, &p, &q0)) fix_rescan32<M, MODE, KR, true>(g, T, K, sink, p, q0, lane);
   }
 }
 
@@ -231,14 +285,30 @@ cudaError_t launch_regular32_table(const TabView& tv, const GeoView& g, const Re
   int dev = 0, max_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (smem <= (size_t)max_optin) {
+  // (list entries pack q << 6: fewer than 2^25 triangles)
+  if (smem <= (size_t)max_optin && g.nt < (1 << 25)) {
     auto kern = k_fill_regular32<M, MODE, true, KR>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, smem_block<M>(), smem);
     int64_t blocks = std::min<int64_t>(pair_grid(g, 2 * std::max(per_sm, 1)), (int64_t)sm_count() * std::max(per_sm, 1));
-    kern<<<(unsigned)blocks, smem_block<M>(), smem, s>>>(g, tv, K, Z, ldz);
+    // the Green lattice's flagged-pair lists: each CTA's count, then its
+    // share of the entries (without the mesh's list, the table is read
+    // through L1 with the corrections in the loop)
+    blocks = std::min<int64_t>(blocks, kFixCounts);
+    if constexpr (MODE != kLagrange) {
+      kern<<<(unsigned)blocks, smem_block<M>(), smem, s>>>(g, tv, K, Z, ldz, 0u);
+    } else if (g.fix && g.fix_cap > kFixCounts / 2) {
+      const int64_t cap = std::min<int64_t>((g.fix_cap - kFixCounts / 2) / blocks, 0xFFFFFFFFll);
+      kern<<<(unsigned)blocks, smem_block<M>(), smem, s>>>(g, tv, K, Z, ldz, (unsigned)cap);
+      auto fix = k_fix_regular32<M, MODE, KR>;
+      e = cudaFuncSetAttribute(fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      fix<<<(unsigned)blocks, smem_block<M>(), smem, s>>>(g, tv, K, Z, ldz, (unsigned)cap);
+    } else {
+      k_fill_regular32<M, MODE, false, KR><<<(unsigned)pair_grid(g, 4), kThreads, 0, s>>>(g, tv, K, Z, ldz, 0u);
+    }
   } else if (MODE == kLagrange && g.bsph) {
     cudaError_t e =
         cudaFuncSetAttribute(k_fill_regular32_win<M, KR>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWinBytes);
@@ -246,7 +316,7 @@ cudaError_t launch_regular32_table(const TabView& tv, const GeoView& g, const Re
     k_fill_regular32_win<M, KR><<<(unsigned)sm_count(), 512, kWinBytes, s>>>(g, tv, g.bsph, K, Z, ldz);
   } else {
     int64_t blocks = pair_grid(g, 4);
-    k_fill_regular32<M, MODE, false, KR><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
+    k_fill_regular32<M, MODE, false, KR><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz, 0u);
   }
   return cudaGetLastError();
 }
@@ -257,10 +327,11 @@ cudaError_t launch_regular32(const GeoView& g, const TabView* table, bool from_e
   if (!table) {
     TabView tv{};
     if (M <= 4) {
-      k_fill_regular32<M, kDirect, false, false><<<(unsigned)sm_count(), smem_block<M>(), 0, s>>>(g, tv, K, Z, ldz);
+      k_fill_regular32<M, kDirect, false, false><<<(unsigned)sm_count(), smem_block<M>(), 0, s>>>(g, tv, K, Z, ldz,
+                                                                                                  0u);
     } else {
       int64_t blocks = pair_grid(g, 4);
-      k_fill_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz);
+      k_fill_regular32<M, kDirect, false, false><<<(unsigned)blocks, kThreads, 0, s>>>(g, tv, K, Z, ldz, 0u);
     }
     return cudaGetLastError();
   }

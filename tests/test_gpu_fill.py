@@ -65,6 +65,31 @@ def test_small_sphere_fp64_both_modes():
         assert rel_fro(z, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("rule", [4, 7])
+@pytest.mark.parametrize("entries", [None, "2100", "0"])
+def test_fp32_coarse_table_corrections_match_oracle(rule, entries, monkeypatch):
+    # A coarse Green table (tol 1e-2, 10 samples per wavelength): nearly every
+    # lattice cell holds samples whose polynomials disagree, or needs its
+    # cubic term, so nearly every point pair takes the exact correction, and
+    # a lost or wrong correction shows at the scale of the left-out cubic
+    # terms (1e-4 of Z), ten times the bound. entries: the flagged-pair list
+    # as sized for the table (corrections kernel); too small for any CTA
+    # (each scans its tasks again); none (corrections in the pair kernel).
+    if entries is not None:
+        monkeypatch.setenv("GF_FIX_ENTRIES", entries)
+    xyz, tri = W.octasphere(2, 1.0)
+    xyz = W.jitter(xyz, tri, 0.02, 3)
+    _, z, _ = gpu_fill(xyz, tri, K, rule, gf.GF_FP32, True, table_tol=1e-2, green_n_per_lambda=10)
+    om = O.Mesh(xyz, tri)
+    lo, hi = om.range(rule)
+    tabs = (O.Table(O.table_params(O.GREEN, K, lo, hi, tol=1e-2, n_per_lambda=10)),
+            O.Table(O.table_params(O.EXP, K, lo, hi, tol=1e-2)))
+    ref = om.z_full(K, rule, mode="table", tables=tabs)
+    direct = om.z_full(K, rule)
+    assert rel_fro(ref, direct) > 3e-5  # the coarse table's own error, which the corrections carry
+    assert rel_fro(z, ref) <= 1e-5 and rel_max(z, ref) <= 1e-5
+
+
 def test_green_from_exp_matches_oracle():
     # regular pairs through the linear Exp table times 1/R (green_from_exp = 1)
     # against the oracle's "exp_over_r" mode: FP64 plate element-wise at 1e-12,
