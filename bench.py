@@ -67,14 +67,14 @@ RANDOM_WAVEFRONTS = {16: 4 * 2.595, 8: 2 * 3.077, 4: 3.530}
 # pair of the cube's smaller case (the kernel's DRAM traffic is the
 # read-modify-write of Z through the row atomics and the mirror-free half, and
 # Z grows with the pair count).
-TRAFFIC_HASH = "a55c453e0485f63c"
-TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1966432768 + 2392417792, 75331278),
-           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298641152 + 283526656, 13073950)}
+TRAFFIC_HASH = "188d6d96b53f69c2"
+TRAFFIC = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (1906964736 + 1992500736, 75331278),
+           "sphere_r1lambda_5120tri_7680rwg_7pt_fp32": (298563584 + 260932608, 13073950)}
 # The table kernel's instruction issue from the same `--set full` capture of
 # the 18432-unknown cube (warp instructions per warp evaluation, fraction of
 # cycles with an instruction issued): the kernel is issue-bound, and the
-# 25-operation model above counts about a quarter of the instructions it needs.
-ISSUE = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (3.869e9 / (75331278 * 16 / 32), 0.781)}
+# 25-operation model above counts under a third of the instructions it needs.
+ISSUE = {"cube_3lambda_12288tri_18432rwg_4pt_fp32": (3.254e9 / (75331278 * 16 / 32), 0.746)}
 TRAFFIC_SCALED_FROM = {"cube_3lambda_49152tri_73728rwg_4pt_fp32": "cube_3lambda_12288tri_18432rwg_4pt_fp32"}
 TRAFFIC_NOTE = ("dram__bytes_read.sum + dram__bytes_write.sum of one launch of the regular-pair table kernel "
                 "(ncu, --clock-control none); the 73728-unknown cube's from the 18432-unknown cube's capture scaled "
@@ -110,7 +110,7 @@ def kernel_traffic(workload, n_pairs):
 # FP64 arithmetic instructions (DADD + DFMA + DMUL, thread level) per (near pair,
 # test point) of the mixed-precision near kernel, from an ncu capture of the
 # 18432-unknown cube (profiles/); valid while the near kernel's sources match.
-NEAR_FP64_OPS_HASH = "dfbefd861ef0f73f"
+NEAR_FP64_OPS_HASH = "9db20f98226f9710"
 NEAR_FP64_OPS_PER_TASK = (59829840 + 165940896 + 64560827) / (332388 * 4)  # 218.4
 FP64_OPS_PER_SM_CLOCK = 2  # GB300: 304 DFMA thread instructions per clock on 152 SMs (ncu peak_sustained)
 
@@ -169,10 +169,10 @@ def job_throughput(world, units_per_rank, seconds):
 
 def kernel_source_hash():
     """Hash of the sources that define the regular-pair table kernel (the
-    shared device code and the regular-pair kernel file)."""
+    shared device code, the regular-pair kernel file and the build flags)."""
     h = hashlib.sha256()
-    for name in ("gf_device.cuh", "gf_regular.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1901_04162_gb300", "csrc", name), "rb").read())
+    for name in ("csrc/gf_device.cuh", "csrc/gf_regular.cu", "build.py"):
+        h.update(open(os.path.join(ROOT, "paper_1901_04162_gb300", name), "rb").read())
     return h.hexdigest()[:16]
 
 
