@@ -43,6 +43,34 @@ def test_small_sphere_vs_oracle_gradient(table, near_fp64):
     assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
 
 
+def test_flagged_cells_gradient():
+    # A Green table of 40 base samples per wavelength (graded to the default
+    # tolerance): the interpolant stays accurate, but nearly every FP32
+    # lattice cell holds samples or needs its cubic term, so nearly every
+    # point pair's value and derivative come from the exact correction after
+    # the kernel's loop. The gradient must match the oracle as the default
+    # table's does, and the direct-evaluation adjoint to 2e-5 (a lost
+    # correction moves it by 2e-4).
+    xyz, tri = W.octasphere(2, 0.8)
+    xyz = W.jitter(xyz, tri, 0.03, 8)
+    om = O.Mesh(xyz, tri)
+    a = W.complex_gaussian(om.ne, 1)
+    b = W.complex_gaussian(om.ne, 2)
+    _, g_ref, dk_ref = om.loss_grad(K, 6, a, b)
+    m = gf.Mesh(xyz, tri)
+    gZ = torch.from_numpy(np.outer(a, np.conj(b)).astype(np.complex64)).cuda()
+    p = gf.gf_params_default(rule=6, green_n_per_lambda=40)
+    lo, hi = m.range(6, gf.GF_FP32)
+    g, dk = gf.gf_fill_backward(m, K, p, gf.Table(K, lo, hi, p), gZ)
+    gd, dkd = gf.gf_fill_backward(m, K, p, None, gZ)
+    torch.cuda.synchronize()
+    g, dk, gd, dkd = g.cpu().numpy(), float(dk.cpu()[0]), gd.cpu().numpy(), float(dkd.cpu()[0])
+    assert np.linalg.norm(g - g_ref) <= 1e-4 * np.linalg.norm(g_ref)
+    assert abs(dk - dk_ref) <= 1e-4 * abs(dk_ref)
+    assert np.linalg.norm(g - gd) <= 2e-5 * np.linalg.norm(gd)
+    assert abs(dk - dkd) <= 2e-5 * abs(dkd)
+
+
 def golden_grad_2048():
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "grad_sphere2048.txt")
     rows = [list(map(float, ln.split())) for ln in open(path)]
