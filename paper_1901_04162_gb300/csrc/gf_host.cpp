@@ -340,11 +340,13 @@ gf::TabView gf_table::One::view() const {
 
 namespace {
 
-// Device memory of destroyed tables and meshes kept for the next one of a
-// similar size on the same device (a table is rebuilt for every range / k;
-// cudaMalloc costs as much as building it). At most kPoolBlocks blocks, kPoolBytes bytes.
-constexpr int kPoolBlocks = 8;
-constexpr size_t kPoolBytes = size_t(1) << 30;
+// Device memory of destroyed tables and meshes (arrays and flagged-pair
+// lists) kept for the next one of a similar size on the same device (a table
+// is rebuilt for every range / k; cudaMalloc costs as much as building it,
+// and a device allocation between stream operations can serialize them). At
+// most kPoolBlocks blocks, kPoolBytes bytes.
+constexpr int kPoolBlocks = 16;
+constexpr size_t kPoolBytes = size_t(2) << 30;
 
 struct ArenaPool {
   std::mutex mu;
@@ -419,9 +421,13 @@ void free_mesh_device(gf_mesh* m) {
   if (m->d_dtri) cudaFree(m->d_dtri);
   if (m->d_dk) cudaFree(m->d_dk);
   if (m->h_range) cudaFreeHost(m->h_range);
-  if (m->d_fix) cudaFree(m->d_fix);
+  if (m->d_fix) {
+    cudaDeviceSynchronize();
+    arena_give(m->device, m->d_fix, m->fix_bytes);
+  }
   m->d_fix = nullptr;
   m->fix_cap = 0;
+  m->fix_bytes = 0;
   m->d_dtri = nullptr;
   m->d_dk = nullptr;
   m->h_range = nullptr;
@@ -1557,12 +1563,27 @@ gf_status gf_fill_parts(const gf_mesh* mc, double k, const gf_params* p, const g
     // CTAs scan their tasks again)
     int64_t need = fix_entries(m->nt, p->rule, tg.n_busy, tg.n_lat);
     if (const char* ev = std::getenv("GF_FIX_ENTRIES")) need = std::max<int64_t>(0, std::atoll(ev));
-    if (m->fix_cap < need) {
-      if (m->d_fix) cudaFree(m->d_fix);
+    if (m->fix_cap < need) {  // from the library's device pool (no allocation once warm)
+      if (m->d_fix) {
+        GF_CUDA(cudaDeviceSynchronize());
+        arena_give(m->device, m->d_fix, m->fix_bytes);
+      }
       m->d_fix = nullptr;
       m->fix_cap = 0;
-      if (cudaMalloc((void**)&m->d_fix, (size_t)need * sizeof(int2)) == cudaSuccess) m->fix_cap = need;
-      else (void)cudaGetLastError();
+      m->fix_bytes = 0;
+      size_t got = 0;
+      void* ptr = arena_take(m->device, (size_t)need * sizeof(int2), &got);
+      if (!ptr) {
+        got = (size_t)need * sizeof(int2);
+        if (cudaMalloc(&ptr, got) != cudaSuccess) {
+          (void)cudaGetLastError();
+          ptr = nullptr;
+          got = 0;
+        }
+      }
+      m->d_fix = static_cast<int2*>(ptr);
+      m->fix_bytes = got;
+      m->fix_cap = (int64_t)(got / sizeof(int2));
     }
     g.fix = need > 0 ? m->d_fix : nullptr;
     g.fix_cap = std::min(m->fix_cap, need);

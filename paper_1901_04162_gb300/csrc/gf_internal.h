@@ -372,6 +372,7 @@ struct gf_mesh {
   int32_t* d_range_list = nullptr;        // range scratch: block pairs that can hold an extreme, count last
   int2* d_fix = nullptr;                   // FP32 Green-table fill scratch: flagged point pairs (grown on demand)
   int64_t fix_cap = 0;
+  size_t fix_bytes = 0;                    // its block of the device pool
 };
 
 struct gf_table {
