@@ -23,8 +23,9 @@
  *     as interleaved (re, im).
  *   - Device pointers, sizes and the stream are the caller's; the caller owns
  *     every buffer it passes. The library owns its handles and the device
- *     memory inside them (geometry, near lists, table images), released by
- *     the matching *_destroy. Handles are bound to the device that was
+ *     memory inside them (geometry, near lists, table images, a mesh's list of
+ *     flagged point pairs), released by the matching *_destroy (kept in a
+ *     small pool for the next handle of a similar size). Handles are bound to the device that was
  *     current at creation; calls must be made with that device current.
  *   - Calls that launch kernels are asynchronous on `stream` (a cudaStream_t,
  *     NULL = legacy default stream) unless stated otherwise.
